@@ -90,7 +90,8 @@ def default_threads() -> int:
 
 def render(surfels, cam, pose, rule: Rule = Rule(), pixels=None, n_threads: int = 0):
     """Render colour, depth (literal sum of w z), normal, opacity, the final
-    transmittance and the number of blended surfels.
+    transmittance, the number of blended surfels and the smallest |cos|
+    between the ray and a blended surfel's normal (``min_cos``).
 
     ``pixels``: optional (P,2) int array of (x, y); then every output has a
     leading P axis instead of (H, W)."""
@@ -104,15 +105,18 @@ def render(surfels, cam, pose, rule: Rule = Rule(), pixels=None, n_threads: int 
     out_o = np.zeros(npx)
     out_t = np.zeros(npx)
     out_c = np.zeros(npx, np.int32)
+    out_m = np.zeros(npx)
     _lib().orc_render(surfels.n, _p(mu), _p(q), _p(sc), _p(op), _p(rgb), _p(_cam5(cam)), W, H,
                       _p(_d(pose.R)), _p(_d(pose.t)), _p(rule.vec()), int(rule.exact), npx,
                       _p(pix, ctypes.c_int), _p(out_rgb), _p(out_d), _p(out_n), _p(out_o), _p(out_t),
-                      _p(out_c, ctypes.c_int), int(n_threads or default_threads()))
+                      _p(out_c, ctypes.c_int), _p(out_m), int(n_threads or default_threads()))
     if pix is None:
         return dict(rgb=out_rgb.reshape(H, W, 3), depth=out_d.reshape(H, W),
                     normal=out_n.reshape(H, W, 3), opacity=out_o.reshape(H, W),
-                    t_final=out_t.reshape(H, W), count=out_c.reshape(H, W))
-    return dict(rgb=out_rgb, depth=out_d, normal=out_n, opacity=out_o, t_final=out_t, count=out_c)
+                    t_final=out_t.reshape(H, W), count=out_c.reshape(H, W),
+                    min_cos=out_m.reshape(H, W))
+    return dict(rgb=out_rgb, depth=out_d, normal=out_n, opacity=out_o, t_final=out_t, count=out_c,
+                min_cos=out_m)
 
 
 def render_bwd(surfels, cam, pose, g_rgb, g_depth, g_normal, g_opacity, rule: Rule = Rule(),

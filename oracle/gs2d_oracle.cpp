@@ -250,13 +250,16 @@ extern "C" {
 // Forward render of the listed pixels (all W*H pixels, row-major, if pix is
 // NULL).  cam5 = (fx, fy, cx, cy, near); rule4 = (alpha_min, alpha_max,
 // t_min, cutoff_r2); R9 row-major world->camera rotation, t3 translation.
-// Outputs per listed pixel: rgb[3], depth, normal[3], opacity, T_final and
-// the number of blended surfels.
+// Outputs per listed pixel: rgb[3], depth, normal[3], opacity, T_final, the
+// number of blended surfels and (if out_mincos is non-NULL) the smallest
+// |cos| between the ray and a blended surfel's normal -- near zero when a
+// surfel is seen edge-on, where the intersection is ill-conditioned.
 int orc_render(int n, const double* mu, const double* quat, const double* scale,
                const double* opacity, const double* rgb, const double* cam5, int W, int H,
                const double* R9, const double* t3, const double* rule4, int exact, int n_pix,
                const int* pix, double* out_rgb, double* out_depth, double* out_normal,
-               double* out_opacity, double* out_tfinal, int* out_count, int n_threads) {
+               double* out_opacity, double* out_tfinal, int* out_count, double* out_mincos,
+               int n_threads) {
   const Cam cam{cam5[0], cam5[1], cam5[2], cam5[3], cam5[4], W, H};
   const Rule rule{rule4[0], rule4[1], rule4[2], rule4[3], exact};
   const std::vector<CamSurfel> S = camera_surfels(n, mu, quat, scale, opacity, rgb, R9, t3);
@@ -270,11 +273,13 @@ int orc_render(int n, const double* mu, const double* quat, const double* scale,
       pixel_coord(k, np, pix, W, x, y);
       pixel_items(S, cam, rule, x, y, items);
       const int nb = blended_count(items, rule);
-      double T = 1.0, D = 0.0;
+      double T = 1.0, D = 0.0, mincos = 1.0;
       V3 C = mk(0, 0, 0), N = mk(0, 0, 0);
+      const V3 rr = mk((x - cam.cx) / cam.fx, (y - cam.cy) / cam.fy, 1.0);
       for (int m = 0; m < nb; ++m) {
         const Item& it = items[m];
         const CamSurfel& s = S[it.id];
+        mincos = std::min(mincos, std::fabs(dot(rr, s.tn_c)) / std::sqrt(dot(rr, rr)));
         const double w = it.a * T;
         C += w * s.col;
         D += w * it.z;
@@ -291,6 +296,7 @@ int orc_render(int n, const double* mu, const double* quat, const double* scale,
       out_opacity[k] = 1.0 - T;
       out_tfinal[k] = T;
       out_count[k] = nb;
+      if (out_mincos) out_mincos[k] = mincos;
     }
   }
   return 0;
@@ -440,16 +446,36 @@ int orc_render_bwd(int n, const double* mu, const double* quat, const double* sc
   return 0;
 }
 
+// Unit vectors (c, s) with A c + B s = rhs: rhs / |(A, B)| clamped to
+// [-1, 1] unless exact (then |rhs| must not exceed |(A, B)|).
+static int unit_solutions(double A, double B, double rhs, bool exact, double cs[2][2]) {
+  const double R = std::sqrt(A * A + B * B);
+  if (!(R > 0.0)) return 0;
+  double t = rhs / R;
+  if (exact && std::fabs(t) > 1.0) return 0;
+  t = std::max(-1.0, std::min(1.0, t));
+  const double q = std::sqrt(std::max(1.0 - t * t, 0.0));
+  const double hx = A / R, hy = B / R;
+  cs[0][0] = t * hx - q * hy;
+  cs[0][1] = t * hy + q * hx;
+  cs[1][0] = t * hx + q * hy;
+  cs[1][1] = t * hy - q * hx;
+  return 2;
+}
+
 // Conservative tile rectangle of each surfel's footprint, in FP64.
-// The footprint is the image of the disc u^2+v^2 <= rho^2 under the
-// homography (xz, yz, z) = K [m_u m_v mu_c] (u, v, 1) (Eq. homo), with
-// rho^2 = 1.01 * min(cutoff_r2, 2 ln(alpha / alpha_min)): beyond it no pixel
-// can pass the cutoff or the alpha_min test.  Its x-extent solves
-// l^T C* l = 0 for the vertical lines l = (1, 0, -x) with the dual conic
-// C* = A diag(1, 1, -1/rho^2) A^T (projective geometry of conics).
-// A disc that reaches the camera plane is not an ellipse in the image and
-// gets the whole image.  Pixels with centres inside [xmin, xmax] are
-// ceil(xmin - 0.5) .. floor(xmax - 0.5); tiles are those pixels // tile size.
+// A pixel can only pass the cutoff and alpha tests inside the disc
+// u^2 + v^2 <= rho^2, rho^2 = 1.01 min(cutoff_r2, 2 ln(alpha / alpha_min)),
+// and only where its hit depth is beyond the near plane; the footprint is the
+// image of that disc clipped to camera depth z >= 0.99 near.  Its boundary is
+// the circle P(c, s) = mu_c + rho (c m_u + s m_v) (c^2 + s^2 = 1) and the
+// chord where the circle meets z = 0.99 near.  The image coordinate
+// x = fx P_x / P_z + cx has its extremes over the (convex) clipped disc at
+// stationary points on the circle -- d/dt (P_x / P_z) = 0, which works out to
+//   c (m_vx mu_z - mu_x m_vz) + s (mu_x m_uz - m_ux mu_z) = rho (m_ux m_vz - m_vx m_uz)
+// -- when they lie in front of the clip plane, or at the chord's ends.  y
+// alike.  Pixels with centres inside [xmin, xmax] are ceil(xmin - 0.5) ..
+// floor(xmax - 0.5); tiles are those pixels // tile size.
 // rect = (tx0, ty0, tx1, ty1), or (1, 1, 0, 0) for a culled surfel.
 int orc_tile_rects(int n, const double* mu, const double* quat, const double* scale,
                    const double* opacity, const double* cam5, int W, int H, const double* R9,
@@ -459,6 +485,7 @@ int orc_tile_rects(int n, const double* mu, const double* quat, const double* sc
   std::vector<double> rgb0(3 * (size_t)n, 0.0);
   const std::vector<CamSurfel> S = camera_surfels(n, mu, quat, scale, opacity, rgb0.data(), R9, t3);
   const double amin = rule4[0], cutoff = rule4[3];
+  const double zmin = 0.99 * cam.near_z;
   for (int i = 0; i < n; ++i) {
     const CamSurfel& s = S[i];
     int* rc = rect_out + 4 * i;
@@ -470,38 +497,42 @@ int orc_tile_rects(int n, const double* mu, const double* quat, const double* sc
     if (!(s.mu_c.z > cam.near_z) || !(s.alpha >= amin)) continue;
     const double rho2 = 1.01 * std::min(cutoff, 2.0 * std::log(s.alpha / amin));
     if (!(rho2 > 0.0)) continue;
-    // rows of A = K M, M = [m_u m_v mu_c]
-    const double M[3][3] = {{s.m_u.x, s.m_v.x, s.mu_c.x},
-                            {s.m_u.y, s.m_v.y, s.mu_c.y},
-                            {s.m_u.z, s.m_v.z, s.mu_c.z}};
-    double A[3][3];
-    for (int c = 0; c < 3; ++c) {
-      A[0][c] = cam.fx * M[0][c] + cam.cx * M[2][c];
-      A[1][c] = cam.fy * M[1][c] + cam.cy * M[2][c];
-      A[2][c] = M[2][c];
+    const double rho = std::sqrt(rho2);
+    const V3 a = s.m_u, b = s.m_v, m = s.mu_c;
+    double cand[6][2];
+    int nc = 0;
+    double cs[2][2];
+    int k = unit_solutions(b.x * m.z - m.x * b.z, m.x * a.z - a.x * m.z, rho * (a.x * b.z - b.x * a.z),
+                           false, cs);
+    for (int j = 0; j < k; ++j) { cand[nc][0] = cs[j][0]; cand[nc][1] = cs[j][1]; ++nc; }
+    const bool open_x = k == 0;
+    k = unit_solutions(b.y * m.z - m.y * b.z, m.y * a.z - a.y * m.z, rho * (a.y * b.z - b.y * a.z),
+                       false, cs);
+    for (int j = 0; j < k; ++j) { cand[nc][0] = cs[j][0]; cand[nc][1] = cs[j][1]; ++nc; }
+    const bool open_y = k == 0;
+    k = unit_solutions(a.z, b.z, (zmin - m.z) / rho, true, cs);
+    for (int j = 0; j < k; ++j) { cand[nc][0] = cs[j][0]; cand[nc][1] = cs[j][1]; ++nc; }
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    bool any = false;
+    for (int j = 0; j < nc; ++j) {
+      const V3 P = m + rho * (cand[j][0] * a + cand[j][1] * b);
+      if (!(P.z >= zmin * (1.0 - 1e-9))) continue;
+      const double x = cam.fx * P.x / P.z + cam.cx, y = cam.fy * P.y / P.z + cam.cy;
+      x0 = std::min(x0, x);
+      x1 = std::max(x1, x);
+      y0 = std::min(y0, y);
+      y1 = std::max(y1, y);
+      any = true;
     }
-    double C[3][3];
-    for (int p = 0; p < 3; ++p)
-      for (int q = 0; q < 3; ++q)
-        C[p][q] = A[p][0] * A[q][0] + A[p][1] * A[q][1] - A[p][2] * A[q][2] / rho2;
-    double x0, x1, y0, y1;
-    if (!(C[2][2] < 0.0)) {
-      x0 = 0.0;
-      x1 = W;
-      y0 = 0.0;
-      y1 = H;
-    } else {
-      const double dx = std::sqrt(std::max(C[0][2] * C[0][2] - C[0][0] * C[2][2], 0.0));
-      const double dy = std::sqrt(std::max(C[1][2] * C[1][2] - C[1][1] * C[2][2], 0.0));
-      const double xa = (C[0][2] + dx) / C[2][2], xb = (C[0][2] - dx) / C[2][2];
-      const double ya = (C[1][2] + dy) / C[2][2], yb = (C[1][2] - dy) / C[2][2];
-      x0 = std::min(xa, xb);
-      x1 = std::max(xa, xb);
-      y0 = std::min(ya, yb);
-      y1 = std::max(ya, yb);
+    if (!any) continue;
+    if (open_x) {
+      x0 = -1e300;
+      x1 = 1e300;
     }
-    if (!std::isfinite(x0) || !std::isfinite(x1) || !std::isfinite(y0) || !std::isfinite(y1))
-      continue;
+    if (open_y) {
+      y0 = -1e300;
+      y1 = 1e300;
+    }
     const double i0 = std::max(std::ceil(x0 - 0.5), 0.0), i1 = std::min(std::floor(x1 - 0.5), W - 1.0);
     const double j0 = std::max(std::ceil(y0 - 0.5), 0.0), j1 = std::min(std::floor(y1 - 0.5), H - 1.0);
     if (i0 > i1 || j0 > j1) continue;

@@ -212,3 +212,28 @@ def test_tracking_converges_from_perturbation(orc):
     pose, losses = orc.track(s, cam, start, img["rgb"], obs_d, n_iter=100, lr=1e-3)
     et, er = orc.pose_error(pose, gt)
     assert et < 0.01 and er < 0.5, (e0, (et, er), losses[:3], losses[-3:])
+
+
+def test_tile_rects_cover_surfels_reaching_past_the_camera_plane(orc):
+    """Large surfels beside the camera whose discs reach behind it: the
+    clipped-disc footprint still covers every pixel they touch, and is far
+    smaller than the image."""
+    rng = np.random.default_rng(4)
+    n = 40
+    mu = np.stack([rng.uniform(-0.4, 0.4, n), rng.uniform(-0.3, 0.3, n), rng.uniform(0.06, 0.2, n)], 1)
+    q = rng.normal(size=(n, 4))
+    s = scenes.Surfels(mu, q, rng.uniform(0.05, 0.15, (n, 2)), rng.uniform(0.5, 0.95, n),
+                       rng.uniform(size=(n, 3)))
+    cam = scenes.Camera(60.0, 60.0, 40.0, 30.0, 80, 60)
+    rect, _ = orc.tile_rects(s, cam, scenes.identity_pose(), orc.Rule(), (8, 8))
+    covered = 0
+    for i in range(n):
+        out = orc.render(s.subset(np.array([i])), cam, scenes.identity_pose())
+        ys, xs = np.nonzero(out["opacity"] > 0)
+        if len(xs) == 0:
+            continue
+        covered += 1
+        r = rect[i]
+        assert r[0] <= xs.min() // 8 and r[2] >= xs.max() // 8
+        assert r[1] <= ys.min() // 8 and r[3] >= ys.max() // 8
+    assert covered > 10
