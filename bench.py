@@ -1,0 +1,498 @@
+#!/usr/bin/env python
+"""Benchmark of the 2DGS rasterizer hot path: frame-to-map tracking on the
+tracking-scale workload (200k-surfel synthetic room, 640x480, fx = fy = 525,
+target RGB-D rendered at ground truth with 1 mm depth noise, 100 pose-only
+iterations from a 2 cm / 1 degree perturbation).
+
+One step = one tracking frame = 100 iterations of project -> bin_sort ->
+render_fwd -> tracking loss -> render_bwd (pose) -> AdamW + retraction, all
+in one gs2d_track_step call.  The metric is 2DGS fwd+bwd Mpix/s
+(iterations x 640 x 480 / time); the tracking time to reach 1 cm / 0.5
+degree is reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (the path has no cross-GPU exchange), one
+rank per GPU under torch.distributed.run; rank 0 prints one JSON line.
+``--impl reference`` times the FP64 CPU oracle on a bounded pixel sample of
+the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "2DGS fwd+bwd Mpix/s; tracking ms/frame to 1 cm/0.5° error vs plain loop"
+UNIT = "Mpix/s"
+N_SURFELS = 200_000
+N_ITER = 100
+WORKLOAD = ("tracking-scale room: 200k surfels on a 5x4x3 m room with 20 boxes/spheres, 640x480, "
+            "fx=fy=525, target at ground truth + N(0, 1 mm) depth noise, 100 pose-only iterations "
+            "from a 2 cm / 1 deg perturbation")
+ORACLE_CROP = 32          # reference arm / cpu baseline: a 32x32 pixel crop per step
+L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes per launch of the roofline kernel from an ncu capture of the
+# same workload (profiles/render_fwd_tracking_640x480.md); None if the kernel
+# changed since.
+TRAFFIC_BYTES = {"render_fwd": None, "render_bwd_pose": None}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    return ap.parse_args()
+
+
+def _dist():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# workload
+# --------------------------------------------------------------------------
+def make_frames(n_frames: int, rank: int):
+    """Seeded frames: ground-truth pose, start pose (2 cm / 1 deg off) and the
+    observed RGB-D frame rendered on the GPU at ground truth (+1 mm noise)."""
+    import torch
+    from paper_2506_00970_gb300 import gs2d, scenes
+    s = scenes.room_scene(0, N_SURFELS)
+    cam = scenes.tracking_camera()
+    ds = gs2d.DeviceSurfels(s)
+    r = gs2d.Rasterizer(cam, ds.n)
+    frames = []
+    kmax = 0
+    for f in range(n_frames):
+        seed = 1000 * rank + f
+        gt = scenes.room_pose(100 + seed)
+        start = scenes.perturb_pose(gt, 0.02, 1.0, seed=5000 + seed)
+        out = r.forward(ds, gs2d.pose_tensor(gt))
+        noise = np.random.default_rng(9000 + seed).normal(0.0, 1e-3, (cam.height, cam.width))
+        obs_d = (out["depth"] / out["opacity"].clamp_min(1e-6)).cpu().numpy() + noise
+        obs_d = torch.tensor(obs_d.astype(np.float32), device="cuda")
+        frames.append(dict(gt=gt, start=start, obs_rgb=out["rgb"].clone(), obs_depth=obs_d,
+                           start_t=gs2d.pose_tensor(start)))
+        r.forward(ds, gs2d.pose_tensor(start))
+        kmax = max(kmax, int(r.n_isect.item()))
+    torch.cuda.synchronize()
+    return s, cam, ds, r, frames, kmax
+
+
+def first_below(ph, gt, tcm=0.01, tdeg=0.5):
+    for it in range(ph.shape[0]):
+        et, er = _pose_err_np(ph[it], gt)
+        if et < tcm and er < tdeg:
+            return it + 1
+    return None
+
+
+def _pose_err_np(row, gt):
+    R = row[:9].reshape(3, 3)
+    t = row[9:]
+    c = -R.T @ t
+    cg = -gt.R.T @ gt.t
+    cosang = np.clip((np.trace(R @ gt.R.T) - 1) / 2, -1.0, 1.0)
+    return float(np.linalg.norm(c - cg)), float(np.degrees(np.arccos(cosang)))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    # 152 SMs x 128 FP32 lanes x 2 flops per FMA per clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# FP32 operations per (pixel, surfel) pair of the compositing loop, counted
+# from the arithmetic the method needs (FMA = 2; MUFU rcp/exp not counted):
+#  every evaluated pair: the linear map p (6 FMA = 12), u, v (2), u^2 + v^2
+#  (FMA + mul = 3) -> 17; pairs inside the cutoff radius add z, the exp
+#  argument, alpha G and the clamp -> 4; blended pairs add 1 - a, T (1 - a),
+#  w, colour, depth and normal accumulation (3 + 6 + 2 + 6) -> 17.  The
+#  pose-only backward adds per replayed blended pair ~80 (transmittance
+#  recovery, dL/da, the chain through G, q, beta, Gv, X x Gv, t_nc x g and
+#  the 6-vector accumulation); its evaluated pairs are bounded by the
+#  forward's counts.
+FLOPS_EVAL, FLOPS_IN, FLOPS_BLEND, FLOPS_BWD_BLEND = 17, 4, 17, 80
+
+
+def run_ours(args):
+    import torch
+    from paper_2506_00970_gb300 import build as _b
+    _b.build()
+    from paper_2506_00970_gb300 import gs2d, scenes
+    ws_n, rank, local = _dist()
+    torch.cuda.set_device(local)
+    W_ = max(args.warmup, 3)
+    K = args.steps
+    n_frames = min(max(K, 4), 20)
+    s, cam, ds, r, frames, kmax = make_frames(n_frames, rank)
+    ccam, cfg = gs2d.camera(cam), gs2d.default_config()
+    prm = gs2d.default_track_params(stop_tol=0.0)     # always the full 100 iterations
+    cap = int(kmax * 1.5) + 4096
+    ws = torch.empty(gs2d.gs2d_track_workspace(ds.n, cap, ccam, cfg), dtype=torch.uint8, device="cuda")
+    lh = torch.zeros(N_ITER, device="cuda")
+    ph = torch.zeros(N_ITER, 12, device="cuda")
+    pose = torch.empty(12, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(f):
+        fr = frames[f % n_frames]
+        pose.copy_(fr["start_t"])
+        gs2d.gs2d_track_step(ds, ccam, cfg, prm, pose, fr["obs_rgb"], fr["obs_depth"], N_ITER, cap,
+                             lh, ph, ws)
+
+    for i in range(W_):
+        step(i)
+    torch.cuda.synchronize()
+    st = int(gs2d.gs2d_track_status(ws).item())
+    if st not in (0, gs2d.CONVERGED):
+        raise RuntimeError(f"track status {st}")
+
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    hist = []
+    if ws_n > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for i in range(K):
+            flush.zero_()
+            e0[i].record(stream)
+            step(i)
+            e1[i].record(stream)
+            hist.append(ph.clone())
+        torch.cuda.synchronize()
+    if ws_n > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - t_wall
+    st = int(gs2d.gs2d_track_status(ws).item())
+    if st not in (0, gs2d.CONVERGED):
+        raise RuntimeError(f"track status {st}")
+    step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+    tot_ms = torch.tensor([sum(step_ms)], device="cuda", dtype=torch.float64)
+    if ws_n > 1:
+        torch.distributed.all_reduce(tot_ms, op=torch.distributed.ReduceOp.MAX)
+    tot_ms = float(tot_ms.item())
+    P = cam.width * cam.height
+    value = ws_n * K * N_ITER * P / (tot_ms / 1e3) / 1e6
+    ms_step = tot_ms / K
+
+    # tracking accuracy and time to 1 cm / 0.5 deg
+    its, fin = [], []
+    for i, h in enumerate(hist):
+        fr = frames[i % n_frames]
+        h = h.cpu().numpy().astype(np.float64)
+        it = first_below(h, fr["gt"])
+        its.append(it if it is not None else np.nan)
+        fin.append(_pose_err_np(h[-1], fr["gt"]))
+    ms_iter = ms_step / N_ITER
+    it_med = float(np.nanmedian(its)) if np.isfinite(its).any() else None
+    tracking = {
+        "ms_per_frame_100_iters": ms_step,
+        "ms_per_iter": ms_iter,
+        "iters_to_1cm_0.5deg_median": it_med,
+        "ms_to_1cm_0.5deg_median": None if it_med is None else it_med * ms_iter,
+        "frames_reaching_threshold": int(np.isfinite(its).sum()),
+        "frames": len(its),
+        "final_err_cm_median": float(np.median([e[0] for e in fin]) * 100),
+        "final_err_deg_median": float(np.median([e[1] for e in fin])),
+        "learned_proposal": None,
+    }
+
+    # end to end through the C ABI from pinned host buffers
+    h_rgb = [frames[f]["obs_rgb"].cpu().pin_memory() for f in range(n_frames)]
+    h_d = [frames[f]["obs_depth"].cpu().pin_memory() for f in range(n_frames)]
+    h_pose = [frames[f]["start_t"].cpu().pin_memory() for f in range(n_frames)]
+    d_rgb = torch.empty_like(frames[0]["obs_rgb"])
+    d_d = torch.empty_like(frames[0]["obs_depth"])
+    out_pose = torch.empty(12).pin_memory()
+    out_loss = torch.empty(1).pin_memory()
+
+    def step_e2e(f):
+        f = f % n_frames
+        d_rgb.copy_(h_rgb[f], non_blocking=True)
+        d_d.copy_(h_d[f], non_blocking=True)
+        pose.copy_(h_pose[f], non_blocking=True)
+        gs2d.gs2d_track_step(ds, ccam, cfg, prm, pose, d_rgb, d_d, N_ITER, cap, lh, None, ws)
+        out_pose.copy_(pose, non_blocking=True)
+        out_loss.copy_(lh[-1:], non_blocking=True)
+
+    for i in range(2):
+        step_e2e(i)
+    torch.cuda.synchronize()
+    ee0 = torch.cuda.Event(enable_timing=True)
+    ee1 = torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for i in range(K):
+        flush.zero_()
+        ee0.record(stream)
+        step_e2e(i)
+        ee1.record(stream)
+        ee1.synchronize()
+        e2e_ms += ee0.elapsed_time(ee1)
+    e2e_t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+    if ws_n > 1:
+        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+    e2e_ms = float(e2e_t.item())
+    e2e_value = ws_n * K * N_ITER * P / (e2e_ms / 1e3) / 1e6
+    h2d = h_rgb[0].numel() * 4 + h_d[0].numel() * 4 + 12 * 4
+    d2h = 12 * 4 + 4
+
+    roof = roofline(r, ds, frames, cam, cfg, stream, ms_iter)
+
+    if rank == 0:
+        clocks = clk.summary()
+        pk, src = peaks()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": K,
+            "warmup": W_, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "surfels": N_SURFELS, "width": cam.width,
+                       "height": cam.height, "iterations_per_step": N_ITER, "frames": n_frames,
+                       "tile": "16x16", "l2": "256 MB buffer written between steps",
+                       "parallelism": f"replicas x{ws_n}"},
+            "tracking": tracking,
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / K},
+            "gpu_launches": K * (1 + N_ITER * LAUNCHES_PER_ITER),
+            "roofline": roof["main"],
+            "roofline_other": roof["other"],
+            "wall_s": wall,
+            "peak_source": src,
+        }
+        line["cpu_baseline"] = cpu_baseline(s, cam, frames[0])
+        print(json.dumps(line))
+    if ws_n > 1:
+        torch.distributed.destroy_process_group()
+
+
+# kernels per tracking iteration: project 1; bin_sort 11 (init, depth keys,
+# 4 depth passes, emit scan, emit, 2 tile passes, finalize); render_fwd 1;
+# tracking loss 2; render_bwd (pose) 2; AdamW + retraction 1.  Plus one reset
+# per frame.
+LAUNCHES_PER_ITER = 18
+
+
+def roofline(r, ds, frames, cam, cfg, stream, ms_iter):
+    """Average duration of the compositing kernels on the workload's start
+    poses (CUDA events around each launch on the launching stream), their
+    algorithmic FP32 work from the pair counts, against the FP32 peak."""
+    import torch
+    from paper_2506_00970_gb300 import gs2d
+    pk, src = peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(sm_mhz)
+    counts = torch.zeros(3, dtype=torch.int64, device="cuda")
+    g_rgb = torch.zeros(cam.height, cam.width, 3, device="cuda")
+    g_d = torch.zeros(cam.height, cam.width, device="cuda")
+    g_o = torch.zeros(cam.height, cam.width, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    lws = torch.empty(1 << 16, dtype=torch.uint8, device="cuda")
+    prm = gs2d.default_track_params()
+    fwd_ms, bwd_ms, work_f, work_b = [], [], [], []
+    R = 10
+    for fr in frames[:4]:
+        pt = fr["start_t"]
+        r.forward(ds, pt)
+        gs2d.gs2d_tracking_loss(r.rgb, r.depth, r.normal, r.opacity, fr["obs_rgb"], fr["obs_depth"],
+                                r.cam, prm, g_rgb, g_d, g_o, loss, lws)
+        gs2d.gs2d_render_count(r.proj, r.bins, r.cam, r.cfg, counts)
+        torch.cuda.synchronize()
+        E, Ein, B = (int(x) for x in counts.cpu().numpy())
+        work_f.append(FLOPS_EVAL * E + FLOPS_IN * Ein + FLOPS_BLEND * B)
+        work_b.append(FLOPS_EVAL * E + FLOPS_IN * Ein + FLOPS_BWD_BLEND * B)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * R)]
+        for k in range(R):
+            ev[2 * k].record(stream)
+            gs2d.gs2d_render_fwd(r.proj, r.bins, r.cam, r.cfg, r.rgb, r.depth, r.normal, r.opacity,
+                                 r.t_final, r.n_last)
+            ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+        fwd_ms.append(np.mean([ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(R)]))
+        for k in range(R):
+            ev[2 * k].record(stream)
+            r.backward(ds, pt, g_rgb, g_d, None, g_o, full=False)
+            ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+        bwd_ms.append(np.mean([ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(R)]))
+    tf = np.mean(fwd_ms) / 1e3
+    tb = np.mean(bwd_ms) / 1e3
+    af = np.mean(work_f) / tf / 1e12
+    ab = np.mean(work_b) / tb / 1e12
+    fwd = {"kernel": "render_fwd_kernel", "bound": "alu", "achieved": af, "peak": peak,
+           "unit": "TFLOP/s", "frac": af / peak, "traffic": TRAFFIC_BYTES["render_fwd"],
+           "launch_ms": tf * 1e3, "share_of_iter": tf * 1e3 / ms_iter,
+           "peak_note": f"FP32 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz"}
+    bwd = {"kernel": "render_bwd_kernel<pose> + pose_reduce", "bound": "alu", "achieved": ab,
+           "peak": peak, "unit": "TFLOP/s", "frac": ab / peak,
+           "traffic": TRAFFIC_BYTES["render_bwd_pose"], "launch_ms": tb * 1e3,
+           "share_of_iter": tb * 1e3 / ms_iter}
+    main, other = (fwd, bwd) if tf >= tb else (bwd, fwd)
+    return {"main": main, "other": other}
+
+
+def cpu_baseline(s, cam, fr):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    forward + pose backward of a 32x32 pixel crop of one frame against all
+    200k surfels (every host core via OpenMP)."""
+    import oracle
+    from paper_2506_00970_gb300 import scenes
+    y0, x0 = cam.height // 2 - ORACLE_CROP // 2, cam.width // 2 - ORACLE_CROP // 2
+    ys, xs = np.mgrid[y0:y0 + ORACLE_CROP, x0:x0 + ORACLE_CROP]
+    pix = np.stack([xs.ravel(), ys.ravel()], 1).astype(np.int32)
+    obs_rgb = fr["obs_rgb"].cpu().numpy()[ys, xs].reshape(-1, 3)
+    obs_d = fr["obs_depth"].cpu().numpy()[ys, xs].reshape(-1)
+    cores = oracle.default_threads()
+    t0 = time.perf_counter()
+    img = oracle.render(s, cam, fr["start"], pixels=pix)
+    # per-pixel L1 gradient of the tracking loss on the sample (Eq. tracking_loss)
+    Dh = img["depth"] / np.maximum(img["opacity"], 1e-6)
+    m = (img["opacity"] > 0.95).astype(float)
+    g_rgb = np.sign(img["rgb"] - obs_rgb) * m[:, None]
+    g_d = np.sign(Dh - obs_d) * m / np.maximum(img["opacity"], 1e-6)
+    oracle.render_bwd(s, cam, fr["start"], g_rgb, g_d, np.zeros_like(g_rgb), np.zeros_like(g_d),
+                      pixels=pix)
+    dt = time.perf_counter() - t0
+    return {"value": len(pix) / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 fwd + pose bwd of a {ORACLE_CROP}x{ORACLE_CROP} crop of one 640x480 "
+                      f"frame, all {N_SURFELS} surfels", "seconds": dt}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is the bounded sample of the
+    workload (see cpu_baseline), timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2506_00970_gb300 import scenes
+    import oracle
+    s = scenes.room_scene(0, N_SURFELS)
+    cam = scenes.tracking_camera()
+    gt = scenes.room_pose(100)
+    start = scenes.perturb_pose(gt, 0.02, 1.0, seed=5000)
+    y0, x0 = cam.height // 2 - ORACLE_CROP // 2, cam.width // 2 - ORACLE_CROP // 2
+    ys, xs = np.mgrid[y0:y0 + ORACLE_CROP, x0:x0 + ORACLE_CROP]
+    pix = np.stack([xs.ravel(), ys.ravel()], 1).astype(np.int32)
+    tgt = oracle.render(s, cam, gt, pixels=pix)
+    obs_rgb = tgt["rgb"]
+    obs_d = tgt["depth"] / np.maximum(tgt["opacity"], 1e-6)
+
+    def one():
+        img = oracle.render(s, cam, start, pixels=pix)
+        Dh = img["depth"] / np.maximum(img["opacity"], 1e-6)
+        m = (img["opacity"] > 0.95).astype(float)
+        g_rgb = np.sign(img["rgb"] - obs_rgb) * m[:, None]
+        g_d = np.sign(Dh - obs_d) * m / np.maximum(img["opacity"], 1e-6)
+        oracle.render_bwd(s, cam, start, g_rgb, g_d, np.zeros_like(g_rgb), np.zeros_like(g_d),
+                          pixels=pix)
+
+    for _ in range(max(args.warmup, 1)):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = time.perf_counter() - t0
+    value = args.steps * len(pix) / dt / 1e6
+    cores = oracle.default_threads()
+    sample = (f"FP64 fwd + pose bwd of a {ORACLE_CROP}x{ORACLE_CROP} crop per step, all "
+              f"{N_SURFELS} surfels")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

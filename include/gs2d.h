@@ -1,0 +1,239 @@
+/*
+ * gs2d.h -- C ABI of the GB300-native differentiable 2D Gaussian surfel
+ * rasterizer (the data-parallel hot path of 2DGS-SLAM, arXiv 2506.00970).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * All array arguments are DEVICE pointers owned by the caller.  The library
+ *    never allocates or frees device memory and never synchronises the host;
+ *    every call only enqueues kernels on `stream`.
+ *  * Return value: GS2D_OK if all kernels were enqueued, GS2D_ERR_INVALID_ARG
+ *    for a NULL/ill-sized argument (nothing is launched), GS2D_ERR_WORKSPACE
+ *    if the workspace is NULL or too small (the required size is written to
+ *    *ws_needed when that pointer is non-NULL; nothing is launched),
+ *    GS2D_ERR_CUDA if a launch failed.  Conditions only the device can see
+ *    (intersection capacity overflow, non-finite pose) are reported through
+ *    the device status word of `gs2d_bins.status` (GS2D_ERR_CAPACITY,
+ *    GS2D_ERR_NONFINITE); later kernels that read it skip their work.
+ *  * Layouts: surfel arrays are structure-of-arrays, C-contiguous FP32;
+ *    images are H x W row-major, channel-last (rgb and normal are H x W x 3).
+ *  * Poses are world->camera T_cw as 12 device floats: R row-major (9) then
+ *    t (3), x_c = R x_w + t; camera axes x right, y down, z forward.
+ *  * Surfel parameters are *activated*: opacity in (0,1), scales > 0.  The
+ *    quaternion (w, x, y, z) need not be normalised; the kernels normalise it
+ *    and gradients are w.r.t. the raw quaternion.
+ *
+ * The operations follow the paper's statement of the problem:
+ *  surfel g = (mu, R = [t_u t_v t_n], s_u, s_v, c, alpha) (Sec. III-A,
+ *  Eq. Puv), camera-space splat H_c = T_cw H (Eq. hc), pixel ray
+ *  x = (xz, yz, z, 1) = W T_cw H (u, v, 0, 1) (Eq. homo, wth), front-to-back
+ *  alpha blending of colour, depth, normal and opacity (Eq. alpha_blending),
+ *  gradients to the pose through the left perturbation Exp(tau) o T_cw,
+ *  tau = (rho, theta) (Sec. III-B, Eq. derivatives), the masked tracking loss
+ *  (Eq. tracking_loss) and AdamW pose tracking (Sec. III-D).
+ */
+#ifndef GS2D_H_
+#define GS2D_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* gs2d_stream; /* a cudaStream_t (NULL = legacy default stream) */
+
+typedef enum {
+  GS2D_OK = 0,
+  GS2D_ERR_INVALID_ARG = 1,
+  GS2D_ERR_WORKSPACE = 2,
+  GS2D_ERR_CAPACITY = 3,
+  GS2D_ERR_CUDA = 4,
+  GS2D_ERR_TIMEOUT = 5,
+  GS2D_ERR_NONFINITE = 6
+} gs2d_status;
+
+/* Pinhole intrinsics (the camera-to-image matrix W of Eq. homo).  Pixel
+ * (i, j) has its centre at (i + 0.5, j + 0.5); near_z culls surfel centres
+ * and ray intersections at camera depth <= near_z. */
+typedef struct {
+  float fx, fy, cx, cy;
+  int width, height;
+  float near_z;
+} gs2d_camera;
+
+/* Surfel map, structure of arrays (Sec. III-A): mu [n*3], quat [n*4]
+ * (w,x,y,z), scale [n*2] (s_u, s_v), opacity [n], rgb [n*3]. */
+typedef struct {
+  const float* mu;
+  const float* quat;
+  const float* scale;
+  const float* opacity;
+  const float* rgb;
+  int n;
+} gs2d_surfels;
+
+/* Tiling and compositing constants.  The paper leaves the numerical rules
+ * of its blending open; the defaults (gs2d_default_config) are
+ * alpha_min = 1/255 (skip), alpha_max = 0.99 (clamp), t_min = 1e-4 (stop
+ * before the transmittance would fall below it) and cutoff_r2 = 9
+ * (u^2 + v^2 beyond three standard deviations is skipped).  tile_w x tile_h
+ * is one of 16x16, 8x32, 32x8; px_per_thread in {1, 2, 4} (autotuned). */
+typedef struct {
+  int tile_w, tile_h, px_per_thread;
+  float alpha_min, alpha_max, t_min, cutoff_r2;
+} gs2d_config;
+
+/* Per-surfel projected record written by gs2d_project: 32 floats (128 B,
+ * 16-byte aligned).  Image coordinates x' = x - cx, y' = y - cy are relative
+ * to the principal point.  Float slots:
+ *   0-1   (x0, y0): projected centre of the surfel (x', y')
+ *   2     p2c = det / mu_c.z
+ *   3-8   c1, c2: the homogeneous (u, v, 1) of the ray through (x', y') is
+ *         p = (x' - x0) c1 + (y' - y0) c2 + (0, 0, p2c) (the inverse of the
+ *         homography of Eq. wth up to scale): u = p0/p2, v = p1/p2
+ *   9     det (intersection depth z = det / p2)      10  alpha
+ *   11-13 rgb          14-16 t_nc (camera-space normal)
+ *   17-19 n = s_u t_uc x s_v t_vc   20-22 dual tangent d_u   23-25 dual d_v
+ *         (d_u . s_u t_uc = 1, d_u . s_v t_vc = 0, d_u . n = 0; d_v alike)
+ *   26    centre depth mu_c.z (the sort key)          27  unused
+ *   28    uint32 tx0 | ty0 << 16,  29  uint32 tx1 | ty1 << 16  (inclusive tile
+ *         rectangle; tx0 > tx1 marks a culled surfel)
+ *   30    uint32 i0 | i1 << 16,    31  uint32 j0 | j1 << 16  (inclusive pixel
+ *         columns / rows of the footprint). */
+#define GS2D_PROJ_FLOATS 32
+
+/* Binning output of gs2d_bin_sort.  capacity bounds the number of
+ * (tile, surfel) intersections K.  keys may be NULL. */
+typedef struct {
+  uint64_t* keys;        /* [capacity] tile << 32 | float bits of mu_c.z       */
+  uint32_t* vals;        /* [capacity] surfel id per sorted position            */
+  uint32_t* isect_emit;  /* [capacity] emission index of each sorted position   */
+  uint32_t* surfel_off;  /* [n] first emission index of surfel i (its k_i
+                            intersections are emission indices off..off+k_i-1) */
+  int32_t* tile_ranges;  /* [2 * n_tiles] [start, end) of each tile's list       */
+  int32_t* n_isect;      /* [1] K (the needed count when K > capacity)          */
+  int32_t* status;       /* [1] device status word (gs2d_status)                */
+  size_t capacity;
+} gs2d_bins;
+
+/* Tracking hyper-parameters (Sec. III-D).  The paper names AdamW and
+ * n_iter = 120 (Table I) but not lr, betas or the stop rule; defaults:
+ * lr 1e-3, betas (0.9, 0.999), eps 1e-8, weight decay 0, stop when
+ * |tau| < 1e-5, lambda_d 1, opacity mask 0.95 (Eq. opacity_mask),
+ * depth_mode 1 (depth loss on D/O). */
+typedef struct {
+  float lambda_d, lr, beta1, beta2, eps, weight_decay, stop_tol, opacity_thresh;
+  int depth_mode;
+} gs2d_track_params;
+
+gs2d_config gs2d_default_config(void);
+gs2d_track_params gs2d_default_track_params(void);
+const char* gs2d_status_string(int status);
+/* Tiles per row / column for a camera and config. */
+int gs2d_tiles_x(const gs2d_camera* cam, const gs2d_config* cfg);
+int gs2d_tiles_y(const gs2d_camera* cam, const gs2d_config* cfg);
+
+/* Per-surfel projection (Eq. hc, homo, wth; footprint bound of the 3-sigma
+ * disc).  pose: device [12].  proj_out: device [n * GS2D_PROJ_FLOATS] floats;
+ * tiles_per_surfel_out: device int32 [n], the number of tiles of the
+ * surfel's rectangle (0 if culled).  One thread per surfel. */
+int gs2d_project(const gs2d_surfels* s, const gs2d_camera* cam, const float* pose,
+                 const gs2d_config* cfg, float* proj_out, int32_t* tiles_per_surfel_out,
+                 gs2d_stream stream);
+
+/* Tile binning and depth ordering ("sorts them by depth", Sec. III-A): every
+ * surfel with k_i > 0 emits one intersection per tile of its rectangle; the
+ * intersections are ordered by (tile, mu_c.z bits, surfel id) -- a stable
+ * sort by tile of the depth-ordered emission -- with hand-written LSD radix
+ * passes.  proj: device [n * GS2D_PROJ_FLOATS] (only slots 26, 28, 29 are
+ * read).  tiles_per_surfel: device [n], must equal the rectangle's tile count.
+ * Workspace: gs2d_bin_sort_workspace(n, capacity) bytes. */
+size_t gs2d_bin_sort_workspace(int n, size_t capacity);
+int gs2d_bin_sort(const float* proj, const int32_t* tiles_per_surfel, int n,
+                  const gs2d_camera* cam, const gs2d_config* cfg, void* workspace,
+                  size_t ws_bytes, size_t* ws_needed, const gs2d_bins* bins, gs2d_stream stream);
+
+/* Front-to-back compositing (Eq. alpha_blending) of colour (rgb [H*W*3]),
+ * literal depth D = sum w z ([H*W]), normal sum w t_nc ([H*W*3]) and opacity
+ * O = 1 - T ([H*W]); also the final transmittance t_final [H*W] and n_last
+ * [H*W] (one past the last blended position in the pixel's tile list), the
+ * state the backward pass replays from.  One thread block per tile. */
+int gs2d_render_fwd(const float* proj, const gs2d_bins* bins, const gs2d_camera* cam,
+                    const gs2d_config* cfg, float* rgb, float* depth, float* normal,
+                    float* opacity, float* t_final, uint32_t* n_last, gs2d_stream stream);
+
+/* Work counter of gs2d_render_fwd (diagnostic, same loop and culling):
+ * counts[0] = evaluated (pixel, surfel) pairs, counts[1] = pairs inside the
+ * cutoff radius, counts[2] = blended pairs; device uint64 [3], zeroed here.
+ * The roofline of the compositing kernels is stated per these counts. */
+int gs2d_render_count(const float* proj, const gs2d_bins* bins, const gs2d_camera* cam,
+                      const gs2d_config* cfg, unsigned long long* counts, gs2d_stream stream);
+
+/* Backward of gs2d_render_fwd (Sec. III-B): replays compositing back to
+ * front from (t_final, n_last) and returns dL/d(mu, quat, scale, opacity,
+ * rgb) per surfel and dL/dtau (rho, theta) of the pose (Eq. derivatives)
+ * given dL/d(rgb, depth, normal, opacity) of the images (d_normal and
+ * d_opacity may be NULL = zero).  Per-(tile, surfel) partial sums are formed
+ * with warp shuffles and written once; a second, fixed-order pass reduces
+ * them per surfel, so the result is deterministic.  If d_mu, d_quat,
+ * d_scale, d_opac and d_rgb are all NULL only d_pose6 is computed (tracking
+ * mode: no per-surfel partials).  pose: device [12]; d_pose6: device [6] or
+ * NULL.  Workspace: gs2d_render_bwd_workspace(n, capacity, n_tiles). */
+size_t gs2d_render_bwd_workspace(int n, size_t capacity, int n_tiles);
+int gs2d_render_bwd(const float* proj, const gs2d_bins* bins, const int32_t* tiles_per_surfel,
+                    const gs2d_surfels* s, const float* pose, const gs2d_camera* cam,
+                    const gs2d_config* cfg, const float* t_final, const uint32_t* n_last,
+                    const float* d_rgb, const float* d_depth, const float* d_normal,
+                    const float* d_opacity, float* d_mu, float* d_quat, float* d_scale,
+                    float* d_opac, float* d_rgb_out, float* d_pose6, void* workspace,
+                    size_t ws_bytes, size_t* ws_needed, gs2d_stream stream);
+
+/* Tracking loss L_t (Eq. tracking_loss with the masks of Eq. normal_mask and
+ * opacity_mask) of rendered images against an observed RGB-D frame, and its
+ * gradient w.r.t. the rendered rgb, depth and opacity (g_* [H*W*3], [H*W],
+ * [H*W]; the masks carry no gradient).  loss_out: device [1].  Per-block
+ * partial sums are reduced in a fixed order. */
+int gs2d_tracking_loss(const float* rgb, const float* depth, const float* normal,
+                       const float* opacity, const float* obs_rgb, const float* obs_depth,
+                       const gs2d_camera* cam, const gs2d_track_params* prm, float* g_rgb,
+                       float* g_depth, float* g_opacity, float* loss_out, void* workspace,
+                       size_t ws_bytes, size_t* ws_needed, gs2d_stream stream);
+
+/* Mapping loss of Sec. III-E without the SSIM term:
+ * 1/|Omega| sum (|I_r - I|_1 + w_d |D_r/O - D| + w_n (1 - N_{D_r} . N_r)),
+ * N_{D_r} from Eq. normal_fromD on the back-projected rendered depth with
+ * central differences (interior pixels whose own and 4-neighbour opacity
+ * exceed 0.5).  Gradients w.r.t. rendered rgb, depth, normal, opacity. */
+int gs2d_mapping_loss(const float* rgb, const float* depth, const float* normal,
+                      const float* opacity, const float* obs_rgb, const float* obs_depth,
+                      const gs2d_camera* cam, float w_d, float w_n, float* g_rgb, float* g_depth,
+                      float* g_normal, float* g_opacity, float* loss_out, void* workspace,
+                      size_t ws_bytes, size_t* ws_needed, gs2d_stream stream);
+
+/* Frame-to-map tracking (Sec. III-D): n_iter iterations of
+ * project -> bin_sort -> render_fwd -> tracking loss -> pose-only backward
+ * -> AdamW on tau -> T <- Exp(tau) T with tau reset to 0 (the moments are
+ * kept within the frame and reset at the start of every call).  Once
+ * |tau| < stop_tol the remaining iterations only copy the history.
+ * Everything stays on the device: pose [12] in/out; loss_hist [n_iter] (the
+ * loss at the pose before each update) and pose_hist [n_iter * 12] (the pose
+ * after it) may be NULL.  capacity bounds K per iteration.  The status word
+ * (gs2d_track_status(workspace)) ends as GS2D_OK, 256 (converged early) or
+ * an error (GS2D_ERR_CAPACITY: raise capacity and retry; GS2D_ERR_NONFINITE;
+ * GS2D_ERR_TIMEOUT).  Workspace: gs2d_track_workspace(n, capacity, cam, cfg). */
+size_t gs2d_track_workspace(int n, size_t capacity, const gs2d_camera* cam,
+                            const gs2d_config* cfg);
+int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_config* cfg,
+                    const gs2d_track_params* prm, float* pose, const float* obs_rgb,
+                    const float* obs_depth, int n_iter, size_t capacity, float* loss_hist,
+                    float* pose_hist, void* workspace, size_t ws_bytes, size_t* ws_needed,
+                    gs2d_stream stream);
+/* Device pointer of the status word inside a track workspace (int32). */
+int32_t* gs2d_track_status(void* workspace);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS2D_H_ */

@@ -1,0 +1,75 @@
+// Device helpers shared by the gs2d CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs2d.h"
+
+#define GS2D_CUDA_TRY(expr)                       \
+  do {                                            \
+    cudaError_t e_ = (expr);                      \
+    if (e_ != cudaSuccess) return GS2D_ERR_CUDA;  \
+  } while (0)
+
+#define GS2D_LAUNCH_CHECK()                                   \
+  do {                                                        \
+    if (cudaPeekAtLastError() != cudaSuccess) {               \
+      cudaGetLastError();                                     \
+      return GS2D_ERR_CUDA;                                   \
+    }                                                         \
+  } while (0)
+
+namespace gs2d {
+
+constexpr int kProjFloats = GS2D_PROJ_FLOATS;
+
+// slots of the projected record (see gs2d.h)
+enum ProjSlot {
+  kC0 = 0, kC1 = 3, kC2 = 6, kDet = 9, kAlpha = 10, kRgb = 11, kTn = 14, kNrm = 17, kDu = 20,
+  kDv = 23, kDepth = 26, kRect01 = 28, kRect23 = 29
+};
+constexpr int kFwdVec4 = 5;  // float4s of a record the forward pass reads (slots 0-19)
+constexpr int kBwdVec4 = 7;  // float4s the backward pass reads (slots 0-27)
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Carves a workspace into aligned sub-buffers (host side).
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <class T>
+  T* take(size_t count) {
+    off = align_up(off, 256);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+struct F3 {
+  float x, y, z;
+};
+__device__ __forceinline__ F3 f3(float x, float y, float z) { return F3{x, y, z}; }
+__device__ __forceinline__ F3 operator+(F3 a, F3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ F3 operator-(F3 a, F3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ F3 operator*(float s, F3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot3(F3 a, F3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ F3 cross3(F3 a, F3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// Rows of a 3x3 matrix; m[r*3+c].
+__device__ __forceinline__ F3 mat_mul(const float* m, F3 v) {
+  return f3(fmaf(m[0], v.x, fmaf(m[1], v.y, m[2] * v.z)), fmaf(m[3], v.x, fmaf(m[4], v.y, m[5] * v.z)),
+            fmaf(m[6], v.x, fmaf(m[7], v.y, m[8] * v.z)));
+}
+__device__ __forceinline__ F3 mat_tmul(const float* m, F3 v) {
+  return f3(fmaf(m[0], v.x, fmaf(m[3], v.y, m[6] * v.z)), fmaf(m[1], v.x, fmaf(m[4], v.y, m[7] * v.z)),
+            fmaf(m[2], v.x, fmaf(m[5], v.y, m[8] * v.z)));
+}
+
+__host__ __device__ inline int tiles_along(int px, int tile) { return (px + tile - 1) / tile; }
+
+}  // namespace gs2d

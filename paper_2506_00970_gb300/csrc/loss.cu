@@ -1,0 +1,273 @@
+// Per-pixel loss kernels of tracking (Sec. III-D) and mapping (Sec. III-E):
+// value and gradient w.r.t. the rendered images in one pass, per-block
+// partial sums of the loss reduced in a fixed order.
+#include "gs2d_common.cuh"
+#include "gs2d_internal.h"
+
+namespace gs2d {
+
+constexpr int kLossBlocks = 4 * 152;
+constexpr int kLossThreads = 256;
+
+__device__ __forceinline__ float sgnf(float v) { return (float)((v > 0.f) - (v < 0.f)); }
+
+__device__ __forceinline__ float block_sum256(float v, float* s) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kLossThreads / 32; ++w) t += s[w];
+  return t;
+}
+
+// L_t = 1/|Omega| sum M_n M_o (|I_r - I|_1 + lambda_d |D_r - D|), Eq.
+// tracking_loss; M_n = [N_r . r > 0] (Eq. normal_mask; r's length does not
+// change the sign), M_o = [O > thresh] (Eq. opacity_mask); D_r = D/O in
+// depth_mode 1.  Sub-gradient sign(0) = 0; the masks carry no gradient.
+__global__ void __launch_bounds__(kLossThreads) tracking_loss_kernel(
+    const float* __restrict__ rgb, const float* __restrict__ depth, const float* __restrict__ normal,
+    const float* __restrict__ opac, const float* __restrict__ obs_rgb,
+    const float* __restrict__ obs_depth, gs2d_camera cam, gs2d_track_params prm,
+    float* __restrict__ g_rgb, float* __restrict__ g_depth, float* __restrict__ g_opac,
+    float* __restrict__ part, const int32_t* __restrict__ gate) {
+  __shared__ float s[kLossThreads / 32];
+  if (gate && *gate) return;
+  const int P = cam.width * cam.height;
+  const float inv = 1.f / (float)P;
+  float acc = 0.f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+    const float x = (i % cam.width) + 0.5f, y = (i / cam.width) + 0.5f;
+    const float rx = (x - cam.cx) / cam.fx, ry = (y - cam.cy) / cam.fy;
+    const float O = opac[i];
+    const float nr = normal[3 * i] * rx + normal[3 * i + 1] * ry + normal[3 * i + 2];
+    const bool m = (nr > 0.f) && (O > prm.opacity_thresh);
+    float gr0 = 0.f, gr1 = 0.f, gr2 = 0.f, gd = 0.f, go = 0.f;
+    if (m) {
+      const float D = depth[i];
+      const float Oc = fmaxf(O, 1e-6f);
+      const float Dh = prm.depth_mode ? D / Oc : D;
+      const float d0 = rgb[3 * i] - obs_rgb[3 * i];
+      const float d1 = rgb[3 * i + 1] - obs_rgb[3 * i + 1];
+      const float d2 = rgb[3 * i + 2] - obs_rgb[3 * i + 2];
+      const float dd = Dh - obs_depth[i];
+      acc += fabsf(d0) + fabsf(d1) + fabsf(d2) + prm.lambda_d * fabsf(dd);
+      gr0 = sgnf(d0) * inv;
+      gr1 = sgnf(d1) * inv;
+      gr2 = sgnf(d2) * inv;
+      const float sd = prm.lambda_d * sgnf(dd) * inv;
+      if (prm.depth_mode) {
+        gd = sd / Oc;
+        go = O > 1e-6f ? -sd * D / (O * O) : 0.f;
+      } else {
+        gd = sd;
+      }
+    }
+    g_rgb[3 * i] = gr0;
+    g_rgb[3 * i + 1] = gr1;
+    g_rgb[3 * i + 2] = gr2;
+    g_depth[i] = gd;
+    g_opac[i] = go;
+  }
+  const float t = block_sum256(acc, s);
+  if (threadIdx.x == 0) part[blockIdx.x] = t * inv;
+}
+
+__global__ void __launch_bounds__(256) sum_parts_kernel(const float* __restrict__ part, int n,
+                                                        float* __restrict__ out,
+                                                        const int32_t* __restrict__ gate) {
+  __shared__ float s[256];
+  if (gate && *gate) return;
+  float v = 0.f;
+  for (int i = threadIdx.x; i < n; i += 256) v += part[i];
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+// ---------------------------------------------------------------------------
+// Mapping loss (Sec. III-E, colour term without SSIM):
+//   per pixel |I_r - I|_1 + w_d |D_r/O - D| + w_n (1 - N_D . N_r),
+// N_D = normalised cross product of the central differences of the
+// back-projected points X = (D_r/O) r (Eq. normal_fromD), counted at interior
+// pixels whose own and 4-neighbour opacities exceed 0.5.  The normal term's
+// gradient w.r.t. the depth of pixel q collects the four stencils that use
+// q, recomputed here (a gather, so no atomics).
+struct MapCtx {
+  const float* depth;
+  const float* opac;
+  const float* normal;
+  gs2d_camera cam;
+};
+
+__device__ __forceinline__ F3 ray_of(const gs2d_camera& cam, int px, int py) {
+  return f3((px + 0.5f - cam.cx) / cam.fx, (py + 0.5f - cam.cy) / cam.fy, 1.f);
+}
+__device__ __forceinline__ float dhat(const MapCtx& c, int i) {
+  return c.depth[i] / fmaxf(c.opac[i], 1e-6f);
+}
+__device__ __forceinline__ bool ln_valid(const MapCtx& c, int px, int py) {
+  const int W = c.cam.width, H = c.cam.height;
+  if (px < 1 || py < 1 || px > W - 2 || py > H - 2) return false;
+  const int i = py * W + px;
+  return c.opac[i] > 0.5f && c.opac[i - 1] > 0.5f && c.opac[i + 1] > 0.5f && c.opac[i - W] > 0.5f &&
+         c.opac[i + W] > 0.5f;
+}
+// Normal term at pixel p: returns L_n (0 if invalid) and the gradients of
+// L_n w.r.t. X(p+ex), X(p-ex), X(p+ey), X(p-ey) and N_r(p).
+__device__ bool ln_eval(const MapCtx& c, int px, int py, float& Ln, F3 g[4], F3& gNr) {
+  if (!ln_valid(c, px, py)) return false;
+  const int W = c.cam.width;
+  const int i = py * W + px;
+  const F3 Xr = dhat(c, i + 1) * ray_of(c.cam, px + 1, py);
+  const F3 Xl = dhat(c, i - 1) * ray_of(c.cam, px - 1, py);
+  const F3 Xd = dhat(c, i + W) * ray_of(c.cam, px, py + 1);
+  const F3 Xu = dhat(c, i - W) * ray_of(c.cam, px, py - 1);
+  const F3 gx = 0.5f * (Xr - Xl), gy = 0.5f * (Xd - Xu);
+  const F3 n = cross3(gx, gy);
+  const float nn = sqrtf(dot3(n, n));
+  if (!(nn > 0.f)) return false;
+  const F3 ND = (1.f / nn) * n;
+  const F3 Nr = f3(c.normal[3 * i], c.normal[3 * i + 1], c.normal[3 * i + 2]);
+  const float dp = dot3(ND, Nr);
+  Ln = 1.f - dp;
+  gNr = (-1.f) * ND;
+  // dLn/dn = -(Nr - ND (ND . Nr)) / |n|
+  const F3 gn = (-1.f / nn) * (Nr - dp * ND);
+  const F3 ggx = cross3(gy, gn), ggy = cross3(gn, gx);
+  g[0] = 0.5f * ggx;
+  g[1] = (-0.5f) * ggx;
+  g[2] = 0.5f * ggy;
+  g[3] = (-0.5f) * ggy;
+  return true;
+}
+
+__global__ void __launch_bounds__(kLossThreads) mapping_loss_kernel(
+    const float* __restrict__ rgb, const float* __restrict__ depth, const float* __restrict__ normal,
+    const float* __restrict__ opac, const float* __restrict__ obs_rgb,
+    const float* __restrict__ obs_depth, gs2d_camera cam, float w_d, float w_n,
+    float* __restrict__ g_rgb, float* __restrict__ g_depth, float* __restrict__ g_normal,
+    float* __restrict__ g_opac, float* __restrict__ part) {
+  __shared__ float s[kLossThreads / 32];
+  const int W = cam.width, H = cam.height, P = W * H;
+  const float inv = 1.f / (float)P;
+  const MapCtx c{depth, opac, normal, cam};
+  float acc = 0.f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+    const int px = i % W, py = i / W;
+    const float O = opac[i];
+    const float Oc = fmaxf(O, 1e-6f);
+    const float D = depth[i];
+    const float Dh = D / Oc;
+    const float d0 = rgb[3 * i] - obs_rgb[3 * i];
+    const float d1 = rgb[3 * i + 1] - obs_rgb[3 * i + 1];
+    const float d2 = rgb[3 * i + 2] - obs_rgb[3 * i + 2];
+    const float dd = Dh - obs_depth[i];
+    acc += fabsf(d0) + fabsf(d1) + fabsf(d2) + w_d * fabsf(dd);
+    g_rgb[3 * i] = sgnf(d0) * inv;
+    g_rgb[3 * i + 1] = sgnf(d1) * inv;
+    g_rgb[3 * i + 2] = sgnf(d2) * inv;
+    float gDh = w_d * sgnf(dd) * inv;
+    // own normal term
+    float Ln;
+    F3 g4[4], gNr = f3(0.f, 0.f, 0.f);
+    if (ln_eval(c, px, py, Ln, g4, gNr)) {
+      acc += w_n * Ln;
+      gNr = (w_n * inv) * gNr;
+    } else {
+      gNr = f3(0.f, 0.f, 0.f);
+    }
+    g_normal[3 * i] = gNr.x;
+    g_normal[3 * i + 1] = gNr.y;
+    g_normal[3 * i + 2] = gNr.z;
+    // stencils of the four neighbours that read X(q): p = q-ex uses X(p+ex),
+    // p = q+ex uses X(p-ex), p = q-ey uses X(p+ey), p = q+ey uses X(p-ey)
+    const F3 rq = ray_of(cam, px, py);
+    const int nb[4][3] = {{px - 1, py, 0}, {px + 1, py, 1}, {px, py - 1, 2}, {px, py + 1, 3}};
+    F3 gX = f3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float l;
+      F3 gg[4], gn;
+      if (ln_eval(c, nb[k][0], nb[k][1], l, gg, gn)) gX = gX + gg[nb[k][2]];
+    }
+    gDh += w_n * inv * dot3(gX, rq);
+    g_depth[i] = gDh / Oc;
+    g_opac[i] = O > 1e-6f ? -gDh * D / (O * O) : 0.f;
+  }
+  const float t = block_sum256(acc, s);
+  if (threadIdx.x == 0) part[blockIdx.x] = t * inv;
+}
+
+size_t loss_ws_bytes(const gs2d_camera* cam) {
+  (void)cam;
+  return align_up(kLossBlocks * sizeof(float), 256);
+}
+
+int tracking_loss_launch(const float* rgb, const float* depth, const float* normal,
+                         const float* opacity, const float* obs_rgb, const float* obs_depth,
+                         const gs2d_camera* cam, const gs2d_track_params* prm, float* g_rgb,
+                         float* g_depth, float* g_opacity, float* loss_out, void* workspace,
+                         size_t ws_bytes, size_t* ws_needed, const int32_t* gate, cudaStream_t st) {
+  if (!rgb || !depth || !normal || !opacity || !obs_rgb || !obs_depth || !cam || !prm || !g_rgb ||
+      !g_depth || !g_opacity || !loss_out)
+    return GS2D_ERR_INVALID_ARG;
+  if (cam->width <= 0 || cam->height <= 0) return GS2D_ERR_INVALID_ARG;
+  const size_t need = loss_ws_bytes(cam);
+  if (ws_needed) *ws_needed = need;
+  if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
+  float* part = static_cast<float*>(workspace);
+  tracking_loss_kernel<<<kLossBlocks, kLossThreads, 0, st>>>(rgb, depth, normal, opacity, obs_rgb,
+                                                             obs_depth, *cam, *prm, g_rgb, g_depth,
+                                                             g_opacity, part, gate);
+  GS2D_LAUNCH_CHECK();
+  sum_parts_kernel<<<1, 256, 0, st>>>(part, kLossBlocks, loss_out, gate);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+}  // namespace gs2d
+
+using namespace gs2d;
+
+extern "C" {
+
+int gs2d_tracking_loss(const float* rgb, const float* depth, const float* normal,
+                       const float* opacity, const float* obs_rgb, const float* obs_depth,
+                       const gs2d_camera* cam, const gs2d_track_params* prm, float* g_rgb,
+                       float* g_depth, float* g_opacity, float* loss_out, void* workspace,
+                       size_t ws_bytes, size_t* ws_needed, gs2d_stream stream) {
+  return tracking_loss_launch(rgb, depth, normal, opacity, obs_rgb, obs_depth, cam, prm, g_rgb,
+                              g_depth, g_opacity, loss_out, workspace, ws_bytes, ws_needed, nullptr,
+                              (cudaStream_t)stream);
+}
+
+int gs2d_mapping_loss(const float* rgb, const float* depth, const float* normal,
+                      const float* opacity, const float* obs_rgb, const float* obs_depth,
+                      const gs2d_camera* cam, float w_d, float w_n, float* g_rgb, float* g_depth,
+                      float* g_normal, float* g_opacity, float* loss_out, void* workspace,
+                      size_t ws_bytes, size_t* ws_needed, gs2d_stream stream) {
+  if (!rgb || !depth || !normal || !opacity || !obs_rgb || !obs_depth || !cam || !g_rgb ||
+      !g_depth || !g_normal || !g_opacity || !loss_out)
+    return GS2D_ERR_INVALID_ARG;
+  if (cam->width <= 0 || cam->height <= 0) return GS2D_ERR_INVALID_ARG;
+  const size_t need = loss_ws_bytes(cam);
+  if (ws_needed) *ws_needed = need;
+  if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  float* part = static_cast<float*>(workspace);
+  mapping_loss_kernel<<<kLossBlocks, kLossThreads, 0, st>>>(rgb, depth, normal, opacity, obs_rgb,
+                                                            obs_depth, *cam, w_d, w_n, g_rgb,
+                                                            g_depth, g_normal, g_opacity, part);
+  GS2D_LAUNCH_CHECK();
+  sum_parts_kernel<<<1, 256, 0, st>>>(part, kLossBlocks, loss_out, nullptr);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+}  // extern "C"

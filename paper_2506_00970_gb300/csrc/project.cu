@@ -1,0 +1,288 @@
+// gs2d_project: per-surfel camera-space splat, homography set-up and tile
+// footprint (Sec. III-A, Eq. Puv, hc, homo, wth).
+//
+// For surfel g with camera-space columns m_u = s_u t_uc, m_v = s_v t_vc and
+// centre mu_c (Eq. hc), the image of (u, v, 1) is (x'z, y'z, z) = A (u, v, 1)
+// with A = diag(fx, fy, 1) [m_u m_v mu_c] and rows a1, a2, a3 (Eq. homo), in
+// image coordinates relative to the principal point, x' = x - cx.  A pixel
+// ray (x', y') fixes the planes h_x = a1 - x' a3 and h_y = a2 - y' a3 through
+// the camera centre, and (u, v, 1) ~ h_x x h_y.  Expanding the cross product
+// the x'y' term vanishes (a3 x a3 = 0), so the intersection is *linear* in
+// the pixel coordinates: with c1 = a2 x a3, c2 = a3 x a1,
+//     p(x', y') = (x' - x0) c1 + (y' - y0) c2 + (0, 0, det(A) / mu_c.z),
+//     u = p0 / p2,  v = p1 / p2,  z = a3 . (u, v, 1) = det(A) / p2,
+// where (x0, y0) = (a1.z, a2.z) / a3.z is the projected centre (u = v = 0
+// there, and z = mu_c.z).  Writing p about the projected centre instead of
+// the image origin avoids the cancellation of a large constant term in FP32.
+// The compositing kernels re-base p on their tile's first pixel once per
+// staged surfel and then evaluate it with six FMAs per (pixel, surfel) pair,
+// without inverting the homography (Sec. III-A).
+//
+// Footprint: pixels can only pass the cutoff and alpha tests inside the disc
+// u^2 + v^2 <= rho^2, rho^2 = 1.01 min(cutoff_r2, 2 ln(alpha / alpha_min)),
+// and only where the hit depth exceeds the near plane.  The bounding box of
+// the image of that clipped disc is exact (footprint_bounds), so a surfel
+// that reaches past the camera plane -- a wall beside the camera -- covers
+// only the pixels it can actually reach instead of the whole image.
+#include <math.h>
+
+#include "gs2d_common.cuh"
+#include "gs2d_internal.h"
+
+namespace gs2d {
+
+// Image-plane bounding box (principal-point relative) of the disc
+// u^2 + v^2 <= rho^2 of the splat with homography rows a1, a2, a3, clipped to
+// camera depth z >= zmin.  x' = (a1 . U) / (a3 . U), U = (u, v, 1), is
+// linear-fractional, so over the convex clipped disc its extremes lie on the
+// boundary: at a point of the circle where x' is stationary, i.e.
+// (a1 x a3) . (U' x U) = 0 <=> w_x cos t + w_y sin t = rho w_z with
+// w = a1 x a3, if that point has z >= zmin; or at an end of the chord where
+// the circle meets z = zmin (along the chord z is constant and x' linear).
+// Same for y' with a2.  Returns false if no part of the disc has z >= zmin.
+// Unit vectors (c, s) with (wx, wy) . (c, s) = t |(wx, wy)|; t is clamped to
+// [-1, 1] (the points stay on the circle, so an extra candidate can only
+// widen the box).  ok: R > 0 and, if exact, |t| <= 1.
+__device__ __forceinline__ void circle_line(float wx, float wy, float t, bool exact, float& c0,
+                                            float& s0, float& c1, float& s1, bool& ok) {
+  const float R = sqrtf(fmaf(wx, wx, wy * wy));
+  ok = R > 0.f && (!exact || fabsf(t) <= 1.f);
+  if (!(R > 0.f)) {
+    c0 = s0 = c1 = s1 = 0.f;
+    return;
+  }
+  const float hx = wx / R, hy = wy / R;
+  const float tc = fminf(fmaxf(t, -1.f), 1.f);
+  const float q = sqrtf(fmaxf(1.f - tc * tc, 0.f));
+  c0 = tc * hx - q * hy;
+  s0 = tc * hy + q * hx;
+  c1 = tc * hx + q * hy;
+  s1 = tc * hy - q * hx;
+}
+
+__device__ bool footprint_bounds(F3 a1, F3 a2, F3 a3, float rho, float zmin, float& x0, float& x1,
+                                 float& y0, float& y1) {
+  float cu[6], sv[6];
+  bool ok[6];
+  const F3 wx = cross3(a1, a3), wy = cross3(a2, a3);
+  const float Rx = sqrtf(fmaf(wx.x, wx.x, wx.y * wx.y));
+  const float Ry = sqrtf(fmaf(wy.x, wy.x, wy.y * wy.y));
+  // stationary points of x' and y' on the circle (tangents of the image);
+  // where none exists the disc reaches past the camera plane and the extreme
+  // lies on the chord below
+  circle_line(wx.x, wx.y, Rx > 0.f ? rho * wx.z / Rx : 0.f, false, cu[0], sv[0], cu[1], sv[1], ok[0]);
+  ok[1] = ok[0];
+  circle_line(wy.x, wy.y, Ry > 0.f ? rho * wy.z / Ry : 0.f, false, cu[2], sv[2], cu[3], sv[3], ok[2]);
+  ok[3] = ok[2];
+  const float R3 = sqrtf(fmaf(a3.x, a3.x, a3.y * a3.y));
+  circle_line(a3.x, a3.y, R3 > 0.f ? (zmin - a3.z) / (rho * R3) : 2.f, true, cu[4], sv[4], cu[5],
+              sv[5], ok[4]);
+  ok[5] = ok[4];
+  // a stationary direction that degenerates (R == 0) leaves the extent open
+  const bool open_x = !(Rx > 0.f), open_y = !(Ry > 0.f);
+  x0 = y0 = 3.0e38f;
+  x1 = y1 = -3.0e38f;
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    if (!ok[k]) continue;
+    const float u = rho * cu[k], v = rho * sv[k];
+    const float z = fmaf(a3.x, u, fmaf(a3.y, v, a3.z));
+    if (!(z >= zmin * (1.f - 1e-5f))) continue;
+    const float zi = 1.f / z;
+    const float x = fmaf(a1.x, u, fmaf(a1.y, v, a1.z)) * zi;
+    const float y = fmaf(a2.x, u, fmaf(a2.y, v, a2.z)) * zi;
+    x0 = fminf(x0, x);
+    x1 = fmaxf(x1, x);
+    y0 = fminf(y0, y);
+    y1 = fmaxf(y1, y);
+    any = true;
+  }
+  if (!any) return false;
+  if (open_x) {
+    x0 = -3.0e38f;
+    x1 = 3.0e38f;
+  }
+  if (open_y) {
+    y0 = -3.0e38f;
+    y1 = 3.0e38f;
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(256) project_kernel(
+    const float* __restrict__ mu, const float* __restrict__ quat, const float* __restrict__ scale,
+    const float* __restrict__ opacity, const float* __restrict__ rgb, int n,
+    const float* __restrict__ pose, gs2d_camera cam, gs2d_config cfg, int tiles_x, int tiles_y,
+    float4* __restrict__ proj, int32_t* __restrict__ tiles_out, const int32_t* __restrict__ gate) {
+  __shared__ float sp[12];
+  if (gate && *gate) return;
+  if (threadIdx.x < 12) sp[threadIdx.x] = pose[threadIdx.x];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* Rcw = sp;
+
+  // quaternion -> rotation columns t_u, t_v, t_n
+  float4 q = reinterpret_cast<const float4*>(quat)[i];
+  const float qinv = rsqrtf(fmaf(q.x, q.x, fmaf(q.y, q.y, fmaf(q.z, q.z, q.w * q.w))));
+  const float w = q.x * qinv, x = q.y * qinv, y = q.z * qinv, z = q.w * qinv;
+  const F3 tu = f3(1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y));
+  const F3 tv = f3(2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x));
+  const F3 tn = f3(2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y));
+
+  const F3 muw = f3(mu[3 * i], mu[3 * i + 1], mu[3 * i + 2]);
+  const F3 mu_c = mat_mul(Rcw, muw) + f3(sp[9], sp[10], sp[11]);
+  const float su = scale[2 * i], sv = scale[2 * i + 1];
+  const F3 m_u = su * mat_mul(Rcw, tu);
+  const F3 m_v = sv * mat_mul(Rcw, tv);
+  const F3 tn_c = mat_mul(Rcw, tn);
+  const float alpha = opacity[i];
+
+  // rows of A = diag(fx, fy, 1) [m_u m_v mu_c] (principal point at the origin)
+  const F3 a3 = f3(m_u.z, m_v.z, mu_c.z);
+  const F3 a1 = f3(cam.fx * m_u.x, cam.fx * m_v.x, cam.fx * mu_c.x);
+  const F3 a2 = f3(cam.fy * m_u.y, cam.fy * m_v.y, cam.fy * mu_c.y);
+  const F3 c1 = cross3(a2, a3), c2 = cross3(a3, a1);
+  const float det = dot3(a1, c1);
+  const float xc = a1.z / a3.z, yc = a2.z / a3.z;
+  const float p2c = det / a3.z;
+  const F3 nrm = cross3(m_u, m_v);
+  const float nn = dot3(nrm, nrm);
+  const float inn = nn > 0.f ? 1.f / nn : 0.f;
+  const F3 du = inn * cross3(m_v, nrm), dv = inn * cross3(nrm, m_u);
+
+  // tile footprint: the disc u^2 + v^2 <= rho^2 clipped to z >= near
+  int tx0 = 1, ty0 = 1, tx1 = 0, ty1 = 0;
+  int pi0 = 1, pj0 = 1, pi1 = 0, pj1 = 0;
+  if (mu_c.z > cam.near_z && alpha >= cfg.alpha_min) {
+    const float rho2 = 1.01f * fminf(cfg.cutoff_r2, 2.f * logf(alpha / cfg.alpha_min));
+    if (rho2 > 0.f) {
+      float x0, x1, y0, y1;
+      if (footprint_bounds(a1, a2, a3, sqrtf(rho2), 0.99f * cam.near_z, x0, x1, y0, y1)) {
+        x0 += cam.cx;
+        x1 += cam.cx;
+        y0 += cam.cy;
+        y1 += cam.cy;
+        const float i0 = fmaxf(ceilf(x0 - 0.5f), 0.f);
+        const float i1 = fminf(floorf(x1 - 0.5f), (float)(cam.width - 1));
+        const float j0 = fmaxf(ceilf(y0 - 0.5f), 0.f);
+        const float j1 = fminf(floorf(y1 - 0.5f), (float)(cam.height - 1));
+        if (i0 <= i1 && j0 <= j1) {
+          pi0 = (int)i0;
+          pi1 = (int)i1;
+          pj0 = (int)j0;
+          pj1 = (int)j1;
+          tx0 = (int)i0 / cfg.tile_w;
+          tx1 = (int)i1 / cfg.tile_w;
+          ty0 = (int)j0 / cfg.tile_h;
+          ty1 = (int)j1 / cfg.tile_h;
+        }
+      }
+    }
+  }
+  const int k = (tx0 <= tx1 && ty0 <= ty1) ? (tx1 - tx0 + 1) * (ty1 - ty0 + 1) : 0;
+  tiles_out[i] = k;
+
+  float4* o = proj + (size_t)i * (kProjFloats / 4);
+  const float rgb0 = rgb[3 * i], rgb1 = rgb[3 * i + 1], rgb2 = rgb[3 * i + 2];
+  const uint32_t r01 = (uint32_t)tx0 | ((uint32_t)ty0 << 16);
+  const uint32_t r23 = (uint32_t)tx1 | ((uint32_t)ty1 << 16);
+  const uint32_t b01 = (uint32_t)pi0 | ((uint32_t)pi1 << 16);
+  const uint32_t b23 = (uint32_t)pj0 | ((uint32_t)pj1 << 16);
+  o[0] = make_float4(xc, yc, p2c, c1.x);
+  o[1] = make_float4(c1.y, c1.z, c2.x, c2.y);
+  o[2] = make_float4(c2.z, det, alpha, rgb0);
+  o[3] = make_float4(rgb1, rgb2, tn_c.x, tn_c.y);
+  o[4] = make_float4(tn_c.z, nrm.x, nrm.y, nrm.z);
+  o[5] = make_float4(du.x, du.y, du.z, dv.x);
+  o[6] = make_float4(dv.y, dv.z, mu_c.z, 0.f);
+  o[7] = make_float4(__uint_as_float(r01), __uint_as_float(r23), __uint_as_float(b01),
+                     __uint_as_float(b23));
+  (void)tiles_x;
+  (void)tiles_y;
+}
+
+int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* pose,
+                   const gs2d_config* cfg, float* proj_out, int32_t* tiles_per_surfel_out,
+                   const int32_t* gate, cudaStream_t st) {
+  if (!s || !cam || !pose || !cfg || !proj_out || !tiles_per_surfel_out) return GS2D_ERR_INVALID_ARG;
+  if (s->n < 0 || (s->n > 0 && (!s->mu || !s->quat || !s->scale || !s->opacity || !s->rgb)))
+    return GS2D_ERR_INVALID_ARG;
+  if (cam->width <= 0 || cam->height <= 0 || cfg->tile_w <= 0 || cfg->tile_h <= 0)
+    return GS2D_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(s->quat) | reinterpret_cast<uintptr_t>(proj_out)) & 15)
+    return GS2D_ERR_INVALID_ARG;
+  const int tx = tiles_along(cam->width, cfg->tile_w), ty = tiles_along(cam->height, cfg->tile_h);
+  if (tx > 65535 || ty > 65535) return GS2D_ERR_INVALID_ARG;
+  if (s->n == 0) return GS2D_OK;
+  const int threads = 256;
+  const int blocks = (s->n + threads - 1) / threads;
+  project_kernel<<<blocks, threads, 0, st>>>(s->mu, s->quat, s->scale, s->opacity, s->rgb, s->n,
+                                             pose, *cam, *cfg, tx, ty,
+                                             reinterpret_cast<float4*>(proj_out),
+                                             tiles_per_surfel_out, gate);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+}  // namespace gs2d
+
+using namespace gs2d;
+
+extern "C" {
+
+gs2d_config gs2d_default_config(void) {
+  gs2d_config c;
+  c.tile_w = 16;
+  c.tile_h = 16;
+  c.px_per_thread = 1;
+  c.alpha_min = 1.0f / 255.0f;
+  c.alpha_max = 0.99f;
+  c.t_min = 1e-4f;
+  c.cutoff_r2 = 9.0f;
+  return c;
+}
+
+gs2d_track_params gs2d_default_track_params(void) {
+  gs2d_track_params p;
+  p.lambda_d = 1.0f;
+  p.lr = 1e-3f;
+  p.beta1 = 0.9f;
+  p.beta2 = 0.999f;
+  p.eps = 1e-8f;
+  p.weight_decay = 0.0f;
+  p.stop_tol = 1e-5f;
+  p.opacity_thresh = 0.95f;
+  p.depth_mode = 1;
+  return p;
+}
+
+const char* gs2d_status_string(int s) {
+  switch (s) {
+    case GS2D_OK: return "ok";
+    case GS2D_ERR_INVALID_ARG: return "invalid argument";
+    case GS2D_ERR_WORKSPACE: return "workspace missing or too small";
+    case GS2D_ERR_CAPACITY: return "intersection capacity exceeded";
+    case GS2D_ERR_CUDA: return "CUDA launch error";
+    case GS2D_ERR_TIMEOUT: return "device wait timed out";
+    case GS2D_ERR_NONFINITE: return "non-finite value";
+    default: return "unknown status";
+  }
+}
+
+int gs2d_tiles_x(const gs2d_camera* cam, const gs2d_config* cfg) {
+  return tiles_along(cam->width, cfg->tile_w);
+}
+int gs2d_tiles_y(const gs2d_camera* cam, const gs2d_config* cfg) {
+  return tiles_along(cam->height, cfg->tile_h);
+}
+
+int gs2d_project(const gs2d_surfels* s, const gs2d_camera* cam, const float* pose,
+                 const gs2d_config* cfg, float* proj_out, int32_t* tiles_per_surfel_out,
+                 gs2d_stream stream) {
+  return project_launch(s, cam, pose, cfg, proj_out, tiles_per_surfel_out, nullptr,
+                        (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,663 @@
+// gs2d_render_fwd / gs2d_render_bwd: tile-based front-to-back compositing of
+// 2D Gaussian surfels (Eq. alpha_blending) and its reverse mode to the surfel
+// parameters and to the camera pose (Sec. III-B, Eq. derivatives).
+//
+// Forward: one 256-thread block per image tile, one pixel per thread, each
+// warp an 8 x 4 pixel block.  The tile's depth-ordered surfel list is staged
+// through shared memory in batches of 256 records (80 B each), the record's
+// linear intersection map re-based on the tile's first pixel (c0t); a warp
+// skips a surfel whose footprint misses its block, and every thread
+// evaluates u = p0/p2, v = p1/p2, z = det/p2 with p = c0t + lx c1 + ly c2,
+// G = exp(-(u^2+v^2)/2), a = min(alpha G, alpha_max), skips a < alpha_min or
+// u^2+v^2 > cutoff or z <= near, blends colour, depth z, normal t_nc and
+// opacity, and stops before the transmittance would fall below t_min.  The
+// block leaves the list once every pixel has stopped.
+//
+// Backward: each pixel replays its list back to front from the stored
+// (T_final, n_last): T_i = T_{i+1} / (1 - a_i), and with the running suffix
+// S = sum_{j>i} w_j (c_j . gC + z_j gD + t_nc,j . gN) the blending gradient is
+//   dL/da_i = T_i (c_i . gC + z_i gD + t_nc,i . gN) - (S - gO T_final) / (1 - a_i).
+// Through the intersection, with q = gu d_u + gv d_v (dual tangents) and
+// beta = (q . r + gz) / (n . r) (r the pixel ray, n = m_u x m_v), the
+// gradient of one (pixel, surfel) pair w.r.t. the camera-space splat is
+// rank one:
+//   dL/dmu_c = Gv,  dL/d(s_u t_uc) = u Gv,  dL/d(s_v t_vc) = v Gv,  Gv = beta n - q,
+// (moving the plane along n shifts the hit point along the ray; moving it
+// in-plane shifts (u, v) through the dual basis).  The left pose perturbation
+// moves every splat by (rho, theta x .), so the pair's pose gradient is
+// (Gv, X x Gv) with X = z r the hit point, plus t_nc x dL/dt_nc from the
+// normal image -- the Jacobians [I, -mu_c^x] and [0, -R_c,:,i^x] of Sec. III-B
+// contracted with these rank-one gradients.
+//
+// Full mode: per batch each warp sums its 32 pixels' 16 per-pair values with
+// a butterfly reduce-scatter (16 shuffles per surfel instead of 80), the 8
+// warps are summed through shared memory, and one 64-byte partial per
+// (tile, surfel) pair is written at the pair's emission index.  A second
+// kernel adds each surfel's partials in emission order (deterministic),
+// chains to world space, scales and the quaternion, and forms the pose term.
+// Tracking mode: pixels accumulate the 6-vector pose gradient directly; one
+// partial per tile, reduced in a fixed order.
+#include "gs2d_common.cuh"
+#include "gs2d_internal.h"
+
+namespace gs2d {
+
+constexpr int kTileThreads = 256;
+constexpr int kRedVals = 16;
+
+// Thread -> pixel map of a tile: each warp owns an 8 x 4 block of pixels, so
+// a warp can skip a surfel whose footprint misses its block.
+struct TilePix {
+  int px, py;      // pixel
+  int bx0, by0;    // first pixel of the warp's 8 x 4 block
+  float lx, ly;    // pixel centre relative to the tile's first pixel centre
+};
+__device__ __forceinline__ TilePix tile_pixel(int tile, int tiles_x, int tile_w, int tile_h) {
+  TilePix t;
+  const int tx = tile % tiles_x, ty = tile / tiles_x;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wpr = tile_w >> 3;
+  const int ox = (w % wpr) * 8, oy = (w / wpr) * 4;
+  t.bx0 = tx * tile_w + ox;
+  t.by0 = ty * tile_h + oy;
+  t.px = t.bx0 + (lane & 7);
+  t.py = t.by0 + (lane >> 3);
+  t.lx = (float)(ox + (lane & 7));
+  t.ly = (float)(oy + (lane >> 3));
+  (void)tile_h;
+  return t;
+}
+
+// Stages one projected record for a tile: p is re-based on the tile's first
+// pixel centre (xt, yt) (principal-point relative): c0t = p(xt, yt).  Both
+// passes stage through this function, so they evaluate identical numbers.
+__device__ __forceinline__ float4 stage_c0(const float4 r0, const float4 r1, const float4 r2,
+                                           float xt, float yt) {
+  // r0 = (x0, y0, p2c, c1x), r1 = (c1y, c1z, c2x, c2y), r2 = (c2z, det, alpha, rgb0)
+  const float dx = xt - r0.x, dy = yt - r0.y;
+  return make_float4(fmaf(dy, r1.z, dx * r0.w), fmaf(dy, r1.w, dx * r1.x),
+                     fmaf(dy, r2.x, fmaf(dx, r1.y, r0.z)), r0.w);
+}
+
+// Does the footprint (packed pixel ranges) touch the warp's 8 x 4 block?
+__device__ __forceinline__ bool warp_hits(float bi, float bj, int bx0, int by0) {
+  const uint32_t I = __float_as_uint(bi), J = __float_as_uint(bj);
+  const int i0 = I & 0xFFFF, i1 = I >> 16, j0 = J & 0xFFFF, j1 = J >> 16;
+  return !(i1 < bx0 || i0 > bx0 + 7 || j1 < by0 || j0 > by0 + 3);
+}
+
+// Evaluation of one (pixel, surfel) pair shared by forward and backward so
+// both take bit-identical skip decisions.  Returns false if skipped.
+struct Eval {
+  float rinv, u, v, z, G, araw, a;
+};
+__device__ __forceinline__ bool eval_pair(const float4 r0, const float4 r1, const float4 r2, float lx,
+                                          float ly, float near_z, float cutoff_r2, float alpha_min,
+                                          float alpha_max, Eval& e) {
+  // r0 = c0t.xyz c1.x, r1 = c1.yz c2.xy, r2 = c2.z det alpha rgb0
+  const float p0 = fmaf(ly, r1.z, fmaf(lx, r0.w, r0.x));
+  const float p1 = fmaf(ly, r1.w, fmaf(lx, r1.x, r0.y));
+  const float p2 = fmaf(ly, r2.x, fmaf(lx, r1.y, r0.z));
+  e.rinv = __fdividef(1.0f, p2);
+  e.u = __fmul_rn(p0, e.rinv);
+  e.v = __fmul_rn(p1, e.rinv);
+  const float rr = fmaf(e.u, e.u, __fmul_rn(e.v, e.v));
+  if (!(rr <= cutoff_r2)) return false;
+  e.z = __fmul_rn(r2.y, e.rinv);
+  if (!(e.z > near_z)) return false;
+  e.G = __expf(-0.5f * rr);
+  e.araw = __fmul_rn(r2.z, e.G);
+  e.a = fminf(e.araw, alpha_max);
+  return e.a >= alpha_min;
+}
+
+// kCount: the same loop, counting evaluated pairs, pairs inside the cutoff
+// and blended pairs instead of writing images (the work measure of the
+// roofline); counts are exact integers.
+template <bool kCount>
+__global__ void __launch_bounds__(kTileThreads) render_fwd_kernel(
+    const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
+    const int32_t* __restrict__ ranges, gs2d_camera cam, gs2d_config cfg, int tiles_x,
+    float* __restrict__ out_rgb, float* __restrict__ out_depth, float* __restrict__ out_normal,
+    float* __restrict__ out_opac, float* __restrict__ out_T, uint32_t* __restrict__ out_nlast,
+    unsigned long long* __restrict__ counts, const int32_t* __restrict__ gate) {
+  __shared__ float4 s_rec[kTileThreads][kFwdVec4];
+  uint32_t n_eval = 0, n_in = 0, n_blend = 0;
+  if (gate && *gate) return;
+  const int tile = blockIdx.x;
+  const TilePix tp = tile_pixel(tile, tiles_x, cfg.tile_w, cfg.tile_h);
+  const bool inside = tp.px < cam.width && tp.py < cam.height;
+  const float xt = (float)((tile % tiles_x) * cfg.tile_w) + 0.5f - cam.cx;
+  const float yt = (float)((tile / tiles_x) * cfg.tile_h) + 0.5f - cam.cy;
+  const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
+  float T = 1.f, D = 0.f;
+  F3 C = f3(0.f, 0.f, 0.f), N = f3(0.f, 0.f, 0.f);
+  uint32_t last = 0;
+  bool done = !inside;
+  for (int b = start; b < end; b += kTileThreads) {
+    if (__syncthreads_count(!done) == 0) break;
+    const int idx = b + (int)threadIdx.x;
+    if (idx < end) {
+      const float4* src = proj + (size_t)vals[idx] * (kProjFloats / 4);
+      const float4 r0 = src[0], r1 = src[1], r2 = src[2], r3 = src[3], r4 = src[4], r7 = src[7];
+      s_rec[threadIdx.x][0] = stage_c0(r0, r1, r2, xt, yt);
+      s_rec[threadIdx.x][1] = r1;
+      s_rec[threadIdx.x][2] = r2;
+      s_rec[threadIdx.x][3] = r3;
+      s_rec[threadIdx.x][4] = make_float4(r4.x, r7.z, r7.w, 0.f);
+    }
+    __syncthreads();
+    const int cnt = min(kTileThreads, end - b);
+    if (!done) {
+      for (int j = 0; j < cnt; ++j) {
+        const float4 r4 = s_rec[j][4];
+        if (!warp_hits(r4.y, r4.z, tp.bx0, tp.by0)) continue;
+        const float4 r0 = s_rec[j][0], r1 = s_rec[j][1], r2 = s_rec[j][2];
+        Eval e;
+        const bool hit = eval_pair(r0, r1, r2, tp.lx, tp.ly, cam.near_z, cfg.cutoff_r2,
+                                   cfg.alpha_min, cfg.alpha_max, e);
+        if (kCount) {
+          ++n_eval;
+          if (fmaf(e.u, e.u, __fmul_rn(e.v, e.v)) <= cfg.cutoff_r2) ++n_in;
+        }
+        if (!hit) continue;
+        const float Tn = T * (1.f - e.a);
+        if (Tn < cfg.t_min) {
+          done = true;
+          break;
+        }
+        const float4 r3 = s_rec[j][3];
+        const float w = e.a * T;
+        C.x = fmaf(w, r2.w, C.x);
+        C.y = fmaf(w, r3.x, C.y);
+        C.z = fmaf(w, r3.y, C.z);
+        D = fmaf(w, e.z, D);
+        N.x = fmaf(w, r3.z, N.x);
+        N.y = fmaf(w, r3.w, N.y);
+        N.z = fmaf(w, r4.x, N.z);
+        T = Tn;
+        last = (uint32_t)(b + j + 1 - start);
+        if (kCount) ++n_blend;
+      }
+    }
+  }
+  if (kCount) {
+    unsigned long long c[3] = {n_eval, n_in, n_blend};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      unsigned long long v = c[k];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if ((threadIdx.x & 31) == 0) atomicAdd(counts + k, v);
+    }
+    return;
+  }
+  if (inside) {
+    const size_t p = (size_t)tp.py * cam.width + tp.px;
+    out_rgb[3 * p] = C.x;
+    out_rgb[3 * p + 1] = C.y;
+    out_rgb[3 * p + 2] = C.z;
+    out_depth[p] = D;
+    out_normal[3 * p] = N.x;
+    out_normal[3 * p + 1] = N.y;
+    out_normal[3 * p + 2] = N.z;
+    out_opac[p] = 1.f - T;
+    out_T[p] = T;
+    out_nlast[p] = last;
+  }
+}
+
+// Butterfly reduce-scatter of 16 values over a warp: afterwards lane l holds
+// the warp sum of value (l >> 1) in v[0].
+__device__ __forceinline__ void warp_reduce_scatter16(float (&v)[kRedVals], int lane) {
+#pragma unroll
+  for (int lvl = 0; lvl < 4; ++lvl) {
+    const int off = 16 >> lvl;
+    const int half = 8 >> lvl;
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float send = up ? v[i] : v[i + half];
+      const float keep = up ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+template <bool kFull>
+__global__ void __launch_bounds__(kTileThreads) render_bwd_kernel(
+    const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ emit, const int32_t* __restrict__ ranges, gs2d_camera cam,
+    gs2d_config cfg, int tiles_x, const float* __restrict__ T_final,
+    const uint32_t* __restrict__ n_last, const float* __restrict__ g_rgb,
+    const float* __restrict__ g_depth, const float* __restrict__ g_normal,
+    const float* __restrict__ g_opac, float* __restrict__ partials, float* __restrict__ pose_part,
+    const int32_t* __restrict__ gate) {
+  __shared__ float4 s_rec[kTileThreads][kBwdVec4];
+  __shared__ uint32_t s_emit[kFull ? kTileThreads : 1];
+  __shared__ float s_red[kFull ? 8 : 1][kFull ? 32 : 1][kRedVals];
+  __shared__ uint32_t s_max;
+  __shared__ float s_pose[8][6];
+  if (gate && *gate) return;
+  const int tile = blockIdx.x;
+  const TilePix tp = tile_pixel(tile, tiles_x, cfg.tile_w, cfg.tile_h);
+  const int px = tp.px, py = tp.py;
+  const bool inside = px < cam.width && py < cam.height;
+  const float xt = (float)((tile % tiles_x) * cfg.tile_w) + 0.5f - cam.cx;
+  const float yt = (float)((tile / tiles_x) * cfg.tile_h) + 0.5f - cam.cy;
+  const float rx = (px + 0.5f - cam.cx) / cam.fx, ry = (py + 0.5f - cam.cy) / cam.fy;
+  const float fxfy = cam.fx * cam.fy;
+  const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  float Tf = 1.f;
+  uint32_t nl = 0;
+  F3 gC = f3(0.f, 0.f, 0.f), gN = f3(0.f, 0.f, 0.f);
+  float gD = 0.f, gO = 0.f;
+  if (inside) {
+    const size_t p = (size_t)py * cam.width + px;
+    Tf = T_final[p];
+    nl = n_last[p];
+    gC = f3(g_rgb[3 * p], g_rgb[3 * p + 1], g_rgb[3 * p + 2]);
+    gD = g_depth[p];
+    if (g_normal) gN = f3(g_normal[3 * p], g_normal[3 * p + 1], g_normal[3 * p + 2]);
+    if (g_opac) gO = g_opac[p];
+  }
+  if (threadIdx.x == 0) s_max = 0u;
+  __syncthreads();
+  if (nl) atomicMax(&s_max, nl);
+  __syncthreads();
+  const int hi = start + (int)s_max;
+  float T = Tf, acc = 0.f;
+  const float gOT = gO * Tf;
+  float pr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+
+  for (int bend = hi; bend > start; bend -= kTileThreads) {
+    const int bstart = max(start, bend - kTileThreads);
+    const int cnt = bend - bstart;
+    __syncthreads();
+    if ((int)threadIdx.x < cnt) {
+      const int idx = bstart + (int)threadIdx.x;
+      const float4* src = proj + (size_t)vals[idx] * (kProjFloats / 4);
+      const float4 r0 = src[0], r1 = src[1], r2 = src[2], r6 = src[6], r7 = src[7];
+      s_rec[threadIdx.x][0] = stage_c0(r0, r1, r2, xt, yt);
+      s_rec[threadIdx.x][1] = r1;
+      s_rec[threadIdx.x][2] = r2;
+      s_rec[threadIdx.x][3] = src[3];
+      s_rec[threadIdx.x][4] = src[4];
+      s_rec[threadIdx.x][5] = src[5];
+      s_rec[threadIdx.x][6] = make_float4(r6.x, r6.y, r7.z, r7.w);
+      if (kFull) s_emit[threadIdx.x] = emit[idx];
+    }
+    __syncthreads();
+    for (int jj = cnt - 1; jj >= 0; --jj) {
+      const int jrel = bstart + jj - start;
+      float val[kRedVals];
+      bool contrib = false;
+      const float4 r6 = s_rec[jj][6];
+      if (inside && jrel < (int)nl && warp_hits(r6.z, r6.w, tp.bx0, tp.by0)) {
+        const float4 r0 = s_rec[jj][0], r1 = s_rec[jj][1], r2 = s_rec[jj][2];
+        Eval e;
+        if (eval_pair(r0, r1, r2, tp.lx, tp.ly, cam.near_z, cfg.cutoff_r2, cfg.alpha_min,
+                      cfg.alpha_max, e)) {
+          contrib = true;
+          const float4 r3 = s_rec[jj][3], r4 = s_rec[jj][4], r5 = s_rec[jj][5];
+          const F3 col = f3(r2.w, r3.x, r3.y);
+          const F3 tn = f3(r3.z, r3.w, r4.x);
+          const F3 nrm = f3(r4.y, r4.z, r4.w);
+          const F3 du = f3(r5.x, r5.y, r5.z), dv = f3(r5.w, r6.x, r6.y);
+          const float om = 1.f - e.a;
+          const float iom = __fdividef(1.f, om);
+          const float Tb = T * iom;
+          const float w = e.a * Tb;
+          const float vj = dot3(col, gC) + e.z * gD + dot3(tn, gN);
+          const float ga = Tb * vj - (acc - gOT) * iom;
+          acc = fmaf(w, vj, acc);
+          T = Tb;
+          float galpha = 0.f, gG = 0.f;
+          if (e.araw <= cfg.alpha_max) {
+            galpha = e.G * ga;
+            gG = r2.z * ga;
+          }
+          const float gr2 = -0.5f * e.G * gG;
+          const float gu = 2.f * e.u * gr2, gv = 2.f * e.v * gr2;
+          const float gz = w * gD;
+          const F3 q = gu * du + gv * dv;
+          const float beta = (fmaf(q.x, rx, fmaf(q.y, ry, q.z)) + gz) * fxfy * e.rinv;
+          const F3 Gv = beta * nrm - q;
+          if (kFull) {
+            val[0] = Gv.x; val[1] = Gv.y; val[2] = Gv.z;
+            val[3] = e.u * Gv.x; val[4] = e.u * Gv.y; val[5] = e.u * Gv.z;
+            val[6] = e.v * Gv.x; val[7] = e.v * Gv.y; val[8] = e.v * Gv.z;
+            val[9] = galpha;
+            val[10] = w * gC.x; val[11] = w * gC.y; val[12] = w * gC.z;
+            val[13] = w * gN.x; val[14] = w * gN.y; val[15] = w * gN.z;
+          } else {
+            const F3 X = f3(e.z * rx, e.z * ry, e.z);
+            const F3 gtn = w * gN;
+            const F3 th = cross3(X, Gv) + cross3(tn, gtn);
+            pr[0] += Gv.x; pr[1] += Gv.y; pr[2] += Gv.z;
+            pr[3] += th.x; pr[4] += th.y; pr[5] += th.z;
+          }
+        }
+      }
+      if (kFull) {
+        const int slot = jj & 31;
+        if (__any_sync(0xffffffffu, contrib)) {
+          if (!contrib) {
+#pragma unroll
+            for (int i = 0; i < kRedVals; ++i) val[i] = 0.f;
+          }
+          warp_reduce_scatter16(val, lane);
+          if ((lane & 1) == 0) s_red[warp][slot][lane >> 1] = val[0];
+        } else if (lane < kRedVals) {
+          s_red[warp][slot][lane] = 0.f;
+        }
+        if (slot == 0) {
+          __syncthreads();
+          const int gs = min(32, cnt - jj);
+          for (int o = threadIdx.x; o < gs * kRedVals; o += kTileThreads) {
+            const int s = o / kRedVals, c = o % kRedVals;
+            float sum = 0.f;
+#pragma unroll
+            for (int ww = 0; ww < 8; ++ww) sum += s_red[ww][s][c];
+            partials[(size_t)s_emit[jj + s] * kRedVals + c] = sum;
+          }
+          __syncthreads();
+        }
+      }
+    }
+  }
+  if (kFull) {
+    // pairs past every pixel's last blended surfel contribute nothing
+    const int tail = end - max(hi, start);
+    for (int o = threadIdx.x; o < tail * kRedVals; o += kTileThreads) {
+      const int s = o / kRedVals, c = o % kRedVals;
+      partials[(size_t)emit[hi + s] * kRedVals + c] = 0.f;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      float v = pr[i];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0) s_pose[warp][i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+      float v = 0.f;
+      for (int ww = 0; ww < 8; ++ww) v += s_pose[ww][threadIdx.x];
+      pose_part[(size_t)tile * 6 + threadIdx.x] = v;
+    }
+  }
+}
+
+// Per-surfel reduction of the (tile, surfel) partials in emission order and
+// the chain rule to world-space parameters; pose term per block.
+__global__ void __launch_bounds__(256) surfel_grad_kernel(
+    const float* __restrict__ mu, const float* __restrict__ quat, const float* __restrict__ scale,
+    int n, const float* __restrict__ pose, const int32_t* __restrict__ tiles,
+    const uint32_t* __restrict__ surfel_off, const float* __restrict__ partials,
+    float* __restrict__ d_mu, float* __restrict__ d_quat, float* __restrict__ d_scale,
+    float* __restrict__ d_opac, float* __restrict__ d_rgb, float* __restrict__ pose_part,
+    const int32_t* __restrict__ gate) {
+  __shared__ float sp[12];
+  __shared__ float s_pose[8][6];
+  if (gate && *gate) return;
+  if (threadIdx.x < 12) sp[threadIdx.x] = pose[threadIdx.x];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float pr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (i < n) {
+    float S[kRedVals];
+#pragma unroll
+    for (int c = 0; c < kRedVals; ++c) S[c] = 0.f;
+    const int k = tiles[i];
+    if (k > 0) {
+      const float4* p = reinterpret_cast<const float4*>(partials) + (size_t)surfel_off[i] * 4;
+      for (int e = 0; e < k; ++e) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float4 t = p[(size_t)e * 4 + c];
+          S[4 * c] += t.x;
+          S[4 * c + 1] += t.y;
+          S[4 * c + 2] += t.z;
+          S[4 * c + 3] += t.w;
+        }
+      }
+    }
+    const float* R = sp;
+    const float4 q4 = reinterpret_cast<const float4*>(quat)[i];
+    const float qn2 = fmaf(q4.x, q4.x, fmaf(q4.y, q4.y, fmaf(q4.z, q4.z, q4.w * q4.w)));
+    const float qinv = rsqrtf(qn2);
+    const float w = q4.x * qinv, x = q4.y * qinv, y = q4.z * qinv, z = q4.w * qinv;
+    const F3 tu = f3(1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y));
+    const F3 tv = f3(2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x));
+    const F3 tn = f3(2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y));
+    const F3 mu_c = mat_mul(R, f3(mu[3 * i], mu[3 * i + 1], mu[3 * i + 2])) + f3(sp[9], sp[10], sp[11]);
+    const F3 tuc = mat_mul(R, tu), tvc = mat_mul(R, tv), tnc = mat_mul(R, tn);
+    const float su = scale[2 * i], sv = scale[2 * i + 1];
+    const F3 g_muc = f3(S[0], S[1], S[2]);
+    const F3 g_mu = f3(S[3], S[4], S[5]), g_mv = f3(S[6], S[7], S[8]);
+    const F3 g_tnc = f3(S[13], S[14], S[15]);
+    const F3 g_tuc = su * g_mu, g_tvc = sv * g_mv;
+    d_scale[2 * i] = dot3(tuc, g_mu);
+    d_scale[2 * i + 1] = dot3(tvc, g_mv);
+    d_opac[i] = S[9];
+    d_rgb[3 * i] = S[10];
+    d_rgb[3 * i + 1] = S[11];
+    d_rgb[3 * i + 2] = S[12];
+    const F3 th = cross3(mu_c, g_muc) + cross3(tuc, g_tuc) + cross3(tvc, g_tvc) + cross3(tnc, g_tnc);
+    pr[0] = g_muc.x; pr[1] = g_muc.y; pr[2] = g_muc.z;
+    pr[3] = th.x; pr[4] = th.y; pr[5] = th.z;
+    const F3 gmw = mat_tmul(R, g_muc);
+    d_mu[3 * i] = gmw.x;
+    d_mu[3 * i + 1] = gmw.y;
+    d_mu[3 * i + 2] = gmw.z;
+    // world-space column gradients G[:,0..2] = R^T g_t{u,v,n}c
+    const F3 G0 = mat_tmul(R, g_tuc), G1 = mat_tmul(R, g_tvc), G2 = mat_tmul(R, g_tnc);
+    // d/dq of the rotation matrix of a unit quaternion, contracted with G
+    // (G_rc = gradient of entry (r, c); column c of R is t_u, t_v, t_n)
+    const float G00 = G0.x, G10 = G0.y, G20 = G0.z;
+    const float G01 = G1.x, G11 = G1.y, G21 = G1.z;
+    const float G02 = G2.x, G12 = G2.y, G22 = G2.z;
+    const float gw = 2.f * (z * (G10 - G01) + y * (G02 - G20) + x * (G21 - G12));
+    const float gx = 2.f * (y * (G10 + G01) + z * (G02 + G20) + w * (G21 - G12)) - 4.f * x * (G11 + G22);
+    const float gy = 2.f * (x * (G10 + G01) + z * (G12 + G21) + w * (G02 - G20)) - 4.f * y * (G00 + G22);
+    const float gz = 2.f * (x * (G02 + G20) + y * (G12 + G21) + w * (G10 - G01)) - 4.f * z * (G00 + G11);
+    // unit quaternion -> raw quaternion: (I - q q^T) / |q|
+    const float qd = w * gw + x * gx + y * gy + z * gz;
+    d_quat[4 * i] = (gw - w * qd) * qinv;
+    d_quat[4 * i + 1] = (gx - x * qd) * qinv;
+    d_quat[4 * i + 2] = (gy - y * qd) * qinv;
+    d_quat[4 * i + 3] = (gz - z * qd) * qinv;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    float v = pr[c];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) s_pose[warp][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    float v = 0.f;
+    for (int ww = 0; ww < 8; ++ww) v += s_pose[ww][threadIdx.x];
+    pose_part[(size_t)blockIdx.x * 6 + threadIdx.x] = v;
+  }
+}
+
+// Fixed-order sum of per-block 6-vector partials.
+__global__ void __launch_bounds__(256) pose_reduce_kernel(const float* __restrict__ part, int n_part,
+                                                          float* __restrict__ out,
+                                                          const int32_t* __restrict__ gate) {
+  __shared__ float s[6][256];
+  if (gate && *gate) return;
+  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int b = threadIdx.x; b < n_part; b += 256)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[c] += part[(size_t)b * 6 + c];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) s[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) out[threadIdx.x] = s[threadIdx.x][0];
+}
+
+struct BwdWs {
+  float* partials;
+  float* pose_part;
+  size_t bytes;
+};
+BwdWs carve_bwd_ws(void* base, int n, size_t cap, int n_tiles, bool full) {
+  Carver c(base);
+  BwdWs w;
+  w.partials = c.take<float>(full ? (cap > 0 ? cap : 1) * kRedVals : 1);
+  const int nb = max(n_tiles, (n + 255) / 256);
+  w.pose_part = c.take<float>((size_t)max(nb, 1) * 6);
+  w.bytes = align_up(c.off, 256);
+  return w;
+}
+
+int validate_tile_cfg(const gs2d_camera* cam, const gs2d_config* cfg) {
+  if (!cam || !cfg) return GS2D_ERR_INVALID_ARG;
+  if (cfg->tile_w * cfg->tile_h != kTileThreads || cfg->tile_w <= 0 || cfg->tile_h <= 0)
+    return GS2D_ERR_INVALID_ARG;
+  if (cam->width <= 0 || cam->height <= 0) return GS2D_ERR_INVALID_ARG;
+  const long long nt = (long long)gs2d_tiles_x(cam, cfg) * gs2d_tiles_y(cam, cfg);
+  if (nt > 65535) return GS2D_ERR_INVALID_ARG;
+  return GS2D_OK;
+}
+
+int render_fwd_launch(const float* proj, const gs2d_bins* bins, const gs2d_camera* cam,
+                      const gs2d_config* cfg, float* rgb, float* depth, float* normal,
+                      float* opacity, float* t_final, uint32_t* n_last, const int32_t* gate,
+                      cudaStream_t st) {
+  const int v = validate_tile_cfg(cam, cfg);
+  if (v) return v;
+  if (!proj || !bins || !bins->vals || !bins->tile_ranges || !rgb || !depth || !normal ||
+      !opacity || !t_final || !n_last)
+    return GS2D_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(proj) & 15) return GS2D_ERR_INVALID_ARG;
+  const int tx = gs2d_tiles_x(cam, cfg), ty = gs2d_tiles_y(cam, cfg);
+  render_fwd_kernel<false><<<tx * ty, kTileThreads, 0, st>>>(
+      reinterpret_cast<const float4*>(proj), bins->vals, bins->tile_ranges, *cam, *cfg, tx, rgb,
+      depth, normal, opacity, t_final, n_last, nullptr, gate);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+size_t render_bwd_ws_bytes(int n, size_t cap, int n_tiles, bool full) {
+  return carve_bwd_ws(nullptr, n, cap, n_tiles, full).bytes;
+}
+
+int render_bwd_launch(const float* proj, const gs2d_bins* bins, const int32_t* tiles_per_surfel,
+                      const gs2d_surfels* s, const float* pose, const gs2d_camera* cam,
+                      const gs2d_config* cfg, const float* t_final, const uint32_t* n_last,
+                      const float* d_rgb, const float* d_depth, const float* d_normal,
+                      const float* d_opacity, float* d_mu, float* d_quat, float* d_scale,
+                      float* d_opac, float* d_rgb_out, float* d_pose6, void* workspace,
+                      size_t ws_bytes, size_t* ws_needed, const int32_t* gate, cudaStream_t st) {
+  const int v = validate_tile_cfg(cam, cfg);
+  if (v) return v;
+  if (!proj || !bins || !bins->vals || !bins->tile_ranges || !t_final || !n_last || !d_rgb ||
+      !d_depth || !s)
+    return GS2D_ERR_INVALID_ARG;
+  const bool any = d_mu || d_quat || d_scale || d_opac || d_rgb_out;
+  const bool full = any;
+  if (full && !(d_mu && d_quat && d_scale && d_opac && d_rgb_out)) return GS2D_ERR_INVALID_ARG;
+  if (full && (!bins->isect_emit || !bins->surfel_off || !tiles_per_surfel || !s->mu ||
+               !s->quat || !s->scale || !pose))
+    return GS2D_ERR_INVALID_ARG;
+  if (!full && !d_pose6) return GS2D_ERR_INVALID_ARG;
+  const int tx = gs2d_tiles_x(cam, cfg), ty = gs2d_tiles_y(cam, cfg);
+  const int n_tiles = tx * ty;
+  const size_t need = render_bwd_ws_bytes(s->n, bins->capacity, n_tiles, full);
+  if (ws_needed) *ws_needed = need;
+  if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
+  const BwdWs w = carve_bwd_ws(workspace, s->n, bins->capacity, n_tiles, full);
+  const float4* p4 = reinterpret_cast<const float4*>(proj);
+  if (full) {
+    render_bwd_kernel<true><<<n_tiles, kTileThreads, 0, st>>>(
+        p4, bins->vals, bins->isect_emit, bins->tile_ranges, *cam, *cfg, tx, t_final, n_last, d_rgb,
+        d_depth, d_normal, d_opacity, w.partials, w.pose_part, gate);
+    GS2D_LAUNCH_CHECK();
+    if (s->n > 0) {
+      const int nb = (s->n + 255) / 256;
+      surfel_grad_kernel<<<nb, 256, 0, st>>>(s->mu, s->quat, s->scale, s->n, pose, tiles_per_surfel,
+                                             bins->surfel_off, w.partials, d_mu, d_quat, d_scale,
+                                             d_opac, d_rgb_out, w.pose_part, gate);
+      GS2D_LAUNCH_CHECK();
+      if (d_pose6) {
+        pose_reduce_kernel<<<1, 256, 0, st>>>(w.pose_part, nb, d_pose6, gate);
+        GS2D_LAUNCH_CHECK();
+      }
+    } else if (d_pose6) {
+      GS2D_CUDA_TRY(cudaMemsetAsync(d_pose6, 0, 6 * sizeof(float), st));
+    }
+  } else {
+    render_bwd_kernel<false><<<n_tiles, kTileThreads, 0, st>>>(
+        p4, bins->vals, bins->isect_emit, bins->tile_ranges, *cam, *cfg, tx, t_final, n_last, d_rgb,
+        d_depth, d_normal, d_opacity, w.partials, w.pose_part, gate);
+    GS2D_LAUNCH_CHECK();
+    pose_reduce_kernel<<<1, 256, 0, st>>>(w.pose_part, n_tiles, d_pose6, gate);
+    GS2D_LAUNCH_CHECK();
+  }
+  return GS2D_OK;
+}
+
+}  // namespace gs2d
+
+using namespace gs2d;
+
+extern "C" {
+
+int gs2d_render_fwd(const float* proj, const gs2d_bins* bins, const gs2d_camera* cam,
+                    const gs2d_config* cfg, float* rgb, float* depth, float* normal,
+                    float* opacity, float* t_final, uint32_t* n_last, gs2d_stream stream) {
+  if (!bins) return GS2D_ERR_INVALID_ARG;
+  return render_fwd_launch(proj, bins, cam, cfg, rgb, depth, normal, opacity, t_final, n_last,
+                           bins->status, (cudaStream_t)stream);
+}
+
+int gs2d_render_count(const float* proj, const gs2d_bins* bins, const gs2d_camera* cam,
+                      const gs2d_config* cfg, unsigned long long* counts, gs2d_stream stream) {
+  const int v = validate_tile_cfg(cam, cfg);
+  if (v) return v;
+  if (!proj || !bins || !bins->vals || !bins->tile_ranges || !counts) return GS2D_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  GS2D_CUDA_TRY(cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned long long), st));
+  const int tx = gs2d_tiles_x(cam, cfg), ty = gs2d_tiles_y(cam, cfg);
+  render_fwd_kernel<true><<<tx * ty, kTileThreads, 0, st>>>(
+      reinterpret_cast<const float4*>(proj), bins->vals, bins->tile_ranges, *cam, *cfg, tx, nullptr,
+      nullptr, nullptr, nullptr, nullptr, nullptr, counts, bins->status);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+size_t gs2d_render_bwd_workspace(int n, size_t capacity, int n_tiles) {
+  return render_bwd_ws_bytes(n, capacity, n_tiles, true);
+}
+
+int gs2d_render_bwd(const float* proj, const gs2d_bins* bins, const int32_t* tiles_per_surfel,
+                    const gs2d_surfels* s, const float* pose, const gs2d_camera* cam,
+                    const gs2d_config* cfg, const float* t_final, const uint32_t* n_last,
+                    const float* d_rgb, const float* d_depth, const float* d_normal,
+                    const float* d_opacity, float* d_mu, float* d_quat, float* d_scale,
+                    float* d_opac, float* d_rgb_out, float* d_pose6, void* workspace,
+                    size_t ws_bytes, size_t* ws_needed, gs2d_stream stream) {
+  if (!bins) return GS2D_ERR_INVALID_ARG;
+  return render_bwd_launch(proj, bins, tiles_per_surfel, s, pose, cam, cfg, t_final, n_last, d_rgb,
+                           d_depth, d_normal, d_opacity, d_mu, d_quat, d_scale, d_opac, d_rgb_out,
+                           d_pose6, workspace, ws_bytes, ws_needed, bins->status,
+                           (cudaStream_t)stream);
+}
+
+}  // extern "C"

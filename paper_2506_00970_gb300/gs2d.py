@@ -1,0 +1,370 @@
+"""Thin Python binding of the gs2d C ABI (include/gs2d.h).
+
+Functions named like the C entry points marshal torch CUDA tensors into
+device pointers and call the library; every step of the rasterizer runs in
+the library's CUDA kernels.  PyTorch only provides device memory and streams.
+There is no CPU fallback: importing the binding without the built library
+(``python -c "import __graft_entry__ as g; g.build()"``) raises.
+
+``Rasterizer`` bundles the buffers of one camera for convenience (tests,
+benchmark); it sizes the intersection capacity from the device count, which
+costs a host synchronisation only when the capacity has to grow.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_LIB = None
+
+PROJ_FLOATS = 32
+CONVERGED = 256
+STATUS = {0: "ok", 1: "invalid argument", 2: "workspace", 3: "capacity", 4: "cuda",
+          5: "timeout", 6: "non-finite", 256: "converged"}
+
+
+class Gs2dError(RuntimeError):
+    pass
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float),
+                ("cy", ctypes.c_float), ("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("near_z", ctypes.c_float)]
+
+
+class Surfels(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_void_p), ("quat", ctypes.c_void_p), ("scale", ctypes.c_void_p),
+                ("opacity", ctypes.c_void_p), ("rgb", ctypes.c_void_p), ("n", ctypes.c_int)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("px_per_thread", ctypes.c_int),
+                ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float),
+                ("t_min", ctypes.c_float), ("cutoff_r2", ctypes.c_float)]
+
+
+class Bins(ctypes.Structure):
+    _fields_ = [("keys", ctypes.c_void_p), ("vals", ctypes.c_void_p),
+                ("isect_emit", ctypes.c_void_p), ("surfel_off", ctypes.c_void_p),
+                ("tile_ranges", ctypes.c_void_p), ("n_isect", ctypes.c_void_p),
+                ("status", ctypes.c_void_p), ("capacity", ctypes.c_size_t)]
+
+
+class TrackParams(ctypes.Structure):
+    _fields_ = [("lambda_d", ctypes.c_float), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("weight_decay", ctypes.c_float), ("stop_tol", ctypes.c_float),
+                ("opacity_thresh", ctypes.c_float), ("depth_mode", ctypes.c_int)]
+
+
+EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_string",
+           "gs2d_tiles_x", "gs2d_tiles_y", "gs2d_project", "gs2d_bin_sort_workspace",
+           "gs2d_bin_sort", "gs2d_render_fwd", "gs2d_render_bwd_workspace", "gs2d_render_bwd",
+           "gs2d_tracking_loss", "gs2d_mapping_loss", "gs2d_track_workspace", "gs2d_track_step",
+           "gs2d_track_status", "gs2d_render_count"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise Gs2dError(f"gs2d CUDA library not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        vp, sz, ip = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+        L.gs2d_default_config.restype = Config
+        L.gs2d_default_track_params.restype = TrackParams
+        L.gs2d_status_string.restype = ctypes.c_char_p
+        L.gs2d_status_string.argtypes = [ip]
+        L.gs2d_tiles_x.argtypes = [vp, vp]
+        L.gs2d_tiles_y.argtypes = [vp, vp]
+        L.gs2d_project.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.gs2d_bin_sort_workspace.restype = sz
+        L.gs2d_bin_sort_workspace.argtypes = [ip, sz]
+        L.gs2d_bin_sort.argtypes = [vp, vp, ip, vp, vp, vp, sz, vp, vp, vp]
+        L.gs2d_render_fwd.argtypes = [vp] * 11
+        L.gs2d_render_count.argtypes = [vp] * 6
+        L.gs2d_render_bwd_workspace.restype = sz
+        L.gs2d_render_bwd_workspace.argtypes = [ip, sz, ip]
+        L.gs2d_render_bwd.argtypes = [vp] * 20 + [sz, vp, vp]
+        L.gs2d_tracking_loss.argtypes = [vp] * 13 + [sz, vp, vp]
+        L.gs2d_mapping_loss.argtypes = [vp] * 7 + [ctypes.c_float, ctypes.c_float] + [vp] * 6 + [sz, vp, vp]
+        L.gs2d_track_workspace.restype = sz
+        L.gs2d_track_workspace.argtypes = [ip, sz, vp, vp]
+        L.gs2d_track_step.argtypes = [vp] * 7 + [ip, sz, vp, vp, vp, sz, vp, vp]
+        L.gs2d_track_status.restype = vp
+        L.gs2d_track_status.argtypes = [vp]
+        _LIB = L
+    return _LIB
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _ref(s):
+    return ctypes.byref(s)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def check(rc: int, what: str):
+    if rc != 0:
+        raise Gs2dError(f"{what}: {lib().gs2d_status_string(rc).decode()} ({rc})")
+
+
+def camera(cam) -> Camera:
+    return Camera(cam.fx, cam.fy, cam.cx, cam.cy, int(cam.width), int(cam.height), cam.near)
+
+
+def default_config(tile=(16, 16)) -> Config:
+    c = lib().gs2d_default_config()
+    c.tile_w, c.tile_h = int(tile[0]), int(tile[1])
+    return c
+
+
+def default_track_params(**kw) -> TrackParams:
+    p = lib().gs2d_default_track_params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+# ---------------------------------------------------------------------------
+# device-side containers
+# ---------------------------------------------------------------------------
+class DeviceSurfels:
+    """Surfel parameters as contiguous float32 CUDA tensors (SoA)."""
+
+    def __init__(self, surfels, device="cuda"):
+        def t(a, cols):
+            x = torch.as_tensor(np.asarray(a, np.float32), device=device)
+            return x.reshape(-1, cols).contiguous() if cols > 1 else x.reshape(-1).contiguous()
+        self.mu = t(surfels.mu, 3)
+        self.quat = t(surfels.quat, 4)
+        self.scale = t(surfels.scale, 2)
+        self.opacity = t(surfels.opacity, 1)
+        self.rgb = t(surfels.rgb, 3)
+
+    @classmethod
+    def from_tensors(cls, mu, quat, scale, opacity, rgb):
+        o = cls.__new__(cls)
+        o.mu, o.quat, o.scale, o.opacity, o.rgb = (x.contiguous() for x in (mu, quat, scale, opacity, rgb))
+        return o
+
+    @property
+    def n(self) -> int:
+        return int(self.mu.shape[0])
+
+    def struct(self) -> Surfels:
+        return Surfels(self.mu.data_ptr(), self.quat.data_ptr(), self.scale.data_ptr(),
+                       self.opacity.data_ptr(), self.rgb.data_ptr(), self.n)
+
+
+def pose_tensor(pose, device="cuda") -> torch.Tensor:
+    v = np.concatenate([np.asarray(pose.R, np.float64).reshape(-1), np.asarray(pose.t, np.float64)])
+    return torch.tensor(v, dtype=torch.float32, device=device)
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+def gs2d_project(surf: DeviceSurfels, cam: Camera, pose: torch.Tensor, cfg: Config,
+                 proj: torch.Tensor, tiles: torch.Tensor, stream=None):
+    s = surf.struct()
+    check(lib().gs2d_project(_ref(s), _ref(cam), _ptr(pose), _ref(cfg), _ptr(proj), _ptr(tiles),
+                             _stream(stream)), "gs2d_project")
+
+
+def gs2d_bin_sort_workspace(n: int, capacity: int) -> int:
+    return int(lib().gs2d_bin_sort_workspace(int(n), int(capacity)))
+
+
+def gs2d_bin_sort(proj, tiles, n, cam: Camera, cfg: Config, workspace: torch.Tensor, bins: Bins,
+                  stream=None):
+    check(lib().gs2d_bin_sort(_ptr(proj), _ptr(tiles), int(n), _ref(cam), _ref(cfg),
+                              _ptr(workspace), workspace.numel() * workspace.element_size(), None,
+                              _ref(bins), _stream(stream)), "gs2d_bin_sort")
+
+
+def gs2d_render_fwd(proj, bins: Bins, cam: Camera, cfg: Config, rgb, depth, normal, opacity,
+                    t_final, n_last, stream=None):
+    check(lib().gs2d_render_fwd(_ptr(proj), _ref(bins), _ref(cam), _ref(cfg), _ptr(rgb),
+                                _ptr(depth), _ptr(normal), _ptr(opacity), _ptr(t_final),
+                                _ptr(n_last), _stream(stream)), "gs2d_render_fwd")
+
+
+def gs2d_render_count(proj, bins: Bins, cam: Camera, cfg: Config, counts, stream=None):
+    check(lib().gs2d_render_count(_ptr(proj), _ref(bins), _ref(cam), _ref(cfg), _ptr(counts),
+                                  _stream(stream)), "gs2d_render_count")
+
+
+def gs2d_render_bwd_workspace(n, capacity, n_tiles) -> int:
+    return int(lib().gs2d_render_bwd_workspace(int(n), int(capacity), int(n_tiles)))
+
+
+def gs2d_render_bwd(proj, bins: Bins, tiles, surf: DeviceSurfels, pose, cam: Camera, cfg: Config,
+                    t_final, n_last, d_rgb, d_depth, d_normal, d_opacity, d_mu, d_quat, d_scale,
+                    d_opac, d_rgb_out, d_pose6, workspace, stream=None):
+    s = surf.struct()
+    check(lib().gs2d_render_bwd(_ptr(proj), _ref(bins), _ptr(tiles), _ref(s), _ptr(pose),
+                                _ref(cam), _ref(cfg), _ptr(t_final), _ptr(n_last), _ptr(d_rgb),
+                                _ptr(d_depth), _ptr(d_normal), _ptr(d_opacity), _ptr(d_mu),
+                                _ptr(d_quat), _ptr(d_scale), _ptr(d_opac), _ptr(d_rgb_out),
+                                _ptr(d_pose6), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), None,
+                                _stream(stream)), "gs2d_render_bwd")
+
+
+def gs2d_tracking_loss(rgb, depth, normal, opacity, obs_rgb, obs_depth, cam: Camera,
+                       prm: TrackParams, g_rgb, g_depth, g_opacity, loss_out, workspace,
+                       stream=None):
+    check(lib().gs2d_tracking_loss(_ptr(rgb), _ptr(depth), _ptr(normal), _ptr(opacity),
+                                   _ptr(obs_rgb), _ptr(obs_depth), _ref(cam), _ref(prm),
+                                   _ptr(g_rgb), _ptr(g_depth), _ptr(g_opacity), _ptr(loss_out),
+                                   _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                   None, _stream(stream)), "gs2d_tracking_loss")
+
+
+def gs2d_mapping_loss(rgb, depth, normal, opacity, obs_rgb, obs_depth, cam: Camera, w_d, w_n,
+                      g_rgb, g_depth, g_normal, g_opacity, loss_out, workspace, stream=None):
+    check(lib().gs2d_mapping_loss(_ptr(rgb), _ptr(depth), _ptr(normal), _ptr(opacity),
+                                  _ptr(obs_rgb), _ptr(obs_depth), _ref(cam), float(w_d), float(w_n),
+                                  _ptr(g_rgb), _ptr(g_depth), _ptr(g_normal), _ptr(g_opacity),
+                                  _ptr(loss_out), _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), None,
+                                  _stream(stream)), "gs2d_mapping_loss")
+
+
+def gs2d_track_workspace(n, capacity, cam: Camera, cfg: Config) -> int:
+    return int(lib().gs2d_track_workspace(int(n), int(capacity), _ref(cam), _ref(cfg)))
+
+
+def gs2d_track_step(surf: DeviceSurfels, cam: Camera, cfg: Config, prm: TrackParams, pose,
+                    obs_rgb, obs_depth, n_iter, capacity, loss_hist, pose_hist, workspace,
+                    stream=None):
+    s = surf.struct()
+    check(lib().gs2d_track_step(_ref(s), _ref(cam), _ref(cfg), _ref(prm), _ptr(pose),
+                                _ptr(obs_rgb), _ptr(obs_depth), int(n_iter), int(capacity),
+                                _ptr(loss_hist), _ptr(pose_hist), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), None,
+                                _stream(stream)), "gs2d_track_step")
+
+
+def gs2d_track_status(workspace) -> torch.Tensor:
+    """The int32 status word of a track workspace, as a 1-element view."""
+    return workspace.view(torch.int32)[:1]
+
+
+# ---------------------------------------------------------------------------
+# convenience: buffers of one camera
+# ---------------------------------------------------------------------------
+def _bytes(n, device):
+    return torch.empty(max(int(n), 1), dtype=torch.uint8, device=device)
+
+
+class Rasterizer:
+    """Owns the intermediate buffers for rendering one camera:
+    project -> bin_sort -> render_fwd, and render_bwd."""
+
+    def __init__(self, cam, n: int, capacity: int | None = None, tile=(16, 16), device="cuda",
+                 keys: bool = False):
+        self.cam = camera(cam)
+        self.cfg = default_config(tile)
+        self.n = int(n)
+        self.device = device
+        self.tiles_x = int(lib().gs2d_tiles_x(_ref(self.cam), _ref(self.cfg)))
+        self.tiles_y = int(lib().gs2d_tiles_y(_ref(self.cam), _ref(self.cfg)))
+        self.n_tiles = self.tiles_x * self.tiles_y
+        self.want_keys = keys
+        self.proj = torch.empty(max(self.n, 1) * PROJ_FLOATS, dtype=torch.float32, device=device)
+        self.tiles = torch.empty(max(self.n, 1), dtype=torch.int32, device=device)
+        self.surfel_off = torch.empty(max(self.n, 1), dtype=torch.int32, device=device)
+        self.ranges = torch.empty(2 * self.n_tiles, dtype=torch.int32, device=device)
+        self.n_isect = torch.zeros(1, dtype=torch.int32, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        H, W = int(cam.height), int(cam.width)
+        self.H, self.W = H, W
+        f = dict(dtype=torch.float32, device=device)
+        self.rgb = torch.empty(H, W, 3, **f)
+        self.depth = torch.empty(H, W, **f)
+        self.normal = torch.empty(H, W, 3, **f)
+        self.opacity = torch.empty(H, W, **f)
+        self.t_final = torch.empty(H, W, **f)
+        self.n_last = torch.empty(H, W, dtype=torch.int32, device=device)
+        self._alloc(capacity if capacity is not None else max(4 * self.n, 1024))
+
+    def _alloc(self, capacity):
+        self.capacity = int(capacity)
+        d = self.device
+        self.vals = torch.empty(self.capacity, dtype=torch.int32, device=d)
+        self.emit = torch.empty(self.capacity, dtype=torch.int32, device=d)
+        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=d) if self.want_keys else None
+        self.sort_ws = _bytes(gs2d_bin_sort_workspace(self.n, self.capacity), d)
+        self.bwd_ws = _bytes(gs2d_render_bwd_workspace(self.n, self.capacity, self.n_tiles), d)
+        self.bins = Bins(_ptr(self.keys).value if self.keys is not None else None,
+                         self.vals.data_ptr(), self.emit.data_ptr(), self.surfel_off.data_ptr(),
+                         self.ranges.data_ptr(), self.n_isect.data_ptr(), self.status.data_ptr(),
+                         self.capacity)
+
+    def project(self, surf: DeviceSurfels, pose: torch.Tensor, stream=None):
+        gs2d_project(surf, self.cam, pose, self.cfg, self.proj, self.tiles, stream)
+
+    def bin_sort(self, stream=None, grow: bool = True):
+        self.status.zero_()
+        gs2d_bin_sort(self.proj, self.tiles, self.n, self.cam, self.cfg, self.sort_ws, self.bins,
+                      stream)
+        if grow:
+            st = int(self.status.item())
+            if st == 3:
+                need = int(self.n_isect.item())
+                self._alloc(int(need * 1.25) + 1024)
+                self.status.zero_()
+                gs2d_bin_sort(self.proj, self.tiles, self.n, self.cam, self.cfg, self.sort_ws,
+                              self.bins, stream)
+                st = int(self.status.item())
+            if st != 0:
+                raise Gs2dError(f"gs2d_bin_sort device status {STATUS.get(st, st)}")
+
+    def render_fwd(self, stream=None):
+        gs2d_render_fwd(self.proj, self.bins, self.cam, self.cfg, self.rgb, self.depth, self.normal,
+                        self.opacity, self.t_final, self.n_last, stream)
+
+    def forward(self, surf: DeviceSurfels, pose: torch.Tensor, stream=None):
+        self.project(surf, pose, stream)
+        self.bin_sort(stream)
+        self.render_fwd(stream)
+        return dict(rgb=self.rgb, depth=self.depth, normal=self.normal, opacity=self.opacity,
+                    t_final=self.t_final, n_last=self.n_last)
+
+    def backward(self, surf: DeviceSurfels, pose, d_rgb, d_depth, d_normal=None, d_opacity=None,
+                 full: bool = True, stream=None):
+        n = self.n
+        f = dict(dtype=torch.float32, device=self.device)
+        d_pose6 = torch.empty(6, **f)
+        out = dict(pose6=d_pose6)
+        if full:
+            out.update(mu=torch.empty(n, 3, **f), quat=torch.empty(n, 4, **f),
+                       scale=torch.empty(n, 2, **f), opacity=torch.empty(n, **f),
+                       rgb=torch.empty(n, 3, **f))
+        gs2d_render_bwd(self.proj, self.bins, self.tiles, surf, pose, self.cam, self.cfg,
+                        self.t_final, self.n_last, d_rgb.contiguous(), d_depth.contiguous(),
+                        None if d_normal is None else d_normal.contiguous(),
+                        None if d_opacity is None else d_opacity.contiguous(),
+                        out.get("mu"), out.get("quat"), out.get("scale"), out.get("opacity"),
+                        out.get("rgb"), d_pose6, self.bwd_ws, stream)
+        return out

@@ -1,0 +1,79 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the
+C ABI binding and compare with the oracle on the same seeded inputs."""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_2506_00970_gb300 import scenes
+
+# tolerances of the parity contract: colour / opacity max-abs, depth and
+# normal relative, gradients relative
+TOL_ABS = 1e-4
+TOL_REL = 1e-4
+TOL_GRAD = 1e-3
+
+
+def to_np(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def gpu_render(surfels, cam, pose, tile=(16, 16), capacity=None, keys=False):
+    from paper_2506_00970_gb300 import gs2d
+    import torch
+    ds = gs2d.DeviceSurfels(surfels)
+    r = gs2d.Rasterizer(cam, ds.n, capacity=capacity, tile=tile, keys=keys)
+    pose_t = gs2d.pose_tensor(pose)
+    out = r.forward(ds, pose_t)
+    torch.cuda.synchronize()
+    return r, ds, pose_t, {k: v.detach().cpu().numpy() for k, v in out.items()}
+
+
+def image_mismatch(a, b, rel, atol):
+    """Elementwise |a-b| <= rel*|b| + atol over pixels (any channel)."""
+    bad = np.abs(a - b) > rel * np.abs(b) + atol
+    if bad.ndim == 3:
+        bad = bad.any(-1)
+    return bad
+
+
+GRAZING_COS = 0.02   # a blended surfel within ~1.1 degrees of edge-on
+
+
+def assert_images_close(gpu, orc, max_bad_frac=1e-4, min_bad=2, grazing_frac=1e-2):
+    """Colour/opacity within TOL_ABS absolute; depth within TOL_REL of the
+    depth; the normal image N = sum w t_nc within TOL_REL of the pixel's
+    opacity O = sum w (which bounds |N|; per-component relative error is
+    meaningless where normals of different surfels cancel).  Pixels whose
+    evaluation sits on a threshold may differ: at most max_bad_frac of them
+    (at least min_bad).  Pixels that blend a surfel seen within ~1 degree of
+    edge-on (oracle min_cos < GRAZING_COS) have an ill-conditioned FP32
+    intersection; they are held to 10x the tolerance and may make up at most
+    grazing_frac of the image."""
+    P = orc["opacity"].size
+    allow = max(min_bad, int(max_bad_frac * P))
+    g = {k: np.asarray(gpu[k], np.float64) for k in ("rgb", "opacity", "depth", "normal")}
+    bad = {
+        "rgb": (np.abs(g["rgb"] - orc["rgb"]) > TOL_ABS).any(-1),
+        "opacity": np.abs(g["opacity"] - orc["opacity"]) > TOL_ABS,
+        "depth": np.abs(g["depth"] - orc["depth"]) > TOL_REL * np.abs(orc["depth"]) + 1e-6,
+        "normal": np.abs(g["normal"] - orc["normal"]).max(-1) > TOL_REL * orc["opacity"] + 1e-6,
+    }
+    bad_any = np.zeros(orc["opacity"].shape, bool)
+    for v in bad.values():
+        bad_any |= v
+    grazing = orc["min_cos"] < GRAZING_COS if "min_cos" in orc else np.zeros_like(bad_any)
+    report = {k: int((v & ~grazing).sum()) for k, v in bad.items()}
+    report["grazing_px"] = int(grazing.sum())
+    assert (bad_any & ~grazing).sum() <= allow, (report, allow)
+    assert grazing.sum() <= max(min_bad, grazing_frac * P), report
+    loose = {
+        "rgb": (np.abs(g["rgb"] - orc["rgb"]) > 10 * TOL_ABS).any(-1),
+        "opacity": np.abs(g["opacity"] - orc["opacity"]) > 10 * TOL_ABS,
+        "depth": np.abs(g["depth"] - orc["depth"]) > 10 * TOL_REL * np.abs(orc["depth"]) + 1e-5,
+        "normal": np.abs(g["normal"] - orc["normal"]).max(-1) > 10 * TOL_REL * orc["opacity"] + 1e-5,
+    }
+    loose_bad = np.zeros_like(bad_any)
+    for v in loose.values():
+        loose_bad |= v
+    assert (loose_bad & grazing).sum() <= allow, report
+    return report, ~bad_any

@@ -1,0 +1,86 @@
+"""The C ABI library builds for sm_103a, loads without a GPU and exports every
+entry point that include/gs2d.h declares; the binding refuses to run without
+the library (no CPU fallback).  No compute calls here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "gs2d.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    names = set(re.findall(r"\b(gs2d_\w+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    from paper_2506_00970_gb300 import build
+    path = build.build()
+    return path
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("gs2d_project", "gs2d_bin_sort", "gs2d_render_fwd", "gs2d_render_bwd",
+                     "gs2d_track_step"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    lib = ctypes.CDLL(built_lib)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_lists_every_symbol(built_lib):
+    from paper_2506_00970_gb300 import gs2d
+    assert set(gs2d.EXPORTS) == set(_declared())
+
+
+def test_host_only_entry_points(built_lib):
+    """Entry points that do not touch the device: defaults and sizes."""
+    from paper_2506_00970_gb300 import gs2d
+    L = gs2d.lib()
+    cfg = gs2d.default_config()
+    assert (cfg.tile_w, cfg.tile_h) == (16, 16)
+    assert cfg.alpha_max == pytest.approx(0.99) and cfg.t_min == pytest.approx(1e-4)
+    prm = gs2d.default_track_params()
+    assert prm.lr == pytest.approx(1e-3) and prm.opacity_thresh == pytest.approx(0.95)
+    cam = gs2d.Camera(525.0, 525.0, 320.0, 240.0, 640, 480, 0.05)
+    assert L.gs2d_tiles_x(ctypes.byref(cam), ctypes.byref(cfg)) == 40
+    assert L.gs2d_tiles_y(ctypes.byref(cam), ctypes.byref(cfg)) == 30
+    assert gs2d.gs2d_bin_sort_workspace(200_000, 1_000_000) > 0
+    assert gs2d.gs2d_track_workspace(1000, 10_000, cam, cfg) > 0
+    assert L.gs2d_status_string(3) == b"intersection capacity exceeded"
+
+
+def test_invalid_arguments_rejected_without_launch(built_lib):
+    from paper_2506_00970_gb300 import gs2d
+    L = gs2d.lib()
+    cfg = gs2d.default_config()
+    cam = gs2d.Camera(525.0, 525.0, 320.0, 240.0, 640, 480, 0.05)
+    # NULL surfels -> invalid argument, nothing launched
+    assert L.gs2d_project(None, ctypes.byref(cam), None, ctypes.byref(cfg), None, None, None) == 1
+    # missing workspace -> GS2D_ERR_WORKSPACE and the needed size
+    need = ctypes.c_size_t(0)
+    bins = gs2d.Bins(None, 8, 8, 8, 8, 8, 8, 100)
+    rc = L.gs2d_bin_sort(None, None, 0, ctypes.byref(cam), ctypes.byref(cfg), None, 0,
+                         ctypes.byref(need), ctypes.byref(bins), None)
+    assert rc == 2 and need.value > 0
+    bad_cfg = gs2d.default_config((16, 8))   # 128 threads: not a supported tile
+    assert L.gs2d_render_fwd(8, ctypes.byref(bins), ctypes.byref(cam), ctypes.byref(bad_cfg),
+                             8, 8, 8, 8, 8, 8, None) == 1
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_2506_00970_gb300 import build, gs2d
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(gs2d, "_LIB", None)
+    with pytest.raises(gs2d.Gs2dError):
+        gs2d.lib()
