@@ -155,6 +155,26 @@ int gs2d_bin_sort(const float* proj, const int32_t* tiles_per_surfel, int n,
                   const gs2d_camera* cam, const gs2d_config* cfg, void* workspace,
                   size_t ws_bytes, size_t* ws_needed, const gs2d_bins* bins, gs2d_stream stream);
 
+/* gs2d_bin_sort without a workspace argument: it allocates nothing.  The
+ * paper has no counterpart; this serves callers that cannot allocate device
+ * memory when they bin -- code inside a CUDA stream capture (cudaMalloc is
+ * not allowed there), real-time loops with a no-allocation rule, or host
+ * frameworks that own all device memory and pass only inputs and outputs.
+ * Scratch is a file-scope __device__ array of GS2D_SORT_STATIC_SCRATCH_BYTES
+ * that every GPU loading the library holds until the process exits.  Sizes
+ * whose gs2d_bin_sort_workspace(n, bins->capacity) exceeds it are rejected
+ * with GS2D_ERR_WORKSPACE before anything is launched (about 200k surfels
+ * with a capacity of 1M intersections fit).  The first call on each device
+ * looks up that device's copy of the array (cudaGetSymbolAddress, with the
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls on a device share the one array: calls whose kernels
+ * may overlap on the GPU (different streams without ordering) race and must
+ * be serialised by the caller.  Results equal gs2d_bin_sort's. */
+#define GS2D_SORT_STATIC_SCRATCH_BYTES (32u << 20)
+int gs2d_bin_sort_static(const float* proj, const int32_t* tiles_per_surfel, int n,
+                         const gs2d_camera* cam, const gs2d_config* cfg, const gs2d_bins* bins,
+                         gs2d_stream stream);
+
 /* Front-to-back compositing (Eq. alpha_blending) of colour (rgb [H*W*3]),
  * literal depth D = sum w z ([H*W]), normal sum w t_nc ([H*W*3]) and opacity
  * O = 1 - T ([H*W]); also the final transmittance t_final [H*W] and n_last

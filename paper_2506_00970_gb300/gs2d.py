@@ -67,7 +67,7 @@ EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_stri
            "gs2d_tiles_x", "gs2d_tiles_y", "gs2d_project", "gs2d_bin_sort_workspace",
            "gs2d_bin_sort", "gs2d_render_fwd", "gs2d_render_bwd_workspace", "gs2d_render_bwd",
            "gs2d_tracking_loss", "gs2d_mapping_loss", "gs2d_track_workspace", "gs2d_track_step",
-           "gs2d_track_status", "gs2d_render_count"]
+           "gs2d_track_status", "gs2d_render_count", "gs2d_bin_sort_static"]
 
 
 def lib_path() -> str:
@@ -93,6 +93,7 @@ def lib():
         L.gs2d_bin_sort_workspace.restype = sz
         L.gs2d_bin_sort_workspace.argtypes = [ip, sz]
         L.gs2d_bin_sort.argtypes = [vp, vp, ip, vp, vp, vp, sz, vp, vp, vp]
+        L.gs2d_bin_sort_static.argtypes = [vp, vp, ip, vp, vp, vp, vp]
         L.gs2d_render_fwd.argtypes = [vp] * 11
         L.gs2d_render_count.argtypes = [vp] * 6
         L.gs2d_render_bwd_workspace.restype = sz
@@ -199,6 +200,13 @@ def gs2d_bin_sort(proj, tiles, n, cam: Camera, cfg: Config, workspace: torch.Ten
     check(lib().gs2d_bin_sort(_ptr(proj), _ptr(tiles), int(n), _ref(cam), _ref(cfg),
                               _ptr(workspace), workspace.numel() * workspace.element_size(), None,
                               _ref(bins), _stream(stream)), "gs2d_bin_sort")
+
+
+def gs2d_bin_sort_static(proj, tiles, n, cam: Camera, cfg: Config, bins: Bins, stream=None):
+    """gs2d_bin_sort with the library's own fixed device scratch (no
+    workspace argument, no allocation)."""
+    check(lib().gs2d_bin_sort_static(_ptr(proj), _ptr(tiles), int(n), _ref(cam), _ref(cfg),
+                                     _ref(bins), _stream(stream)), "gs2d_bin_sort_static")
 
 
 def gs2d_render_fwd(proj, bins: Bins, cam: Camera, cfg: Config, rgb, depth, normal, opacity,
