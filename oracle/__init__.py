@@ -123,7 +123,9 @@ def render_bwd(surfels, cam, pose, g_rgb, g_depth, g_normal, g_opacity, rule: Ru
                pixels=None, n_threads: int = 0):
     """Gradients of L w.r.t. the surfel parameters and the pose tangent,
     given dL/d(rgb, depth, normal, opacity) of the rendered images (or of the
-    listed pixels).  Returns dict(mu, quat, scale, opacity, rgb, pose6)."""
+    listed pixels).  Returns dict(mu, quat, scale, opacity, rgb, pose6) and
+    min_cos, per surfel the smallest |cos| between a ray it blends into and
+    its normal (an ill-conditioning measure for the parity tests)."""
     mu, q, sc, op, rgb = _surfel_arrays(surfels)
     W, H = cam.width, cam.height
     pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int32)
@@ -135,13 +137,14 @@ def render_bwd(surfels, cam, pose, g_rgb, g_depth, g_normal, g_opacity, rule: Ru
     d_o = np.zeros(n)
     d_c = np.zeros((n, 3))
     d_pose = np.zeros(6)
+    d_mc = np.ones(n)
     _lib().orc_render_bwd(n, _p(mu), _p(q), _p(sc), _p(op), _p(rgb), _p(_cam5(cam)), W, H,
                           _p(_d(pose.R)), _p(_d(pose.t)), _p(rule.vec()), int(rule.exact), npx,
                           _p(pix, ctypes.c_int), _p(_d(g_rgb).reshape(-1)),
                           _p(_d(g_depth).reshape(-1)), _p(_d(g_normal).reshape(-1)),
                           _p(_d(g_opacity).reshape(-1)), _p(d_mu), _p(d_q), _p(d_s), _p(d_o),
-                          _p(d_c), _p(d_pose), int(n_threads or default_threads()))
-    return dict(mu=d_mu, quat=d_q, scale=d_s, opacity=d_o, rgb=d_c, pose6=d_pose)
+                          _p(d_c), _p(d_pose), _p(d_mc), int(n_threads or default_threads()))
+    return dict(mu=d_mu, quat=d_q, scale=d_s, opacity=d_o, rgb=d_c, pose6=d_pose, min_cos=d_mc)
 
 
 def tile_rects(surfels, cam, pose, rule: Rule = Rule(), tile=(16, 16)):

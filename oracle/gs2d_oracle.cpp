@@ -304,14 +304,17 @@ int orc_render(int n, const double* mu, const double* quat, const double* scale,
 
 // Reverse mode of orc_render.  g_* are dL/d(rgb, depth, normal, opacity) per
 // listed pixel.  Writes dL/d(mu, quat (raw), scale, opacity, rgb) per surfel
-// and dL/dtau, tau = (rho, theta), for the left perturbation of T_cw.
+// and dL/dtau, tau = (rho, theta), for the left perturbation of T_cw; and, if
+// d_mincos is non-NULL, per surfel the smallest |cos| between a pixel ray it
+// blends into and its normal (1 if it blends into none): near zero marks a
+// surfel seen edge-on, whose intersection is ill-conditioned.
 int orc_render_bwd(int n, const double* mu, const double* quat, const double* scale,
                    const double* opacity, const double* rgb, const double* cam5, int W, int H,
                    const double* R9, const double* t3, const double* rule4, int exact, int n_pix,
                    const int* pix, const double* g_rgb, const double* g_depth,
                    const double* g_normal, const double* g_opac, double* d_mu, double* d_quat,
                    double* d_scale, double* d_opacity, double* d_rgb, double* d_pose6,
-                   int n_threads) {
+                   double* d_mincos, int n_threads) {
   const Cam cam{cam5[0], cam5[1], cam5[2], cam5[3], cam5[4], W, H};
   const Rule rule{rule4[0], rule4[1], rule4[2], rule4[3], exact};
   const std::vector<CamSurfel> S = camera_surfels(n, mu, quat, scale, opacity, rgb, R9, t3);
@@ -326,8 +329,10 @@ int orc_render_bwd(int n, const double* mu, const double* quat, const double* sc
   struct Acc {
     V3 g_mu_c, g_mu, g_mv, g_tn_c, g_col;
     double g_alpha;
+    double mincos;  // smallest |cos(ray, normal)| over the pixels it blends into
   };
-  std::vector<std::vector<Acc>> acc(nt, std::vector<Acc>(n, Acc{}));
+  std::vector<std::vector<Acc>> acc(nt, std::vector<Acc>(n, Acc{mk(0, 0, 0), mk(0, 0, 0), mk(0, 0, 0),
+                                                                 mk(0, 0, 0), mk(0, 0, 0), 0.0, 1.0}));
 #pragma omp parallel num_threads(nt)
   {
 #ifdef _OPENMP
@@ -366,6 +371,7 @@ int orc_render_bwd(int n, const double* mu, const double* quat, const double* sc
         g_Tm += g_w * it.a;
         gT = g_Tm;
         Acc& a = A[it.id];
+        a.mincos = std::min(a.mincos, std::fabs(dot(r, s.tn_c)) / std::sqrt(dot(r, r)));
         a.g_col += w * gC;
         a.g_tn_c += w * gN;
         double g_z = w * gD;
@@ -398,8 +404,10 @@ int orc_render_bwd(int n, const double* mu, const double* quat, const double* sc
   V3 g_rho = mk(0, 0, 0), g_theta = mk(0, 0, 0);
   for (int i = 0; i < n; ++i) {
     Acc t{};
+    t.mincos = 1.0;
     for (int th = 0; th < nt; ++th) {
       const Acc& a = acc[th][i];
+      t.mincos = std::min(t.mincos, a.mincos);
       t.g_mu_c += a.g_mu_c;
       t.g_mu += a.g_mu;
       t.g_mv += a.g_mv;
@@ -433,6 +441,7 @@ int orc_render_bwd(int n, const double* mu, const double* quat, const double* sc
     const double qd = s.qn[0] * gq[0] + s.qn[1] * gq[1] + s.qn[2] * gq[2] + s.qn[3] * gq[3];
     for (int k = 0; k < 4; ++k) d_quat[4 * i + k] = (gq[k] - s.qn[k] * qd) / s.qlen;
     d_opacity[i] = t.g_alpha;
+    if (d_mincos) d_mincos[i] = t.mincos;
     d_rgb[3 * i] = t.g_col.x;
     d_rgb[3 * i + 1] = t.g_col.y;
     d_rgb[3 * i + 2] = t.g_col.z;
