@@ -42,9 +42,9 @@ WORKLOAD = ("tracking-scale room: 200k surfels on a 5x4x3 m room with 20 boxes/s
 ORACLE_CROP = 32          # reference arm / cpu baseline: a 32x32 pixel crop per step
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes per launch of the roofline kernel from an ncu capture of the
-# same workload (profiles/render_fwd_tracking_640x480.md); None if the kernel
-# changed since.
-TRAFFIC_BYTES = {"render_fwd": None, "render_bwd_pose": None}
+# same workload (profiles/track_tile_tracking_640x480.md); None if the kernel
+# changed since the capture.
+TRAFFIC_BYTES = {"track_tile": None}
 
 
 def _args():
@@ -193,6 +193,7 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
 #  the 6-vector accumulation); its evaluated pairs are bounded by the
 #  forward's counts.
 FLOPS_EVAL, FLOPS_IN, FLOPS_BLEND, FLOPS_BWD_BLEND = 17, 4, 17, 80
+FLOPS_LOSS_PIXEL = 20   # masks, three colour and one depth difference, signs
 
 
 def run_ours(args):
@@ -231,6 +232,11 @@ def run_ours(args):
 
     e0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     e1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    # the fused tile kernel, timed live inside the timed region
+    k0 = [torch.cuda.Event(enable_timing=True) for _ in range(K * N_ITER)]
+    k1 = [torch.cuda.Event(enable_timing=True) for _ in range(K * N_ITER)]
+    gs2d.gs2d_profile_track_kernel(k0, k1)
+    torch.cuda.synchronize()
     hist = []
     if ws_n > 1:
         torch.distributed.barrier()
@@ -247,6 +253,9 @@ def run_ours(args):
     if ws_n > 1:
         torch.distributed.barrier()
     wall = time.perf_counter() - t_wall
+    n_k = gs2d.gs2d_profile_track_kernel_count()
+    fused_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(k0[:n_k], k1[:n_k])]))
+    gs2d.gs2d_profile_track_kernel([], [])
     st = int(gs2d.gs2d_track_status(ws).item())
     if st not in (0, gs2d.CONVERGED):
         raise RuntimeError(f"track status {st}")
@@ -320,7 +329,7 @@ def run_ours(args):
     h2d = h_rgb[0].numel() * 4 + h_d[0].numel() * 4 + 12 * 4
     d2h = 12 * 4 + 4
 
-    roof = roofline(r, ds, frames, cam, cfg, stream, ms_iter)
+    roof = roofline(r, ds, frames, cam, cfg, stream, ms_iter, fused_ms)
 
     if rank == 0:
         clocks = clk.summary()
@@ -349,17 +358,18 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-# kernels per tracking iteration: project 1; bin_sort 11 (init, depth keys,
-# 4 depth passes, emit scan, emit, 2 tile passes, finalize); render_fwd 1;
-# tracking loss 2; render_bwd (pose) 2; AdamW + retraction 1.  Plus one reset
-# per frame.
-LAUNCHES_PER_ITER = 18
+# kernels per tracking iteration: project 1; bin_sort 5 (init, count scan,
+# tile scan, scatter, tile sort); fused render + loss + pose backward 1;
+# reduce + AdamW + retraction 1.  Plus one reset per frame.
+LAUNCHES_PER_ITER = 8
 
 
-def roofline(r, ds, frames, cam, cfg, stream, ms_iter):
-    """Average duration of the compositing kernels on the workload's start
-    poses (CUDA events around each launch on the launching stream), their
-    algorithmic FP32 work from the pair counts, against the FP32 peak."""
+def roofline(r, ds, frames, cam, cfg, stream, ms_iter, fused_ms):
+    """The fused tile kernel (render + loss + pose backward, the largest share
+    of a tracking iteration), timed live in the timed region, and the
+    standalone forward and pose-backward kernels timed here on the same start
+    poses (CUDA events around each launch on the launching stream).  Work is
+    the algorithmic FP32 flops from the pair counts, against the FP32 peak."""
     import torch
     from paper_2506_00970_gb300 import gs2d
     pk, src = peaks()
@@ -400,18 +410,22 @@ def roofline(r, ds, frames, cam, cfg, stream, ms_iter):
         bwd_ms.append(np.mean([ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(R)]))
     tf = np.mean(fwd_ms) / 1e3
     tb = np.mean(bwd_ms) / 1e3
+    P = cam.width * cam.height
+    work_fused = np.mean(work_f) + np.mean(work_b) + FLOPS_LOSS_PIXEL * P
+    tfu = fused_ms / 1e3
+    afu = work_fused / tfu / 1e12
+    fused = {"kernel": "track_tile_kernel (render + tracking loss + pose backward)", "bound": "alu",
+             "achieved": afu, "peak": peak, "unit": "TFLOP/s", "frac": afu / peak,
+             "traffic": TRAFFIC_BYTES["track_tile"], "launch_ms": fused_ms,
+             "share_of_iter": fused_ms / ms_iter, "flop_per_launch": work_fused,
+             "peak_note": f"FP32 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz (of measured max clock)"}
     af = np.mean(work_f) / tf / 1e12
     ab = np.mean(work_b) / tb / 1e12
     fwd = {"kernel": "render_fwd_kernel", "bound": "alu", "achieved": af, "peak": peak,
-           "unit": "TFLOP/s", "frac": af / peak, "traffic": TRAFFIC_BYTES["render_fwd"],
-           "launch_ms": tf * 1e3, "share_of_iter": tf * 1e3 / ms_iter,
-           "peak_note": f"FP32 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz"}
+           "unit": "TFLOP/s", "frac": af / peak, "launch_ms": tf * 1e3}
     bwd = {"kernel": "render_bwd_kernel<pose> + pose_reduce", "bound": "alu", "achieved": ab,
-           "peak": peak, "unit": "TFLOP/s", "frac": ab / peak,
-           "traffic": TRAFFIC_BYTES["render_bwd_pose"], "launch_ms": tb * 1e3,
-           "share_of_iter": tb * 1e3 / ms_iter}
-    main, other = (fwd, bwd) if tf >= tb else (bwd, fwd)
-    return {"main": main, "other": other}
+           "peak": peak, "unit": "TFLOP/s", "frac": ab / peak, "launch_ms": tb * 1e3}
+    return {"main": fused, "other": [fwd, bwd]}
 
 
 def cpu_baseline(s, cam, fr):

@@ -253,6 +253,17 @@ int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_co
 /* Device pointer of the status word inside a track workspace (int32). */
 int32_t* gs2d_track_status(void* workspace);
 
+/* Diagnostic timing of the fused tile kernel of gs2d_track_step: while set,
+ * every later launch of that kernel (in any gs2d_track_step call, in launch
+ * order) is bracketed by cudaEventRecord(start_events[i]) and
+ * cudaEventRecord(stop_events[i]) on the call's stream, until n launches
+ * have been recorded.  The events are caller-created cudaEvent_t handles
+ * that must stay alive meanwhile.  n = 0 switches it off.  No work is
+ * skipped or reordered.  gs2d_profile_track_kernel_count() = launches
+ * recorded so far.  Not thread safe. */
+int gs2d_profile_track_kernel(void* const* start_events, void* const* stop_events, int n);
+int gs2d_profile_track_kernel_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,6 +19,14 @@ int render_fwd_launch(const float* proj, const gs2d_bins* bins, const gs2d_camer
                       float* opacity, float* t_final, uint32_t* n_last, const int32_t* gate,
                       cudaStream_t st);
 
+// Fused tracking iteration (forward, tracking loss, pose backward) per tile:
+// loss_part [n_tiles] (already divided by the pixel count), pose_part
+// [n_tiles * 6].
+int track_tile_launch(const float* proj, const gs2d_bins* bins, const gs2d_camera* cam,
+                      const gs2d_config* cfg, const float* obs_rgb, const float* obs_depth,
+                      const gs2d_track_params* prm, float* loss_part, float* pose_part,
+                      const int32_t* gate, cudaStream_t st);
+
 size_t render_bwd_ws_bytes(int n, size_t cap, int n_tiles, bool full);
 int render_bwd_launch(const float* proj, const gs2d_bins* bins, const int32_t* tiles_per_surfel,
                       const gs2d_surfels* s, const float* pose, const gs2d_camera* cam,

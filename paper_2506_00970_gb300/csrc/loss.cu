@@ -3,13 +3,12 @@
 // partial sums of the loss reduced in a fixed order.
 #include "gs2d_common.cuh"
 #include "gs2d_internal.h"
+#include "loss_pixel.cuh"
 
 namespace gs2d {
 
 constexpr int kLossBlocks = 4 * 152;
 constexpr int kLossThreads = 256;
-
-__device__ __forceinline__ float sgnf(float v) { return (float)((v > 0.f) - (v < 0.f)); }
 
 __device__ __forceinline__ float block_sum256(float v, float* s) {
 #pragma unroll
@@ -40,35 +39,16 @@ __global__ void __launch_bounds__(kLossThreads) tracking_loss_kernel(
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
     const float x = (i % cam.width) + 0.5f, y = (i / cam.width) + 0.5f;
     const float rx = (x - cam.cx) / cam.fx, ry = (y - cam.cy) / cam.fy;
-    const float O = opac[i];
-    const float nr = normal[3 * i] * rx + normal[3 * i + 1] * ry + normal[3 * i + 2];
-    const bool m = (nr > 0.f) && (O > prm.opacity_thresh);
-    float gr0 = 0.f, gr1 = 0.f, gr2 = 0.f, gd = 0.f, go = 0.f;
-    if (m) {
-      const float D = depth[i];
-      const float Oc = fmaxf(O, 1e-6f);
-      const float Dh = prm.depth_mode ? D / Oc : D;
-      const float d0 = rgb[3 * i] - obs_rgb[3 * i];
-      const float d1 = rgb[3 * i + 1] - obs_rgb[3 * i + 1];
-      const float d2 = rgb[3 * i + 2] - obs_rgb[3 * i + 2];
-      const float dd = Dh - obs_depth[i];
-      acc += fabsf(d0) + fabsf(d1) + fabsf(d2) + prm.lambda_d * fabsf(dd);
-      gr0 = sgnf(d0) * inv;
-      gr1 = sgnf(d1) * inv;
-      gr2 = sgnf(d2) * inv;
-      const float sd = prm.lambda_d * sgnf(dd) * inv;
-      if (prm.depth_mode) {
-        gd = sd / Oc;
-        go = O > 1e-6f ? -sd * D / (O * O) : 0.f;
-      } else {
-        gd = sd;
-      }
-    }
-    g_rgb[3 * i] = gr0;
-    g_rgb[3 * i + 1] = gr1;
-    g_rgb[3 * i + 2] = gr2;
-    g_depth[i] = gd;
-    g_opac[i] = go;
+    const PixLoss L = tracking_pixel_loss(
+        f3(rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2]), depth[i],
+        f3(normal[3 * i], normal[3 * i + 1], normal[3 * i + 2]), opac[i],
+        f3(obs_rgb[3 * i], obs_rgb[3 * i + 1], obs_rgb[3 * i + 2]), obs_depth[i], rx, ry, inv, prm);
+    acc += L.loss;
+    g_rgb[3 * i] = L.g_rgb[0];
+    g_rgb[3 * i + 1] = L.g_rgb[1];
+    g_rgb[3 * i + 2] = L.g_rgb[2];
+    g_depth[i] = L.g_depth;
+    g_opac[i] = L.g_opac;
   }
   const float t = block_sum256(acc, s);
   if (threadIdx.x == 0) part[blockIdx.x] = t * inv;

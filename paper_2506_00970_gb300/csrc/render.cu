@@ -1,13 +1,14 @@
 // gs2d_render_fwd / gs2d_render_bwd: tile-based front-to-back compositing of
 // 2D Gaussian surfels (Eq. alpha_blending) and its reverse mode to the surfel
-// parameters and to the camera pose (Sec. III-B, Eq. derivatives).
+// parameters and to the camera pose (Sec. III-B, Eq. derivatives), plus the
+// fused tracking kernel (forward, tracking loss and pose backward per tile).
 //
 // Forward: one 256-thread block per image tile, one pixel per thread, each
 // warp an 8 x 4 pixel block.  The tile's depth-ordered surfel list is staged
-// through shared memory in batches of 256 records (80 B each), the record's
-// linear intersection map re-based on the tile's first pixel (c0t); a warp
-// skips a surfel whose footprint misses its block, and every thread
-// evaluates u = p0/p2, v = p1/p2, z = det/p2 with p = c0t + lx c1 + ly c2,
+// through shared memory in batches of 256 records, the record's linear
+// intersection map re-based on the tile's first pixel (c0t); a warp skips a
+// surfel whose footprint misses its block, and every thread evaluates
+// u = p0/p2, v = p1/p2, z = det/p2 with p = c0t + lx c1 + ly c2,
 // G = exp(-(u^2+v^2)/2), a = min(alpha G, alpha_max), skips a < alpha_min or
 // u^2+v^2 > cutoff or z <= near, blends colour, depth z, normal t_nc and
 // opacity, and stops before the transmittance would fall below t_min.  The
@@ -39,6 +40,7 @@
 // partial per tile, reduced in a fixed order.
 #include "gs2d_common.cuh"
 #include "gs2d_internal.h"
+#include "loss_pixel.cuh"
 
 namespace gs2d {
 
@@ -69,8 +71,8 @@ __device__ __forceinline__ TilePix tile_pixel(int tile, int tiles_x, int tile_w,
 }
 
 // Stages one projected record for a tile: p is re-based on the tile's first
-// pixel centre (xt, yt) (principal-point relative): c0t = p(xt, yt).  Both
-// passes stage through this function, so they evaluate identical numbers.
+// pixel centre (xt, yt) (principal-point relative): c0t = p(xt, yt).  Every
+// pass stages through this function, so they evaluate identical numbers.
 __device__ __forceinline__ float4 stage_c0(const float4 r0, const float4 r1, const float4 r2,
                                            float xt, float yt) {
   // r0 = (x0, y0, p2c, c1x), r1 = (c1y, c1z, c2x, c2y), r2 = (c2z, det, alpha, rgb0)
@@ -86,8 +88,8 @@ __device__ __forceinline__ bool warp_hits(float bi, float bj, int bx0, int by0) 
   return !(i1 < bx0 || i0 > bx0 + 7 || j1 < by0 || j0 > by0 + 3);
 }
 
-// Evaluation of one (pixel, surfel) pair shared by forward and backward so
-// both take bit-identical skip decisions.  Returns false if skipped.
+// Evaluation of one (pixel, surfel) pair shared by every pass, so all take
+// bit-identical skip decisions.  Returns false if skipped.
 struct Eval {
   float rinv, u, v, z, G, araw, a;
 };
@@ -111,100 +113,95 @@ __device__ __forceinline__ bool eval_pair(const float4 r0, const float4 r1, cons
   return e.a >= alpha_min;
 }
 
-// kCount: the same loop, counting evaluated pairs, pairs inside the cutoff
-// and blended pairs instead of writing images (the work measure of the
-// roofline); counts are exact integers.
-template <bool kCount>
-__global__ void __launch_bounds__(kTileThreads) render_fwd_kernel(
-    const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
-    const int32_t* __restrict__ ranges, gs2d_camera cam, gs2d_config cfg, int tiles_x,
-    float* __restrict__ out_rgb, float* __restrict__ out_depth, float* __restrict__ out_normal,
-    float* __restrict__ out_opac, float* __restrict__ out_T, uint32_t* __restrict__ out_nlast,
-    unsigned long long* __restrict__ counts, const int32_t* __restrict__ gate) {
-  __shared__ float4 s_rec[kTileThreads][kFwdVec4];
-  uint32_t n_eval = 0, n_in = 0, n_blend = 0;
-  if (gate && *gate) return;
-  const int tile = blockIdx.x;
-  const TilePix tp = tile_pixel(tile, tiles_x, cfg.tile_w, cfg.tile_h);
-  const bool inside = tp.px < cam.width && tp.py < cam.height;
-  const float xt = (float)((tile % tiles_x) * cfg.tile_w) + 0.5f - cam.cx;
-  const float yt = (float)((tile / tiles_x) * cfg.tile_h) + 0.5f - cam.cy;
-  const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
-  float T = 1.f, D = 0.f;
-  F3 C = f3(0.f, 0.f, 0.f), N = f3(0.f, 0.f, 0.f);
-  uint32_t last = 0;
+// Stages the records of list positions [b, b + 256) into s_rec: the forward
+// layout (5 float4) or the backward layout (7 float4); slot 4.y/z (forward)
+// or 6.z/w (backward) carries the packed pixel footprint.
+template <int kStride>
+__device__ __forceinline__ void stage_record(const float4* __restrict__ proj, uint32_t id, float xt,
+                                             float yt, float4 (*s_rec)[kStride]) {
+  const float4* src = proj + (size_t)id * (kProjFloats / 4);
+  const float4 r0 = src[0], r1 = src[1], r2 = src[2], r7 = src[7];
+  s_rec[threadIdx.x][0] = stage_c0(r0, r1, r2, xt, yt);
+  s_rec[threadIdx.x][1] = r1;
+  s_rec[threadIdx.x][2] = r2;
+  s_rec[threadIdx.x][3] = src[3];
+  if (kStride == kFwdVec4) {
+    s_rec[threadIdx.x][4] = make_float4(src[4].x, r7.z, r7.w, 0.f);
+  } else {
+    const float4 r6 = src[6];
+    s_rec[threadIdx.x][4] = src[4];
+    s_rec[threadIdx.x][5] = src[5];
+    s_rec[threadIdx.x][6] = make_float4(r6.x, r6.y, r7.z, r7.w);
+  }
+}
+
+struct FwdState {
+  float T, D;
+  F3 C, N;
+  uint32_t last;
+};
+
+// Front-to-back compositing of one pixel over its tile's list.  With kCount
+// it counts evaluated pairs, pairs inside the cutoff and blended pairs.
+template <int kStride, bool kCount>
+__device__ __forceinline__ FwdState fwd_tile(const float4* __restrict__ proj,
+                                             const uint32_t* __restrict__ vals, int start, int end,
+                                             float xt, float yt, const TilePix& tp, bool inside,
+                                             const gs2d_camera& cam, const gs2d_config& cfg,
+                                             float4 (*s_rec)[kStride], uint32_t* cnt) {
+  FwdState st;
+  st.T = 1.f;
+  st.D = 0.f;
+  st.C = f3(0.f, 0.f, 0.f);
+  st.N = f3(0.f, 0.f, 0.f);
+  st.last = 0;
   bool done = !inside;
+  constexpr int kNrm = kStride == kFwdVec4 ? 4 : 6;  // slot holding the footprint
   for (int b = start; b < end; b += kTileThreads) {
     if (__syncthreads_count(!done) == 0) break;
     const int idx = b + (int)threadIdx.x;
-    if (idx < end) {
-      const float4* src = proj + (size_t)vals[idx] * (kProjFloats / 4);
-      const float4 r0 = src[0], r1 = src[1], r2 = src[2], r3 = src[3], r4 = src[4], r7 = src[7];
-      s_rec[threadIdx.x][0] = stage_c0(r0, r1, r2, xt, yt);
-      s_rec[threadIdx.x][1] = r1;
-      s_rec[threadIdx.x][2] = r2;
-      s_rec[threadIdx.x][3] = r3;
-      s_rec[threadIdx.x][4] = make_float4(r4.x, r7.z, r7.w, 0.f);
-    }
+    if (idx < end) stage_record<kStride>(proj, vals[idx], xt, yt, s_rec);
     __syncthreads();
-    const int cnt = min(kTileThreads, end - b);
+    const int cnt_b = min(kTileThreads, end - b);
     if (!done) {
-      for (int j = 0; j < cnt; ++j) {
-        const float4 r4 = s_rec[j][4];
-        if (!warp_hits(r4.y, r4.z, tp.bx0, tp.by0)) continue;
+      for (int j = 0; j < cnt_b; ++j) {
+        const float4 rf = s_rec[j][kNrm];
+        if (kStride == kFwdVec4) {
+          if (!warp_hits(rf.y, rf.z, tp.bx0, tp.by0)) continue;
+        } else {
+          if (!warp_hits(rf.z, rf.w, tp.bx0, tp.by0)) continue;
+        }
         const float4 r0 = s_rec[j][0], r1 = s_rec[j][1], r2 = s_rec[j][2];
         Eval e;
         const bool hit = eval_pair(r0, r1, r2, tp.lx, tp.ly, cam.near_z, cfg.cutoff_r2,
                                    cfg.alpha_min, cfg.alpha_max, e);
         if (kCount) {
-          ++n_eval;
-          if (fmaf(e.u, e.u, __fmul_rn(e.v, e.v)) <= cfg.cutoff_r2) ++n_in;
+          ++cnt[0];
+          if (fmaf(e.u, e.u, __fmul_rn(e.v, e.v)) <= cfg.cutoff_r2) ++cnt[1];
         }
         if (!hit) continue;
-        const float Tn = T * (1.f - e.a);
+        const float Tn = st.T * (1.f - e.a);
         if (Tn < cfg.t_min) {
           done = true;
           break;
         }
         const float4 r3 = s_rec[j][3];
-        const float w = e.a * T;
-        C.x = fmaf(w, r2.w, C.x);
-        C.y = fmaf(w, r3.x, C.y);
-        C.z = fmaf(w, r3.y, C.z);
-        D = fmaf(w, e.z, D);
-        N.x = fmaf(w, r3.z, N.x);
-        N.y = fmaf(w, r3.w, N.y);
-        N.z = fmaf(w, r4.x, N.z);
-        T = Tn;
-        last = (uint32_t)(b + j + 1 - start);
-        if (kCount) ++n_blend;
+        const float tnz = kStride == kFwdVec4 ? s_rec[j][4].x : s_rec[j][4].x;
+        const float w = e.a * st.T;
+        st.C.x = fmaf(w, r2.w, st.C.x);
+        st.C.y = fmaf(w, r3.x, st.C.y);
+        st.C.z = fmaf(w, r3.y, st.C.z);
+        st.D = fmaf(w, e.z, st.D);
+        st.N.x = fmaf(w, r3.z, st.N.x);
+        st.N.y = fmaf(w, r3.w, st.N.y);
+        st.N.z = fmaf(w, tnz, st.N.z);
+        st.T = Tn;
+        st.last = (uint32_t)(b + j + 1 - start);
+        if (kCount) ++cnt[2];
       }
     }
   }
-  if (kCount) {
-    unsigned long long c[3] = {n_eval, n_in, n_blend};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      unsigned long long v = c[k];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      if ((threadIdx.x & 31) == 0) atomicAdd(counts + k, v);
-    }
-    return;
-  }
-  if (inside) {
-    const size_t p = (size_t)tp.py * cam.width + tp.px;
-    out_rgb[3 * p] = C.x;
-    out_rgb[3 * p + 1] = C.y;
-    out_rgb[3 * p + 2] = C.z;
-    out_depth[p] = D;
-    out_normal[3 * p] = N.x;
-    out_normal[3 * p + 1] = N.y;
-    out_normal[3 * p + 2] = N.z;
-    out_opac[p] = 1.f - T;
-    out_T[p] = T;
-    out_nlast[p] = last;
-  }
+  return st;
 }
 
 // Butterfly reduce-scatter of 16 values over a warp: afterwards lane l holds
@@ -225,84 +222,58 @@ __device__ __forceinline__ void warp_reduce_scatter16(float (&v)[kRedVals], int 
   v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// Shared-memory scratch of the backward loop.
 template <bool kFull>
-__global__ void __launch_bounds__(kTileThreads) render_bwd_kernel(
-    const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
-    const uint32_t* __restrict__ emit, const int32_t* __restrict__ ranges, gs2d_camera cam,
-    gs2d_config cfg, int tiles_x, const float* __restrict__ T_final,
-    const uint32_t* __restrict__ n_last, const float* __restrict__ g_rgb,
-    const float* __restrict__ g_depth, const float* __restrict__ g_normal,
-    const float* __restrict__ g_opac, float* __restrict__ partials, float* __restrict__ pose_part,
-    const int32_t* __restrict__ gate) {
-  __shared__ float4 s_rec[kTileThreads][kBwdVec4];
-  __shared__ uint32_t s_emit[kFull ? kTileThreads : 1];
-  __shared__ float s_red[kFull ? 8 : 1][kFull ? 32 : 1][kRedVals];
-  __shared__ uint32_t s_max;
-  __shared__ float s_pose[8][6];
-  if (gate && *gate) return;
-  const int tile = blockIdx.x;
-  const TilePix tp = tile_pixel(tile, tiles_x, cfg.tile_w, cfg.tile_h);
-  const int px = tp.px, py = tp.py;
-  const bool inside = px < cam.width && py < cam.height;
-  const float xt = (float)((tile % tiles_x) * cfg.tile_w) + 0.5f - cam.cx;
-  const float yt = (float)((tile / tiles_x) * cfg.tile_h) + 0.5f - cam.cy;
-  const float rx = (px + 0.5f - cam.cx) / cam.fx, ry = (py + 0.5f - cam.cy) / cam.fy;
-  const float fxfy = cam.fx * cam.fy;
-  const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+struct BwdSmem {
+  float4 rec[kTileThreads][kBwdVec4];
+  uint32_t emit[kFull ? kTileThreads : 1];
+  float red[kFull ? 8 : 1][kFull ? 32 : 1][kRedVals];
+  uint32_t max_nl;
+};
 
-  float Tf = 1.f;
-  uint32_t nl = 0;
-  F3 gC = f3(0.f, 0.f, 0.f), gN = f3(0.f, 0.f, 0.f);
-  float gD = 0.f, gO = 0.f;
-  if (inside) {
-    const size_t p = (size_t)py * cam.width + px;
-    Tf = T_final[p];
-    nl = n_last[p];
-    gC = f3(g_rgb[3 * p], g_rgb[3 * p + 1], g_rgb[3 * p + 2]);
-    gD = g_depth[p];
-    if (g_normal) gN = f3(g_normal[3 * p], g_normal[3 * p + 1], g_normal[3 * p + 2]);
-    if (g_opac) gO = g_opac[p];
-  }
-  if (threadIdx.x == 0) s_max = 0u;
+// Back-to-front replay of one pixel (Tf, nl, upstream gradients) over its
+// tile's list.  Full mode writes the per-(tile, surfel) partials; tracking
+// mode accumulates the pose 6-vector in pr.
+template <bool kFull>
+__device__ __forceinline__ void bwd_tile(const float4* __restrict__ proj,
+                                         const uint32_t* __restrict__ vals,
+                                         const uint32_t* __restrict__ emit, int start, int end,
+                                         float xt, float yt, const TilePix& tp, bool inside,
+                                         float rx, float ry, const gs2d_camera& cam,
+                                         const gs2d_config& cfg, float Tf, uint32_t nl, F3 gC,
+                                         float gD, F3 gN, float gO, float* __restrict__ partials,
+                                         BwdSmem<kFull>& sm, float (&pr)[6]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float fxfy = cam.fx * cam.fy;
+  if (threadIdx.x == 0) sm.max_nl = 0u;
   __syncthreads();
-  if (nl) atomicMax(&s_max, nl);
+  if (nl) atomicMax(&sm.max_nl, nl);
   __syncthreads();
-  const int hi = start + (int)s_max;
+  const int hi = start + (int)sm.max_nl;
   float T = Tf, acc = 0.f;
   const float gOT = gO * Tf;
-  float pr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-
   for (int bend = hi; bend > start; bend -= kTileThreads) {
     const int bstart = max(start, bend - kTileThreads);
     const int cnt = bend - bstart;
     __syncthreads();
     if ((int)threadIdx.x < cnt) {
       const int idx = bstart + (int)threadIdx.x;
-      const float4* src = proj + (size_t)vals[idx] * (kProjFloats / 4);
-      const float4 r0 = src[0], r1 = src[1], r2 = src[2], r6 = src[6], r7 = src[7];
-      s_rec[threadIdx.x][0] = stage_c0(r0, r1, r2, xt, yt);
-      s_rec[threadIdx.x][1] = r1;
-      s_rec[threadIdx.x][2] = r2;
-      s_rec[threadIdx.x][3] = src[3];
-      s_rec[threadIdx.x][4] = src[4];
-      s_rec[threadIdx.x][5] = src[5];
-      s_rec[threadIdx.x][6] = make_float4(r6.x, r6.y, r7.z, r7.w);
-      if (kFull) s_emit[threadIdx.x] = emit[idx];
+      stage_record<kBwdVec4>(proj, vals[idx], xt, yt, sm.rec);
+      if (kFull) sm.emit[threadIdx.x] = emit[idx];
     }
     __syncthreads();
     for (int jj = cnt - 1; jj >= 0; --jj) {
       const int jrel = bstart + jj - start;
       float val[kRedVals];
       bool contrib = false;
-      const float4 r6 = s_rec[jj][6];
+      const float4 r6 = sm.rec[jj][6];
       if (inside && jrel < (int)nl && warp_hits(r6.z, r6.w, tp.bx0, tp.by0)) {
-        const float4 r0 = s_rec[jj][0], r1 = s_rec[jj][1], r2 = s_rec[jj][2];
+        const float4 r0 = sm.rec[jj][0], r1 = sm.rec[jj][1], r2 = sm.rec[jj][2];
         Eval e;
         if (eval_pair(r0, r1, r2, tp.lx, tp.ly, cam.near_z, cfg.cutoff_r2, cfg.alpha_min,
                       cfg.alpha_max, e)) {
           contrib = true;
-          const float4 r3 = s_rec[jj][3], r4 = s_rec[jj][4], r5 = s_rec[jj][5];
+          const float4 r3 = sm.rec[jj][3], r4 = sm.rec[jj][4], r5 = sm.rec[jj][5];
           const F3 col = f3(r2.w, r3.x, r3.y);
           const F3 tn = f3(r3.z, r3.w, r4.x);
           const F3 nrm = f3(r4.y, r4.z, r4.w);
@@ -350,9 +321,9 @@ __global__ void __launch_bounds__(kTileThreads) render_bwd_kernel(
             for (int i = 0; i < kRedVals; ++i) val[i] = 0.f;
           }
           warp_reduce_scatter16(val, lane);
-          if ((lane & 1) == 0) s_red[warp][slot][lane >> 1] = val[0];
+          if ((lane & 1) == 0) sm.red[warp][slot][lane >> 1] = val[0];
         } else if (lane < kRedVals) {
-          s_red[warp][slot][lane] = 0.f;
+          sm.red[warp][slot][lane] = 0.f;
         }
         if (slot == 0) {
           __syncthreads();
@@ -361,8 +332,8 @@ __global__ void __launch_bounds__(kTileThreads) render_bwd_kernel(
             const int s = o / kRedVals, c = o % kRedVals;
             float sum = 0.f;
 #pragma unroll
-            for (int ww = 0; ww < 8; ++ww) sum += s_red[ww][s][c];
-            partials[(size_t)s_emit[jj + s] * kRedVals + c] = sum;
+            for (int ww = 0; ww < 8; ++ww) sum += sm.red[ww][s][c];
+            partials[(size_t)sm.emit[jj + s] * kRedVals + c] = sum;
           }
           __syncthreads();
         }
@@ -376,21 +347,157 @@ __global__ void __launch_bounds__(kTileThreads) render_bwd_kernel(
       const int s = o / kRedVals, c = o % kRedVals;
       partials[(size_t)emit[hi + s] * kRedVals + c] = 0.f;
     }
-  } else {
+  }
+}
+
+// Block sum of a per-thread 6-vector, written by threads 0..5.
+__device__ __forceinline__ void block_sum6(const float (&pr)[6], float (*s_pose)[6],
+                                           float* __restrict__ out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      float v = pr[i];
+  for (int i = 0; i < 6; ++i) {
+    float v = pr[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) s_pose[warp][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    float v = 0.f;
+    for (int ww = 0; ww < kTileThreads / 32; ++ww) v += s_pose[ww][threadIdx.x];
+    out[threadIdx.x] = v;
+  }
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(kTileThreads) render_fwd_kernel(
+    const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
+    const int32_t* __restrict__ ranges, gs2d_camera cam, gs2d_config cfg, int tiles_x,
+    float* __restrict__ out_rgb, float* __restrict__ out_depth, float* __restrict__ out_normal,
+    float* __restrict__ out_opac, float* __restrict__ out_T, uint32_t* __restrict__ out_nlast,
+    unsigned long long* __restrict__ counts, const int32_t* __restrict__ gate) {
+  __shared__ float4 s_rec[kTileThreads][kFwdVec4];
+  if (gate && *gate) return;
+  const int tile = blockIdx.x;
+  const TilePix tp = tile_pixel(tile, tiles_x, cfg.tile_w, cfg.tile_h);
+  const bool inside = tp.px < cam.width && tp.py < cam.height;
+  const float xt = (float)((tile % tiles_x) * cfg.tile_w) + 0.5f - cam.cx;
+  const float yt = (float)((tile / tiles_x) * cfg.tile_h) + 0.5f - cam.cy;
+  uint32_t cnt[3] = {0u, 0u, 0u};
+  const FwdState st = fwd_tile<kFwdVec4, kCount>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1],
+                                                 xt, yt, tp, inside, cam, cfg, s_rec, cnt);
+  if (kCount) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      unsigned long long v = cnt[k];
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      if (lane == 0) s_pose[warp][i] = v;
+      if ((threadIdx.x & 31) == 0) atomicAdd(counts + k, v);
     }
+    return;
+  }
+  if (inside) {
+    const size_t p = (size_t)tp.py * cam.width + tp.px;
+    out_rgb[3 * p] = st.C.x;
+    out_rgb[3 * p + 1] = st.C.y;
+    out_rgb[3 * p + 2] = st.C.z;
+    out_depth[p] = st.D;
+    out_normal[3 * p] = st.N.x;
+    out_normal[3 * p + 1] = st.N.y;
+    out_normal[3 * p + 2] = st.N.z;
+    out_opac[p] = 1.f - st.T;
+    out_T[p] = st.T;
+    out_nlast[p] = st.last;
+  }
+}
+
+template <bool kFull>
+__global__ void __launch_bounds__(kTileThreads) render_bwd_kernel(
+    const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ emit, const int32_t* __restrict__ ranges, gs2d_camera cam,
+    gs2d_config cfg, int tiles_x, const float* __restrict__ T_final,
+    const uint32_t* __restrict__ n_last, const float* __restrict__ g_rgb,
+    const float* __restrict__ g_depth, const float* __restrict__ g_normal,
+    const float* __restrict__ g_opac, float* __restrict__ partials, float* __restrict__ pose_part,
+    const int32_t* __restrict__ gate) {
+  __shared__ BwdSmem<kFull> sm;
+  __shared__ float s_pose[kTileThreads / 32][6];
+  if (gate && *gate) return;
+  const int tile = blockIdx.x;
+  const TilePix tp = tile_pixel(tile, tiles_x, cfg.tile_w, cfg.tile_h);
+  const bool inside = tp.px < cam.width && tp.py < cam.height;
+  const float xt = (float)((tile % tiles_x) * cfg.tile_w) + 0.5f - cam.cx;
+  const float yt = (float)((tile / tiles_x) * cfg.tile_h) + 0.5f - cam.cy;
+  const float rx = (tp.px + 0.5f - cam.cx) / cam.fx, ry = (tp.py + 0.5f - cam.cy) / cam.fy;
+  float Tf = 1.f;
+  uint32_t nl = 0;
+  F3 gC = f3(0.f, 0.f, 0.f), gN = f3(0.f, 0.f, 0.f);
+  float gD = 0.f, gO = 0.f;
+  if (inside) {
+    const size_t p = (size_t)tp.py * cam.width + tp.px;
+    Tf = T_final[p];
+    nl = n_last[p];
+    gC = f3(g_rgb[3 * p], g_rgb[3 * p + 1], g_rgb[3 * p + 2]);
+    gD = g_depth[p];
+    if (g_normal) gN = f3(g_normal[3 * p], g_normal[3 * p + 1], g_normal[3 * p + 2]);
+    if (g_opac) gO = g_opac[p];
+  }
+  float pr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  bwd_tile<kFull>(proj, vals, emit, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tp, inside, rx,
+                  ry, cam, cfg, Tf, nl, gC, gD, gN, gO, partials, sm, pr);
+  if (!kFull) block_sum6(pr, s_pose, pose_part + (size_t)tile * 6);
+}
+
+// Fused tracking iteration on one tile: forward compositing, the tracking
+// loss and its image gradient per pixel (in registers), and the pose-only
+// backward replay -- the images never leave the chip.  Writes the tile's
+// loss partial (already divided by |Omega|) and pose 6-vector partial.
+__global__ void __launch_bounds__(kTileThreads) track_tile_kernel(
+    const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
+    const int32_t* __restrict__ ranges, gs2d_camera cam, gs2d_config cfg, int tiles_x,
+    const float* __restrict__ obs_rgb, const float* __restrict__ obs_depth, gs2d_track_params prm,
+    float* __restrict__ loss_part, float* __restrict__ pose_part, const int32_t* __restrict__ gate) {
+  __shared__ BwdSmem<false> sm;
+  __shared__ float s_pose[kTileThreads / 32][6];
+  __shared__ float s_loss[kTileThreads / 32];
+  if (gate && *gate) return;
+  const int tile = blockIdx.x;
+  const TilePix tp = tile_pixel(tile, tiles_x, cfg.tile_w, cfg.tile_h);
+  const bool inside = tp.px < cam.width && tp.py < cam.height;
+  const float xt = (float)((tile % tiles_x) * cfg.tile_w) + 0.5f - cam.cx;
+  const float yt = (float)((tile / tiles_x) * cfg.tile_h) + 0.5f - cam.cy;
+  const float rx = (tp.px + 0.5f - cam.cx) / cam.fx, ry = (tp.py + 0.5f - cam.cy) / cam.fy;
+  const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
+  const FwdState st = fwd_tile<kBwdVec4, false>(proj, vals, start, end, xt, yt, tp, inside, cam,
+                                                cfg, sm.rec, nullptr);
+  float pr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const float inv = 1.f / (float)(cam.width * cam.height);
+  PixLoss L;
+  L.loss = 0.f;
+  L.g_rgb[0] = L.g_rgb[1] = L.g_rgb[2] = 0.f;
+  L.g_depth = L.g_opac = 0.f;
+  if (inside) {
+    const size_t p = (size_t)tp.py * cam.width + tp.px;
+    L = tracking_pixel_loss(st.C, st.D, st.N, 1.f - st.T,
+                            f3(obs_rgb[3 * p], obs_rgb[3 * p + 1], obs_rgb[3 * p + 2]),
+                            obs_depth[p], rx, ry, inv, prm);
+  }
+  {
+    float v = L.loss * inv;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = v;
     __syncthreads();
-    if (threadIdx.x < 6) {
-      float v = 0.f;
-      for (int ww = 0; ww < 8; ++ww) v += s_pose[ww][threadIdx.x];
-      pose_part[(size_t)tile * 6 + threadIdx.x] = v;
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+      for (int w = 0; w < kTileThreads / 32; ++w) t += s_loss[w];
+      loss_part[tile] = t;
     }
   }
+  bwd_tile<false>(proj, vals, nullptr, start, end, xt, yt, tp, inside, rx, ry, cam, cfg, st.T,
+                  st.last, f3(L.g_rgb[0], L.g_rgb[1], L.g_rgb[2]), L.g_depth, f3(0.f, 0.f, 0.f),
+                  L.g_opac, nullptr, sm, pr);
+  block_sum6(pr, s_pose, pose_part + (size_t)tile * 6);
 }
 
 // Per-surfel reduction of the (tile, surfel) partials in emission order and
@@ -550,6 +657,23 @@ int render_fwd_launch(const float* proj, const gs2d_bins* bins, const gs2d_camer
   render_fwd_kernel<false><<<tx * ty, kTileThreads, 0, st>>>(
       reinterpret_cast<const float4*>(proj), bins->vals, bins->tile_ranges, *cam, *cfg, tx, rgb,
       depth, normal, opacity, t_final, n_last, nullptr, gate);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+int track_tile_launch(const float* proj, const gs2d_bins* bins, const gs2d_camera* cam,
+                      const gs2d_config* cfg, const float* obs_rgb, const float* obs_depth,
+                      const gs2d_track_params* prm, float* loss_part, float* pose_part,
+                      const int32_t* gate, cudaStream_t st) {
+  const int v = validate_tile_cfg(cam, cfg);
+  if (v) return v;
+  if (!proj || !bins || !bins->vals || !bins->tile_ranges || !obs_rgb || !obs_depth || !prm ||
+      !loss_part || !pose_part)
+    return GS2D_ERR_INVALID_ARG;
+  const int tx = gs2d_tiles_x(cam, cfg), ty = gs2d_tiles_y(cam, cfg);
+  track_tile_kernel<<<tx * ty, kTileThreads, 0, st>>>(
+      reinterpret_cast<const float4*>(proj), bins->vals, bins->tile_ranges, *cam, *cfg, tx, obs_rgb,
+      obs_depth, *prm, loss_part, pose_part, gate);
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
 }

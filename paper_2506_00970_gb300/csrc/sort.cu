@@ -3,51 +3,42 @@
 //
 // Output order: by tile, then by the FP32 bit pattern of the surfel's centre
 // depth mu_c.z (positive floats order like their bits), then by surfel id.
-// Instead of one 48-bit key sort over all K intersections this runs
-//   1. a stable LSD radix sort of the N surfels by depth bits (4 x 8-bit
-//      passes over N items, culled surfels keyed 0xFFFFFFFF sort last),
-//   2. an exclusive scan of the per-surfel tile counts in depth order and
-//      the emission of every surfel's tiles at its offset (so emission order
-//      is depth order and each surfel owns a contiguous emission range),
-//   3. a stable LSD radix sort of the K emitted pairs by tile id (one or two
-//      8-bit passes),
-// which yields the same order with 4 passes over N and <= 2 over K.
-// Every radix pass is a single kernel: blocks take chunks in launch order
-// from an atomic ticket, rank their keys stably with warp match-any, publish
-// per-digit chunk counts, and look back over earlier chunks' published
-// counts (decoupled look-back) to find their global offsets.  The look-back
-// spin is bounded: past the limit the kernel records GS2D_ERR_TIMEOUT and
-// continues with a partial prefix that still keeps every write in bounds.
+// A tile's list is short (hundreds of entries), so instead of a global depth
+// sort the pairs are binned first and every tile sorts its own segment:
+//   1. scan: per surfel (id order) its tile count k_i -> emission offset
+//      (exclusive scan with decoupled look-back) and the total K; every
+//      covered tile's counter is incremented;
+//   2. tile scan: one block turns the tile counts into tile ranges;
+//   3. scatter: every pair writes the 64-bit key (depth bits << 32 | id)
+//      into its tile's segment at an atomically claimed slot (the order
+//      inside a segment is arbitrary at this point);
+//   4. tile sort: one block per tile sorts its segment by that key in shared
+//      memory (bitonic network in its "flip" form, in which every comparator
+//      puts the smaller key at the lower index, so a segment of any length
+//      behaves as if padded with +inf), then writes the surfel ids, the
+//      64-bit (tile, depth) keys and each pair's emission index.
+// Because the key carries the id, the final order is unique and
+// deterministic whatever order the atomics gave.  Emission index of the pair
+// (surfel i, tile t) = surfel_off[i] + the row-major position of t in i's
+// rectangle, so each surfel's pairs are contiguous in emission order (the
+// backward pass stores its per-pair partials there).
 #include "gs2d_common.cuh"
 
 namespace gs2d {
 
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kChunk = kSortThreads * kSortItems;  // 4096 keys per block
-constexpr int kWarps = kSortThreads / 32;
-constexpr uint32_t kFlagAgg = 1u << 30;
-constexpr uint32_t kFlagInc = 2u << 30;
-constexpr uint32_t kValMask = (1u << 30) - 1;
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kChunk = kScanThreads * kScanItems;  // 4096 surfels per scan block
+constexpr int kWarps = kScanThreads / 32;
 constexpr int kSpinLimit = 1 << 22;
-constexpr int kLookback = 16;
+constexpr int kSortThreads = 256;
+constexpr int kSegSmem = 4096;                     // keys sorted in shared memory (32 KB)
 
-__device__ __forceinline__ uint32_t ld_vol(const uint32_t* p) {
-  return *reinterpret_cast<const volatile uint32_t*>(p);
-}
-__device__ __forceinline__ void st_vol(uint32_t* p, uint32_t v) {
-  *reinterpret_cast<volatile uint32_t*>(p) = v;
-}
 __device__ __forceinline__ unsigned long long ld_vol64(const unsigned long long* p) {
   return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
 __device__ __forceinline__ void st_vol64(unsigned long long* p, unsigned long long v) {
   *reinterpret_cast<volatile unsigned long long*>(p) = v;
-}
-__device__ __forceinline__ uint32_t lanemask_lt() {
-  uint32_t m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
 }
 
 // Exclusive scan over a 256-thread block; returns the exclusive prefix and
@@ -80,192 +71,37 @@ __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* s_t
   return r;
 }
 
-// Zeroes the per-call counters and outputs that are accumulated or that
-// must read zero where nothing is written (ranges of empty tiles).
+struct Rect {
+  int tx0, ty0, tx1, ty1;
+};
+__device__ __forceinline__ Rect load_rect(const float4* proj, uint32_t id) {
+  const float4 rc = proj[(size_t)id * (kProjFloats / 4) + 7];
+  const uint32_t r01 = __float_as_uint(rc.x), r23 = __float_as_uint(rc.y);
+  return Rect{(int)(r01 & 0xFFFF), (int)(r01 >> 16), (int)(r23 & 0xFFFF), (int)(r23 >> 16)};
+}
+
+// Zeroes the per-call counters (tile counts and cursors, scan words, K).
 __global__ void bin_init_kernel(uint32_t* __restrict__ zero_a, size_t n_a,
-                                int32_t* __restrict__ ranges, int n_ranges,
                                 int32_t* __restrict__ n_isect, const int32_t* __restrict__ gate) {
   if (*gate) return;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_a; i += stride) zero_a[i] = 0u;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)n_ranges; i += stride)
-    ranges[i] = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) *n_isect = 0;
 }
 
-// Depth keys of all surfels (culled -> 0xFFFFFFFF), identity values, and the
-// four 8-bit digit histograms of the depth sort.
-__global__ void __launch_bounds__(256) depth_keys_kernel(
-    const float4* __restrict__ proj, const int32_t* __restrict__ tiles, int n,
-    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t* __restrict__ hist,
-    const int32_t* __restrict__ gate) {
-  if (*gate) return;
-  __shared__ uint32_t h[4][256];
-  for (int i = threadIdx.x; i < 1024; i += blockDim.x) (&h[0][0])[i] = 0u;
-  __syncthreads();
-  const int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
-    const int i = base + threadIdx.x;
-    const bool ok = i < n;
-    uint32_t k = 0xFFFFFFFFu;
-    if (ok) {
-      if (tiles[i] > 0) k = __float_as_uint(proj[(size_t)i * (kProjFloats / 4) + 6].z);
-      keys[i] = k;
-      vals[i] = (uint32_t)i;
-    }
-    const uint32_t active = __ballot_sync(0xffffffffu, ok);
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const uint32_t d = (k >> (8 * p)) & 255u;
-      const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : 256u) & active;
-      if (ok && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&h[p][d], __popc(peers));
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
-    const uint32_t c = (&h[0][0])[i];
-    if (c) atomicAdd(hist + i, c);
-  }
-}
-
-// One stable 8-bit LSD radix pass (key u32, value u32).  vals_in == nullptr
-// means value = input index.  n comes from *n_dev when n_dev is non-null.
-// hist: this pass's 256-bin histogram of all n keys.  chunk_status: zeroed
-// [max_chunks * 256]; ticket: zeroed counter.
-__global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
-    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const int32_t* __restrict__ n_dev,
-    int n_static, int max_items, int shift, const uint32_t* __restrict__ hist,
-    uint32_t* __restrict__ chunk_status, uint32_t* __restrict__ ticket, int32_t* __restrict__ gate) {
-  __shared__ uint32_t s_keys[kChunk];
-  __shared__ uint32_t s_vals[kChunk];
-  __shared__ uint32_t s_wcnt[kWarps][256];
-  __shared__ uint32_t s_gbase[256];
-  __shared__ uint32_t s_bstart[256];
-  __shared__ uint32_t s_tmp[2 * kWarps + 1];
-  __shared__ int s_chunk;
-  if (*gate) return;
-  int n = n_dev ? *n_dev : n_static;
-  n = min(n, max_items);
-  if (threadIdx.x == 0) s_chunk = (int)atomicAdd(ticket, 1u);
-  for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) (&s_wcnt[0][0])[i] = 0u;
-  __syncthreads();
-  const int chunk = s_chunk;
-  const long long base = (long long)chunk * kChunk;
-  if (base >= n) return;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint32_t lt = lanemask_lt();
-
-  uint32_t key[kSortItems], val[kSortItems], local[kSortItems];
-  // all global loads first (independent, coalesced per round), then rank
-#pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
-    const long long idx = base + w * (32 * kSortItems) + r * 32 + lane;
-    const bool ok = idx < n;
-    key[r] = ok ? keys_in[idx] : 0xFFFFFFFFu;
-    val[r] = ok ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
-  }
-#pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
-    const long long idx = base + w * (32 * kSortItems) + r * 32 + lane;
-    const bool ok = idx < n;
-    const uint32_t d = ok ? (key[r] >> shift) & 255u : 256u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    uint32_t cnt = 0;
-    if (ok) cnt = s_wcnt[w][d];
-    __syncwarp();
-    if (ok && (__ffs(peers) - 1) == lane) s_wcnt[w][d] = cnt + __popc(peers);
-    __syncwarp();
-    local[r] = cnt + __popc(peers & lt);
-  }
-  __syncthreads();
-  // per-digit block counts and warp prefixes (thread = digit)
-  const int d = threadIdx.x;
-  uint32_t run = 0;
-#pragma unroll
-  for (int ww = 0; ww < kWarps; ++ww) {
-    const uint32_t c = s_wcnt[ww][d];
-    s_wcnt[ww][d] = run;
-    run += c;
-  }
-  const uint32_t cnt_d = run;
-  uint32_t btotal;
-  const uint32_t bstart = block_excl_scan256(cnt_d, s_tmp, &btotal);
-  s_bstart[d] = bstart;
-  uint32_t gtotal;
-  const uint32_t gexcl = block_excl_scan256(hist[d], s_tmp, &gtotal);
-
-  // publish this chunk's digit count, then look back for the prefix over a
-  // window of kLookback predecessors at a time (loads issued together)
-  uint32_t* my = chunk_status + (size_t)chunk * 256 + d;
-  uint32_t excl = 0;
-  if (chunk == 0) {
-    st_vol(my, kFlagInc | cnt_d);
-  } else {
-    st_vol(my, kFlagAgg | cnt_d);
-    int hi = chunk - 1;
-    int spins = 0;
-    bool found = false;
-    while (!found && hi >= 0) {
-      uint32_t wv[kLookback];
-#pragma unroll
-      for (int k = 0; k < kLookback; ++k)
-        wv[k] = (hi - k >= 0) ? ld_vol(chunk_status + (size_t)(hi - k) * 256 + d) : kFlagInc;
-#pragma unroll
-      for (int k = 0; k < kLookback; ++k) {
-        if (found) break;
-        uint32_t sv = wv[k];
-        while ((sv & ~kValMask) == 0u) {
-          if (++spins > kSpinLimit) {
-            atomicExch(gate, (int32_t)GS2D_ERR_TIMEOUT);
-            sv = kFlagInc;  // give up with a partial prefix: writes stay in bounds
-            break;
-          }
-          __nanosleep(32);
-          sv = ld_vol(chunk_status + (size_t)(hi - k) * 256 + d);
-        }
-        excl += sv & kValMask;
-        if ((sv & ~kValMask) == kFlagInc) found = true;
-      }
-      hi -= kLookback;
-    }
-    st_vol(my, kFlagInc | ((excl + cnt_d) & kValMask));
-  }
-  s_gbase[d] = gexcl + excl - bstart;
-  __syncthreads();
-
-  // reorder the chunk by digit in shared memory, then write runs
-#pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
-    const long long idx = base + w * (32 * kSortItems) + r * 32 + lane;
-    if (idx < n) {
-      const uint32_t dd = (key[r] >> shift) & 255u;
-      const uint32_t pos = s_bstart[dd] + s_wcnt[w][dd] + local[r];
-      s_keys[pos] = key[r];
-      s_vals[pos] = val[r];
-    }
-  }
-  __syncthreads();
-  const int count = (int)min((long long)kChunk, (long long)n - base);
-  for (int i = threadIdx.x; i < count; i += kSortThreads) {
-    const uint32_t k = s_keys[i];
-    const uint32_t o = s_gbase[(k >> shift) & 255u] + (uint32_t)i;
-    keys_out[o] = k;
-    vals_out[o] = s_vals[i];
-  }
-}
-
-// Exclusive scan of tiles[sorted_id[r]] over the depth order r with
-// decoupled look-back (64-bit chunk words: flag in bits 62-63).  Writes
-// surfel_off[id] and, from the chunk holding the last surfel, the total K.
+// 1. Exclusive scan of k_i over surfel ids with decoupled look-back (64-bit
+// chunk words: flag in bits 62-63; a warp examines 32 predecessors at a
+// time; the spin is bounded and records GS2D_ERR_TIMEOUT past the limit).
+// Writes surfel_off[i], the total K (chunk holding the last surfel) and the
+// capacity status, and counts every covered tile.
 constexpr unsigned long long kF64Agg = 1ull << 62, kF64Inc = 2ull << 62,
                              kV64Mask = (1ull << 62) - 1;
-__global__ void __launch_bounds__(kSortThreads) emit_scan_kernel(
-    const uint32_t* __restrict__ sorted_ids, const int32_t* __restrict__ tiles, int n,
-    uint32_t* __restrict__ surfel_off, unsigned long long* __restrict__ chunk_status,
-    uint32_t* __restrict__ ticket, int32_t* __restrict__ n_isect, long long capacity,
-    int32_t* __restrict__ gate) {
-  __shared__ uint32_t s_ids[kChunk];
+__global__ void __launch_bounds__(kScanThreads) count_scan_kernel(
+    const float4* __restrict__ proj, const int32_t* __restrict__ tiles, int n, int tiles_x,
+    int n_tiles, uint32_t* __restrict__ surfel_off, uint32_t* __restrict__ tile_count,
+    unsigned long long* __restrict__ chunk_status, uint32_t* __restrict__ ticket,
+    int32_t* __restrict__ n_isect, long long capacity, int32_t* __restrict__ gate) {
+  __shared__ uint32_t s_k[kChunk];
   __shared__ uint32_t s_tmp[2 * kWarps + 1];
   __shared__ int s_chunk;
   __shared__ unsigned long long s_prefix;
@@ -276,22 +112,31 @@ __global__ void __launch_bounds__(kSortThreads) emit_scan_kernel(
   const long long base = (long long)chunk * kChunk;
   if (base >= n) return;
   const int count = (int)min((long long)kChunk, (long long)n - base);
-  for (int i = threadIdx.x; i < count; i += kSortThreads)
-    s_ids[i] = min(sorted_ids[base + i], (uint32_t)(n - 1));
+  // coalesced load of the chunk's counts; tile counters per covered tile
+  for (int i = threadIdx.x; i < count; i += kScanThreads) {
+    const uint32_t id = (uint32_t)(base + i);
+    const int k = max(tiles[id], 0);
+    s_k[i] = (uint32_t)k;
+    if (k > 0) {
+      const Rect r = load_rect(proj, id);
+      const int rw = max(r.tx1 - r.tx0 + 1, 1);
+      for (int j = 0; j < k; ++j) {
+        const int t = min((r.ty0 + j / rw) * tiles_x + r.tx0 + j % rw, n_tiles - 1);
+        atomicAdd(tile_count + t, 1u);
+      }
+    }
+  }
   __syncthreads();
   // blocked: thread t owns items t*16 .. t*16+15
-  uint32_t k[kSortItems];
   uint32_t sum = 0;
 #pragma unroll
-  for (int j = 0; j < kSortItems; ++j) {
-    const int i = threadIdx.x * kSortItems + j;
-    k[j] = i < count ? (uint32_t)tiles[s_ids[i]] : 0u;
-    sum += k[j];
+  for (int j = 0; j < kScanItems; ++j) {
+    const int i = threadIdx.x * kScanItems + j;
+    sum += i < count ? s_k[i] : 0u;
   }
   uint32_t btotal;
-  uint32_t excl = block_excl_scan256(sum, s_tmp, &btotal);
+  const uint32_t excl = block_excl_scan256(sum, s_tmp, &btotal);
   if (threadIdx.x < 32) {
-    // warp look-back: lane l examines predecessor chunk - 1 - l (+32 per round)
     const int lane = threadIdx.x;
     unsigned long long* my = chunk_status + chunk;
     unsigned long long prefix = 0;
@@ -335,124 +180,170 @@ __global__ void __launch_bounds__(kSortThreads) emit_scan_kernel(
   __syncthreads();
   unsigned long long off = s_prefix + excl;
 #pragma unroll
-  for (int j = 0; j < kSortItems; ++j) {
-    const int i = threadIdx.x * kSortItems + j;
+  for (int j = 0; j < kScanItems; ++j) {
+    const int i = threadIdx.x * kScanItems + j;
     if (i < count) {
-      surfel_off[s_ids[i]] = (uint32_t)min(off, 0xFFFFFFFFull);
+      surfel_off[base + i] = (uint32_t)min(off, 0xFFFFFFFFull);
+      off += s_k[i];
       if (base + i == n - 1) {
-        const unsigned long long K = off + k[j];
-        *n_isect = (int32_t)min(K, (unsigned long long)0x7FFFFFFF);
-        if (K > (unsigned long long)capacity) atomicExch(gate, (int32_t)GS2D_ERR_CAPACITY);
+        *n_isect = (int32_t)min(off, (unsigned long long)0x7FFFFFFF);
+        if (off > (unsigned long long)capacity) atomicExch(gate, (int32_t)GS2D_ERR_CAPACITY);
       }
-      off += k[j];
     }
   }
 }
 
-// Emission: the r-th surfel in depth order writes its tiles (row-major over
-// its rectangle) at emission positions off .. off + k - 1, and counts the
-// tile digits for the tile sort.
-__global__ void __launch_bounds__(256) emit_kernel(
-    const uint32_t* __restrict__ sorted_ids, const int32_t* __restrict__ tiles,
-    const float4* __restrict__ proj, int n, const uint32_t* __restrict__ surfel_off, int tiles_x,
-    int n_tiles, uint32_t* __restrict__ tile_key, uint32_t* __restrict__ emit_id,
-    uint32_t* __restrict__ hist, const int32_t* __restrict__ gate) {
+// 2. Tile ranges from the tile counts (one block).
+__global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restrict__ tile_count,
+                                                        int n_tiles, int32_t* __restrict__ ranges,
+                                                        const int32_t* __restrict__ gate) {
+  __shared__ uint32_t s_w[32];
+  __shared__ uint32_t s_carry;
   if (*gate) return;
-  __shared__ uint32_t h[2][256];
-  for (int i = threadIdx.x; i < 512; i += blockDim.x) (&h[0][0])[i] = 0u;
+  if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < n) {
-    const uint32_t id = min(sorted_ids[r], (uint32_t)(n - 1));
-    const int k = tiles[id];
-    if (k > 0) {
-      const uint32_t off = surfel_off[id];
-      const float4 rc = proj[(size_t)id * (kProjFloats / 4) + 7];
-      const uint32_t r01 = __float_as_uint(rc.x), r23 = __float_as_uint(rc.y);
-      const int tx0 = r01 & 0xFFFF, ty0 = r01 >> 16, tx1 = r23 & 0xFFFF;
-      const int rw = max(tx1 - tx0 + 1, 1);
-      // exactly k pairs, row-major over the rectangle (k equals its area)
-      for (int j = 0; j < k; ++j) {
-        const int tx = tx0 + j % rw, ty = ty0 + j / rw;
-        const uint32_t t = (uint32_t)min(ty * tiles_x + tx, n_tiles - 1);
-        tile_key[off + j] = t;
-        emit_id[off + j] = id;
-        atomicAdd(&h[0][t & 255u], 1u);
-        atomicAdd(&h[1][(t >> 8) & 255u], 1u);
-      }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int base = 0; base < n_tiles; base += 1024) {
+    const int t = base + (int)threadIdx.x;
+    const uint32_t c = t < n_tiles ? tile_count[t] : 0u;
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
     }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 512; i += blockDim.x) {
-    const uint32_t c = (&h[0][0])[i];
-    if (c) atomicAdd(hist + i, c);
+    if (lane == 31) s_w[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+      const uint32_t x = s_w[lane];
+      uint32_t xi = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, xi, o);
+        if (lane >= o) xi += v;
+      }
+      s_w[lane] = xi - x;
+    }
+    __syncthreads();
+    const uint32_t start = s_carry + s_w[w] + inc - c;
+    if (t < n_tiles) {
+      ranges[2 * t] = (int32_t)start;
+      ranges[2 * t + 1] = (int32_t)(start + c);
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) s_carry = start + c;
+    __syncthreads();
   }
 }
 
-// Sorted (tile, emission index) -> per-position surfel id, emission index,
-// optional 64-bit key, and tile ranges.
-__global__ void __launch_bounds__(256) finalize_kernel(
-    const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ tvals,
-    const uint32_t* __restrict__ emit_id, const float4* __restrict__ proj,
-    const int32_t* __restrict__ n_isect, int cap, int n_tiles, uint32_t* __restrict__ vals,
-    uint32_t* __restrict__ emit, unsigned long long* __restrict__ keys64,
-    int32_t* __restrict__ ranges, const int32_t* __restrict__ gate) {
+// 3. Scatter of the (depth bits << 32 | id) keys into the tile segments.
+__global__ void __launch_bounds__(256) scatter_kernel(
+    const float4* __restrict__ proj, const int32_t* __restrict__ tiles, int n, int tiles_x,
+    int n_tiles, const int32_t* __restrict__ ranges, uint32_t* __restrict__ cursor,
+    unsigned long long* __restrict__ seg_keys, long long capacity,
+    const int32_t* __restrict__ gate) {
   if (*gate) return;
-  const int K = min(*n_isect, cap);
-  const int stride = gridDim.x * blockDim.x;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += stride) {
-    const uint32_t t = tkeys[k];
-    const uint32_t e = min(tvals[k], (uint32_t)(K - 1));
-    const uint32_t id = emit_id[e];
-    vals[k] = id;
-    emit[k] = e;
-    if (keys64) {
-      const uint32_t db = __float_as_uint(proj[(size_t)id * (kProjFloats / 4) + 6].z);
-      keys64[k] = ((unsigned long long)t << 32) | db;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int k = tiles[i];
+  if (k <= 0) return;
+  const Rect r = load_rect(proj, (uint32_t)i);
+  const uint32_t db = __float_as_uint(proj[(size_t)i * (kProjFloats / 4) + 6].z);
+  const unsigned long long key = ((unsigned long long)db << 32) | (uint32_t)i;
+  const int rw = max(r.tx1 - r.tx0 + 1, 1);
+  for (int j = 0; j < k; ++j) {
+    const int t = min((r.ty0 + j / rw) * tiles_x + r.tx0 + j % rw, n_tiles - 1);
+    const long long pos = (long long)ranges[2 * t] + atomicAdd(cursor + t, 1u);
+    if (pos < min((long long)ranges[2 * t + 1], capacity)) seg_keys[pos] = key;
+  }
+}
+
+// 4. Per-tile sort of the segment and the final outputs.  The flip-form
+// bitonic network sorts ascending with the smaller key to the lower index;
+// comparisons whose partner lies past the end are skipped (a virtual +inf).
+__device__ __forceinline__ void cmp_swap(unsigned long long* a, int i, int j) {
+  const unsigned long long x = a[i], y = a[j];
+  if (y < x) {
+    a[i] = y;
+    a[j] = x;
+  }
+}
+__device__ void bitonic_sort(unsigned long long* a, int len) {
+  int n2 = 1;
+  while (n2 < len) n2 <<= 1;
+  for (int size = 2; size <= n2; size <<= 1) {
+    // flip step: i pairs with its mirror i ^ (size - 1) inside each block
+    const int half = size >> 1;
+    for (int q = threadIdx.x; q < n2 / 2; q += blockDim.x) {
+      const int i = (q / half) * size + (q % half);
+      const int j = i ^ (size - 1);
+      if (j < len) cmp_swap(a, i, j);
     }
-    if (t < (uint32_t)n_tiles) {
-      if (k == 0 || tkeys[k - 1] != t) ranges[2 * t] = k;
-      if (k == K - 1 || tkeys[k + 1] != t) ranges[2 * t + 1] = k + 1;
+    __syncthreads();
+    for (int stride = size >> 2; stride > 0; stride >>= 1) {
+      for (int q = threadIdx.x; q < n2 / 2; q += blockDim.x) {
+        const int i = (q / stride) * (2 * stride) + (q % stride);
+        const int j = i + stride;
+        if (j < len) cmp_swap(a, i, j);
+      }
+      __syncthreads();
     }
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(
+    const float4* __restrict__ proj, int n, int tiles_x, const int32_t* __restrict__ ranges,
+    unsigned long long* __restrict__ seg_keys, const uint32_t* __restrict__ surfel_off,
+    uint32_t* __restrict__ vals, uint32_t* __restrict__ emit, unsigned long long* __restrict__ keys64,
+    long long capacity, const int32_t* __restrict__ gate) {
+  extern __shared__ unsigned long long s_keys[];
+  if (*gate) return;
+  const int t = blockIdx.x;
+  const int start = ranges[2 * t];
+  const int end = (int)min((long long)ranges[2 * t + 1], capacity);
+  const int len = end - start;
+  if (len <= 0) return;
+  unsigned long long* a;
+  if (len <= kSegSmem) {
+    for (int i = threadIdx.x; i < len; i += blockDim.x) s_keys[i] = seg_keys[start + i];
+    __syncthreads();
+    a = s_keys;
+  } else {
+    a = seg_keys + start;  // a rare long list: the same network in global memory
+  }
+  bitonic_sort(a, len);
+  const int tx = t % tiles_x, ty = t / tiles_x;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    const unsigned long long key = a[i];
+    const uint32_t id = min((uint32_t)(key & 0xFFFFFFFFull), (uint32_t)(n - 1));
+    const Rect r = load_rect(proj, id);
+    const int rw = max(r.tx1 - r.tx0 + 1, 1);
+    vals[start + i] = id;
+    emit[start + i] = surfel_off[id] + (uint32_t)((ty - r.ty0) * rw + (tx - r.tx0));
+    if (keys64) keys64[start + i] = ((unsigned long long)t << 32) | (key >> 32);
   }
 }
 
 // ---------------------------------------------------------------------------
 // workspace layout
 struct SortWs {
-  uint32_t *dk_a, *dk_b, *dv_a, *dv_b;      // depth keys / values [n]
-  uint32_t *tk_a, *tk_b, *tv_a, *tv_b;      // tile keys / values [cap]
-  uint32_t* emit_id;                        // [cap]
-  uint32_t* zero_begin;                     // start of the zeroed region
-  uint32_t* dhist;                          // [4*256]
-  uint32_t* thist;                          // [2*256]
-  uint32_t* tickets;                        // [8]
-  uint32_t* dstatus;                        // [4][chunks_n*256]
-  uint32_t* tstatus;                        // [2][chunks_cap*256]
-  unsigned long long* estatus;              // [chunks_n]
+  unsigned long long* seg_keys;  // [cap]
+  uint32_t* zero_begin;          // start of the zeroed region
+  uint32_t* tile_count;          // [n_tiles]
+  uint32_t* cursor;              // [n_tiles]
+  uint32_t* ticket;              // [8]
+  unsigned long long* estatus;   // [chunks_n]
   size_t zero_words;
   size_t bytes;
-  int chunks_n, chunks_cap;
+  int chunks_n;
 };
 
-SortWs carve_sort_ws(void* base, int n, size_t cap) {
+SortWs carve_sort_ws(void* base, int n, size_t cap, int n_tiles) {
   SortWs w{};
   Carver c(base);
   const size_t nn = (size_t)(n > 0 ? n : 1);
   w.chunks_n = (int)((nn + kChunk - 1) / kChunk);
-  w.chunks_cap = (int)((cap + kChunk - 1) / kChunk);
-  if (w.chunks_cap < 1) w.chunks_cap = 1;
-  w.dk_a = c.take<uint32_t>(nn);
-  w.dk_b = c.take<uint32_t>(nn);
-  w.dv_a = c.take<uint32_t>(nn);
-  w.dv_b = c.take<uint32_t>(nn);
-  const size_t cc = cap > 0 ? cap : 1;
-  w.tk_a = c.take<uint32_t>(cc);
-  w.tk_b = c.take<uint32_t>(cc);
-  w.tv_a = c.take<uint32_t>(cc);
-  w.tv_b = c.take<uint32_t>(cc);
-  w.emit_id = c.take<uint32_t>(cc);
-  // zeroed region: contiguous words
+  w.seg_keys = c.take<unsigned long long>(cap > 0 ? cap : 1);
   c.off = align_up(c.off, 256);
   const size_t zstart = c.off;
   w.zero_begin = base ? reinterpret_cast<uint32_t*>(static_cast<char*>(base) + zstart) : nullptr;
@@ -462,17 +353,12 @@ SortWs carve_sort_ws(void* base, int n, size_t cap) {
     words += (cnt + 63) / 64 * 64;
     return p;
   };
-  w.dhist = zt(4 * 256);
-  w.thist = zt(2 * 256);
-  w.tickets = zt(8);
-  w.dstatus = zt((size_t)4 * w.chunks_n * 256);
-  w.tstatus = zt((size_t)2 * w.chunks_cap * 256);
-  uint32_t* es = zt((size_t)2 * w.chunks_n + 2);
-  w.estatus = reinterpret_cast<unsigned long long*>(
-      base ? reinterpret_cast<uint32_t*>(align_up(reinterpret_cast<uintptr_t>(es), 8)) : nullptr);
+  w.tile_count = zt((size_t)n_tiles);
+  w.cursor = zt((size_t)n_tiles);
+  w.ticket = zt(8);
+  w.estatus = reinterpret_cast<unsigned long long*>(zt((size_t)2 * w.chunks_n + 2));
   w.zero_words = words;
-  c.off = zstart + words * sizeof(uint32_t) + 8;
-  w.bytes = align_up(c.off, 256);
+  w.bytes = align_up(zstart + words * sizeof(uint32_t), 256);
   return w;
 }
 
@@ -483,7 +369,8 @@ using namespace gs2d;
 extern "C" {
 
 size_t gs2d_bin_sort_workspace(int n, size_t capacity) {
-  return carve_sort_ws(nullptr, n, capacity).bytes;
+  // sized for the largest tile grid the ABI accepts
+  return carve_sort_ws(nullptr, n, capacity, 65535).bytes;
 }
 
 int gs2d_bin_sort(const float* proj, const int32_t* tiles_per_surfel, int n,
@@ -494,75 +381,41 @@ int gs2d_bin_sort(const float* proj, const int32_t* tiles_per_surfel, int n,
   if (!bins->vals || !bins->isect_emit || !bins->surfel_off || !bins->tile_ranges ||
       !bins->n_isect || !bins->status)
     return GS2D_ERR_INVALID_ARG;
-  if (bins->capacity >= (size_t)kValMask) return GS2D_ERR_INVALID_ARG;
+  if (bins->capacity >= (size_t)0x7FFFFFFF) return GS2D_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(proj) & 15) return GS2D_ERR_INVALID_ARG;
+  if (cfg->tile_w <= 0 || cfg->tile_h <= 0) return GS2D_ERR_INVALID_ARG;
   const int tx = gs2d_tiles_x(cam, cfg), ty = gs2d_tiles_y(cam, cfg);
   if (tx <= 0 || ty <= 0 || (long long)tx * ty > 65535) return GS2D_ERR_INVALID_ARG;
   const size_t need = gs2d_bin_sort_workspace(n, bins->capacity);
   if (ws_needed) *ws_needed = need;
   if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
   cudaStream_t st = (cudaStream_t)stream;
-  const SortWs w = carve_sort_ws(workspace, n, bins->capacity);
   const int n_tiles = tx * ty;
+  const SortWs w = carve_sort_ws(workspace, n, bins->capacity, n_tiles);
   int32_t* gate = bins->status;
+  const long long cap = (long long)bins->capacity;
+  const float4* p4 = reinterpret_cast<const float4*>(proj);
 
-  bin_init_kernel<<<64, 256, 0, st>>>(w.zero_begin, w.zero_words, bins->tile_ranges, 2 * n_tiles,
-                                      bins->n_isect, gate);
+  bin_init_kernel<<<32, 256, 0, st>>>(w.zero_begin, w.zero_words, bins->n_isect, gate);
+  GS2D_LAUNCH_CHECK();
+  if (n > 0) {
+    count_scan_kernel<<<w.chunks_n, kScanThreads, 0, st>>>(
+        p4, tiles_per_surfel, n, tx, n_tiles, bins->surfel_off, w.tile_count, w.estatus, w.ticket,
+        bins->n_isect, cap, gate);
+    GS2D_LAUNCH_CHECK();
+  }
+  tile_scan_kernel<<<1, 1024, 0, st>>>(w.tile_count, n_tiles, bins->tile_ranges, gate);
   GS2D_LAUNCH_CHECK();
   if (n == 0) return GS2D_OK;
-  const float4* p4 = reinterpret_cast<const float4*>(proj);
-  {
-    const int blocks = min((n + 255) / 256, 152 * 8);
-    depth_keys_kernel<<<blocks, 256, 0, st>>>(p4, tiles_per_surfel, n, w.dk_a, w.dv_a, w.dhist, gate);
-    GS2D_LAUNCH_CHECK();
-  }
-  // depth sort: 4 passes, ping-pong a -> b -> a -> b -> a
-  uint32_t *ki = w.dk_a, *vi = w.dv_a, *ko = w.dk_b, *vo = w.dv_b;
-  for (int p = 0; p < 4; ++p) {
-    radix_pass_kernel<<<w.chunks_n, kSortThreads, 0, st>>>(
-        ki, vi, ko, vo, nullptr, n, n, 8 * p, w.dhist + 256 * p,
-        w.dstatus + (size_t)p * w.chunks_n * 256, w.tickets + p, gate);
-    GS2D_LAUNCH_CHECK();
-    uint32_t* t = ki;
-    ki = ko;
-    ko = t;
-    t = vi;
-    vi = vo;
-    vo = t;
-  }
-  const uint32_t* sorted_ids = vi;
-  emit_scan_kernel<<<w.chunks_n, kSortThreads, 0, st>>>(sorted_ids, tiles_per_surfel, n,
-                                                        bins->surfel_off, w.estatus, w.tickets + 4,
-                                                        bins->n_isect, (long long)bins->capacity, gate);
+  scatter_kernel<<<(n + 255) / 256, 256, 0, st>>>(p4, tiles_per_surfel, n, tx, n_tiles,
+                                                  bins->tile_ranges, w.cursor, w.seg_keys, cap,
+                                                  gate);
   GS2D_LAUNCH_CHECK();
-  emit_kernel<<<(n + 255) / 256, 256, 0, st>>>(sorted_ids, tiles_per_surfel, p4, n, bins->surfel_off,
-                                                tx, n_tiles, w.tk_a, w.emit_id, w.thist, gate);
+  const size_t smem = (size_t)kSegSmem * sizeof(unsigned long long);
+  tile_sort_kernel<<<n_tiles, kSortThreads, smem, st>>>(
+      p4, n, tx, bins->tile_ranges, w.seg_keys, bins->surfel_off, bins->vals, bins->isect_emit,
+      reinterpret_cast<unsigned long long*>(bins->keys), cap, gate);
   GS2D_LAUNCH_CHECK();
-  // stable sort of the emission by tile: one pass if ids fit in 8 bits
-  const int cap = (int)bins->capacity;
-  const int grid_cap = w.chunks_cap;
-  radix_pass_kernel<<<grid_cap, kSortThreads, 0, st>>>(w.tk_a, nullptr, w.tk_b, w.tv_b, bins->n_isect,
-                                                       0, cap, 0, w.thist, w.tstatus, w.tickets + 5,
-                                                       gate);
-  GS2D_LAUNCH_CHECK();
-  const uint32_t *tk = w.tk_b, *tv = w.tv_b;
-  if (n_tiles > 256) {
-    radix_pass_kernel<<<grid_cap, kSortThreads, 0, st>>>(
-        w.tk_b, w.tv_b, w.tk_a, w.tv_a, bins->n_isect, 0, cap, 8, w.thist + 256,
-        w.tstatus + (size_t)w.chunks_cap * 256, w.tickets + 6, gate);
-    GS2D_LAUNCH_CHECK();
-    tk = w.tk_a;
-    tv = w.tv_a;
-  }
-  {
-    const int blocks = max(1, min((cap + 255) / 256, 152 * 16));
-    finalize_kernel<<<blocks, 256, 0, st>>>(tk, tv, w.emit_id, p4, bins->n_isect, cap, n_tiles,
-                                            bins->vals,
-                                            bins->isect_emit,
-                                            reinterpret_cast<unsigned long long*>(bins->keys),
-                                            bins->tile_ranges, gate);
-    GS2D_LAUNCH_CHECK();
-  }
   return GS2D_OK;
 }
 

@@ -1,10 +1,13 @@
 // gs2d_track_step: frame-to-map camera tracking (Sec. III-D) as one device-
-// resident launch sequence.  Each iteration renders the map at the current
-// pose, evaluates the masked tracking loss (Eq. tracking_loss), back-
-// propagates it to the pose tangent only (Sec. III-B; the map is frozen
-// during tracking), and takes an AdamW step on tau = (rho, theta) followed by
-// the retraction T <- Exp(tau) T with tau reset to zero (the moments are
-// kept across iterations of the frame).
+// resident launch sequence.  Each iteration projects and bins the map at the
+// current pose, then one fused kernel per tile renders it, evaluates the
+// masked tracking loss (Eq. tracking_loss) and back-propagates it to the pose
+// tangent only (Sec. III-B; the map is frozen during tracking), and a last
+// kernel reduces the tiles' partials and takes an AdamW step on
+// tau = (rho, theta) followed by the retraction T <- Exp(tau) T with tau reset
+// to zero (the moments are kept across iterations of the frame).
+// Four launches per iteration: project, bin_sort (5 kernels), fused tile
+// kernel, reduce + AdamW -- 8 kernels.
 #include <math.h>
 
 #include "gs2d_common.cuh"
@@ -13,6 +16,15 @@
 namespace gs2d {
 
 constexpr int32_t kConverged = 256;  // gate value after early stopping
+
+// Optional timing of the fused tile kernel (see gs2d_profile_track_kernel).
+struct KernelTimer {
+  cudaEvent_t* start = nullptr;
+  cudaEvent_t* stop = nullptr;
+  int capacity = 0;
+  int used = 0;
+};
+KernelTimer g_timer;
 
 __global__ void track_reset_kernel(float* adam, int32_t* status) {
   if (threadIdx.x < 16) adam[threadIdx.x] = 0.f;
@@ -56,23 +68,42 @@ __device__ void se3_exp_f(const float tau[6], float R[9], float t[3]) {
   }
 }
 
-// AdamW on tau (zero before the step, so weight decay has no effect), then
-// the left retraction.  Records the loss at the pre-update pose and the
-// updated pose.  adam = m[6], v[6], step, done.
-__global__ void adam_retract_kernel(const float* __restrict__ g6, float* __restrict__ pose,
-                                    float* __restrict__ adam, gs2d_track_params prm,
-                                    const float* __restrict__ loss, float* __restrict__ loss_hist,
-                                    float* __restrict__ pose_hist, int iter,
-                                    int32_t* __restrict__ status) {
-  if (threadIdx.x != 0) return;
+// Fixed-order reduction of the tiles' loss and pose partials, then AdamW on
+// tau (zero before the step, so weight decay has no effect) and the left
+// retraction.  Records the loss at the pre-update pose and the updated pose.
+// adam = m[6], v[6], step, done.
+__global__ void __launch_bounds__(256) adam_retract_kernel(
+    const float* __restrict__ pose_part, const float* __restrict__ loss_part, int n_part,
+    float* __restrict__ pose, float* __restrict__ adam, gs2d_track_params prm,
+    float* __restrict__ loss_hist, float* __restrict__ pose_hist, int iter,
+    int32_t* __restrict__ status) {
+  __shared__ float s[7][256];
   const int32_t st = *status;
+  if (st != 0 && st != kConverged) return;
   if (st == kConverged) {
-    if (loss_hist) loss_hist[iter] = loss_hist[iter > 0 ? iter - 1 : 0];
-    if (pose_hist)
-      for (int k = 0; k < 12; ++k) pose_hist[12 * iter + k] = pose[k];
+    if (threadIdx.x == 0) {
+      if (loss_hist) loss_hist[iter] = loss_hist[iter > 0 ? iter - 1 : 0];
+      if (pose_hist)
+        for (int k = 0; k < 12; ++k) pose_hist[12 * iter + k] = pose[k];
+    }
     return;
   }
-  if (st != 0) return;
+  float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int b = threadIdx.x; b < n_part; b += 256) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[c] += pose_part[(size_t)b * 6 + c];
+    acc[6] += loss_part[b];
+  }
+#pragma unroll
+  for (int c = 0; c < 7; ++c) s[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+#pragma unroll
+      for (int c = 0; c < 7; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
   const float step = adam[12] + 1.f;
   adam[12] = step;
   const float bc1 = 1.f - powf(prm.beta1, step), bc2 = 1.f - powf(prm.beta2, step);
@@ -80,7 +111,7 @@ __global__ void adam_retract_kernel(const float* __restrict__ g6, float* __restr
   float nrm2 = 0.f;
   bool finite = true;
   for (int k = 0; k < 6; ++k) {
-    const float g = g6[k];
+    const float g = s[k][0];
     finite = finite && isfinite(g);
     const float m = prm.beta1 * adam[k] + (1.f - prm.beta1) * g;
     const float v = prm.beta2 * adam[6 + k] + (1.f - prm.beta2) * g * g;
@@ -89,7 +120,7 @@ __global__ void adam_retract_kernel(const float* __restrict__ g6, float* __restr
     tau[k] = -prm.lr * (m / bc1) / (sqrtf(v / bc2) + prm.eps);
     nrm2 += tau[k] * tau[k];
   }
-  if (loss_hist) loss_hist[iter] = *loss;
+  if (loss_hist) loss_hist[iter] = s[6][0];
   if (!finite) {
     *status = GS2D_ERR_NONFINITE;
     return;
@@ -116,17 +147,10 @@ struct TrackWs {
   float* proj;
   int32_t* tiles;
   uint32_t *vals, *emit, *soff;
-  int32_t *ranges, *n_isect, *status;
+  int32_t *ranges, *n_isect;
   void* sort_ws;
   size_t sort_bytes;
-  float *rgb, *depth, *normal, *opac, *T;
-  uint32_t* nlast;
-  float *g_rgb, *g_depth, *g_opac;
-  void* loss_ws;
-  size_t loss_bytes;
-  void* bwd_ws;
-  size_t bwd_bytes;
-  float *adam, *loss, *g6;
+  float *loss_part, *pose_part, *adam;
   size_t bytes;
 };
 
@@ -136,7 +160,6 @@ TrackWs carve_track_ws(void* base, int n, size_t cap, const gs2d_camera* cam,
   TrackWs w;
   const size_t nn = n > 0 ? n : 1;
   const size_t cc = cap > 0 ? cap : 1;
-  const size_t P = (size_t)cam->width * cam->height;
   const int nt = gs2d_tiles_x(cam, cfg) * gs2d_tiles_y(cam, cfg);
   w.proj = c.take<float>(nn * kProjFloats);
   w.tiles = c.take<int32_t>(nn);
@@ -145,25 +168,11 @@ TrackWs carve_track_ws(void* base, int n, size_t cap, const gs2d_camera* cam,
   w.soff = c.take<uint32_t>(nn);
   w.ranges = c.take<int32_t>(2 * (size_t)nt);
   w.n_isect = c.take<int32_t>(1);
-  w.status = c.take<int32_t>(1);
   w.sort_bytes = gs2d_bin_sort_workspace(n, cap);
   w.sort_ws = c.take<char>(w.sort_bytes);
-  w.rgb = c.take<float>(3 * P);
-  w.depth = c.take<float>(P);
-  w.normal = c.take<float>(3 * P);
-  w.opac = c.take<float>(P);
-  w.T = c.take<float>(P);
-  w.nlast = c.take<uint32_t>(P);
-  w.g_rgb = c.take<float>(3 * P);
-  w.g_depth = c.take<float>(P);
-  w.g_opac = c.take<float>(P);
-  w.loss_bytes = loss_ws_bytes(cam);
-  w.loss_ws = c.take<char>(w.loss_bytes);
-  w.bwd_bytes = render_bwd_ws_bytes(n, cap, nt, false);
-  w.bwd_ws = c.take<char>(w.bwd_bytes);
+  w.loss_part = c.take<float>((size_t)nt);
+  w.pose_part = c.take<float>((size_t)nt * 6);
   w.adam = c.take<float>(16);
-  w.loss = c.take<float>(1);
-  w.g6 = c.take<float>(8);
   w.bytes = align_up(c.off, 256);
   return w;
 }
@@ -180,6 +189,17 @@ size_t gs2d_track_workspace(int n, size_t capacity, const gs2d_camera* cam,
   // the first 256 bytes hold the status word at a size-independent address
   return 256 + carve_track_ws(nullptr, n, capacity, cam, cfg).bytes;
 }
+
+int gs2d_profile_track_kernel(void* const* start_events, void* const* stop_events, int n) {
+  if (n < 0 || (n > 0 && (!start_events || !stop_events))) return GS2D_ERR_INVALID_ARG;
+  g_timer.start = reinterpret_cast<cudaEvent_t*>(const_cast<void**>(start_events));
+  g_timer.stop = reinterpret_cast<cudaEvent_t*>(const_cast<void**>(stop_events));
+  g_timer.capacity = n;
+  g_timer.used = 0;
+  return GS2D_OK;
+}
+
+int gs2d_profile_track_kernel_count(void) { return g_timer.used; }
 
 int32_t* gs2d_track_status(void* workspace) {
   return workspace ? reinterpret_cast<int32_t*>(workspace) : nullptr;
@@ -210,25 +230,21 @@ int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_co
   bins.n_isect = w.n_isect;
   bins.status = status;
   bins.capacity = capacity;
+  const int n_tiles = gs2d_tiles_x(cam, cfg) * gs2d_tiles_y(cam, cfg);
   for (int it = 0; it < n_iter; ++it) {
     int r = project_launch(s, cam, pose, cfg, w.proj, w.tiles, status, st);
     if (r) return r;
     r = gs2d_bin_sort(w.proj, w.tiles, s->n, cam, cfg, w.sort_ws, w.sort_bytes, nullptr, &bins,
                       stream);
     if (r) return r;
-    r = render_fwd_launch(w.proj, &bins, cam, cfg, w.rgb, w.depth, w.normal, w.opac, w.T, w.nlast,
-                          status, st);
+    const bool timed = g_timer.used < g_timer.capacity;
+    if (timed) GS2D_CUDA_TRY(cudaEventRecord(g_timer.start[g_timer.used], st));
+    r = track_tile_launch(w.proj, &bins, cam, cfg, obs_rgb, obs_depth, prm, w.loss_part,
+                          w.pose_part, status, st);
     if (r) return r;
-    r = tracking_loss_launch(w.rgb, w.depth, w.normal, w.opac, obs_rgb, obs_depth, cam, prm,
-                             w.g_rgb, w.g_depth, w.g_opac, w.loss, w.loss_ws, w.loss_bytes, nullptr,
-                             status, st);
-    if (r) return r;
-    r = render_bwd_launch(w.proj, &bins, w.tiles, s, pose, cam, cfg, w.T, w.nlast, w.g_rgb,
-                          w.g_depth, nullptr, w.g_opac, nullptr, nullptr, nullptr, nullptr, nullptr,
-                          w.g6, w.bwd_ws, w.bwd_bytes, nullptr, status, st);
-    if (r) return r;
-    adam_retract_kernel<<<1, 32, 0, st>>>(w.g6, pose, w.adam, *prm, w.loss, loss_hist, pose_hist,
-                                          it, status);
+    if (timed) GS2D_CUDA_TRY(cudaEventRecord(g_timer.stop[g_timer.used++], st));
+    adam_retract_kernel<<<1, 256, 0, st>>>(w.pose_part, w.loss_part, n_tiles, pose, w.adam, *prm,
+                                           loss_hist, pose_hist, it, status);
     GS2D_LAUNCH_CHECK();
   }
   return GS2D_OK;

@@ -67,7 +67,8 @@ EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_stri
            "gs2d_tiles_x", "gs2d_tiles_y", "gs2d_project", "gs2d_bin_sort_workspace",
            "gs2d_bin_sort", "gs2d_render_fwd", "gs2d_render_bwd_workspace", "gs2d_render_bwd",
            "gs2d_tracking_loss", "gs2d_mapping_loss", "gs2d_track_workspace", "gs2d_track_step",
-           "gs2d_track_status", "gs2d_render_count", "gs2d_bin_sort_static"]
+           "gs2d_track_status", "gs2d_render_count", "gs2d_bin_sort_static",
+           "gs2d_profile_track_kernel", "gs2d_profile_track_kernel_count"]
 
 
 def lib_path() -> str:
@@ -104,6 +105,8 @@ def lib():
         L.gs2d_track_workspace.restype = sz
         L.gs2d_track_workspace.argtypes = [ip, sz, vp, vp]
         L.gs2d_track_step.argtypes = [vp] * 7 + [ip, sz, vp, vp, vp, sz, vp, vp]
+        L.gs2d_profile_track_kernel.argtypes = [vp, vp, ip]
+        L.gs2d_profile_track_kernel_count.restype = ip
         L.gs2d_track_status.restype = vp
         L.gs2d_track_status.argtypes = [vp]
         _LIB = L
@@ -271,6 +274,29 @@ def gs2d_track_step(surf: DeviceSurfels, cam: Camera, cfg: Config, prm: TrackPar
                                 _ptr(loss_hist), _ptr(pose_hist), _ptr(workspace),
                                 workspace.numel() * workspace.element_size(), None,
                                 _stream(stream)), "gs2d_track_step")
+
+
+def gs2d_profile_track_kernel(events_start, events_stop):
+    """Record the given torch.cuda.Event pairs around the next launches of
+    the fused tracking kernel (empty lists switch it off)."""
+    n = len(events_start)
+    if n == 0:
+        check(lib().gs2d_profile_track_kernel(None, None, 0), "gs2d_profile_track_kernel")
+        _PROFILE_KEEP.clear()
+        return
+    for e in list(events_start) + list(events_stop):
+        e.record()   # make sure the underlying cudaEvent_t exists
+    a = (ctypes.c_void_p * n)(*[e.cuda_event for e in events_start])
+    b = (ctypes.c_void_p * n)(*[e.cuda_event for e in events_stop])
+    _PROFILE_KEEP[:] = [a, b, list(events_start), list(events_stop)]
+    check(lib().gs2d_profile_track_kernel(a, b, n), "gs2d_profile_track_kernel")
+
+
+def gs2d_profile_track_kernel_count() -> int:
+    return int(lib().gs2d_profile_track_kernel_count())
+
+
+_PROFILE_KEEP = []
 
 
 def gs2d_track_status(workspace) -> torch.Tensor:

@@ -75,7 +75,11 @@ def test_bin_sort_bit_exact(torch_cuda, orc, n, tiles_x, tiles_y, seed):
     assert K == len(ov)
     np.testing.assert_array_equal(r.vals[:K].cpu().numpy().astype(np.uint32), ov)
     np.testing.assert_array_equal(r.keys[:K].cpu().numpy().view(np.uint64), ok)
-    np.testing.assert_array_equal(r.ranges.cpu().numpy().reshape(-1, 2), orng)
+    # non-empty tiles: identical ranges; an empty tile may sit anywhere (start == end)
+    grng = r.ranges.cpu().numpy().reshape(-1, 2)
+    nonempty = orng[:, 1] > orng[:, 0]
+    np.testing.assert_array_equal(grng[nonempty], orng[nonempty])
+    assert np.all(grng[~nonempty, 0] == grng[~nonempty, 1])
     # emission indices: a permutation; each surfel's block is contiguous
     emit = r.emit[:K].cpu().numpy()
     assert np.array_equal(np.sort(emit), np.arange(K))
@@ -188,20 +192,10 @@ def test_render_edge_cases(torch_cuda, orc):
 # ---------------------------------------------------------------------------
 # backward
 # ---------------------------------------------------------------------------
-def view_cos(s, pose):
-    """|cos| between each surfel's normal and the ray to its centre."""
-    from scipy.spatial.transform import Rotation
-    q = s.quat / np.linalg.norm(s.quat, axis=1, keepdims=True)
-    n_w = Rotation.from_quat(np.concatenate([q[:, 1:], q[:, :1]], 1)).as_matrix()[:, :, 2]
-    n_c = n_w @ pose.R.T
-    mu_c = s.mu @ pose.R.T + pose.t
-    return np.abs(np.sum(n_c * mu_c, 1)) / np.linalg.norm(mu_c, axis=1)
-
-
 def _grad_close(a, b, name, tol=TOL_GRAD, rows=None):
     """max |a - b| <= tol * max |b| over the array, and per element for
     elements above 1% of the array's scale (99.8% of them), on the rows (surfels) selected by
-    ``rows`` -- those not seen within ~6 degrees of edge-on, where the FP32
+    ``rows`` -- those not seen within ~3 degrees of edge-on at any pixel, where the FP32
     intersection is ill-conditioned."""
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
@@ -238,7 +232,7 @@ def test_render_bwd_slab_all_params_and_pose(torch_cuda, orc):
     T = lambda a: torch.tensor(np.asarray(a, np.float32), device="cuda")
     gg = r.backward(ds, pose_t, T(d_rgb), T(d_depth), None, None, full=True)
     torch.cuda.synchronize()
-    ok = view_cos(s, pose) > 0.1
+    ok = og["min_cos"] > 0.05
     for k in ("mu", "quat", "scale", "opacity", "rgb", "pose6"):
         _grad_close(to_np(gg[k]), og[k], k, rows=ok)
     # tracking mode returns the same pose gradient
@@ -254,7 +248,7 @@ def test_render_bwd_with_normal_and_opacity_grads(torch_cuda, orc):
     og = orc.render_bwd(s, cam, pose, *up)
     T = lambda a: torch.tensor(np.asarray(a, np.float32), device="cuda")
     gg = r.backward(ds, pose_t, T(up[0]), T(up[1]), T(up[2]), T(up[3]), full=True)
-    ok = view_cos(s, pose) > 0.1
+    ok = og["min_cos"] > 0.05
     for k in ("mu", "quat", "scale", "opacity", "rgb", "pose6"):
         _grad_close(to_np(gg[k]), og[k], k, rows=ok)
     gp = r.backward(ds, pose_t, T(up[0]), T(up[1]), T(up[2]), T(up[3]), full=False)
@@ -292,6 +286,6 @@ def test_render_bwd_room_pixel_subset(torch_cuda, orc):
     gg = r.backward(ds, pose_t, *(T(u) for u in up), full=True)
     touched = np.abs(og["rgb"]).sum(1) > 0
     assert touched.sum() > 100
-    ok = view_cos(s, pose) > 0.1
+    ok = og["min_cos"] > 0.05
     for k in ("mu", "quat", "scale", "opacity", "rgb", "pose6"):
         _grad_close(to_np(gg[k]), og[k], k, rows=ok)
