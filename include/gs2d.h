@@ -255,9 +255,10 @@ int32_t* gs2d_track_status(void* workspace);
 
 /* Diagnostic timing of the fused tile kernel of gs2d_track_step: while set,
  * every later launch of that kernel (in any gs2d_track_step call, in launch
- * order) is bracketed by cudaEventRecord(start_events[i]) and
- * cudaEventRecord(stop_events[i]) on the call's stream, until n launches
- * have been recorded.  The events are caller-created cudaEvent_t handles
+ * order) is bracketed by records of start_events[i] and stop_events[i] on
+ * the call's stream (event-record nodes when the stream is being captured
+ * into a CUDA graph, so every replay records them), until n launches have
+ * been recorded.  The events are caller-created cudaEvent_t handles
  * that must stay alive meanwhile.  n = 0 switches it off.  No work is
  * skipped or reordered.  gs2d_profile_track_kernel_count() = launches
  * recorded so far.  Not thread safe. */

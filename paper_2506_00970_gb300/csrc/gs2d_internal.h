@@ -14,18 +14,35 @@ int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* p
                    const gs2d_config* cfg, float* proj_out, int32_t* tiles_per_surfel_out,
                    const int32_t* gate, cudaStream_t st);
 
+// gs2d_bin_sort; with need_emit false the emission offsets and indices
+// (used only by the full backward) are not computed.
+int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
+                    const gs2d_camera* cam, const gs2d_config* cfg, void* workspace,
+                    size_t ws_bytes, size_t* ws_needed, const gs2d_bins* bins, bool need_emit,
+                    cudaStream_t st);
+
 int render_fwd_launch(const float* proj, const gs2d_bins* bins, const gs2d_camera* cam,
                       const gs2d_config* cfg, float* rgb, float* depth, float* normal,
                       float* opacity, float* t_final, uint32_t* n_last, const int32_t* gate,
                       cudaStream_t st);
 
-// Fused tracking iteration (forward, tracking loss, pose backward) per tile:
-// loss_part [n_tiles] (already divided by the pixel count), pose_part
-// [n_tiles * 6].
+// The pose-update state the fused tracking kernel's last block works on.
+struct TrackStep {
+  float* pose;       // [12] in/out
+  float* adam;       // [16] m, v, step, done
+  float* loss_hist;  // [n_iter] or NULL
+  float* pose_hist;  // [n_iter * 12] or NULL
+  int iter;
+  uint32_t* counter; // blocks finished in this iteration (reset by the last)
+};
+
+// Fused tracking iteration per tile (forward, tracking loss, pose backward)
+// with the pose update in the last block: loss_part [n_tiles] (already
+// divided by the pixel count), pose_part [n_tiles * 6].  status is the gate.
 int track_tile_launch(const float* proj, const gs2d_bins* bins, const gs2d_camera* cam,
                       const gs2d_config* cfg, const float* obs_rgb, const float* obs_depth,
                       const gs2d_track_params* prm, float* loss_part, float* pose_part,
-                      const int32_t* gate, cudaStream_t st);
+                      const TrackStep& ts, int32_t* status, cudaStream_t st);
 
 size_t render_bwd_ws_bytes(int n, size_t cap, int n_tiles, bool full);
 int render_bwd_launch(const float* proj, const gs2d_bins* bins, const int32_t* tiles_per_surfel,

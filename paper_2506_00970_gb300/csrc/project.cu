@@ -110,17 +110,13 @@ __device__ bool footprint_bounds(F3 a1, F3 a2, F3 a3, float rho, float zmin, flo
   return true;
 }
 
-__global__ void __launch_bounds__(256) project_kernel(
-    const float* __restrict__ mu, const float* __restrict__ quat, const float* __restrict__ scale,
-    const float* __restrict__ opacity, const float* __restrict__ rgb, int n,
-    const float* __restrict__ pose, gs2d_camera cam, gs2d_config cfg, int tiles_x, int tiles_y,
-    float4* __restrict__ proj, int32_t* __restrict__ tiles_out, const int32_t* __restrict__ gate) {
-  __shared__ float sp[12];
-  if (gate && *gate) return;
-  if (threadIdx.x < 12) sp[threadIdx.x] = pose[threadIdx.x];
-  __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ __forceinline__ void project_one(int i, const float* __restrict__ mu,
+                                            const float* __restrict__ quat,
+                                            const float* __restrict__ scale,
+                                            const float* __restrict__ opacity,
+                                            const float* __restrict__ rgb, const float* sp,
+                                            const gs2d_camera& cam, const gs2d_config& cfg,
+                                            float4* o, int32_t* __restrict__ tiles_out) {
   const float* Rcw = sp;
 
   // quaternion -> rotation columns t_u, t_v, t_n
@@ -184,7 +180,6 @@ __global__ void __launch_bounds__(256) project_kernel(
   const int k = (tx0 <= tx1 && ty0 <= ty1) ? (tx1 - tx0 + 1) * (ty1 - ty0 + 1) : 0;
   tiles_out[i] = k;
 
-  float4* o = proj + (size_t)i * (kProjFloats / 4);
   const float rgb0 = rgb[3 * i], rgb1 = rgb[3 * i + 1], rgb2 = rgb[3 * i + 2];
   const uint32_t r01 = (uint32_t)tx0 | ((uint32_t)ty0 << 16);
   const uint32_t r23 = (uint32_t)tx1 | ((uint32_t)ty1 << 16);
@@ -199,9 +194,31 @@ __global__ void __launch_bounds__(256) project_kernel(
   o[6] = make_float4(dv.y, dv.z, mu_c.z, 0.f);
   o[7] = make_float4(__uint_as_float(r01), __uint_as_float(r23), __uint_as_float(b01),
                      __uint_as_float(b23));
-  (void)tiles_x;
-  (void)tiles_y;
 }
+
+__global__ void __launch_bounds__(256) project_kernel(
+    const float* __restrict__ mu, const float* __restrict__ quat, const float* __restrict__ scale,
+    const float* __restrict__ opacity, const float* __restrict__ rgb, int n,
+    const float* __restrict__ pose, gs2d_camera cam, gs2d_config cfg, int tiles_x, int tiles_y,
+    float4* __restrict__ proj, int32_t* __restrict__ tiles_out, const int32_t* __restrict__ gate) {
+  // records are assembled in shared memory (9 float4 per thread: padded so
+  // both the per-thread writes and the block's coalesced copy-out are free
+  // of bank conflicts) and written as one contiguous 32 KB run per block
+  __shared__ float4 s_out[256 * 9];
+  __shared__ float sp[12];
+  if (gate && *gate) return;
+  if (threadIdx.x < 12) sp[threadIdx.x] = pose[threadIdx.x];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) project_one(i, mu, quat, scale, opacity, rgb, sp, cam, cfg, s_out + threadIdx.x * 9,
+                         tiles_out);
+  __syncthreads();
+  const int base = blockIdx.x * blockDim.x;
+  const int valid = min((int)blockDim.x, n - base);
+  float4* dst = proj + (size_t)base * (kProjFloats / 4);
+  for (int v = threadIdx.x; v < valid * 8; v += blockDim.x) dst[v] = s_out[(v >> 3) * 9 + (v & 7)];
+}
+
 
 int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* pose,
                    const gs2d_config* cfg, float* proj_out, int32_t* tiles_per_surfel_out,

@@ -41,6 +41,7 @@
 #include "gs2d_common.cuh"
 #include "gs2d_internal.h"
 #include "loss_pixel.cuh"
+#include "track_update.cuh"
 
 namespace gs2d {
 
@@ -86,6 +87,40 @@ __device__ __forceinline__ bool warp_hits(float bi, float bj, int bx0, int by0) 
   const uint32_t I = __float_as_uint(bi), J = __float_as_uint(bj);
   const int i0 = I & 0xFFFF, i1 = I >> 16, j0 = J & 0xFFFF, j1 = J >> 16;
   return !(i1 < bx0 || i0 > bx0 + 7 || j1 < by0 || j0 > by0 + 3);
+}
+
+// Mask of the tile's 8 warp blocks (8 x 4 pixels each) that a footprint
+// (packed pixel ranges) touches; bit w for warp w.
+__device__ __forceinline__ uint32_t footprint_mask(float bi, float bj, int tile_x0, int tile_y0,
+                                                   int tile_w) {
+  const uint32_t I = __float_as_uint(bi), J = __float_as_uint(bj);
+  const int i0 = (int)(I & 0xFFFF) - tile_x0, i1 = (int)(I >> 16) - tile_x0;
+  const int j0 = (int)(J & 0xFFFF) - tile_y0, j1 = (int)(J >> 16) - tile_y0;
+  const int wpr = tile_w >> 3;
+  uint32_t m = 0u;
+#pragma unroll
+  for (int w = 0; w < kTileThreads / 32; ++w) {
+    const int ox = (w % wpr) * 8, oy = (w / wpr) * 4;
+    if (!(i1 < ox || i0 > ox + 7 || j1 < oy || j0 > oy + 3)) m |= 1u << w;
+  }
+  return m;
+}
+
+// Per-warp compaction of a staged batch: the indices (in staging order) of
+// the surfels whose footprint touches this warp's block.  Returns the count.
+__device__ __forceinline__ int warp_hit_list(const uint32_t* s_mask, uint8_t* my_list, int cnt,
+                                             int warp, int lane) {
+  int n = 0;
+#pragma unroll
+  for (int c = 0; c < kTileThreads; c += 32) {
+    const int j = c + lane;
+    const bool hit = j < cnt && ((s_mask[j] >> warp) & 1u);
+    const uint32_t b = __ballot_sync(0xffffffffu, hit);
+    if (hit) my_list[n + __popc(b & ((1u << lane) - 1u))] = (uint8_t)j;
+    n += __popc(b);
+  }
+  __syncwarp();
+  return n;
 }
 
 // Evaluation of one (pixel, surfel) pair shared by every pass, so all take
@@ -141,14 +176,22 @@ struct FwdState {
   uint32_t last;
 };
 
-// Front-to-back compositing of one pixel over its tile's list.  With kCount
-// it counts evaluated pairs, pairs inside the cutoff and blended pairs.
+// Front-to-back compositing of one pixel over its tile's list.  Each warp
+// visits only the staged surfels whose footprint touches its block.  With
+// kCount it counts evaluated pairs, pairs inside the cutoff and blended pairs.
+struct HitLists {
+  uint32_t mask[kTileThreads];
+  uint8_t list[kTileThreads / 32][kTileThreads];
+};
+
 template <int kStride, bool kCount>
 __device__ __forceinline__ FwdState fwd_tile(const float4* __restrict__ proj,
                                              const uint32_t* __restrict__ vals, int start, int end,
-                                             float xt, float yt, const TilePix& tp, bool inside,
+                                             float xt, float yt, int tile_x0, int tile_y0,
+                                             const TilePix& tp, bool inside,
                                              const gs2d_camera& cam, const gs2d_config& cfg,
-                                             float4 (*s_rec)[kStride], uint32_t* cnt) {
+                                             float4 (*s_rec)[kStride], HitLists& hl,
+                                             uint32_t* cnt) {
   FwdState st;
   st.T = 1.f;
   st.D = 0.f;
@@ -156,21 +199,24 @@ __device__ __forceinline__ FwdState fwd_tile(const float4* __restrict__ proj,
   st.N = f3(0.f, 0.f, 0.f);
   st.last = 0;
   bool done = !inside;
-  constexpr int kNrm = kStride == kFwdVec4 ? 4 : 6;  // slot holding the footprint
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kFp = kStride == kFwdVec4 ? 4 : 6;  // slot holding the footprint
   for (int b = start; b < end; b += kTileThreads) {
     if (__syncthreads_count(!done) == 0) break;
     const int idx = b + (int)threadIdx.x;
-    if (idx < end) stage_record<kStride>(proj, vals[idx], xt, yt, s_rec);
+    if (idx < end) {
+      stage_record<kStride>(proj, vals[idx], xt, yt, s_rec);
+      const float4 rf = s_rec[threadIdx.x][kFp];
+      hl.mask[threadIdx.x] = kStride == kFwdVec4
+                                 ? footprint_mask(rf.y, rf.z, tile_x0, tile_y0, cfg.tile_w)
+                                 : footprint_mask(rf.z, rf.w, tile_x0, tile_y0, cfg.tile_w);
+    }
     __syncthreads();
     const int cnt_b = min(kTileThreads, end - b);
+    const int nh = warp_hit_list(hl.mask, hl.list[warp], cnt_b, warp, lane);
     if (!done) {
-      for (int j = 0; j < cnt_b; ++j) {
-        const float4 rf = s_rec[j][kNrm];
-        if (kStride == kFwdVec4) {
-          if (!warp_hits(rf.y, rf.z, tp.bx0, tp.by0)) continue;
-        } else {
-          if (!warp_hits(rf.z, rf.w, tp.bx0, tp.by0)) continue;
-        }
+      for (int k = 0; k < nh; ++k) {
+        const int j = hl.list[warp][k];
         const float4 r0 = s_rec[j][0], r1 = s_rec[j][1], r2 = s_rec[j][2];
         Eval e;
         const bool hit = eval_pair(r0, r1, r2, tp.lx, tp.ly, cam.near_z, cfg.cutoff_r2,
@@ -186,7 +232,7 @@ __device__ __forceinline__ FwdState fwd_tile(const float4* __restrict__ proj,
           break;
         }
         const float4 r3 = s_rec[j][3];
-        const float tnz = kStride == kFwdVec4 ? s_rec[j][4].x : s_rec[j][4].x;
+        const float tnz = s_rec[j][4].x;
         const float w = e.a * st.T;
         st.C.x = fmaf(w, r2.w, st.C.x);
         st.C.y = fmaf(w, r3.x, st.C.y);
@@ -350,6 +396,73 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ proj,
   }
 }
 
+// Pose-only back-to-front replay (tracking): like bwd_tile but each warp
+// visits only the surfels whose footprint touches its block, and the pair's
+// pose gradient (Gv, X x Gv + t_nc x dL/dt_nc) is accumulated in pr.
+__device__ __forceinline__ void bwd_tile_pose(const float4* __restrict__ proj,
+                                              const uint32_t* __restrict__ vals, int start, int end,
+                                              float xt, float yt, int tile_x0, int tile_y0,
+                                              const TilePix& tp, bool inside, float rx, float ry,
+                                              const gs2d_camera& cam, const gs2d_config& cfg,
+                                              float Tf, uint32_t nl, F3 gC, float gD, F3 gN,
+                                              float gO, BwdSmem<false>& sm, HitLists& hl,
+                                              float (&pr)[6]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float fxfy = cam.fx * cam.fy;
+  if (threadIdx.x == 0) sm.max_nl = 0u;
+  __syncthreads();
+  if (nl) atomicMax(&sm.max_nl, nl);
+  __syncthreads();
+  const int hi = start + (int)sm.max_nl;
+  float T = Tf, acc = 0.f;
+  const float gOT = gO * Tf;
+  for (int bend = hi; bend > start; bend -= kTileThreads) {
+    const int bstart = max(start, bend - kTileThreads);
+    const int cnt = bend - bstart;
+    __syncthreads();
+    if ((int)threadIdx.x < cnt) {
+      stage_record<kBwdVec4>(proj, vals[bstart + (int)threadIdx.x], xt, yt, sm.rec);
+      const float4 rf = sm.rec[threadIdx.x][6];
+      hl.mask[threadIdx.x] = footprint_mask(rf.z, rf.w, tile_x0, tile_y0, cfg.tile_w);
+    }
+    __syncthreads();
+    const int nh = warp_hit_list(hl.mask, hl.list[warp], cnt, warp, lane);
+    if (!inside) continue;
+    for (int k = nh - 1; k >= 0; --k) {
+      const int jj = hl.list[warp][k];
+      if (bstart + jj - start >= (int)nl) continue;
+      const float4 r0 = sm.rec[jj][0], r1 = sm.rec[jj][1], r2 = sm.rec[jj][2];
+      Eval e;
+      if (!eval_pair(r0, r1, r2, tp.lx, tp.ly, cam.near_z, cfg.cutoff_r2, cfg.alpha_min,
+                     cfg.alpha_max, e))
+        continue;
+      const float4 r3 = sm.rec[jj][3], r4 = sm.rec[jj][4], r5 = sm.rec[jj][5], r6 = sm.rec[jj][6];
+      const F3 col = f3(r2.w, r3.x, r3.y);
+      const F3 tn = f3(r3.z, r3.w, r4.x);
+      const F3 nrm = f3(r4.y, r4.z, r4.w);
+      const F3 du = f3(r5.x, r5.y, r5.z), dv = f3(r5.w, r6.x, r6.y);
+      const float iom = __fdividef(1.f, 1.f - e.a);
+      const float Tb = T * iom;
+      const float w = e.a * Tb;
+      const float vj = dot3(col, gC) + e.z * gD + dot3(tn, gN);
+      const float ga = Tb * vj - (acc - gOT) * iom;
+      acc = fmaf(w, vj, acc);
+      T = Tb;
+      const float gG = e.araw <= cfg.alpha_max ? r2.z * ga : 0.f;
+      const float gr2 = -0.5f * e.G * gG;
+      const float gu = 2.f * e.u * gr2, gv = 2.f * e.v * gr2;
+      const float gz = w * gD;
+      const F3 q = gu * du + gv * dv;
+      const float beta = (fmaf(q.x, rx, fmaf(q.y, ry, q.z)) + gz) * fxfy * e.rinv;
+      const F3 Gv = beta * nrm - q;
+      const F3 X = f3(e.z * rx, e.z * ry, e.z);
+      const F3 th = cross3(X, Gv) + cross3(tn, w * gN);
+      pr[0] += Gv.x; pr[1] += Gv.y; pr[2] += Gv.z;
+      pr[3] += th.x; pr[4] += th.y; pr[5] += th.z;
+    }
+  }
+}
+
 // Block sum of a per-thread 6-vector, written by threads 0..5.
 __device__ __forceinline__ void block_sum6(const float (&pr)[6], float (*s_pose)[6],
                                            float* __restrict__ out) {
@@ -377,15 +490,18 @@ __global__ void __launch_bounds__(kTileThreads) render_fwd_kernel(
     float* __restrict__ out_opac, float* __restrict__ out_T, uint32_t* __restrict__ out_nlast,
     unsigned long long* __restrict__ counts, const int32_t* __restrict__ gate) {
   __shared__ float4 s_rec[kTileThreads][kFwdVec4];
+  __shared__ HitLists hl;
   if (gate && *gate) return;
   const int tile = blockIdx.x;
   const TilePix tp = tile_pixel(tile, tiles_x, cfg.tile_w, cfg.tile_h);
   const bool inside = tp.px < cam.width && tp.py < cam.height;
-  const float xt = (float)((tile % tiles_x) * cfg.tile_w) + 0.5f - cam.cx;
-  const float yt = (float)((tile / tiles_x) * cfg.tile_h) + 0.5f - cam.cy;
+  const int tile_x0 = (tile % tiles_x) * cfg.tile_w, tile_y0 = (tile / tiles_x) * cfg.tile_h;
+  const float xt = (float)tile_x0 + 0.5f - cam.cx;
+  const float yt = (float)tile_y0 + 0.5f - cam.cy;
   uint32_t cnt[3] = {0u, 0u, 0u};
   const FwdState st = fwd_tile<kFwdVec4, kCount>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1],
-                                                 xt, yt, tp, inside, cam, cfg, s_rec, cnt);
+                                                 xt, yt, tile_x0, tile_y0, tp, inside, cam, cfg,
+                                                 s_rec, hl, cnt);
   if (kCount) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -421,13 +537,15 @@ __global__ void __launch_bounds__(kTileThreads) render_bwd_kernel(
     const float* __restrict__ g_opac, float* __restrict__ partials, float* __restrict__ pose_part,
     const int32_t* __restrict__ gate) {
   __shared__ BwdSmem<kFull> sm;
+  __shared__ HitLists hl;
   __shared__ float s_pose[kTileThreads / 32][6];
   if (gate && *gate) return;
   const int tile = blockIdx.x;
   const TilePix tp = tile_pixel(tile, tiles_x, cfg.tile_w, cfg.tile_h);
   const bool inside = tp.px < cam.width && tp.py < cam.height;
-  const float xt = (float)((tile % tiles_x) * cfg.tile_w) + 0.5f - cam.cx;
-  const float yt = (float)((tile / tiles_x) * cfg.tile_h) + 0.5f - cam.cy;
+  const int tile_x0 = (tile % tiles_x) * cfg.tile_w, tile_y0 = (tile / tiles_x) * cfg.tile_h;
+  const float xt = (float)tile_x0 + 0.5f - cam.cx;
+  const float yt = (float)tile_y0 + 0.5f - cam.cy;
   const float rx = (tp.px + 0.5f - cam.cx) / cam.fx, ry = (tp.py + 0.5f - cam.cy) / cam.fy;
   float Tf = 1.f;
   uint32_t nl = 0;
@@ -443,9 +561,14 @@ __global__ void __launch_bounds__(kTileThreads) render_bwd_kernel(
     if (g_opac) gO = g_opac[p];
   }
   float pr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  bwd_tile<kFull>(proj, vals, emit, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tp, inside, rx,
-                  ry, cam, cfg, Tf, nl, gC, gD, gN, gO, partials, sm, pr);
-  if (!kFull) block_sum6(pr, s_pose, pose_part + (size_t)tile * 6);
+  if constexpr (kFull) {
+    bwd_tile<true>(proj, vals, emit, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tp, inside, rx,
+                   ry, cam, cfg, Tf, nl, gC, gD, gN, gO, partials, sm, pr);
+  } else {
+    bwd_tile_pose(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0, tile_y0, tp,
+                  inside, rx, ry, cam, cfg, Tf, nl, gC, gD, gN, gO, sm, hl, pr);
+    block_sum6(pr, s_pose, pose_part + (size_t)tile * 6);
+  }
 }
 
 // Fused tracking iteration on one tile: forward compositing, the tracking
@@ -456,20 +579,31 @@ __global__ void __launch_bounds__(kTileThreads) track_tile_kernel(
     const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
     const int32_t* __restrict__ ranges, gs2d_camera cam, gs2d_config cfg, int tiles_x,
     const float* __restrict__ obs_rgb, const float* __restrict__ obs_depth, gs2d_track_params prm,
-    float* __restrict__ loss_part, float* __restrict__ pose_part, const int32_t* __restrict__ gate) {
+    float* __restrict__ loss_part, float* __restrict__ pose_part, TrackStep ts,
+    int32_t* __restrict__ status) {
   __shared__ BwdSmem<false> sm;
+  __shared__ HitLists hl;
   __shared__ float s_pose[kTileThreads / 32][6];
   __shared__ float s_loss[kTileThreads / 32];
-  if (gate && *gate) return;
+  __shared__ bool s_last;
+  {
+    const int32_t g = *status;
+    if (g != 0) {
+      if (g == kConverged && blockIdx.x == 0 && threadIdx.x == 0)
+        record_converged(ts.pose, ts.loss_hist, ts.pose_hist, ts.iter);
+      return;
+    }
+  }
   const int tile = blockIdx.x;
   const TilePix tp = tile_pixel(tile, tiles_x, cfg.tile_w, cfg.tile_h);
   const bool inside = tp.px < cam.width && tp.py < cam.height;
-  const float xt = (float)((tile % tiles_x) * cfg.tile_w) + 0.5f - cam.cx;
-  const float yt = (float)((tile / tiles_x) * cfg.tile_h) + 0.5f - cam.cy;
+  const int tile_x0 = (tile % tiles_x) * cfg.tile_w, tile_y0 = (tile / tiles_x) * cfg.tile_h;
+  const float xt = (float)tile_x0 + 0.5f - cam.cx;
+  const float yt = (float)tile_y0 + 0.5f - cam.cy;
   const float rx = (tp.px + 0.5f - cam.cx) / cam.fx, ry = (tp.py + 0.5f - cam.cy) / cam.fy;
   const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
-  const FwdState st = fwd_tile<kBwdVec4, false>(proj, vals, start, end, xt, yt, tp, inside, cam,
-                                                cfg, sm.rec, nullptr);
+  const FwdState st = fwd_tile<kBwdVec4, false>(proj, vals, start, end, xt, yt, tile_x0, tile_y0,
+                                                tp, inside, cam, cfg, sm.rec, hl, nullptr);
   float pr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const float inv = 1.f / (float)(cam.width * cam.height);
   PixLoss L;
@@ -494,10 +628,21 @@ __global__ void __launch_bounds__(kTileThreads) track_tile_kernel(
       loss_part[tile] = t;
     }
   }
-  bwd_tile<false>(proj, vals, nullptr, start, end, xt, yt, tp, inside, rx, ry, cam, cfg, st.T,
-                  st.last, f3(L.g_rgb[0], L.g_rgb[1], L.g_rgb[2]), L.g_depth, f3(0.f, 0.f, 0.f),
-                  L.g_opac, nullptr, sm, pr);
+  bwd_tile_pose(proj, vals, start, end, xt, yt, tile_x0, tile_y0, tp, inside, rx, ry, cam, cfg,
+                st.T, st.last, f3(L.g_rgb[0], L.g_rgb[1], L.g_rgb[2]), L.g_depth, f3(0.f, 0.f, 0.f),
+                L.g_opac, sm, hl, pr);
   block_sum6(pr, s_pose, pose_part + (size_t)tile * 6);
+  // the last block to finish reduces every tile's partials and updates the pose
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ts.counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  float(*s_red)[256] = reinterpret_cast<float(*)[256]>(&sm.rec[0][0]);  // 7 x 256 floats fit
+  reduce_and_step(pose_part, loss_part, gridDim.x, ts.pose, ts.adam, prm, ts.loss_hist,
+                  ts.pose_hist, ts.iter, status, s_red);
+  if (threadIdx.x == 0) *ts.counter = 0u;
 }
 
 // Per-surfel reduction of the (tile, surfel) partials in emission order and
@@ -664,16 +809,16 @@ int render_fwd_launch(const float* proj, const gs2d_bins* bins, const gs2d_camer
 int track_tile_launch(const float* proj, const gs2d_bins* bins, const gs2d_camera* cam,
                       const gs2d_config* cfg, const float* obs_rgb, const float* obs_depth,
                       const gs2d_track_params* prm, float* loss_part, float* pose_part,
-                      const int32_t* gate, cudaStream_t st) {
+                      const TrackStep& ts, int32_t* status, cudaStream_t st) {
   const int v = validate_tile_cfg(cam, cfg);
   if (v) return v;
   if (!proj || !bins || !bins->vals || !bins->tile_ranges || !obs_rgb || !obs_depth || !prm ||
-      !loss_part || !pose_part)
+      !loss_part || !pose_part || !ts.pose || !ts.adam || !ts.counter || !status)
     return GS2D_ERR_INVALID_ARG;
   const int tx = gs2d_tiles_x(cam, cfg), ty = gs2d_tiles_y(cam, cfg);
   track_tile_kernel<<<tx * ty, kTileThreads, 0, st>>>(
       reinterpret_cast<const float4*>(proj), bins->vals, bins->tile_ranges, *cam, *cfg, tx, obs_rgb,
-      obs_depth, *prm, loss_part, pose_part, gate);
+      obs_depth, *prm, loss_part, pose_part, ts, status);
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
 }

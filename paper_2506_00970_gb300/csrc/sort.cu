@@ -23,6 +23,7 @@
 // rectangle, so each surfel's pairs are contiguous in emission order (the
 // backward pass stores its per-pair partials there).
 #include "gs2d_common.cuh"
+#include "gs2d_internal.h"
 
 namespace gs2d {
 
@@ -31,8 +32,8 @@ constexpr int kScanItems = 16;
 constexpr int kChunk = kScanThreads * kScanItems;  // 4096 surfels per scan block
 constexpr int kWarps = kScanThreads / 32;
 constexpr int kSpinLimit = 1 << 22;
-constexpr int kSortThreads = 256;
-constexpr int kSegSmem = 4096;                     // keys sorted in shared memory (32 KB)
+constexpr int kSortThreads = 128;
+constexpr int kSegSmem = 2048;                     // keys sorted in shared memory (16 KB)
 
 __device__ __forceinline__ unsigned long long ld_vol64(const unsigned long long* p) {
   return *reinterpret_cast<const volatile unsigned long long*>(p);
@@ -89,18 +90,47 @@ __global__ void bin_init_kernel(uint32_t* __restrict__ zero_a, size_t n_a,
   if (blockIdx.x == 0 && threadIdx.x == 0) *n_isect = 0;
 }
 
-// 1. Exclusive scan of k_i over surfel ids with decoupled look-back (64-bit
+// Per-block tile histograms live in shared memory when the tile grid fits.
+constexpr int kSmemTiles = 6144;  // 2 x 24 KB: the scatter's histogram + bases
+
+// 1a. Tile counts: every covered tile's counter is incremented, through a
+// per-block shared-memory histogram (one global atomic per block and tile).
+__global__ void __launch_bounds__(kScanThreads) count_kernel(
+    const float4* __restrict__ proj, const int32_t* __restrict__ tiles, int n, int tiles_x,
+    int n_tiles, uint32_t* __restrict__ tile_count, const int32_t* __restrict__ gate) {
+  extern __shared__ uint32_t s_hist[];
+  if (*gate) return;
+  const bool local = n_tiles <= kSmemTiles;
+  if (local)
+    for (int t = threadIdx.x; t < n_tiles; t += kScanThreads) s_hist[t] = 0u;
+  __syncthreads();
+  const int stride = gridDim.x * kScanThreads;
+  for (int i = blockIdx.x * kScanThreads + threadIdx.x; i < n; i += stride) {
+    const int k = tiles[i];
+    if (k <= 0) continue;
+    const Rect r = load_rect(proj, (uint32_t)i);
+    const int rw = max(r.tx1 - r.tx0 + 1, 1);
+    for (int j = 0; j < k; ++j) {
+      const int t = min((r.ty0 + j / rw) * tiles_x + r.tx0 + j % rw, n_tiles - 1);
+      atomicAdd(local ? s_hist + t : tile_count + t, 1u);
+    }
+  }
+  if (!local) return;
+  __syncthreads();
+  for (int t = threadIdx.x; t < n_tiles; t += kScanThreads)
+    if (s_hist[t]) atomicAdd(tile_count + t, s_hist[t]);
+}
+
+// 1b. Exclusive scan of k_i over surfel ids with decoupled look-back (64-bit
 // chunk words: flag in bits 62-63; a warp examines 32 predecessors at a
-// time; the spin is bounded and records GS2D_ERR_TIMEOUT past the limit).
-// Writes surfel_off[i], the total K (chunk holding the last surfel) and the
-// capacity status, and counts every covered tile.
+// time; the spin is bounded and records GS2D_ERR_TIMEOUT past the limit):
+// the emission offsets surfel_off[i].
 constexpr unsigned long long kF64Agg = 1ull << 62, kF64Inc = 2ull << 62,
                              kV64Mask = (1ull << 62) - 1;
-__global__ void __launch_bounds__(kScanThreads) count_scan_kernel(
-    const float4* __restrict__ proj, const int32_t* __restrict__ tiles, int n, int tiles_x,
-    int n_tiles, uint32_t* __restrict__ surfel_off, uint32_t* __restrict__ tile_count,
+__global__ void __launch_bounds__(kScanThreads) emit_scan_kernel(
+    const int32_t* __restrict__ tiles, int n, uint32_t* __restrict__ surfel_off,
     unsigned long long* __restrict__ chunk_status, uint32_t* __restrict__ ticket,
-    int32_t* __restrict__ n_isect, long long capacity, int32_t* __restrict__ gate) {
+    int32_t* __restrict__ gate) {
   __shared__ uint32_t s_k[kChunk];
   __shared__ uint32_t s_tmp[2 * kWarps + 1];
   __shared__ int s_chunk;
@@ -112,20 +142,7 @@ __global__ void __launch_bounds__(kScanThreads) count_scan_kernel(
   const long long base = (long long)chunk * kChunk;
   if (base >= n) return;
   const int count = (int)min((long long)kChunk, (long long)n - base);
-  // coalesced load of the chunk's counts; tile counters per covered tile
-  for (int i = threadIdx.x; i < count; i += kScanThreads) {
-    const uint32_t id = (uint32_t)(base + i);
-    const int k = max(tiles[id], 0);
-    s_k[i] = (uint32_t)k;
-    if (k > 0) {
-      const Rect r = load_rect(proj, id);
-      const int rw = max(r.tx1 - r.tx0 + 1, 1);
-      for (int j = 0; j < k; ++j) {
-        const int t = min((r.ty0 + j / rw) * tiles_x + r.tx0 + j % rw, n_tiles - 1);
-        atomicAdd(tile_count + t, 1u);
-      }
-    }
-  }
+  for (int i = threadIdx.x; i < count; i += kScanThreads) s_k[i] = (uint32_t)max(tiles[base + i], 0);
   __syncthreads();
   // blocked: thread t owns items t*16 .. t*16+15
   uint32_t sum = 0;
@@ -185,18 +202,16 @@ __global__ void __launch_bounds__(kScanThreads) count_scan_kernel(
     if (i < count) {
       surfel_off[base + i] = (uint32_t)min(off, 0xFFFFFFFFull);
       off += s_k[i];
-      if (base + i == n - 1) {
-        *n_isect = (int32_t)min(off, (unsigned long long)0x7FFFFFFF);
-        if (off > (unsigned long long)capacity) atomicExch(gate, (int32_t)GS2D_ERR_CAPACITY);
-      }
     }
   }
 }
 
-// 2. Tile ranges from the tile counts (one block).
+// 2. Tile ranges from the tile counts (one block), K and the capacity check.
 __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restrict__ tile_count,
                                                         int n_tiles, int32_t* __restrict__ ranges,
-                                                        const int32_t* __restrict__ gate) {
+                                                        int32_t* __restrict__ n_isect,
+                                                        long long capacity,
+                                                        int32_t* __restrict__ gate) {
   __shared__ uint32_t s_w[32];
   __shared__ uint32_t s_carry;
   if (*gate) return;
@@ -234,26 +249,55 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
     if (threadIdx.x == 1023) s_carry = start + c;
     __syncthreads();
   }
+  // K and the capacity check (ranges beyond the capacity are never read)
+  if (threadIdx.x == 0) {
+    const unsigned long long K = s_carry;
+    *n_isect = (int32_t)min(K, (unsigned long long)0x7FFFFFFF);
+    if (K > (unsigned long long)capacity) atomicExch(gate, (int32_t)GS2D_ERR_CAPACITY);
+  }
 }
 
 // 3. Scatter of the (depth bits << 32 | id) keys into the tile segments.
+// A block counts its own pairs per tile in shared memory, claims one run of
+// slots per tile with a single global atomic, and hands the slots out with
+// shared-memory atomics.
 __global__ void __launch_bounds__(256) scatter_kernel(
     const float4* __restrict__ proj, const int32_t* __restrict__ tiles, int n, int tiles_x,
     int n_tiles, const int32_t* __restrict__ ranges, uint32_t* __restrict__ cursor,
     unsigned long long* __restrict__ seg_keys, long long capacity,
     const int32_t* __restrict__ gate) {
+  extern __shared__ uint32_t s_cnt[];  // [n_tiles] counts, then [n_tiles] bases
   if (*gate) return;
+  const bool local = n_tiles <= kSmemTiles;
+  uint32_t* s_base = s_cnt + (local ? n_tiles : 0);
+  if (local)
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) s_cnt[t] = 0u;
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int k = tiles[i];
-  if (k <= 0) return;
-  const Rect r = load_rect(proj, (uint32_t)i);
-  const uint32_t db = __float_as_uint(proj[(size_t)i * (kProjFloats / 4) + 6].z);
-  const unsigned long long key = ((unsigned long long)db << 32) | (uint32_t)i;
-  const int rw = max(r.tx1 - r.tx0 + 1, 1);
+  const int k = i < n ? tiles[i] : 0;
+  Rect r{1, 1, 0, 0};
+  unsigned long long key = 0ull;
+  int rw = 1;
+  if (k > 0) {
+    r = load_rect(proj, (uint32_t)i);
+    rw = max(r.tx1 - r.tx0 + 1, 1);
+    const uint32_t db = __float_as_uint(proj[(size_t)i * (kProjFloats / 4) + 6].z);
+    key = ((unsigned long long)db << 32) | (uint32_t)i;
+  }
+  if (local) {
+    for (int j = 0; j < k; ++j)
+      atomicAdd(s_cnt + min((r.ty0 + j / rw) * tiles_x + r.tx0 + j % rw, n_tiles - 1), 1u);
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+      const uint32_t c = s_cnt[t];
+      s_base[t] = c ? (uint32_t)ranges[2 * t] + atomicAdd(cursor + t, c) : 0u;
+    }
+    __syncthreads();
+  }
   for (int j = 0; j < k; ++j) {
     const int t = min((r.ty0 + j / rw) * tiles_x + r.tx0 + j % rw, n_tiles - 1);
-    const long long pos = (long long)ranges[2 * t] + atomicAdd(cursor + t, 1u);
+    const long long pos = local ? (long long)atomicAdd(s_base + t, 1u)
+                                : (long long)ranges[2 * t] + atomicAdd(cursor + t, 1u);
     if (pos < min((long long)ranges[2 * t + 1], capacity)) seg_keys[pos] = key;
   }
 }
@@ -316,10 +360,12 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(
   for (int i = threadIdx.x; i < len; i += blockDim.x) {
     const unsigned long long key = a[i];
     const uint32_t id = min((uint32_t)(key & 0xFFFFFFFFull), (uint32_t)(n - 1));
-    const Rect r = load_rect(proj, id);
-    const int rw = max(r.tx1 - r.tx0 + 1, 1);
     vals[start + i] = id;
-    emit[start + i] = surfel_off[id] + (uint32_t)((ty - r.ty0) * rw + (tx - r.tx0));
+    if (emit) {
+      const Rect r = load_rect(proj, id);
+      const int rw = max(r.tx1 - r.tx0 + 1, 1);
+      emit[start + i] = surfel_off[id] + (uint32_t)((ty - r.ty0) * rw + (tx - r.tx0));
+    }
     if (keys64) keys64[start + i] = ((unsigned long long)t << 32) | (key >> 32);
   }
 }
@@ -362,6 +408,58 @@ SortWs carve_sort_ws(void* base, int n, size_t cap, int n_tiles) {
   return w;
 }
 
+int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
+                    const gs2d_camera* cam, const gs2d_config* cfg, void* workspace,
+                    size_t ws_bytes, size_t* ws_needed, const gs2d_bins* bins, bool need_emit,
+                    cudaStream_t st) {
+  if (!cam || !cfg || !bins || n < 0) return GS2D_ERR_INVALID_ARG;
+  if (n > 0 && (!proj || !tiles_per_surfel)) return GS2D_ERR_INVALID_ARG;
+  if (!bins->vals || !bins->tile_ranges || !bins->n_isect || !bins->status) return GS2D_ERR_INVALID_ARG;
+  if (need_emit && (!bins->isect_emit || !bins->surfel_off)) return GS2D_ERR_INVALID_ARG;
+  if (bins->capacity >= (size_t)0x7FFFFFFF) return GS2D_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(proj) & 15) return GS2D_ERR_INVALID_ARG;
+  if (cfg->tile_w <= 0 || cfg->tile_h <= 0) return GS2D_ERR_INVALID_ARG;
+  const int tx = gs2d_tiles_x(cam, cfg), ty = gs2d_tiles_y(cam, cfg);
+  if (tx <= 0 || ty <= 0 || (long long)tx * ty > 65535) return GS2D_ERR_INVALID_ARG;
+  const size_t need = gs2d_bin_sort_workspace(n, bins->capacity);
+  if (ws_needed) *ws_needed = need;
+  if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
+  const int n_tiles = tx * ty;
+  const SortWs w = carve_sort_ws(workspace, n, bins->capacity, n_tiles);
+  int32_t* gate = bins->status;
+  const long long cap = (long long)bins->capacity;
+  const float4* p4 = reinterpret_cast<const float4*>(proj);
+  const size_t hist_smem = n_tiles <= kSmemTiles ? (size_t)n_tiles * sizeof(uint32_t) : 0;
+
+  bin_init_kernel<<<32, 256, 0, st>>>(w.zero_begin, w.zero_words, bins->n_isect, gate);
+  GS2D_LAUNCH_CHECK();
+  if (n > 0) {
+    const int blocks = min((n + kScanThreads - 1) / kScanThreads, 152 * 4);
+    count_kernel<<<blocks, kScanThreads, hist_smem, st>>>(p4, tiles_per_surfel, n, tx, n_tiles,
+                                                          w.tile_count, gate);
+    GS2D_LAUNCH_CHECK();
+    if (need_emit) {
+      emit_scan_kernel<<<w.chunks_n, kScanThreads, 0, st>>>(tiles_per_surfel, n, bins->surfel_off,
+                                                            w.estatus, w.ticket, gate);
+      GS2D_LAUNCH_CHECK();
+    }
+  }
+  tile_scan_kernel<<<1, 1024, 0, st>>>(w.tile_count, n_tiles, bins->tile_ranges, bins->n_isect, cap,
+                                       gate);
+  GS2D_LAUNCH_CHECK();
+  if (n == 0) return GS2D_OK;
+  scatter_kernel<<<(n + 255) / 256, 256, 2 * hist_smem, st>>>(
+      p4, tiles_per_surfel, n, tx, n_tiles, bins->tile_ranges, w.cursor, w.seg_keys, cap, gate);
+  GS2D_LAUNCH_CHECK();
+  const size_t smem = (size_t)kSegSmem * sizeof(unsigned long long);
+  tile_sort_kernel<<<n_tiles, kSortThreads, smem, st>>>(
+      p4, n, tx, bins->tile_ranges, w.seg_keys, need_emit ? bins->surfel_off : nullptr,
+      bins->vals, need_emit ? bins->isect_emit : nullptr,
+      reinterpret_cast<unsigned long long*>(bins->keys), cap, gate);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
 }  // namespace gs2d
 
 using namespace gs2d;
@@ -376,47 +474,8 @@ size_t gs2d_bin_sort_workspace(int n, size_t capacity) {
 int gs2d_bin_sort(const float* proj, const int32_t* tiles_per_surfel, int n,
                   const gs2d_camera* cam, const gs2d_config* cfg, void* workspace,
                   size_t ws_bytes, size_t* ws_needed, const gs2d_bins* bins, gs2d_stream stream) {
-  if (!cam || !cfg || !bins || n < 0) return GS2D_ERR_INVALID_ARG;
-  if (n > 0 && (!proj || !tiles_per_surfel)) return GS2D_ERR_INVALID_ARG;
-  if (!bins->vals || !bins->isect_emit || !bins->surfel_off || !bins->tile_ranges ||
-      !bins->n_isect || !bins->status)
-    return GS2D_ERR_INVALID_ARG;
-  if (bins->capacity >= (size_t)0x7FFFFFFF) return GS2D_ERR_INVALID_ARG;
-  if (reinterpret_cast<uintptr_t>(proj) & 15) return GS2D_ERR_INVALID_ARG;
-  if (cfg->tile_w <= 0 || cfg->tile_h <= 0) return GS2D_ERR_INVALID_ARG;
-  const int tx = gs2d_tiles_x(cam, cfg), ty = gs2d_tiles_y(cam, cfg);
-  if (tx <= 0 || ty <= 0 || (long long)tx * ty > 65535) return GS2D_ERR_INVALID_ARG;
-  const size_t need = gs2d_bin_sort_workspace(n, bins->capacity);
-  if (ws_needed) *ws_needed = need;
-  if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
-  cudaStream_t st = (cudaStream_t)stream;
-  const int n_tiles = tx * ty;
-  const SortWs w = carve_sort_ws(workspace, n, bins->capacity, n_tiles);
-  int32_t* gate = bins->status;
-  const long long cap = (long long)bins->capacity;
-  const float4* p4 = reinterpret_cast<const float4*>(proj);
-
-  bin_init_kernel<<<32, 256, 0, st>>>(w.zero_begin, w.zero_words, bins->n_isect, gate);
-  GS2D_LAUNCH_CHECK();
-  if (n > 0) {
-    count_scan_kernel<<<w.chunks_n, kScanThreads, 0, st>>>(
-        p4, tiles_per_surfel, n, tx, n_tiles, bins->surfel_off, w.tile_count, w.estatus, w.ticket,
-        bins->n_isect, cap, gate);
-    GS2D_LAUNCH_CHECK();
-  }
-  tile_scan_kernel<<<1, 1024, 0, st>>>(w.tile_count, n_tiles, bins->tile_ranges, gate);
-  GS2D_LAUNCH_CHECK();
-  if (n == 0) return GS2D_OK;
-  scatter_kernel<<<(n + 255) / 256, 256, 0, st>>>(p4, tiles_per_surfel, n, tx, n_tiles,
-                                                  bins->tile_ranges, w.cursor, w.seg_keys, cap,
-                                                  gate);
-  GS2D_LAUNCH_CHECK();
-  const size_t smem = (size_t)kSegSmem * sizeof(unsigned long long);
-  tile_sort_kernel<<<n_tiles, kSortThreads, smem, st>>>(
-      p4, n, tx, bins->tile_ranges, w.seg_keys, bins->surfel_off, bins->vals, bins->isect_emit,
-      reinterpret_cast<unsigned long long*>(bins->keys), cap, gate);
-  GS2D_LAUNCH_CHECK();
-  return GS2D_OK;
+  return bin_sort_launch(proj, tiles_per_surfel, n, cam, cfg, workspace, ws_bytes, ws_needed, bins,
+                         true, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -147,6 +147,43 @@ def test_track_step_first_gradient_and_convergence(torch_cuda, orc):
     assert lh[-1] < 0.5 * lh[0]
 
 
+def test_track_step_graph_replay_is_bit_identical(torch_cuda, orc):
+    """A tracking frame captured into a CUDA graph and replayed reproduces
+    the direct call exactly (every reduction has a fixed order), twice."""
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d
+    s, cam, gt = _track_setup(orc, n=20_000, seed=2)
+    ds = gs2d.DeviceSurfels(s)
+    r, _, _, img = gpu_render(s, cam, gt)
+    obs_rgb = torch.tensor(img["rgb"], device="cuda")
+    obs_d = torch.tensor(img["depth"] / np.maximum(img["opacity"], 1e-6), device="cuda")
+    start = gs2d.pose_tensor(scenes.perturb_pose(gt, 0.02, 1.0, seed=6))
+    ccam, cfg = gs2d.camera(cam), gs2d.default_config()
+    prm = gs2d.default_track_params(stop_tol=0.0)
+    cap = 8 * s.n
+    ws = torch.empty(gs2d.gs2d_track_workspace(s.n, cap, ccam, cfg), dtype=torch.uint8, device="cuda")
+    pose = torch.empty(12, device="cuda")
+    lh = torch.zeros(30, device="cuda")
+    ph = torch.zeros(30, 12, device="cuda")
+
+    def run():
+        gs2d.gs2d_track_step(ds, ccam, cfg, prm, pose, obs_rgb, obs_d, 30, cap, lh, ph, ws)
+
+    pose.copy_(start)
+    run()
+    torch.cuda.synchronize()
+    direct = (ph.clone(), lh.clone())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        run()
+    for _ in range(2):
+        pose.copy_(start)
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(gs2d.gs2d_track_status(ws).item()) == 0
+        assert torch.equal(ph, direct[0]) and torch.equal(lh, direct[1])
+
+
 def test_track_step_capacity_error_is_reported(torch_cuda):
     torch = torch_cuda
     from paper_2506_00970_gb300 import gs2d
