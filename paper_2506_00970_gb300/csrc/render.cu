@@ -397,8 +397,13 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ proj,
 }
 
 // Pose-only back-to-front replay (tracking): like bwd_tile but each warp
-// visits only the surfels whose footprint touches its block, and the pair's
-// pose gradient (Gv, X x Gv + t_nc x dL/dt_nc) is accumulated in pr.
+// visits only the surfels whose footprint touches its block, and the pose
+// gradient is accumulated per pixel.  With the hit point X = z r and r fixed
+// per pixel, sum_pairs X x Gv = r x sum_pairs z Gv, so a pair only adds Gv
+// and z Gv; with q = s (u d_u + v d_v), s = -G dL/dG, the pair's
+// Gv = beta n - q, beta = (q . r + gz) / (n . r).  kNormal adds the normal
+// image's term t_nc x w gN per pair (tracking has no normal gradient).
+template <bool kNormal>
 __device__ __forceinline__ void bwd_tile_pose(const float4* __restrict__ proj,
                                               const uint32_t* __restrict__ vals, int start, int end,
                                               float xt, float yt, int tile_x0, int tile_y0,
@@ -416,6 +421,7 @@ __device__ __forceinline__ void bwd_tile_pose(const float4* __restrict__ proj,
   const int hi = start + (int)sm.max_nl;
   float T = Tf, acc = 0.f;
   const float gOT = gO * Tf;
+  F3 sG = f3(0.f, 0.f, 0.f), szG = f3(0.f, 0.f, 0.f), sN = f3(0.f, 0.f, 0.f);
   for (int bend = hi; bend > start; bend -= kTileThreads) {
     const int bstart = max(start, bend - kTileThreads);
     const int cnt = bend - bstart;
@@ -437,30 +443,41 @@ __device__ __forceinline__ void bwd_tile_pose(const float4* __restrict__ proj,
                      cfg.alpha_max, e))
         continue;
       const float4 r3 = sm.rec[jj][3], r4 = sm.rec[jj][4], r5 = sm.rec[jj][5], r6 = sm.rec[jj][6];
-      const F3 col = f3(r2.w, r3.x, r3.y);
-      const F3 tn = f3(r3.z, r3.w, r4.x);
-      const F3 nrm = f3(r4.y, r4.z, r4.w);
-      const F3 du = f3(r5.x, r5.y, r5.z), dv = f3(r5.w, r6.x, r6.y);
       const float iom = __fdividef(1.f, 1.f - e.a);
       const float Tb = T * iom;
       const float w = e.a * Tb;
-      const float vj = dot3(col, gC) + e.z * gD + dot3(tn, gN);
+      float vj = fmaf(r2.w, gC.x, fmaf(r3.x, gC.y, fmaf(r3.y, gC.z, e.z * gD)));
+      if (kNormal) vj = fmaf(r3.z, gN.x, fmaf(r3.w, gN.y, fmaf(r4.x, gN.z, vj)));
       const float ga = Tb * vj - (acc - gOT) * iom;
       acc = fmaf(w, vj, acc);
       T = Tb;
-      const float gG = e.araw <= cfg.alpha_max ? r2.z * ga : 0.f;
-      const float gr2 = -0.5f * e.G * gG;
-      const float gu = 2.f * e.u * gr2, gv = 2.f * e.v * gr2;
-      const float gz = w * gD;
-      const F3 q = gu * du + gv * dv;
-      const float beta = (fmaf(q.x, rx, fmaf(q.y, ry, q.z)) + gz) * fxfy * e.rinv;
-      const F3 Gv = beta * nrm - q;
-      const F3 X = f3(e.z * rx, e.z * ry, e.z);
-      const F3 th = cross3(X, Gv) + cross3(tn, w * gN);
-      pr[0] += Gv.x; pr[1] += Gv.y; pr[2] += Gv.z;
-      pr[3] += th.x; pr[4] += th.y; pr[5] += th.z;
+      const float s = e.araw <= cfg.alpha_max ? -e.G * r2.z * ga : 0.f;
+      // P = u d_u + v d_v; q = s P
+      const float Px = fmaf(e.u, r5.x, e.v * r5.w);
+      const float Py = fmaf(e.u, r5.y, e.v * r6.x);
+      const float Pz = fmaf(e.u, r5.z, e.v * r6.y);
+      const float Pr = fmaf(Px, rx, fmaf(Py, ry, Pz));
+      const float beta = fmaf(s, Pr, w * gD) * fxfy * e.rinv;
+      const float Gx = fmaf(beta, r4.y, -s * Px);
+      const float Gy = fmaf(beta, r4.z, -s * Py);
+      const float Gz = fmaf(beta, r4.w, -s * Pz);
+      sG.x += Gx;
+      sG.y += Gy;
+      sG.z += Gz;
+      szG.x = fmaf(e.z, Gx, szG.x);
+      szG.y = fmaf(e.z, Gy, szG.y);
+      szG.z = fmaf(e.z, Gz, szG.z);
+      if (kNormal) sN = sN + w * f3(r3.z, r3.w, r4.x);
     }
   }
+  // theta: r x sum z Gv (+ sum_pairs t_nc x w gN = N x gN over the pairs)
+  const F3 th = cross3(f3(rx, ry, 1.f), szG) + cross3(sN, gN);
+  pr[0] += sG.x;
+  pr[1] += sG.y;
+  pr[2] += sG.z;
+  pr[3] += th.x;
+  pr[4] += th.y;
+  pr[5] += th.z;
 }
 
 // Block sum of a per-thread 6-vector, written by threads 0..5.
@@ -565,8 +582,13 @@ __global__ void __launch_bounds__(kTileThreads) render_bwd_kernel(
     bwd_tile<true>(proj, vals, emit, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tp, inside, rx,
                    ry, cam, cfg, Tf, nl, gC, gD, gN, gO, partials, sm, pr);
   } else {
-    bwd_tile_pose(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0, tile_y0, tp,
-                  inside, rx, ry, cam, cfg, Tf, nl, gC, gD, gN, gO, sm, hl, pr);
+    if (g_normal)
+      bwd_tile_pose<true>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0,
+                          tile_y0, tp, inside, rx, ry, cam, cfg, Tf, nl, gC, gD, gN, gO, sm, hl, pr);
+    else
+      bwd_tile_pose<false>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0,
+                           tile_y0, tp, inside, rx, ry, cam, cfg, Tf, nl, gC, gD, gN, gO, sm, hl,
+                           pr);
     block_sum6(pr, s_pose, pose_part + (size_t)tile * 6);
   }
 }
@@ -628,8 +650,8 @@ __global__ void __launch_bounds__(kTileThreads) track_tile_kernel(
       loss_part[tile] = t;
     }
   }
-  bwd_tile_pose(proj, vals, start, end, xt, yt, tile_x0, tile_y0, tp, inside, rx, ry, cam, cfg,
-                st.T, st.last, f3(L.g_rgb[0], L.g_rgb[1], L.g_rgb[2]), L.g_depth, f3(0.f, 0.f, 0.f),
+  bwd_tile_pose<false>(proj, vals, start, end, xt, yt, tile_x0, tile_y0, tp, inside, rx, ry, cam,
+                       cfg, st.T, st.last, f3(L.g_rgb[0], L.g_rgb[1], L.g_rgb[2]), L.g_depth, f3(0.f, 0.f, 0.f),
                 L.g_opac, sm, hl, pr);
   block_sum6(pr, s_pose, pose_part + (size_t)tile * 6);
   // the last block to finish reduces every tile's partials and updates the pose
