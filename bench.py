@@ -44,7 +44,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes per launch of the roofline kernel from an ncu capture of the
 # same workload (profiles/track_tile_tracking_640x480.md); None if the kernel
 # changed since the capture.
-TRAFFIC_BYTES = {"track_tile": None}
+TRAFFIC_BYTES = {"track_tile": 6317056}
 
 
 def _args():
