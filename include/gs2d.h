@@ -210,6 +210,59 @@ int gs2d_render_bwd(const float* proj, const gs2d_bins* bins, const int32_t* til
                     float* d_opac, float* d_rgb_out, float* d_pose6, void* workspace,
                     size_t ws_bytes, size_t* ws_needed, gs2d_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Batches of views (the mapping window of Sec. III-E renders several
+ * keyframes per iteration, each over the active map M_A of Sec. III-C; the
+ * tracking of several frames is the same pattern).  Every view carries its
+ * camera, tile configuration, pose, optional active-surfel subset and its own
+ * caller-owned buffers; up to GS2D_MAX_VIEWS views per call.  The render
+ * passes are single persistent launches over all (view, tile) work items,
+ * taken from an atomic queue (no waiting), so views of different sizes
+ * share the GPU; the view table travels by value in the kernel parameters,
+ * so the calls can be captured in a CUDA graph.  Results per view equal the
+ * single-view entry points'. */
+#define GS2D_MAX_VIEWS 32
+typedef struct {
+  gs2d_camera cam;
+  gs2d_config cfg;            /* per view: tile shape may differ per resolution */
+  const float* pose;          /* device [12] world->camera                          */
+  const int32_t* active;      /* device [n_active] surfel ids drawn, or NULL = all  */
+  int n_active;
+  float* proj;                /* [m * GS2D_PROJ_FLOATS], m = active ? n_active : n  */
+  int32_t* tiles_per_surfel;  /* [m]                                                */
+  gs2d_bins bins;             /* vals / isect_emit [capacity], surfel_off [m], ...  */
+  float* rgb;                 /* forward outputs: H x W x 3, H x W, H x W x 3,     */
+  float* depth;               /*   H x W, H x W, H x W (as gs2d_render_fwd)        */
+  float* normal;
+  float* opacity;
+  float* t_final;
+  uint32_t* n_last;
+  const float* d_rgb;         /* backward inputs (d_normal, d_opacity may be NULL)  */
+  const float* d_depth;
+  const float* d_normal;
+  const float* d_opacity;
+  float* d_pose6;             /* [6] this view's pose gradient, or NULL             */
+} gs2d_view;
+
+/* Projection of every view (one launch; record j of a view is surfel
+ * active[j], or j).  Binning of every view (gs2d_bin_sort per view, each on
+ * its own slice of the workspace; each view's bins.status must be 0).  The
+ * forward pass of every view in one persistent launch.  The backward pass of
+ * every view in one persistent launch, then the per-surfel reductions view by
+ * view in a fixed order: d_* (device [n*3], [n*4], [n*2], [n], [n*3]) receive
+ * the sum over views (surfels outside every subset get zero). */
+int gs2d_project_batch(const gs2d_surfels* s, const gs2d_view* views, int n_views,
+                       gs2d_stream stream);
+size_t gs2d_bin_sort_batch_workspace(const gs2d_view* views, int n_views, int n);
+int gs2d_bin_sort_batch(const gs2d_view* views, int n_views, int n, void* workspace,
+                        size_t ws_bytes, size_t* ws_needed, gs2d_stream stream);
+size_t gs2d_render_batch_workspace(const gs2d_view* views, int n_views, int n);
+int gs2d_render_fwd_batch(const gs2d_view* views, int n_views, void* workspace, size_t ws_bytes,
+                          size_t* ws_needed, gs2d_stream stream);
+int gs2d_render_bwd_batch(const gs2d_view* views, int n_views, const gs2d_surfels* s, float* d_mu,
+                          float* d_quat, float* d_scale, float* d_opac, float* d_rgb,
+                          void* workspace, size_t ws_bytes, size_t* ws_needed, gs2d_stream stream);
+
 /* Tracking loss L_t (Eq. tracking_loss with the masks of Eq. normal_mask and
  * opacity_mask) of rendered images against an observed RGB-D frame, and its
  * gradient w.r.t. the rendered rgb, depth and opacity (g_* [H*W*3], [H*W],

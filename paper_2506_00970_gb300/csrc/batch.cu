@@ -1,0 +1,318 @@
+// Batched views: one persistent launch per render pass over every
+// (view, tile) work item of up to GS2D_MAX_VIEWS views -- the keyframes of a
+// mapping window (Sec. III-E) or frames of uneven resolution, each over its
+// own active surfel subset (Sec. III-C).  Blocks take items from an atomic
+// counter (no spinning), so large and small views balance across the SMs.
+// The view table is a by-value kernel parameter: a launch is fully described
+// by its arguments and can be captured in a CUDA graph.  The per-tile work is
+// the single-view code of tile_loops.cuh, so every view's images and partial
+// gradients equal those of the single-view entry points.
+#include "gs2d_common.cuh"
+#include "gs2d_internal.h"
+#include "tile_loops.cuh"
+
+namespace gs2d {
+
+struct ViewDev {
+  gs2d_camera cam;
+  gs2d_config cfg;
+  int tiles_x, n_tiles, item0;      // first work item of this view
+  const float4* proj;
+  const uint32_t* vals;
+  const uint32_t* emit;
+  const int32_t* ranges;
+  const int32_t* status;
+  float *rgb, *depth, *normal, *opac, *T;
+  uint32_t* nlast;
+  const float *d_rgb, *d_depth, *d_normal, *d_opac;
+  float* partials;                  // this view's (tile, surfel) partials
+};
+struct ViewTable {
+  int n_views, n_items;
+  ViewDev v[GS2D_MAX_VIEWS];
+};
+
+__device__ __forceinline__ int view_of(const ViewTable& tab, int item) {
+  int v = 0;
+  while (v + 1 < tab.n_views && item >= tab.v[v + 1].item0) ++v;
+  return v;
+}
+
+__global__ void __launch_bounds__(kTileThreads) fwd_batch_kernel(ViewTable tab,
+                                                                 uint32_t* __restrict__ queue) {
+  __shared__ float4 s_rec[kTileThreads][kFwdVec4];
+  __shared__ HitLists hl;
+  __shared__ int s_item;
+  while (true) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= tab.n_items) return;
+    const ViewDev& V = tab.v[view_of(tab, item)];
+    if (V.status && *V.status) continue;
+    const int tile = item - V.item0;
+    const TilePix tp = tile_pixel(tile, V.tiles_x, V.cfg.tile_w, V.cfg.tile_h);
+    const bool inside = tp.px < V.cam.width && tp.py < V.cam.height;
+    const int tile_x0 = (tile % V.tiles_x) * V.cfg.tile_w;
+    const int tile_y0 = (tile / V.tiles_x) * V.cfg.tile_h;
+    const float xt = (float)tile_x0 + 0.5f - V.cam.cx, yt = (float)tile_y0 + 0.5f - V.cam.cy;
+    const FwdState st = fwd_tile<kFwdVec4, false>(V.proj, V.vals, V.ranges[2 * tile],
+                                                  V.ranges[2 * tile + 1], xt, yt, tile_x0, tile_y0,
+                                                  tp, inside, V.cam, V.cfg, s_rec, hl, nullptr);
+    if (inside) {
+      const size_t p = (size_t)tp.py * V.cam.width + tp.px;
+      V.rgb[3 * p] = st.C.x;
+      V.rgb[3 * p + 1] = st.C.y;
+      V.rgb[3 * p + 2] = st.C.z;
+      V.depth[p] = st.D;
+      V.normal[3 * p] = st.N.x;
+      V.normal[3 * p + 1] = st.N.y;
+      V.normal[3 * p + 2] = st.N.z;
+      V.opac[p] = 1.f - st.T;
+      V.T[p] = st.T;
+      V.nlast[p] = st.last;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kTileThreads) bwd_batch_kernel(ViewTable tab,
+                                                                 uint32_t* __restrict__ queue) {
+  __shared__ BwdSmem<true> sm;
+  __shared__ int s_item;
+  while (true) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= tab.n_items) return;
+    const ViewDev& V = tab.v[view_of(tab, item)];
+    if (V.status && *V.status) continue;
+    const int tile = item - V.item0;
+    const TilePix tp = tile_pixel(tile, V.tiles_x, V.cfg.tile_w, V.cfg.tile_h);
+    const bool inside = tp.px < V.cam.width && tp.py < V.cam.height;
+    const float xt = (float)((tile % V.tiles_x) * V.cfg.tile_w) + 0.5f - V.cam.cx;
+    const float yt = (float)((tile / V.tiles_x) * V.cfg.tile_h) + 0.5f - V.cam.cy;
+    const float rx = (tp.px + 0.5f - V.cam.cx) / V.cam.fx, ry = (tp.py + 0.5f - V.cam.cy) / V.cam.fy;
+    float Tf = 1.f;
+    uint32_t nl = 0;
+    F3 gC = f3(0.f, 0.f, 0.f), gN = f3(0.f, 0.f, 0.f);
+    float gD = 0.f, gO = 0.f;
+    if (inside) {
+      const size_t p = (size_t)tp.py * V.cam.width + tp.px;
+      Tf = V.T[p];
+      nl = V.nlast[p];
+      gC = f3(V.d_rgb[3 * p], V.d_rgb[3 * p + 1], V.d_rgb[3 * p + 2]);
+      gD = V.d_depth[p];
+      if (V.d_normal) gN = f3(V.d_normal[3 * p], V.d_normal[3 * p + 1], V.d_normal[3 * p + 2]);
+      if (V.d_opac) gO = V.d_opac[p];
+    }
+    float pr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bwd_tile<true>(V.proj, V.vals, V.emit, V.ranges[2 * tile], V.ranges[2 * tile + 1], xt, yt, tp,
+                   inside, rx, ry, V.cam, V.cfg, Tf, nl, gC, gD, gN, gO, V.partials, sm, pr);
+  }
+}
+
+__global__ void zero_words_kernel(uint32_t* p, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    p[i] = 0u;
+}
+
+namespace {
+
+int view_tiles(const gs2d_view& w, int* tx) {
+  *tx = gs2d_tiles_x(&w.cam, &w.cfg);
+  return *tx * gs2d_tiles_y(&w.cam, &w.cfg);
+}
+
+int check_view(const gs2d_view& w) {
+  if (w.cam.width <= 0 || w.cam.height <= 0) return GS2D_ERR_INVALID_ARG;
+  if (w.cfg.tile_w * w.cfg.tile_h != kTileThreads || w.cfg.tile_w % 8 || w.cfg.tile_h % 4)
+    return GS2D_ERR_INVALID_ARG;
+  int tx;
+  const long long nt = view_tiles(w, &tx);
+  if (nt <= 0 || nt > 65535) return GS2D_ERR_INVALID_ARG;
+  if (!w.proj || !w.bins.vals || !w.bins.tile_ranges || !w.bins.status) return GS2D_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(w.proj) & 15) return GS2D_ERR_INVALID_ARG;
+  return GS2D_OK;
+}
+
+struct BatchWs {
+  uint32_t* queue;        // [2] fwd, bwd work counters
+  float* partials[GS2D_MAX_VIEWS];
+  float* pose_part;       // [max parts * 6]
+  size_t bytes;
+};
+
+BatchWs carve_batch_ws(void* base, const gs2d_view* views, int n_views, int n) {
+  Carver c(base);
+  BatchWs w{};
+  w.queue = c.take<uint32_t>(64);
+  int max_parts = 1;
+  for (int v = 0; v < n_views; ++v) {
+    const size_t cap = views[v].bins.capacity > 0 ? views[v].bins.capacity : 1;
+    w.partials[v] = c.take<float>(cap * 16);
+    const int m = views[v].active ? views[v].n_active : n;
+    max_parts = max(max_parts, (m + 255) / 256);
+  }
+  w.pose_part = c.take<float>((size_t)max_parts * 6);
+  w.bytes = align_up(c.off, 256);
+  return w;
+}
+
+int persistent_grid(const void* kernel) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kTileThreads, 0) != cudaSuccess)
+    return 0;
+  return sms * max(per_sm, 1);
+}
+
+int build_table(const gs2d_view* views, int n_views, const BatchWs* w, ViewTable* tab) {
+  if (!views || n_views <= 0 || n_views > GS2D_MAX_VIEWS) return GS2D_ERR_INVALID_ARG;
+  tab->n_views = n_views;
+  int items = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const gs2d_view& s = views[v];
+    const int r = check_view(s);
+    if (r) return r;
+    ViewDev& d = tab->v[v];
+    d.cam = s.cam;
+    d.cfg = s.cfg;
+    d.n_tiles = view_tiles(s, &d.tiles_x);
+    d.item0 = items;
+    items += d.n_tiles;
+    d.proj = reinterpret_cast<const float4*>(s.proj);
+    d.vals = s.bins.vals;
+    d.emit = s.bins.isect_emit;
+    d.ranges = s.bins.tile_ranges;
+    d.status = s.bins.status;
+    d.rgb = s.rgb;
+    d.depth = s.depth;
+    d.normal = s.normal;
+    d.opac = s.opacity;
+    d.T = s.t_final;
+    d.nlast = s.n_last;
+    d.d_rgb = s.d_rgb;
+    d.d_depth = s.d_depth;
+    d.d_normal = s.d_normal;
+    d.d_opac = s.d_opacity;
+    d.partials = w ? w->partials[v] : nullptr;
+  }
+  tab->n_items = items;
+  return GS2D_OK;
+}
+
+}  // namespace
+}  // namespace gs2d
+
+using namespace gs2d;
+
+extern "C" {
+
+size_t gs2d_bin_sort_batch_workspace(const gs2d_view* views, int n_views, int n) {
+  if (!views || n_views <= 0 || n_views > GS2D_MAX_VIEWS) return 0;
+  size_t total = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const int m = views[v].active ? views[v].n_active : n;
+    total += align_up(gs2d_bin_sort_workspace(m, views[v].bins.capacity), 256);
+  }
+  return total;
+}
+
+int gs2d_bin_sort_batch(const gs2d_view* views, int n_views, int n, void* workspace,
+                        size_t ws_bytes, size_t* ws_needed, gs2d_stream stream) {
+  if (!views || n_views <= 0 || n_views > GS2D_MAX_VIEWS || n < 0) return GS2D_ERR_INVALID_ARG;
+  const size_t need = gs2d_bin_sort_batch_workspace(views, n_views, n);
+  if (ws_needed) *ws_needed = need;
+  if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
+  char* base = static_cast<char*>(workspace);
+  for (int v = 0; v < n_views; ++v) {
+    const gs2d_view& w = views[v];
+    const int m = w.active ? w.n_active : n;
+    const size_t bytes = align_up(gs2d_bin_sort_workspace(m, w.bins.capacity), 256);
+    const int r = gs2d_bin_sort(w.proj, w.tiles_per_surfel, m, &w.cam, &w.cfg, base, bytes, nullptr,
+                                &w.bins, stream);
+    if (r) return r;
+    base += bytes;
+  }
+  return GS2D_OK;
+}
+
+size_t gs2d_render_batch_workspace(const gs2d_view* views, int n_views, int n) {
+  if (!views || n_views <= 0 || n_views > GS2D_MAX_VIEWS) return 0;
+  return carve_batch_ws(nullptr, views, n_views, n).bytes;
+}
+
+int gs2d_render_fwd_batch(const gs2d_view* views, int n_views, void* workspace, size_t ws_bytes,
+                          size_t* ws_needed, gs2d_stream stream) {
+  ViewTable tab;
+  int r = build_table(views, n_views, nullptr, &tab);
+  if (r) return r;
+  for (int v = 0; v < n_views; ++v)
+    if (!views[v].rgb || !views[v].depth || !views[v].normal || !views[v].opacity ||
+        !views[v].t_final || !views[v].n_last)
+      return GS2D_ERR_INVALID_ARG;
+  const size_t need = gs2d_render_batch_workspace(views, n_views, 0);
+  if (ws_needed) *ws_needed = need;
+  if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const BatchWs w = carve_batch_ws(workspace, views, n_views, 0);
+  zero_words_kernel<<<1, 64, 0, st>>>(w.queue, 2);
+  GS2D_LAUNCH_CHECK();
+  const int grid = min(persistent_grid(reinterpret_cast<const void*>(fwd_batch_kernel)), tab.n_items);
+  if (grid <= 0) return GS2D_ERR_CUDA;
+  fwd_batch_kernel<<<grid, kTileThreads, 0, st>>>(tab, w.queue);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+int gs2d_render_bwd_batch(const gs2d_view* views, int n_views, const gs2d_surfels* s, float* d_mu,
+                          float* d_quat, float* d_scale, float* d_opac, float* d_rgb,
+                          void* workspace, size_t ws_bytes, size_t* ws_needed, gs2d_stream stream) {
+  if (!s || !s->mu || !s->quat || !s->scale || s->n <= 0) return GS2D_ERR_INVALID_ARG;
+  if (!d_mu || !d_quat || !d_scale || !d_opac || !d_rgb) return GS2D_ERR_INVALID_ARG;
+  const size_t need = gs2d_render_batch_workspace(views, n_views, s->n);
+  if (ws_needed) *ws_needed = need;
+  if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
+  const BatchWs w = carve_batch_ws(workspace, views, n_views, s->n);
+  ViewTable tab;
+  int r = build_table(views, n_views, &w, &tab);
+  if (r) return r;
+  for (int v = 0; v < n_views; ++v) {
+    const gs2d_view& x = views[v];
+    if (!x.t_final || !x.n_last || !x.d_rgb || !x.d_depth || !x.bins.isect_emit ||
+        !x.bins.surfel_off || !x.tiles_per_surfel || !x.pose)
+      return GS2D_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  zero_words_kernel<<<1, 64, 0, st>>>(w.queue, 2);
+  GS2D_LAUNCH_CHECK();
+  const int grid = min(persistent_grid(reinterpret_cast<const void*>(bwd_batch_kernel)), tab.n_items);
+  if (grid <= 0) return GS2D_ERR_CUDA;
+  bwd_batch_kernel<<<grid, kTileThreads, 0, st>>>(tab, w.queue + 1);
+  GS2D_LAUNCH_CHECK();
+  // surfels outside every view's subset receive zero: clear, then add view by view
+  GS2D_CUDA_TRY(cudaMemsetAsync(d_mu, 0, sizeof(float) * 3 * s->n, st));
+  GS2D_CUDA_TRY(cudaMemsetAsync(d_quat, 0, sizeof(float) * 4 * s->n, st));
+  GS2D_CUDA_TRY(cudaMemsetAsync(d_scale, 0, sizeof(float) * 2 * s->n, st));
+  GS2D_CUDA_TRY(cudaMemsetAsync(d_opac, 0, sizeof(float) * s->n, st));
+  GS2D_CUDA_TRY(cudaMemsetAsync(d_rgb, 0, sizeof(float) * 3 * s->n, st));
+  for (int v = 0; v < n_views; ++v) {
+    const gs2d_view& x = views[v];
+    const int m = x.active ? x.n_active : s->n;
+    r = surfel_grad_launch(s, x.active, m, 1, x.pose, x.tiles_per_surfel, x.bins.surfel_off,
+                           w.partials[v], d_mu, d_quat, d_scale, d_opac, d_rgb, w.pose_part,
+                           x.bins.status, st);
+    if (r) return r;
+    if (x.d_pose6) {
+      r = pose_reduce_launch(w.pose_part, (m + 255) / 256, x.d_pose6, x.bins.status, st);
+      if (r) return r;
+    }
+  }
+  return GS2D_OK;
+}
+
+}  // extern "C"

@@ -60,4 +60,15 @@ int tracking_loss_launch(const float* rgb, const float* depth, const float* norm
                          float* g_depth, float* g_opacity, float* loss_out, void* workspace,
                          size_t ws_bytes, size_t* ws_needed, const int32_t* gate, cudaStream_t st);
 
+// Per-surfel reduction of one view's (tile, surfel) partials (record i is
+// surfel active[i] or i; accumulate adds into the outputs) and the block
+// partials of that view's pose gradient; fixed-order pose reduction.
+int surfel_grad_launch(const gs2d_surfels* s, const int32_t* active, int m, int accumulate,
+                       const float* pose, const int32_t* tiles, const uint32_t* surfel_off,
+                       const float* partials, float* d_mu, float* d_quat, float* d_scale,
+                       float* d_opac, float* d_rgb, float* pose_part, const int32_t* gate,
+                       cudaStream_t st);
+int pose_reduce_launch(const float* part, int n_part, float* out, const int32_t* gate,
+                       cudaStream_t st);
+
 }  // namespace gs2d

@@ -116,7 +116,7 @@ __device__ __forceinline__ void project_one(int i, const float* __restrict__ mu,
                                             const float* __restrict__ opacity,
                                             const float* __restrict__ rgb, const float* sp,
                                             const gs2d_camera& cam, const gs2d_config& cfg,
-                                            float4* o, int32_t* __restrict__ tiles_out) {
+                                            float4* o, int32_t* __restrict__ k_out) {
   const float* Rcw = sp;
 
   // quaternion -> rotation columns t_u, t_v, t_n
@@ -178,7 +178,7 @@ __device__ __forceinline__ void project_one(int i, const float* __restrict__ mu,
     }
   }
   const int k = (tx0 <= tx1 && ty0 <= ty1) ? (tx1 - tx0 + 1) * (ty1 - ty0 + 1) : 0;
-  tiles_out[i] = k;
+  *k_out = k;
 
   const float rgb0 = rgb[3 * i], rgb1 = rgb[3 * i + 1], rgb2 = rgb[3 * i + 2];
   const uint32_t r01 = (uint32_t)tx0 | ((uint32_t)ty0 << 16);
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256) project_kernel(
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) project_one(i, mu, quat, scale, opacity, rgb, sp, cam, cfg, s_out + threadIdx.x * 9,
-                         tiles_out);
+                         tiles_out + i);
   __syncthreads();
   const int base = blockIdx.x * blockDim.x;
   const int valid = min((int)blockDim.x, n - base);
@@ -219,6 +219,43 @@ __global__ void __launch_bounds__(256) project_kernel(
   for (int v = threadIdx.x; v < valid * 8; v += blockDim.x) dst[v] = s_out[(v >> 3) * 9 + (v & 7)];
 }
 
+// All views of a batch in one launch (blockIdx.y = view): record j of a view
+// is surfel active[j] (or j), written to that view's record array.
+struct ProjView {
+  const float* pose;
+  const int32_t* active;
+  int m;
+  float4* proj;
+  int32_t* tiles;
+  const int32_t* status;
+  gs2d_camera cam;
+  gs2d_config cfg;
+};
+struct ProjTable {
+  ProjView v[GS2D_MAX_VIEWS];
+};
+
+__global__ void __launch_bounds__(256) project_batch_kernel(
+    const float* __restrict__ mu, const float* __restrict__ quat, const float* __restrict__ scale,
+    const float* __restrict__ opacity, const float* __restrict__ rgb, int n, ProjTable tab) {
+  __shared__ float4 s_out[256 * 9];
+  __shared__ float sp[12];
+  const ProjView& pv = tab.v[blockIdx.y];
+  const int base = blockIdx.x * blockDim.x;
+  if (base >= pv.m || (pv.status && *pv.status)) return;
+  if (threadIdx.x < 12) sp[threadIdx.x] = pv.pose[threadIdx.x];
+  __syncthreads();
+  const int j = base + threadIdx.x;
+  if (j < pv.m) {
+    const int sid = pv.active ? min(max(pv.active[j], 0), n - 1) : j;
+    project_one(sid, mu, quat, scale, opacity, rgb, sp, pv.cam, pv.cfg, s_out + threadIdx.x * 9,
+                pv.tiles + j);
+  }
+  __syncthreads();
+  const int valid = min((int)blockDim.x, pv.m - base);
+  float4* dst = pv.proj + (size_t)base * (kProjFloats / 4);
+  for (int v = threadIdx.x; v < valid * 8; v += blockDim.x) dst[v] = s_out[(v >> 3) * 9 + (v & 7)];
+}
 
 int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* pose,
                    const gs2d_config* cfg, float* proj_out, int32_t* tiles_per_surfel_out,
@@ -300,6 +337,34 @@ int gs2d_project(const gs2d_surfels* s, const gs2d_camera* cam, const float* pos
                  gs2d_stream stream) {
   return project_launch(s, cam, pose, cfg, proj_out, tiles_per_surfel_out, nullptr,
                         (cudaStream_t)stream);
+}
+
+int gs2d_project_batch(const gs2d_surfels* s, const gs2d_view* views, int n_views,
+                       gs2d_stream stream) {
+  if (!s || !views || n_views <= 0 || n_views > GS2D_MAX_VIEWS) return GS2D_ERR_INVALID_ARG;
+  if (s->n <= 0 || !s->mu || !s->quat || !s->scale || !s->opacity || !s->rgb)
+    return GS2D_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(s->quat) & 15) return GS2D_ERR_INVALID_ARG;
+  ProjTable tab;
+  int max_m = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const gs2d_view& w = views[v];
+    if (!w.pose || !w.proj || !w.tiles_per_surfel || (reinterpret_cast<uintptr_t>(w.proj) & 15))
+      return GS2D_ERR_INVALID_ARG;
+    if (w.cam.width <= 0 || w.cam.height <= 0 || w.cfg.tile_w <= 0 || w.cfg.tile_h <= 0)
+      return GS2D_ERR_INVALID_ARG;
+    const int m = w.active ? w.n_active : s->n;
+    if (m < 0 || (w.active && m > s->n)) return GS2D_ERR_INVALID_ARG;
+    tab.v[v] = ProjView{w.pose, w.active, m, reinterpret_cast<float4*>(w.proj), w.tiles_per_surfel,
+                        w.bins.status, w.cam, w.cfg};
+    max_m = max(max_m, m);
+  }
+  if (max_m == 0) return GS2D_OK;
+  const dim3 grid((max_m + 255) / 256, n_views);
+  project_batch_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(s->mu, s->quat, s->scale,
+                                                               s->opacity, s->rgb, s->n, tab);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
 }
 
 }  // extern "C"

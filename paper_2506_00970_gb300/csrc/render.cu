@@ -41,463 +41,10 @@
 #include "gs2d_common.cuh"
 #include "gs2d_internal.h"
 #include "loss_pixel.cuh"
+#include "tile_loops.cuh"
 #include "track_update.cuh"
 
 namespace gs2d {
-
-constexpr int kTileThreads = 256;
-constexpr int kRedVals = 16;
-
-// Thread -> pixel map of a tile: each warp owns an 8 x 4 block of pixels, so
-// a warp can skip a surfel whose footprint misses its block.
-struct TilePix {
-  int px, py;      // pixel
-  int bx0, by0;    // first pixel of the warp's 8 x 4 block
-  float lx, ly;    // pixel centre relative to the tile's first pixel centre
-};
-__device__ __forceinline__ TilePix tile_pixel(int tile, int tiles_x, int tile_w, int tile_h) {
-  TilePix t;
-  const int tx = tile % tiles_x, ty = tile / tiles_x;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wpr = tile_w >> 3;
-  const int ox = (w % wpr) * 8, oy = (w / wpr) * 4;
-  t.bx0 = tx * tile_w + ox;
-  t.by0 = ty * tile_h + oy;
-  t.px = t.bx0 + (lane & 7);
-  t.py = t.by0 + (lane >> 3);
-  t.lx = (float)(ox + (lane & 7));
-  t.ly = (float)(oy + (lane >> 3));
-  (void)tile_h;
-  return t;
-}
-
-// Stages one projected record for a tile: p is re-based on the tile's first
-// pixel centre (xt, yt) (principal-point relative): c0t = p(xt, yt).  Every
-// pass stages through this function, so they evaluate identical numbers.
-__device__ __forceinline__ float4 stage_c0(const float4 r0, const float4 r1, const float4 r2,
-                                           float xt, float yt) {
-  // r0 = (x0, y0, p2c, c1x), r1 = (c1y, c1z, c2x, c2y), r2 = (c2z, det, alpha, rgb0)
-  const float dx = xt - r0.x, dy = yt - r0.y;
-  return make_float4(fmaf(dy, r1.z, dx * r0.w), fmaf(dy, r1.w, dx * r1.x),
-                     fmaf(dy, r2.x, fmaf(dx, r1.y, r0.z)), r0.w);
-}
-
-// Does the footprint (packed pixel ranges) touch the warp's 8 x 4 block?
-__device__ __forceinline__ bool warp_hits(float bi, float bj, int bx0, int by0) {
-  const uint32_t I = __float_as_uint(bi), J = __float_as_uint(bj);
-  const int i0 = I & 0xFFFF, i1 = I >> 16, j0 = J & 0xFFFF, j1 = J >> 16;
-  return !(i1 < bx0 || i0 > bx0 + 7 || j1 < by0 || j0 > by0 + 3);
-}
-
-// Mask of the tile's 8 warp blocks (8 x 4 pixels each) that a footprint
-// (packed pixel ranges) touches; bit w for warp w.
-__device__ __forceinline__ uint32_t footprint_mask(float bi, float bj, int tile_x0, int tile_y0,
-                                                   int tile_w) {
-  const uint32_t I = __float_as_uint(bi), J = __float_as_uint(bj);
-  const int i0 = (int)(I & 0xFFFF) - tile_x0, i1 = (int)(I >> 16) - tile_x0;
-  const int j0 = (int)(J & 0xFFFF) - tile_y0, j1 = (int)(J >> 16) - tile_y0;
-  const int wpr = tile_w >> 3;
-  uint32_t m = 0u;
-#pragma unroll
-  for (int w = 0; w < kTileThreads / 32; ++w) {
-    const int ox = (w % wpr) * 8, oy = (w / wpr) * 4;
-    if (!(i1 < ox || i0 > ox + 7 || j1 < oy || j0 > oy + 3)) m |= 1u << w;
-  }
-  return m;
-}
-
-// Per-warp compaction of a staged batch: the indices (in staging order) of
-// the surfels whose footprint touches this warp's block.  Returns the count.
-__device__ __forceinline__ int warp_hit_list(const uint32_t* s_mask, uint8_t* my_list, int cnt,
-                                             int warp, int lane) {
-  int n = 0;
-#pragma unroll
-  for (int c = 0; c < kTileThreads; c += 32) {
-    const int j = c + lane;
-    const bool hit = j < cnt && ((s_mask[j] >> warp) & 1u);
-    const uint32_t b = __ballot_sync(0xffffffffu, hit);
-    if (hit) my_list[n + __popc(b & ((1u << lane) - 1u))] = (uint8_t)j;
-    n += __popc(b);
-  }
-  __syncwarp();
-  return n;
-}
-
-// Evaluation of one (pixel, surfel) pair shared by every pass, so all take
-// bit-identical skip decisions.  Returns false if skipped.
-struct Eval {
-  float rinv, u, v, z, G, araw, a;
-};
-__device__ __forceinline__ bool eval_pair(const float4 r0, const float4 r1, const float4 r2, float lx,
-                                          float ly, float near_z, float cutoff_r2, float alpha_min,
-                                          float alpha_max, Eval& e) {
-  // r0 = c0t.xyz c1.x, r1 = c1.yz c2.xy, r2 = c2.z det alpha rgb0
-  const float p0 = fmaf(ly, r1.z, fmaf(lx, r0.w, r0.x));
-  const float p1 = fmaf(ly, r1.w, fmaf(lx, r1.x, r0.y));
-  const float p2 = fmaf(ly, r2.x, fmaf(lx, r1.y, r0.z));
-  e.rinv = __fdividef(1.0f, p2);
-  e.u = __fmul_rn(p0, e.rinv);
-  e.v = __fmul_rn(p1, e.rinv);
-  const float rr = fmaf(e.u, e.u, __fmul_rn(e.v, e.v));
-  if (!(rr <= cutoff_r2)) return false;
-  e.z = __fmul_rn(r2.y, e.rinv);
-  if (!(e.z > near_z)) return false;
-  e.G = __expf(-0.5f * rr);
-  e.araw = __fmul_rn(r2.z, e.G);
-  e.a = fminf(e.araw, alpha_max);
-  return e.a >= alpha_min;
-}
-
-// Stages the records of list positions [b, b + 256) into s_rec: the forward
-// layout (5 float4) or the backward layout (7 float4); slot 4.y/z (forward)
-// or 6.z/w (backward) carries the packed pixel footprint.
-template <int kStride>
-__device__ __forceinline__ void stage_record(const float4* __restrict__ proj, uint32_t id, float xt,
-                                             float yt, float4 (*s_rec)[kStride]) {
-  const float4* src = proj + (size_t)id * (kProjFloats / 4);
-  const float4 r0 = src[0], r1 = src[1], r2 = src[2], r7 = src[7];
-  s_rec[threadIdx.x][0] = stage_c0(r0, r1, r2, xt, yt);
-  s_rec[threadIdx.x][1] = r1;
-  s_rec[threadIdx.x][2] = r2;
-  s_rec[threadIdx.x][3] = src[3];
-  if (kStride == kFwdVec4) {
-    s_rec[threadIdx.x][4] = make_float4(src[4].x, r7.z, r7.w, 0.f);
-  } else {
-    const float4 r6 = src[6];
-    s_rec[threadIdx.x][4] = src[4];
-    s_rec[threadIdx.x][5] = src[5];
-    s_rec[threadIdx.x][6] = make_float4(r6.x, r6.y, r7.z, r7.w);
-  }
-}
-
-struct FwdState {
-  float T, D;
-  F3 C, N;
-  uint32_t last;
-};
-
-// Front-to-back compositing of one pixel over its tile's list.  Each warp
-// visits only the staged surfels whose footprint touches its block.  With
-// kCount it counts evaluated pairs, pairs inside the cutoff and blended pairs.
-struct HitLists {
-  uint32_t mask[kTileThreads];
-  uint8_t list[kTileThreads / 32][kTileThreads];
-};
-
-template <int kStride, bool kCount>
-__device__ __forceinline__ FwdState fwd_tile(const float4* __restrict__ proj,
-                                             const uint32_t* __restrict__ vals, int start, int end,
-                                             float xt, float yt, int tile_x0, int tile_y0,
-                                             const TilePix& tp, bool inside,
-                                             const gs2d_camera& cam, const gs2d_config& cfg,
-                                             float4 (*s_rec)[kStride], HitLists& hl,
-                                             uint32_t* cnt) {
-  FwdState st;
-  st.T = 1.f;
-  st.D = 0.f;
-  st.C = f3(0.f, 0.f, 0.f);
-  st.N = f3(0.f, 0.f, 0.f);
-  st.last = 0;
-  bool done = !inside;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int kFp = kStride == kFwdVec4 ? 4 : 6;  // slot holding the footprint
-  for (int b = start; b < end; b += kTileThreads) {
-    if (__syncthreads_count(!done) == 0) break;
-    const int idx = b + (int)threadIdx.x;
-    if (idx < end) {
-      stage_record<kStride>(proj, vals[idx], xt, yt, s_rec);
-      const float4 rf = s_rec[threadIdx.x][kFp];
-      hl.mask[threadIdx.x] = kStride == kFwdVec4
-                                 ? footprint_mask(rf.y, rf.z, tile_x0, tile_y0, cfg.tile_w)
-                                 : footprint_mask(rf.z, rf.w, tile_x0, tile_y0, cfg.tile_w);
-    }
-    __syncthreads();
-    const int cnt_b = min(kTileThreads, end - b);
-    const int nh = warp_hit_list(hl.mask, hl.list[warp], cnt_b, warp, lane);
-    if (!done) {
-      for (int k = 0; k < nh; ++k) {
-        const int j = hl.list[warp][k];
-        const float4 r0 = s_rec[j][0], r1 = s_rec[j][1], r2 = s_rec[j][2];
-        Eval e;
-        const bool hit = eval_pair(r0, r1, r2, tp.lx, tp.ly, cam.near_z, cfg.cutoff_r2,
-                                   cfg.alpha_min, cfg.alpha_max, e);
-        if (kCount) {
-          ++cnt[0];
-          if (fmaf(e.u, e.u, __fmul_rn(e.v, e.v)) <= cfg.cutoff_r2) ++cnt[1];
-        }
-        if (!hit) continue;
-        const float Tn = st.T * (1.f - e.a);
-        if (Tn < cfg.t_min) {
-          done = true;
-          break;
-        }
-        const float4 r3 = s_rec[j][3];
-        const float tnz = s_rec[j][4].x;
-        const float w = e.a * st.T;
-        st.C.x = fmaf(w, r2.w, st.C.x);
-        st.C.y = fmaf(w, r3.x, st.C.y);
-        st.C.z = fmaf(w, r3.y, st.C.z);
-        st.D = fmaf(w, e.z, st.D);
-        st.N.x = fmaf(w, r3.z, st.N.x);
-        st.N.y = fmaf(w, r3.w, st.N.y);
-        st.N.z = fmaf(w, tnz, st.N.z);
-        st.T = Tn;
-        st.last = (uint32_t)(b + j + 1 - start);
-        if (kCount) ++cnt[2];
-      }
-    }
-  }
-  return st;
-}
-
-// Butterfly reduce-scatter of 16 values over a warp: afterwards lane l holds
-// the warp sum of value (l >> 1) in v[0].
-__device__ __forceinline__ void warp_reduce_scatter16(float (&v)[kRedVals], int lane) {
-#pragma unroll
-  for (int lvl = 0; lvl < 4; ++lvl) {
-    const int off = 16 >> lvl;
-    const int half = 8 >> lvl;
-    const bool up = (lane & off) != 0;
-#pragma unroll
-    for (int i = 0; i < half; ++i) {
-      const float send = up ? v[i] : v[i + half];
-      const float keep = up ? v[i + half] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-    }
-  }
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-}
-
-// Shared-memory scratch of the backward loop.
-template <bool kFull>
-struct BwdSmem {
-  float4 rec[kTileThreads][kBwdVec4];
-  uint32_t emit[kFull ? kTileThreads : 1];
-  float red[kFull ? 8 : 1][kFull ? 32 : 1][kRedVals];
-  uint32_t max_nl;
-};
-
-// Back-to-front replay of one pixel (Tf, nl, upstream gradients) over its
-// tile's list.  Full mode writes the per-(tile, surfel) partials; tracking
-// mode accumulates the pose 6-vector in pr.
-template <bool kFull>
-__device__ __forceinline__ void bwd_tile(const float4* __restrict__ proj,
-                                         const uint32_t* __restrict__ vals,
-                                         const uint32_t* __restrict__ emit, int start, int end,
-                                         float xt, float yt, const TilePix& tp, bool inside,
-                                         float rx, float ry, const gs2d_camera& cam,
-                                         const gs2d_config& cfg, float Tf, uint32_t nl, F3 gC,
-                                         float gD, F3 gN, float gO, float* __restrict__ partials,
-                                         BwdSmem<kFull>& sm, float (&pr)[6]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float fxfy = cam.fx * cam.fy;
-  if (threadIdx.x == 0) sm.max_nl = 0u;
-  __syncthreads();
-  if (nl) atomicMax(&sm.max_nl, nl);
-  __syncthreads();
-  const int hi = start + (int)sm.max_nl;
-  float T = Tf, acc = 0.f;
-  const float gOT = gO * Tf;
-  for (int bend = hi; bend > start; bend -= kTileThreads) {
-    const int bstart = max(start, bend - kTileThreads);
-    const int cnt = bend - bstart;
-    __syncthreads();
-    if ((int)threadIdx.x < cnt) {
-      const int idx = bstart + (int)threadIdx.x;
-      stage_record<kBwdVec4>(proj, vals[idx], xt, yt, sm.rec);
-      if (kFull) sm.emit[threadIdx.x] = emit[idx];
-    }
-    __syncthreads();
-    for (int jj = cnt - 1; jj >= 0; --jj) {
-      const int jrel = bstart + jj - start;
-      float val[kRedVals];
-      bool contrib = false;
-      const float4 r6 = sm.rec[jj][6];
-      if (inside && jrel < (int)nl && warp_hits(r6.z, r6.w, tp.bx0, tp.by0)) {
-        const float4 r0 = sm.rec[jj][0], r1 = sm.rec[jj][1], r2 = sm.rec[jj][2];
-        Eval e;
-        if (eval_pair(r0, r1, r2, tp.lx, tp.ly, cam.near_z, cfg.cutoff_r2, cfg.alpha_min,
-                      cfg.alpha_max, e)) {
-          contrib = true;
-          const float4 r3 = sm.rec[jj][3], r4 = sm.rec[jj][4], r5 = sm.rec[jj][5];
-          const F3 col = f3(r2.w, r3.x, r3.y);
-          const F3 tn = f3(r3.z, r3.w, r4.x);
-          const F3 nrm = f3(r4.y, r4.z, r4.w);
-          const F3 du = f3(r5.x, r5.y, r5.z), dv = f3(r5.w, r6.x, r6.y);
-          const float om = 1.f - e.a;
-          const float iom = __fdividef(1.f, om);
-          const float Tb = T * iom;
-          const float w = e.a * Tb;
-          const float vj = dot3(col, gC) + e.z * gD + dot3(tn, gN);
-          const float ga = Tb * vj - (acc - gOT) * iom;
-          acc = fmaf(w, vj, acc);
-          T = Tb;
-          float galpha = 0.f, gG = 0.f;
-          if (e.araw <= cfg.alpha_max) {
-            galpha = e.G * ga;
-            gG = r2.z * ga;
-          }
-          const float gr2 = -0.5f * e.G * gG;
-          const float gu = 2.f * e.u * gr2, gv = 2.f * e.v * gr2;
-          const float gz = w * gD;
-          const F3 q = gu * du + gv * dv;
-          const float beta = (fmaf(q.x, rx, fmaf(q.y, ry, q.z)) + gz) * fxfy * e.rinv;
-          const F3 Gv = beta * nrm - q;
-          if (kFull) {
-            val[0] = Gv.x; val[1] = Gv.y; val[2] = Gv.z;
-            val[3] = e.u * Gv.x; val[4] = e.u * Gv.y; val[5] = e.u * Gv.z;
-            val[6] = e.v * Gv.x; val[7] = e.v * Gv.y; val[8] = e.v * Gv.z;
-            val[9] = galpha;
-            val[10] = w * gC.x; val[11] = w * gC.y; val[12] = w * gC.z;
-            val[13] = w * gN.x; val[14] = w * gN.y; val[15] = w * gN.z;
-          } else {
-            const F3 X = f3(e.z * rx, e.z * ry, e.z);
-            const F3 gtn = w * gN;
-            const F3 th = cross3(X, Gv) + cross3(tn, gtn);
-            pr[0] += Gv.x; pr[1] += Gv.y; pr[2] += Gv.z;
-            pr[3] += th.x; pr[4] += th.y; pr[5] += th.z;
-          }
-        }
-      }
-      if (kFull) {
-        const int slot = jj & 31;
-        if (__any_sync(0xffffffffu, contrib)) {
-          if (!contrib) {
-#pragma unroll
-            for (int i = 0; i < kRedVals; ++i) val[i] = 0.f;
-          }
-          warp_reduce_scatter16(val, lane);
-          if ((lane & 1) == 0) sm.red[warp][slot][lane >> 1] = val[0];
-        } else if (lane < kRedVals) {
-          sm.red[warp][slot][lane] = 0.f;
-        }
-        if (slot == 0) {
-          __syncthreads();
-          const int gs = min(32, cnt - jj);
-          for (int o = threadIdx.x; o < gs * kRedVals; o += kTileThreads) {
-            const int s = o / kRedVals, c = o % kRedVals;
-            float sum = 0.f;
-#pragma unroll
-            for (int ww = 0; ww < 8; ++ww) sum += sm.red[ww][s][c];
-            partials[(size_t)sm.emit[jj + s] * kRedVals + c] = sum;
-          }
-          __syncthreads();
-        }
-      }
-    }
-  }
-  if (kFull) {
-    // pairs past every pixel's last blended surfel contribute nothing
-    const int tail = end - max(hi, start);
-    for (int o = threadIdx.x; o < tail * kRedVals; o += kTileThreads) {
-      const int s = o / kRedVals, c = o % kRedVals;
-      partials[(size_t)emit[hi + s] * kRedVals + c] = 0.f;
-    }
-  }
-}
-
-// Pose-only back-to-front replay (tracking): like bwd_tile but each warp
-// visits only the surfels whose footprint touches its block, and the pose
-// gradient is accumulated per pixel.  With the hit point X = z r and r fixed
-// per pixel, sum_pairs X x Gv = r x sum_pairs z Gv, so a pair only adds Gv
-// and z Gv; with q = s (u d_u + v d_v), s = -G dL/dG, the pair's
-// Gv = beta n - q, beta = (q . r + gz) / (n . r).  kNormal adds the normal
-// image's term t_nc x w gN per pair (tracking has no normal gradient).
-template <bool kNormal>
-__device__ __forceinline__ void bwd_tile_pose(const float4* __restrict__ proj,
-                                              const uint32_t* __restrict__ vals, int start, int end,
-                                              float xt, float yt, int tile_x0, int tile_y0,
-                                              const TilePix& tp, bool inside, float rx, float ry,
-                                              const gs2d_camera& cam, const gs2d_config& cfg,
-                                              float Tf, uint32_t nl, F3 gC, float gD, F3 gN,
-                                              float gO, BwdSmem<false>& sm, HitLists& hl,
-                                              float (&pr)[6]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float fxfy = cam.fx * cam.fy;
-  if (threadIdx.x == 0) sm.max_nl = 0u;
-  __syncthreads();
-  if (nl) atomicMax(&sm.max_nl, nl);
-  __syncthreads();
-  const int hi = start + (int)sm.max_nl;
-  float T = Tf, acc = 0.f;
-  const float gOT = gO * Tf;
-  F3 sG = f3(0.f, 0.f, 0.f), szG = f3(0.f, 0.f, 0.f), sN = f3(0.f, 0.f, 0.f);
-  for (int bend = hi; bend > start; bend -= kTileThreads) {
-    const int bstart = max(start, bend - kTileThreads);
-    const int cnt = bend - bstart;
-    __syncthreads();
-    if ((int)threadIdx.x < cnt) {
-      stage_record<kBwdVec4>(proj, vals[bstart + (int)threadIdx.x], xt, yt, sm.rec);
-      const float4 rf = sm.rec[threadIdx.x][6];
-      hl.mask[threadIdx.x] = footprint_mask(rf.z, rf.w, tile_x0, tile_y0, cfg.tile_w);
-    }
-    __syncthreads();
-    const int nh = warp_hit_list(hl.mask, hl.list[warp], cnt, warp, lane);
-    if (!inside) continue;
-    for (int k = nh - 1; k >= 0; --k) {
-      const int jj = hl.list[warp][k];
-      if (bstart + jj - start >= (int)nl) continue;
-      const float4 r0 = sm.rec[jj][0], r1 = sm.rec[jj][1], r2 = sm.rec[jj][2];
-      Eval e;
-      if (!eval_pair(r0, r1, r2, tp.lx, tp.ly, cam.near_z, cfg.cutoff_r2, cfg.alpha_min,
-                     cfg.alpha_max, e))
-        continue;
-      const float4 r3 = sm.rec[jj][3], r4 = sm.rec[jj][4], r5 = sm.rec[jj][5], r6 = sm.rec[jj][6];
-      const float iom = __fdividef(1.f, 1.f - e.a);
-      const float Tb = T * iom;
-      const float w = e.a * Tb;
-      float vj = fmaf(r2.w, gC.x, fmaf(r3.x, gC.y, fmaf(r3.y, gC.z, e.z * gD)));
-      if (kNormal) vj = fmaf(r3.z, gN.x, fmaf(r3.w, gN.y, fmaf(r4.x, gN.z, vj)));
-      const float ga = Tb * vj - (acc - gOT) * iom;
-      acc = fmaf(w, vj, acc);
-      T = Tb;
-      const float s = e.araw <= cfg.alpha_max ? -e.G * r2.z * ga : 0.f;
-      // P = u d_u + v d_v; q = s P
-      const float Px = fmaf(e.u, r5.x, e.v * r5.w);
-      const float Py = fmaf(e.u, r5.y, e.v * r6.x);
-      const float Pz = fmaf(e.u, r5.z, e.v * r6.y);
-      const float Pr = fmaf(Px, rx, fmaf(Py, ry, Pz));
-      const float beta = fmaf(s, Pr, w * gD) * fxfy * e.rinv;
-      const float Gx = fmaf(beta, r4.y, -s * Px);
-      const float Gy = fmaf(beta, r4.z, -s * Py);
-      const float Gz = fmaf(beta, r4.w, -s * Pz);
-      sG.x += Gx;
-      sG.y += Gy;
-      sG.z += Gz;
-      szG.x = fmaf(e.z, Gx, szG.x);
-      szG.y = fmaf(e.z, Gy, szG.y);
-      szG.z = fmaf(e.z, Gz, szG.z);
-      if (kNormal) sN = sN + w * f3(r3.z, r3.w, r4.x);
-    }
-  }
-  // theta: r x sum z Gv (+ sum_pairs t_nc x w gN = N x gN over the pairs)
-  const F3 th = cross3(f3(rx, ry, 1.f), szG) + cross3(sN, gN);
-  pr[0] += sG.x;
-  pr[1] += sG.y;
-  pr[2] += sG.z;
-  pr[3] += th.x;
-  pr[4] += th.y;
-  pr[5] += th.z;
-}
-
-// Block sum of a per-thread 6-vector, written by threads 0..5.
-__device__ __forceinline__ void block_sum6(const float (&pr)[6], float (*s_pose)[6],
-                                           float* __restrict__ out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    float v = pr[i];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) s_pose[warp][i] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 6) {
-    float v = 0.f;
-    for (int ww = 0; ww < kTileThreads / 32; ++ww) v += s_pose[ww][threadIdx.x];
-    out[threadIdx.x] = v;
-  }
-}
 
 template <bool kCount>
 __global__ void __launch_bounds__(kTileThreads) render_fwd_kernel(
@@ -669,13 +216,15 @@ __global__ void __launch_bounds__(kTileThreads) track_tile_kernel(
 
 // Per-surfel reduction of the (tile, surfel) partials in emission order and
 // the chain rule to world-space parameters; pose term per block.
+// Record i is surfel active[i] (or i); with accumulate the gradients are
+// added to the outputs (several views, one after another).
 __global__ void __launch_bounds__(256) surfel_grad_kernel(
     const float* __restrict__ mu, const float* __restrict__ quat, const float* __restrict__ scale,
-    int n, const float* __restrict__ pose, const int32_t* __restrict__ tiles,
-    const uint32_t* __restrict__ surfel_off, const float* __restrict__ partials,
-    float* __restrict__ d_mu, float* __restrict__ d_quat, float* __restrict__ d_scale,
-    float* __restrict__ d_opac, float* __restrict__ d_rgb, float* __restrict__ pose_part,
-    const int32_t* __restrict__ gate) {
+    int n, const int32_t* __restrict__ active, int accumulate, const float* __restrict__ pose,
+    const int32_t* __restrict__ tiles, const uint32_t* __restrict__ surfel_off,
+    const float* __restrict__ partials, float* __restrict__ d_mu, float* __restrict__ d_quat,
+    float* __restrict__ d_scale, float* __restrict__ d_opac, float* __restrict__ d_rgb,
+    float* __restrict__ pose_part, int n_all, const int32_t* __restrict__ gate) {
   __shared__ float sp[12];
   __shared__ float s_pose[8][6];
   if (gate && *gate) return;
@@ -702,33 +251,36 @@ __global__ void __launch_bounds__(256) surfel_grad_kernel(
       }
     }
     const float* R = sp;
-    const float4 q4 = reinterpret_cast<const float4*>(quat)[i];
+    const int sid = active ? min(max(active[i], 0), n_all - 1) : i;
+    const float4 q4 = reinterpret_cast<const float4*>(quat)[sid];
     const float qn2 = fmaf(q4.x, q4.x, fmaf(q4.y, q4.y, fmaf(q4.z, q4.z, q4.w * q4.w)));
     const float qinv = rsqrtf(qn2);
     const float w = q4.x * qinv, x = q4.y * qinv, y = q4.z * qinv, z = q4.w * qinv;
     const F3 tu = f3(1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y));
     const F3 tv = f3(2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x));
     const F3 tn = f3(2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y));
-    const F3 mu_c = mat_mul(R, f3(mu[3 * i], mu[3 * i + 1], mu[3 * i + 2])) + f3(sp[9], sp[10], sp[11]);
+    const F3 mu_c = mat_mul(R, f3(mu[3 * sid], mu[3 * sid + 1], mu[3 * sid + 2])) + f3(sp[9], sp[10], sp[11]);
     const F3 tuc = mat_mul(R, tu), tvc = mat_mul(R, tv), tnc = mat_mul(R, tn);
-    const float su = scale[2 * i], sv = scale[2 * i + 1];
+    const float su = scale[2 * sid], sv = scale[2 * sid + 1];
     const F3 g_muc = f3(S[0], S[1], S[2]);
     const F3 g_mu = f3(S[3], S[4], S[5]), g_mv = f3(S[6], S[7], S[8]);
     const F3 g_tnc = f3(S[13], S[14], S[15]);
     const F3 g_tuc = su * g_mu, g_tvc = sv * g_mv;
-    d_scale[2 * i] = dot3(tuc, g_mu);
-    d_scale[2 * i + 1] = dot3(tvc, g_mv);
-    d_opac[i] = S[9];
-    d_rgb[3 * i] = S[10];
-    d_rgb[3 * i + 1] = S[11];
-    d_rgb[3 * i + 2] = S[12];
+    // o(p, v): write, or add when accumulating over views
+    auto o = [&](float* p, float v) { *p = accumulate ? *p + v : v; };
+    o(d_scale + 2 * sid, dot3(tuc, g_mu));
+    o(d_scale + 2 * sid + 1, dot3(tvc, g_mv));
+    o(d_opac + sid, S[9]);
+    o(d_rgb + 3 * sid, S[10]);
+    o(d_rgb + 3 * sid + 1, S[11]);
+    o(d_rgb + 3 * sid + 2, S[12]);
     const F3 th = cross3(mu_c, g_muc) + cross3(tuc, g_tuc) + cross3(tvc, g_tvc) + cross3(tnc, g_tnc);
     pr[0] = g_muc.x; pr[1] = g_muc.y; pr[2] = g_muc.z;
     pr[3] = th.x; pr[4] = th.y; pr[5] = th.z;
     const F3 gmw = mat_tmul(R, g_muc);
-    d_mu[3 * i] = gmw.x;
-    d_mu[3 * i + 1] = gmw.y;
-    d_mu[3 * i + 2] = gmw.z;
+    o(d_mu + 3 * sid, gmw.x);
+    o(d_mu + 3 * sid + 1, gmw.y);
+    o(d_mu + 3 * sid + 2, gmw.z);
     // world-space column gradients G[:,0..2] = R^T g_t{u,v,n}c
     const F3 G0 = mat_tmul(R, g_tuc), G1 = mat_tmul(R, g_tvc), G2 = mat_tmul(R, g_tnc);
     // d/dq of the rotation matrix of a unit quaternion, contracted with G
@@ -742,10 +294,10 @@ __global__ void __launch_bounds__(256) surfel_grad_kernel(
     const float gz = 2.f * (x * (G02 + G20) + y * (G12 + G21) + w * (G10 - G01)) - 4.f * z * (G00 + G11);
     // unit quaternion -> raw quaternion: (I - q q^T) / |q|
     const float qd = w * gw + x * gx + y * gy + z * gz;
-    d_quat[4 * i] = (gw - w * qd) * qinv;
-    d_quat[4 * i + 1] = (gx - x * qd) * qinv;
-    d_quat[4 * i + 2] = (gy - y * qd) * qinv;
-    d_quat[4 * i + 3] = (gz - z * qd) * qinv;
+    o(d_quat + 4 * sid, (gw - w * qd) * qinv);
+    o(d_quat + 4 * sid + 1, (gx - x * qd) * qinv);
+    o(d_quat + 4 * sid + 2, (gy - y * qd) * qinv);
+    o(d_quat + 4 * sid + 3, (gz - z * qd) * qinv);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -845,6 +397,27 @@ int track_tile_launch(const float* proj, const gs2d_bins* bins, const gs2d_camer
   return GS2D_OK;
 }
 
+int surfel_grad_launch(const gs2d_surfels* s, const int32_t* active, int m, int accumulate,
+                       const float* pose, const int32_t* tiles, const uint32_t* surfel_off,
+                       const float* partials, float* d_mu, float* d_quat, float* d_scale,
+                       float* d_opac, float* d_rgb, float* pose_part, const int32_t* gate,
+                       cudaStream_t st) {
+  if (m <= 0) return GS2D_OK;
+  surfel_grad_kernel<<<(m + 255) / 256, 256, 0, st>>>(s->mu, s->quat, s->scale, m, active,
+                                                      accumulate, pose, tiles, surfel_off, partials,
+                                                      d_mu, d_quat, d_scale, d_opac, d_rgb,
+                                                      pose_part, s->n, gate);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+int pose_reduce_launch(const float* part, int n_part, float* out, const int32_t* gate,
+                       cudaStream_t st) {
+  pose_reduce_kernel<<<1, 256, 0, st>>>(part, n_part, out, gate);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
 size_t render_bwd_ws_bytes(int n, size_t cap, int n_tiles, bool full) {
   return carve_bwd_ws(nullptr, n, cap, n_tiles, full).bytes;
 }
@@ -882,9 +455,10 @@ int render_bwd_launch(const float* proj, const gs2d_bins* bins, const int32_t* t
     GS2D_LAUNCH_CHECK();
     if (s->n > 0) {
       const int nb = (s->n + 255) / 256;
-      surfel_grad_kernel<<<nb, 256, 0, st>>>(s->mu, s->quat, s->scale, s->n, pose, tiles_per_surfel,
-                                             bins->surfel_off, w.partials, d_mu, d_quat, d_scale,
-                                             d_opac, d_rgb_out, w.pose_part, gate);
+      surfel_grad_kernel<<<nb, 256, 0, st>>>(s->mu, s->quat, s->scale, s->n, nullptr, 0, pose,
+                                             tiles_per_surfel, bins->surfel_off, w.partials, d_mu,
+                                             d_quat, d_scale, d_opac, d_rgb_out, w.pose_part, s->n,
+                                             gate);
       GS2D_LAUNCH_CHECK();
       if (d_pose6) {
         pose_reduce_kernel<<<1, 256, 0, st>>>(w.pose_part, nb, d_pose6, gate);

@@ -63,12 +63,27 @@ class TrackParams(ctypes.Structure):
                 ("opacity_thresh", ctypes.c_float), ("depth_mode", ctypes.c_int)]
 
 
+class View(ctypes.Structure):
+    _fields_ = [("cam", Camera), ("cfg", Config), ("pose", ctypes.c_void_p),
+                ("active", ctypes.c_void_p), ("n_active", ctypes.c_int),
+                ("proj", ctypes.c_void_p), ("tiles_per_surfel", ctypes.c_void_p), ("bins", Bins),
+                ("rgb", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("normal", ctypes.c_void_p),
+                ("opacity", ctypes.c_void_p), ("t_final", ctypes.c_void_p),
+                ("n_last", ctypes.c_void_p), ("d_rgb", ctypes.c_void_p),
+                ("d_depth", ctypes.c_void_p), ("d_normal", ctypes.c_void_p),
+                ("d_opacity", ctypes.c_void_p), ("d_pose6", ctypes.c_void_p)]
+
+
+MAX_VIEWS = 32
+
 EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_string",
            "gs2d_tiles_x", "gs2d_tiles_y", "gs2d_project", "gs2d_bin_sort_workspace",
            "gs2d_bin_sort", "gs2d_render_fwd", "gs2d_render_bwd_workspace", "gs2d_render_bwd",
            "gs2d_tracking_loss", "gs2d_mapping_loss", "gs2d_track_workspace", "gs2d_track_step",
            "gs2d_track_status", "gs2d_render_count", "gs2d_bin_sort_static",
-           "gs2d_profile_track_kernel", "gs2d_profile_track_kernel_count"]
+           "gs2d_profile_track_kernel", "gs2d_profile_track_kernel_count",
+           "gs2d_project_batch", "gs2d_bin_sort_batch_workspace", "gs2d_bin_sort_batch",
+           "gs2d_render_batch_workspace", "gs2d_render_fwd_batch", "gs2d_render_bwd_batch"]
 
 
 def lib_path() -> str:
@@ -107,6 +122,14 @@ def lib():
         L.gs2d_track_step.argtypes = [vp] * 7 + [ip, sz, vp, vp, vp, sz, vp, vp]
         L.gs2d_profile_track_kernel.argtypes = [vp, vp, ip]
         L.gs2d_profile_track_kernel_count.restype = ip
+        L.gs2d_project_batch.argtypes = [vp, vp, ip, vp]
+        L.gs2d_bin_sort_batch_workspace.restype = sz
+        L.gs2d_bin_sort_batch_workspace.argtypes = [vp, ip, ip]
+        L.gs2d_bin_sort_batch.argtypes = [vp, ip, ip, vp, sz, vp, vp]
+        L.gs2d_render_batch_workspace.restype = sz
+        L.gs2d_render_batch_workspace.argtypes = [vp, ip, ip]
+        L.gs2d_render_fwd_batch.argtypes = [vp, ip, vp, sz, vp, vp]
+        L.gs2d_render_bwd_batch.argtypes = [vp, ip, vp, vp, vp, vp, vp, vp, vp, sz, vp, vp]
         L.gs2d_track_status.restype = vp
         L.gs2d_track_status.argtypes = [vp]
         _LIB = L
@@ -302,6 +325,115 @@ _PROFILE_KEEP = []
 def gs2d_track_status(workspace) -> torch.Tensor:
     """The int32 status word of a track workspace, as a 1-element view."""
     return workspace.view(torch.int32)[:1]
+
+
+def gs2d_project_batch(surf: DeviceSurfels, views, stream=None):
+    arr = (View * len(views))(*views)
+    sv = surf.struct()
+    check(lib().gs2d_project_batch(_ref(sv), arr, len(views), _stream(stream)), "gs2d_project_batch")
+
+
+def gs2d_bin_sort_batch(views, n, workspace, stream=None):
+    arr = (View * len(views))(*views)
+    check(lib().gs2d_bin_sort_batch(arr, len(views), int(n), _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(), None,
+                                    _stream(stream)), "gs2d_bin_sort_batch")
+
+
+def gs2d_render_fwd_batch(views, workspace, stream=None):
+    arr = (View * len(views))(*views)
+    check(lib().gs2d_render_fwd_batch(arr, len(views), _ptr(workspace),
+                                      workspace.numel() * workspace.element_size(), None,
+                                      _stream(stream)), "gs2d_render_fwd_batch")
+
+
+def gs2d_render_bwd_batch(views, surf: DeviceSurfels, d_mu, d_quat, d_scale, d_opac, d_rgb,
+                          workspace, stream=None):
+    arr = (View * len(views))(*views)
+    sv = surf.struct()
+    check(lib().gs2d_render_bwd_batch(arr, len(views), _ref(sv), _ptr(d_mu), _ptr(d_quat),
+                                      _ptr(d_scale), _ptr(d_opac), _ptr(d_rgb), _ptr(workspace),
+                                      workspace.numel() * workspace.element_size(), None,
+                                      _stream(stream)), "gs2d_render_bwd_batch")
+
+
+class BatchRasterizer:
+    """Buffers of a batch of views (up to 32): per view its records, bins,
+    images and upstream gradients; projection, binning and the two render
+    passes each run as one batched call."""
+
+    def __init__(self, cams, n: int, actives=None, tiles=None, capacities=None, device="cuda"):
+        self.n = int(n)
+        self.device = device
+        self.nv = len(cams)
+        assert 0 < self.nv <= MAX_VIEWS
+        self.views = []
+        self.keep = []
+        f = dict(dtype=torch.float32, device=device)
+        for v, cam in enumerate(cams):
+            act = None if actives is None or actives[v] is None else \
+                torch.as_tensor(np.asarray(actives[v], np.int32), device=device)
+            m = self.n if act is None else int(act.numel())
+            cfg = default_config(tiles[v] if tiles else (16, 16))
+            ccam = camera(cam)
+            tx = int(lib().gs2d_tiles_x(_ref(ccam), _ref(cfg)))
+            ty = int(lib().gs2d_tiles_y(_ref(ccam), _ref(cfg)))
+            cap = int(capacities[v]) if capacities else max(8 * m, 1024)
+            H, W = int(cam.height), int(cam.width)
+            b = dict(pose=torch.empty(12, **f), active=act,
+                     proj=torch.empty(max(m, 1) * PROJ_FLOATS, **f),
+                     tiles=torch.empty(max(m, 1), dtype=torch.int32, device=device),
+                     vals=torch.empty(cap, dtype=torch.int32, device=device),
+                     emit=torch.empty(cap, dtype=torch.int32, device=device),
+                     off=torch.empty(max(m, 1), dtype=torch.int32, device=device),
+                     ranges=torch.empty(2 * tx * ty, dtype=torch.int32, device=device),
+                     n_isect=torch.zeros(1, dtype=torch.int32, device=device),
+                     status=torch.zeros(1, dtype=torch.int32, device=device),
+                     rgb=torch.empty(H, W, 3, **f), depth=torch.empty(H, W, **f),
+                     normal=torch.empty(H, W, 3, **f), opacity=torch.empty(H, W, **f),
+                     t_final=torch.empty(H, W, **f),
+                     n_last=torch.empty(H, W, dtype=torch.int32, device=device),
+                     d_rgb=torch.zeros(H, W, 3, **f), d_depth=torch.zeros(H, W, **f),
+                     d_normal=torch.zeros(H, W, 3, **f), d_opacity=torch.zeros(H, W, **f),
+                     d_pose6=torch.zeros(6, **f), m=m, cap=cap, cam=cam, cfg=cfg)
+            bins = Bins(None, b["vals"].data_ptr(), b["emit"].data_ptr(), b["off"].data_ptr(),
+                        b["ranges"].data_ptr(), b["n_isect"].data_ptr(), b["status"].data_ptr(), cap)
+            view = View(ccam, cfg, b["pose"].data_ptr(), _ptr(act).value if act is not None else None,
+                        m, b["proj"].data_ptr(), b["tiles"].data_ptr(), bins, b["rgb"].data_ptr(),
+                        b["depth"].data_ptr(), b["normal"].data_ptr(), b["opacity"].data_ptr(),
+                        b["t_final"].data_ptr(), b["n_last"].data_ptr(), b["d_rgb"].data_ptr(),
+                        b["d_depth"].data_ptr(), b["d_normal"].data_ptr(),
+                        b["d_opacity"].data_ptr(), b["d_pose6"].data_ptr())
+            self.views.append(view)
+            self.keep.append(b)
+        self.sort_ws = _bytes(lib().gs2d_bin_sort_batch_workspace(
+            (View * self.nv)(*self.views), self.nv, self.n), device)
+        self.render_ws = _bytes(lib().gs2d_render_batch_workspace(
+            (View * self.nv)(*self.views), self.nv, self.n), device)
+        self.grads = dict(mu=torch.empty(self.n, 3, **f), quat=torch.empty(self.n, 4, **f),
+                          scale=torch.empty(self.n, 2, **f), opacity=torch.empty(self.n, **f),
+                          rgb=torch.empty(self.n, 3, **f))
+
+    def set_poses(self, poses):
+        for b, p in zip(self.keep, poses):
+            b["pose"].copy_(p if isinstance(p, torch.Tensor) else pose_tensor(p, self.device))
+
+    def forward(self, surf: DeviceSurfels, stream=None, check_status=True):
+        for b in self.keep:
+            b["status"].zero_()
+        gs2d_project_batch(surf, self.views, stream)
+        gs2d_bin_sort_batch(self.views, self.n, self.sort_ws, stream)
+        gs2d_render_fwd_batch(self.views, self.render_ws, stream)
+        if check_status:
+            st = [int(b["status"].item()) for b in self.keep]
+            if any(st):
+                raise Gs2dError(f"batch status {st} (n_isect {[int(b['n_isect'].item()) for b in self.keep]})")
+
+    def backward(self, surf: DeviceSurfels, stream=None):
+        g = self.grads
+        gs2d_render_bwd_batch(self.views, surf, g["mu"], g["quat"], g["scale"], g["opacity"],
+                              g["rgb"], self.render_ws, stream)
+        return g
 
 
 # ---------------------------------------------------------------------------

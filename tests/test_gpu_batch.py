@@ -1,0 +1,152 @@
+"""Batched views (one persistent launch per render pass over all views):
+per-view images equal the single-view entry points bit for bit; surfel
+gradients summed over views, with active subsets, uneven resolutions and
+per-view tile shapes, equal the sum of the oracle's per-view gradients."""
+import numpy as np
+import pytest
+
+from paper_2506_00970_gb300 import scenes
+from gpu_helpers import TOL_GRAD, gpu_render, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_00970_gb300 import gs2d
+    gs2d.lib()
+    return torch
+
+
+def _setup(n_views=4, seed=0):
+    s = scenes.slab_scene(seed, 3000)
+    rng = np.random.default_rng(seed)
+    cams = [scenes.Camera(150.0, 150.0, 80.0, 60.0, 160, 120),
+            scenes.Camera(100.0, 100.0, 48.0, 32.0, 96, 64),
+            scenes.Camera(170.0, 170.0, 100.5, 75.0, 200, 150),
+            scenes.Camera(120.0, 120.0, 60.0, 44.0, 120, 88)][:n_views]
+    poses = [scenes.perturb_pose(scenes.identity_pose(), 0.05, 3.0, seed=10 + v) for v in range(n_views)]
+    actives = [None, np.sort(rng.choice(s.n, 1800, replace=False)).astype(np.int32), None,
+               np.sort(rng.choice(s.n, 900, replace=False)).astype(np.int32)][:n_views]
+    tiles = [(16, 16), (8, 32), (32, 8), (16, 16)][:n_views]
+    return s, cams, poses, actives, tiles
+
+
+def test_batch_forward_equals_single_views(torch_cuda):
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d
+    s, cams, poses, actives, tiles = _setup()
+    ds = gs2d.DeviceSurfels(s)
+    br = gs2d.BatchRasterizer(cams, s.n, actives=actives, tiles=tiles)
+    br.set_poses(poses)
+    br.forward(ds)
+    torch.cuda.synchronize()
+    for v in range(len(cams)):
+        sub = s if actives[v] is None else s.subset(actives[v])
+        _, _, _, g = gpu_render(sub, cams[v], poses[v], tile=tiles[v])
+        b = br.keep[v]
+        for k in ("rgb", "depth", "normal", "opacity", "t_final", "n_last"):
+            np.testing.assert_array_equal(b[k].cpu().numpy(), g[k], err_msg=f"view {v} {k}")
+
+
+def _well_conditioned(orc, s, cams, poses, actives, min_cos=0.02):
+    """The scene without surfels that some view sees within ~1.1 degrees of
+    edge-on (oracle min_cos), where the FP32 ray-surfel intersection is
+    ill-conditioned; active subsets are re-indexed."""
+    mc = np.ones(s.n)
+    for v in range(len(cams)):
+        ids = np.arange(s.n) if actives[v] is None else actives[v]
+        z3 = np.zeros((cams[v].height, cams[v].width, 3))
+        z1 = np.zeros((cams[v].height, cams[v].width))
+        og = orc.render_bwd(s.subset(ids), cams[v], poses[v], z3, z1, z3, z1)
+        mc[ids] = np.minimum(mc[ids], og["min_cos"])
+    keep = np.nonzero(mc > min_cos)[0]
+    new_id = np.full(s.n, -1, np.int64)
+    new_id[keep] = np.arange(len(keep))
+    acts = [None if a is None else new_id[a][new_id[a] >= 0].astype(np.int32) for a in actives]
+    return s.subset(keep), acts
+
+
+def test_batch_backward_matches_oracle_sum(torch_cuda, orc):
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d
+    s, cams, poses, actives, tiles = _setup()
+    s, actives = _well_conditioned(orc, s, cams, poses, actives)
+    ds = gs2d.DeviceSurfels(s)
+    br = gs2d.BatchRasterizer(cams, s.n, actives=actives, tiles=tiles)
+    br.set_poses(poses)
+    br.forward(ds)
+    total = {k: np.zeros(getattr(s, k).shape) for k in ("mu", "quat", "scale", "opacity", "rgb")}
+    mincos = np.ones(s.n)
+    pose6 = []
+    for v in range(len(cams)):
+        up = scenes.random_upstream(20 + v, cams[v].height, cams[v].width)
+        # L1-like signs on colour and depth
+        d_rgb, d_d = np.sign(up[0]), np.sign(up[1])
+        b = br.keep[v]
+        b["d_rgb"].copy_(torch.tensor(d_rgb, dtype=torch.float32))
+        b["d_depth"].copy_(torch.tensor(d_d, dtype=torch.float32))
+        ids = np.arange(s.n) if actives[v] is None else actives[v]
+        og = orc.render_bwd(s.subset(ids), cams[v], poses[v], d_rgb, d_d, np.zeros_like(d_rgb),
+                            np.zeros_like(d_d))
+        for k in total:
+            total[k][ids] += og[k]
+        mincos[ids] = np.minimum(mincos[ids], og["min_cos"])
+        pose6.append(og["pose6"])
+    g = br.backward(ds)
+    torch.cuda.synchronize()
+    # per element: surfels seen within ~3 degrees of edge-on are left out.
+    # A pixel whose alpha sits on the 1/255 skip threshold (or a pair on the
+    # 3-sigma cutoff) is decided differently in FP32 and FP64 and moves its
+    # surfel's gradient by one pixel's term: at most max(2, 1e-3 n) such rows.
+    cond = np.ones(s.n, bool)
+    ok = mincos > 0.05
+    allow = max(2, int(1e-3 * s.n))
+    for k in total:
+        a, r = to_np(g[k])[cond], total[k][cond]
+        okc = ok[cond]
+        scale = np.abs(r).max()
+        row_err = np.abs(a - r).reshape(len(r), -1).max(1)
+        assert np.sum(row_err > TOL_GRAD * scale) <= allow, (k, np.sort(row_err)[-4:] / scale)
+        big = (np.abs(r) > 1e-2 * scale)
+        big[~okc] = False
+        rel = np.abs(a - r)[big] / np.abs(r[big])
+        assert np.mean(rel > TOL_GRAD) < 2e-3, (k, np.mean(rel > TOL_GRAD))
+    # the batch equals the single-view entry points summed over views (same
+    # per-pair arithmetic; only the FP32 order of the sum over views differs)
+    single = {k: np.zeros(getattr(s, k).shape) for k in total}
+    for v in range(len(cams)):
+        ids = np.arange(s.n) if actives[v] is None else actives[v]
+        sub = s.subset(ids)
+        r, dsub, pt, _ = gpu_render(sub, cams[v], poses[v], tile=tiles[v])
+        b = br.keep[v]
+        gv = r.backward(dsub, pt, b["d_rgb"], b["d_depth"], None, None, full=True)
+        for k in single:
+            single[k][ids] += to_np(gv[k])
+    torch.cuda.synchronize()
+    for k in single:
+        a = to_np(g[k])
+        assert np.abs(a - single[k]).max() <= 1e-6 * np.abs(single[k]).max() * len(cams), k
+    for v in range(len(cams)):
+        p = br.keep[v]["d_pose6"].cpu().numpy().astype(np.float64)
+        assert np.abs(p - pose6[v]).max() <= TOL_GRAD * np.abs(pose6[v]).max(), (v, p, pose6[v])
+    # surfels outside every subset and every view get exactly zero
+    seen = np.zeros(s.n, bool)
+    for v in range(len(cams)):
+        seen[np.arange(s.n) if actives[v] is None else actives[v]] = True
+    assert seen.all() or np.all(to_np(g["mu"])[~seen] == 0)
+
+
+def test_batch_capacity_error_is_per_view(torch_cuda):
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d
+    s, cams, poses, actives, tiles = _setup(n_views=2)
+    ds = gs2d.DeviceSurfels(s)
+    br = gs2d.BatchRasterizer(cams, s.n, actives=actives, tiles=tiles, capacities=[50, 100000])
+    br.set_poses(poses)
+    with pytest.raises(gs2d.Gs2dError):
+        br.forward(ds)
+    assert int(br.keep[0]["status"].item()) == 3 and int(br.keep[1]["status"].item()) == 0
