@@ -45,6 +45,10 @@ L2_FLUSH_BYTES = 256 << 20
 # same workload (profiles/track_tile_tracking_640x480.md); None if the kernel
 # changed since the capture.
 TRAFFIC_BYTES = {"track_tile": 6317056}
+# batched workloads reported beside the tracking line
+MAP_SURFELS, MAP_VIEWS = 1_000_000, 8
+UNEVEN_SURFELS, UNEVEN_VIEWS = 2_000_000, 32
+MAP_W_D, MAP_W_N = 0.5, 0.02
 
 
 def _args():
@@ -351,6 +355,8 @@ def run_ours(args):
     d2h = 12 * 4 + 4
 
     roof = roofline(r, ds, frames, cam, cfg, stream, ms_iter, fused_ms)
+    del graph
+    batch = batch_workloads(K, W_, flush)
 
     if rank == 0:
         clocks = clk.summary()
@@ -371,6 +377,7 @@ def run_ours(args):
             "gpu_launches": K * (1 + N_ITER * LAUNCHES_PER_ITER),
             "roofline": roof["main"],
             "roofline_other": roof["other"],
+            **batch,
             "wall_s": wall,
             "peak_source": src,
         }
@@ -449,6 +456,171 @@ def roofline(r, ds, frames, cam, cfg, stream, ms_iter, fused_ms):
     bwd = {"kernel": "render_bwd_kernel<pose> + pose_reduce", "bound": "alu", "achieved": ab,
            "peak": peak, "unit": "TFLOP/s", "frac": ab / peak, "launch_ms": tb * 1e3}
     return {"main": fused, "other": [fwd, bwd]}
+
+
+def _perturbed_map(s, seed):
+    """The map being optimised: the true map with centres moved by N(0, 3 mm)
+    and colours by N(0, 0.05), so every loss term has a gradient."""
+    from paper_2506_00970_gb300 import scenes
+    rng = np.random.default_rng(seed)
+    return scenes.Surfels(s.mu + rng.normal(0, 3e-3, s.mu.shape), s.quat, s.scale, s.opacity,
+                          np.clip(s.rgb + rng.normal(0, 0.05, s.rgb.shape), 0, 1))
+
+
+def measure_batch(name, s_true, cams, poses, actives, K, W_, flush, seed):
+    """One batched mapping step over all views: project, bin_sort, forward
+    (one persistent launch), the mapping loss per view (colour L1 + 0.5 depth
+    L1 + 0.02 normal consistency) and backward (one persistent launch + the
+    per-surfel reductions), gradients to every surfel parameter.  Tile shapes
+    come from the autotuner per resolution class.  Timed as direct calls
+    (per phase) and as one CUDA graph replay per step."""
+    import torch
+    from paper_2506_00970_gb300 import autotune, gs2d
+    stream = torch.cuda.current_stream()
+    ds_true = gs2d.DeviceSurfels(s_true)
+    ds = gs2d.DeviceSurfels(_perturbed_map(s_true, seed))
+    t0 = time.perf_counter()
+    tiles, sweep = autotune.tune_tiles(ds, cams, poses, actives)
+    tune_s = time.perf_counter() - t0
+    br = gs2d.BatchRasterizer(cams, ds.n, actives=actives, tiles=tiles)
+    br.set_poses(poses)
+    br.fit(ds_true)
+    br.forward(ds_true)
+    obs = []
+    for v, b in enumerate(br.keep):
+        noise = torch.randn(b["depth"].shape, generator=torch.Generator("cuda").manual_seed(seed + v),
+                            device="cuda") * 1e-3
+        obs.append((b["rgb"].clone(), b["depth"] / b["opacity"].clamp_min(1e-6) + noise))
+    del ds_true
+    kv = br.fit(ds)
+    loss = torch.zeros(len(cams), device="cuda")
+    lws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+
+    def losses():
+        for v, b in enumerate(br.keep):
+            gs2d.gs2d_mapping_loss(b["rgb"], b["depth"], b["normal"], b["opacity"], obs[v][0],
+                                   obs[v][1], b["ccam"], MAP_W_D, MAP_W_N, b["d_rgb"],
+                                   b["d_depth"], b["d_normal"], b["d_opacity"], loss[v:v + 1], lws)
+
+    def step():
+        br.forward(ds, check_status=False)
+        losses()
+        br.backward(ds)
+
+    # direct calls, per phase
+    phases = ("project", "bin_sort", "render_fwd", "loss", "render_bwd")
+    per = {k: [] for k in phases}
+    direct = []
+    for i in range(W_ + K):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        for b in br.keep:
+            b["status"].zero_()
+        ev[0].record(stream)
+        gs2d.gs2d_project_batch(ds, br.views)
+        ev[1].record(stream)
+        gs2d.gs2d_bin_sort_batch(br.views, br.n, br.sort_ws)
+        ev[2].record(stream)
+        gs2d.gs2d_render_fwd_batch(br.views, br.render_ws)
+        ev[3].record(stream)
+        losses()
+        ev[4].record(stream)
+        br.backward(ds)
+        ev[5].record(stream)
+        ev[5].synchronize()
+        if i >= W_:
+            for j, k in enumerate(phases):
+                per[k].append(ev[j].elapsed_time(ev[j + 1]))
+            direct.append(ev[0].elapsed_time(ev[5]))
+    st = [int(b["status"].item()) for b in br.keep]
+    if any(st):
+        raise RuntimeError(f"{name}: batch status {st}")
+    # one CUDA graph per step
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        step()
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for _ in range(W_):
+        graph.replay()
+    torch.cuda.synchronize()
+    gms = []
+    for _ in range(K):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        e1.synchronize()
+        gms.append(e0.elapsed_time(e1))
+    st = [int(b["status"].item()) for b in br.keep]
+    if any(st):
+        raise RuntimeError(f"{name}: batch status {st}")
+    # algorithmic FP32 work of the two compositing launches from pair counts
+    counts = torch.zeros(3, dtype=torch.int64, device="cuda")
+    E = np.zeros(3)
+    for b in br.keep:
+        gs2d.gs2d_render_count(b["proj"], b["bins"], b["ccam"], b["cfg"], counts)
+        torch.cuda.synchronize()
+        E += counts.cpu().numpy()
+    pk, src = peaks()
+    peak = fp32_peak_tflops(float(pk.get("sm_max_mhz", 2070.0)))
+    w_f = FLOPS_EVAL * E[0] + FLOPS_IN * E[1] + FLOPS_BLEND * E[2]
+    w_b = FLOPS_EVAL * E[0] + FLOPS_IN * E[1] + FLOPS_BWD_BLEND * E[2]
+    tf, tb = np.median(per["render_fwd"]) / 1e3, np.median(per["render_bwd"]) / 1e3
+    P = sum(int(c.width) * int(c.height) for c in cams)
+    g_ms = float(np.median(gms))
+    out = {
+        "value": P / (g_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": g_ms,
+        "ms_per_step_direct": float(np.median(direct)),
+        "mpix_per_s_direct": P / (np.median(direct) / 1e3) / 1e6,
+        "phase_ms": {k: float(np.median(v)) for k, v in per.items()},
+        "views": len(cams), "pixels": P, "surfels": int(ds.n),
+        "active_sizes": [int(b["m"]) for b in br.keep], "intersections": [int(k) for k in kv],
+        "resolutions": sorted({f"{c.width}x{c.height}" for c in cams}),
+        "tiles": [f"{t[0]}x{t[1]}" for t in tiles], "autotune_ms": sweep,
+        "autotune_s": tune_s, "loss": [float(x) for x in loss.cpu().numpy()],
+        "pairs": {"evaluated": int(E[0]), "inside_cutoff": int(E[1]), "blended": int(E[2])},
+        "roofline": [
+            {"kernel": "fwd_batch_kernel (persistent)", "bound": "alu",
+             "achieved": w_f / tf / 1e12, "peak": peak, "unit": "TFLOP/s",
+             "frac": w_f / tf / 1e12 / peak, "launch_ms": tf * 1e3},
+            {"kernel": "bwd_batch_kernel (persistent) + per-view surfel reductions",
+             "bound": "alu", "achieved": w_b / tb / 1e12, "peak": peak, "unit": "TFLOP/s",
+             "frac": w_b / tb / 1e12 / peak, "launch_ms": tb * 1e3,
+             "note": "flops count the pose-chain work per blended pair only (a lower bound)"}],
+        "launch": "one CUDA graph per step",
+        "peak_mem_gb": torch.cuda.max_memory_allocated() / 1e9,
+    }
+    del graph, br, ds
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch_workloads(K, W_, flush):
+    """The mapping window (1M surfels, 8 keyframes at 1200x680 on a smooth
+    trajectory) and the uneven batch (32 views of a 2M-surfel room, mixed
+    resolutions, active subsets of 50k-1M surfels)."""
+    from paper_2506_00970_gb300 import scenes
+    s1 = scenes.room_scene(1, MAP_SURFELS)
+    cams = [scenes.mapping_camera()] * MAP_VIEWS
+    poses = scenes.room_trajectory(2, MAP_VIEWS)
+    mw = measure_batch("mapping window", s1, cams, poses, None, K, W_, flush, 31)
+    mw["workload"] = (f"mapping window: {MAP_SURFELS} surfels, {MAP_VIEWS} keyframes 1200x680 "
+                      f"fx=fy=600 on a smooth trajectory, colour L1 + {MAP_W_D} depth L1 + "
+                      f"{MAP_W_N} normal consistency, gradients to all surfel parameters")
+    del s1
+    s2 = scenes.room_scene(3, UNEVEN_SURFELS)
+    cams, poses, actives = scenes.uneven_batch(4, s2, UNEVEN_VIEWS)
+    ub = measure_batch("uneven batch", s2, cams, poses, actives, K, W_, flush, 47)
+    ub["workload"] = (f"uneven batch: {UNEVEN_VIEWS} views of a {UNEVEN_SURFELS}-surfel room, "
+                      "resolutions from {320x240, 640x480, 1200x680}, active subsets of "
+                      "50k-1M surfels (log-uniform), same loss as the mapping window")
+    return {"mapping_window": mw, "uneven_batch": ub}
 
 
 def cpu_baseline(s, cam, fr):

@@ -79,7 +79,9 @@ typedef struct {
  * alpha_min = 1/255 (skip), alpha_max = 0.99 (clamp), t_min = 1e-4 (stop
  * before the transmittance would fall below it) and cutoff_r2 = 9
  * (u^2 + v^2 beyond three standard deviations is skipped).  tile_w x tile_h
- * is one of 16x16, 8x32, 32x8; px_per_thread in {1, 2, 4} (autotuned). */
+ * is one of 16x16, 8x32, 32x8 (one thread per pixel, a 256-thread block per
+ * tile; the batch autotuner picks the shape per resolution class);
+ * px_per_thread must be 1 (other values return GS2D_ERR_INVALID_ARG). */
 typedef struct {
   int tile_w, tile_h, px_per_thread;
   float alpha_min, alpha_max, t_min, cutoff_r2;

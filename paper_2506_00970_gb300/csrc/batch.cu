@@ -128,7 +128,8 @@ int view_tiles(const gs2d_view& w, int* tx) {
 
 int check_view(const gs2d_view& w) {
   if (w.cam.width <= 0 || w.cam.height <= 0) return GS2D_ERR_INVALID_ARG;
-  if (w.cfg.tile_w * w.cfg.tile_h != kTileThreads || w.cfg.tile_w % 8 || w.cfg.tile_h % 4)
+  if (w.cfg.tile_w * w.cfg.tile_h != kTileThreads || w.cfg.tile_w <= 0 || w.cfg.tile_w % 8 ||
+      w.cfg.tile_h <= 0 || w.cfg.tile_h % 4 || w.cfg.px_per_thread != 1)
     return GS2D_ERR_INVALID_ARG;
   int tx;
   const long long nt = view_tiles(w, &tx);

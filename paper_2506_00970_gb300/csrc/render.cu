@@ -354,7 +354,9 @@ BwdWs carve_bwd_ws(void* base, int n, size_t cap, int n_tiles, bool full) {
 
 int validate_tile_cfg(const gs2d_camera* cam, const gs2d_config* cfg) {
   if (!cam || !cfg) return GS2D_ERR_INVALID_ARG;
-  if (cfg->tile_w * cfg->tile_h != kTileThreads || cfg->tile_w <= 0 || cfg->tile_h <= 0)
+  // one thread per pixel; warps cover 8 x 4 pixel blocks of the tile
+  if (cfg->tile_w * cfg->tile_h != kTileThreads || cfg->tile_w <= 0 || cfg->tile_h <= 0 ||
+      cfg->tile_w % 8 || cfg->tile_h % 4 || cfg->px_per_thread != 1)
     return GS2D_ERR_INVALID_ARG;
   if (cam->width <= 0 || cam->height <= 0) return GS2D_ERR_INVALID_ARG;
   const long long nt = (long long)gs2d_tiles_x(cam, cfg) * gs2d_tiles_y(cam, cfg);

@@ -367,7 +367,6 @@ class BatchRasterizer:
         self.device = device
         self.nv = len(cams)
         assert 0 < self.nv <= MAX_VIEWS
-        self.views = []
         self.keep = []
         f = dict(dtype=torch.float32, device=device)
         for v, cam in enumerate(cams):
@@ -378,13 +377,10 @@ class BatchRasterizer:
             ccam = camera(cam)
             tx = int(lib().gs2d_tiles_x(_ref(ccam), _ref(cfg)))
             ty = int(lib().gs2d_tiles_y(_ref(ccam), _ref(cfg)))
-            cap = int(capacities[v]) if capacities else max(8 * m, 1024)
             H, W = int(cam.height), int(cam.width)
             b = dict(pose=torch.empty(12, **f), active=act,
                      proj=torch.empty(max(m, 1) * PROJ_FLOATS, **f),
                      tiles=torch.empty(max(m, 1), dtype=torch.int32, device=device),
-                     vals=torch.empty(cap, dtype=torch.int32, device=device),
-                     emit=torch.empty(cap, dtype=torch.int32, device=device),
                      off=torch.empty(max(m, 1), dtype=torch.int32, device=device),
                      ranges=torch.empty(2 * tx * ty, dtype=torch.int32, device=device),
                      n_isect=torch.zeros(1, dtype=torch.int32, device=device),
@@ -395,28 +391,67 @@ class BatchRasterizer:
                      n_last=torch.empty(H, W, dtype=torch.int32, device=device),
                      d_rgb=torch.zeros(H, W, 3, **f), d_depth=torch.zeros(H, W, **f),
                      d_normal=torch.zeros(H, W, 3, **f), d_opacity=torch.zeros(H, W, **f),
-                     d_pose6=torch.zeros(6, **f), m=m, cap=cap, cam=cam, cfg=cfg)
-            bins = Bins(None, b["vals"].data_ptr(), b["emit"].data_ptr(), b["off"].data_ptr(),
-                        b["ranges"].data_ptr(), b["n_isect"].data_ptr(), b["status"].data_ptr(), cap)
-            view = View(ccam, cfg, b["pose"].data_ptr(), _ptr(act).value if act is not None else None,
-                        m, b["proj"].data_ptr(), b["tiles"].data_ptr(), bins, b["rgb"].data_ptr(),
-                        b["depth"].data_ptr(), b["normal"].data_ptr(), b["opacity"].data_ptr(),
-                        b["t_final"].data_ptr(), b["n_last"].data_ptr(), b["d_rgb"].data_ptr(),
-                        b["d_depth"].data_ptr(), b["d_normal"].data_ptr(),
-                        b["d_opacity"].data_ptr(), b["d_pose6"].data_ptr())
-            self.views.append(view)
+                     d_pose6=torch.zeros(6, **f), m=m, cam=cam, ccam=ccam, cfg=cfg,
+                     n_tiles=tx * ty)
+            self._alloc_bins(b, int(capacities[v]) if capacities else max(8 * m, 1024))
             self.keep.append(b)
-        self.sort_ws = _bytes(lib().gs2d_bin_sort_batch_workspace(
-            (View * self.nv)(*self.views), self.nv, self.n), device)
-        self.render_ws = _bytes(lib().gs2d_render_batch_workspace(
-            (View * self.nv)(*self.views), self.nv, self.n), device)
+        self._rebuild()
         self.grads = dict(mu=torch.empty(self.n, 3, **f), quat=torch.empty(self.n, 4, **f),
                           scale=torch.empty(self.n, 2, **f), opacity=torch.empty(self.n, **f),
                           rgb=torch.empty(self.n, 3, **f))
 
+    def _alloc_bins(self, b, cap):
+        b["cap"] = int(cap)
+        b["vals"] = torch.empty(b["cap"], dtype=torch.int32, device=self.device)
+        b["emit"] = torch.empty(b["cap"], dtype=torch.int32, device=self.device)
+
+    def _rebuild(self):
+        """The C view table and the batch workspaces from the buffers."""
+        self.views = []
+        for b in self.keep:
+            act = b["active"]
+            bins = Bins(None, b["vals"].data_ptr(), b["emit"].data_ptr(), b["off"].data_ptr(),
+                        b["ranges"].data_ptr(), b["n_isect"].data_ptr(), b["status"].data_ptr(),
+                        b["cap"])
+            b["bins"] = bins
+            self.views.append(View(
+                b["ccam"], b["cfg"], b["pose"].data_ptr(),
+                _ptr(act).value if act is not None else None, b["m"], b["proj"].data_ptr(),
+                b["tiles"].data_ptr(), bins, b["rgb"].data_ptr(), b["depth"].data_ptr(),
+                b["normal"].data_ptr(), b["opacity"].data_ptr(), b["t_final"].data_ptr(),
+                b["n_last"].data_ptr(), b["d_rgb"].data_ptr(), b["d_depth"].data_ptr(),
+                b["d_normal"].data_ptr(), b["d_opacity"].data_ptr(), b["d_pose6"].data_ptr()))
+        arr = (View * self.nv)(*self.views)
+        self.sort_ws = None
+        self.render_ws = None
+        self.sort_ws = _bytes(lib().gs2d_bin_sort_batch_workspace(arr, self.nv, self.n),
+                              self.device)
+        self.render_ws = _bytes(lib().gs2d_render_batch_workspace(arr, self.nv, self.n),
+                                self.device)
+
     def set_poses(self, poses):
         for b, p in zip(self.keep, poses):
             b["pose"].copy_(p if isinstance(p, torch.Tensor) else pose_tensor(p, self.device))
+
+    def fit(self, surf: DeviceSurfels, margin: float = 1.25, stream=None):
+        """Project and bin at the current poses and regrow every view whose
+        intersection count exceeded its capacity (to margin x the count).
+        Returns the counts K per view."""
+        for b in self.keep:
+            b["status"].zero_()
+        gs2d_project_batch(surf, self.views, stream)
+        gs2d_bin_sort_batch(self.views, self.n, self.sort_ws, stream)
+        k = [int(b["n_isect"].item()) for b in self.keep]
+        grow = False
+        for b, kv in zip(self.keep, k):
+            if kv > b["cap"]:
+                self._alloc_bins(b, int(kv * margin) + 1024)
+                grow = True
+        if grow:
+            self._rebuild()
+        for b in self.keep:
+            b["status"].zero_()
+        return k
 
     def forward(self, surf: DeviceSurfels, stream=None, check_status=True):
         for b in self.keep:

@@ -305,6 +305,31 @@ def uneven_cameras(seed: int, n_views: int):
     return cams
 
 
+def active_subset(s: Surfels, pose: Pose, size: int, reach: float = 1.5) -> np.ndarray:
+    """An active-map subset for one view: the ``size`` surfels nearest to a
+    point ``reach`` metres ahead of the camera along its optical axis (a ball
+    around the viewed region, grown until it holds ``size`` surfels), as
+    sorted int32 ids."""
+    eye = -pose.R.T @ pose.t
+    ahead = eye + reach * pose.R[2]
+    d2 = np.sum((s.mu - ahead) ** 2, axis=1)
+    size = min(int(size), s.n)
+    ids = np.argpartition(d2, size - 1)[:size] if size < s.n else np.arange(s.n)
+    return np.sort(ids).astype(np.int32)
+
+
+def uneven_batch(seed: int, s: Surfels, n_views: int = 32, sizes=(50_000, 1_000_000)):
+    """Views of one room for the uneven batch: resolution drawn from
+    {320x240, 640x480, 1200x680}, a pose from the room's camera zone, and an
+    active subset whose size is log-uniform in ``sizes``."""
+    rng = np.random.default_rng(seed)
+    cams = uneven_cameras(seed, n_views)
+    poses = [room_pose(10_000 + 97 * seed + v) for v in range(n_views)]
+    lo, hi = np.log(sizes[0]), np.log(sizes[1])
+    actives = [active_subset(s, p, int(np.exp(rng.uniform(lo, hi)))) for p in poses]
+    return cams, poses, actives
+
+
 # --------------------------------------------------------------------------
 # generic random tensors for kernel-level tests
 # --------------------------------------------------------------------------

@@ -150,3 +150,68 @@ def test_batch_capacity_error_is_per_view(torch_cuda):
     with pytest.raises(gs2d.Gs2dError):
         br.forward(ds)
     assert int(br.keep[0]["status"].item()) == 3 and int(br.keep[1]["status"].item()) == 0
+
+
+def test_batch_fit_grows_capacity_and_graph_replay_is_bit_identical(torch_cuda):
+    """fit() regrows views whose intersections overflow; a whole batched
+    step (forward + backward) captured in a CUDA graph and replayed
+    reproduces the direct calls bit for bit."""
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d
+    s, cams, poses, actives, tiles = _setup(n_views=3)
+    ds = gs2d.DeviceSurfels(s)
+    br = gs2d.BatchRasterizer(cams, s.n, actives=actives, tiles=tiles, capacities=[64, 64, 64])
+    br.set_poses(poses)
+    k = br.fit(ds)
+    assert all(kv > 64 for kv in k)
+    assert all(b["cap"] >= kv for b, kv in zip(br.keep, k))
+    for v, b in enumerate(br.keep):
+        up = scenes.random_upstream(40 + v, cams[v].height, cams[v].width)
+        b["d_rgb"].copy_(torch.tensor(up[0], dtype=torch.float32))
+        b["d_depth"].copy_(torch.tensor(up[1], dtype=torch.float32))
+
+    def step():
+        br.forward(ds, check_status=False)
+        br.backward(ds)
+
+    br.forward(ds)
+    g = br.backward(ds)
+    torch.cuda.synchronize()
+    ref = {k: v.clone() for k, v in g.items()}
+    ref_img = [b["rgb"].clone() for b in br.keep]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for _ in range(2):
+        for t in g.values():
+            t.fill_(float("nan"))
+        graph.replay()
+        torch.cuda.synchronize()
+        assert all(int(b["status"].item()) == 0 for b in br.keep)
+        for k in ref:
+            assert torch.equal(g[k], ref[k]), k
+        for b, im in zip(br.keep, ref_img):
+            assert torch.equal(b["rgb"], im)
+
+
+def test_autotune_picks_a_candidate_and_caches(torch_cuda, tmp_path):
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import autotune, gs2d
+    s, cams, poses, actives, _ = _setup(n_views=2)
+    ds = gs2d.DeviceSurfels(s)
+    path = str(tmp_path / "tune.json")
+    autotune._cache.clear()
+    tiles, table = autotune.tune_tiles(ds, cams, poses, actives, reps=1, cache_path=path)
+    assert all(t in autotune.TILE_SHAPES for t in tiles)
+    assert set(table) == {f"{c.width}x{c.height}" for c in cams}
+    for c, t in zip(cams, tiles):
+        row = table[f"{c.width}x{c.height}"]
+        assert row[f"{t[0]}x{t[1]}"] == min(row.values())
+    autotune._cache.clear()
+    tiles2, table2 = autotune.tune_tiles(ds, cams, poses, actives, cache_path=path)
+    assert tiles2 == tiles and table2 == {}

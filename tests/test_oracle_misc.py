@@ -237,3 +237,22 @@ def test_tile_rects_cover_surfels_reaching_past_the_camera_plane(orc):
         assert r[0] <= xs.min() // 8 and r[2] >= xs.max() // 8
         assert r[1] <= ys.min() // 8 and r[3] >= ys.max() // 8
     assert covered > 10
+
+
+def test_active_subset_is_the_nearest_ball():
+    """The active-map subset of a view holds exactly the requested number of
+    surfels, sorted, and every chosen surfel is at least as close to the
+    point ahead of the camera as every surfel left out."""
+    s = scenes.room_scene(5, 20_000)
+    pose = scenes.room_pose(7)
+    ids = scenes.active_subset(s, pose, 3000, reach=1.5)
+    assert ids.dtype == np.int32 and len(ids) == 3000 and np.all(np.diff(ids) > 0)
+    eye = -pose.R.T @ pose.t
+    ahead = eye + 1.5 * pose.R[2]
+    d = np.linalg.norm(s.mu - ahead, axis=1)
+    out = np.setdiff1d(np.arange(s.n), ids)
+    assert d[ids].max() <= d[out].min()
+    cams, poses, acts = scenes.uneven_batch(1, s, n_views=6, sizes=(500, 5000))
+    assert len(cams) == len(poses) == len(acts) == 6
+    assert all(500 <= len(a) <= 5000 for a in acts)
+    assert {(c.width, c.height) for c in cams} <= {(320, 240), (640, 480), (1200, 680)}
