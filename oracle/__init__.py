@@ -23,6 +23,10 @@ Contents (each cites the passage it follows):
     mapping loss of Sec. III-E without the SSIM term.
   * ``track``                    -- the frame-to-map tracking loop of
     Sec. III-D: render, loss, pose gradient, AdamW, retraction.
+  * ``net`` (oracle/net.py)      -- the learned tracking-pose proposal
+    network (not in the paper; it replaces the starting pose of the loop of
+    Sec. III-D): convolutions, MLP, loss, their reverse mode, input packing
+    and the se(3) target.
 Parity pins live in ``tests/test_oracle_*.py``.  The convergence *rate* of
 ``track`` is "parity unpinned": the paper prints no per-iteration numbers.
 """

@@ -330,6 +330,16 @@ def uneven_batch(seed: int, s: Surfels, n_views: int = 32, sizes=(50_000, 1_000_
     return cams, poses, actives
 
 
+def net_init(seed: int, blocks) -> np.ndarray:
+    """Seeded initial parameters of a network as one flat float32 vector:
+    ``blocks`` is a list of (count, fan_in); a block with fan_in > 0 is drawn
+    from N(0, 2 / fan_in) (He initialisation), one with fan_in == 0 is zero."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0.0, math.sqrt(2.0 / f), int(c)) if f > 0 else np.zeros(int(c))
+             for c, f in blocks]
+    return np.concatenate(parts).astype(np.float32)
+
+
 # --------------------------------------------------------------------------
 # generic random tensors for kernel-level tests
 # --------------------------------------------------------------------------
