@@ -49,6 +49,8 @@ TRAFFIC_BYTES = {"track_tile": 6317056}
 MAP_SURFELS, MAP_VIEWS = 1_000_000, 8
 UNEVEN_SURFELS, UNEVEN_VIEWS = 2_000_000, 32
 MAP_W_D, MAP_W_N = 0.5, 0.02
+# learned proposal: training pairs, AdamW steps at batch 256, held-out frames
+PROP_PAIRS, PROP_STEPS, PROP_EVAL_FRAMES = 100_000, 3000, 256
 
 
 def _args():
@@ -357,6 +359,7 @@ def run_ours(args):
     roof = roofline(r, ds, frames, cam, cfg, stream, ms_iter, fused_ms)
     del graph
     batch = batch_workloads(K, W_, flush)
+    tracking["learned_proposal"] = learned_proposal(flush)
 
     if rank == 0:
         clocks = clk.summary()
@@ -621,6 +624,74 @@ def batch_workloads(K, W_, flush):
                       "resolutions from {320x240, 640x480, 1200x680}, active subsets of "
                       "50k-1M surfels (log-uniform), same loss as the mapping window")
     return {"mapping_window": mw, "uneven_batch": ub}
+
+
+def net_flops_per_sample():
+    """Algorithmic FLOPs of the proposal network per sample (2 per
+    multiply-add): forward; training = forward + weight gradients (same
+    products) + data gradients (all but the first layer's)."""
+    hw = [(120, 160), (60, 80), (30, 40), (15, 20), (8, 10), (4, 5), (2, 3)]
+    ch = [8, 32, 64, 128, 256, 256, 256]
+    conv = [2 * hw[l + 1][0] * hw[l + 1][1] * ch[l + 1] * 9 * ch[l] for l in range(6)]
+    fc = [2 * 1536 * 256, 2 * 256 * 6]
+    fwd = sum(conv) + sum(fc)
+    return fwd, fwd + fwd + (fwd - conv[0])
+
+
+def learned_proposal(flush):
+    """Train the proposal network on self-rendered pairs (4 rooms, 160x120,
+    perturbations up to 5 cm / 3 deg) and compare tracking from the proposal
+    with the plain loop on frames of a held-out room."""
+    import torch
+    from paper_2506_00970_gb300 import gs2d, proposal, scenes
+    t0 = time.perf_counter()
+    rooms = [scenes.room_scene(100 + r, N_SURFELS) for r in range(4)]
+    X, Y = proposal.make_pairs(rooms, PROP_PAIRS, seed=1)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    tr = proposal.Trainer(seed=0, batch=256)
+    t0 = time.perf_counter()
+    hist = tr.fit(X, Y, PROP_STEPS, lr=1e-3, log_every=PROP_STEPS // 4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # tensor-core throughput of the network kernels (batch 256)
+    stream = torch.cuda.current_stream()
+    y = torch.empty(256, 6, device="cuda")
+    fwd_ms, step_ms = [], []
+    for k in range(8):
+        sl = slice(256 * k, 256 * (k + 1))
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        gs2d.gs2d_net_forward(tr.params, X[sl], y, tr.ws)
+        e[1].record(stream)
+        gs2d.gs2d_net_grad(tr.params, X[sl], Y[sl], tr.loss, tr.grad, tr.ws)
+        gs2d.gs2d_net_adamw(tr.params, tr.grad, tr.m, tr.v, tr.step + 1, lr=0.0)
+        e[2].record(stream)
+        e[2].synchronize()
+        if k >= 2:
+            fwd_ms.append(e[0].elapsed_time(e[1]))
+            step_ms.append(e[1].elapsed_time(e[2]))
+    del X, Y
+    torch.cuda.empty_cache()
+    ev = proposal.evaluate(scenes.room_scene(200, N_SURFELS), tr.params, PROP_EVAL_FRAMES, seed=3)
+    fl_f, fl_t = net_flops_per_sample()
+    pk, _ = peaks()
+    peak = float(pk.get("bf16_tflops", 1900.0))
+    f_ms, s_ms = float(np.median(fwd_ms)), float(np.median(step_ms))
+    ev.update({
+        "train_pairs": PROP_PAIRS, "train_steps": PROP_STEPS, "batch": 256,
+        "pair_gen_s": gen_s, "train_s": train_s, "train_loss": hist,
+        "held_out_room": "room seed 200 (training rooms 100-103)",
+        "net": {"fwd_batch256_ms": f_ms, "train_step_batch256_ms": s_ms,
+                "fwd_gflop_per_batch": fl_f * 256 / 1e9, "train_gflop_per_batch": fl_t * 256 / 1e9,
+                "roofline": {"kernel": "gemm_kernel (mma.sync bf16, all layers)", "bound": "tensor",
+                             "achieved": fl_f * 256 / (f_ms / 1e3) / 1e12, "peak": peak,
+                             "unit": "TFLOP/s", "frac": fl_f * 256 / (f_ms / 1e3) / 1e12 / peak,
+                             "train_achieved": fl_t * 256 / (s_ms / 1e3) / 1e12,
+                             "peak_note": "dense bf16, of measured (cuBLAS burst)"}},
+    })
+    return ev
 
 
 def cpu_baseline(s, cam, fr):

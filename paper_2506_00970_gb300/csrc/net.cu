@@ -1,0 +1,888 @@
+// Learned tracking-pose proposal network (not in the paper; it proposes the
+// starting pose of the tracking loop of Sec. III-D): forward, loss,
+// backward and AdamW on BF16 tensor cores with FP32 accumulation.
+//
+// Every contraction of the network -- each convolution's forward (implicit
+// im2col GEMM), data gradient (stride-2 transposed gather) and weight
+// gradient (split-K GEMM over the pixels), and each fully connected layer's
+// three products -- runs through one tiled GEMM kernel
+//     C[M, N] = sum_k A[m, k] B[n, k]
+// whose operand tiles are gathered straight from the NHWC activations and
+// the weights by an address mode (no im2col buffer is materialised):
+//   K-major modes (8 consecutive k of one row are contiguous):
+//     K_DENSE   row-major [rows][ld] matrix
+//     K_IM2COL  conv forward: row = (b, oy, ox), k = tap * C + c
+//     K_DGRAD   conv data gradient: row = input pixel (b, iy, ix),
+//               k = tap * C_out + co, reading dZ at ((iy + 1 - ky) / 2,
+//               (ix + 1 - kx) / 2) when both are even and in range
+//   row-major modes (8 consecutive rows of one k are contiguous):
+//     R_DENSE   element (row, k) at p[k * ld + row]
+//     R_IM2COL  conv weight gradient: row = tap * C + c, k = (b, oy, ox)
+//     R_WT      conv weights read transposed: row = c_in, k = tap * C_out + co
+// Tiles of 128 x 64 x 32 move global -> shared memory with 16-byte cp.async
+// (zero-filled where the gather falls outside), three stages deep; warps
+// read fragments with ldmatrix (.trans for row-major tiles) and issue
+// mma.m16n8k16 bf16 x bf16 -> f32.  Epilogues: bias + ReLU -> bf16, bias ->
+// f32, ReLU mask of the stored activation -> bf16, or FP32 split-K partials
+// that a second kernel sums in a fixed order.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "gs2d_common.cuh"
+#include "gs2d_net.h"
+#include "track_update.cuh"
+
+namespace gs2d {
+namespace net {
+
+typedef __nv_bfloat16 bf16;
+
+enum Mode { K_DENSE = 0, K_IM2COL = 1, K_DGRAD = 2, R_DENSE = 3, R_IM2COL = 4, R_WT = 5 };
+enum Epi { E_BIAS_RELU = 0, E_BIAS_F32 = 1, E_MASK = 2, E_PARTIAL = 3 };
+
+constexpr int BM = 128, BN = 64, BK = 32, STAGES = 3, THREADS = 256, PAD = 8;
+constexpr int kLayers = GS2D_NET_LAYERS;
+constexpr int kConv = 6;
+constexpr int kCin[kConv] = {8, 32, 64, 128, 256, 256};
+constexpr int kCout[kConv] = {32, 64, 128, 256, 256, 256};
+constexpr int kHin[kConv + 1] = {120, 60, 30, 15, 8, 4, 2};
+constexpr int kWin[kConv + 1] = {160, 80, 40, 20, 10, 5, 3};
+constexpr int kFlat = 2 * 3 * 256;
+constexpr int kHidden = 256;
+constexpr int kOut = GS2D_NET_OUT;
+constexpr int kOutPad = 8;  // FC2 rows padded to 8 in the bf16 weight copy
+
+struct Operand {
+  const bf16* p;
+  int ld;                // dense modes: leading dimension; R_WT: C_out
+  int rows;              // valid rows (M or N); multiple of 8 for row-major modes
+  int H, W, C, Ho, Wo;   // conv geometry (input H x W x C, output Ho x Wo)
+};
+
+struct Gemm {
+  int M, N, K, k_split;
+  Operand a, b;
+  void* out;
+  int ldc;
+  const float* bias;
+  const bf16* mask;
+  int n_valid;
+};
+
+template <int MODE>
+__device__ __forceinline__ const bf16* kmajor_addr(const Operand& o, int row, int k, int kend) {
+  if (row >= o.rows || k >= kend) return nullptr;
+  if (MODE == K_DENSE) return o.p + (size_t)row * o.ld + k;
+  if (MODE == K_IM2COL) {
+    const int hw = o.Ho * o.Wo;
+    const int b = row / hw, r = row - b * hw, oy = r / o.Wo, ox = r - oy * o.Wo;
+    const int tap = k / o.C, c = k - tap * o.C, ky = tap / 3, kx = tap - ky * 3;
+    const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
+    if (iy < 0 || iy >= o.H || ix < 0 || ix >= o.W) return nullptr;
+    return o.p + (((size_t)b * o.H + iy) * o.W + ix) * o.C + c;
+  }
+  // K_DGRAD
+  const int hw = o.H * o.W;
+  const int b = row / hw, r = row - b * hw, iy = r / o.W, ix = r - iy * o.W;
+  const int tap = k / o.C, c = k - tap * o.C, ky = tap / 3, kx = tap - ky * 3;
+  const int ty = iy + 1 - ky, tx = ix + 1 - kx;
+  if (ty < 0 || tx < 0 || (ty & 1) || (tx & 1)) return nullptr;
+  const int oy = ty >> 1, ox = tx >> 1;
+  if (oy >= o.Ho || ox >= o.Wo) return nullptr;
+  return o.p + (((size_t)b * o.Ho + oy) * o.Wo + ox) * o.C + c;
+}
+
+template <int MODE>
+__device__ __forceinline__ const bf16* rowmajor_addr(const Operand& o, int row0, int k, int kend) {
+  if (row0 >= o.rows || k >= kend) return nullptr;
+  if (MODE == R_DENSE) return o.p + (size_t)k * o.ld + row0;
+  if (MODE == R_IM2COL) {
+    const int tap = row0 / o.C, c = row0 - tap * o.C, ky = tap / 3, kx = tap - ky * 3;
+    const int hw = o.Ho * o.Wo;
+    const int b = k / hw, r = k - b * hw, oy = r / o.Wo, ox = r - oy * o.Wo;
+    const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
+    if (iy < 0 || iy >= o.H || ix < 0 || ix >= o.W) return nullptr;
+    return o.p + (((size_t)b * o.H + iy) * o.W + ix) * o.C + c;
+  }
+  // R_WT
+  const int tap = k / o.ld, co = k - tap * o.ld;
+  return o.p + ((size_t)co * 9 + tap) * o.C + row0;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void* p) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(s));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t r[4], const void* p) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(s));
+}
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int MODE>
+__host__ __device__ constexpr bool is_kmajor() {
+  return MODE <= K_DGRAD;
+}
+template <int MODE, int ROWS>
+__host__ __device__ constexpr int tile_elems() {
+  return is_kmajor<MODE>() ? ROWS * (BK + PAD) : BK * (ROWS + PAD);
+}
+
+// One stage: ROWS x BK tile of an operand into shared memory.
+template <int MODE, int ROWS>
+__device__ __forceinline__ void load_tile(bf16* s, const Operand& o, int r0, int k0, int kend) {
+  constexpr int kVec = ROWS * BK / 8;
+  for (int v = threadIdx.x; v < kVec; v += THREADS) {
+    if (is_kmajor<MODE>()) {
+      const int r = v >> 2, kq = (v & 3) * 8;
+      const bf16* src = kmajor_addr<MODE>(o, r0 + r, k0 + kq, kend);
+      cp_async16(s + r * (BK + PAD) + kq, src ? src : o.p, src != nullptr);
+    } else {
+      const int kk = v / (ROWS / 8), rq = (v % (ROWS / 8)) * 8;
+      const bf16* src = rowmajor_addr<MODE>(o, r0 + rq, k0 + kk, kend);
+      cp_async16(s + kk * (ROWS + PAD) + rq, src ? src : o.p, src != nullptr);
+    }
+  }
+}
+
+// A fragment of the m16 x k16 sub-tile at (r0, k0) of a stage.
+template <int MODE, int ROWS>
+__device__ __forceinline__ void frag_a(uint32_t a[4], const bf16* s, int r0, int k0) {
+  const int l = threadIdx.x & 31, i = l >> 3, rr = l & 7;
+  if (is_kmajor<MODE>())
+    ldsm_x4(a, s + (r0 + rr + 8 * (i & 1)) * (BK + PAD) + k0 + 8 * (i >> 1));
+  else
+    ldsm_x4_t(a, s + (k0 + 8 * (i >> 1) + rr) * (ROWS + PAD) + r0 + 8 * (i & 1));
+}
+// B fragments of two n8 x k16 sub-tiles at (n0, k0), (n0 + 8, k0).
+template <int MODE, int ROWS>
+__device__ __forceinline__ void frag_b(uint32_t b[4], const bf16* s, int n0, int k0) {
+  const int l = threadIdx.x & 31, i = l >> 3, rr = l & 7;
+  if (is_kmajor<MODE>())
+    ldsm_x4(b, s + (n0 + rr + 8 * (i >> 1)) * (BK + PAD) + k0 + 8 * (i & 1));
+  else
+    ldsm_x4_t(b, s + (k0 + 8 * (i & 1) + rr) * (ROWS + PAD) + n0 + 8 * (i >> 1));
+}
+
+template <int EPI>
+__device__ __forceinline__ void store2(const Gemm& g, int row, int col, float v0, float v1) {
+  if (row >= g.M) return;
+  if (EPI == E_BIAS_RELU) {
+    if (col >= g.N) return;
+    const float x0 = fmaxf(v0 + g.bias[col], 0.f), x1 = fmaxf(v1 + g.bias[col + 1], 0.f);
+    *reinterpret_cast<__nv_bfloat162*>(static_cast<bf16*>(g.out) + (size_t)row * g.ldc + col) =
+        __floats2bfloat162_rn(x0, x1);
+  } else if (EPI == E_BIAS_F32) {
+    float* o = static_cast<float*>(g.out) + (size_t)row * g.ldc;
+    if (col < g.n_valid) o[col] = v0 + g.bias[col];
+    if (col + 1 < g.n_valid) o[col + 1] = v1 + g.bias[col + 1];
+  } else if (EPI == E_MASK) {
+    if (col >= g.N) return;
+    const size_t off = (size_t)row * g.ldc + col;
+    const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(g.mask + off);
+    const float x0 = __bfloat162float(m.x) > 0.f ? v0 : 0.f;
+    const float x1 = __bfloat162float(m.y) > 0.f ? v1 : 0.f;
+    *reinterpret_cast<__nv_bfloat162*>(static_cast<bf16*>(g.out) + off) = __floats2bfloat162_rn(x0, x1);
+  } else {
+    if (col >= g.N) return;
+    float* o = static_cast<float*>(g.out) + ((size_t)blockIdx.z * g.M + row) * g.N + col;
+    *reinterpret_cast<float2*>(o) = make_float2(v0, v1);
+  }
+}
+
+// grid: (ceil(M / BM), ceil(N / BN), splits); 256 threads = 4 (M) x 2 (N)
+// warps of 32 x 32 outputs each.
+template <int AM, int BMODE, int EPI>
+__global__ void __launch_bounds__(THREADS) gemm_kernel(const Gemm g) {
+  constexpr int kA = tile_elems<AM, BM>(), kB = tile_elems<BMODE, BN>();
+  __shared__ __align__(128) bf16 smem[STAGES * (kA + kB)];
+  bf16* sA = smem;
+  bf16* sB = smem + STAGES * kA;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int kbeg = blockIdx.z * g.k_split;
+  const int kend = min(g.K, kbeg + g.k_split);
+  const int ntiles = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+  const int warp = threadIdx.x >> 5, wm = (warp & 3) * 32, wn = (warp >> 2) * 32;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+#pragma unroll
+  for (int s = 0; s < STAGES - 1; ++s) {
+    if (s < ntiles) {
+      load_tile<AM, BM>(sA + s * kA, g.a, m0, kbeg + s * BK, kend);
+      load_tile<BMODE, BN>(sB + s * kB, g.b, n0, kbeg + s * BK, kend);
+    }
+    cp_async_commit();
+  }
+  for (int kt = 0; kt < ntiles; ++kt) {
+    cp_async_wait<STAGES - 2>();
+    __syncthreads();
+    const int nk = kt + STAGES - 1;
+    if (nk < ntiles) {
+      const int st = nk % STAGES;
+      load_tile<AM, BM>(sA + st * kA, g.a, m0, kbeg + nk * BK, kend);
+      load_tile<BMODE, BN>(sB + st * kB, g.b, n0, kbeg + nk * BK, kend);
+    }
+    cp_async_commit();
+    const bf16* a_s = sA + (kt % STAGES) * kA;
+    const bf16* b_s = sB + (kt % STAGES) * kB;
+#pragma unroll
+    for (int ks = 0; ks < BK; ks += 16) {
+      uint32_t af[2][4], bfr[2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) frag_a<AM, BM>(af[i], a_s, wm + 16 * i, ks);
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) frag_b<BMODE, BN>(bfr[jj], b_s, wn + 16 * jj, ks);
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          mma_bf16(acc[i][j], af[i], bfr[j >> 1][2 * (j & 1)], bfr[j >> 1][2 * (j & 1) + 1]);
+    }
+  }
+  cp_async_wait<0>();
+  const int l = threadIdx.x & 31, gq = l >> 2, cq = l & 3;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int row = m0 + wm + 16 * i + gq, col = n0 + wn + 8 * j + 2 * cq;
+      store2<EPI>(g, row, col, acc[i][j][0], acc[i][j][1]);
+      store2<EPI>(g, row + 8, col, acc[i][j][2], acc[i][j][3]);
+    }
+}
+
+// out[m * n_out + n] = sum_s part[(s * M + m) * N + n] for m < m_valid,
+// n < n_valid, summed in split order.
+__global__ void reduce_partials_kernel(const float* __restrict__ part, int S, int M, int N,
+                                       int m_valid, int n_valid, float* __restrict__ out) {
+  const size_t total = (size_t)m_valid * n_valid;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e / n_valid), n = (int)(e % n_valid);
+    float acc = 0.f;
+    for (int s = 0; s < S; ++s) acc += part[((size_t)s * M + m) * N + n];
+    out[e] = acc;
+  }
+}
+
+// Column sums of a bf16 matrix [rows][C] (C divides 256) over row chunks:
+// part[chunk * C + c]; rows of a chunk are summed in a fixed order.
+__global__ void __launch_bounds__(256) colsum_partial_kernel(const bf16* __restrict__ z, int rows,
+                                                             int C, int rows_per_block,
+                                                             float* __restrict__ part) {
+  __shared__ float s[256];
+  const int t = threadIdx.x, nsub = 256 / C, col = t % C, sub = t / C;
+  const int r0 = blockIdx.x * rows_per_block, r1 = min(rows, r0 + rows_per_block);
+  float acc = 0.f;
+  for (int r = r0 + sub; r < r1; r += nsub) acc += __bfloat162float(z[(size_t)r * C + col]);
+  s[t] = acc;
+  __syncthreads();
+  if (t < C) {
+    float tot = 0.f;
+    for (int k = 0; k < nsub; ++k) tot += s[k * C + t];
+    part[(size_t)blockIdx.x * C + t] = tot;
+  }
+}
+
+// bfloat16 copy of the weights; FC2 rows padded with zeros to 8.
+struct CastArgs {
+  const float* src[kLayers];
+  bf16* dst[kLayers];
+  int count[kLayers];      // floats copied
+  int padded[kLayers];     // bf16 elements written (>= count; the rest zero)
+};
+__global__ void cast_weights_kernel(const CastArgs a) {
+  const int L = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.padded[L]; i += gridDim.x * blockDim.x)
+    a.dst[L][i] = __float2bfloat16_rn(i < a.count[L] ? a.src[L][i] : 0.f);
+}
+
+// Loss 1/(2B) sum |y - t|^2 (one block, fixed order) and dz2 = (y - t) / B
+// in bf16, [B][8] with the two padding columns zero.
+__global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ y,
+                                                   const float* __restrict__ t, int B,
+                                                   float* __restrict__ loss, bf16* __restrict__ dz) {
+  __shared__ float s[256];
+  float acc = 0.f;
+  const float inv = 1.f / (float)B;
+  for (int e = threadIdx.x; e < B * kOutPad; e += 256) {
+    const int b = e / kOutPad, j = e % kOutPad;
+    float d = 0.f;
+    if (j < kOut) {
+      d = y[b * kOut + j] - t[b * kOut + j];
+      acc += d * d;
+    }
+    dz[e] = __float2bfloat16_rn(d * inv);
+  }
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = 0.5f * s[0] * inv;
+}
+
+__global__ void pack_kernel(const float* __restrict__ r_rgb, const float* __restrict__ r_d,
+                            const float* __restrict__ r_o, const float* __restrict__ o_rgb,
+                            const float* __restrict__ o_d, size_t n_px, bf16* __restrict__ x) {
+  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_px;
+       p += (size_t)gridDim.x * blockDim.x) {
+    const float o = r_o[p];
+    const float dr = o > 0.5f ? r_d[p] / o - GS2D_NET_DEPTH_OFFSET : 0.f;
+    const float od = o_d[p];
+    const float dd = od > 0.f ? od - GS2D_NET_DEPTH_OFFSET : 0.f;
+    __nv_bfloat162 v[4];
+    v[0] = __floats2bfloat162_rn(r_rgb[3 * p], r_rgb[3 * p + 1]);
+    v[1] = __floats2bfloat162_rn(r_rgb[3 * p + 2], dr);
+    v[2] = __floats2bfloat162_rn(o_rgb[3 * p], o_rgb[3 * p + 1]);
+    v[3] = __floats2bfloat162_rn(o_rgb[3 * p + 2], dd);
+    *reinterpret_cast<uint4*>(x + 8 * p) = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
+__global__ void adamw_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                             float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps,
+                             float wd, float bc1, float bc2) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    float pi = p[i] * (1.f - lr * wd);
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    pi -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    p[i] = pi;
+  }
+}
+
+__global__ void apply_kernel(const float* __restrict__ y, int B, float* __restrict__ poses) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  float tau[6], dR[9], dt[3], R[9], t[3];
+  for (int k = 0; k < 6; ++k) tau[k] = y[6 * b + k] * GS2D_NET_TAU_SCALE;
+  se3_exp_f(tau, dR, dt);
+  float* P = poses + 12 * b;
+  for (int k = 0; k < 9; ++k) R[k] = P[k];
+  for (int k = 0; k < 3; ++k) t[k] = P[9 + k];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c)
+      P[3 * r + c] = dR[3 * r] * R[c] + dR[3 * r + 1] * R[3 + c] + dR[3 * r + 2] * R[6 + c];
+    P[9 + r] = dR[3 * r] * t[0] + dR[3 * r + 1] * t[1] + dR[3 * r + 2] * t[2] + dt[r];
+  }
+}
+
+// SE(3) logarithm: rotation vector w with |w| = atan2(|v| / 2, (tr R - 1) / 2)
+// along v = vee(R - R^T), rho = V(w)^-1 t with V^-1 = I - K/2 +
+// (1 - A / (2B)) / th^2 K^2, A = sin th / th, B = (1 - cos th) / th^2.
+__device__ __forceinline__ void se3_log_f(const float R[9], const float t[3], float tau[6]) {
+  const float vx = R[7] - R[5], vy = R[2] - R[6], vz = R[3] - R[1];
+  const float s2 = 0.5f * sqrtf(vx * vx + vy * vy + vz * vz);
+  const float c = 0.5f * (R[0] + R[4] + R[8] - 1.f);
+  const float th = atan2f(s2, c);
+  const float f = s2 > 1e-7f ? th / (2.f * s2) : 0.5f;
+  const float w[3] = {f * vx, f * vy, f * vz};
+  const float th2 = th * th;
+  float D;
+  if (th < 1e-2f) {
+    D = 1.f / 12.f + th2 / 720.f;
+  } else {
+    const float A = sinf(th) / th, B = (1.f - cosf(th)) / th2;
+    D = (1.f - A / (2.f * B)) / th2;
+  }
+  const float K[9] = {0.f, -w[2], w[1], w[2], 0.f, -w[0], -w[1], w[0], 0.f};
+  for (int r = 0; r < 3; ++r) {
+    float acc = 0.f;
+    for (int q = 0; q < 3; ++q) {
+      const float K2 = K[3 * r] * K[q] + K[3 * r + 1] * K[3 + q] + K[3 * r + 2] * K[6 + q];
+      const float Vi = ((r == q) ? 1.f : 0.f) - 0.5f * K[3 * r + q] + D * K2;
+      acc += Vi * t[q];
+    }
+    tau[r] = acc;
+  }
+  tau[3] = w[0];
+  tau[4] = w[1];
+  tau[5] = w[2];
+}
+
+__global__ void target_kernel(const float* __restrict__ init, const float* __restrict__ gt, int B,
+                              float* __restrict__ target) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const float* Pi = init + 12 * b;
+  const float* Pg = gt + 12 * b;
+  float R[9], t[3], tau[6];
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 3; ++q)
+      R[3 * r + q] = Pg[3 * r] * Pi[3 * q] + Pg[3 * r + 1] * Pi[3 * q + 1] + Pg[3 * r + 2] * Pi[3 * q + 2];
+  for (int r = 0; r < 3; ++r)
+    t[r] = Pg[9 + r] - (R[3 * r] * Pi[9] + R[3 * r + 1] * Pi[10] + R[3 * r + 2] * Pi[11]);
+  se3_log_f(R, t, tau);
+  for (int k = 0; k < 6; ++k) target[6 * b + k] = tau[k] / GS2D_NET_TAU_SCALE;
+}
+
+__global__ void accept_kernel(const float* __restrict__ lp, const float* __restrict__ li,
+                              const float* __restrict__ prop, int B, float* __restrict__ poses,
+                              int32_t* __restrict__ accepted) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const bool take = lp[b] <= li[b];
+  if (take)
+    for (int k = 0; k < 12; ++k) poses[12 * b + k] = prop[12 * b + k];
+  if (accepted) accepted[b] = take ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+struct Layout {
+  size_t w_off[kLayers], b_off[kLayers], total;
+  int fan_in[kLayers], rows[kLayers], wcount[kLayers], wpadded[kLayers];
+  size_t wbf_off[kLayers], wbf_total;  // bf16 weight copy (elements)
+};
+
+Layout layout() {
+  Layout L{};
+  size_t off = 0, boff = 0;
+  for (int l = 0; l < kLayers; ++l) {
+    int rows, fan;
+    if (l < kConv) {
+      rows = kCout[l];
+      fan = 9 * kCin[l];
+    } else if (l == kConv) {
+      rows = kHidden;
+      fan = kFlat;
+    } else {
+      rows = kOut;
+      fan = kHidden;
+    }
+    L.rows[l] = rows;
+    L.fan_in[l] = fan;
+    L.w_off[l] = off;
+    off += (size_t)rows * fan;
+    L.b_off[l] = off;
+    off += rows;
+    L.wcount[l] = rows * fan;
+    L.wpadded[l] = (l == kLayers - 1 ? kOutPad : rows) * fan;
+    L.wbf_off[l] = boff;
+    boff += align_up((size_t)L.wpadded[l], 64);
+  }
+  L.total = off;
+  L.wbf_total = boff;
+  return L;
+}
+
+struct Ws {
+  bf16* wbf;
+  bf16* act[kConv + 1];  // act[0] unused (the caller's x), act[1..6] conv outputs
+  bf16* h;               // [B][256]
+  float* y;              // [B][6]
+  bf16* dz2;             // [B][8]
+  bf16* dzA;
+  bf16* dzB;
+  float* part;
+  size_t part_floats;
+  float* loss;
+  size_t bytes;
+};
+
+int splits_for(int M, int N, int K) {
+  const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  int s = (2 * 152 + tiles - 1) / tiles;
+  s = max(1, min(s, (K + 255) / 256));
+  return s;
+}
+int k_split_for(int K, int s) { return (int)align_up((size_t)((K + s - 1) / s), BK); }
+
+size_t max_partials(int B) {
+  size_t mx = 0;
+  auto upd = [&](int M, int N, int K) {
+    const int s = splits_for(M, N, K);
+    const int ks = k_split_for(K, s);
+    const int S = (K + ks - 1) / ks;
+    mx = max(mx, (size_t)S * M * N);
+  };
+  for (int l = 0; l < kConv; ++l) {
+    upd(kCout[l], 9 * kCin[l], B * kHin[l + 1] * kWin[l + 1]);
+    const int rows = B * kHin[l + 1] * kWin[l + 1];
+    mx = max(mx, (size_t)((rows + 1023) / 1024) * kCout[l]);
+  }
+  upd(kHidden, kFlat, B);
+  upd(kOutPad, kHidden, B);
+  mx = max(mx, (size_t)((B + 1023) / 1024) * kHidden);
+  return mx;
+}
+
+Ws carve(void* base, int B) {
+  const Layout L = layout();
+  Ws w{};
+  Carver c(base);
+  w.wbf = c.take<bf16>(L.wbf_total);
+  size_t dz_max = (size_t)B * kFlat;
+  for (int l = 1; l <= kConv; ++l) {
+    const size_t n = (size_t)B * kHin[l] * kWin[l] * kCout[l - 1];
+    w.act[l] = c.take<bf16>(n);
+    dz_max = max(dz_max, n);
+  }
+  w.h = c.take<bf16>((size_t)B * kHidden);
+  w.y = c.take<float>((size_t)B * kOut);
+  w.dz2 = c.take<bf16>((size_t)B * kOutPad);
+  w.dzA = c.take<bf16>(dz_max);
+  w.dzB = c.take<bf16>(dz_max);
+  w.part_floats = max_partials(B);
+  w.part = c.take<float>(w.part_floats);
+  w.loss = c.take<float>(64);
+  w.bytes = align_up(c.off, 256);
+  return w;
+}
+
+Operand op(const bf16* p, int ld, int rows) {
+  Operand o{};
+  o.p = p;
+  o.ld = ld;
+  o.rows = rows;
+  return o;
+}
+Operand conv_op(const bf16* p, int rows, int l, int C) {
+  Operand o{};
+  o.p = p;
+  o.rows = rows;
+  o.H = kHin[l];
+  o.W = kWin[l];
+  o.Ho = kHin[l + 1];
+  o.Wo = kWin[l + 1];
+  o.C = C;
+  return o;
+}
+
+template <int AM, int BMODE, int EPI>
+int run(Gemm g, int splits, cudaStream_t st, int* n_splits = nullptr) {
+  g.k_split = splits > 1 ? k_split_for(g.K, splits) : (int)align_up((size_t)g.K, BK);
+  const int S = max((g.K + g.k_split - 1) / g.k_split, 1);
+  const dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, S);
+  if (grid.y > 65535 || grid.z > 65535) return GS2D_ERR_INVALID_ARG;
+  gemm_kernel<AM, BMODE, EPI><<<grid, THREADS, 0, st>>>(g);
+  GS2D_LAUNCH_CHECK();
+  if (n_splits) *n_splits = S;
+  return GS2D_OK;
+}
+
+// weight gradient by split-K partials, reduced into out (m_valid x N)
+template <int AM, int BMODE>
+int wgrad(Gemm g, int m_valid, float* part, float* out, cudaStream_t st) {
+  g.out = part;
+  int S = 0;
+  const int r = run<AM, BMODE, E_PARTIAL>(g, splits_for(g.M, g.N, g.K), st, &S);
+  if (r) return r;
+  const size_t total = (size_t)m_valid * g.N;
+  const int blocks = (int)min((total + 255) / 256, (size_t)4096);
+  reduce_partials_kernel<<<blocks, 256, 0, st>>>(part, S, g.M, g.N, m_valid, g.N, out);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+int bias_grad(const bf16* z, int rows, int C, int c_valid, float* part, float* out, cudaStream_t st) {
+  const int rpb = 1024;
+  const int chunks = (rows + rpb - 1) / rpb;
+  colsum_partial_kernel<<<chunks, 256, 0, st>>>(z, rows, C, rpb, part);
+  GS2D_LAUNCH_CHECK();
+  reduce_partials_kernel<<<1, 256, 0, st>>>(part, chunks, 1, C, 1, c_valid, out);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+int cast(const float* params, const Ws& w, cudaStream_t st) {
+  const Layout L = layout();
+  CastArgs a{};
+  for (int l = 0; l < kLayers; ++l) {
+    a.src[l] = params + L.w_off[l];
+    a.dst[l] = w.wbf + L.wbf_off[l];
+    a.count[l] = L.wcount[l];
+    a.padded[l] = L.wpadded[l];
+  }
+  cast_weights_kernel<<<dim3(64, kLayers), 256, 0, st>>>(a);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+int forward(const float* params, const bf16* x, int B, const Ws& w, float* y, cudaStream_t st) {
+  const Layout L = layout();
+  int r = cast(params, w, st);
+  if (r) return r;
+  const bf16* in = x;
+  for (int l = 0; l < kConv; ++l) {
+    Gemm g{};
+    g.M = B * kHin[l + 1] * kWin[l + 1];
+    g.N = kCout[l];
+    g.K = 9 * kCin[l];
+    g.a = conv_op(in, g.M, l, kCin[l]);
+    g.b = op(w.wbf + L.wbf_off[l], g.K, g.N);
+    g.out = w.act[l + 1];
+    g.ldc = g.N;
+    g.bias = params + L.b_off[l];
+    r = run<K_IM2COL, K_DENSE, E_BIAS_RELU>(g, 1, st);
+    if (r) return r;
+    in = w.act[l + 1];
+  }
+  {
+    Gemm g{};
+    g.M = B;
+    g.N = kHidden;
+    g.K = kFlat;
+    g.a = op(in, kFlat, B);
+    g.b = op(w.wbf + L.wbf_off[kConv], kFlat, kHidden);
+    g.out = w.h;
+    g.ldc = kHidden;
+    g.bias = params + L.b_off[kConv];
+    r = run<K_DENSE, K_DENSE, E_BIAS_RELU>(g, 1, st);
+    if (r) return r;
+  }
+  {
+    Gemm g{};
+    g.M = B;
+    g.N = kOutPad;
+    g.K = kHidden;
+    g.a = op(w.h, kHidden, B);
+    g.b = op(w.wbf + L.wbf_off[kConv + 1], kHidden, kOutPad);
+    g.out = y;
+    g.ldc = kOut;
+    g.bias = params + L.b_off[kConv + 1];
+    g.n_valid = kOut;
+    r = run<K_DENSE, K_DENSE, E_BIAS_F32>(g, 1, st);
+    if (r) return r;
+  }
+  return GS2D_OK;
+}
+
+int backward(const float* params, const bf16* x, int B, const Ws& w, float* grad, cudaStream_t st) {
+  const Layout L = layout();
+  int r;
+  // FC2: dz2 [B][8]
+  {
+    Gemm g{};
+    g.M = kOutPad;
+    g.N = kHidden;
+    g.K = B;
+    g.a = op(w.dz2, kOutPad, kOutPad);
+    g.b = op(w.h, kHidden, kHidden);
+    r = wgrad<R_DENSE, R_DENSE>(g, kOut, w.part, grad + L.w_off[kConv + 1], st);
+    if (r) return r;
+    r = bias_grad(w.dz2, B, kOutPad, kOut, w.part, grad + L.b_off[kConv + 1], st);
+    if (r) return r;
+    Gemm d{};
+    d.M = B;
+    d.N = kHidden;
+    d.K = kOutPad;
+    d.a = op(w.dz2, kOutPad, B);
+    d.b = op(w.wbf + L.wbf_off[kConv + 1], kHidden, kHidden);
+    d.out = w.dzA;
+    d.ldc = kHidden;
+    d.mask = w.h;
+    r = run<K_DENSE, R_DENSE, E_MASK>(d, 1, st);
+    if (r) return r;
+  }
+  // FC1: dz1 = dzA [B][256]
+  {
+    Gemm g{};
+    g.M = kHidden;
+    g.N = kFlat;
+    g.K = B;
+    g.a = op(w.dzA, kHidden, kHidden);
+    g.b = op(w.act[kConv], kFlat, kFlat);
+    r = wgrad<R_DENSE, R_DENSE>(g, kHidden, w.part, grad + L.w_off[kConv], st);
+    if (r) return r;
+    r = bias_grad(w.dzA, B, kHidden, kHidden, w.part, grad + L.b_off[kConv], st);
+    if (r) return r;
+    Gemm d{};
+    d.M = B;
+    d.N = kFlat;
+    d.K = kHidden;
+    d.a = op(w.dzA, kHidden, B);
+    d.b = op(w.wbf + L.wbf_off[kConv], kFlat, kFlat);
+    d.out = w.dzB;
+    d.ldc = kFlat;
+    d.mask = w.act[kConv];
+    r = run<K_DENSE, R_DENSE, E_MASK>(d, 1, st);
+    if (r) return r;
+  }
+  // conv layers, last to first: dz of layer l's output is in cur
+  bf16* cur = w.dzB;
+  bf16* nxt = w.dzA;
+  for (int l = kConv - 1; l >= 0; --l) {
+    const bf16* a_in = l == 0 ? x : w.act[l];
+    const int P = B * kHin[l + 1] * kWin[l + 1];
+    Gemm g{};
+    g.M = kCout[l];
+    g.N = 9 * kCin[l];
+    g.K = P;
+    g.a = op(cur, kCout[l], kCout[l]);
+    g.b = conv_op(a_in, g.N, l, kCin[l]);
+    r = wgrad<R_DENSE, R_IM2COL>(g, kCout[l], w.part, grad + L.w_off[l], st);
+    if (r) return r;
+    r = bias_grad(cur, P, kCout[l], kCout[l], w.part, grad + L.b_off[l], st);
+    if (r) return r;
+    if (l == 0) break;
+    Gemm d{};
+    d.M = B * kHin[l] * kWin[l];
+    d.N = kCin[l];
+    d.K = 9 * kCout[l];
+    d.a = conv_op(cur, d.M, l, kCout[l]);
+    Operand wt{};
+    wt.p = w.wbf + L.wbf_off[l];
+    wt.ld = kCout[l];
+    wt.rows = kCin[l];
+    wt.C = kCin[l];
+    d.b = wt;
+    d.out = nxt;
+    d.ldc = kCin[l];
+    d.mask = w.act[l];
+    r = run<K_DGRAD, R_WT, E_MASK>(d, 1, st);
+    if (r) return r;
+    bf16* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  return GS2D_OK;
+}
+
+bool aligned16(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+}  // namespace net
+}  // namespace gs2d
+
+using namespace gs2d;
+using namespace gs2d::net;
+
+extern "C" {
+
+size_t gs2d_net_param_count(void) { return layout().total; }
+
+int gs2d_net_layout(size_t* w_off, size_t* b_off, int* fan_in) {
+  if (!w_off || !b_off || !fan_in) return GS2D_ERR_INVALID_ARG;
+  const Layout L = layout();
+  for (int l = 0; l < kLayers; ++l) {
+    w_off[l] = L.w_off[l];
+    b_off[l] = L.b_off[l];
+    fan_in[l] = L.fan_in[l];
+  }
+  return GS2D_OK;
+}
+
+size_t gs2d_net_workspace(int batch) {
+  if (batch <= 0) return 0;
+  return carve(nullptr, batch).bytes;
+}
+
+int gs2d_net_pack_input(const float* r_rgb, const float* r_depth, const float* r_opacity,
+                        const float* o_rgb, const float* o_depth, int batch, int height,
+                        int width, uint16_t* x, gs2d_stream stream) {
+  if (batch <= 0 || height <= 0 || width <= 0) return GS2D_ERR_INVALID_ARG;
+  if (!r_rgb || !r_depth || !r_opacity || !o_rgb || !o_depth || !aligned16(x))
+    return GS2D_ERR_INVALID_ARG;
+  const size_t n = (size_t)batch * height * width;
+  const int blocks = (int)min((n + 255) / 256, (size_t)152 * 16);
+  pack_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(r_rgb, r_depth, r_opacity, o_rgb, o_depth, n,
+                                                       reinterpret_cast<bf16*>(x));
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+int gs2d_net_forward(const float* params, const uint16_t* x, int batch, float* y, void* workspace,
+                     size_t ws_bytes, size_t* ws_needed, gs2d_stream stream) {
+  if (batch <= 0 || !params || !y || !aligned16(x)) return GS2D_ERR_INVALID_ARG;
+  const size_t need = gs2d_net_workspace(batch);
+  if (ws_needed) *ws_needed = need;
+  if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
+  const Ws w = carve(workspace, batch);
+  return forward(params, reinterpret_cast<const bf16*>(x), batch, w, y, (cudaStream_t)stream);
+}
+
+int gs2d_net_grad(const float* params, const uint16_t* x, const float* target, int batch,
+                  float* loss, float* grad, float* y, void* workspace, size_t ws_bytes,
+                  size_t* ws_needed, gs2d_stream stream) {
+  if (batch <= 0 || !params || !target || !loss || !grad || !aligned16(x))
+    return GS2D_ERR_INVALID_ARG;
+  const size_t need = gs2d_net_workspace(batch);
+  if (ws_needed) *ws_needed = need;
+  if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Ws w = carve(workspace, batch);
+  const bf16* xb = reinterpret_cast<const bf16*>(x);
+  int r = forward(params, xb, batch, w, w.y, st);
+  if (r) return r;
+  loss_kernel<<<1, 256, 0, st>>>(w.y, target, batch, loss, w.dz2);
+  GS2D_LAUNCH_CHECK();
+  r = backward(params, xb, batch, w, grad, st);
+  if (r) return r;
+  if (y) GS2D_CUDA_TRY(cudaMemcpyAsync(y, w.y, sizeof(float) * kOut * batch,
+                                       cudaMemcpyDeviceToDevice, st));
+  return GS2D_OK;
+}
+
+int gs2d_net_adamw(float* params, const float* grad, float* m, float* v, size_t n, int step,
+                   float lr, float beta1, float beta2, float eps, float weight_decay,
+                   gs2d_stream stream) {
+  if (!params || !grad || !m || !v || n == 0 || step < 1) return GS2D_ERR_INVALID_ARG;
+  const float bc1 = (float)(1.0 - pow((double)beta1, step));
+  const float bc2 = (float)(1.0 - pow((double)beta2, step));
+  const int blocks = (int)min((n + 255) / 256, (size_t)152 * 8);
+  adamw_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(params, grad, m, v, n, lr, beta1, beta2, eps,
+                                                        weight_decay, bc1, bc2);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+int gs2d_net_apply(const float* y, int batch, float* poses, gs2d_stream stream) {
+  if (batch <= 0 || !y || !poses) return GS2D_ERR_INVALID_ARG;
+  apply_kernel<<<(batch + 127) / 128, 128, 0, (cudaStream_t)stream>>>(y, batch, poses);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+int gs2d_net_target(const float* poses_init, const float* poses_gt, int batch, float* target,
+                    gs2d_stream stream) {
+  if (batch <= 0 || !poses_init || !poses_gt || !target) return GS2D_ERR_INVALID_ARG;
+  target_kernel<<<(batch + 127) / 128, 128, 0, (cudaStream_t)stream>>>(poses_init, poses_gt, batch,
+                                                                      target);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+int gs2d_net_accept(const float* loss_prop, const float* loss_init, const float* proposal,
+                    int batch, float* poses, int32_t* accepted, gs2d_stream stream) {
+  if (batch <= 0 || !loss_prop || !loss_init || !proposal || !poses) return GS2D_ERR_INVALID_ARG;
+  accept_kernel<<<(batch + 127) / 128, 128, 0, (cudaStream_t)stream>>>(loss_prop, loss_init, proposal,
+                                                                      batch, poses, accepted);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+}  // extern "C"

@@ -83,7 +83,15 @@ EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_stri
            "gs2d_track_status", "gs2d_render_count", "gs2d_bin_sort_static",
            "gs2d_profile_track_kernel", "gs2d_profile_track_kernel_count",
            "gs2d_project_batch", "gs2d_bin_sort_batch_workspace", "gs2d_bin_sort_batch",
-           "gs2d_render_batch_workspace", "gs2d_render_fwd_batch", "gs2d_render_bwd_batch"]
+           "gs2d_render_batch_workspace", "gs2d_render_fwd_batch", "gs2d_render_bwd_batch",
+           "gs2d_net_param_count", "gs2d_net_layout", "gs2d_net_workspace",
+           "gs2d_net_pack_input", "gs2d_net_forward", "gs2d_net_grad", "gs2d_net_adamw",
+           "gs2d_net_apply", "gs2d_net_target", "gs2d_net_accept"]
+
+NET_LAYERS = 8
+NET_IN = (120, 160, 8)
+NET_OUT = 6
+NET_TAU_SCALE = 0.03
 
 
 def lib_path() -> str:
@@ -132,6 +140,18 @@ def lib():
         L.gs2d_render_bwd_batch.argtypes = [vp, ip, vp, vp, vp, vp, vp, vp, vp, sz, vp, vp]
         L.gs2d_track_status.restype = vp
         L.gs2d_track_status.argtypes = [vp]
+        fl = ctypes.c_float
+        L.gs2d_net_param_count.restype = sz
+        L.gs2d_net_layout.argtypes = [vp, vp, vp]
+        L.gs2d_net_workspace.restype = sz
+        L.gs2d_net_workspace.argtypes = [ip]
+        L.gs2d_net_pack_input.argtypes = [vp] * 5 + [ip, ip, ip, vp, vp]
+        L.gs2d_net_forward.argtypes = [vp, vp, ip, vp, vp, sz, vp, vp]
+        L.gs2d_net_grad.argtypes = [vp, vp, vp, ip, vp, vp, vp, vp, sz, vp, vp]
+        L.gs2d_net_adamw.argtypes = [vp, vp, vp, vp, sz, ip, fl, fl, fl, fl, fl, vp]
+        L.gs2d_net_apply.argtypes = [vp, ip, vp, vp]
+        L.gs2d_net_target.argtypes = [vp, vp, ip, vp, vp]
+        L.gs2d_net_accept.argtypes = [vp, vp, vp, ip, vp, vp, vp]
         _LIB = L
     return _LIB
 
@@ -357,6 +377,81 @@ def gs2d_render_bwd_batch(views, surf: DeviceSurfels, d_mu, d_quat, d_scale, d_o
                                       _stream(stream)), "gs2d_render_bwd_batch")
 
 
+# ---------------------------------------------------------------------------
+# learned pose proposal (include/gs2d_net.h)
+# ---------------------------------------------------------------------------
+def gs2d_net_param_count() -> int:
+    return int(lib().gs2d_net_param_count())
+
+
+def gs2d_net_layout():
+    w = (ctypes.c_size_t * NET_LAYERS)()
+    b = (ctypes.c_size_t * NET_LAYERS)()
+    f = (ctypes.c_int * NET_LAYERS)()
+    check(lib().gs2d_net_layout(w, b, f), "gs2d_net_layout")
+    return list(w), list(b), list(f)
+
+
+def gs2d_net_workspace(batch: int) -> int:
+    return int(lib().gs2d_net_workspace(int(batch)))
+
+
+def gs2d_net_pack_input(r_rgb, r_depth, r_opacity, o_rgb, o_depth, x, stream=None):
+    B, H, W = r_depth.shape
+    check(lib().gs2d_net_pack_input(_ptr(r_rgb), _ptr(r_depth), _ptr(r_opacity), _ptr(o_rgb),
+                                    _ptr(o_depth), B, H, W, _ptr(x), _stream(stream)),
+          "gs2d_net_pack_input")
+
+
+def gs2d_net_forward(params, x, y, workspace, stream=None):
+    check(lib().gs2d_net_forward(_ptr(params), _ptr(x), int(x.shape[0]), _ptr(y), _ptr(workspace),
+                                 workspace.numel() * workspace.element_size(), None,
+                                 _stream(stream)), "gs2d_net_forward")
+
+
+def gs2d_net_grad(params, x, target, loss, grad, workspace, y=None, stream=None):
+    check(lib().gs2d_net_grad(_ptr(params), _ptr(x), _ptr(target), int(x.shape[0]), _ptr(loss),
+                              _ptr(grad), _ptr(y), _ptr(workspace),
+                              workspace.numel() * workspace.element_size(), None,
+                              _stream(stream)), "gs2d_net_grad")
+
+
+def gs2d_net_adamw(params, grad, m, v, step, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, wd=0.0,
+                   stream=None):
+    check(lib().gs2d_net_adamw(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(),
+                               int(step), float(lr), float(betas[0]), float(betas[1]), float(eps),
+                               float(wd), _stream(stream)), "gs2d_net_adamw")
+
+
+def gs2d_net_apply(y, poses, stream=None):
+    check(lib().gs2d_net_apply(_ptr(y), int(y.shape[0]), _ptr(poses), _stream(stream)),
+          "gs2d_net_apply")
+
+
+def gs2d_net_target(poses_init, poses_gt, target, stream=None):
+    check(lib().gs2d_net_target(_ptr(poses_init), _ptr(poses_gt), int(poses_init.shape[0]),
+                                _ptr(target), _stream(stream)), "gs2d_net_target")
+
+
+def gs2d_net_accept(loss_prop, loss_init, proposal, poses, accepted=None, stream=None):
+    check(lib().gs2d_net_accept(_ptr(loss_prop), _ptr(loss_init), _ptr(proposal),
+                                int(poses.shape[0]), _ptr(poses), _ptr(accepted),
+                                _stream(stream)), "gs2d_net_accept")
+
+
+def net_init_blocks():
+    """(count, fan_in) blocks of the flat parameter vector, in layout order,
+    for the seeded initialiser (weights He-normal, biases zero)."""
+    w_off, b_off, fan = gs2d_net_layout()
+    total = gs2d_net_param_count()
+    blocks = []
+    for l in range(NET_LAYERS):
+        blocks.append((b_off[l] - w_off[l], fan[l]))
+        end = w_off[l + 1] if l + 1 < NET_LAYERS else total
+        blocks.append((end - b_off[l], 0))
+    return blocks
+
+
 class BatchRasterizer:
     """Buffers of a batch of views (up to 32): per view its records, bins,
     images and upstream gradients; projection, binning and the two render
@@ -369,6 +464,15 @@ class BatchRasterizer:
         assert 0 < self.nv <= MAX_VIEWS
         self.keep = []
         f = dict(dtype=torch.float32, device=device)
+        # views of one size share stacked [V, H, W, ...] image tensors
+        sizes = {(int(c.height), int(c.width)) for c in cams}
+        self.stacked = None
+        if len(sizes) == 1:
+            H, W = sizes.pop()
+            V = self.nv
+            self.stacked = dict(rgb=torch.empty(V, H, W, 3, **f), depth=torch.empty(V, H, W, **f),
+                                normal=torch.empty(V, H, W, 3, **f),
+                                opacity=torch.empty(V, H, W, **f))
         for v, cam in enumerate(cams):
             act = None if actives is None or actives[v] is None else \
                 torch.as_tensor(np.asarray(actives[v], np.int32), device=device)
@@ -385,8 +489,10 @@ class BatchRasterizer:
                      ranges=torch.empty(2 * tx * ty, dtype=torch.int32, device=device),
                      n_isect=torch.zeros(1, dtype=torch.int32, device=device),
                      status=torch.zeros(1, dtype=torch.int32, device=device),
-                     rgb=torch.empty(H, W, 3, **f), depth=torch.empty(H, W, **f),
-                     normal=torch.empty(H, W, 3, **f), opacity=torch.empty(H, W, **f),
+                     rgb=self.stacked["rgb"][v] if self.stacked else torch.empty(H, W, 3, **f),
+                     depth=self.stacked["depth"][v] if self.stacked else torch.empty(H, W, **f),
+                     normal=self.stacked["normal"][v] if self.stacked else torch.empty(H, W, 3, **f),
+                     opacity=self.stacked["opacity"][v] if self.stacked else torch.empty(H, W, **f),
                      t_final=torch.empty(H, W, **f),
                      n_last=torch.empty(H, W, dtype=torch.int32, device=device),
                      d_rgb=torch.zeros(H, W, 3, **f), d_depth=torch.zeros(H, W, **f),

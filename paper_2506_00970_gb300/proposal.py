@@ -1,0 +1,341 @@
+"""Learned tracking-pose proposal (not in the paper): self-rendered training
+pairs, training on the BF16 tensor-core network kernels of gs2d_net.h, and
+frame tracking that starts the plain loop of Sec. III-D from the proposal --
+or, when the proposal raises the tracking loss (Eq. tracking_loss), from the
+usual starting pose.
+
+Workload: rooms of the synthetic room generator rendered at 160x120,
+fx = fy = 150; starting poses perturbed from ground truth by up to 5 cm and
+3 degrees (magnitudes uniform, directions random); the observed frame is the
+ground-truth render with expected depth D/O + N(0, 1 mm), 0 where the
+rendered opacity is at most 0.5.  Everything runs through the C ABI; torch
+only holds device memory, draws the sensor noise and captures CUDA graphs.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import gs2d, scenes
+
+CAM = scenes.Camera(150.0, 150.0, 80.0, 60.0, 160, 120)
+MAX_T, MAX_DEG = 0.05, 3.0
+VIEWS = 32
+
+
+def poses_tensor(poses, device="cuda"):
+    return torch.stack([gs2d.pose_tensor(p, device) for p in poses])
+
+
+def pose_error(P12, gt) -> tuple[float, float]:
+    """Camera-centre distance (m) and geodesic rotation angle (degrees)
+    between a pose given as 12 floats and a ground-truth Pose."""
+    P = np.asarray(P12, np.float64)
+    R, t = P[:9].reshape(3, 3), P[9:]
+    c = -R.T @ t
+    cg = -gt.R.T @ gt.t
+    cosang = np.clip((np.trace(R @ gt.R.T) - 1.0) / 2.0, -1.0, 1.0)
+    return float(np.linalg.norm(c - cg)), math.degrees(math.acos(cosang))
+
+
+def first_below(pose_hist, gt, tcm=0.01, tdeg=0.5):
+    """1-based index of the first iteration whose pose is within tcm metres
+    and tdeg degrees of gt, 0 if the starting pose already is, or None."""
+    for it in range(pose_hist.shape[0]):
+        et, er = pose_error(pose_hist[it], gt)
+        if et < tcm and er < tdeg:
+            return it + 1
+    return None
+
+
+def observed_depth(depth, opacity, gen, sigma=1e-3):
+    """Synthetic sensor depth from a render: D/O + N(0, sigma), 0 where the
+    opacity is at most 0.5."""
+    noise = torch.randn(depth.shape, generator=gen, device=depth.device) * sigma
+    return torch.where(opacity > 0.5, depth / opacity.clamp_min(1e-6) + noise,
+                       torch.zeros_like(depth))
+
+
+class ViewRenderer:
+    """Forward renders of up to VIEWS poses of CAM per batched call."""
+
+    def __init__(self, surf: gs2d.DeviceSurfels, views: int = VIEWS):
+        self.surf = surf
+        self.views = views
+        self.br = gs2d.BatchRasterizer([CAM] * views, surf.n, capacities=[3 * surf.n] * views)
+
+    def render(self, poses_t):
+        n = poses_t.shape[0]
+        pad = [poses_t[min(i, n - 1)] for i in range(self.views)]
+        self.br.set_poses(pad)
+        self.br.forward(self.surf)
+        return self.br.stacked
+
+
+def make_pairs(rooms, n_pairs: int, seed: int, device="cuda"):
+    """Training pairs over the given rooms (Surfels): x [n, 120, 160, 8]
+    bfloat16 (rendered at the perturbed pose + observed at ground truth) and
+    the target y* [n, 6]."""
+    X = torch.empty(n_pairs, 120, 160, 8, dtype=torch.bfloat16, device=device)
+    Y = torch.empty(n_pairs, 6, device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    per_room = -(-n_pairs // len(rooms))
+    i = 0
+    for r, s in enumerate(rooms):
+        ds = gs2d.DeviceSurfels(s)
+        vr = ViewRenderer(ds)
+        obs_rgb = torch.empty(VIEWS, 120, 160, 3, device=device)
+        obs_d = torch.empty(VIEWS, 120, 160, device=device)
+        c0 = 0
+        while c0 < per_room and i < n_pairs:
+            cnt = min(VIEWS, n_pairs - i, per_room - c0)
+            k = seed * 10_000_000 + r * 1_000_000 + c0
+            gts = [scenes.room_pose(k + j) for j in range(cnt)]
+            inits = [scenes.perturb_uniform(g, MAX_T, MAX_DEG, k + j) for j, g in enumerate(gts)]
+            G, I = poses_tensor(gts, device), poses_tensor(inits, device)
+            img = vr.render(G)
+            obs_rgb.copy_(img["rgb"])
+            obs_d.copy_(observed_depth(img["depth"], img["opacity"], gen))
+            img = vr.render(I)
+            gs2d.gs2d_net_pack_input(img["rgb"][:cnt], img["depth"][:cnt], img["opacity"][:cnt],
+                                     obs_rgb[:cnt], obs_d[:cnt], X[i:i + cnt])
+            gs2d.gs2d_net_target(I, G, Y[i:i + cnt])
+            i += cnt
+            c0 += cnt
+        del vr, ds
+    return X[:i], Y[:i]
+
+
+class Trainer:
+    """AdamW on FP32 master weights; every step is one gs2d_net_grad (forward,
+    loss, backward) and one gs2d_net_adamw on a contiguous batch."""
+
+    def __init__(self, seed: int = 0, batch: int = 256, device="cuda"):
+        self.batch = batch
+        self.params = torch.tensor(scenes.net_init(seed, gs2d.net_init_blocks()), device=device)
+        n = self.params.numel()
+        self.m = torch.zeros(n, device=device)
+        self.v = torch.zeros(n, device=device)
+        self.grad = torch.empty(n, device=device)
+        self.loss = torch.empty(1, device=device)
+        self.ws = torch.empty(gs2d.gs2d_net_workspace(batch), dtype=torch.uint8, device=device)
+        self.step = 0
+
+    def fit(self, X, Y, steps: int, lr=1e-3, lr_min=1e-5, wd=1e-4, log_every=0):
+        B = self.batch
+        nb = X.shape[0] // B
+        hist = []
+        for k in range(steps):
+            j = k % nb
+            self.step += 1
+            lr_t = lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * k / max(steps, 1)))
+            gs2d.gs2d_net_grad(self.params, X[j * B:(j + 1) * B], Y[j * B:(j + 1) * B], self.loss,
+                               self.grad, self.ws)
+            gs2d.gs2d_net_adamw(self.params, self.grad, self.m, self.v, self.step, lr=lr_t, wd=wd)
+            if log_every and (k % log_every == 0 or k == steps - 1):
+                hist.append((k, float(self.loss.item())))
+        return hist
+
+    def eval_loss(self, X, Y):
+        """Mean loss over contiguous batches of (X, Y) (no update)."""
+        B = self.batch
+        tot, nb = 0.0, X.shape[0] // B
+        for j in range(nb):
+            gs2d.gs2d_net_grad(self.params, X[j * B:(j + 1) * B], Y[j * B:(j + 1) * B], self.loss,
+                               self.grad, self.ws)
+            tot += float(self.loss.item())
+        return tot / max(nb, 1)
+
+
+class Proposer:
+    """One frame's proposal as a fixed launch sequence (capturable in a CUDA
+    graph, no host round trip): render at the current pose, tracking loss
+    there, pack with the observation, network forward, apply, render at the
+    proposal, tracking loss there, keep the better pose."""
+
+    def __init__(self, surf: gs2d.DeviceSurfels, params, capacity: int, device="cuda"):
+        self.surf = surf
+        self.params = params
+        self.r = gs2d.Rasterizer(CAM, surf.n, capacity=capacity, device=device)
+        f = dict(dtype=torch.float32, device=device)
+        self.pose = torch.empty(1, 12, **f)
+        self.prop = torch.empty(1, 12, **f)
+        self.obs_rgb = torch.empty(120, 160, 3, **f)
+        self.obs_d = torch.empty(120, 160, **f)
+        self.x = torch.empty(1, 120, 160, 8, dtype=torch.bfloat16, device=device)
+        self.y = torch.empty(1, 6, **f)
+        self.ws = torch.empty(gs2d.gs2d_net_workspace(1), dtype=torch.uint8, device=device)
+        self.g = [torch.empty(120, 160, 3, **f), torch.empty(120, 160, **f), torch.empty(120, 160, **f)]
+        self.loss_init = torch.empty(1, **f)
+        self.loss_prop = torch.empty(1, **f)
+        self.lws = torch.empty(1 << 16, dtype=torch.uint8, device=device)
+        self.accepted = torch.zeros(1, dtype=torch.int32, device=device)
+        self.prm = gs2d.default_track_params()
+
+    def _render(self, pose_row):
+        r = self.r
+        r.status.zero_()
+        r.project(self.surf, pose_row)
+        gs2d.gs2d_bin_sort(r.proj, r.tiles, r.n, r.cam, r.cfg, r.sort_ws, r.bins)
+        r.render_fwd()
+
+    def _loss(self, out):
+        r = self.r
+        gs2d.gs2d_tracking_loss(r.rgb, r.depth, r.normal, r.opacity, self.obs_rgb, self.obs_d, r.cam,
+                                self.prm, self.g[0], self.g[1], self.g[2], out, self.lws)
+
+    def run(self):
+        r = self.r
+        self._render(self.pose[0])
+        self._loss(self.loss_init)
+        gs2d.gs2d_net_pack_input(r.rgb[None], r.depth[None], r.opacity[None], self.obs_rgb[None],
+                                 self.obs_d[None], self.x)
+        gs2d.gs2d_net_forward(self.params, self.x, self.y, self.ws)
+        self.prop.copy_(self.pose)
+        gs2d.gs2d_net_apply(self.y, self.prop)
+        self._render(self.prop[0])
+        self._loss(self.loss_prop)
+        gs2d.gs2d_net_accept(self.loss_prop, self.loss_init, self.prop, self.pose, self.accepted)
+
+    def status(self) -> int:
+        return int(self.r.status.item())
+
+
+def capture(fn, warm: int = 1):
+    """fn's launches as a CUDA graph (after warm-up calls on a side stream)."""
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(warm):
+            fn()
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return g
+
+
+def timed_replays(graph, reps: int, before=None) -> list[float]:
+    st = torch.cuda.current_stream()
+    out = []
+    for _ in range(reps):
+        if before is not None:
+            before()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        graph.replay()
+        e1.record(st)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def evaluate(scene, params, n_frames: int, seed: int, n_iter: int = 100, device="cuda"):
+    """Plain loop vs proposal + loop on held-out frames of one room: per frame
+    the iterations to 1 cm / 0.5 degrees (pose history of the fused tracking
+    step), the proposal's own error, and the GPU time of one proposal and of
+    one tracking iteration (CUDA graph replays)."""
+    ds = gs2d.DeviceSurfels(scene)
+    vr = ViewRenderer(ds)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    gts, inits = [], []
+    obs_rgb = torch.empty(n_frames, 120, 160, 3, device=device)
+    obs_d = torch.empty(n_frames, 120, 160, device=device)
+    kmax = 0
+    for c0 in range(0, n_frames, VIEWS):
+        cnt = min(VIEWS, n_frames - c0)
+        k = seed * 10_000_000 + c0
+        g = [scenes.room_pose(k + j) for j in range(cnt)]
+        it = [scenes.perturb_uniform(p, MAX_T, MAX_DEG, k + j) for j, p in enumerate(g)]
+        img = vr.render(poses_tensor(g, device))
+        obs_rgb[c0:c0 + cnt] = img["rgb"][:cnt]
+        obs_d[c0:c0 + cnt] = observed_depth(img["depth"][:cnt], img["opacity"][:cnt], gen)
+        vr.render(poses_tensor(it, device))
+        kmax = max([kmax] + [int(b["n_isect"].item()) for b in vr.br.keep])
+        gts += g
+        inits += it
+    del vr
+    cap = 4 * kmax + 4096
+    # the proposal, one frame per replay
+    pr = Proposer(ds, params, cap, device)
+    pr.pose.copy_(poses_tensor(inits[:1], device))
+    pr.obs_rgb.copy_(obs_rgb[0])
+    pr.obs_d.copy_(obs_d[0])
+    pg = capture(pr.run)
+    # the plain loop, one frame (n_iter iterations) per replay
+    ccam, cfg = gs2d.camera(CAM), gs2d.default_config()
+    prm = gs2d.default_track_params(stop_tol=0.0)
+    tws = torch.empty(gs2d.gs2d_track_workspace(ds.n, cap, ccam, cfg), dtype=torch.uint8,
+                      device=device)
+    tpose = torch.empty(12, device=device)
+    t_rgb = torch.empty(120, 160, 3, device=device)
+    t_d = torch.empty(120, 160, device=device)
+    lh = torch.zeros(n_iter, device=device)
+    ph = torch.zeros(n_iter, 12, device=device)
+    tpose.copy_(pr.pose[0])
+    t_rgb.copy_(obs_rgb[0])
+    t_d.copy_(obs_d[0])
+
+    def track():
+        gs2d.gs2d_track_step(ds, ccam, cfg, prm, tpose, t_rgb, t_d, n_iter, cap, lh, ph, tws)
+
+    tg = capture(track)
+    init_t = poses_tensor(inits, device)
+    res = dict(start=[], prop=[], plain_it=[], learned_it=[], accepted=[])
+    prop_ms, iter_ms = [], []
+    for f in range(n_frames):
+        gt = gts[f]
+        res["start"].append(pose_error(init_t[f].cpu().numpy(), gt))
+        # plain loop from the usual start
+        tpose.copy_(init_t[f])
+        t_rgb.copy_(obs_rgb[f])
+        t_d.copy_(obs_d[f])
+        iter_ms += [m / n_iter for m in timed_replays(tg, 1)]
+        if int(gs2d.gs2d_track_status(tws).item()) not in (0, gs2d.CONVERGED):
+            raise gs2d.Gs2dError("tracking status")
+        res["plain_it"].append(first_below(ph.cpu().numpy(), gt))
+        # proposal, then the same loop from the chosen pose
+        pr.pose.copy_(init_t[f:f + 1])
+        pr.obs_rgb.copy_(obs_rgb[f])
+        pr.obs_d.copy_(obs_d[f])
+        prop_ms += timed_replays(pg, 1)
+        if pr.status() != 0:
+            raise gs2d.Gs2dError(f"proposal render status {pr.status()}")
+        res["accepted"].append(int(pr.accepted.item()))
+        start = pr.pose[0].clone()
+        res["prop"].append(pose_error(start.cpu().numpy(), gt))
+        if pose_error(start.cpu().numpy(), gt)[0] < 0.01 and pose_error(start.cpu().numpy(), gt)[1] < 0.5:
+            res["learned_it"].append(0)
+            continue
+        tpose.copy_(start)
+        timed_replays(tg, 1)
+        res["learned_it"].append(first_below(ph.cpu().numpy(), gt))
+    ms_iter = float(np.median(iter_ms))
+    ms_prop = float(np.median(prop_ms))
+    cap_it = lambda v: n_iter if v is None else v
+    plain_ms = np.array([cap_it(v) * ms_iter for v in res["plain_it"]])
+    learned_ms = np.array([ms_prop + cap_it(v) * ms_iter for v in res["learned_it"]])
+    st = np.array(res["start"])
+    pp = np.array(res["prop"])
+    return {
+        "frames": n_frames,
+        "ms_per_iter": ms_iter,
+        "proposal_ms": ms_prop,
+        "plain": {"ms_to_1cm_0.5deg_median": float(np.median(plain_ms)),
+                  "ms_mean": float(np.mean(plain_ms)),
+                  "iters_median": float(np.median([cap_it(v) for v in res["plain_it"]])),
+                  "reached": int(sum(v is not None for v in res["plain_it"]))},
+        "learned": {"ms_to_1cm_0.5deg_median": float(np.median(learned_ms)),
+                    "ms_mean": float(np.mean(learned_ms)),
+                    "iters_median": float(np.median([cap_it(v) for v in res["learned_it"]])),
+                    "reached": int(sum(v is not None for v in res["learned_it"])),
+                    "accepted_frac": float(np.mean(res["accepted"]))},
+        "speedup_median": float(np.median(plain_ms) / max(np.median(learned_ms), 1e-9)),
+        "start_err_median_cm_deg": [float(np.median(st[:, 0]) * 100), float(np.median(st[:, 1]))],
+        "proposal_err_median_cm_deg": [float(np.median(pp[:, 0]) * 100), float(np.median(pp[:, 1]))],
+    }

@@ -116,6 +116,13 @@ def perturb_pose(pose: Pose, trans_m: float, rot_deg: float, seed: int) -> Pose:
 # --------------------------------------------------------------------------
 # workload 1: random slab in front of the camera
 # --------------------------------------------------------------------------
+def perturb_uniform(pose: Pose, max_trans_m: float, max_rot_deg: float, seed: int) -> Pose:
+    """perturb_pose with magnitudes drawn uniformly in [0, max]."""
+    rng = np.random.default_rng(seed)
+    return perturb_pose(pose, rng.uniform(0.0, max_trans_m), rng.uniform(0.0, max_rot_deg),
+                        seed=seed + 7_000_000)
+
+
 def slab_scene(seed: int = 0, n: int = 4096) -> Surfels:
     """Centres uniform in [-1,1]^2 x [1,3] m (camera frame = world frame),
     log-uniform scales in [1,5] cm, uniform random rotations,

@@ -1,17 +1,20 @@
 """The C ABI library builds for sm_103a, loads without a GPU and exports every
-entry point that include/gs2d.h declares; the binding refuses to run without
+entry point that the headers under include/ declare; the binding refuses to run without
 the library (no CPU fallback).  No compute calls here."""
 import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "gs2d.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "\n".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc))
+                    if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     src = re.sub(r"//[^\n]*", "", src)
     names = set(re.findall(r"\b(gs2d_\w+)\s*\(", src))
@@ -84,3 +87,21 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(gs2d, "_LIB", None)
     with pytest.raises(gs2d.Gs2dError):
         gs2d.lib()
+
+
+def test_network_layout_matches_the_oracle(built_lib):
+    """The flat parameter layout of the network kernels equals the oracle's
+    (both written from the definition in include/gs2d_net.h)."""
+    from oracle import net
+    from paper_2506_00970_gb300 import gs2d
+    items, total = net.param_layout()
+    assert gs2d.gs2d_net_param_count() == total
+    w_off, b_off, fan = gs2d.gs2d_net_layout()
+    names = [n for n, _, _ in items]
+    offs = {n: o for n, _, o in items}
+    for l in range(gs2d.NET_LAYERS):
+        wn, bn = names[2 * l], names[2 * l + 1]
+        assert (w_off[l], b_off[l]) == (offs[wn], offs[bn])
+        shape = dict((n, s) for n, s, _ in items)[wn]
+        assert fan[l] == int(np.prod(shape[1:]))
+    assert gs2d.gs2d_net_workspace(256) > 0 and gs2d.gs2d_net_workspace(0) == 0

@@ -1,0 +1,57 @@
+"""The learned tracking-pose proposal end to end on the GPU: self-rendered
+training pairs, a short training run on the network kernels, and tracking
+on frames of a room not seen in training.  The proposal must bring the
+starting pose closer to the ground truth and shorten the GPU time the plain
+loop of Sec. III-D needs to reach 1 cm / 0.5 degrees."""
+import numpy as np
+import pytest
+
+from paper_2506_00970_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_00970_gb300 import gs2d
+    gs2d.lib()
+    return torch
+
+
+def test_pairs_have_the_targets_of_their_poses(torch_cuda):
+    """Pairs are well formed: the target's rotation is the drawn angle
+    (at most 3 degrees), its translation V^-1 dt is within 5 cm times
+    (1 + theta), inputs are finite and colours in range."""
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import proposal
+    room = scenes.room_scene(7, 50_000)
+    X, Y = proposal.make_pairs([room], 64, seed=5)
+    torch.cuda.synchronize()
+    assert X.shape == (64, 120, 160, 8) and Y.shape == (64, 6)
+    y = Y.cpu().numpy() * 0.03
+    t_cm = np.linalg.norm(y[:, :3], axis=1) * 100
+    r_deg = np.degrees(np.linalg.norm(y[:, 3:], axis=1))
+    assert r_deg.max() <= 3.0 + 1e-3 and r_deg.min() >= 0.0
+    assert t_cm.max() <= 5.0 * (1.0 + np.radians(3.0)) + 1e-3
+    x = X.float().cpu().numpy()
+    assert np.isfinite(x).all() and np.abs(x[..., 4:7]).max() <= 1.0
+
+
+def test_trained_proposal_shortens_tracking(torch_cuda):
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import proposal
+    rooms = [scenes.room_scene(100 + r, 100_000) for r in range(2)]
+    X, Y = proposal.make_pairs(rooms, 16_384, seed=1)
+    tr = proposal.Trainer(seed=0, batch=256)
+    hist = tr.fit(X, Y, 1200, lr=1e-3, log_every=400)
+    del X, Y
+    torch.cuda.empty_cache()
+    assert hist[-1][1] < 0.5 * hist[0][1], hist
+    ev = proposal.evaluate(scenes.room_scene(200, 100_000), tr.params, 48, seed=3)
+    st, pp = ev["start_err_median_cm_deg"], ev["proposal_err_median_cm_deg"]
+    assert pp[1] < st[1], (st, pp)
+    assert ev["learned"]["ms_to_1cm_0.5deg_median"] < ev["plain"]["ms_to_1cm_0.5deg_median"], ev
+    assert ev["learned"]["reached"] >= ev["plain"]["reached"] - 1, ev
