@@ -16,12 +16,17 @@
 //      memory (bitonic network in its "flip" form, in which every comparator
 //      puts the smaller key at the lower index, so a segment of any length
 //      behaves as if padded with +inf), then writes the surfel ids, the
-//      64-bit (tile, depth) keys and each pair's emission index.
+//      64-bit (tile, depth) keys and each pair's emission index.  Segments
+//      longer than 2048 keys (dense views of large maps) go to a 1024-thread
+//      block that sorts 16384-key chunks in shared memory and merges the
+//      sorted runs in global memory.
 // Because the key carries the id, the final order is unique and
 // deterministic whatever order the atomics gave.  Emission index of the pair
 // (surfel i, tile t) = surfel_off[i] + the row-major position of t in i's
 // rectangle, so each surfel's pairs are contiguous in emission order (the
 // backward pass stores its per-pair partials there).
+#include <mutex>
+
 #include "gs2d_common.cuh"
 #include "gs2d_internal.h"
 
@@ -34,6 +39,8 @@ constexpr int kWarps = kScanThreads / 32;
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kSortThreads = 128;
 constexpr int kSegSmem = 2048;                     // keys sorted in shared memory (16 KB)
+constexpr int kLongThreads = 1024;                 // long segments: one 1024-thread block
+constexpr int kLongChunk = 16384;                  // keys per shared-memory chunk (128 KB)
 
 __device__ __forceinline__ unsigned long long ld_vol64(const unsigned long long* p) {
   return *reinterpret_cast<const volatile unsigned long long*>(p);
@@ -335,27 +342,12 @@ __device__ void bitonic_sort(unsigned long long* a, int len) {
   }
 }
 
-__global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(
-    const float4* __restrict__ proj, int n, int tiles_x, const int32_t* __restrict__ ranges,
-    unsigned long long* __restrict__ seg_keys, const uint32_t* __restrict__ surfel_off,
-    uint32_t* __restrict__ vals, uint32_t* __restrict__ emit, unsigned long long* __restrict__ keys64,
-    long long capacity, const int32_t* __restrict__ gate) {
-  extern __shared__ unsigned long long s_keys[];
-  if (*gate) return;
-  const int t = blockIdx.x;
-  const int start = ranges[2 * t];
-  const int end = (int)min((long long)ranges[2 * t + 1], capacity);
-  const int len = end - start;
-  if (len <= 0) return;
-  unsigned long long* a;
-  if (len <= kSegSmem) {
-    for (int i = threadIdx.x; i < len; i += blockDim.x) s_keys[i] = seg_keys[start + i];
-    __syncthreads();
-    a = s_keys;
-  } else {
-    a = seg_keys + start;  // a rare long list: the same network in global memory
-  }
-  bitonic_sort(a, len);
+// The final outputs of a tile's sorted segment a[0, len).
+__device__ __forceinline__ void write_outputs(const unsigned long long* a, int len, int start, int t,
+                                              int tiles_x, int n, const float4* __restrict__ proj,
+                                              const uint32_t* __restrict__ surfel_off,
+                                              uint32_t* __restrict__ vals, uint32_t* __restrict__ emit,
+                                              unsigned long long* __restrict__ keys64) {
   const int tx = t % tiles_x, ty = t / tiles_x;
   for (int i = threadIdx.x; i < len; i += blockDim.x) {
     const unsigned long long key = a[i];
@@ -370,10 +362,105 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(
   }
 }
 
+// Segments of at most kSegSmem keys: sorted in shared memory by 128 threads.
+__global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(
+    const float4* __restrict__ proj, int n, int tiles_x, const int32_t* __restrict__ ranges,
+    unsigned long long* __restrict__ seg_keys, const uint32_t* __restrict__ surfel_off,
+    uint32_t* __restrict__ vals, uint32_t* __restrict__ emit, unsigned long long* __restrict__ keys64,
+    long long capacity, const int32_t* __restrict__ gate) {
+  extern __shared__ unsigned long long s_keys[];
+  if (*gate) return;
+  const int t = blockIdx.x;
+  const int start = ranges[2 * t];
+  const int end = (int)min((long long)ranges[2 * t + 1], capacity);
+  const int len = end - start;
+  if (len <= 0 || len > kSegSmem) return;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) s_keys[i] = seg_keys[start + i];
+  __syncthreads();
+  bitonic_sort(s_keys, len);
+  write_outputs(s_keys, len, start, t, tiles_x, n, proj, surfel_off, vals, emit, keys64);
+}
+
+// Position in the merge of sorted runs A[0, la) and B[0, lb) (unique keys):
+// the number i of elements taken from A among the first d outputs.
+__device__ __forceinline__ int co_rank(const unsigned long long* A, int la, const unsigned long long* B,
+                                       int lb, int d) {
+  int lo = max(0, d - lb), hi = min(d, la);
+  while (lo < hi) {
+    const int i = (lo + hi) >> 1;  // i from A, d - i from B
+    if (A[i] < B[d - i - 1])
+      lo = i + 1;
+    else
+      hi = i;
+  }
+  return lo;
+}
+
+// Segments longer than kSegSmem: chunks of kLongChunk keys are sorted in
+// shared memory by 1024 threads, then adjacent sorted runs are merged in
+// global memory (seg_keys <-> seg_tmp), each thread producing a contiguous
+// span of the output located by a co-rank search.
+__global__ void __launch_bounds__(kLongThreads) tile_sort_long_kernel(
+    const float4* __restrict__ proj, int n, int tiles_x, const int32_t* __restrict__ ranges,
+    unsigned long long* __restrict__ seg_keys, unsigned long long* __restrict__ seg_tmp,
+    const uint32_t* __restrict__ surfel_off, uint32_t* __restrict__ vals, uint32_t* __restrict__ emit,
+    unsigned long long* __restrict__ keys64, long long capacity, const int32_t* __restrict__ gate) {
+  extern __shared__ unsigned long long s_keys[];
+  if (*gate) return;
+  const int t = blockIdx.x;
+  const int start = ranges[2 * t];
+  const int end = (int)min((long long)ranges[2 * t + 1], capacity);
+  const int len = end - start;
+  if (len <= kSegSmem) return;
+  unsigned long long* src = seg_keys + start;
+  unsigned long long* dst = seg_tmp + start;
+  const int chunks = (len + kLongChunk - 1) / kLongChunk;
+  for (int c = 0; c < chunks; ++c) {
+    const int c0 = c * kLongChunk, cl = min(kLongChunk, len - c0);
+    for (int i = threadIdx.x; i < cl; i += blockDim.x) s_keys[i] = src[c0 + i];
+    __syncthreads();
+    bitonic_sort(s_keys, cl);
+    if (chunks == 1) {
+      write_outputs(s_keys, len, start, t, tiles_x, n, proj, surfel_off, vals, emit, keys64);
+      return;
+    }
+    for (int i = threadIdx.x; i < cl; i += blockDim.x) src[c0 + i] = s_keys[i];
+    __syncthreads();
+  }
+  const int span = (len + blockDim.x - 1) / blockDim.x;
+  for (int w = kLongChunk; w < len; w <<= 1) {
+    const int p0 = min(len, (int)threadIdx.x * span), p1 = min(len, p0 + span);
+    int p = p0;
+    while (p < p1) {
+      // the run pair holding output position p
+      const int lo = (p / (2 * w)) * (2 * w);
+      const int mid = min(lo + w, len), hi = min(lo + 2 * w, len);
+      const unsigned long long* A = src + lo;
+      const unsigned long long* B = src + mid;
+      const int la = mid - lo, lb = hi - mid;
+      int i = co_rank(A, la, B, lb, p - lo);
+      int j = (p - lo) - i;
+      const int stop = min(p1, hi);
+      for (; p < stop; ++p) {
+        if (j >= lb || (i < la && A[i] < B[j]))
+          dst[p] = A[i++];
+        else
+          dst[p] = B[j++];
+      }
+    }
+    __syncthreads();
+    unsigned long long* x = src;
+    src = dst;
+    dst = x;
+  }
+  write_outputs(src, len, start, t, tiles_x, n, proj, surfel_off, vals, emit, keys64);
+}
+
 // ---------------------------------------------------------------------------
 // workspace layout
 struct SortWs {
   unsigned long long* seg_keys;  // [cap]
+  unsigned long long* seg_tmp;   // [cap] merge buffer of long segments
   uint32_t* zero_begin;          // start of the zeroed region
   uint32_t* tile_count;          // [n_tiles]
   uint32_t* cursor;              // [n_tiles]
@@ -390,6 +477,7 @@ SortWs carve_sort_ws(void* base, int n, size_t cap, int n_tiles) {
   const size_t nn = (size_t)(n > 0 ? n : 1);
   w.chunks_n = (int)((nn + kChunk - 1) / kChunk);
   w.seg_keys = c.take<unsigned long long>(cap > 0 ? cap : 1);
+  w.seg_tmp = c.take<unsigned long long>(cap > 0 ? cap : 1);
   c.off = align_up(c.off, 256);
   const size_t zstart = c.off;
   w.zero_begin = base ? reinterpret_cast<uint32_t*>(static_cast<char*>(base) + zstart) : nullptr;
@@ -406,6 +494,22 @@ SortWs carve_sort_ws(void* base, int n, size_t cap, int n_tiles) {
   w.zero_words = words;
   w.bytes = align_up(zstart + words * sizeof(uint32_t), 256);
   return w;
+}
+
+// The long-segment kernel's dynamic shared memory exceeds the 48 KB default:
+// raise its limit once per device (before any stream capture that bins).
+cudaError_t long_sort_smem_ready(size_t bytes) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(tile_sort_long_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bytes);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
 }
 
 int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
@@ -454,6 +558,14 @@ int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
   const size_t smem = (size_t)kSegSmem * sizeof(unsigned long long);
   tile_sort_kernel<<<n_tiles, kSortThreads, smem, st>>>(
       p4, n, tx, bins->tile_ranges, w.seg_keys, need_emit ? bins->surfel_off : nullptr,
+      bins->vals, need_emit ? bins->isect_emit : nullptr,
+      reinterpret_cast<unsigned long long*>(bins->keys), cap, gate);
+  GS2D_LAUNCH_CHECK();
+  // segments longer than kSegSmem (blocks of shorter ones return at once)
+  const size_t long_smem = (size_t)kLongChunk * sizeof(unsigned long long);
+  if (long_sort_smem_ready(long_smem) != cudaSuccess) return GS2D_ERR_CUDA;
+  tile_sort_long_kernel<<<n_tiles, kLongThreads, long_smem, st>>>(
+      p4, n, tx, bins->tile_ranges, w.seg_keys, w.seg_tmp, need_emit ? bins->surfel_off : nullptr,
       bins->vals, need_emit ? bins->isect_emit : nullptr,
       reinterpret_cast<unsigned long long*>(bins->keys), cap, gate);
   GS2D_LAUNCH_CHECK();

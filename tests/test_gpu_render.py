@@ -51,7 +51,10 @@ def _records_to_proj(torch, rect, depth, count):
 
 @pytest.mark.parametrize("n,tiles_x,tiles_y,seed", [
     (0, 5, 4, 0), (1, 5, 4, 1), (7, 3, 2, 2), (4097, 10, 8, 3),
-    (20000, 40, 30, 4), (150_000, 75, 43, 5)])
+    (20000, 40, 30, 4), (150_000, 75, 43, 5),
+    # long tile segments: ~6k keys (one shared-memory chunk of the long
+    # path) and ~40k keys (three chunks, two merge passes) per tile
+    (9000, 2, 2, 6), (60000, 2, 2, 7)])
 def test_bin_sort_bit_exact(torch_cuda, orc, n, tiles_x, tiles_y, seed):
     torch = torch_cuda
     from paper_2506_00970_gb300 import gs2d
