@@ -1,0 +1,147 @@
+"""Small fixed workloads of the hot path, one per command, for profilers
+(ncu) and quick timing:  python -m paper_2506_00970_gb300.cases <case> [reps]
+
+  track    tracking frames: 200k-surfel room, 640x480, 10 iterations each
+  mapping  a batched mapping step: 300k-surfel room, 4 keyframes at 1200x680
+           (project, bin_sort, persistent forward, mapping loss, persistent
+           backward + per-surfel reductions)
+  uneven   a batched step over 8 views of mixed resolution with active
+           subsets of a 1M-surfel room
+  net      the proposal network at batch 256: forward, then forward + loss +
+           backward (gs2d_net_grad) + AdamW
+  sort     bin_sort of a 200k-surfel room at 160x120 (long tile segments)
+
+Each case runs ``reps`` times (default 3) after one warm-up and prints the
+mean device time per repetition (CUDA events).
+"""
+from __future__ import annotations
+
+import sys
+
+import numpy as np
+import torch
+
+from . import build as _build
+from . import gs2d, scenes
+
+
+def _timed(fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def case_track(reps):
+    s = scenes.room_scene(0, 200_000)
+    cam = scenes.tracking_camera()
+    ds = gs2d.DeviceSurfels(s)
+    r = gs2d.Rasterizer(cam, ds.n)
+    gt = scenes.room_pose(100)
+    out = r.forward(ds, gs2d.pose_tensor(gt))
+    obs_rgb = out["rgb"].clone()
+    obs_d = out["depth"] / out["opacity"].clamp_min(1e-6)
+    start = gs2d.pose_tensor(scenes.perturb_pose(gt, 0.02, 1.0, seed=5))
+    ccam, cfg = gs2d.camera(cam), gs2d.default_config()
+    prm = gs2d.default_track_params(stop_tol=0.0)
+    cap = 8 * ds.n
+    ws = torch.empty(gs2d.gs2d_track_workspace(ds.n, cap, ccam, cfg), dtype=torch.uint8, device="cuda")
+    pose = torch.empty(12, device="cuda")
+
+    def run():
+        pose.copy_(start)
+        gs2d.gs2d_track_step(ds, ccam, cfg, prm, pose, obs_rgb, obs_d, 10, cap, None, None, ws)
+
+    return _timed(run, reps)
+
+
+def _batch(s, cams, poses, actives, reps):
+    ds = gs2d.DeviceSurfels(s)
+    br = gs2d.BatchRasterizer(cams, ds.n, actives=actives)
+    br.set_poses(poses)
+    br.fit(ds)
+    br.forward(ds)
+    obs = [(b["rgb"].clone(), b["depth"] / b["opacity"].clamp_min(1e-6) + 0.01) for b in br.keep]
+    loss = torch.zeros(len(cams), device="cuda")
+    lws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+
+    def run():
+        br.forward(ds, check_status=False)
+        for v, b in enumerate(br.keep):
+            gs2d.gs2d_mapping_loss(b["rgb"], b["depth"], b["normal"], b["opacity"], obs[v][0],
+                                   obs[v][1], b["ccam"], 0.5, 0.02, b["d_rgb"], b["d_depth"],
+                                   b["d_normal"], b["d_opacity"], loss[v:v + 1], lws)
+        br.backward(ds)
+
+    return _timed(run, reps)
+
+
+def case_mapping(reps):
+    s = scenes.room_scene(1, 300_000)
+    poses = scenes.room_trajectory(2, 4)
+    return _batch(s, [scenes.mapping_camera()] * 4, poses, None, reps)
+
+
+def case_uneven(reps):
+    s = scenes.room_scene(3, 1_000_000)
+    cams, poses, actives = scenes.uneven_batch(4, s, 8, sizes=(50_000, 500_000))
+    return _batch(s, cams, poses, actives, reps)
+
+
+def case_net(reps):
+    B = 256
+    params = torch.tensor(scenes.net_init(0, gs2d.net_init_blocks()), device="cuda")
+    n = params.numel()
+    rng = np.random.default_rng(1)
+    x = torch.tensor(rng.uniform(-1, 1, (B, 120, 160, 8)), dtype=torch.float32,
+                     device="cuda").to(torch.bfloat16)
+    t = torch.tensor(rng.normal(0, 1, (B, 6)), dtype=torch.float32, device="cuda")
+    ws = torch.empty(gs2d.gs2d_net_workspace(B), dtype=torch.uint8, device="cuda")
+    y = torch.empty(B, 6, device="cuda")
+    grad = torch.empty(n, device="cuda")
+    m = torch.zeros(n, device="cuda")
+    v = torch.zeros(n, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    step = [0]
+
+    def run():
+        gs2d.gs2d_net_forward(params, x, y, ws)
+        gs2d.gs2d_net_grad(params, x, t, loss, grad, ws)
+        step[0] += 1
+        gs2d.gs2d_net_adamw(params, grad, m, v, step[0], lr=1e-4)
+
+    return _timed(run, reps)
+
+
+def case_sort(reps):
+    s = scenes.room_scene(100, 200_000)
+    cam = scenes.Camera(150.0, 150.0, 80.0, 60.0, 160, 120)
+    ds = gs2d.DeviceSurfels(s)
+    r = gs2d.Rasterizer(cam, ds.n, capacity=4 * ds.n)
+    r.project(ds, gs2d.pose_tensor(scenes.room_pose(3)))
+    return _timed(lambda: r.bin_sort(grow=False), reps)
+
+
+CASES = {"track": case_track, "mapping": case_mapping, "uneven": case_uneven, "net": case_net,
+         "sort": case_sort}
+
+
+def main(argv):
+    if len(argv) < 1 or argv[0] not in CASES:
+        print(__doc__)
+        return 2
+    reps = int(argv[1]) if len(argv) > 1 else 3
+    _build.build()
+    ms = CASES[argv[0]](reps)
+    print(f"{argv[0]}: {ms:.3f} ms per repetition")
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main(sys.argv[1:]))

@@ -273,81 +273,100 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ proj,
       if (kFull) sm.emit[threadIdx.x] = emit[idx];
     }
     __syncthreads();
-    for (int jj = cnt - 1; jj >= 0; --jj) {
-      const int jrel = bstart + jj - start;
-      float val[kRedVals];
-      bool contrib = false;
-      const float4 r6 = sm.rec[jj][6];
-      if (inside && jrel < (int)nl && warp_hits(r6.z, r6.w, tp.bx0, tp.by0)) {
-        const float4 r0 = sm.rec[jj][0], r1 = sm.rec[jj][1], r2 = sm.rec[jj][2];
-        Eval e;
-        if (eval_pair(r0, r1, r2, tp.lx, tp.ly, cam.near_z, cfg.cutoff_r2, cfg.alpha_min,
-                      cfg.alpha_max, e)) {
-          contrib = true;
-          const float4 r3 = sm.rec[jj][3], r4 = sm.rec[jj][4], r5 = sm.rec[jj][5];
-          const F3 col = f3(r2.w, r3.x, r3.y);
-          const F3 tn = f3(r3.z, r3.w, r4.x);
-          const F3 nrm = f3(r4.y, r4.z, r4.w);
-          const F3 du = f3(r5.x, r5.y, r5.z), dv = f3(r5.w, r6.x, r6.y);
-          const float om = 1.f - e.a;
-          const float iom = __fdividef(1.f, om);
-          const float Tb = T * iom;
-          const float w = e.a * Tb;
-          const float vj = dot3(col, gC) + e.z * gD + dot3(tn, gN);
-          const float ga = Tb * vj - (acc - gOT) * iom;
-          acc = fmaf(w, vj, acc);
-          T = Tb;
-          float galpha = 0.f, gG = 0.f;
-          if (e.araw <= cfg.alpha_max) {
-            galpha = e.G * ga;
-            gG = r2.z * ga;
+    // chunks of 32 staged entries, back to front; per chunk one ballot finds
+    // the entries whose footprint touches this warp's block, and only those
+    // are replayed (the others cannot reach any of its pixels)
+    for (int c_lo = ((cnt - 1) >> 5) << 5; c_lo >= 0; c_lo -= 32) {
+      const int c_n = min(32, cnt - c_lo);
+      bool h = false;
+      if (lane < c_n) {
+        const float4 r6 = sm.rec[c_lo + lane][6];
+        h = warp_hits(r6.z, r6.w, tp.bx0, tp.by0);
+      }
+      uint32_t hits = __ballot_sync(0xffffffffu, h);
+      if (kFull && !h) {
+        float4* z = reinterpret_cast<float4*>(&sm.red[warp][lane][0]);
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < kRedVals / 4; ++q) z[q] = zero;
+      }
+      while (hits) {
+        const int slot = 31 - __clz(hits);
+        hits &= ~(1u << slot);
+        const int jj = c_lo + slot;
+        const int jrel = bstart + jj - start;
+        float val[kRedVals];
+        bool contrib = false;
+        if (inside && jrel < (int)nl) {
+          const float4 r0 = sm.rec[jj][0], r1 = sm.rec[jj][1], r2 = sm.rec[jj][2];
+          Eval e;
+          if (eval_pair(r0, r1, r2, tp.lx, tp.ly, cam.near_z, cfg.cutoff_r2, cfg.alpha_min,
+                        cfg.alpha_max, e)) {
+            contrib = true;
+            const float4 r3 = sm.rec[jj][3], r4 = sm.rec[jj][4], r5 = sm.rec[jj][5];
+            const float4 r6 = sm.rec[jj][6];
+            const F3 col = f3(r2.w, r3.x, r3.y);
+            const F3 tn = f3(r3.z, r3.w, r4.x);
+            const F3 nrm = f3(r4.y, r4.z, r4.w);
+            const F3 du = f3(r5.x, r5.y, r5.z), dv = f3(r5.w, r6.x, r6.y);
+            const float om = 1.f - e.a;
+            const float iom = __fdividef(1.f, om);
+            const float Tb = T * iom;
+            const float w = e.a * Tb;
+            const float vj = dot3(col, gC) + e.z * gD + dot3(tn, gN);
+            const float ga = Tb * vj - (acc - gOT) * iom;
+            acc = fmaf(w, vj, acc);
+            T = Tb;
+            float galpha = 0.f, gG = 0.f;
+            if (e.araw <= cfg.alpha_max) {
+              galpha = e.G * ga;
+              gG = r2.z * ga;
+            }
+            const float gr2 = -0.5f * e.G * gG;
+            const float gu = 2.f * e.u * gr2, gv = 2.f * e.v * gr2;
+            const float gz = w * gD;
+            const F3 q = gu * du + gv * dv;
+            const float beta = (fmaf(q.x, rx, fmaf(q.y, ry, q.z)) + gz) * fxfy * e.rinv;
+            const F3 Gv = beta * nrm - q;
+            if (kFull) {
+              val[0] = Gv.x; val[1] = Gv.y; val[2] = Gv.z;
+              val[3] = e.u * Gv.x; val[4] = e.u * Gv.y; val[5] = e.u * Gv.z;
+              val[6] = e.v * Gv.x; val[7] = e.v * Gv.y; val[8] = e.v * Gv.z;
+              val[9] = galpha;
+              val[10] = w * gC.x; val[11] = w * gC.y; val[12] = w * gC.z;
+              val[13] = w * gN.x; val[14] = w * gN.y; val[15] = w * gN.z;
+            } else {
+              const F3 X = f3(e.z * rx, e.z * ry, e.z);
+              const F3 gtn = w * gN;
+              const F3 th = cross3(X, Gv) + cross3(tn, gtn);
+              pr[0] += Gv.x; pr[1] += Gv.y; pr[2] += Gv.z;
+              pr[3] += th.x; pr[4] += th.y; pr[5] += th.z;
+            }
           }
-          const float gr2 = -0.5f * e.G * gG;
-          const float gu = 2.f * e.u * gr2, gv = 2.f * e.v * gr2;
-          const float gz = w * gD;
-          const F3 q = gu * du + gv * dv;
-          const float beta = (fmaf(q.x, rx, fmaf(q.y, ry, q.z)) + gz) * fxfy * e.rinv;
-          const F3 Gv = beta * nrm - q;
-          if (kFull) {
-            val[0] = Gv.x; val[1] = Gv.y; val[2] = Gv.z;
-            val[3] = e.u * Gv.x; val[4] = e.u * Gv.y; val[5] = e.u * Gv.z;
-            val[6] = e.v * Gv.x; val[7] = e.v * Gv.y; val[8] = e.v * Gv.z;
-            val[9] = galpha;
-            val[10] = w * gC.x; val[11] = w * gC.y; val[12] = w * gC.z;
-            val[13] = w * gN.x; val[14] = w * gN.y; val[15] = w * gN.z;
-          } else {
-            const F3 X = f3(e.z * rx, e.z * ry, e.z);
-            const F3 gtn = w * gN;
-            const F3 th = cross3(X, Gv) + cross3(tn, gtn);
-            pr[0] += Gv.x; pr[1] += Gv.y; pr[2] += Gv.z;
-            pr[3] += th.x; pr[4] += th.y; pr[5] += th.z;
+        }
+        if (kFull) {
+          if (__any_sync(0xffffffffu, contrib)) {
+            if (!contrib) {
+#pragma unroll
+              for (int i = 0; i < kRedVals; ++i) val[i] = 0.f;
+            }
+            warp_reduce_scatter16(val, lane);
+            if ((lane & 1) == 0) sm.red[warp][slot][lane >> 1] = val[0];
+          } else if (lane < kRedVals) {
+            sm.red[warp][slot][lane] = 0.f;
           }
         }
       }
       if (kFull) {
-        const int slot = jj & 31;
-        if (__any_sync(0xffffffffu, contrib)) {
-          if (!contrib) {
+        __syncthreads();
+        for (int o = threadIdx.x; o < c_n * kRedVals; o += kTileThreads) {
+          const int s = o / kRedVals, c = o % kRedVals;
+          float sum = 0.f;
 #pragma unroll
-            for (int i = 0; i < kRedVals; ++i) val[i] = 0.f;
-          }
-          warp_reduce_scatter16(val, lane);
-          if ((lane & 1) == 0) sm.red[warp][slot][lane >> 1] = val[0];
-        } else if (lane < kRedVals) {
-          sm.red[warp][slot][lane] = 0.f;
+          for (int ww = 0; ww < 8; ++ww) sum += sm.red[ww][s][c];
+          partials[(size_t)sm.emit[c_lo + s] * kRedVals + c] = sum;
         }
-        if (slot == 0) {
-          __syncthreads();
-          const int gs = min(32, cnt - jj);
-          for (int o = threadIdx.x; o < gs * kRedVals; o += kTileThreads) {
-            const int s = o / kRedVals, c = o % kRedVals;
-            float sum = 0.f;
-#pragma unroll
-            for (int ww = 0; ww < 8; ++ww) sum += sm.red[ww][s][c];
-            partials[(size_t)sm.emit[jj + s] * kRedVals + c] = sum;
-          }
-          __syncthreads();
-        }
+        __syncthreads();
       }
     }
   }
