@@ -37,7 +37,10 @@ namespace net {
 
 typedef __nv_bfloat16 bf16;
 
-enum Mode { K_DENSE = 0, K_IM2COL = 1, K_DGRAD = 2, R_DENSE = 3, R_IM2COL = 4, R_WT = 5 };
+enum Mode {
+  K_DENSE = 0, K_IM2COL = 1, K_DGRAD = 2, K_DGRADP = 3,  // K-major
+  R_DENSE = 4, R_IM2COL = 5, R_WT = 6, R_WTP = 7         // row-major
+};
 enum Epi { E_BIAS_RELU = 0, E_BIAS_F32 = 1, E_MASK = 2, E_PARTIAL = 3 };
 
 constexpr int BM = 128, BN = 64, BK = 32, STAGES = 3, THREADS = 256, PAD = 8;
@@ -54,10 +57,22 @@ constexpr int kOutPad = 8;  // FC2 rows padded to 8 in the bf16 weight copy
 
 struct Operand {
   const bf16* p;
-  int ld;                // dense modes: leading dimension; R_WT: C_out
+  int ld;                // dense modes: leading dimension; R_WT(P): C_out
   int rows;              // valid rows (M or N); multiple of 8 for row-major modes
   int H, W, C, Ho, Wo;   // conv geometry (input H x W x C, output Ho x Wo)
+  int py, px, Hc, Wc;    // parity class of the data gradient (K_DGRADP, R_WTP)
 };
+
+// Taps of a parity class of the stride-2 data gradient: input row iy gets
+// contributions from ky = 1 when iy is even and ky in {0, 2} when it is odd
+// (iy + 1 - ky must be even); likewise for columns.  Tap t of the class is
+// (t / nx, t % nx) over its ny x nx taps.
+__device__ __forceinline__ void class_tap(int py, int px, int t, int& ky, int& kx) {
+  const int nx = px ? 2 : 1;
+  const int tyi = t / nx, txi = t - tyi * nx;
+  ky = py ? 2 * tyi : 1;
+  kx = px ? 2 * txi : 1;
+}
 
 struct Gemm {
   int M, N, K, k_split;
@@ -67,6 +82,10 @@ struct Gemm {
   const float* bias;
   const bf16* mask;
   int n_valid;
+  void* part;            // split-K partials [S][M][N] (FP32)
+  // output row remap of a parity-class data gradient: GEMM row (b, cy, cx)
+  // -> pixel (b, 2 cy + py, 2 cx + px) of an H x W map
+  int remap, rH, rW, rHc, rWc, rpy, rpx;
 };
 
 template <int MODE>
@@ -80,6 +99,17 @@ __device__ __forceinline__ const bf16* kmajor_addr(const Operand& o, int row, in
     const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
     if (iy < 0 || iy >= o.H || ix < 0 || ix >= o.W) return nullptr;
     return o.p + (((size_t)b * o.H + iy) * o.W + ix) * o.C + c;
+  }
+  if (MODE == K_DGRADP) {
+    const int hw = o.Hc * o.Wc;
+    const int b = row / hw, r = row - b * hw, cy = r / o.Wc, cx = r - cy * o.Wc;
+    const int iy = 2 * cy + o.py, ix = 2 * cx + o.px;
+    const int t = k / o.C, c = k - t * o.C;
+    int ky, kx;
+    class_tap(o.py, o.px, t, ky, kx);
+    const int oy = (iy + 1 - ky) >> 1, ox = (ix + 1 - kx) >> 1;
+    if (oy < 0 || oy >= o.Ho || ox < 0 || ox >= o.Wo) return nullptr;
+    return o.p + (((size_t)b * o.Ho + oy) * o.Wo + ox) * o.C + c;
   }
   // K_DGRAD
   const int hw = o.H * o.W;
@@ -103,6 +133,12 @@ __device__ __forceinline__ const bf16* rowmajor_addr(const Operand& o, int row0,
     const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
     if (iy < 0 || iy >= o.H || ix < 0 || ix >= o.W) return nullptr;
     return o.p + (((size_t)b * o.H + iy) * o.W + ix) * o.C + c;
+  }
+  if (MODE == R_WTP) {
+    const int t = k / o.ld, co = k - t * o.ld;
+    int ky, kx;
+    class_tap(o.py, o.px, t, ky, kx);
+    return o.p + ((size_t)co * 9 + ky * 3 + kx) * o.C + row0;
   }
   // R_WT
   const int tap = k / o.ld, co = k - tap * o.ld;
@@ -143,7 +179,7 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32
 
 template <int MODE>
 __host__ __device__ constexpr bool is_kmajor() {
-  return MODE <= K_DGRAD;
+  return MODE < R_DENSE;
 }
 template <int MODE, int ROWS>
 __host__ __device__ constexpr int tile_elems() {
@@ -186,29 +222,56 @@ __device__ __forceinline__ void frag_b(uint32_t b[4], const bf16* s, int n0, int
     ldsm_x4_t(b, s + (k0 + 8 * (i & 1) + rr) * (ROWS + PAD) + n0 + 8 * (i >> 1));
 }
 
+// Output offset of GEMM row `row` (times the row stride ldc).
+__device__ __forceinline__ size_t out_row(const Gemm& g, int row) {
+  if (!g.remap) return (size_t)row;
+  const int hw = g.rHc * g.rWc;
+  const int b = row / hw, r = row - b * hw, cy = r / g.rWc, cx = r - cy * g.rWc;
+  return ((size_t)b * g.rH + 2 * cy + g.rpy) * g.rW + 2 * cx + g.rpx;
+}
+
 template <int EPI>
-__device__ __forceinline__ void store2(const Gemm& g, int row, int col, float v0, float v1) {
+__device__ __forceinline__ void apply_epi(const Gemm& g, int row, int col, float v0, float v1) {
   if (row >= g.M) return;
   if (EPI == E_BIAS_RELU) {
     if (col >= g.N) return;
     const float x0 = fmaxf(v0 + g.bias[col], 0.f), x1 = fmaxf(v1 + g.bias[col + 1], 0.f);
-    *reinterpret_cast<__nv_bfloat162*>(static_cast<bf16*>(g.out) + (size_t)row * g.ldc + col) =
+    *reinterpret_cast<__nv_bfloat162*>(static_cast<bf16*>(g.out) + out_row(g, row) * g.ldc + col) =
         __floats2bfloat162_rn(x0, x1);
   } else if (EPI == E_BIAS_F32) {
-    float* o = static_cast<float*>(g.out) + (size_t)row * g.ldc;
+    float* o = static_cast<float*>(g.out) + out_row(g, row) * g.ldc;
     if (col < g.n_valid) o[col] = v0 + g.bias[col];
     if (col + 1 < g.n_valid) o[col + 1] = v1 + g.bias[col + 1];
   } else if (EPI == E_MASK) {
     if (col >= g.N) return;
-    const size_t off = (size_t)row * g.ldc + col;
+    const size_t off = out_row(g, row) * g.ldc + col;
     const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(g.mask + off);
     const float x0 = __bfloat162float(m.x) > 0.f ? v0 : 0.f;
     const float x1 = __bfloat162float(m.y) > 0.f ? v1 : 0.f;
     *reinterpret_cast<__nv_bfloat162*>(static_cast<bf16*>(g.out) + off) = __floats2bfloat162_rn(x0, x1);
   } else {
     if (col >= g.N) return;
-    float* o = static_cast<float*>(g.out) + ((size_t)blockIdx.z * g.M + row) * g.N + col;
+    float* o = static_cast<float*>(g.part) + ((size_t)blockIdx.z * g.M + row) * g.N + col;
     *reinterpret_cast<float2*>(o) = make_float2(v0, v1);
+  }
+}
+
+// Sums the split-K partials of column pairs in split order and applies the
+// epilogue.
+template <int EPI>
+__global__ void splitk_epilogue_kernel(const Gemm g, int S) {
+  const size_t pairs = (size_t)g.M * (g.N / 2);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < pairs;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int row = (int)(e / (g.N / 2)), col = 2 * (int)(e % (g.N / 2));
+    float v0 = 0.f, v1 = 0.f;
+    for (int z = 0; z < S; ++z) {
+      const float2 p = *reinterpret_cast<const float2*>(
+          static_cast<const float*>(g.part) + ((size_t)z * g.M + row) * g.N + col);
+      v0 += p.x;
+      v1 += p.y;
+    }
+    apply_epi<EPI>(g, row, col, v0, v1);
   }
 }
 
@@ -274,8 +337,8 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const Gemm g) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int row = m0 + wm + 16 * i + gq, col = n0 + wn + 8 * j + 2 * cq;
-      store2<EPI>(g, row, col, acc[i][j][0], acc[i][j][1]);
-      store2<EPI>(g, row + 8, col, acc[i][j][2], acc[i][j][3]);
+      apply_epi<EPI>(g, row, col, acc[i][j][0], acc[i][j][1]);
+      apply_epi<EPI>(g, row + 8, col, acc[i][j][2], acc[i][j][3]);
     }
 }
 
@@ -293,22 +356,36 @@ __global__ void reduce_partials_kernel(const float* __restrict__ part, int S, in
   }
 }
 
-// Column sums of a bf16 matrix [rows][C] (C divides 256) over row chunks:
-// part[chunk * C + c]; rows of a chunk are summed in a fixed order.
+// Column sums of a bf16 matrix [rows][C] (C a multiple of 8 dividing 2048)
+// over chunks of rows: part[chunk * C + c].  Thread t sums columns
+// 8 (t % (C/8)) .. +7 over rows sub, sub + nsub, ... of the chunk (16-byte
+// loads, a warp reads whole rows); the subs are then added in order.
 __global__ void __launch_bounds__(256) colsum_partial_kernel(const bf16* __restrict__ z, int rows,
                                                              int C, int rows_per_block,
                                                              float* __restrict__ part) {
-  __shared__ float s[256];
-  const int t = threadIdx.x, nsub = 256 / C, col = t % C, sub = t / C;
+  __shared__ float s[256 * 8];
+  const int t = threadIdx.x, groups = C / 8, nsub = 256 / groups;
+  const int g8 = t % groups, sub = t / groups;
   const int r0 = blockIdx.x * rows_per_block, r1 = min(rows, r0 + rows_per_block);
-  float acc = 0.f;
-  for (int r = r0 + sub; r < r1; r += nsub) acc += __bfloat162float(z[(size_t)r * C + col]);
-  s[t] = acc;
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (sub < nsub)
+    for (int r = r0 + sub; r < r1; r += nsub) {
+      const uint4 v = *reinterpret_cast<const uint4*>(z + (size_t)r * C + 8 * g8);
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[2 * q] += __low2float(h[q]);
+        acc[2 * q + 1] += __high2float(h[q]);
+      }
+    }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s[t * 8 + q] = acc[q];
   __syncthreads();
-  if (t < C) {
+  for (int c = t; c < C; c += 256) {
+    const int gc = c / 8, q = c % 8;
     float tot = 0.f;
-    for (int k = 0; k < nsub; ++k) tot += s[k * C + t];
-    part[(size_t)blockIdx.x * C + t] = tot;
+    for (int k = 0; k < nsub; ++k) tot += s[(k * groups + gc) * 8 + q];
+    part[(size_t)blockIdx.x * C + c] = tot;
   }
 }
 
@@ -522,6 +599,23 @@ int splits_for(int M, int N, int K) {
 }
 int k_split_for(int K, int s) { return (int)align_up((size_t)((K + s - 1) / s), BK); }
 
+// Split-K count of a forward or data-gradient GEMM from its shape per sample
+// at a nominal batch of 256 -- never from the actual batch, so every output
+// row sums the same K ranges in the same order whatever the batch size.
+constexpr int kNominalBatch = 256;
+int splits_nominal(int rows_per_sample, int N, int K) {
+  const long long tiles = ((long long)rows_per_sample * kNominalBatch + BM - 1) / BM *
+                          ((N + BN - 1) / BN);
+  if (tiles >= 2 * 152) return 1;
+  const int s = (int)((2 * 152 + tiles - 1) / tiles);
+  return max(1, min(s, K / 128));
+}
+int splits_count(int K, int s) {
+  const int ks = s > 1 ? k_split_for(K, s) : (int)align_up((size_t)K, BK);
+  return max((K + ks - 1) / ks, 1);
+}
+int class_hc(int H, int py) { return (H + 1 - py) / 2; }
+
 size_t max_partials(int B) {
   size_t mx = 0;
   auto upd = [&](int M, int N, int K) {
@@ -530,13 +624,25 @@ size_t max_partials(int B) {
     const int S = (K + ks - 1) / ks;
     mx = max(mx, (size_t)S * M * N);
   };
+  auto nom = [&](int rps, int N, int K) {
+    mx = max(mx, (size_t)splits_count(K, splits_nominal(rps, N, K)) * B * rps * N);
+  };
   for (int l = 0; l < kConv; ++l) {
     upd(kCout[l], 9 * kCin[l], B * kHin[l + 1] * kWin[l + 1]);
     const int rows = B * kHin[l + 1] * kWin[l + 1];
     mx = max(mx, (size_t)((rows + 1023) / 1024) * kCout[l]);
+    nom(kHin[l + 1] * kWin[l + 1], kCout[l], 9 * kCin[l]);
+    for (int py = 0; py < 2; ++py)
+      for (int px = 0; px < 2; ++px)
+        nom(class_hc(kHin[l], py) * class_hc(kWin[l], px), kCin[l],
+            (py ? 2 : 1) * (px ? 2 : 1) * kCout[l]);
   }
   upd(kHidden, kFlat, B);
   upd(kOutPad, kHidden, B);
+  nom(1, kHidden, kFlat);
+  nom(1, kOutPad, kHidden);
+  nom(1, kFlat, kHidden);
+  nom(1, kHidden, kOutPad);
   mx = max(mx, (size_t)((B + 1023) / 1024) * kHidden);
   return mx;
 }
@@ -595,10 +701,28 @@ int run(Gemm g, int splits, cudaStream_t st, int* n_splits = nullptr) {
   return GS2D_OK;
 }
 
+// A forward or data-gradient GEMM with its epilogue: split-K (at the
+// nominal-batch count for rows_per_sample) through FP32 partials and a
+// fixed-order reduction when the tile grid is small.
+template <int AM, int BMODE, int EPI>
+int fused(Gemm g, int rows_per_sample, float* part, cudaStream_t st) {
+  const int s = splits_nominal(rows_per_sample, g.N, g.K);
+  if (s <= 1) return run<AM, BMODE, EPI>(g, 1, st);
+  g.part = part;
+  int S = 0;
+  int r = run<AM, BMODE, E_PARTIAL>(g, s, st, &S);
+  if (r) return r;
+  const size_t pairs = (size_t)g.M * (g.N / 2);
+  const int blocks = (int)max((size_t)1, min((pairs + 255) / 256, (size_t)4096));
+  splitk_epilogue_kernel<EPI><<<blocks, 256, 0, st>>>(g, S);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
 // weight gradient by split-K partials, reduced into out (m_valid x N)
 template <int AM, int BMODE>
 int wgrad(Gemm g, int m_valid, float* part, float* out, cudaStream_t st) {
-  g.out = part;
+  g.part = part;
   int S = 0;
   const int r = run<AM, BMODE, E_PARTIAL>(g, splits_for(g.M, g.N, g.K), st, &S);
   if (r) return r;
@@ -648,7 +772,7 @@ int forward(const float* params, const bf16* x, int B, const Ws& w, float* y, cu
     g.out = w.act[l + 1];
     g.ldc = g.N;
     g.bias = params + L.b_off[l];
-    r = run<K_IM2COL, K_DENSE, E_BIAS_RELU>(g, 1, st);
+    r = fused<K_IM2COL, K_DENSE, E_BIAS_RELU>(g, kHin[l + 1] * kWin[l + 1], w.part, st);
     if (r) return r;
     in = w.act[l + 1];
   }
@@ -662,7 +786,7 @@ int forward(const float* params, const bf16* x, int B, const Ws& w, float* y, cu
     g.out = w.h;
     g.ldc = kHidden;
     g.bias = params + L.b_off[kConv];
-    r = run<K_DENSE, K_DENSE, E_BIAS_RELU>(g, 1, st);
+    r = fused<K_DENSE, K_DENSE, E_BIAS_RELU>(g, 1, w.part, st);
     if (r) return r;
   }
   {
@@ -676,7 +800,7 @@ int forward(const float* params, const bf16* x, int B, const Ws& w, float* y, cu
     g.ldc = kOut;
     g.bias = params + L.b_off[kConv + 1];
     g.n_valid = kOut;
-    r = run<K_DENSE, K_DENSE, E_BIAS_F32>(g, 1, st);
+    r = fused<K_DENSE, K_DENSE, E_BIAS_F32>(g, 1, w.part, st);
     if (r) return r;
   }
   return GS2D_OK;
@@ -706,7 +830,7 @@ int backward(const float* params, const bf16* x, int B, const Ws& w, float* grad
     d.out = w.dzA;
     d.ldc = kHidden;
     d.mask = w.h;
-    r = run<K_DENSE, R_DENSE, E_MASK>(d, 1, st);
+    r = fused<K_DENSE, R_DENSE, E_MASK>(d, 1, w.part, st);
     if (r) return r;
   }
   // FC1: dz1 = dzA [B][256]
@@ -730,7 +854,7 @@ int backward(const float* params, const bf16* x, int B, const Ws& w, float* grad
     d.out = w.dzB;
     d.ldc = kFlat;
     d.mask = w.act[kConv];
-    r = run<K_DENSE, R_DENSE, E_MASK>(d, 1, st);
+    r = fused<K_DENSE, R_DENSE, E_MASK>(d, 1, w.part, st);
     if (r) return r;
   }
   // conv layers, last to first: dz of layer l's output is in cur
@@ -750,22 +874,41 @@ int backward(const float* params, const bf16* x, int B, const Ws& w, float* grad
     r = bias_grad(cur, P, kCout[l], kCout[l], w.part, grad + L.b_off[l], st);
     if (r) return r;
     if (l == 0) break;
-    Gemm d{};
-    d.M = B * kHin[l] * kWin[l];
-    d.N = kCin[l];
-    d.K = 9 * kCout[l];
-    d.a = conv_op(cur, d.M, l, kCout[l]);
-    Operand wt{};
-    wt.p = w.wbf + L.wbf_off[l];
-    wt.ld = kCout[l];
-    wt.rows = kCin[l];
-    wt.C = kCin[l];
-    d.b = wt;
-    d.out = nxt;
-    d.ldc = kCin[l];
-    d.mask = w.act[l];
-    r = run<K_DGRAD, R_WT, E_MASK>(d, 1, st);
-    if (r) return r;
+    // data gradient: one GEMM per parity class of the input pixels, each
+    // with only the taps that reach it (9 taps over the 4 classes)
+    for (int py = 0; py < 2; ++py)
+      for (int px = 0; px < 2; ++px) {
+        const int Hc = class_hc(kHin[l], py), Wc = class_hc(kWin[l], px);
+        Gemm d{};
+        d.M = B * Hc * Wc;
+        d.N = kCin[l];
+        d.K = (py ? 2 : 1) * (px ? 2 : 1) * kCout[l];
+        d.a = conv_op(cur, d.M, l, kCout[l]);
+        d.a.py = py;
+        d.a.px = px;
+        d.a.Hc = Hc;
+        d.a.Wc = Wc;
+        Operand wt{};
+        wt.p = w.wbf + L.wbf_off[l];
+        wt.ld = kCout[l];
+        wt.rows = kCin[l];
+        wt.C = kCin[l];
+        wt.py = py;
+        wt.px = px;
+        d.b = wt;
+        d.out = nxt;
+        d.ldc = kCin[l];
+        d.mask = w.act[l];
+        d.remap = 1;
+        d.rH = kHin[l];
+        d.rW = kWin[l];
+        d.rHc = Hc;
+        d.rWc = Wc;
+        d.rpy = py;
+        d.rpx = px;
+        r = fused<K_DGRADP, R_WTP, E_MASK>(d, Hc * Wc, w.part, st);
+        if (r) return r;
+      }
     bf16* t = cur;
     cur = nxt;
     nxt = t;
