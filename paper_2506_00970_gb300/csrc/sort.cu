@@ -218,6 +218,8 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
                                                         int n_tiles, int32_t* __restrict__ ranges,
                                                         int32_t* __restrict__ n_isect,
                                                         long long capacity,
+                                                        uint32_t* __restrict__ long_list,
+                                                        uint32_t* __restrict__ n_long,
                                                         int32_t* __restrict__ gate) {
   __shared__ uint32_t s_w[32];
   __shared__ uint32_t s_carry;
@@ -251,6 +253,7 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
     if (t < n_tiles) {
       ranges[2 * t] = (int32_t)start;
       ranges[2 * t + 1] = (int32_t)(start + c);
+      if (c > (uint32_t)kSegSmem) long_list[atomicAdd(n_long, 1u)] = (uint32_t)t;
     }
     __syncthreads();
     if (threadIdx.x == 1023) s_carry = start + c;
@@ -400,14 +403,14 @@ __device__ __forceinline__ int co_rank(const unsigned long long* A, int la, cons
 // shared memory by 1024 threads, then adjacent sorted runs are merged in
 // global memory (seg_keys <-> seg_tmp), each thread producing a contiguous
 // span of the output located by a co-rank search.
-__global__ void __launch_bounds__(kLongThreads) tile_sort_long_kernel(
-    const float4* __restrict__ proj, int n, int tiles_x, const int32_t* __restrict__ ranges,
-    unsigned long long* __restrict__ seg_keys, unsigned long long* __restrict__ seg_tmp,
-    const uint32_t* __restrict__ surfel_off, uint32_t* __restrict__ vals, uint32_t* __restrict__ emit,
-    unsigned long long* __restrict__ keys64, long long capacity, const int32_t* __restrict__ gate) {
-  extern __shared__ unsigned long long s_keys[];
-  if (*gate) return;
-  const int t = blockIdx.x;
+// One long segment (tile t) by the whole block.
+__device__ void sort_long_segment(int t, const float4* __restrict__ proj, int n, int tiles_x,
+                                  const int32_t* __restrict__ ranges,
+                                  unsigned long long* __restrict__ seg_keys,
+                                  unsigned long long* __restrict__ seg_tmp,
+                                  const uint32_t* __restrict__ surfel_off, uint32_t* __restrict__ vals,
+                                  uint32_t* __restrict__ emit, unsigned long long* __restrict__ keys64,
+                                  long long capacity, unsigned long long* s_keys) {
   const int start = ranges[2 * t];
   const int end = (int)min((long long)ranges[2 * t + 1], capacity);
   const int len = end - start;
@@ -456,11 +459,31 @@ __global__ void __launch_bounds__(kLongThreads) tile_sort_long_kernel(
   write_outputs(src, len, start, t, tiles_x, n, proj, surfel_off, vals, emit, keys64);
 }
 
+// Segments longer than kSegSmem, listed by the tile scan: a small persistent
+// grid takes them one per block.
+__global__ void __launch_bounds__(kLongThreads) tile_sort_long_kernel(
+    const float4* __restrict__ proj, int n, int tiles_x, const int32_t* __restrict__ ranges,
+    const uint32_t* __restrict__ long_list, const uint32_t* __restrict__ n_long,
+    unsigned long long* __restrict__ seg_keys, unsigned long long* __restrict__ seg_tmp,
+    const uint32_t* __restrict__ surfel_off, uint32_t* __restrict__ vals, uint32_t* __restrict__ emit,
+    unsigned long long* __restrict__ keys64, long long capacity, const int32_t* __restrict__ gate) {
+  extern __shared__ unsigned long long s_keys[];
+  if (*gate) return;
+  const int cnt = (int)*n_long;
+  for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+    sort_long_segment((int)long_list[i], proj, n, tiles_x, ranges, seg_keys, seg_tmp, surfel_off,
+                      vals, emit, keys64, capacity, s_keys);
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // workspace layout
 struct SortWs {
   unsigned long long* seg_keys;  // [cap]
   unsigned long long* seg_tmp;   // [cap] merge buffer of long segments
+  uint32_t* long_list;           // [n_tiles] tiles with segments over kSegSmem
+  uint32_t* n_long;              // [1] (zeroed per call)
   uint32_t* zero_begin;          // start of the zeroed region
   uint32_t* tile_count;          // [n_tiles]
   uint32_t* cursor;              // [n_tiles]
@@ -478,6 +501,7 @@ SortWs carve_sort_ws(void* base, int n, size_t cap, int n_tiles) {
   w.chunks_n = (int)((nn + kChunk - 1) / kChunk);
   w.seg_keys = c.take<unsigned long long>(cap > 0 ? cap : 1);
   w.seg_tmp = c.take<unsigned long long>(cap > 0 ? cap : 1);
+  w.long_list = c.take<uint32_t>((size_t)(n_tiles > 0 ? n_tiles : 1));
   c.off = align_up(c.off, 256);
   const size_t zstart = c.off;
   w.zero_begin = base ? reinterpret_cast<uint32_t*>(static_cast<char*>(base) + zstart) : nullptr;
@@ -490,6 +514,7 @@ SortWs carve_sort_ws(void* base, int n, size_t cap, int n_tiles) {
   w.tile_count = zt((size_t)n_tiles);
   w.cursor = zt((size_t)n_tiles);
   w.ticket = zt(8);
+  w.n_long = zt(1);
   w.estatus = reinterpret_cast<unsigned long long*>(zt((size_t)2 * w.chunks_n + 2));
   w.zero_words = words;
   w.bytes = align_up(zstart + words * sizeof(uint32_t), 256);
@@ -549,7 +574,7 @@ int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
     }
   }
   tile_scan_kernel<<<1, 1024, 0, st>>>(w.tile_count, n_tiles, bins->tile_ranges, bins->n_isect, cap,
-                                       gate);
+                                       w.long_list, w.n_long, gate);
   GS2D_LAUNCH_CHECK();
   if (n == 0) return GS2D_OK;
   scatter_kernel<<<(n + 255) / 256, 256, 2 * hist_smem, st>>>(
@@ -564,8 +589,9 @@ int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
   // segments longer than kSegSmem (blocks of shorter ones return at once)
   const size_t long_smem = (size_t)kLongChunk * sizeof(unsigned long long);
   if (long_sort_smem_ready(long_smem) != cudaSuccess) return GS2D_ERR_CUDA;
-  tile_sort_long_kernel<<<n_tiles, kLongThreads, long_smem, st>>>(
-      p4, n, tx, bins->tile_ranges, w.seg_keys, w.seg_tmp, need_emit ? bins->surfel_off : nullptr,
+  tile_sort_long_kernel<<<min(n_tiles, 152), kLongThreads, long_smem, st>>>(
+      p4, n, tx, bins->tile_ranges, w.long_list, w.n_long, w.seg_keys, w.seg_tmp,
+      need_emit ? bins->surfel_off : nullptr,
       bins->vals, need_emit ? bins->isect_emit : nullptr,
       reinterpret_cast<unsigned long long*>(bins->keys), cap, gate);
   GS2D_LAUNCH_CHECK();
