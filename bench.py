@@ -483,9 +483,9 @@ def measure_batch(name, s_true, cams, poses, actives, K, W_, flush, seed):
     ds_true = gs2d.DeviceSurfels(s_true)
     ds = gs2d.DeviceSurfels(_perturbed_map(s_true, seed))
     t0 = time.perf_counter()
-    tiles, sweep = autotune.tune_tiles(ds, cams, poses, actives)
+    px, tiles, sweep = autotune.tune(ds, cams, poses, actives)
     tune_s = time.perf_counter() - t0
-    br = gs2d.BatchRasterizer(cams, ds.n, actives=actives, tiles=tiles)
+    br = gs2d.BatchRasterizer(cams, ds.n, actives=actives, tiles=tiles, px=px)
     br.set_poses(poses)
     br.fit(ds_true)
     br.forward(ds_true)
@@ -585,7 +585,8 @@ def measure_batch(name, s_true, cams, poses, actives, K, W_, flush, seed):
         "views": len(cams), "pixels": P, "surfels": int(ds.n),
         "active_sizes": [int(b["m"]) for b in br.keep], "intersections": [int(k) for k in kv],
         "resolutions": sorted({f"{c.width}x{c.height}" for c in cams}),
-        "tiles": [f"{t[0]}x{t[1]}" for t in tiles], "autotune_ms": sweep,
+        "px_per_thread": px, "tiles": [f"{t[0]}x{t[1]}" for t in tiles],
+        "autotune_ms_per_view": sweep,
         "autotune_s": tune_s, "loss": [float(x) for x in loss.cpu().numpy()],
         "pairs": {"evaluated": int(E[0]), "inside_cutoff": int(E[1]), "blended": int(E[2])},
         "roofline": [

@@ -1,15 +1,15 @@
-"""Tile-shape autotuner for batched rendering.
+"""Tile-shape and pixels-per-thread autotuner for batched rendering.
 
-For every resolution class (width x height) of a batch, each candidate tile
-shape is timed on a forward + backward pass of up to ``max_views`` of that
-class's views (CUDA events on the launching stream, the median of ``reps``
-repetitions after one warm-up) and the fastest is kept.  Results are cached
-per device name and resolution class, in memory and optionally in a JSON file,
-so a later batch with the same classes skips the sweep.
-
-The compositing kernels map one thread to one pixel (a 256-thread block per
-tile), so the candidates are the three 256-pixel shapes; the pixels-per-thread
-field of the config stays 1.
+For every pixels-per-thread count P (1, 2, 4) and every resolution class
+(width x height) of a batch, each tile shape of P is timed on a forward +
+backward pass of up to ``max_views`` of that class's views (CUDA events on
+the launching stream, the median of ``reps`` repetitions after one warm-up);
+the fastest shape per class is kept.  One batched launch runs one P, so P is
+chosen for the whole batch: the one whose per-class best times, weighted by
+the number of views in each class, sum lowest.  Results are cached per device
+name and resolution class (and the P decision per set of classes), in memory
+and optionally in a JSON file, so a later batch with the same classes skips
+the sweep.
 """
 from __future__ import annotations
 
@@ -21,13 +21,14 @@ import torch
 
 from . import gs2d
 
-TILE_SHAPES = ((16, 16), (8, 32), (32, 8))
+TILE_SHAPES = gs2d.TILE_SHAPES
+PX_COUNTS = (1, 2, 4)
 
-_cache: dict[str, list[int]] = {}
+_cache: dict[str, list] = {}
 
 
-def _key(device_name: str, w: int, h: int) -> str:
-    return f"{device_name}|{w}x{h}"
+def _key(device_name: str, w: int, h: int, px: int) -> str:
+    return f"{device_name}|{w}x{h}|px{px}"
 
 
 def _load(path):
@@ -46,11 +47,11 @@ def _store(path):
             json.dump(_cache, f, indent=1, sort_keys=True)
 
 
-def time_batch(surf, cams, poses, actives, tile, reps=3, stream=None):
+def time_batch(surf, cams, poses, actives, tile, px=1, reps=3, stream=None):
     """Median ms of project + bin_sort + forward + backward of one batch with
-    one tile shape for all views (unit upstream gradients on colour and
-    depth)."""
-    br = gs2d.BatchRasterizer(cams, surf.n, actives=actives, tiles=[tile] * len(cams))
+    one tile shape and pixels-per-thread count for all views (unit upstream
+    gradients on colour and depth)."""
+    br = gs2d.BatchRasterizer(cams, surf.n, actives=actives, tiles=[tile] * len(cams), px=px)
     br.set_poses(poses)
     br.fit(surf)
     for b in br.keep:
@@ -75,33 +76,46 @@ def time_batch(surf, cams, poses, actives, tile, reps=3, stream=None):
     return float(np.median(ms))
 
 
-def tune_tiles(surf, cams, poses, actives=None, max_views=3, reps=3, cache_path=None,
-               stream=None):
-    """Tile shape per view: the fastest candidate of the view's resolution
-    class.  Returns (tiles per view, sweep table {class: {tile: ms}})."""
+def tune(surf, cams, poses, actives=None, max_views=3, reps=3, cache_path=None, stream=None,
+         px_counts=PX_COUNTS):
+    """(P, tile shape per view, sweep table {"pxP": {class: {tile: ms}}})."""
     _load(cache_path)
     dev = torch.cuda.get_device_name()
     classes: dict[tuple[int, int], list[int]] = {}
     for v, c in enumerate(cams):
         classes.setdefault((int(c.width), int(c.height)), []).append(v)
     table = {}
-    best = {}
-    for (w, h), idx in classes.items():
-        key = _key(dev, w, h)
-        if key in _cache:
-            best[(w, h)] = tuple(_cache[key])
-            continue
-        pick = idx[:max_views]
-        sub_c = [cams[v] for v in pick]
-        sub_p = [poses[v] for v in pick]
-        sub_a = None if actives is None else [actives[v] for v in pick]
-        t = {}
-        for tile in TILE_SHAPES:
-            t[f"{tile[0]}x{tile[1]}"] = time_batch(surf, sub_c, sub_p, sub_a, tile, reps, stream)
-        table[f"{w}x{h}"] = t
-        win = min(t, key=t.get)
-        best[(w, h)] = tuple(int(x) for x in win.split("x"))
-        _cache[key] = list(best[(w, h)])
-        torch.cuda.empty_cache()
+    best = {}      # (px, class) -> (tile, ms)
+    for px in px_counts:
+        for (w, h), idx in classes.items():
+            key = _key(dev, w, h, px)
+            if key in _cache:
+                tw, th, ms = _cache[key]
+                best[(px, (w, h))] = ((int(tw), int(th)), float(ms))
+                continue
+            pick = idx[:max_views]
+            sub_c = [cams[v] for v in pick]
+            sub_p = [poses[v] for v in pick]
+            sub_a = None if actives is None else [actives[v] for v in pick]
+            t = {}
+            for tile in TILE_SHAPES[px]:
+                t[f"{tile[0]}x{tile[1]}"] = time_batch(surf, sub_c, sub_p, sub_a, tile, px, reps,
+                                                       stream) / len(pick)
+            table.setdefault(f"px{px}", {})[f"{w}x{h}"] = t
+            win = min(t, key=t.get)
+            tile = tuple(int(x) for x in win.split("x"))
+            best[(px, (w, h))] = (tile, t[win])
+            _cache[key] = [tile[0], tile[1], t[win]]
+            torch.cuda.empty_cache()
     _store(cache_path)
-    return [best[(int(c.width), int(c.height))] for c in cams], table
+    total = {px: sum(best[(px, cl)][1] * len(idx) for cl, idx in classes.items())
+             for px in px_counts}
+    px = min(total, key=total.get)
+    tiles = [best[(px, (int(c.width), int(c.height)))][0] for c in cams]
+    return px, tiles, table
+
+
+def tune_tiles(surf, cams, poses, actives=None, **kw):
+    """Tile shape per view at one pixel per thread (see ``tune``)."""
+    px, tiles, table = tune(surf, cams, poses, actives, px_counts=(1,), **kw)
+    return tiles, table.get("px1", {})

@@ -12,7 +12,9 @@
   sort     bin_sort of a 200k-surfel room at 160x120 (long tile segments)
 
 Each case runs ``reps`` times (default 3) after one warm-up and prints the
-mean device time per repetition (CUDA events).
+mean device time per repetition (CUDA events).  An optional third argument
+sets the pixels per thread of the rendering cases (1, 2 or 4; the tile is the
+first shape of that count).
 """
 from __future__ import annotations
 
@@ -38,17 +40,18 @@ def _timed(fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def case_track(reps):
+def case_track(reps, px=1):
     s = scenes.room_scene(0, 200_000)
     cam = scenes.tracking_camera()
     ds = gs2d.DeviceSurfels(s)
-    r = gs2d.Rasterizer(cam, ds.n)
+    tile = gs2d.TILE_SHAPES[px][0]
+    r = gs2d.Rasterizer(cam, ds.n, tile=tile, px=px)
     gt = scenes.room_pose(100)
     out = r.forward(ds, gs2d.pose_tensor(gt))
     obs_rgb = out["rgb"].clone()
     obs_d = out["depth"] / out["opacity"].clamp_min(1e-6)
     start = gs2d.pose_tensor(scenes.perturb_pose(gt, 0.02, 1.0, seed=5))
-    ccam, cfg = gs2d.camera(cam), gs2d.default_config()
+    ccam, cfg = gs2d.camera(cam), gs2d.default_config(tile, px)
     prm = gs2d.default_track_params(stop_tol=0.0)
     cap = 8 * ds.n
     ws = torch.empty(gs2d.gs2d_track_workspace(ds.n, cap, ccam, cfg), dtype=torch.uint8, device="cuda")
@@ -61,9 +64,9 @@ def case_track(reps):
     return _timed(run, reps)
 
 
-def _batch(s, cams, poses, actives, reps):
+def _batch(s, cams, poses, actives, reps, px=1):
     ds = gs2d.DeviceSurfels(s)
-    br = gs2d.BatchRasterizer(cams, ds.n, actives=actives)
+    br = gs2d.BatchRasterizer(cams, ds.n, actives=actives, px=px)
     br.set_poses(poses)
     br.fit(ds)
     br.forward(ds)
@@ -82,19 +85,19 @@ def _batch(s, cams, poses, actives, reps):
     return _timed(run, reps)
 
 
-def case_mapping(reps):
+def case_mapping(reps, px=1):
     s = scenes.room_scene(1, 300_000)
     poses = scenes.room_trajectory(2, 4)
-    return _batch(s, [scenes.mapping_camera()] * 4, poses, None, reps)
+    return _batch(s, [scenes.mapping_camera()] * 4, poses, None, reps, px)
 
 
-def case_uneven(reps):
+def case_uneven(reps, px=1):
     s = scenes.room_scene(3, 1_000_000)
     cams, poses, actives = scenes.uneven_batch(4, s, 8, sizes=(50_000, 500_000))
-    return _batch(s, cams, poses, actives, reps)
+    return _batch(s, cams, poses, actives, reps, px)
 
 
-def case_net(reps):
+def case_net(reps, px=1):
     B = 256
     params = torch.tensor(scenes.net_init(0, gs2d.net_init_blocks()), device="cuda")
     n = params.numel()
@@ -119,7 +122,7 @@ def case_net(reps):
     return _timed(run, reps)
 
 
-def case_sort(reps):
+def case_sort(reps, px=1):
     s = scenes.room_scene(100, 200_000)
     cam = scenes.Camera(150.0, 150.0, 80.0, 60.0, 160, 120)
     ds = gs2d.DeviceSurfels(s)
@@ -137,9 +140,10 @@ def main(argv):
         print(__doc__)
         return 2
     reps = int(argv[1]) if len(argv) > 1 else 3
+    px = int(argv[2]) if len(argv) > 2 else 1
     _build.build()
-    ms = CASES[argv[0]](reps)
-    print(f"{argv[0]}: {ms:.3f} ms per repetition")
+    ms = CASES[argv[0]](reps, px)
+    print(f"{argv[0]} (px {px}): {ms:.3f} ms per repetition")
     return 0
 
 

@@ -40,7 +40,8 @@ __device__ __forceinline__ int view_of(const ViewTable& tab, int item) {
   return v;
 }
 
-__global__ void __launch_bounds__(kTileThreads) fwd_batch_kernel(ViewTable tab,
+template <int P>
+__global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) fwd_batch_kernel(ViewTable tab,
                                                                  uint32_t* __restrict__ queue) {
   __shared__ float4 s_rec[kTileThreads][kFwdVec4];
   __shared__ HitLists hl;
@@ -54,31 +55,37 @@ __global__ void __launch_bounds__(kTileThreads) fwd_batch_kernel(ViewTable tab,
     const ViewDev& V = tab.v[view_of(tab, item)];
     if (V.status && *V.status) continue;
     const int tile = item - V.item0;
-    const TilePix tp = tile_pixel(tile, V.tiles_x, V.cfg.tile_w, V.cfg.tile_h);
-    const bool inside = tp.px < V.cam.width && tp.py < V.cam.height;
+    const TilePix<P> tp = tile_pixel<P>(tile, V.tiles_x, V.cfg.tile_w, V.cfg.tile_h);
+    bool inside[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) inside[k] = tp.px < V.cam.width && tp.py + 4 * k < V.cam.height;
     const int tile_x0 = (tile % V.tiles_x) * V.cfg.tile_w;
     const int tile_y0 = (tile / V.tiles_x) * V.cfg.tile_h;
     const float xt = (float)tile_x0 + 0.5f - V.cam.cx, yt = (float)tile_y0 + 0.5f - V.cam.cy;
-    const FwdState st = fwd_tile<kFwdVec4, false>(V.proj, V.vals, V.ranges[2 * tile],
-                                                  V.ranges[2 * tile + 1], xt, yt, tile_x0, tile_y0,
-                                                  tp, inside, V.cam, V.cfg, s_rec, hl, nullptr);
-    if (inside) {
-      const size_t p = (size_t)tp.py * V.cam.width + tp.px;
-      V.rgb[3 * p] = st.C.x;
-      V.rgb[3 * p + 1] = st.C.y;
-      V.rgb[3 * p + 2] = st.C.z;
-      V.depth[p] = st.D;
-      V.normal[3 * p] = st.N.x;
-      V.normal[3 * p + 1] = st.N.y;
-      V.normal[3 * p + 2] = st.N.z;
-      V.opac[p] = 1.f - st.T;
-      V.T[p] = st.T;
-      V.nlast[p] = st.last;
+    FwdState st[P];
+    fwd_tile<kFwdVec4, false, P>(V.proj, V.vals, V.ranges[2 * tile], V.ranges[2 * tile + 1], xt, yt,
+                                 tile_x0, tile_y0, tp, inside, V.cam, V.cfg, s_rec, hl, nullptr,
+                                 st);
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      if (!inside[k]) continue;
+      const size_t p = (size_t)(tp.py + 4 * k) * V.cam.width + tp.px;
+      V.rgb[3 * p] = st[k].C.x;
+      V.rgb[3 * p + 1] = st[k].C.y;
+      V.rgb[3 * p + 2] = st[k].C.z;
+      V.depth[p] = st[k].D;
+      V.normal[3 * p] = st[k].N.x;
+      V.normal[3 * p + 1] = st[k].N.y;
+      V.normal[3 * p + 2] = st[k].N.z;
+      V.opac[p] = 1.f - st[k].T;
+      V.T[p] = st[k].T;
+      V.nlast[p] = st[k].last;
     }
   }
 }
 
-__global__ void __launch_bounds__(kTileThreads) bwd_batch_kernel(ViewTable tab,
+template <int P>
+__global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) bwd_batch_kernel(ViewTable tab,
                                                                  uint32_t* __restrict__ queue) {
   __shared__ BwdSmem<true> sm;
   __shared__ int s_item;
@@ -91,27 +98,34 @@ __global__ void __launch_bounds__(kTileThreads) bwd_batch_kernel(ViewTable tab,
     const ViewDev& V = tab.v[view_of(tab, item)];
     if (V.status && *V.status) continue;
     const int tile = item - V.item0;
-    const TilePix tp = tile_pixel(tile, V.tiles_x, V.cfg.tile_w, V.cfg.tile_h);
-    const bool inside = tp.px < V.cam.width && tp.py < V.cam.height;
+    const TilePix<P> tp = tile_pixel<P>(tile, V.tiles_x, V.cfg.tile_w, V.cfg.tile_h);
+    bool inside[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) inside[k] = tp.px < V.cam.width && tp.py + 4 * k < V.cam.height;
     const float xt = (float)((tile % V.tiles_x) * V.cfg.tile_w) + 0.5f - V.cam.cx;
     const float yt = (float)((tile / V.tiles_x) * V.cfg.tile_h) + 0.5f - V.cam.cy;
     const float rx = (tp.px + 0.5f - V.cam.cx) / V.cam.fx, ry = (tp.py + 0.5f - V.cam.cy) / V.cam.fy;
-    float Tf = 1.f;
-    uint32_t nl = 0;
-    F3 gC = f3(0.f, 0.f, 0.f), gN = f3(0.f, 0.f, 0.f);
-    float gD = 0.f, gO = 0.f;
-    if (inside) {
-      const size_t p = (size_t)tp.py * V.cam.width + tp.px;
-      Tf = V.T[p];
-      nl = V.nlast[p];
-      gC = f3(V.d_rgb[3 * p], V.d_rgb[3 * p + 1], V.d_rgb[3 * p + 2]);
-      gD = V.d_depth[p];
-      if (V.d_normal) gN = f3(V.d_normal[3 * p], V.d_normal[3 * p + 1], V.d_normal[3 * p + 2]);
-      if (V.d_opac) gO = V.d_opac[p];
+    PixGrad pg[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      pg[k].Tf = 1.f;
+      pg[k].nl = 0;
+      pg[k].gC = f3(0.f, 0.f, 0.f);
+      pg[k].gN = f3(0.f, 0.f, 0.f);
+      pg[k].gD = 0.f;
+      pg[k].gO = 0.f;
+      if (!inside[k]) continue;
+      const size_t p = (size_t)(tp.py + 4 * k) * V.cam.width + tp.px;
+      pg[k].Tf = V.T[p];
+      pg[k].nl = V.nlast[p];
+      pg[k].gC = f3(V.d_rgb[3 * p], V.d_rgb[3 * p + 1], V.d_rgb[3 * p + 2]);
+      pg[k].gD = V.d_depth[p];
+      if (V.d_normal) pg[k].gN = f3(V.d_normal[3 * p], V.d_normal[3 * p + 1], V.d_normal[3 * p + 2]);
+      if (V.d_opac) pg[k].gO = V.d_opac[p];
     }
     float pr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    bwd_tile<true>(V.proj, V.vals, V.emit, V.ranges[2 * tile], V.ranges[2 * tile + 1], xt, yt, tp,
-                   inside, rx, ry, V.cam, V.cfg, Tf, nl, gC, gD, gN, gO, V.partials, sm, pr);
+    bwd_tile<true, P>(V.proj, V.vals, V.emit, V.ranges[2 * tile], V.ranges[2 * tile + 1], xt, yt,
+                      tp, inside, rx, ry, V.cam, V.cfg, pg, V.partials, sm, pr);
   }
 }
 
@@ -130,9 +144,7 @@ int view_tiles(const gs2d_view& w, int* tx) {
 
 int check_view(const gs2d_view& w) {
   if (w.cam.width <= 0 || w.cam.height <= 0) return GS2D_ERR_INVALID_ARG;
-  if (w.cfg.tile_w * w.cfg.tile_h != kTileThreads || w.cfg.tile_w <= 0 || w.cfg.tile_w % 8 ||
-      w.cfg.tile_h <= 0 || w.cfg.tile_h % 4 || w.cfg.px_per_thread != 1)
-    return GS2D_ERR_INVALID_ARG;
+  if (!tile_cfg_ok(w.cfg)) return GS2D_ERR_INVALID_ARG;
   int tx;
   const long long nt = view_tiles(w, &tx);
   if (nt <= 0 || nt > 65535) return GS2D_ERR_INVALID_ARG;
@@ -181,6 +193,8 @@ int build_table(const gs2d_view* views, int n_views, const BatchWs* w, ViewTable
     const gs2d_view& s = views[v];
     const int r = check_view(s);
     if (r) return r;
+    // one persistent launch runs one pixels-per-thread variant
+    if (s.cfg.px_per_thread != views[0].cfg.px_per_thread) return GS2D_ERR_INVALID_ARG;
     ViewDev& d = tab->v[v];
     d.cam = s.cam;
     d.cfg = s.cfg;
@@ -308,9 +322,12 @@ int gs2d_render_fwd_batch(const gs2d_view* views, int n_views, void* workspace, 
   const BatchWs w = carve_batch_ws(workspace, views, n_views, 0);
   zero_words_kernel<<<1, 64, 0, st>>>(w.queue, 2);
   GS2D_LAUNCH_CHECK();
-  const int grid = min(persistent_grid(reinterpret_cast<const void*>(fwd_batch_kernel)), tab.n_items);
-  if (grid <= 0) return GS2D_ERR_CUDA;
-  fwd_batch_kernel<<<grid, kTileThreads, 0, st>>>(tab, w.queue);
+  GS2D_DISPATCH_P(views[0].cfg.px_per_thread, {
+    const int grid = min(persistent_grid(reinterpret_cast<const void*>(fwd_batch_kernel<P>)),
+                         tab.n_items);
+    if (grid <= 0) return GS2D_ERR_CUDA;
+    fwd_batch_kernel<P><<<grid, kTileThreads, 0, st>>>(tab, w.queue);
+  });
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
 }
@@ -336,9 +353,12 @@ int gs2d_render_bwd_batch(const gs2d_view* views, int n_views, const gs2d_surfel
   cudaStream_t st = (cudaStream_t)stream;
   zero_words_kernel<<<1, 64, 0, st>>>(w.queue, 2);
   GS2D_LAUNCH_CHECK();
-  const int grid = min(persistent_grid(reinterpret_cast<const void*>(bwd_batch_kernel)), tab.n_items);
-  if (grid <= 0) return GS2D_ERR_CUDA;
-  bwd_batch_kernel<<<grid, kTileThreads, 0, st>>>(tab, w.queue + 1);
+  GS2D_DISPATCH_P(views[0].cfg.px_per_thread, {
+    const int grid = min(persistent_grid(reinterpret_cast<const void*>(bwd_batch_kernel<P>)),
+                         tab.n_items);
+    if (grid <= 0) return GS2D_ERR_CUDA;
+    bwd_batch_kernel<P><<<grid, kTileThreads, 0, st>>>(tab, w.queue + 1);
+  });
   GS2D_LAUNCH_CHECK();
   // surfels outside every view's subset receive zero: clear, then add view by view
   GS2D_CUDA_TRY(cudaMemsetAsync(d_mu, 0, sizeof(float) * 3 * s->n, st));

@@ -46,8 +46,8 @@
 
 namespace gs2d {
 
-template <bool kCount>
-__global__ void __launch_bounds__(kTileThreads) render_fwd_kernel(
+template <bool kCount, int P>
+__global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) render_fwd_kernel(
     const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
     const int32_t* __restrict__ ranges, gs2d_camera cam, gs2d_config cfg, int tiles_x,
     float* __restrict__ out_rgb, float* __restrict__ out_depth, float* __restrict__ out_normal,
@@ -57,15 +57,17 @@ __global__ void __launch_bounds__(kTileThreads) render_fwd_kernel(
   __shared__ HitLists hl;
   if (gate && *gate) return;
   const int tile = blockIdx.x;
-  const TilePix tp = tile_pixel(tile, tiles_x, cfg.tile_w, cfg.tile_h);
-  const bool inside = tp.px < cam.width && tp.py < cam.height;
+  const TilePix<P> tp = tile_pixel<P>(tile, tiles_x, cfg.tile_w, cfg.tile_h);
+  bool inside[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) inside[k] = tp.px < cam.width && tp.py + 4 * k < cam.height;
   const int tile_x0 = (tile % tiles_x) * cfg.tile_w, tile_y0 = (tile / tiles_x) * cfg.tile_h;
   const float xt = (float)tile_x0 + 0.5f - cam.cx;
   const float yt = (float)tile_y0 + 0.5f - cam.cy;
   uint32_t cnt[3] = {0u, 0u, 0u};
-  const FwdState st = fwd_tile<kFwdVec4, kCount>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1],
-                                                 xt, yt, tile_x0, tile_y0, tp, inside, cam, cfg,
-                                                 s_rec, hl, cnt);
+  FwdState st[P];
+  fwd_tile<kFwdVec4, kCount, P>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0,
+                                tile_y0, tp, inside, cam, cfg, s_rec, hl, cnt, st);
   if (kCount) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -76,23 +78,51 @@ __global__ void __launch_bounds__(kTileThreads) render_fwd_kernel(
     }
     return;
   }
-  if (inside) {
-    const size_t p = (size_t)tp.py * cam.width + tp.px;
-    out_rgb[3 * p] = st.C.x;
-    out_rgb[3 * p + 1] = st.C.y;
-    out_rgb[3 * p + 2] = st.C.z;
-    out_depth[p] = st.D;
-    out_normal[3 * p] = st.N.x;
-    out_normal[3 * p + 1] = st.N.y;
-    out_normal[3 * p + 2] = st.N.z;
-    out_opac[p] = 1.f - st.T;
-    out_T[p] = st.T;
-    out_nlast[p] = st.last;
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    if (!inside[k]) continue;
+    const size_t p = (size_t)(tp.py + 4 * k) * cam.width + tp.px;
+    out_rgb[3 * p] = st[k].C.x;
+    out_rgb[3 * p + 1] = st[k].C.y;
+    out_rgb[3 * p + 2] = st[k].C.z;
+    out_depth[p] = st[k].D;
+    out_normal[3 * p] = st[k].N.x;
+    out_normal[3 * p + 1] = st[k].N.y;
+    out_normal[3 * p + 2] = st[k].N.z;
+    out_opac[p] = 1.f - st[k].T;
+    out_T[p] = st[k].T;
+    out_nlast[p] = st[k].last;
   }
 }
 
-template <bool kFull>
-__global__ void __launch_bounds__(kTileThreads) render_bwd_kernel(
+// Upstream gradients and compositing state of the thread's P pixels.
+template <int P>
+__device__ __forceinline__ void load_pix_grads(const TilePix<P>& tp, const bool (&inside)[P],
+                                               const gs2d_camera& cam, const float* T_final,
+                                               const uint32_t* n_last, const float* g_rgb,
+                                               const float* g_depth, const float* g_normal,
+                                               const float* g_opac, PixGrad (&pg)[P]) {
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    pg[k].Tf = 1.f;
+    pg[k].nl = 0;
+    pg[k].gC = f3(0.f, 0.f, 0.f);
+    pg[k].gN = f3(0.f, 0.f, 0.f);
+    pg[k].gD = 0.f;
+    pg[k].gO = 0.f;
+    if (!inside[k]) continue;
+    const size_t p = (size_t)(tp.py + 4 * k) * cam.width + tp.px;
+    pg[k].Tf = T_final[p];
+    pg[k].nl = n_last[p];
+    pg[k].gC = f3(g_rgb[3 * p], g_rgb[3 * p + 1], g_rgb[3 * p + 2]);
+    pg[k].gD = g_depth[p];
+    if (g_normal) pg[k].gN = f3(g_normal[3 * p], g_normal[3 * p + 1], g_normal[3 * p + 2]);
+    if (g_opac) pg[k].gO = g_opac[p];
+  }
+}
+
+template <bool kFull, int P>
+__global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) render_bwd_kernel(
     const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ emit, const int32_t* __restrict__ ranges, gs2d_camera cam,
     gs2d_config cfg, int tiles_x, const float* __restrict__ T_final,
@@ -105,37 +135,27 @@ __global__ void __launch_bounds__(kTileThreads) render_bwd_kernel(
   __shared__ float s_pose[kTileThreads / 32][6];
   if (gate && *gate) return;
   const int tile = blockIdx.x;
-  const TilePix tp = tile_pixel(tile, tiles_x, cfg.tile_w, cfg.tile_h);
-  const bool inside = tp.px < cam.width && tp.py < cam.height;
+  const TilePix<P> tp = tile_pixel<P>(tile, tiles_x, cfg.tile_w, cfg.tile_h);
+  bool inside[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) inside[k] = tp.px < cam.width && tp.py + 4 * k < cam.height;
   const int tile_x0 = (tile % tiles_x) * cfg.tile_w, tile_y0 = (tile / tiles_x) * cfg.tile_h;
   const float xt = (float)tile_x0 + 0.5f - cam.cx;
   const float yt = (float)tile_y0 + 0.5f - cam.cy;
   const float rx = (tp.px + 0.5f - cam.cx) / cam.fx, ry = (tp.py + 0.5f - cam.cy) / cam.fy;
-  float Tf = 1.f;
-  uint32_t nl = 0;
-  F3 gC = f3(0.f, 0.f, 0.f), gN = f3(0.f, 0.f, 0.f);
-  float gD = 0.f, gO = 0.f;
-  if (inside) {
-    const size_t p = (size_t)tp.py * cam.width + tp.px;
-    Tf = T_final[p];
-    nl = n_last[p];
-    gC = f3(g_rgb[3 * p], g_rgb[3 * p + 1], g_rgb[3 * p + 2]);
-    gD = g_depth[p];
-    if (g_normal) gN = f3(g_normal[3 * p], g_normal[3 * p + 1], g_normal[3 * p + 2]);
-    if (g_opac) gO = g_opac[p];
-  }
+  PixGrad pg[P];
+  load_pix_grads<P>(tp, inside, cam, T_final, n_last, g_rgb, g_depth, g_normal, g_opac, pg);
   float pr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if constexpr (kFull) {
-    bwd_tile<true>(proj, vals, emit, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tp, inside, rx,
-                   ry, cam, cfg, Tf, nl, gC, gD, gN, gO, partials, sm, pr);
+    bwd_tile<true, P>(proj, vals, emit, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tp, inside,
+                      rx, ry, cam, cfg, pg, partials, sm, pr);
   } else {
     if (g_normal)
-      bwd_tile_pose<true>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0,
-                          tile_y0, tp, inside, rx, ry, cam, cfg, Tf, nl, gC, gD, gN, gO, sm, hl, pr);
+      bwd_tile_pose<true, P>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0,
+                             tile_y0, tp, inside, rx, ry, cam, cfg, pg, sm, hl, pr);
     else
-      bwd_tile_pose<false>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0,
-                           tile_y0, tp, inside, rx, ry, cam, cfg, Tf, nl, gC, gD, gN, gO, sm, hl,
-                           pr);
+      bwd_tile_pose<false, P>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0,
+                              tile_y0, tp, inside, rx, ry, cam, cfg, pg, sm, hl, pr);
     block_sum6(pr, s_pose, pose_part + (size_t)tile * 6);
   }
 }
@@ -144,7 +164,8 @@ __global__ void __launch_bounds__(kTileThreads) render_bwd_kernel(
 // loss and its image gradient per pixel (in registers), and the pose-only
 // backward replay -- the images never leave the chip.  Writes the tile's
 // loss partial (already divided by |Omega|) and pose 6-vector partial.
-__global__ void __launch_bounds__(kTileThreads) track_tile_kernel(
+template <int P>
+__global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) track_tile_kernel(
     const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
     const int32_t* __restrict__ ranges, gs2d_camera cam, gs2d_config cfg, int tiles_x,
     const float* __restrict__ obs_rgb, const float* __restrict__ obs_depth, gs2d_track_params prm,
@@ -164,29 +185,44 @@ __global__ void __launch_bounds__(kTileThreads) track_tile_kernel(
     }
   }
   const int tile = blockIdx.x;
-  const TilePix tp = tile_pixel(tile, tiles_x, cfg.tile_w, cfg.tile_h);
-  const bool inside = tp.px < cam.width && tp.py < cam.height;
+  const TilePix<P> tp = tile_pixel<P>(tile, tiles_x, cfg.tile_w, cfg.tile_h);
+  bool inside[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) inside[k] = tp.px < cam.width && tp.py + 4 * k < cam.height;
   const int tile_x0 = (tile % tiles_x) * cfg.tile_w, tile_y0 = (tile / tiles_x) * cfg.tile_h;
   const float xt = (float)tile_x0 + 0.5f - cam.cx;
   const float yt = (float)tile_y0 + 0.5f - cam.cy;
   const float rx = (tp.px + 0.5f - cam.cx) / cam.fx, ry = (tp.py + 0.5f - cam.cy) / cam.fy;
   const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
-  const FwdState st = fwd_tile<kBwdVec4, false>(proj, vals, start, end, xt, yt, tile_x0, tile_y0,
-                                                tp, inside, cam, cfg, sm.rec, hl, nullptr);
+  FwdState st[P];
+  fwd_tile<kBwdVec4, false, P>(proj, vals, start, end, xt, yt, tile_x0, tile_y0, tp, inside, cam,
+                               cfg, sm.rec, hl, nullptr, st);
   float pr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const float inv = 1.f / (float)(cam.width * cam.height);
-  PixLoss L;
-  L.loss = 0.f;
-  L.g_rgb[0] = L.g_rgb[1] = L.g_rgb[2] = 0.f;
-  L.g_depth = L.g_opac = 0.f;
-  if (inside) {
-    const size_t p = (size_t)tp.py * cam.width + tp.px;
-    L = tracking_pixel_loss(st.C, st.D, st.N, 1.f - st.T,
-                            f3(obs_rgb[3 * p], obs_rgb[3 * p + 1], obs_rgb[3 * p + 2]),
-                            obs_depth[p], rx, ry, inv, prm);
+  PixGrad pg[P];
+  float loss = 0.f;
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    PixLoss L;
+    L.loss = 0.f;
+    L.g_rgb[0] = L.g_rgb[1] = L.g_rgb[2] = 0.f;
+    L.g_depth = L.g_opac = 0.f;
+    if (inside[k]) {
+      const size_t p = (size_t)(tp.py + 4 * k) * cam.width + tp.px;
+      L = tracking_pixel_loss(st[k].C, st[k].D, st[k].N, 1.f - st[k].T,
+                              f3(obs_rgb[3 * p], obs_rgb[3 * p + 1], obs_rgb[3 * p + 2]),
+                              obs_depth[p], rx, ry + (4.f * k) / cam.fy, inv, prm);
+    }
+    loss += L.loss * inv;
+    pg[k].Tf = st[k].T;
+    pg[k].nl = st[k].last;
+    pg[k].gC = f3(L.g_rgb[0], L.g_rgb[1], L.g_rgb[2]);
+    pg[k].gN = f3(0.f, 0.f, 0.f);
+    pg[k].gD = L.g_depth;
+    pg[k].gO = L.g_opac;
   }
   {
-    float v = L.loss * inv;
+    float v = loss;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = v;
@@ -197,9 +233,8 @@ __global__ void __launch_bounds__(kTileThreads) track_tile_kernel(
       loss_part[tile] = t;
     }
   }
-  bwd_tile_pose<false>(proj, vals, start, end, xt, yt, tile_x0, tile_y0, tp, inside, rx, ry, cam,
-                       cfg, st.T, st.last, f3(L.g_rgb[0], L.g_rgb[1], L.g_rgb[2]), L.g_depth, f3(0.f, 0.f, 0.f),
-                L.g_opac, sm, hl, pr);
+  bwd_tile_pose<false, P>(proj, vals, start, end, xt, yt, tile_x0, tile_y0, tp, inside, rx, ry, cam,
+                          cfg, pg, sm, hl, pr);
   block_sum6(pr, s_pose, pose_part + (size_t)tile * 6);
   // the last block to finish reduces every tile's partials and updates the pose
   __threadfence();
@@ -354,10 +389,8 @@ BwdWs carve_bwd_ws(void* base, int n, size_t cap, int n_tiles, bool full) {
 
 int validate_tile_cfg(const gs2d_camera* cam, const gs2d_config* cfg) {
   if (!cam || !cfg) return GS2D_ERR_INVALID_ARG;
-  // one thread per pixel; warps cover 8 x 4 pixel blocks of the tile
-  if (cfg->tile_w * cfg->tile_h != kTileThreads || cfg->tile_w <= 0 || cfg->tile_h <= 0 ||
-      cfg->tile_w % 8 || cfg->tile_h % 4 || cfg->px_per_thread != 1)
-    return GS2D_ERR_INVALID_ARG;
+  // P pixels per thread; warps cover 8 x 4P pixel blocks of the tile
+  if (!tile_cfg_ok(*cfg)) return GS2D_ERR_INVALID_ARG;
   if (cam->width <= 0 || cam->height <= 0) return GS2D_ERR_INVALID_ARG;
   const long long nt = (long long)gs2d_tiles_x(cam, cfg) * gs2d_tiles_y(cam, cfg);
   if (nt > 65535) return GS2D_ERR_INVALID_ARG;
@@ -375,9 +408,9 @@ int render_fwd_launch(const float* proj, const gs2d_bins* bins, const gs2d_camer
     return GS2D_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(proj) & 15) return GS2D_ERR_INVALID_ARG;
   const int tx = gs2d_tiles_x(cam, cfg), ty = gs2d_tiles_y(cam, cfg);
-  render_fwd_kernel<false><<<tx * ty, kTileThreads, 0, st>>>(
+  GS2D_DISPATCH_P(cfg->px_per_thread, render_fwd_kernel<false, P><<<tx * ty, kTileThreads, 0, st>>>(
       reinterpret_cast<const float4*>(proj), bins->vals, bins->tile_ranges, *cam, *cfg, tx, rgb,
-      depth, normal, opacity, t_final, n_last, nullptr, gate);
+      depth, normal, opacity, t_final, n_last, nullptr, gate));
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
 }
@@ -392,9 +425,9 @@ int track_tile_launch(const float* proj, const gs2d_bins* bins, const gs2d_camer
       !loss_part || !pose_part || !ts.pose || !ts.adam || !ts.counter || !status)
     return GS2D_ERR_INVALID_ARG;
   const int tx = gs2d_tiles_x(cam, cfg), ty = gs2d_tiles_y(cam, cfg);
-  track_tile_kernel<<<tx * ty, kTileThreads, 0, st>>>(
+  GS2D_DISPATCH_P(cfg->px_per_thread, track_tile_kernel<P><<<tx * ty, kTileThreads, 0, st>>>(
       reinterpret_cast<const float4*>(proj), bins->vals, bins->tile_ranges, *cam, *cfg, tx, obs_rgb,
-      obs_depth, *prm, loss_part, pose_part, ts, status);
+      obs_depth, *prm, loss_part, pose_part, ts, status));
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
 }
@@ -451,9 +484,9 @@ int render_bwd_launch(const float* proj, const gs2d_bins* bins, const int32_t* t
   const BwdWs w = carve_bwd_ws(workspace, s->n, bins->capacity, n_tiles, full);
   const float4* p4 = reinterpret_cast<const float4*>(proj);
   if (full) {
-    render_bwd_kernel<true><<<n_tiles, kTileThreads, 0, st>>>(
+    GS2D_DISPATCH_P(cfg->px_per_thread, render_bwd_kernel<true, P><<<n_tiles, kTileThreads, 0, st>>>(
         p4, bins->vals, bins->isect_emit, bins->tile_ranges, *cam, *cfg, tx, t_final, n_last, d_rgb,
-        d_depth, d_normal, d_opacity, w.partials, w.pose_part, gate);
+        d_depth, d_normal, d_opacity, w.partials, w.pose_part, gate));
     GS2D_LAUNCH_CHECK();
     if (s->n > 0) {
       const int nb = (s->n + 255) / 256;
@@ -470,9 +503,9 @@ int render_bwd_launch(const float* proj, const gs2d_bins* bins, const int32_t* t
       GS2D_CUDA_TRY(cudaMemsetAsync(d_pose6, 0, 6 * sizeof(float), st));
     }
   } else {
-    render_bwd_kernel<false><<<n_tiles, kTileThreads, 0, st>>>(
+    GS2D_DISPATCH_P(cfg->px_per_thread, render_bwd_kernel<false, P><<<n_tiles, kTileThreads, 0, st>>>(
         p4, bins->vals, bins->isect_emit, bins->tile_ranges, *cam, *cfg, tx, t_final, n_last, d_rgb,
-        d_depth, d_normal, d_opacity, w.partials, w.pose_part, gate);
+        d_depth, d_normal, d_opacity, w.partials, w.pose_part, gate));
     GS2D_LAUNCH_CHECK();
     pose_reduce_kernel<<<1, 256, 0, st>>>(w.pose_part, n_tiles, d_pose6, gate);
     GS2D_LAUNCH_CHECK();
@@ -502,9 +535,9 @@ int gs2d_render_count(const float* proj, const gs2d_bins* bins, const gs2d_camer
   cudaStream_t st = (cudaStream_t)stream;
   GS2D_CUDA_TRY(cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned long long), st));
   const int tx = gs2d_tiles_x(cam, cfg), ty = gs2d_tiles_y(cam, cfg);
-  render_fwd_kernel<true><<<tx * ty, kTileThreads, 0, st>>>(
+  GS2D_DISPATCH_P(cfg->px_per_thread, render_fwd_kernel<true, P><<<tx * ty, kTileThreads, 0, st>>>(
       reinterpret_cast<const float4*>(proj), bins->vals, bins->tile_ranges, *cam, *cfg, tx, nullptr,
-      nullptr, nullptr, nullptr, nullptr, nullptr, counts, bins->status);
+      nullptr, nullptr, nullptr, nullptr, nullptr, counts, bins->status));
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
 }

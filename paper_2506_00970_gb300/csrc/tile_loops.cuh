@@ -13,19 +13,24 @@ namespace gs2d {
 constexpr int kTileThreads = 256;
 constexpr int kRedVals = 16;
 
-// Thread -> pixel map of a tile: each warp owns an 8 x 4 block of pixels, so
-// a warp can skip a surfel whose footprint misses its block.
+// Thread -> pixel map of a tile with P pixels per thread: each warp owns an
+// 8 x 4P block of pixels (lane l: column l & 7, rows (l >> 3) + 4k for
+// k < P), so a warp can skip a surfel whose footprint misses its block.  A
+// tile holds 256 P pixels: tile_w a multiple of 8, tile_h of 4P, and
+// (tile_w / 8) x (tile_h / 4P) = 8 warps.
+template <int P>
 struct TilePix {
-  int px, py;      // pixel
-  int bx0, by0;    // first pixel of the warp's 8 x 4 block
-  float lx, ly;    // pixel centre relative to the tile's first pixel centre
+  int px, py;      // the thread's first pixel; pixel k is (px, py + 4k)
+  int bx0, by0;    // first pixel of the warp's 8 x 4P block
+  float lx, ly;    // first pixel's centre relative to the tile's first pixel centre
 };
-__device__ __forceinline__ TilePix tile_pixel(int tile, int tiles_x, int tile_w, int tile_h) {
-  TilePix t;
+template <int P>
+__device__ __forceinline__ TilePix<P> tile_pixel(int tile, int tiles_x, int tile_w, int tile_h) {
+  TilePix<P> t;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wpr = tile_w >> 3;
-  const int ox = (w % wpr) * 8, oy = (w / wpr) * 4;
+  const int ox = (w % wpr) * 8, oy = (w / wpr) * 4 * P;
   t.bx0 = tx * tile_w + ox;
   t.by0 = ty * tile_h + oy;
   t.px = t.bx0 + (lane & 7);
@@ -35,6 +40,34 @@ __device__ __forceinline__ TilePix tile_pixel(int tile, int tiles_x, int tile_w,
   (void)tile_h;
   return t;
 }
+
+// A tile shape for P pixels per thread: 256 P pixels, widths a multiple of
+// 8, heights of 4P (eight 8 x 4P warp blocks), P in {1, 2, 4}.
+__host__ __device__ inline bool tile_cfg_ok(const gs2d_config& c) {
+  const int P = c.px_per_thread;
+  if (P != 1 && P != 2 && P != 4) return false;
+  return c.tile_w > 0 && c.tile_h > 0 && c.tile_w * c.tile_h == kTileThreads * P &&
+         c.tile_w % 8 == 0 && c.tile_h % (4 * P) == 0;
+}
+
+// Runs the statement given after p (which names P) with P = p in {1, 2, 4}.
+#define GS2D_DISPATCH_P(p, ...)           \
+  do {                                    \
+    switch (p) {                          \
+      case 2: {                           \
+        constexpr int P = 2;              \
+        __VA_ARGS__;                      \
+      } break;                            \
+      case 4: {                           \
+        constexpr int P = 4;              \
+        __VA_ARGS__;                      \
+      } break;                            \
+      default: {                          \
+        constexpr int P = 1;              \
+        __VA_ARGS__;                      \
+      } break;                            \
+    }                                     \
+  } while (0)
 
 // Stages one projected record for a tile: p is re-based on the tile's first
 // pixel centre (xt, yt) (principal-point relative): c0t = p(xt, yt).  Every
@@ -47,15 +80,17 @@ __device__ __forceinline__ float4 stage_c0(const float4 r0, const float4 r1, con
                      fmaf(dy, r2.x, fmaf(dx, r1.y, r0.z)), r0.w);
 }
 
-// Does the footprint (packed pixel ranges) touch the warp's 8 x 4 block?
+// Does the footprint (packed pixel ranges) touch the warp's 8 x 4P block?
+template <int P>
 __device__ __forceinline__ bool warp_hits(float bi, float bj, int bx0, int by0) {
   const uint32_t I = __float_as_uint(bi), J = __float_as_uint(bj);
   const int i0 = I & 0xFFFF, i1 = I >> 16, j0 = J & 0xFFFF, j1 = J >> 16;
-  return !(i1 < bx0 || i0 > bx0 + 7 || j1 < by0 || j0 > by0 + 3);
+  return !(i1 < bx0 || i0 > bx0 + 7 || j1 < by0 || j0 > by0 + 4 * P - 1);
 }
 
-// Mask of the tile's 8 warp blocks (8 x 4 pixels each) that a footprint
+// Mask of the tile's 8 warp blocks (8 x 4P pixels each) that a footprint
 // (packed pixel ranges) touches; bit w for warp w.
+template <int P>
 __device__ __forceinline__ uint32_t footprint_mask(float bi, float bj, int tile_x0, int tile_y0,
                                                    int tile_w) {
   const uint32_t I = __float_as_uint(bi), J = __float_as_uint(bj);
@@ -65,8 +100,8 @@ __device__ __forceinline__ uint32_t footprint_mask(float bi, float bj, int tile_
   uint32_t m = 0u;
 #pragma unroll
   for (int w = 0; w < kTileThreads / 32; ++w) {
-    const int ox = (w % wpr) * 8, oy = (w / wpr) * 4;
-    if (!(i1 < ox || i0 > ox + 7 || j1 < oy || j0 > oy + 3)) m |= 1u << w;
+    const int ox = (w % wpr) * 8, oy = (w / wpr) * 4 * P;
+    if (!(i1 < ox || i0 > ox + 7 || j1 < oy || j0 > oy + 4 * P - 1)) m |= 1u << w;
   }
   return m;
 }
@@ -141,47 +176,58 @@ struct FwdState {
   uint32_t last;
 };
 
-// Front-to-back compositing of one pixel over its tile's list.  Each warp
-// visits only the staged surfels whose footprint touches its block.  With
+// Front-to-back compositing of the thread's P pixels over its tile's list.
+// Each warp visits only the staged surfels whose footprint touches its
+// block; a surfel's staged record is read once for all P pixels.  With
 // kCount it counts evaluated pairs, pairs inside the cutoff and blended pairs.
 struct HitLists {
   uint32_t mask[kTileThreads];
   uint8_t list[kTileThreads / 32][kTileThreads];
 };
 
-template <int kStride, bool kCount>
-__device__ __forceinline__ FwdState fwd_tile(const float4* __restrict__ proj,
-                                             const uint32_t* __restrict__ vals, int start, int end,
-                                             float xt, float yt, int tile_x0, int tile_y0,
-                                             const TilePix& tp, bool inside,
-                                             const gs2d_camera& cam, const gs2d_config& cfg,
-                                             float4 (*s_rec)[kStride], HitLists& hl,
-                                             uint32_t* cnt) {
-  FwdState st;
-  st.T = 1.f;
-  st.D = 0.f;
-  st.C = f3(0.f, 0.f, 0.f);
-  st.N = f3(0.f, 0.f, 0.f);
-  st.last = 0;
-  bool done = !inside;
+template <int kStride, bool kCount, int P>
+__device__ __forceinline__ void fwd_tile(const float4* __restrict__ proj,
+                                         const uint32_t* __restrict__ vals, int start, int end,
+                                         float xt, float yt, int tile_x0, int tile_y0,
+                                         const TilePix<P>& tp, const bool (&inside)[P],
+                                         const gs2d_camera& cam, const gs2d_config& cfg,
+                                         float4 (*s_rec)[kStride], HitLists& hl, uint32_t* cnt,
+                                         FwdState (&st)[P]) {
+  bool done[P];
+  bool all_done = true;
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    st[k].T = 1.f;
+    st[k].D = 0.f;
+    st[k].C = f3(0.f, 0.f, 0.f);
+    st[k].N = f3(0.f, 0.f, 0.f);
+    st[k].last = 0;
+    done[k] = !inside[k];
+    all_done = all_done && done[k];
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int kFp = kStride == kFwdVec4 ? 4 : 6;  // slot holding the footprint
+  float lyk[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) lyk[k] = k ? tp.ly + 4.f * k : tp.ly;
   for (int b = start; b < end; b += kTileThreads) {
-    if (__syncthreads_count(!done) == 0) break;
+    if (__syncthreads_count(!all_done) == 0) break;
     const int idx = b + (int)threadIdx.x;
     if (idx < end) {
       stage_record<kStride>(proj, vals[idx], xt, yt, s_rec);
       const float4 rf = s_rec[threadIdx.x][kFp];
       hl.mask[threadIdx.x] = kStride == kFwdVec4
-                                 ? footprint_mask(rf.y, rf.z, tile_x0, tile_y0, cfg.tile_w)
-                                 : footprint_mask(rf.z, rf.w, tile_x0, tile_y0, cfg.tile_w);
+                                 ? footprint_mask<P>(rf.y, rf.z, tile_x0, tile_y0, cfg.tile_w)
+                                 : footprint_mask<P>(rf.z, rf.w, tile_x0, tile_y0, cfg.tile_w);
     }
     __syncthreads();
     const int cnt_b = min(kTileThreads, end - b);
     const int nh = warp_hit_list(hl.mask, hl.list[warp], cnt_b, warp, lane);
-    if (!done) {
-      for (int k = 0; k < nh; ++k) {
-        const int j = hl.list[warp][k];
+    if (P == 1 && !all_done) {
+      // one pixel: stop at its saturation
+      FwdState& q = st[0];
+      for (int h = 0; h < nh; ++h) {
+        const int j = hl.list[warp][h];
         const float4 r0 = s_rec[j][0], r1 = s_rec[j][1], r2 = s_rec[j][2];
         Eval e;
         const bool hit = eval_pair(r0, r1, r2, tp.lx, tp.ly, cam.near_z, cfg.cutoff_r2,
@@ -191,28 +237,66 @@ __device__ __forceinline__ FwdState fwd_tile(const float4* __restrict__ proj,
           if (fmaf(e.u, e.u, __fmul_rn(e.v, e.v)) <= cfg.cutoff_r2) ++cnt[1];
         }
         if (!hit) continue;
-        const float Tn = st.T * (1.f - e.a);
+        const float Tn = q.T * (1.f - e.a);
         if (Tn < cfg.t_min) {
-          done = true;
+          all_done = true;
           break;
         }
         const float4 r3 = s_rec[j][3];
         const float tnz = s_rec[j][4].x;
-        const float w = e.a * st.T;
-        st.C.x = fmaf(w, r2.w, st.C.x);
-        st.C.y = fmaf(w, r3.x, st.C.y);
-        st.C.z = fmaf(w, r3.y, st.C.z);
-        st.D = fmaf(w, e.z, st.D);
-        st.N.x = fmaf(w, r3.z, st.N.x);
-        st.N.y = fmaf(w, r3.w, st.N.y);
-        st.N.z = fmaf(w, tnz, st.N.z);
-        st.T = Tn;
-        st.last = (uint32_t)(b + j + 1 - start);
+        const float w = e.a * q.T;
+        q.C.x = fmaf(w, r2.w, q.C.x);
+        q.C.y = fmaf(w, r3.x, q.C.y);
+        q.C.z = fmaf(w, r3.y, q.C.z);
+        q.D = fmaf(w, e.z, q.D);
+        q.N.x = fmaf(w, r3.z, q.N.x);
+        q.N.y = fmaf(w, r3.w, q.N.y);
+        q.N.z = fmaf(w, tnz, q.N.z);
+        q.T = Tn;
+        q.last = (uint32_t)(b + j + 1 - start);
         if (kCount) ++cnt[2];
+      }
+    } else if (!all_done) {
+      for (int h = 0; h < nh; ++h) {
+        const int j = hl.list[warp][h];
+        const float4 r0 = s_rec[j][0], r1 = s_rec[j][1], r2 = s_rec[j][2];
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+          if (done[k]) continue;
+          Eval e;
+          const bool hit = eval_pair(r0, r1, r2, tp.lx, lyk[k], cam.near_z, cfg.cutoff_r2,
+                                     cfg.alpha_min, cfg.alpha_max, e);
+          if (kCount) {
+            ++cnt[0];
+            if (fmaf(e.u, e.u, __fmul_rn(e.v, e.v)) <= cfg.cutoff_r2) ++cnt[1];
+          }
+          if (!hit) continue;
+          const float Tn = st[k].T * (1.f - e.a);
+          if (Tn < cfg.t_min) {
+            done[k] = true;
+            continue;
+          }
+          const float4 r3 = s_rec[j][3];
+          const float tnz = s_rec[j][4].x;
+          const float w = e.a * st[k].T;
+          st[k].C.x = fmaf(w, r2.w, st[k].C.x);
+          st[k].C.y = fmaf(w, r3.x, st[k].C.y);
+          st[k].C.z = fmaf(w, r3.y, st[k].C.z);
+          st[k].D = fmaf(w, e.z, st[k].D);
+          st[k].N.x = fmaf(w, r3.z, st[k].N.x);
+          st[k].N.y = fmaf(w, r3.w, st[k].N.y);
+          st[k].N.z = fmaf(w, tnz, st[k].N.z);
+          st[k].T = Tn;
+          st[k].last = (uint32_t)(b + j + 1 - start);
+          if (kCount) ++cnt[2];
+        }
+        all_done = true;
+#pragma unroll
+        for (int k = 0; k < P; ++k) all_done = all_done && done[k];
+        if (all_done) break;
       }
     }
   }
-  return st;
 }
 
 // Butterfly reduce-scatter of 16 values over a warp: afterwards lane l holds
@@ -242,27 +326,48 @@ struct BwdSmem {
   uint32_t max_nl;
 };
 
-// Back-to-front replay of one pixel (Tf, nl, upstream gradients) over its
-// tile's list.  Full mode writes the per-(tile, surfel) partials; tracking
-// mode accumulates the pose 6-vector in pr.
-template <bool kFull>
+// Per-pixel inputs of a backward replay: final transmittance, number of
+// blended list entries, upstream gradients of colour, depth, normal, opacity.
+struct PixGrad {
+  float Tf;
+  uint32_t nl;
+  F3 gC, gN;
+  float gD, gO;
+};
+
+// Back-to-front replay of the thread's P pixels over the tile's list.  Full
+// mode sums a pair's 16 gradient terms over the P pixels, reduces them over
+// the warp and then the block, and writes the per-(tile, surfel) partials;
+// pose mode accumulates the pose 6-vector in pr.  ry is the first pixel's
+// ray y; pixel k's is ry + 4k / fy.
+template <bool kFull, int P>
 __device__ __forceinline__ void bwd_tile(const float4* __restrict__ proj,
                                          const uint32_t* __restrict__ vals,
                                          const uint32_t* __restrict__ emit, int start, int end,
-                                         float xt, float yt, const TilePix& tp, bool inside,
-                                         float rx, float ry, const gs2d_camera& cam,
-                                         const gs2d_config& cfg, float Tf, uint32_t nl, F3 gC,
-                                         float gD, F3 gN, float gO, float* __restrict__ partials,
+                                         float xt, float yt, const TilePix<P>& tp,
+                                         const bool (&inside)[P], float rx, float ry,
+                                         const gs2d_camera& cam, const gs2d_config& cfg,
+                                         const PixGrad (&pg)[P], float* __restrict__ partials,
                                          BwdSmem<kFull>& sm, float (&pr)[6]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float fxfy = cam.fx * cam.fy;
   if (threadIdx.x == 0) sm.max_nl = 0u;
   __syncthreads();
-  if (nl) atomicMax(&sm.max_nl, nl);
+  uint32_t my_nl = 0;
+#pragma unroll
+  for (int k = 0; k < P; ++k) my_nl = max(my_nl, pg[k].nl);
+  if (my_nl) atomicMax(&sm.max_nl, my_nl);
   __syncthreads();
   const int hi = start + (int)sm.max_nl;
-  float T = Tf, acc = 0.f;
-  const float gOT = gO * Tf;
+  float T[P], acc[P], gOT[P], lyk[P], ryk[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    T[k] = pg[k].Tf;
+    acc[k] = 0.f;
+    gOT[k] = pg[k].gO * pg[k].Tf;
+    lyk[k] = k ? tp.ly + 4.f * k : tp.ly;
+    ryk[k] = k ? ry + (4.f * k) / cam.fy : ry;
+  }
   for (int bend = hi; bend > start; bend -= kTileThreads) {
     const int bstart = max(start, bend - kTileThreads);
     const int cnt = bend - bstart;
@@ -281,7 +386,7 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ proj,
       bool h = false;
       if (lane < c_n) {
         const float4 r6 = sm.rec[c_lo + lane][6];
-        h = warp_hits(r6.z, r6.w, tp.bx0, tp.by0);
+        h = warp_hits<P>(r6.z, r6.w, tp.bx0, tp.by0);
       }
       uint32_t hits = __ballot_sync(0xffffffffu, h);
       if (kFull && !h) {
@@ -297,52 +402,55 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ proj,
         const int jrel = bstart + jj - start;
         float val[kRedVals];
         bool contrib = false;
-        if (inside && jrel < (int)nl) {
-          const float4 r0 = sm.rec[jj][0], r1 = sm.rec[jj][1], r2 = sm.rec[jj][2];
+        const float4 r0 = sm.rec[jj][0], r1 = sm.rec[jj][1], r2 = sm.rec[jj][2];
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+          if (!(inside[k] && jrel < (int)pg[k].nl)) continue;
           Eval e;
-          if (eval_pair(r0, r1, r2, tp.lx, tp.ly, cam.near_z, cfg.cutoff_r2, cfg.alpha_min,
-                        cfg.alpha_max, e)) {
-            contrib = true;
-            const float4 r3 = sm.rec[jj][3], r4 = sm.rec[jj][4], r5 = sm.rec[jj][5];
-            const float4 r6 = sm.rec[jj][6];
-            const F3 col = f3(r2.w, r3.x, r3.y);
-            const F3 tn = f3(r3.z, r3.w, r4.x);
-            const F3 nrm = f3(r4.y, r4.z, r4.w);
-            const F3 du = f3(r5.x, r5.y, r5.z), dv = f3(r5.w, r6.x, r6.y);
-            const float om = 1.f - e.a;
-            const float iom = __fdividef(1.f, om);
-            const float Tb = T * iom;
-            const float w = e.a * Tb;
-            const float vj = dot3(col, gC) + e.z * gD + dot3(tn, gN);
-            const float ga = Tb * vj - (acc - gOT) * iom;
-            acc = fmaf(w, vj, acc);
-            T = Tb;
-            float galpha = 0.f, gG = 0.f;
-            if (e.araw <= cfg.alpha_max) {
-              galpha = e.G * ga;
-              gG = r2.z * ga;
-            }
-            const float gr2 = -0.5f * e.G * gG;
-            const float gu = 2.f * e.u * gr2, gv = 2.f * e.v * gr2;
-            const float gz = w * gD;
-            const F3 q = gu * du + gv * dv;
-            const float beta = (fmaf(q.x, rx, fmaf(q.y, ry, q.z)) + gz) * fxfy * e.rinv;
-            const F3 Gv = beta * nrm - q;
-            if (kFull) {
-              val[0] = Gv.x; val[1] = Gv.y; val[2] = Gv.z;
-              val[3] = e.u * Gv.x; val[4] = e.u * Gv.y; val[5] = e.u * Gv.z;
-              val[6] = e.v * Gv.x; val[7] = e.v * Gv.y; val[8] = e.v * Gv.z;
-              val[9] = galpha;
-              val[10] = w * gC.x; val[11] = w * gC.y; val[12] = w * gC.z;
-              val[13] = w * gN.x; val[14] = w * gN.y; val[15] = w * gN.z;
-            } else {
-              const F3 X = f3(e.z * rx, e.z * ry, e.z);
-              const F3 gtn = w * gN;
-              const F3 th = cross3(X, Gv) + cross3(tn, gtn);
-              pr[0] += Gv.x; pr[1] += Gv.y; pr[2] += Gv.z;
-              pr[3] += th.x; pr[4] += th.y; pr[5] += th.z;
-            }
+          if (!eval_pair(r0, r1, r2, tp.lx, lyk[k], cam.near_z, cfg.cutoff_r2, cfg.alpha_min,
+                         cfg.alpha_max, e))
+            continue;
+          const float4 r3 = sm.rec[jj][3], r4 = sm.rec[jj][4], r5 = sm.rec[jj][5];
+          const float4 r6 = sm.rec[jj][6];
+          const F3 col = f3(r2.w, r3.x, r3.y);
+          const F3 tn = f3(r3.z, r3.w, r4.x);
+          const F3 nrm = f3(r4.y, r4.z, r4.w);
+          const F3 du = f3(r5.x, r5.y, r5.z), dv = f3(r5.w, r6.x, r6.y);
+          const F3 gC = pg[k].gC, gN = pg[k].gN;
+          const float gD = pg[k].gD;
+          const float om = 1.f - e.a;
+          const float iom = __fdividef(1.f, om);
+          const float Tb = T[k] * iom;
+          const float w = e.a * Tb;
+          const float vj = dot3(col, gC) + e.z * gD + dot3(tn, gN);
+          const float ga = Tb * vj - (acc[k] - gOT[k]) * iom;
+          acc[k] = fmaf(w, vj, acc[k]);
+          T[k] = Tb;
+          float galpha = 0.f, gG = 0.f;
+          if (e.araw <= cfg.alpha_max) {
+            galpha = e.G * ga;
+            gG = r2.z * ga;
           }
+          const float gr2 = -0.5f * e.G * gG;
+          const float gu = 2.f * e.u * gr2, gv = 2.f * e.v * gr2;
+          const float gz = w * gD;
+          const F3 q = gu * du + gv * dv;
+          const float beta = (fmaf(q.x, rx, fmaf(q.y, ryk[k], q.z)) + gz) * fxfy * e.rinv;
+          const F3 Gv = beta * nrm - q;
+          if (kFull) {
+            const float t[kRedVals] = {Gv.x, Gv.y, Gv.z, e.u * Gv.x, e.u * Gv.y, e.u * Gv.z,
+                                       e.v * Gv.x, e.v * Gv.y, e.v * Gv.z, galpha, w * gC.x,
+                                       w * gC.y, w * gC.z, w * gN.x, w * gN.y, w * gN.z};
+#pragma unroll
+            for (int i = 0; i < kRedVals; ++i) val[i] = contrib ? val[i] + t[i] : t[i];
+          } else {
+            const F3 X = f3(e.z * rx, e.z * ryk[k], e.z);
+            const F3 gtn = w * gN;
+            const F3 th = cross3(X, Gv) + cross3(tn, gtn);
+            pr[0] += Gv.x; pr[1] += Gv.y; pr[2] += Gv.z;
+            pr[3] += th.x; pr[4] += th.y; pr[5] += th.z;
+          }
+          contrib = true;
         }
         if (kFull) {
           if (__any_sync(0xffffffffu, contrib)) {
@@ -387,25 +495,46 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ proj,
 // and z Gv; with q = s (u d_u + v d_v), s = -G dL/dG, the pair's
 // Gv = beta n - q, beta = (q . r + gz) / (n . r).  kNormal adds the normal
 // image's term t_nc x w gN per pair (tracking has no normal gradient).
-template <bool kNormal>
+template <bool kNormal, int P>
 __device__ __forceinline__ void bwd_tile_pose(const float4* __restrict__ proj,
                                               const uint32_t* __restrict__ vals, int start, int end,
                                               float xt, float yt, int tile_x0, int tile_y0,
-                                              const TilePix& tp, bool inside, float rx, float ry,
-                                              const gs2d_camera& cam, const gs2d_config& cfg,
-                                              float Tf, uint32_t nl, F3 gC, float gD, F3 gN,
-                                              float gO, BwdSmem<false>& sm, HitLists& hl,
-                                              float (&pr)[6]) {
+                                              const TilePix<P>& tp, const bool (&inside)[P],
+                                              float rx, float ry, const gs2d_camera& cam,
+                                              const gs2d_config& cfg, const PixGrad (&pg)[P],
+                                              BwdSmem<false>& sm, HitLists& hl, float (&pr)[6]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float fxfy = cam.fx * cam.fy;
   if (threadIdx.x == 0) sm.max_nl = 0u;
   __syncthreads();
-  if (nl) atomicMax(&sm.max_nl, nl);
+  uint32_t my_nl = 0;
+  bool any_inside = false;
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    my_nl = max(my_nl, pg[k].nl);
+    any_inside = any_inside || inside[k];
+  }
+  if (my_nl) atomicMax(&sm.max_nl, my_nl);
   __syncthreads();
   const int hi = start + (int)sm.max_nl;
-  float T = Tf, acc = 0.f;
-  const float gOT = gO * Tf;
-  F3 sG = f3(0.f, 0.f, 0.f), szG = f3(0.f, 0.f, 0.f), sN = f3(0.f, 0.f, 0.f);
+  float T[P], acc[P], gOT[P];
+  F3 szG[P];
+  F3 sG = f3(0.f, 0.f, 0.f), sNg = f3(0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    T[k] = pg[k].Tf;
+    acc[k] = 0.f;
+    gOT[k] = pg[k].gO * pg[k].Tf;
+    szG[k] = f3(0.f, 0.f, 0.f);
+  }
+  F3 sN[P];
+  float lyk[P], ryk[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    sN[k] = f3(0.f, 0.f, 0.f);
+    lyk[k] = k ? tp.ly + 4.f * k : tp.ly;
+    ryk[k] = k ? ry + (4.f * k) / cam.fy : ry;
+  }
   for (int bend = hi; bend > start; bend -= kTileThreads) {
     const int bstart = max(start, bend - kTileThreads);
     const int cnt = bend - bstart;
@@ -413,49 +542,59 @@ __device__ __forceinline__ void bwd_tile_pose(const float4* __restrict__ proj,
     if ((int)threadIdx.x < cnt) {
       stage_record<kBwdVec4>(proj, vals[bstart + (int)threadIdx.x], xt, yt, sm.rec);
       const float4 rf = sm.rec[threadIdx.x][6];
-      hl.mask[threadIdx.x] = footprint_mask(rf.z, rf.w, tile_x0, tile_y0, cfg.tile_w);
+      hl.mask[threadIdx.x] = footprint_mask<P>(rf.z, rf.w, tile_x0, tile_y0, cfg.tile_w);
     }
     __syncthreads();
     const int nh = warp_hit_list(hl.mask, hl.list[warp], cnt, warp, lane);
-    if (!inside) continue;
-    for (int k = nh - 1; k >= 0; --k) {
-      const int jj = hl.list[warp][k];
-      if (bstart + jj - start >= (int)nl) continue;
+    if (!any_inside) continue;
+    for (int h = nh - 1; h >= 0; --h) {
+      const int jj = hl.list[warp][h];
+      const int jrel = bstart + jj - start;
       const float4 r0 = sm.rec[jj][0], r1 = sm.rec[jj][1], r2 = sm.rec[jj][2];
-      Eval e;
-      if (!eval_pair(r0, r1, r2, tp.lx, tp.ly, cam.near_z, cfg.cutoff_r2, cfg.alpha_min,
-                     cfg.alpha_max, e))
-        continue;
-      const float4 r3 = sm.rec[jj][3], r4 = sm.rec[jj][4], r5 = sm.rec[jj][5], r6 = sm.rec[jj][6];
-      const float iom = __fdividef(1.f, 1.f - e.a);
-      const float Tb = T * iom;
-      const float w = e.a * Tb;
-      float vj = fmaf(r2.w, gC.x, fmaf(r3.x, gC.y, fmaf(r3.y, gC.z, e.z * gD)));
-      if (kNormal) vj = fmaf(r3.z, gN.x, fmaf(r3.w, gN.y, fmaf(r4.x, gN.z, vj)));
-      const float ga = Tb * vj - (acc - gOT) * iom;
-      acc = fmaf(w, vj, acc);
-      T = Tb;
-      const float s = e.araw <= cfg.alpha_max ? -e.G * r2.z * ga : 0.f;
-      // P = u d_u + v d_v; q = s P
-      const float Px = fmaf(e.u, r5.x, e.v * r5.w);
-      const float Py = fmaf(e.u, r5.y, e.v * r6.x);
-      const float Pz = fmaf(e.u, r5.z, e.v * r6.y);
-      const float Pr = fmaf(Px, rx, fmaf(Py, ry, Pz));
-      const float beta = fmaf(s, Pr, w * gD) * fxfy * e.rinv;
-      const float Gx = fmaf(beta, r4.y, -s * Px);
-      const float Gy = fmaf(beta, r4.z, -s * Py);
-      const float Gz = fmaf(beta, r4.w, -s * Pz);
-      sG.x += Gx;
-      sG.y += Gy;
-      sG.z += Gz;
-      szG.x = fmaf(e.z, Gx, szG.x);
-      szG.y = fmaf(e.z, Gy, szG.y);
-      szG.z = fmaf(e.z, Gz, szG.z);
-      if (kNormal) sN = sN + w * f3(r3.z, r3.w, r4.x);
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        if (!inside[k] || jrel >= (int)pg[k].nl) continue;
+        Eval e;
+        if (!eval_pair(r0, r1, r2, tp.lx, lyk[k], cam.near_z, cfg.cutoff_r2, cfg.alpha_min,
+                       cfg.alpha_max, e))
+          continue;
+        const F3 gC = pg[k].gC, gN = pg[k].gN;
+        const float gD = pg[k].gD;
+        const float4 r3 = sm.rec[jj][3], r4 = sm.rec[jj][4], r5 = sm.rec[jj][5], r6 = sm.rec[jj][6];
+        const float iom = __fdividef(1.f, 1.f - e.a);
+        const float Tb = T[k] * iom;
+        const float w = e.a * Tb;
+        float vj = fmaf(r2.w, gC.x, fmaf(r3.x, gC.y, fmaf(r3.y, gC.z, e.z * gD)));
+        if (kNormal) vj = fmaf(r3.z, gN.x, fmaf(r3.w, gN.y, fmaf(r4.x, gN.z, vj)));
+        const float ga = Tb * vj - (acc[k] - gOT[k]) * iom;
+        acc[k] = fmaf(w, vj, acc[k]);
+        T[k] = Tb;
+        const float s = e.araw <= cfg.alpha_max ? -e.G * r2.z * ga : 0.f;
+        // P = u d_u + v d_v; q = s P
+        const float Px = fmaf(e.u, r5.x, e.v * r5.w);
+        const float Py = fmaf(e.u, r5.y, e.v * r6.x);
+        const float Pz = fmaf(e.u, r5.z, e.v * r6.y);
+        const float Pr = fmaf(Px, rx, fmaf(Py, ryk[k], Pz));
+        const float beta = fmaf(s, Pr, w * gD) * fxfy * e.rinv;
+        const float Gx = fmaf(beta, r4.y, -s * Px);
+        const float Gy = fmaf(beta, r4.z, -s * Py);
+        const float Gz = fmaf(beta, r4.w, -s * Pz);
+        sG.x += Gx;
+        sG.y += Gy;
+        sG.z += Gz;
+        szG[k].x = fmaf(e.z, Gx, szG[k].x);
+        szG[k].y = fmaf(e.z, Gy, szG[k].y);
+        szG[k].z = fmaf(e.z, Gz, szG[k].z);
+        if (kNormal) sN[k] = sN[k] + w * f3(r3.z, r3.w, r4.x);
+      }
     }
   }
   // theta: r x sum z Gv (+ sum_pairs t_nc x w gN = N x gN over the pairs)
-  const F3 th = cross3(f3(rx, ry, 1.f), szG) + cross3(sN, gN);
+  F3 th = f3(0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < P; ++k)
+    th = th + cross3(f3(rx, ryk[k], 1.f), szG[k]) + cross3(sN[k], pg[k].gN);
+  (void)sNg;
   pr[0] += sG.x;
   pr[1] += sG.y;
   pr[2] += sG.z;

@@ -178,10 +178,18 @@ def camera(cam) -> Camera:
     return Camera(cam.fx, cam.fy, cam.cx, cam.cy, int(cam.width), int(cam.height), cam.near)
 
 
-def default_config(tile=(16, 16)) -> Config:
+def default_config(tile=(16, 16), px: int = 1) -> Config:
+    """The library's default compositing constants with a tile shape and a
+    pixels-per-thread count (tile_w * tile_h = 256 px)."""
     c = lib().gs2d_default_config()
     c.tile_w, c.tile_h = int(tile[0]), int(tile[1])
+    c.px_per_thread = int(px)
     return c
+
+
+# tile shapes of each pixels-per-thread count (256 P pixels, widths a
+# multiple of 8, heights of 4P)
+TILE_SHAPES = {1: ((16, 16), (8, 32), (32, 8)), 2: ((16, 32), (32, 16)), 4: ((32, 32), (16, 64))}
 
 
 def default_track_params(**kw) -> TrackParams:
@@ -457,8 +465,10 @@ class BatchRasterizer:
     images and upstream gradients; projection, binning and the two render
     passes each run as one batched call."""
 
-    def __init__(self, cams, n: int, actives=None, tiles=None, capacities=None, device="cuda"):
+    def __init__(self, cams, n: int, actives=None, tiles=None, capacities=None, device="cuda",
+                 px: int = 1):
         self.n = int(n)
+        self.px = int(px)
         self.device = device
         self.nv = len(cams)
         assert 0 < self.nv <= MAX_VIEWS
@@ -477,7 +487,7 @@ class BatchRasterizer:
             act = None if actives is None or actives[v] is None else \
                 torch.as_tensor(np.asarray(actives[v], np.int32), device=device)
             m = self.n if act is None else int(act.numel())
-            cfg = default_config(tiles[v] if tiles else (16, 16))
+            cfg = default_config(tiles[v] if tiles else TILE_SHAPES[self.px][0], self.px)
             ccam = camera(cam)
             tx = int(lib().gs2d_tiles_x(_ref(ccam), _ref(cfg)))
             ty = int(lib().gs2d_tiles_y(_ref(ccam), _ref(cfg)))
@@ -589,9 +599,9 @@ class Rasterizer:
     project -> bin_sort -> render_fwd, and render_bwd."""
 
     def __init__(self, cam, n: int, capacity: int | None = None, tile=(16, 16), device="cuda",
-                 keys: bool = False):
+                 keys: bool = False, px: int = 1):
         self.cam = camera(cam)
-        self.cfg = default_config(tile)
+        self.cfg = default_config(tile, px)
         self.n = int(n)
         self.device = device
         self.tiles_x = int(lib().gs2d_tiles_x(_ref(self.cam), _ref(self.cfg)))

@@ -17,11 +17,11 @@ def to_np(t):
     return t.detach().cpu().numpy().astype(np.float64)
 
 
-def gpu_render(surfels, cam, pose, tile=(16, 16), capacity=None, keys=False):
+def gpu_render(surfels, cam, pose, tile=(16, 16), capacity=None, keys=False, px=1):
     from paper_2506_00970_gb300 import gs2d
     import torch
     ds = gs2d.DeviceSurfels(surfels)
-    r = gs2d.Rasterizer(cam, ds.n, capacity=capacity, tile=tile, keys=keys)
+    r = gs2d.Rasterizer(cam, ds.n, capacity=capacity, tile=tile, keys=keys, px=px)
     pose_t = gs2d.pose_tensor(pose)
     out = r.forward(ds, pose_t)
     torch.cuda.synchronize()

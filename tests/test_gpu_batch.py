@@ -35,18 +35,22 @@ def _setup(n_views=4, seed=0):
     return s, cams, poses, actives, tiles
 
 
-def test_batch_forward_equals_single_views(torch_cuda):
+@pytest.mark.parametrize("px", [1, 2, 4])
+def test_batch_forward_equals_single_views(torch_cuda, px):
     torch = torch_cuda
     from paper_2506_00970_gb300 import gs2d
     s, cams, poses, actives, tiles = _setup()
+    if px != 1:
+        shapes = gs2d.TILE_SHAPES[px]
+        tiles = [shapes[v % len(shapes)] for v in range(len(cams))]
     ds = gs2d.DeviceSurfels(s)
-    br = gs2d.BatchRasterizer(cams, s.n, actives=actives, tiles=tiles)
+    br = gs2d.BatchRasterizer(cams, s.n, actives=actives, tiles=tiles, px=px)
     br.set_poses(poses)
     br.forward(ds)
     torch.cuda.synchronize()
     for v in range(len(cams)):
         sub = s if actives[v] is None else s.subset(actives[v])
-        _, _, _, g = gpu_render(sub, cams[v], poses[v], tile=tiles[v])
+        _, _, _, g = gpu_render(sub, cams[v], poses[v], tile=tiles[v], px=px)
         b = br.keep[v]
         for k in ("rgb", "depth", "normal", "opacity", "t_final", "n_last"):
             np.testing.assert_array_equal(b[k].cpu().numpy(), g[k], err_msg=f"view {v} {k}")
@@ -207,7 +211,7 @@ def test_autotune_picks_a_candidate_and_caches(torch_cuda, tmp_path):
     path = str(tmp_path / "tune.json")
     autotune._cache.clear()
     tiles, table = autotune.tune_tiles(ds, cams, poses, actives, reps=1, cache_path=path)
-    assert all(t in autotune.TILE_SHAPES for t in tiles)
+    assert all(t in autotune.TILE_SHAPES[1] for t in tiles)
     assert set(table) == {f"{c.width}x{c.height}" for c in cams}
     for c, t in zip(cams, tiles):
         row = table[f"{c.width}x{c.height}"]
@@ -215,3 +219,42 @@ def test_autotune_picks_a_candidate_and_caches(torch_cuda, tmp_path):
     autotune._cache.clear()
     tiles2, table2 = autotune.tune_tiles(ds, cams, poses, actives, cache_path=path)
     assert tiles2 == tiles and table2 == {}
+
+
+def test_batch_backward_two_pixels_per_thread_equals_single_views(torch_cuda):
+    """The persistent backward with 2 pixels per thread equals the
+    single-view backward (same per-pair arithmetic) summed over views."""
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d
+    s, cams, poses, actives, _ = _setup(n_views=3)
+    tiles = [(16, 32), (32, 16), (16, 32)]
+    ds = gs2d.DeviceSurfels(s)
+    br = gs2d.BatchRasterizer(cams, s.n, actives=actives, tiles=tiles, px=2)
+    br.set_poses(poses)
+    br.forward(ds)
+    for v, b in enumerate(br.keep):
+        up = scenes.random_upstream(70 + v, cams[v].height, cams[v].width)
+        b["d_rgb"].copy_(torch.tensor(up[0], dtype=torch.float32))
+        b["d_depth"].copy_(torch.tensor(up[1], dtype=torch.float32))
+    g = br.backward(ds)
+    single = {k: np.zeros(getattr(s, k).shape) for k in g}
+    for v in range(len(cams)):
+        ids = np.arange(s.n) if actives[v] is None else actives[v]
+        r, dsub, pt, _ = gpu_render(s.subset(ids), cams[v], poses[v], tile=tiles[v], px=2)
+        b = br.keep[v]
+        gv = r.backward(dsub, pt, b["d_rgb"], b["d_depth"], None, None, full=True)
+        for k in single:
+            single[k][ids] += to_np(gv[k])
+    torch.cuda.synchronize()
+    for k in single:
+        assert np.abs(to_np(g[k]) - single[k]).max() <= 1e-6 * np.abs(single[k]).max() * 3, k
+
+
+def test_autotune_sweeps_pixels_per_thread(torch_cuda):
+    from paper_2506_00970_gb300 import autotune, gs2d
+    s, cams, poses, actives, _ = _setup(n_views=2)
+    ds = gs2d.DeviceSurfels(s)
+    autotune._cache.clear()
+    px, tiles, table = autotune.tune(ds, cams, poses, actives, reps=1)
+    assert px in (1, 2, 4) and all(t in gs2d.TILE_SHAPES[px] for t in tiles)
+    assert set(table) == {"px1", "px2", "px4"}

@@ -143,9 +143,14 @@ def test_project_rects_and_depth(torch_cuda, orc, which):
 # ---------------------------------------------------------------------------
 # forward
 # ---------------------------------------------------------------------------
-def test_render_fwd_slab_full_image(torch_cuda, orc):
+# tile shapes with 1, 2 and 4 pixels per thread
+TILE_PX = [((16, 16), 1), ((16, 32), 2), ((32, 16), 2), ((64, 8), 2), ((32, 32), 4), ((16, 64), 4)]
+
+
+@pytest.mark.parametrize("tile,px", TILE_PX)
+def test_render_fwd_slab_full_image(torch_cuda, orc, tile, px):
     s, cam, pose = scenes.slab_scene(0), scenes.slab_camera(), scenes.identity_pose()
-    _, _, _, g = gpu_render(s, cam, pose)
+    _, _, _, g = gpu_render(s, cam, pose, tile=tile, px=px)
     o = orc.render(s, cam, pose)
     rep, ok = assert_images_close(g, o)
     assert o["opacity"].max() > 0.9 and (o["count"] > 3).mean() > 0.3
@@ -175,19 +180,20 @@ def test_render_fwd_room_sampled_pixels(torch_cuda, orc):
     assert np.median(o["opacity"]) > 0.95
 
 
-def test_render_edge_cases(torch_cuda, orc):
+@pytest.mark.parametrize("tile,px", [((16, 16), 1), ((16, 32), 2), ((32, 32), 4)])
+def test_render_edge_cases(torch_cuda, orc, tile, px):
     cam = scenes.Camera(50.0, 50.0, 20.5, 10.0, 37, 21)   # ragged tiles both ways
     # everything behind the camera: empty image
     s = scenes.slab_scene(2, 300)
     s.mu[:, 2] *= -1
-    _, _, _, g = gpu_render(s, cam, scenes.identity_pose())
+    _, _, _, g = gpu_render(s, cam, scenes.identity_pose(), tile=tile, px=px)
     assert np.all(g["opacity"] == 0) and np.all(g["t_final"] == 1) and np.all(g["n_last"] == 0)
     # a single surfel, and a surfel straddling the camera plane (full-image footprint)
     s1 = scenes.Surfels(np.array([[0.0, 0.0, 1.0], [0.05, 0.0, 0.06]]),
                         np.array([[1.0, 0, 0, 0], [0.7, 0.7, 0.0, 0.0]]),
                         np.array([[0.05, 0.05], [0.3, 0.3]]), np.array([0.8, 0.6]),
                         np.array([[1.0, 0.5, 0.2], [0.1, 0.9, 0.3]]))
-    _, _, _, g = gpu_render(s1, cam, scenes.identity_pose())
+    _, _, _, g = gpu_render(s1, cam, scenes.identity_pose(), tile=tile, px=px)
     o = orc.render(s1, cam, scenes.identity_pose())
     assert_images_close(g, o)
 
@@ -219,12 +225,14 @@ def _slab_loss_setup(orc):
     return s, cam, gt, tgt
 
 
-def test_render_bwd_slab_all_params_and_pose(torch_cuda, orc):
+@pytest.mark.parametrize("tile,px", [((16, 16), 1), ((32, 16), 2), ((32, 32), 4)])
+def test_render_bwd_slab_all_params_and_pose(torch_cuda, orc, tile, px):
     """Workload 1: L1 colour + L1 depth against a target rendered at a pose
-    offset by 2 cm / 1 degree; gradients to all surfel params and the pose."""
+    offset by 2 cm / 1 degree; gradients to all surfel params and the pose
+    (1, 2 and 4 pixels per thread)."""
     torch = torch_cuda
     s, cam, pose, tgt = _slab_loss_setup(orc)
-    r, ds, pose_t, g = gpu_render(s, cam, pose)
+    r, ds, pose_t, g = gpu_render(s, cam, pose, tile=tile, px=px)
     # upstream gradient of sum|rgb - rgb_t| + sum|D - D_t| from the oracle image
     o = orc.render(s, cam, pose)
     d_rgb = np.sign(o["rgb"] - tgt["rgb"])
@@ -243,10 +251,11 @@ def test_render_bwd_slab_all_params_and_pose(torch_cuda, orc):
     _grad_close(to_np(gp["pose6"]), og["pose6"], "pose6 (tracking mode)")
 
 
-def test_render_bwd_with_normal_and_opacity_grads(torch_cuda, orc):
+@pytest.mark.parametrize("tile,px", [((16, 16), 1), ((16, 64), 4)])
+def test_render_bwd_with_normal_and_opacity_grads(torch_cuda, orc, tile, px):
     torch = torch_cuda
     s, cam, pose = scenes.slab_scene(4), scenes.slab_camera(), scenes.identity_pose()
-    r, ds, pose_t, _ = gpu_render(s, cam, pose)
+    r, ds, pose_t, _ = gpu_render(s, cam, pose, tile=tile, px=px)
     up = scenes.random_upstream(5, cam.height, cam.width)
     og = orc.render_bwd(s, cam, pose, *up)
     T = lambda a: torch.tensor(np.asarray(a, np.float32), device="cuda")

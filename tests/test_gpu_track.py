@@ -94,10 +94,12 @@ def _track_setup(orc, n=30_000, seed=0):
     return s, cam, gt
 
 
-def test_track_step_first_gradient_and_convergence(torch_cuda, orc):
+@pytest.mark.parametrize("tile,px", [((16, 16), 1), ((32, 16), 2), ((32, 32), 4)])
+def test_track_step_first_gradient_and_convergence(torch_cuda, orc, tile, px):
     """The fused tracking step: its first pose gradient equals the oracle's at
     the start pose (through the loss and the pose-only backward), and 100
-    iterations from a 2 cm / 1 degree perturbation reach 1 cm / 0.5 degree."""
+    iterations from a 2 cm / 1 degree perturbation reach 1 cm / 0.5 degree
+    (1, 2 and 4 pixels per thread)."""
     torch = torch_cuda
     from paper_2506_00970_gb300 import gs2d
     s, cam, gt = _track_setup(orc)
@@ -112,7 +114,7 @@ def test_track_step_first_gradient_and_convergence(torch_cuda, orc):
 
     ds = gs2d.DeviceSurfels(s)
     ccam = gs2d.camera(cam)
-    cfg = gs2d.default_config()
+    cfg = gs2d.default_config(tile, px)
     prm = gs2d.default_track_params()
     n_iter = 100
     cap = 8 * s.n
