@@ -12,13 +12,17 @@
 //   K-major modes (8 consecutive k of one row are contiguous):
 //     K_DENSE   row-major [rows][ld] matrix
 //     K_IM2COL  conv forward: row = (b, oy, ox), k = tap * C + c
-//     K_DGRAD   conv data gradient: row = input pixel (b, iy, ix),
-//               k = tap * C_out + co, reading dZ at ((iy + 1 - ky) / 2,
-//               (ix + 1 - kx) / 2) when both are even and in range
+//     K_DGRADP  conv data gradient of one parity class (py, px) of the input
+//               pixels: row = (b, cy, cx) -> pixel (2 cy + py, 2 cx + px),
+//               k = t * C_out + co over the class's taps t, reading dZ at
+//               ((iy + 1 - ky) / 2, (ix + 1 - kx) / 2)
 //   row-major modes (8 consecutive rows of one k are contiguous):
 //     R_DENSE   element (row, k) at p[k * ld + row]
 //     R_IM2COL  conv weight gradient: row = tap * C + c, k = (b, oy, ox)
-//     R_WT      conv weights read transposed: row = c_in, k = tap * C_out + co
+//     R_WTP     conv weights read transposed for a parity class:
+//               row = c_in, k = t * C_out + co
+// Pixel and tap indices come from shifts (channel counts are powers of two)
+// and precomputed reciprocal multiplies (no integer division in the loop).
 // Tiles of 128 x 64 x 32 move global -> shared memory with 16-byte cp.async
 // (zero-filled where the gather falls outside), three stages deep; warps
 // read fragments with ldmatrix (.trans for row-major tiles) and issue
@@ -38,8 +42,8 @@ namespace net {
 typedef __nv_bfloat16 bf16;
 
 enum Mode {
-  K_DENSE = 0, K_IM2COL = 1, K_DGRAD = 2, K_DGRADP = 3,  // K-major
-  R_DENSE = 4, R_IM2COL = 5, R_WT = 6, R_WTP = 7         // row-major
+  K_DENSE = 0, K_IM2COL = 1, K_DGRADP = 3,  // K-major
+  R_DENSE = 4, R_IM2COL = 5, R_WTP = 7      // row-major
 };
 enum Epi { E_BIAS_RELU = 0, E_BIAS_F32 = 1, E_MASK = 2, E_PARTIAL = 3 };
 
@@ -55,12 +59,31 @@ constexpr int kHidden = 256;
 constexpr int kOut = GS2D_NET_OUT;
 constexpr int kOutPad = 8;  // FC2 rows padded to 8 in the bf16 weight copy
 
+// Division by a runtime constant d for numerators below 2^31: with
+// s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1,
+// n / d = (umulhi(n, m) + n) >> s (the round-up reciprocal method).
+struct FastDiv {
+  uint32_t m, s;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t s = 0;
+  while ((1ull << s) < d) ++s;
+  const unsigned long long m = ((1ull << 32) * ((1ull << s) - d)) / d + 1;
+  return FastDiv{(uint32_t)m, s};
+}
+__device__ __forceinline__ int fdiv(int n, FastDiv f) {
+  return (int)(((unsigned long long)__umulhi((uint32_t)n, f.m) + (uint32_t)n) >> f.s);
+}
+
 struct Operand {
   const bf16* p;
-  int ld;                // dense modes: leading dimension; R_WT(P): C_out
+  int ld;                // dense modes: leading dimension; R_WTP: C_out
   int rows;              // valid rows (M or N); multiple of 8 for row-major modes
   int H, W, C, Ho, Wo;   // conv geometry (input H x W x C, output Ho x Wo)
   int py, px, Hc, Wc;    // parity class of the data gradient (K_DGRADP, R_WTP)
+  int c_shift;           // log2 C (channel counts are powers of two)
+  int ld_shift;          // log2 ld (R_WTP)
+  FastDiv f_hw, f_w;     // pixels per image and per row of the indexed pixel grid
 };
 
 // Taps of a parity class of the stride-2 data gradient: input row iy gets
@@ -92,33 +115,24 @@ template <int MODE>
 __device__ __forceinline__ const bf16* kmajor_addr(const Operand& o, int row, int k, int kend) {
   if (row >= o.rows || k >= kend) return nullptr;
   if (MODE == K_DENSE) return o.p + (size_t)row * o.ld + k;
+  const int tap = k >> o.c_shift, c = k & ((1 << o.c_shift) - 1);
   if (MODE == K_IM2COL) {
-    const int hw = o.Ho * o.Wo;
-    const int b = row / hw, r = row - b * hw, oy = r / o.Wo, ox = r - oy * o.Wo;
-    const int tap = k / o.C, c = k - tap * o.C, ky = tap / 3, kx = tap - ky * 3;
+    // row = (b, oy, ox) over the output grid Ho x Wo
+    const int b = fdiv(row, o.f_hw), r = row - b * o.Ho * o.Wo;
+    const int oy = fdiv(r, o.f_w), ox = r - oy * o.Wo;
+    const int ky = tap / 3, kx = tap - ky * 3;
     const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
     if (iy < 0 || iy >= o.H || ix < 0 || ix >= o.W) return nullptr;
     return o.p + (((size_t)b * o.H + iy) * o.W + ix) * o.C + c;
   }
-  if (MODE == K_DGRADP) {
-    const int hw = o.Hc * o.Wc;
-    const int b = row / hw, r = row - b * hw, cy = r / o.Wc, cx = r - cy * o.Wc;
-    const int iy = 2 * cy + o.py, ix = 2 * cx + o.px;
-    const int t = k / o.C, c = k - t * o.C;
-    int ky, kx;
-    class_tap(o.py, o.px, t, ky, kx);
-    const int oy = (iy + 1 - ky) >> 1, ox = (ix + 1 - kx) >> 1;
-    if (oy < 0 || oy >= o.Ho || ox < 0 || ox >= o.Wo) return nullptr;
-    return o.p + (((size_t)b * o.Ho + oy) * o.Wo + ox) * o.C + c;
-  }
-  // K_DGRAD
-  const int hw = o.H * o.W;
-  const int b = row / hw, r = row - b * hw, iy = r / o.W, ix = r - iy * o.W;
-  const int tap = k / o.C, c = k - tap * o.C, ky = tap / 3, kx = tap - ky * 3;
-  const int ty = iy + 1 - ky, tx = ix + 1 - kx;
-  if (ty < 0 || tx < 0 || (ty & 1) || (tx & 1)) return nullptr;
-  const int oy = ty >> 1, ox = tx >> 1;
-  if (oy >= o.Ho || ox >= o.Wo) return nullptr;
+  // K_DGRADP: row = (b, cy, cx) over the class grid Hc x Wc
+  const int b = fdiv(row, o.f_hw), r = row - b * o.Hc * o.Wc;
+  const int cy = fdiv(r, o.f_w), cx = r - cy * o.Wc;
+  const int iy = 2 * cy + o.py, ix = 2 * cx + o.px;
+  int ky, kx;
+  class_tap(o.py, o.px, tap, ky, kx);
+  const int oy = (iy + 1 - ky) >> 1, ox = (ix + 1 - kx) >> 1;
+  if (oy < 0 || oy >= o.Ho || ox < 0 || ox >= o.Wo) return nullptr;
   return o.p + (((size_t)b * o.Ho + oy) * o.Wo + ox) * o.C + c;
 }
 
@@ -127,22 +141,20 @@ __device__ __forceinline__ const bf16* rowmajor_addr(const Operand& o, int row0,
   if (row0 >= o.rows || k >= kend) return nullptr;
   if (MODE == R_DENSE) return o.p + (size_t)k * o.ld + row0;
   if (MODE == R_IM2COL) {
-    const int tap = row0 / o.C, c = row0 - tap * o.C, ky = tap / 3, kx = tap - ky * 3;
-    const int hw = o.Ho * o.Wo;
-    const int b = k / hw, r = k - b * hw, oy = r / o.Wo, ox = r - oy * o.Wo;
+    // row0 = tap * C + c, k = (b, oy, ox) over the output grid
+    const int tap = row0 >> o.c_shift, c = row0 & ((1 << o.c_shift) - 1);
+    const int ky = tap / 3, kx = tap - ky * 3;
+    const int b = fdiv(k, o.f_hw), r = k - b * o.Ho * o.Wo;
+    const int oy = fdiv(r, o.f_w), ox = r - oy * o.Wo;
     const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
     if (iy < 0 || iy >= o.H || ix < 0 || ix >= o.W) return nullptr;
     return o.p + (((size_t)b * o.H + iy) * o.W + ix) * o.C + c;
   }
-  if (MODE == R_WTP) {
-    const int t = k / o.ld, co = k - t * o.ld;
-    int ky, kx;
-    class_tap(o.py, o.px, t, ky, kx);
-    return o.p + ((size_t)co * 9 + ky * 3 + kx) * o.C + row0;
-  }
-  // R_WT
-  const int tap = k / o.ld, co = k - tap * o.ld;
-  return o.p + ((size_t)co * 9 + tap) * o.C + row0;
+  // R_WTP: weights W[co][ky][kx][ci] read as (row = ci, k = t * C_out + co)
+  const int t = k >> o.ld_shift, co = k & ((1 << o.ld_shift) - 1);
+  int ky, kx;
+  class_tap(o.py, o.px, t, ky, kx);
+  return o.p + ((size_t)co * 9 + ky * 3 + kx) * o.C + row0;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
@@ -677,6 +689,13 @@ Operand op(const bf16* p, int ld, int rows) {
   o.rows = rows;
   return o;
 }
+int log2_exact(int v) {
+  int s = 0;
+  while ((1 << s) < v) ++s;
+  return s;
+}
+// Gathers over the output grid of conv layer l (K_IM2COL, R_IM2COL) with C
+// channels of the gathered tensor (a power of two).
 Operand conv_op(const bf16* p, int rows, int l, int C) {
   Operand o{};
   o.p = p;
@@ -686,6 +705,9 @@ Operand conv_op(const bf16* p, int rows, int l, int C) {
   o.Ho = kHin[l + 1];
   o.Wo = kWin[l + 1];
   o.C = C;
+  o.c_shift = log2_exact(C);
+  o.f_hw = make_fastdiv((uint32_t)(o.Ho * o.Wo));
+  o.f_w = make_fastdiv((uint32_t)o.Wo);
   return o;
 }
 
@@ -888,9 +910,12 @@ int backward(const float* params, const bf16* x, int B, const Ws& w, float* grad
         d.a.px = px;
         d.a.Hc = Hc;
         d.a.Wc = Wc;
+        d.a.f_hw = make_fastdiv((uint32_t)(Hc * Wc));
+        d.a.f_w = make_fastdiv((uint32_t)Wc);
         Operand wt{};
         wt.p = w.wbf + L.wbf_off[l];
         wt.ld = kCout[l];
+        wt.ld_shift = log2_exact(kCout[l]);
         wt.rows = kCin[l];
         wt.C = kCin[l];
         wt.py = py;
