@@ -111,52 +111,6 @@ struct Gemm {
   int remap, rH, rW, rHc, rWc, rpy, rpx;
 };
 
-template <int MODE>
-__device__ __forceinline__ const bf16* kmajor_addr(const Operand& o, int row, int k, int kend) {
-  if (row >= o.rows || k >= kend) return nullptr;
-  if (MODE == K_DENSE) return o.p + (size_t)row * o.ld + k;
-  const int tap = k >> o.c_shift, c = k & ((1 << o.c_shift) - 1);
-  if (MODE == K_IM2COL) {
-    // row = (b, oy, ox) over the output grid Ho x Wo
-    const int b = fdiv(row, o.f_hw), r = row - b * o.Ho * o.Wo;
-    const int oy = fdiv(r, o.f_w), ox = r - oy * o.Wo;
-    const int ky = tap / 3, kx = tap - ky * 3;
-    const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
-    if (iy < 0 || iy >= o.H || ix < 0 || ix >= o.W) return nullptr;
-    return o.p + (((size_t)b * o.H + iy) * o.W + ix) * o.C + c;
-  }
-  // K_DGRADP: row = (b, cy, cx) over the class grid Hc x Wc
-  const int b = fdiv(row, o.f_hw), r = row - b * o.Hc * o.Wc;
-  const int cy = fdiv(r, o.f_w), cx = r - cy * o.Wc;
-  const int iy = 2 * cy + o.py, ix = 2 * cx + o.px;
-  int ky, kx;
-  class_tap(o.py, o.px, tap, ky, kx);
-  const int oy = (iy + 1 - ky) >> 1, ox = (ix + 1 - kx) >> 1;
-  if (oy < 0 || oy >= o.Ho || ox < 0 || ox >= o.Wo) return nullptr;
-  return o.p + (((size_t)b * o.Ho + oy) * o.Wo + ox) * o.C + c;
-}
-
-template <int MODE>
-__device__ __forceinline__ const bf16* rowmajor_addr(const Operand& o, int row0, int k, int kend) {
-  if (row0 >= o.rows || k >= kend) return nullptr;
-  if (MODE == R_DENSE) return o.p + (size_t)k * o.ld + row0;
-  if (MODE == R_IM2COL) {
-    // row0 = tap * C + c, k = (b, oy, ox) over the output grid
-    const int tap = row0 >> o.c_shift, c = row0 & ((1 << o.c_shift) - 1);
-    const int ky = tap / 3, kx = tap - ky * 3;
-    const int b = fdiv(k, o.f_hw), r = k - b * o.Ho * o.Wo;
-    const int oy = fdiv(r, o.f_w), ox = r - oy * o.Wo;
-    const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
-    if (iy < 0 || iy >= o.H || ix < 0 || ix >= o.W) return nullptr;
-    return o.p + (((size_t)b * o.H + iy) * o.W + ix) * o.C + c;
-  }
-  // R_WTP: weights W[co][ky][kx][ci] read as (row = ci, k = t * C_out + co)
-  const int t = k >> o.ld_shift, co = k & ((1 << o.ld_shift) - 1);
-  int ky, kx;
-  class_tap(o.py, o.px, t, ky, kx);
-  return o.p + ((size_t)co * 9 + ky * 3 + kx) * o.C + row0;
-}
-
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   const int n = valid ? 16 : 0;
@@ -198,22 +152,109 @@ __host__ __device__ constexpr int tile_elems() {
   return is_kmajor<MODE>() ? ROWS * (BK + PAD) : BK * (ROWS + PAD);
 }
 
-// One stage: ROWS x BK tile of an operand into shared memory.
+// Per-thread gather state of one operand tile: a thread always loads the
+// same rows (K-major) or row group (row-major) of the tile, so their pixel
+// coordinates are found once; each K step only locates its tap and channel.
 template <int MODE, int ROWS>
-__device__ __forceinline__ void load_tile(bf16* s, const Operand& o, int r0, int k0, int kend) {
-  constexpr int kVec = ROWS * BK / 8;
-  for (int v = threadIdx.x; v < kVec; v += THREADS) {
-    if (is_kmajor<MODE>()) {
-      const int r = v >> 2, kq = (v & 3) * 8;
-      const bf16* src = kmajor_addr<MODE>(o, r0 + r, k0 + kq, kend);
-      cp_async16(s + r * (BK + PAD) + kq, src ? src : o.p, src != nullptr);
-    } else {
-      const int kk = v / (ROWS / 8), rq = (v % (ROWS / 8)) * 8;
-      const bf16* src = rowmajor_addr<MODE>(o, r0 + rq, k0 + kk, kend);
-      cp_async16(s + kk * (ROWS + PAD) + rq, src ? src : o.p, src != nullptr);
+struct Loader {
+  static constexpr int kVec = ROWS * BK / 8;
+  static constexpr int kPer = kVec / THREADS;  // 16-byte vectors per thread and stage
+  const bf16* base[kPer];  // K-major: row start (dense) or image start (gathers)
+  int iy0[kPer], ix0[kPer];
+  bool ok[kPer];
+  int ky, kx, c;            // R_IM2COL: the row group's tap and channel
+
+  __device__ __forceinline__ Loader(const Operand& o, int r0) {
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int v = threadIdx.x + i * THREADS;
+      if (is_kmajor<MODE>()) {
+        const int row = r0 + (v >> 2);
+        ok[i] = row < o.rows;
+        iy0[i] = ix0[i] = 0;
+        if (MODE == K_DENSE) {
+          base[i] = o.p + (size_t)row * o.ld;
+        } else if (MODE == K_IM2COL) {
+          const int b = fdiv(row, o.f_hw), r = row - b * o.Ho * o.Wo;
+          const int oy = fdiv(r, o.f_w), ox = r - oy * o.Wo;
+          base[i] = o.p + (size_t)b * o.H * o.W * o.C;
+          iy0[i] = 2 * oy - 1;
+          ix0[i] = 2 * ox - 1;
+        } else {  // K_DGRADP
+          const int b = fdiv(row, o.f_hw), r = row - b * o.Hc * o.Wc;
+          const int cy = fdiv(r, o.f_w), cx = r - cy * o.Wc;
+          base[i] = o.p + (size_t)b * o.Ho * o.Wo * o.C;
+          iy0[i] = 2 * cy + o.py;
+          ix0[i] = 2 * cx + o.px;
+        }
+      } else {
+        const int row0 = r0 + (v % (ROWS / 8)) * 8;
+        ok[i] = row0 < o.rows;
+        base[i] = o.p;
+        iy0[i] = ix0[i] = 0;
+      }
+    }
+    ky = kx = c = 0;
+    if (MODE == R_IM2COL) {
+      const int row0 = r0 + (threadIdx.x % (ROWS / 8)) * 8;
+      const int tap = row0 >> o.c_shift;
+      c = row0 & ((1 << o.c_shift) - 1);
+      ky = tap / 3;
+      kx = tap - ky * 3;
     }
   }
-}
+
+  __device__ __forceinline__ const bf16* kaddr(const Operand& o, int i, int k, int kend) const {
+    if (!ok[i] || k >= kend) return nullptr;
+    if (MODE == K_DENSE) return base[i] + k;
+    const int tap = k >> o.c_shift, ch = k & ((1 << o.c_shift) - 1);
+    if (MODE == K_IM2COL) {
+      const int tky = tap / 3, tkx = tap - tky * 3;
+      const int iy = iy0[i] + tky, ix = ix0[i] + tkx;
+      if (iy < 0 || iy >= o.H || ix < 0 || ix >= o.W) return nullptr;
+      return base[i] + ((size_t)iy * o.W + ix) * o.C + ch;
+    }
+    int tky, tkx;  // K_DGRADP
+    class_tap(o.py, o.px, tap, tky, tkx);
+    const int oy = (iy0[i] + 1 - tky) >> 1, ox = (ix0[i] + 1 - tkx) >> 1;
+    if (oy < 0 || oy >= o.Ho || ox < 0 || ox >= o.Wo) return nullptr;
+    return base[i] + ((size_t)oy * o.Wo + ox) * o.C + ch;
+  }
+
+  __device__ __forceinline__ const bf16* raddr(const Operand& o, int i, int row0, int k,
+                                               int kend) const {
+    if (!ok[i] || k >= kend) return nullptr;
+    if (MODE == R_DENSE) return o.p + (size_t)k * o.ld + row0;
+    if (MODE == R_IM2COL) {
+      const int b = fdiv(k, o.f_hw), r = k - b * o.Ho * o.Wo;
+      const int oy = fdiv(r, o.f_w), ox = r - oy * o.Wo;
+      const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
+      if (iy < 0 || iy >= o.H || ix < 0 || ix >= o.W) return nullptr;
+      return o.p + (((size_t)b * o.H + iy) * o.W + ix) * o.C + c;
+    }
+    const int t = k >> o.ld_shift, co = k & ((1 << o.ld_shift) - 1);  // R_WTP
+    int tky, tkx;
+    class_tap(o.py, o.px, t, tky, tkx);
+    return o.p + ((size_t)co * 9 + tky * 3 + tkx) * o.C + row0;
+  }
+
+  // One stage: the ROWS x BK tile at k0 into shared memory.
+  __device__ __forceinline__ void load(bf16* s, const Operand& o, int r0, int k0, int kend) const {
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int v = threadIdx.x + i * THREADS;
+      if (is_kmajor<MODE>()) {
+        const int r = v >> 2, kq = (v & 3) * 8;
+        const bf16* src = kaddr(o, i, k0 + kq, kend);
+        cp_async16(s + r * (BK + PAD) + kq, src ? src : o.p, src != nullptr);
+      } else {
+        const int kk = v / (ROWS / 8), rq = (v % (ROWS / 8)) * 8;
+        const bf16* src = raddr(o, i, r0 + rq, k0 + kk, kend);
+        cp_async16(s + kk * (ROWS + PAD) + rq, src ? src : o.p, src != nullptr);
+      }
+    }
+  }
+};
 
 // A fragment of the m16 x k16 sub-tile at (r0, k0) of a stage.
 template <int MODE, int ROWS>
@@ -300,6 +341,8 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const Gemm g) {
   const int kend = min(g.K, kbeg + g.k_split);
   const int ntiles = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
   const int warp = threadIdx.x >> 5, wm = (warp & 3) * 32, wn = (warp >> 2) * 32;
+  const Loader<AM, BM> la(g.a, m0);
+  const Loader<BMODE, BN> lb(g.b, n0);
   float acc[2][4][4];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -311,8 +354,8 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const Gemm g) {
 #pragma unroll
   for (int s = 0; s < STAGES - 1; ++s) {
     if (s < ntiles) {
-      load_tile<AM, BM>(sA + s * kA, g.a, m0, kbeg + s * BK, kend);
-      load_tile<BMODE, BN>(sB + s * kB, g.b, n0, kbeg + s * BK, kend);
+      la.load(sA + s * kA, g.a, m0, kbeg + s * BK, kend);
+      lb.load(sB + s * kB, g.b, n0, kbeg + s * BK, kend);
     }
     cp_async_commit();
   }
@@ -322,8 +365,8 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const Gemm g) {
     const int nk = kt + STAGES - 1;
     if (nk < ntiles) {
       const int st = nk % STAGES;
-      load_tile<AM, BM>(sA + st * kA, g.a, m0, kbeg + nk * BK, kend);
-      load_tile<BMODE, BN>(sB + st * kB, g.b, n0, kbeg + nk * BK, kend);
+      la.load(sA + st * kA, g.a, m0, kbeg + nk * BK, kend);
+      lb.load(sB + st * kB, g.b, n0, kbeg + nk * BK, kend);
     }
     cp_async_commit();
     const bf16* a_s = sA + (kt % STAGES) * kA;
