@@ -109,6 +109,7 @@ struct Gemm {
   // output row remap of a parity-class data gradient: GEMM row (b, cy, cx)
   // -> pixel (b, 2 cy + py, 2 cx + px) of an H x W map
   int remap, rH, rW, rHc, rWc, rpy, rpx;
+  int* err;              // set to 1 by a tensor-core kernel whose wait timed out
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
@@ -155,10 +156,10 @@ __host__ __device__ constexpr int tile_elems() {
 // Per-thread gather state of one operand tile: a thread always loads the
 // same rows (K-major) or row group (row-major) of the tile, so their pixel
 // coordinates are found once; each K step only locates its tap and channel.
-template <int MODE, int ROWS>
+template <int MODE, int ROWS, int NT = THREADS, int KB = BK>
 struct Loader {
-  static constexpr int kVec = ROWS * BK / 8;
-  static constexpr int kPer = kVec / THREADS;  // 16-byte vectors per thread and stage
+  static constexpr int kVec = ROWS * KB / 8;
+  static constexpr int kPer = kVec / NT;  // 16-byte vectors per thread and stage
   const bf16* base[kPer];  // K-major: row start (dense) or image start (gathers)
   int iy0[kPer], ix0[kPer];
   bool ok[kPer];
@@ -167,9 +168,9 @@ struct Loader {
   __device__ __forceinline__ Loader(const Operand& o, int r0) {
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
-      const int v = threadIdx.x + i * THREADS;
+      const int v = threadIdx.x + i * NT;
       if (is_kmajor<MODE>()) {
-        const int row = r0 + (v >> 2);
+        const int row = r0 + v / (KB / 8);
         ok[i] = row < o.rows;
         iy0[i] = ix0[i] = 0;
         if (MODE == K_DENSE) {
@@ -238,11 +239,35 @@ struct Loader {
     return o.p + ((size_t)co * 9 + tky * 3 + tkx) * o.C + row0;
   }
 
+  // One stage in the tcgen05 operand layout: 8 x 8 core matrices of 128
+  // bytes (16 contiguous bytes along K for K-major tiles, along the rows for
+  // row-major tiles).  K-major: core (row group g, k group q) at
+  // g * 512 + q * 128 bytes; row-major: core (k group q, row group g) at
+  // q * (ROWS / 8) * 128 + g * 128 bytes.
+  __device__ __forceinline__ void load_core(unsigned char* s, const Operand& o, int r0, int k0,
+                                            int kend) const {
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int v = threadIdx.x + i * NT;
+      if (is_kmajor<MODE>()) {
+        const int r = v / (KB / 8), kq = (v % (KB / 8)) * 8;
+        const bf16* src = kaddr(o, i, k0 + kq, kend);
+        cp_async16(s + (r >> 3) * (KB / 8) * 128 + (kq >> 3) * 128 + (r & 7) * 16, src ? src : o.p,
+                   src != nullptr);
+      } else {
+        const int kk = v / (ROWS / 8), rq = (v % (ROWS / 8)) * 8;
+        const bf16* src = raddr(o, i, r0 + rq, k0 + kk, kend);
+        cp_async16(s + (kk >> 3) * (ROWS / 8) * 128 + (rq >> 3) * 128 + (kk & 7) * 16,
+                   src ? src : o.p, src != nullptr);
+      }
+    }
+  }
+
   // One stage: the ROWS x BK tile at k0 into shared memory.
   __device__ __forceinline__ void load(bf16* s, const Operand& o, int r0, int k0, int kend) const {
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
-      const int v = threadIdx.x + i * THREADS;
+      const int v = threadIdx.x + i * NT;
       if (is_kmajor<MODE>()) {
         const int r = v >> 2, kq = (v & 3) * 8;
         const bf16* src = kaddr(o, i, k0 + kq, kend);
@@ -395,6 +420,184 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const Gemm g) {
       apply_epi<EPI>(g, row, col, acc[i][j][0], acc[i][j][1]);
       apply_epi<EPI>(g, row + 8, col, acc[i][j][2], acc[i][j][3]);
     }
+}
+
+// ---------------------------------------------------------------------------
+// The same GEMM on the 5th-generation tensor cores: one elected thread issues
+// tcgen05.mma (M = 128, N = 64, K = 16, bf16 x bf16 -> f32) from shared-memory
+// descriptors, the accumulator lives in tensor memory (128 lanes x 64
+// columns), and each of the four warps reads its 32 lanes back with
+// tcgen05.ld for the epilogue.  Operand tiles are gathered by the same
+// loaders (cp.async) into the no-swizzle core-matrix layout; a stage is
+// refilled after the tcgen05.commit of the MMAs that read it arrives on the
+// stage's mbarrier.  Every wait is bounded: past the limit the kernel records
+// an error in *err, stops issuing work, and still frees its tensor memory.
+constexpr int TC_THREADS = 256, TC_STAGES = 3, TC_COLS = 64, TC_BK = 64;
+constexpr int TC_A_BYTES = BM * TC_BK * 2, TC_B_BYTES = BN * TC_BK * 2;
+constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES;  // 72 KB
+constexpr int kTcSpin = 1 << 24;
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+// Shared-memory matrix descriptor, no swizzle: start address, the byte step
+// between core matrices along K (leading) and along M / N (stride).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t k_step, uint32_t mn_step) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((k_step >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((mn_step >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: f32 accumulate, bf16 A and B, A / B
+// K-major (0) or M/N-major (1), N = 64, M = 128.
+__host__ __device__ constexpr uint32_t tc_idesc(bool a_mn, bool b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (a_mn ? 1u << 15 : 0u) | (b_mn ? 1u << 16 : 0u) |
+         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int spins = 0; spins < kTcSpin; ++spins) {
+    uint32_t ok;
+    asm volatile(
+        "{.reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;}\n"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+template <int AM, int BMODE, int EPI>
+__global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const Gemm g) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ __align__(8) uint64_t s_bar[TC_STAGES + 1];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int kbeg = blockIdx.z * g.k_split;
+  const int kend = min(g.K, kbeg + g.k_split);
+  const int ntiles = kend > kbeg ? (kend - kbeg + TC_BK - 1) / TC_BK : 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr bool a_mn = !is_kmajor<AM>(), b_mn = !is_kmajor<BMODE>();
+  // descriptor steps: K-major core matrices 128 B apart along K and
+  // TC_BK / 8 x 128 B along the rows; row-major ones 128 B apart along the
+  // rows and ROWS / 8 x 128 B apart along K
+  constexpr uint32_t a_k = a_mn ? (BM / 8) * 128 : 128, a_mn_step = a_mn ? 128 : (TC_BK / 8) * 128;
+  constexpr uint32_t b_k = b_mn ? (BN / 8) * 128 : 128, b_mn_step = b_mn ? 128 : (TC_BK / 8) * 128;
+  constexpr uint32_t idesc = tc_idesc(a_mn, b_mn);
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int i = 0; i <= TC_STAGES; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&s_bar[i])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
+                 "r"(TC_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+
+  const Loader<AM, BM, TC_THREADS, TC_BK> la(g.a, m0);
+  const Loader<BMODE, BN, TC_THREADS, TC_BK> lb(g.b, n0);
+  auto stage_a = [&](int s) { return tc_smem + s * TC_STAGE_BYTES; };
+  auto stage_b = [&](int s) { return tc_smem + s * TC_STAGE_BYTES + TC_A_BYTES; };
+
+#pragma unroll
+  for (int s = 0; s < TC_STAGES - 1; ++s) {
+    if (s < ntiles) {
+      la.load_core(stage_a(s), g.a, m0, kbeg + s * TC_BK, kend);
+      lb.load_core(stage_b(s), g.b, n0, kbeg + s * TC_BK, kend);
+    }
+    cp_async_commit();
+  }
+  bool fail = false;
+  for (int kt = 0; kt < ntiles; ++kt) {
+    const int st = kt % TC_STAGES;
+    cp_async_wait<TC_STAGES - 2>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && !fail) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = su32(stage_a(st)), sb = su32(stage_b(st));
+#pragma unroll
+      for (int j = 0; j < TC_BK / 16; ++j) {
+        const uint64_t ad = smem_desc(sa + j * 2 * a_k, a_k, a_mn_step);
+        const uint64_t bd = smem_desc(sb + j * 2 * b_k, b_k, b_mn_step);
+        const uint32_t acc = (kt > 0 || j > 0) ? 1u : 0u;
+        asm volatile(
+            "{.reg .pred p; setp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       su32(&s_bar[st])) : "memory");
+    }
+    // refill the stage read by the previous k-tile once its MMAs are done
+    const int nk = kt + TC_STAGES - 1;
+    if (nk < ntiles) {
+      const int sl = nk % TC_STAGES;
+      if (kt >= 1 && !fail) fail = !mbar_wait(su32(&s_bar[sl]), (uint32_t)(((kt - 1) / TC_STAGES) & 1));
+      if (!fail) {
+        la.load_core(stage_a(sl), g.a, m0, kbeg + nk * TC_BK, kend);
+        lb.load_core(stage_b(sl), g.b, n0, kbeg + nk * TC_BK, kend);
+      }
+    }
+    cp_async_commit();
+  }
+  cp_async_wait<0>();
+  // all MMAs done: a last commit arrives on the final barrier
+  if (threadIdx.x == 0 && ntiles > 0 && !fail)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     su32(&s_bar[TC_STAGES])) : "memory");
+  if (ntiles > 0 && !fail) fail = !mbar_wait(su32(&s_bar[TC_STAGES]), 0u);
+  if (fail) atomicExch(&s_fail, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (!s_fail) {
+    // warp w reads the accumulator lanes of its quadrant (w % 4) and half the
+    // columns (w / 4) into the (now idle) stage buffers as a row-major FP32
+    // tile; then consecutive threads take consecutive column pairs of a row,
+    // so the epilogue's loads and stores are coalesced
+    constexpr int kLd = BN + 2;  // floats per staged row
+    float* tile = reinterpret_cast<float*>(tc_smem);
+    const int quad = warp & 3, half = warp >> 2;
+    const int lrow = 32 * quad + lane;
+#pragma unroll
+    for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
+      uint32_t r[16];
+      const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0;
+      if (ntiles > 0) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+            "%10, %11, %12, %13, %14, %15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+              "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+              "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) r[j] = 0u;
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) tile[lrow * kLd + c0 + j] = __uint_as_float(r[j]);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < BM * (BN / 2); e += TC_THREADS) {
+      const int rr = e / (BN / 2), cc = 2 * (e % (BN / 2));
+      const float2 v = *reinterpret_cast<const float2*>(&tile[rr * kLd + cc]);
+      apply_epi<EPI>(g, m0 + rr, n0 + cc, v.x, v.y);
+    }
+  } else if (threadIdx.x == 0 && g.err) {
+    atomicExch(g.err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS));
 }
 
 // out[m * n_out + n] = sum_s part[(s * M + m) * N + n] for m < m_valid,
@@ -643,6 +846,7 @@ struct Ws {
   float* part;
   size_t part_floats;
   float* loss;
+  int* err;              // tensor-core wait timeouts (0 = none)
   size_t bytes;
 };
 
@@ -652,7 +856,7 @@ int splits_for(int M, int N, int K) {
   s = max(1, min(s, (K + 255) / 256));
   return s;
 }
-int k_split_for(int K, int s) { return (int)align_up((size_t)((K + s - 1) / s), BK); }
+int k_split_for(int K, int s) { return (int)align_up((size_t)((K + s - 1) / s), 64); }
 
 // Split-K count of a forward or data-gradient GEMM from its shape per sample
 // at a nominal batch of 256 -- never from the actual batch, so every output
@@ -666,7 +870,7 @@ int splits_nominal(int rows_per_sample, int N, int K) {
   return max(1, min(s, K / 128));
 }
 int splits_count(int K, int s) {
-  const int ks = s > 1 ? k_split_for(K, s) : (int)align_up((size_t)K, BK);
+  const int ks = s > 1 ? k_split_for(K, s) : (int)align_up((size_t)K, 64);
   return max((K + ks - 1) / ks, 1);
 }
 int class_hc(int H, int py) { return (H + 1 - py) / 2; }
@@ -721,6 +925,7 @@ Ws carve(void* base, int B) {
   w.part_floats = max_partials(B);
   w.part = c.take<float>(w.part_floats);
   w.loss = c.take<float>(64);
+  w.err = c.take<int>(64);
   w.bytes = align_up(c.off, 256);
   return w;
 }
@@ -754,13 +959,33 @@ Operand conv_op(const bf16* p, int rows, int l, int C) {
   return o;
 }
 
+// Launches one GEMM.  Split-K partial products (the deep-K weight
+// gradients and the split deep layers) run on the tcgen05 kernel; GEMMs with
+// a direct epilogue (large M, the gather-bound convolutions) on the mma.sync
+// kernel, whose smaller blocks keep more warps resident to hide the gathers
+// (profiles/ holds the per-kind comparison).
 template <int AM, int BMODE, int EPI>
 int run(Gemm g, int splits, cudaStream_t st, int* n_splits = nullptr) {
-  g.k_split = splits > 1 ? k_split_for(g.K, splits) : (int)align_up((size_t)g.K, BK);
+  constexpr bool tc = EPI == E_PARTIAL;
+  const int align = tc ? TC_BK : BK;
+  g.k_split = splits > 1 ? k_split_for(g.K, splits) : (int)align_up((size_t)g.K, align);
   const int S = max((g.K + g.k_split - 1) / g.k_split, 1);
   const dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, S);
   if (grid.y > 65535 || grid.z > 65535) return GS2D_ERR_INVALID_ARG;
-  gemm_kernel<AM, BMODE, EPI><<<grid, THREADS, 0, st>>>(g);
+  if constexpr (tc) {
+    static bool ready[64] = {};
+    int dev = 0;
+    GS2D_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return GS2D_ERR_CUDA;
+    if (!ready[dev]) {
+      GS2D_CUDA_TRY(cudaFuncSetAttribute(gemm_tc_kernel<AM, BMODE, EPI>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+      ready[dev] = true;
+    }
+    gemm_tc_kernel<AM, BMODE, EPI><<<grid, TC_THREADS, TC_SMEM, st>>>(g);
+  } else {
+    gemm_kernel<AM, BMODE, EPI><<<grid, THREADS, 0, st>>>(g);
+  }
   GS2D_LAUNCH_CHECK();
   if (n_splits) *n_splits = S;
   return GS2D_OK;
@@ -824,11 +1049,13 @@ int cast(const float* params, const Ws& w, cudaStream_t st) {
 
 int forward(const float* params, const bf16* x, int B, const Ws& w, float* y, cudaStream_t st) {
   const Layout L = layout();
+  GS2D_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   int r = cast(params, w, st);
   if (r) return r;
   const bf16* in = x;
   for (int l = 0; l < kConv; ++l) {
     Gemm g{};
+    g.err = w.err;
     g.M = B * kHin[l + 1] * kWin[l + 1];
     g.N = kCout[l];
     g.K = 9 * kCin[l];
@@ -843,6 +1070,7 @@ int forward(const float* params, const bf16* x, int B, const Ws& w, float* y, cu
   }
   {
     Gemm g{};
+    g.err = w.err;
     g.M = B;
     g.N = kHidden;
     g.K = kFlat;
@@ -856,6 +1084,7 @@ int forward(const float* params, const bf16* x, int B, const Ws& w, float* y, cu
   }
   {
     Gemm g{};
+    g.err = w.err;
     g.M = B;
     g.N = kOutPad;
     g.K = kHidden;
@@ -877,6 +1106,7 @@ int backward(const float* params, const bf16* x, int B, const Ws& w, float* grad
   // FC2: dz2 [B][8]
   {
     Gemm g{};
+    g.err = w.err;
     g.M = kOutPad;
     g.N = kHidden;
     g.K = B;
@@ -887,6 +1117,7 @@ int backward(const float* params, const bf16* x, int B, const Ws& w, float* grad
     r = bias_grad(w.dz2, B, kOutPad, kOut, w.part, grad + L.b_off[kConv + 1], st);
     if (r) return r;
     Gemm d{};
+    d.err = w.err;
     d.M = B;
     d.N = kHidden;
     d.K = kOutPad;
@@ -901,6 +1132,7 @@ int backward(const float* params, const bf16* x, int B, const Ws& w, float* grad
   // FC1: dz1 = dzA [B][256]
   {
     Gemm g{};
+    g.err = w.err;
     g.M = kHidden;
     g.N = kFlat;
     g.K = B;
@@ -911,6 +1143,7 @@ int backward(const float* params, const bf16* x, int B, const Ws& w, float* grad
     r = bias_grad(w.dzA, B, kHidden, kHidden, w.part, grad + L.b_off[kConv], st);
     if (r) return r;
     Gemm d{};
+    d.err = w.err;
     d.M = B;
     d.N = kFlat;
     d.K = kHidden;
@@ -929,6 +1162,7 @@ int backward(const float* params, const bf16* x, int B, const Ws& w, float* grad
     const bf16* a_in = l == 0 ? x : w.act[l];
     const int P = B * kHin[l + 1] * kWin[l + 1];
     Gemm g{};
+    g.err = w.err;
     g.M = kCout[l];
     g.N = 9 * kCin[l];
     g.K = P;
@@ -945,6 +1179,7 @@ int backward(const float* params, const bf16* x, int B, const Ws& w, float* grad
       for (int px = 0; px < 2; ++px) {
         const int Hc = class_hc(kHin[l], py), Wc = class_hc(kWin[l], px);
         Gemm d{};
+        d.err = w.err;
         d.M = B * Hc * Wc;
         d.N = kCin[l];
         d.K = (py ? 2 : 1) * (px ? 2 : 1) * kCout[l];
