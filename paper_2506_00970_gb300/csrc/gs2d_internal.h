@@ -15,11 +15,19 @@ int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* p
                    const int32_t* gate, cudaStream_t st);
 
 // gs2d_bin_sort; with need_emit false the emission offsets and indices
-// (used only by the full backward) are not computed.
+// (used only by the full backward) are not computed.  flags:
+// kSortPreZeroed -- the caller has zeroed the counter region
+// (sort_zero_region) since the last binning, so no init launch;
+// kSortLongInBlock -- tiles with segments over 2048 keys are sorted by their
+// own 128-thread block (chunks + merges) instead of a separate launch.
+constexpr unsigned kSortPreZeroed = 1u, kSortLongInBlock = 2u;
 int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
                     const gs2d_camera* cam, const gs2d_config* cfg, void* workspace,
                     size_t ws_bytes, size_t* ws_needed, const gs2d_bins* bins, bool need_emit,
-                    cudaStream_t st);
+                    cudaStream_t st, unsigned flags = 0u);
+// The counter region of a sort workspace that every binning needs zeroed.
+void sort_zero_region(void* workspace, int n, size_t capacity, int n_tiles, uint32_t** begin,
+                      size_t* words);
 
 int render_fwd_launch(const float* proj, const gs2d_bins* bins, const gs2d_camera* cam,
                       const gs2d_config* cfg, float* rgb, float* depth, float* normal,
@@ -34,6 +42,8 @@ struct TrackStep {
   float* pose_hist;  // [n_iter * 12] or NULL
   int iter;
   uint32_t* counter; // blocks finished in this iteration (reset by the last)
+  uint32_t* sort_zero;   // binning counters the last block zeroes for the next
+  size_t sort_zero_words;  // iteration's binning (kSortPreZeroed)
 };
 
 // Fused tracking iteration per tile (forward, tracking loss, pose backward)

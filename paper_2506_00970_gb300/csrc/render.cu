@@ -247,6 +247,10 @@ __global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) t
   reduce_and_step(pose_part, loss_part, gridDim.x, ts.pose, ts.adam, prm, ts.loss_hist,
                   ts.pose_hist, ts.iter, status, s_red);
   if (threadIdx.x == 0) *ts.counter = 0u;
+  // the next iteration's binning starts from zeroed counters (its kernels
+  // run after this one; this iteration's binning finished before it)
+  if (ts.sort_zero)
+    for (size_t i = threadIdx.x; i < ts.sort_zero_words; i += blockDim.x) ts.sort_zero[i] = 0u;
 }
 
 // Per-surfel reduction of the (tile, surfel) partials in emission order and

@@ -365,25 +365,6 @@ __device__ __forceinline__ void write_outputs(const unsigned long long* a, int l
   }
 }
 
-// Segments of at most kSegSmem keys: sorted in shared memory by 128 threads.
-__global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(
-    const float4* __restrict__ proj, int n, int tiles_x, const int32_t* __restrict__ ranges,
-    unsigned long long* __restrict__ seg_keys, const uint32_t* __restrict__ surfel_off,
-    uint32_t* __restrict__ vals, uint32_t* __restrict__ emit, unsigned long long* __restrict__ keys64,
-    long long capacity, const int32_t* __restrict__ gate) {
-  extern __shared__ unsigned long long s_keys[];
-  if (*gate) return;
-  const int t = blockIdx.x;
-  const int start = ranges[2 * t];
-  const int end = (int)min((long long)ranges[2 * t + 1], capacity);
-  const int len = end - start;
-  if (len <= 0 || len > kSegSmem) return;
-  for (int i = threadIdx.x; i < len; i += blockDim.x) s_keys[i] = seg_keys[start + i];
-  __syncthreads();
-  bitonic_sort(s_keys, len);
-  write_outputs(s_keys, len, start, t, tiles_x, n, proj, surfel_off, vals, emit, keys64);
-}
-
 // Position in the merge of sorted runs A[0, la) and B[0, lb) (unique keys):
 // the number i of elements taken from A among the first d outputs.
 __device__ __forceinline__ int co_rank(const unsigned long long* A, int la, const unsigned long long* B,
@@ -404,6 +385,7 @@ __device__ __forceinline__ int co_rank(const unsigned long long* A, int la, cons
 // global memory (seg_keys <-> seg_tmp), each thread producing a contiguous
 // span of the output located by a co-rank search.
 // One long segment (tile t) by the whole block.
+template <int kChunkKeys>
 __device__ void sort_long_segment(int t, const float4* __restrict__ proj, int n, int tiles_x,
                                   const int32_t* __restrict__ ranges,
                                   unsigned long long* __restrict__ seg_keys,
@@ -417,9 +399,9 @@ __device__ void sort_long_segment(int t, const float4* __restrict__ proj, int n,
   if (len <= kSegSmem) return;
   unsigned long long* src = seg_keys + start;
   unsigned long long* dst = seg_tmp + start;
-  const int chunks = (len + kLongChunk - 1) / kLongChunk;
+  const int chunks = (len + kChunkKeys - 1) / kChunkKeys;
   for (int c = 0; c < chunks; ++c) {
-    const int c0 = c * kLongChunk, cl = min(kLongChunk, len - c0);
+    const int c0 = c * kChunkKeys, cl = min(kChunkKeys, len - c0);
     for (int i = threadIdx.x; i < cl; i += blockDim.x) s_keys[i] = src[c0 + i];
     __syncthreads();
     bitonic_sort(s_keys, cl);
@@ -431,7 +413,7 @@ __device__ void sort_long_segment(int t, const float4* __restrict__ proj, int n,
     __syncthreads();
   }
   const int span = (len + blockDim.x - 1) / blockDim.x;
-  for (int w = kLongChunk; w < len; w <<= 1) {
+  for (int w = kChunkKeys; w < len; w <<= 1) {
     const int p0 = min(len, (int)threadIdx.x * span), p1 = min(len, p0 + span);
     int p = p0;
     while (p < p1) {
@@ -459,6 +441,35 @@ __device__ void sort_long_segment(int t, const float4* __restrict__ proj, int n,
   write_outputs(src, len, start, t, tiles_x, n, proj, surfel_off, vals, emit, keys64);
 }
 
+// Segments of at most kSegSmem keys: sorted in shared memory by 128 threads (and,
+// with long_here, longer ones too).
+__global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(
+    const float4* __restrict__ proj, int n, int tiles_x, const int32_t* __restrict__ ranges,
+    unsigned long long* __restrict__ seg_keys, unsigned long long* __restrict__ seg_tmp,
+    const uint32_t* __restrict__ surfel_off, uint32_t* __restrict__ vals,
+    uint32_t* __restrict__ emit, unsigned long long* __restrict__ keys64, long long capacity,
+    int long_here, const int32_t* __restrict__ gate) {
+  extern __shared__ unsigned long long s_keys[];
+  if (*gate) return;
+  const int t = blockIdx.x;
+  const int start = ranges[2 * t];
+  const int end = (int)min((long long)ranges[2 * t + 1], capacity);
+  const int len = end - start;
+  if (len <= 0) return;
+  if (len > kSegSmem) {
+    // a long segment in this block (2048-key chunks + merges) when no
+    // separate long-segment launch follows
+    if (long_here)
+      sort_long_segment<kSegSmem>(t, proj, n, tiles_x, ranges, seg_keys, seg_tmp, surfel_off, vals,
+                                  emit, keys64, capacity, s_keys);
+    return;
+  }
+  for (int i = threadIdx.x; i < len; i += blockDim.x) s_keys[i] = seg_keys[start + i];
+  __syncthreads();
+  bitonic_sort(s_keys, len);
+  write_outputs(s_keys, len, start, t, tiles_x, n, proj, surfel_off, vals, emit, keys64);
+}
+
 // Segments longer than kSegSmem, listed by the tile scan: a small persistent
 // grid takes them one per block.
 __global__ void __launch_bounds__(kLongThreads) tile_sort_long_kernel(
@@ -471,8 +482,8 @@ __global__ void __launch_bounds__(kLongThreads) tile_sort_long_kernel(
   if (*gate) return;
   const int cnt = (int)*n_long;
   for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
-    sort_long_segment((int)long_list[i], proj, n, tiles_x, ranges, seg_keys, seg_tmp, surfel_off,
-                      vals, emit, keys64, capacity, s_keys);
+    sort_long_segment<kLongChunk>((int)long_list[i], proj, n, tiles_x, ranges, seg_keys, seg_tmp,
+                                  surfel_off, vals, emit, keys64, capacity, s_keys);
     __syncthreads();
   }
 }
@@ -537,10 +548,17 @@ cudaError_t long_sort_smem_ready(size_t bytes) {
   return e;
 }
 
+void sort_zero_region(void* workspace, int n, size_t capacity, int n_tiles, uint32_t** begin,
+                      size_t* words) {
+  const SortWs w = carve_sort_ws(workspace, n, capacity, n_tiles);
+  *begin = w.zero_begin;
+  *words = w.zero_words;
+}
+
 int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
                     const gs2d_camera* cam, const gs2d_config* cfg, void* workspace,
                     size_t ws_bytes, size_t* ws_needed, const gs2d_bins* bins, bool need_emit,
-                    cudaStream_t st) {
+                    cudaStream_t st, unsigned flags) {
   if (!cam || !cfg || !bins || n < 0) return GS2D_ERR_INVALID_ARG;
   if (n > 0 && (!proj || !tiles_per_surfel)) return GS2D_ERR_INVALID_ARG;
   if (!bins->vals || !bins->tile_ranges || !bins->n_isect || !bins->status) return GS2D_ERR_INVALID_ARG;
@@ -560,8 +578,10 @@ int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
   const float4* p4 = reinterpret_cast<const float4*>(proj);
   const size_t hist_smem = n_tiles <= kSmemTiles ? (size_t)n_tiles * sizeof(uint32_t) : 0;
 
-  bin_init_kernel<<<32, 256, 0, st>>>(w.zero_begin, w.zero_words, bins->n_isect, gate);
-  GS2D_LAUNCH_CHECK();
+  if (!(flags & kSortPreZeroed)) {
+    bin_init_kernel<<<32, 256, 0, st>>>(w.zero_begin, w.zero_words, bins->n_isect, gate);
+    GS2D_LAUNCH_CHECK();
+  }
   if (n > 0) {
     const int blocks = min((n + kScanThreads - 1) / kScanThreads, 152 * 4);
     count_kernel<<<blocks, kScanThreads, hist_smem, st>>>(p4, tiles_per_surfel, n, tx, n_tiles,
@@ -581,20 +601,22 @@ int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
       p4, tiles_per_surfel, n, tx, n_tiles, bins->tile_ranges, w.cursor, w.seg_keys, cap, gate);
   GS2D_LAUNCH_CHECK();
   const size_t smem = (size_t)kSegSmem * sizeof(unsigned long long);
+  const bool long_here = (flags & kSortLongInBlock) != 0;
   tile_sort_kernel<<<n_tiles, kSortThreads, smem, st>>>(
-      p4, n, tx, bins->tile_ranges, w.seg_keys, need_emit ? bins->surfel_off : nullptr,
+      p4, n, tx, bins->tile_ranges, w.seg_keys, w.seg_tmp, need_emit ? bins->surfel_off : nullptr,
       bins->vals, need_emit ? bins->isect_emit : nullptr,
-      reinterpret_cast<unsigned long long*>(bins->keys), cap, gate);
+      reinterpret_cast<unsigned long long*>(bins->keys), cap, long_here ? 1 : 0, gate);
   GS2D_LAUNCH_CHECK();
-  // segments longer than kSegSmem (blocks of shorter ones return at once)
-  const size_t long_smem = (size_t)kLongChunk * sizeof(unsigned long long);
-  if (long_sort_smem_ready(long_smem) != cudaSuccess) return GS2D_ERR_CUDA;
-  tile_sort_long_kernel<<<min(n_tiles, 152), kLongThreads, long_smem, st>>>(
-      p4, n, tx, bins->tile_ranges, w.long_list, w.n_long, w.seg_keys, w.seg_tmp,
-      need_emit ? bins->surfel_off : nullptr,
-      bins->vals, need_emit ? bins->isect_emit : nullptr,
-      reinterpret_cast<unsigned long long*>(bins->keys), cap, gate);
-  GS2D_LAUNCH_CHECK();
+  if (!long_here) {
+    // segments longer than kSegSmem (blocks of shorter ones return at once)
+    const size_t long_smem = (size_t)kLongChunk * sizeof(unsigned long long);
+    if (long_sort_smem_ready(long_smem) != cudaSuccess) return GS2D_ERR_CUDA;
+    tile_sort_long_kernel<<<min(n_tiles, 152), kLongThreads, long_smem, st>>>(
+        p4, n, tx, bins->tile_ranges, w.long_list, w.n_long, w.seg_keys, w.seg_tmp,
+        need_emit ? bins->surfel_off : nullptr, bins->vals, need_emit ? bins->isect_emit : nullptr,
+        reinterpret_cast<unsigned long long*>(bins->keys), cap, gate);
+    GS2D_LAUNCH_CHECK();
+  }
   return GS2D_OK;
 }
 

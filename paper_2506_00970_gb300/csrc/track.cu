@@ -36,12 +36,14 @@ cudaError_t record_timing_event(cudaEvent_t ev, cudaStream_t st) {
       ev, st, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 
-__global__ void track_reset_kernel(float* adam, uint32_t* counter, int32_t* status) {
+__global__ void track_reset_kernel(float* adam, uint32_t* counter, int32_t* status,
+                                   uint32_t* sort_zero, size_t sort_zero_words) {
   if (threadIdx.x < 16) adam[threadIdx.x] = 0.f;
   if (threadIdx.x == 0) {
     *counter = 0u;
     *status = 0;
   }
+  for (size_t i = threadIdx.x; i < sort_zero_words; i += blockDim.x) sort_zero[i] = 0u;
 }
 
 struct TrackWs {
@@ -122,7 +124,13 @@ int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_co
   // byte 0..255: the status word (stable address for gs2d_track_status)
   int32_t* status = reinterpret_cast<int32_t*>(workspace);
   const TrackWs w = carve_track_ws(static_cast<char*>(workspace) + 256, s->n, capacity, cam, cfg);
-  track_reset_kernel<<<1, 32, 0, st>>>(w.adam, w.counter, status);
+  // binning counters: zeroed here for the first iteration and by the fused
+  // kernel's last block for every later one (no init launch per iteration)
+  uint32_t* zero_begin = nullptr;
+  size_t zero_words = 0;
+  sort_zero_region(w.sort_ws, s->n, capacity, gs2d_tiles_x(cam, cfg) * gs2d_tiles_y(cam, cfg),
+                   &zero_begin, &zero_words);
+  track_reset_kernel<<<1, 256, 0, st>>>(w.adam, w.counter, status, zero_begin, zero_words);
   GS2D_LAUNCH_CHECK();
   gs2d_bins bins;
   bins.keys = nullptr;
@@ -137,11 +145,11 @@ int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_co
     int r = project_launch(s, cam, pose, cfg, w.proj, w.tiles, status, st);
     if (r) return r;
     r = bin_sort_launch(w.proj, w.tiles, s->n, cam, cfg, w.sort_ws, w.sort_bytes, nullptr, &bins,
-                        false, st);
+                        false, st, kSortPreZeroed | kSortLongInBlock);
     if (r) return r;
     const bool timed = g_timer.used < g_timer.capacity;
     if (timed) GS2D_CUDA_TRY(record_timing_event(g_timer.start[g_timer.used], st));
-    TrackStep ts{pose, w.adam, loss_hist, pose_hist, it, w.counter};
+    TrackStep ts{pose, w.adam, loss_hist, pose_hist, it, w.counter, zero_begin, zero_words};
     r = track_tile_launch(w.proj, &bins, cam, cfg, obs_rgb, obs_depth, prm, w.loss_part,
                           w.pose_part, ts, status, st);
     if (r) return r;

@@ -203,3 +203,40 @@ def test_track_step_capacity_error_is_reported(torch_cuda):
     torch.cuda.synchronize()
     assert int(gs2d.gs2d_track_status(ws).item()) == 3
     assert torch.equal(pose_t, before)
+
+
+def test_track_step_on_dense_low_resolution_view(torch_cuda, orc):
+    """A 300k-surfel slab filling a 160x120 view: most tiles hold more than
+    2048 list entries, which the tracking step sorts inside the tile-sort
+    block.  Its first loss equals the standalone render + tracking loss (whose
+    binning sorts long segments in the separate long-segment launch), and the
+    loop lowers the loss."""
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d
+    s = scenes.slab_scene(3, 300_000)
+    cam = scenes.slab_camera()
+    gt = scenes.identity_pose()
+    ds = gs2d.DeviceSurfels(s)
+    r, _, _, img = gpu_render(s, cam, gt, capacity=8 * s.n)
+    counts = np.diff(r.ranges.cpu().numpy().reshape(-1, 2), axis=1).ravel()
+    assert (counts > 2048).mean() > 0.3
+    obs_rgb = torch.tensor(img["rgb"], device="cuda")
+    obs_d = torch.tensor(img["depth"] / np.maximum(img["opacity"], 1e-6), device="cuda")
+    start = scenes.perturb_pose(gt, 0.02, 1.0, seed=8)
+    r2, _, pt, _ = gpu_render(s, cam, start, capacity=8 * s.n)
+    f = dict(dtype=torch.float32, device="cuda")
+    g = [torch.empty(120, 160, 3, **f), torch.empty(120, 160, **f), torch.empty(120, 160, **f)]
+    loss = torch.empty(1, **f)
+    lws = torch.empty(1 << 16, dtype=torch.uint8, device="cuda")
+    ccam, cfg, prm = gs2d.camera(cam), gs2d.default_config(), gs2d.default_track_params()
+    gs2d.gs2d_tracking_loss(r2.rgb, r2.depth, r2.normal, r2.opacity, obs_rgb, obs_d, ccam, prm,
+                            *g, loss, lws)
+    cap = 8 * s.n
+    ws = torch.empty(gs2d.gs2d_track_workspace(s.n, cap, ccam, cfg), dtype=torch.uint8, device="cuda")
+    lh = torch.zeros(5, device="cuda")
+    pose = pt.clone()
+    gs2d.gs2d_track_step(ds, ccam, cfg, prm, pose, obs_rgb, obs_d, 5, cap, lh, None, ws)
+    torch.cuda.synchronize()
+    assert int(gs2d.gs2d_track_status(ws).item()) in (0, gs2d.CONVERGED)
+    assert float(lh[0].item()) == pytest.approx(float(loss.item()), rel=1e-4)
+    assert float(lh[-1].item()) < float(lh[0].item())
