@@ -234,7 +234,7 @@ def run_ours(args):
     def track():
         gs2d.gs2d_track_step(ds, ccam, cfg, prm, pose, obs_rgb, obs_d, N_ITER, cap, lh, ph, ws)
 
-    # one direct call, then capture a whole frame (reset + 100 x 6 kernels)
+    # one direct call, then capture a whole frame (reset + 100 x 4 kernels)
     # into a CUDA graph; the fused tile kernel's launches are bracketed by
     # event-record nodes inside the graph
     load(0)
@@ -372,7 +372,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "surfels": N_SURFELS, "width": cam.width,
                        "height": cam.height, "iterations_per_step": N_ITER, "frames": n_frames,
                        "tile": "16x16", "l2": "256 MB buffer written between steps",
-                       "launch": "one CUDA graph per frame (reset + 100 x 6 kernels)",
+                       "launch": "one CUDA graph per frame (reset + 100 x 4 kernels)",
                        "parallelism": f"replicas x{ws_n}"},
             "tracking": tracking,
             "clocks": clocks,
@@ -391,12 +391,12 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-# kernels per tracking iteration: project 1; bin_sort 4 (tile counts, tile
-# scan, scatter, tile sort -- the counters are zeroed by the previous
-# iteration's fused kernel, long tile segments are sorted in-block); fused
-# render + loss + pose backward with the reduction + AdamW + retraction in
-# its last block 1.  Plus one reset per frame.
-LAUNCHES_PER_ITER = 6
+# kernels per tracking iteration: projection with the tile counts and (in
+# its last block) the tile scan 1; scatter 1; per-tile sort 1 (long
+# segments in-block; the counters are zeroed by the previous iteration's
+# fused kernel); fused render + loss + pose backward with the reduction +
+# AdamW + retraction in its last block 1.  Plus one reset per frame.
+LAUNCHES_PER_ITER = 4
 
 
 def roofline(r, ds, frames, cam, cfg, stream, ms_iter, fused_ms):

@@ -10,9 +10,25 @@
 
 namespace gs2d {
 
+// Binning state a fused projection fills: tile counts (shared-memory
+// histograms flushed with global atomics), then, by its last block, the tile
+// ranges, K, the capacity check and the long-tile list.
+struct SortFuse {
+  uint32_t* tile_count;
+  int32_t* ranges;
+  int32_t* n_isect;
+  long long capacity;
+  uint32_t* long_list;
+  uint32_t* n_long;
+  uint32_t* done;   // block completion counter (zeroed before the launch)
+  int tiles_x, n_tiles, long_len;
+};
+
+// Per-surfel projection; with fuse, also the binning's tile counts and scan
+// (the binning then runs with kSortPreScanned).
 int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* pose,
                    const gs2d_config* cfg, float* proj_out, int32_t* tiles_per_surfel_out,
-                   const int32_t* gate, cudaStream_t st);
+                   const int32_t* gate, cudaStream_t st, const SortFuse* fuse = nullptr);
 
 // gs2d_bin_sort; with need_emit false the emission offsets and indices
 // (used only by the full backward) are not computed.  flags:
@@ -20,11 +36,15 @@ int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* p
 // (sort_zero_region) since the last binning, so no init launch;
 // kSortLongInBlock -- tiles with segments over 2048 keys are sorted by their
 // own 128-thread block (chunks + merges) instead of a separate launch.
-constexpr unsigned kSortPreZeroed = 1u, kSortLongInBlock = 2u;
+// kSortPreScanned -- a fused projection already counted and scanned the
+// tiles (implies pre-zeroed counters; no emission offsets).
+constexpr unsigned kSortPreZeroed = 1u, kSortLongInBlock = 2u, kSortPreScanned = 4u;
 int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
                     const gs2d_camera* cam, const gs2d_config* cfg, void* workspace,
                     size_t ws_bytes, size_t* ws_needed, const gs2d_bins* bins, bool need_emit,
                     cudaStream_t st, unsigned flags = 0u);
+// Pointers of a sort workspace for a fused projection.
+SortFuse sort_fuse_args(void* workspace, int n, const gs2d_bins* bins, int tiles_x, int n_tiles);
 // The counter region of a sort workspace that every binning needs zeroed.
 void sort_zero_region(void* workspace, int n, size_t capacity, int n_tiles, uint32_t** begin,
                       size_t* words);

@@ -27,6 +27,7 @@
 #include <math.h>
 
 #include "gs2d_common.cuh"
+#include "tile_scan.cuh"
 #include "gs2d_internal.h"
 
 namespace gs2d {
@@ -196,27 +197,73 @@ __device__ __forceinline__ void project_one(int i, const float* __restrict__ mu,
                      __uint_as_float(b23));
 }
 
+template <bool kFuse>
 __global__ void __launch_bounds__(256) project_kernel(
     const float* __restrict__ mu, const float* __restrict__ quat, const float* __restrict__ scale,
     const float* __restrict__ opacity, const float* __restrict__ rgb, int n,
     const float* __restrict__ pose, gs2d_camera cam, gs2d_config cfg, int tiles_x, int tiles_y,
-    float4* __restrict__ proj, int32_t* __restrict__ tiles_out, const int32_t* __restrict__ gate) {
+    float4* __restrict__ proj, int32_t* __restrict__ tiles_out, const int32_t* __restrict__ gate,
+    SortFuse fz, int32_t* __restrict__ status) {
   // records are assembled in shared memory (9 float4 per thread: padded so
   // both the per-thread writes and the block's coalesced copy-out are free
   // of bank conflicts) and written as one contiguous 32 KB run per block
   __shared__ float4 s_out[256 * 9];
   __shared__ float sp[12];
+  __shared__ uint32_t s_w[32];
+  __shared__ uint32_t s_carry;
+  __shared__ bool s_last;
   if (gate && *gate) return;
   if (threadIdx.x < 12) sp[threadIdx.x] = pose[threadIdx.x];
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) project_one(i, mu, quat, scale, opacity, rgb, sp, cam, cfg, s_out + threadIdx.x * 9,
-                         tiles_out + i);
+  uint32_t r01 = 1u, r23 = 0u;  // an empty rectangle
+  if (i < n) {
+    project_one(i, mu, quat, scale, opacity, rgb, sp, cam, cfg, s_out + threadIdx.x * 9,
+                tiles_out + i);
+    if (kFuse) {
+      const float4 rc = s_out[threadIdx.x * 9 + 7];
+      r01 = __float_as_uint(rc.x);
+      r23 = __float_as_uint(rc.y);
+    }
+  }
   __syncthreads();
   const int base = blockIdx.x * blockDim.x;
   const int valid = min((int)blockDim.x, n - base);
   float4* dst = proj + (size_t)base * (kProjFloats / 4);
   for (int v = threadIdx.x; v < valid * 8; v += blockDim.x) dst[v] = s_out[(v >> 3) * 9 + (v & 7)];
+  if (!kFuse) return;
+  // tile counts: the staging buffer becomes the block's histogram (when the
+  // tile grid fits), flushed with one global atomic per touched tile
+  __syncthreads();
+  uint32_t* hist = reinterpret_cast<uint32_t*>(s_out);
+  const bool local = fz.n_tiles <= 256 * 9 * 4;
+  if (local)
+    for (int t = threadIdx.x; t < fz.n_tiles; t += blockDim.x) hist[t] = 0u;
+  __syncthreads();
+  {
+    const int tx0 = (int)(r01 & 0xFFFF), ty0 = (int)(r01 >> 16);
+    const int tx1 = (int)(r23 & 0xFFFF), ty1 = (int)(r23 >> 16);
+    if (tx0 <= tx1 && ty0 <= ty1) {
+      const int rw = tx1 - tx0 + 1, k = rw * (ty1 - ty0 + 1);
+      for (int j = 0; j < k; ++j) {
+        const int t = min((ty0 + j / rw) * fz.tiles_x + tx0 + j % rw, fz.n_tiles - 1);
+        atomicAdd(local ? hist + t : fz.tile_count + t, 1u);
+      }
+    }
+  }
+  __syncthreads();
+  if (local)
+    for (int t = threadIdx.x; t < fz.n_tiles; t += blockDim.x)
+      if (hist[t]) atomicAdd(fz.tile_count + t, hist[t]);
+  // the last block to finish turns the counts into tile ranges
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(fz.done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  tile_scan_block(fz.tile_count, fz.n_tiles, fz.ranges, fz.n_isect, fz.capacity, fz.long_list,
+                  fz.n_long, fz.long_len, status, s_w, &s_carry);
 }
 
 // All views of a batch in one launch (blockIdx.y = view): record j of a view
@@ -259,7 +306,7 @@ __global__ void __launch_bounds__(256) project_batch_kernel(
 
 int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* pose,
                    const gs2d_config* cfg, float* proj_out, int32_t* tiles_per_surfel_out,
-                   const int32_t* gate, cudaStream_t st) {
+                   const int32_t* gate, cudaStream_t st, const SortFuse* fuse) {
   if (!s || !cam || !pose || !cfg || !proj_out || !tiles_per_surfel_out) return GS2D_ERR_INVALID_ARG;
   if (s->n < 0 || (s->n > 0 && (!s->mu || !s->quat || !s->scale || !s->opacity || !s->rgb)))
     return GS2D_ERR_INVALID_ARG;
@@ -269,13 +316,21 @@ int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* p
     return GS2D_ERR_INVALID_ARG;
   const int tx = tiles_along(cam->width, cfg->tile_w), ty = tiles_along(cam->height, cfg->tile_h);
   if (tx > 65535 || ty > 65535) return GS2D_ERR_INVALID_ARG;
-  if (s->n == 0) return GS2D_OK;
   const int threads = 256;
-  const int blocks = (s->n + threads - 1) / threads;
-  project_kernel<<<blocks, threads, 0, st>>>(s->mu, s->quat, s->scale, s->opacity, s->rgb, s->n,
-                                             pose, *cam, *cfg, tx, ty,
-                                             reinterpret_cast<float4*>(proj_out),
-                                             tiles_per_surfel_out, gate);
+  if (fuse) {
+    // with no surfel one block still runs the (empty) scan
+    const int blocks = max((s->n + threads - 1) / threads, 1);
+    project_kernel<true><<<blocks, threads, 0, st>>>(
+        s->mu, s->quat, s->scale, s->opacity, s->rgb, s->n, pose, *cam, *cfg, tx, ty,
+        reinterpret_cast<float4*>(proj_out), tiles_per_surfel_out, gate, *fuse,
+        const_cast<int32_t*>(gate));
+  } else {
+    if (s->n == 0) return GS2D_OK;
+    const int blocks = (s->n + threads - 1) / threads;
+    project_kernel<false><<<blocks, threads, 0, st>>>(
+        s->mu, s->quat, s->scale, s->opacity, s->rgb, s->n, pose, *cam, *cfg, tx, ty,
+        reinterpret_cast<float4*>(proj_out), tiles_per_surfel_out, gate, SortFuse{}, nullptr);
+  }
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
 }

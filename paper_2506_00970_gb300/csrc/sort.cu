@@ -29,6 +29,7 @@
 
 #include "gs2d_common.cuh"
 #include "gs2d_internal.h"
+#include "tile_scan.cuh"
 
 namespace gs2d {
 
@@ -224,47 +225,8 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
   __shared__ uint32_t s_w[32];
   __shared__ uint32_t s_carry;
   if (*gate) return;
-  if (threadIdx.x == 0) s_carry = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int base = 0; base < n_tiles; base += 1024) {
-    const int t = base + (int)threadIdx.x;
-    const uint32_t c = t < n_tiles ? tile_count[t] : 0u;
-    uint32_t inc = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += v;
-    }
-    if (lane == 31) s_w[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-      const uint32_t x = s_w[lane];
-      uint32_t xi = x;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, xi, o);
-        if (lane >= o) xi += v;
-      }
-      s_w[lane] = xi - x;
-    }
-    __syncthreads();
-    const uint32_t start = s_carry + s_w[w] + inc - c;
-    if (t < n_tiles) {
-      ranges[2 * t] = (int32_t)start;
-      ranges[2 * t + 1] = (int32_t)(start + c);
-      if (c > (uint32_t)kSegSmem) long_list[atomicAdd(n_long, 1u)] = (uint32_t)t;
-    }
-    __syncthreads();
-    if (threadIdx.x == 1023) s_carry = start + c;
-    __syncthreads();
-  }
-  // K and the capacity check (ranges beyond the capacity are never read)
-  if (threadIdx.x == 0) {
-    const unsigned long long K = s_carry;
-    *n_isect = (int32_t)min(K, (unsigned long long)0x7FFFFFFF);
-    if (K > (unsigned long long)capacity) atomicExch(gate, (int32_t)GS2D_ERR_CAPACITY);
-  }
+  tile_scan_block(tile_count, n_tiles, ranges, n_isect, capacity, long_list, n_long, kSegSmem, gate,
+                  s_w, &s_carry);
 }
 
 // 3. Scatter of the (depth bits << 32 | id) keys into the tile segments.
@@ -495,6 +457,7 @@ struct SortWs {
   unsigned long long* seg_tmp;   // [cap] merge buffer of long segments
   uint32_t* long_list;           // [n_tiles] tiles with segments over kSegSmem
   uint32_t* n_long;              // [1] (zeroed per call)
+  uint32_t* proj_done;           // [1] blocks of a fused projection finished (zeroed per call)
   uint32_t* zero_begin;          // start of the zeroed region
   uint32_t* tile_count;          // [n_tiles]
   uint32_t* cursor;              // [n_tiles]
@@ -526,6 +489,7 @@ SortWs carve_sort_ws(void* base, int n, size_t cap, int n_tiles) {
   w.cursor = zt((size_t)n_tiles);
   w.ticket = zt(8);
   w.n_long = zt(1);
+  w.proj_done = zt(1);
   w.estatus = reinterpret_cast<unsigned long long*>(zt((size_t)2 * w.chunks_n + 2));
   w.zero_words = words;
   w.bytes = align_up(zstart + words * sizeof(uint32_t), 256);
@@ -546,6 +510,22 @@ cudaError_t long_sort_smem_ready(size_t bytes) {
                            (int)bytes);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
   return e;
+}
+
+SortFuse sort_fuse_args(void* workspace, int n, const gs2d_bins* bins, int tiles_x, int n_tiles) {
+  const SortWs w = carve_sort_ws(workspace, n, bins->capacity, n_tiles);
+  SortFuse f;
+  f.tile_count = w.tile_count;
+  f.ranges = bins->tile_ranges;
+  f.n_isect = bins->n_isect;
+  f.capacity = (long long)bins->capacity;
+  f.long_list = w.long_list;
+  f.n_long = w.n_long;
+  f.done = w.proj_done;
+  f.tiles_x = tiles_x;
+  f.n_tiles = n_tiles;
+  f.long_len = kSegSmem;
+  return f;
 }
 
 void sort_zero_region(void* workspace, int n, size_t capacity, int n_tiles, uint32_t** begin,
@@ -582,7 +562,8 @@ int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
     bin_init_kernel<<<32, 256, 0, st>>>(w.zero_begin, w.zero_words, bins->n_isect, gate);
     GS2D_LAUNCH_CHECK();
   }
-  if (n > 0) {
+  const bool scanned = (flags & kSortPreScanned) != 0;
+  if (n > 0 && !scanned) {
     const int blocks = min((n + kScanThreads - 1) / kScanThreads, 152 * 4);
     count_kernel<<<blocks, kScanThreads, hist_smem, st>>>(p4, tiles_per_surfel, n, tx, n_tiles,
                                                           w.tile_count, gate);
@@ -593,9 +574,11 @@ int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
       GS2D_LAUNCH_CHECK();
     }
   }
-  tile_scan_kernel<<<1, 1024, 0, st>>>(w.tile_count, n_tiles, bins->tile_ranges, bins->n_isect, cap,
-                                       w.long_list, w.n_long, gate);
-  GS2D_LAUNCH_CHECK();
+  if (!scanned) {
+    tile_scan_kernel<<<1, 1024, 0, st>>>(w.tile_count, n_tiles, bins->tile_ranges, bins->n_isect,
+                                         cap, w.long_list, w.n_long, gate);
+    GS2D_LAUNCH_CHECK();
+  }
   if (n == 0) return GS2D_OK;
   scatter_kernel<<<(n + 255) / 256, 256, 2 * hist_smem, st>>>(
       p4, tiles_per_surfel, n, tx, n_tiles, bins->tile_ranges, w.cursor, w.seg_keys, cap, gate);

@@ -141,11 +141,16 @@ int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_co
   bins.n_isect = w.n_isect;
   bins.status = status;
   bins.capacity = capacity;
+  // projection, tile counts and tile scan in one launch; the binning keeps
+  // the scatter and the per-tile sort
+  const int tiles_x = gs2d_tiles_x(cam, cfg);
+  const SortFuse fuse = sort_fuse_args(w.sort_ws, s->n, &bins, tiles_x,
+                                       tiles_x * gs2d_tiles_y(cam, cfg));
   for (int it = 0; it < n_iter; ++it) {
-    int r = project_launch(s, cam, pose, cfg, w.proj, w.tiles, status, st);
+    int r = project_launch(s, cam, pose, cfg, w.proj, w.tiles, status, st, &fuse);
     if (r) return r;
     r = bin_sort_launch(w.proj, w.tiles, s->n, cam, cfg, w.sort_ws, w.sort_bytes, nullptr, &bins,
-                        false, st, kSortPreZeroed | kSortLongInBlock);
+                        false, st, kSortPreZeroed | kSortLongInBlock | kSortPreScanned);
     if (r) return r;
     const bool timed = g_timer.used < g_timer.capacity;
     if (timed) GS2D_CUDA_TRY(record_timing_event(g_timer.start[g_timer.used], st));
