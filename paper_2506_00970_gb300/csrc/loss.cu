@@ -127,6 +127,20 @@ __device__ bool ln_eval(const MapCtx& c, int px, int py, float& Ln, F3 g[4], F3&
   return true;
 }
 
+// Tiles of 32 x 8 pixels; a block strides over tiles in a fixed order.
+// Phase 1 evaluates the normal term once for every position of the tile and
+// its one-pixel edge ring (the four neighbours' stencils read it) into
+// shared memory; phase 2 forms each pixel's outputs, gathering the
+// neighbours' gradients w.r.t. its back-projected point from there.
+constexpr int kMapTW = 32, kMapTH = 8;
+constexpr int kMapRW = kMapTW + 2, kMapRH = kMapTH + 2;  // with the ring
+struct MapSmem {
+  float g[kMapRH][kMapRW][12];  // dL_n / dX of the four stencil points
+  float ln[kMapTH][kMapTW];     // L_n of the tile's own pixels
+  float gn[kMapTH][kMapTW][3];  // dL_n / dN_r of the tile's own pixels
+  bool ok[kMapRH][kMapRW];
+};
+
 __global__ void __launch_bounds__(kLossThreads) mapping_loss_kernel(
     const float* __restrict__ rgb, const float* __restrict__ depth, const float* __restrict__ normal,
     const float* __restrict__ opac, const float* __restrict__ obs_rgb,
@@ -134,51 +148,83 @@ __global__ void __launch_bounds__(kLossThreads) mapping_loss_kernel(
     float* __restrict__ g_rgb, float* __restrict__ g_depth, float* __restrict__ g_normal,
     float* __restrict__ g_opac, float* __restrict__ part) {
   __shared__ float s[kLossThreads / 32];
+  __shared__ MapSmem sm;
   const int W = cam.width, H = cam.height, P = W * H;
   const float inv = 1.f / (float)P;
   const MapCtx c{depth, opac, normal, cam};
+  const int tiles_x = (W + kMapTW - 1) / kMapTW, tiles_y = (H + kMapTH - 1) / kMapTH;
   float acc = 0.f;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
-    const int px = i % W, py = i / W;
-    const float O = opac[i];
-    const float Oc = fmaxf(O, 1e-6f);
-    const float D = depth[i];
-    const float Dh = D / Oc;
-    const float d0 = rgb[3 * i] - obs_rgb[3 * i];
-    const float d1 = rgb[3 * i + 1] - obs_rgb[3 * i + 1];
-    const float d2 = rgb[3 * i + 2] - obs_rgb[3 * i + 2];
-    const float dd = Dh - obs_depth[i];
-    acc += fabsf(d0) + fabsf(d1) + fabsf(d2) + w_d * fabsf(dd);
-    g_rgb[3 * i] = sgnf(d0) * inv;
-    g_rgb[3 * i + 1] = sgnf(d1) * inv;
-    g_rgb[3 * i + 2] = sgnf(d2) * inv;
-    float gDh = w_d * sgnf(dd) * inv;
-    // own normal term
-    float Ln;
-    F3 g4[4], gNr = f3(0.f, 0.f, 0.f);
-    if (ln_eval(c, px, py, Ln, g4, gNr)) {
-      acc += w_n * Ln;
-      gNr = (w_n * inv) * gNr;
-    } else {
-      gNr = f3(0.f, 0.f, 0.f);
-    }
-    g_normal[3 * i] = gNr.x;
-    g_normal[3 * i + 1] = gNr.y;
-    g_normal[3 * i + 2] = gNr.z;
-    // stencils of the four neighbours that read X(q): p = q-ex uses X(p+ex),
-    // p = q+ex uses X(p-ex), p = q-ey uses X(p+ey), p = q+ey uses X(p-ey)
-    const F3 rq = ray_of(cam, px, py);
-    const int nb[4][3] = {{px - 1, py, 0}, {px + 1, py, 1}, {px, py - 1, 2}, {px, py + 1, 3}};
-    F3 gX = f3(0.f, 0.f, 0.f);
+  for (int tile = blockIdx.x; tile < tiles_x * tiles_y; tile += gridDim.x) {
+    const int x0 = (tile % tiles_x) * kMapTW, y0 = (tile / tiles_x) * kMapTH;
+    __syncthreads();
+    // phase 1: the normal term on the tile and its ring
+    for (int e = threadIdx.x; e < kMapRW * kMapRH; e += blockDim.x) {
+      const int ry = e / kMapRW, rx = e % kMapRW;
+      const int px = x0 + rx - 1, py = y0 + ry - 1;
+      const bool tile_px = rx >= 1 && rx <= kMapTW && ry >= 1 && ry <= kMapTH;
+      const bool ring = !tile_px && !((rx == 0 || rx == kMapRW - 1) && (ry == 0 || ry == kMapRH - 1));
+      float Ln = 0.f;
+      F3 g4[4], gNr = f3(0.f, 0.f, 0.f);
+      bool ok = false;
+      if ((tile_px || ring) && px >= 0 && py >= 0 && px < W && py < H)
+        ok = ln_eval(c, px, py, Ln, g4, gNr);
+      sm.ok[ry][rx] = ok;
+      if (ok)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      float l;
-      F3 gg[4], gn;
-      if (ln_eval(c, nb[k][0], nb[k][1], l, gg, gn)) gX = gX + gg[nb[k][2]];
+        for (int k = 0; k < 4; ++k) {
+          sm.g[ry][rx][3 * k] = g4[k].x;
+          sm.g[ry][rx][3 * k + 1] = g4[k].y;
+          sm.g[ry][rx][3 * k + 2] = g4[k].z;
+        }
+      if (tile_px) {
+        sm.ln[ry - 1][rx - 1] = ok ? Ln : 0.f;
+        sm.gn[ry - 1][rx - 1][0] = ok ? gNr.x : 0.f;
+        sm.gn[ry - 1][rx - 1][1] = ok ? gNr.y : 0.f;
+        sm.gn[ry - 1][rx - 1][2] = ok ? gNr.z : 0.f;
+      }
     }
-    gDh += w_n * inv * dot3(gX, rq);
-    g_depth[i] = gDh / Oc;
-    g_opac[i] = O > 1e-6f ? -gDh * D / (O * O) : 0.f;
+    __syncthreads();
+    // phase 2: one pixel per thread
+    const int lx = threadIdx.x % kMapTW, ly = threadIdx.x / kMapTW;
+    const int px = x0 + lx, py = y0 + ly;
+    if (px < W && py < H) {
+      const int i = py * W + px;
+      const float O = opac[i];
+      const float Oc = fmaxf(O, 1e-6f);
+      const float D = depth[i];
+      const float Dh = D / Oc;
+      const float d0 = rgb[3 * i] - obs_rgb[3 * i];
+      const float d1 = rgb[3 * i + 1] - obs_rgb[3 * i + 1];
+      const float d2 = rgb[3 * i + 2] - obs_rgb[3 * i + 2];
+      const float dd = Dh - obs_depth[i];
+      acc += fabsf(d0) + fabsf(d1) + fabsf(d2) + w_d * fabsf(dd);
+      g_rgb[3 * i] = sgnf(d0) * inv;
+      g_rgb[3 * i + 1] = sgnf(d1) * inv;
+      g_rgb[3 * i + 2] = sgnf(d2) * inv;
+      float gDh = w_d * sgnf(dd) * inv;
+      // own normal term
+      const int ry = ly + 1, rx = lx + 1;
+      if (sm.ok[ry][rx]) acc += w_n * sm.ln[ly][lx];
+      const float sn = w_n * inv;
+      g_normal[3 * i] = sn * sm.gn[ly][lx][0];
+      g_normal[3 * i + 1] = sn * sm.gn[ly][lx][1];
+      g_normal[3 * i + 2] = sn * sm.gn[ly][lx][2];
+      // stencils of the four neighbours that read X(q): p = q-ex uses X(p+ex)
+      // (slot 0), p = q+ex uses X(p-ex) (1), p = q-ey uses X(p+ey) (2),
+      // p = q+ey uses X(p-ey) (3)
+      const F3 rq = ray_of(cam, px, py);
+      const int nb[4][3] = {{rx - 1, ry, 0}, {rx + 1, ry, 1}, {rx, ry - 1, 2}, {rx, ry + 1, 3}};
+      F3 gX = f3(0.f, 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int qx = nb[k][0], qy = nb[k][1], sl = nb[k][2];
+        if (sm.ok[qy][qx])
+          gX = gX + f3(sm.g[qy][qx][3 * sl], sm.g[qy][qx][3 * sl + 1], sm.g[qy][qx][3 * sl + 2]);
+      }
+      gDh += w_n * inv * dot3(gX, rq);
+      g_depth[i] = gDh / Oc;
+      g_opac[i] = O > 1e-6f ? -gDh * D / (O * O) : 0.f;
+    }
   }
   const float t = block_sum256(acc, s);
   if (threadIdx.x == 0) part[blockIdx.x] = t * inv;
