@@ -51,7 +51,7 @@ MAP_SURFELS, MAP_VIEWS = 1_000_000, 8
 UNEVEN_SURFELS, UNEVEN_VIEWS = 2_000_000, 32
 MAP_W_D, MAP_W_N = 0.5, 0.02
 # learned proposal: training pairs, AdamW steps at batch 256, held-out frames
-PROP_PAIRS, PROP_STEPS, PROP_EVAL_FRAMES = 100_000, 3000, 256
+PROP_PAIRS, PROP_STEPS, PROP_EVAL_FRAMES = 100_000, 6000, 256
 
 
 def _args():
