@@ -64,14 +64,8 @@ def _args():
 
 
 def _dist():
-    import torch
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    return ws, rank, local
+    from paper_2506_00970_gb300 import replicas
+    return replicas.init("nccl")
 
 
 # --------------------------------------------------------------------------
@@ -136,7 +130,7 @@ def make_frames(n_frames: int, rank: int):
     """Seeded frames: ground-truth pose, start pose (2 cm / 1 deg off) and the
     observed RGB-D frame rendered on the GPU at ground truth (+1 mm noise)."""
     import torch
-    from paper_2506_00970_gb300 import gs2d, scenes
+    from paper_2506_00970_gb300 import gs2d, replicas, scenes
     s = scenes.room_scene(0, N_SURFELS)
     cam = scenes.tracking_camera()
     ds = gs2d.DeviceSurfels(s)
@@ -144,7 +138,7 @@ def make_frames(n_frames: int, rank: int):
     frames = []
     kmax = 0
     for f in range(n_frames):
-        seed = 1000 * rank + f
+        seed = replicas.seed_base(rank) + f
         gt = scenes.room_pose(100 + seed)
         start = scenes.perturb_pose(gt, 0.02, 1.0, seed=5000 + seed)
         out = r.forward(ds, gs2d.pose_tensor(gt))
@@ -205,6 +199,7 @@ FLOPS_LOSS_PIXEL = 20   # masks, three colour and one depth difference, signs
 
 def run_ours(args):
     import torch
+    from paper_2506_00970_gb300 import replicas
     from paper_2506_00970_gb300 import build as _b
     _b.build()
     from paper_2506_00970_gb300 import gs2d, scenes
@@ -265,8 +260,7 @@ def run_ours(args):
     e0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     e1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     hist, fused = [], []
-    if ws_n > 1:
-        torch.distributed.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
     with ClockSampler(local) as clk:
@@ -280,20 +274,16 @@ def run_ours(args):
             fused.extend(a.elapsed_time(b) for a, b in zip(k0, k1))
             hist.append(ph.clone())
         torch.cuda.synchronize()
-    if ws_n > 1:
-        torch.distributed.barrier()
+    replicas.barrier()
     wall = time.perf_counter() - t_wall
     fused_ms = float(np.mean(fused))
     st = int(gs2d.gs2d_track_status(ws).item())
     if st not in (0, gs2d.CONVERGED):
         raise RuntimeError(f"track status {st}")
     step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
-    tot_ms = torch.tensor([sum(step_ms)], device="cuda", dtype=torch.float64)
-    if ws_n > 1:
-        torch.distributed.all_reduce(tot_ms, op=torch.distributed.ReduceOp.MAX)
-    tot_ms = float(tot_ms.item())
+    tot_ms = replicas.max_over_ranks(sum(step_ms), device="cuda")
     P = cam.width * cam.height
-    value = ws_n * K * N_ITER * P / (tot_ms / 1e3) / 1e6
+    value = replicas.weak_scaling_value(ws_n, K * N_ITER * P, tot_ms) / 1e6
     ms_step = tot_ms / K
 
     # tracking accuracy and time to 1 cm / 0.5 deg
@@ -349,11 +339,8 @@ def run_ours(args):
         ee1.record(stream)
         ee1.synchronize()
         e2e_ms += ee0.elapsed_time(ee1)
-    e2e_t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-    if ws_n > 1:
-        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
-    e2e_ms = float(e2e_t.item())
-    e2e_value = ws_n * K * N_ITER * P / (e2e_ms / 1e3) / 1e6
+    e2e_ms = replicas.max_over_ranks(e2e_ms, device="cuda")
+    e2e_value = replicas.weak_scaling_value(ws_n, K * N_ITER * P, e2e_ms) / 1e6
     h2d = h_rgb[0].numel() * 4 + h_d[0].numel() * 4 + 12 * 4
     d2h = 12 * 4 + 4
 
@@ -387,8 +374,7 @@ def run_ours(args):
         }
         line["cpu_baseline"] = cpu_baseline(s, cam, frames[0])
         print(json.dumps(line))
-    if ws_n > 1:
-        torch.distributed.destroy_process_group()
+    replicas.finish()
 
 
 # kernels per tracking iteration: projection with the tile counts and (in
