@@ -216,6 +216,33 @@ int gs2d_render_bwd(const float* proj, const gs2d_bins* bins, const int32_t* til
                     float* d_opac, float* d_rgb_out, float* d_pose6, void* workspace,
                     size_t ws_bytes, size_t* ws_needed, gs2d_stream stream);
 
+/* Per-surfel contribution of a view (Sec. III-D, Eq. weight and Eq.
+ * contribution): contrib[i] = sum over all pixels p of w_i(p) = a_i(p) T_i(p),
+ * the blending weight record i receives in gs2d_render_fwd's compositing
+ * (same clamp, skip and stop rules; records culled or never reached get 0).
+ * Summed per (tile, surfel) pair and then per surfel in emission order:
+ * deterministic.  A surfel is visible from the view when contrib > 0.5.
+ * Inputs as gs2d_render_fwd plus tiles_per_surfel [n] and the emission
+ * arrays of bins (as gs2d_bin_sort fills them); contrib: device [n] FP32.
+ * Workspace: gs2d_render_contrib_workspace(bins->capacity) bytes. */
+size_t gs2d_render_contrib_workspace(size_t capacity);
+int gs2d_render_contrib(const float* proj, const gs2d_bins* bins, const int32_t* tiles_per_surfel,
+                        int n, const gs2d_camera* cam, const gs2d_config* cfg, float* contrib,
+                        void* workspace, size_t ws_bytes, size_t* ws_needed, gs2d_stream stream);
+
+/* Covisibility of two views A and B (Sec. III-D): with the visible sets
+ * G_X = {i : contrib_X[i] > vis_threshold} (0.5 in the paper),
+ * counts[0] = |G_A n G_B|, counts[1] = |G_A u G_B| (device uint32 [2]),
+ * score = counts[0] / counts[1] (0 when both are empty; device [1], may be
+ * NULL) and the keyframe rule is_keyframe = score < c_k or
+ * |t_A - t_B| > d_k, t the translation of each world-to-camera pose
+ * (device [12] each; c_k = 0.9 and d_k = 0.15 m in Table I; device int32
+ * [1], may be NULL, then the poses may be NULL).  contrib_a / contrib_b:
+ * device [n], both indexed by the same surfel ids. */
+int gs2d_covisibility(const float* contrib_a, const float* contrib_b, int n, float vis_threshold,
+                      const float* pose_a, const float* pose_b, float c_k, float d_k,
+                      uint32_t* counts, float* score, int32_t* is_keyframe, gs2d_stream stream);
+
 /* ------------------------------------------------------------------------
  * Batches of views (the mapping window of Sec. III-E renders several
  * keyframes per iteration, each over the active map M_A of Sec. III-C; the

@@ -11,6 +11,10 @@ Contents (each cites the passage it follows):
     hand-written reverse mode (C++, ``gs2d_oracle.cpp``): Sec. III-A
     (Eq. Puv, hc, homo, wth, alpha_blending) and Sec. III-B
     (Eq. derivatives, the manifold derivative and its Jacobians).
+  * ``contrib``                  -- per-surfel contribution, the sum of its
+    blending weights over the image (Sec. III-D, Eq. weight, contribution);
+    ``visible`` / ``covisibility`` / ``keyframe_rule`` -- the visibility
+    threshold, the covisibility score and the keyframe rule of Sec. III-D.
   * ``tile_rects`` / ``bin_sort`` -- FP64 tile footprint and a stable library
     sort of (tile, depth) keys ("sorts them by depth", Sec. III-A).
   * ``se3_exp`` / ``se3_log``     -- SE(3) exponential / logarithm used by the
@@ -55,6 +59,7 @@ def _lib():
         lib.orc_render_bwd.restype = ctypes.c_int
         lib.orc_tile_rects.restype = ctypes.c_int
         lib.orc_bin_sort.restype = ctypes.c_longlong
+        lib.orc_contrib.restype = ctypes.c_int
         _LIB = lib
     return _LIB
 
@@ -149,6 +154,53 @@ def render_bwd(surfels, cam, pose, g_rgb, g_depth, g_normal, g_opacity, rule: Ru
                           _p(_d(g_opacity).reshape(-1)), _p(d_mu), _p(d_q), _p(d_s), _p(d_o),
                           _p(d_c), _p(d_pose), _p(d_mc), int(n_threads or default_threads()))
     return dict(mu=d_mu, quat=d_q, scale=d_s, opacity=d_o, rgb=d_c, pose6=d_pose, min_cos=d_mc)
+
+
+def contrib(surfels, cam, pose, rule: Rule = Rule(), pixels=None, n_threads: int = 0):
+    """Per-surfel contribution C_k = sum_p w_k(p) over the image (or the
+    listed pixels), Eq. contribution of Sec. III-D with w_k(p) of Eq. weight
+    (the renderer's items and stop rule).  Also, per surfel: ``ambiguous``
+    (a candidate at a pixel whose evaluation lies within a small relative
+    margin of a threshold), ``bbox`` (x0, y0, x1, y1 of the listed pixels
+    where it is a candidate; x0 = -1 if none) and ``min_cos``."""
+    mu, q, sc, op, rgb = _surfel_arrays(surfels)
+    W, H = cam.width, cam.height
+    pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int32)
+    npx = W * H if pix is None else pix.shape[0]
+    n = surfels.n
+    out = np.zeros(n)
+    flag = np.zeros(n, np.int32)
+    bbox = np.zeros((n, 4), np.int32)
+    mc = np.ones(n)
+    _lib().orc_contrib(n, _p(mu), _p(q), _p(sc), _p(op), _p(rgb), _p(_cam5(cam)), W, H,
+                       _p(_d(pose.R)), _p(_d(pose.t)), _p(rule.vec()), int(rule.exact), npx,
+                       _p(pix, ctypes.c_int), _p(out), _p(flag, ctypes.c_int),
+                       _p(bbox, ctypes.c_int), _p(mc), int(n_threads or default_threads()))
+    return dict(contrib=out, ambiguous=flag.astype(bool), bbox=bbox, min_cos=mc)
+
+
+def visible(c, threshold: float = 0.5):
+    """Visibility of Sec. III-D: a surfel is visible from a view when its
+    contribution exceeds 0.5."""
+    return np.asarray(c) > threshold
+
+
+def covisibility(c_a, c_b, threshold: float = 0.5):
+    """(|G_A n G_B|, |G_A u G_B|, S_cov) with G_X the surfels visible from
+    view X (Sec. III-D); S_cov = 0 when both sets are empty."""
+    ga = set(np.flatnonzero(visible(c_a, threshold)).tolist())
+    gb = set(np.flatnonzero(visible(c_b, threshold)).tolist())
+    inter, union = len(ga & gb), len(ga | gb)
+    return inter, union, (inter / union if union else 0.0)
+
+
+def keyframe_rule(score, t_a, t_b, c_k: float = 0.9, d_k: float = 0.15):
+    """Keyframe selection of Sec. III-D: a new keyframe when the
+    covisibility with the last keyframe falls below c_k or the distance
+    between the translation vectors of the two world-to-camera poses exceeds
+    d_k (Table I: 0.9 and 15 cm)."""
+    d = math.sqrt(sum((float(a) - float(b)) ** 2 for a, b in zip(t_a, t_b)))
+    return bool(score < c_k or d > d_k)
 
 
 def tile_rects(surfels, cam, pose, rule: Rule = Rule(), tile=(16, 16)):

@@ -302,6 +302,159 @@ int orc_render(int n, const double* mu, const double* quat, const double* scale,
   return 0;
 }
 
+struct Cand {
+  double depth_c;
+  int id;
+  bool on_edge;
+};
+
+// Per-surfel contribution (Sec. III-D, Eq. weight and Eq. contribution):
+// out_contrib[i] = sum over the listed pixels of w_i(p) = a_i T_i, the
+// blending weight of surfel i in pixel p (the same items and stop rule as
+// orc_render).  Diagnostics for the parity tests, per surfel:
+//   out_flag[i]  = 1 if, at some pixel, i is a candidate (a valid
+//                  intersection in front of the near plane, inside or near
+//                  the cutoff and alpha_min bounds) at or after the first
+//                  candidate in blending order whose evaluation sits within
+//                  a small relative margin of a threshold (cutoff radius,
+//                  alpha_min, near plane, or the stop test on T) and that
+//                  the pixel reaches (an FP32 evaluation may legitimately
+//                  decide that one otherwise, which changes the weights
+//                  from there on), or the item whose stop test sits within
+//                  a small margin of t_min, or the item after it;
+//   out_bbox[4i..4i+3] = x0, y0, x1, y1 of the listed pixels where i is a
+//                  candidate (x0 = -1 if none);
+//   out_mincos[i] = smallest |cos| between a ray it blends into and its
+//                  normal (1 if none).
+int orc_contrib(int n, const double* mu, const double* quat, const double* scale,
+                const double* opacity, const double* rgb, const double* cam5, int W, int H,
+                const double* R9, const double* t3, const double* rule4, int exact, int n_pix,
+                const int* pix, double* out_contrib, int* out_flag, int* out_bbox,
+                double* out_mincos, int n_threads) {
+  const Cam cam{cam5[0], cam5[1], cam5[2], cam5[3], cam5[4], W, H};
+  const Rule rule{rule4[0], rule4[1], rule4[2], rule4[3], exact};
+  const std::vector<CamSurfel> S = camera_surfels(n, mu, quat, scale, opacity, rgb, R9, t3);
+  const int np = pix ? n_pix : W * H;
+  const double tight = 2e-5, loose_t = 1e-4;
+  const int nt = n_threads_or_default(n_threads);
+  std::vector<std::vector<double>> acc(nt), mc(nt);
+  std::vector<std::vector<int>> flag(nt), box(nt);
+#pragma omp parallel num_threads(nt)
+  {
+#ifdef _OPENMP
+    const int tid = omp_get_thread_num();
+#else
+    const int tid = 0;
+#endif
+    acc[tid].assign(n, 0.0);
+    mc[tid].assign(n, 1.0);
+    flag[tid].assign(n, 0);
+    box[tid].assign(4 * (size_t)n, -1);
+    std::vector<Item> items;
+    std::vector<Cand> cand;
+#pragma omp for schedule(dynamic, 16)
+    for (int k = 0; k < np; ++k) {
+      double x, y;
+      pixel_coord(k, np, pix, W, x, y);
+      const int px = (int)std::floor(x), py = (int)std::floor(y);
+      const V3 r = mk((x - cam.cx) / cam.fx, (y - cam.cy) / cam.fy, 1.0);
+      // candidates (loose bounds) in blending order, each with its margin flag
+      cand.clear();
+      for (int i = 0; i < n; ++i) {
+        const CamSurfel& s = S[i];
+        if (!(s.mu_c.z > cam.near_z)) continue;
+        Hit h = intersect(s, r);
+        if (!h.ok || !(h.z > cam.near_z * (1.0 - tight))) continue;
+        const double r2 = h.u * h.u + h.v * h.v;
+        if (r2 > rule.cutoff_r2 * (1.0 + tight)) continue;
+        const double a = s.alpha * std::exp(-0.5 * r2);
+        if (a < rule.alpha_min * (1.0 - tight)) continue;
+        const bool on_edge = std::fabs(r2 - rule.cutoff_r2) <= tight * rule.cutoff_r2 ||
+                             std::fabs(a - rule.alpha_min) <= tight * rule.alpha_min ||
+                             std::fabs(h.z - cam.near_z) <= tight * cam.near_z;
+        cand.push_back(Cand{s.mu_c.z, i, on_edge});
+      }
+      std::sort(cand.begin(), cand.end(), [](const Cand& p, const Cand& q) {
+        if (p.depth_c != q.depth_c) return p.depth_c < q.depth_c;
+        return p.id < q.id;
+      });
+      auto pos_of = [&](int id) {
+        for (int c = 0; c < (int)cand.size(); ++c)
+          if (cand[c].id == id) return c;
+        return (int)cand.size();
+      };
+      pixel_items(S, cam, rule, x, y, items);
+      const int nb = blended_count(items, rule);
+      // a decision taken otherwise at candidate position m changes the
+      // weights from m on; positions after the stop are reached by neither
+      // side unless the stop itself moves
+      const int p_stop = nb < (int)items.size() ? pos_of(items[nb].id) : (int)cand.size();
+      int first = (int)cand.size();
+      for (int c = 0; c <= p_stop && c < (int)cand.size(); ++c)
+        if (cand[c].on_edge) {
+          first = c;
+          break;
+        }
+      // the stop test near t_min moves the stop by one item: only that item
+      // and the next one can change weight (by about t_min a / (1 - a))
+      double T = 1.0;
+      for (int m = 0; m < (int)items.size() && m <= nb; ++m) {
+        const double Tn = T * (1.0 - items[m].a);
+        if (!rule.exact && std::fabs(Tn - rule.t_min) <= loose_t * rule.t_min) {
+          flag[tid][items[m].id] = 1;
+          if (m + 1 < (int)items.size()) flag[tid][items[m + 1].id] = 1;
+        }
+        if (m == nb) break;
+        const Item& it = items[m];
+        const CamSurfel& s = S[it.id];
+        acc[tid][it.id] += it.a * T;
+        mc[tid][it.id] = std::min(mc[tid][it.id],
+                                  std::fabs(dot(r, s.tn_c)) / std::sqrt(dot(r, r)));
+        T = Tn;
+      }
+      for (int c = first; c < (int)cand.size(); ++c) flag[tid][cand[c].id] = 1;
+      for (const Cand& cd : cand) {
+        const int i = cd.id;
+        int* b = &box[tid][4 * (size_t)i];
+        if (b[0] < 0) {
+          b[0] = b[2] = px;
+          b[1] = b[3] = py;
+        } else {
+          b[0] = std::min(b[0], px);
+          b[1] = std::min(b[1], py);
+          b[2] = std::max(b[2], px);
+          b[3] = std::max(b[3], py);
+        }
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    double c = 0.0, m = 1.0;
+    int f = 0, b0 = -1, b1 = -1, b2 = -1, b3 = -1;
+    for (int t = 0; t < nt; ++t) {
+      c += acc[t][i];
+      m = std::min(m, mc[t][i]);
+      f |= flag[t][i];
+      const int* b = &box[t][4 * (size_t)i];
+      if (b[0] < 0) continue;
+      if (b0 < 0) {
+        b0 = b[0], b1 = b[1], b2 = b[2], b3 = b[3];
+      } else {
+        b0 = std::min(b0, b[0]), b1 = std::min(b1, b[1]);
+        b2 = std::max(b2, b[2]), b3 = std::max(b3, b[3]);
+      }
+    }
+    out_contrib[i] = c;
+    if (out_flag) out_flag[i] = f;
+    if (out_bbox) {
+      out_bbox[4 * i] = b0, out_bbox[4 * i + 1] = b1, out_bbox[4 * i + 2] = b2,
+      out_bbox[4 * i + 3] = b3;
+    }
+    if (out_mincos) out_mincos[i] = m;
+  }
+  return 0;
+}
+
 // Reverse mode of orc_render.  g_* are dL/d(rgb, depth, normal, opacity) per
 // listed pixel.  Writes dL/d(mu, quat (raw), scale, opacity, rgb) per surfel
 // and dL/dtau, tau = (rho, theta), for the left perturbation of T_cw; and, if

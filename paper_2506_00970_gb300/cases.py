@@ -10,6 +10,8 @@
   net      the proposal network at batch 256: forward, then forward + loss +
            backward (gs2d_net_grad) + AdamW
   sort     bin_sort of a 200k-surfel room at 160x120 (long tile segments)
+  contrib  per-surfel contributions (gs2d_render_contrib) of a 200k-surfel room
+           at 640x480
 
 Each case runs ``reps`` times (default 3) after one warm-up and prints the
 mean device time per repetition (CUDA events).  An optional third argument
@@ -131,8 +133,18 @@ def case_sort(reps, px=1):
     return _timed(lambda: r.bin_sort(grow=False), reps)
 
 
+def case_contrib(reps, px=1):
+    s = scenes.room_scene(0, 200_000)
+    cam = scenes.tracking_camera()
+    ds = gs2d.DeviceSurfels(s)
+    r = gs2d.Rasterizer(cam, ds.n, tile=gs2d.TILE_SHAPES[px][0], px=px)
+    r.forward(ds, gs2d.pose_tensor(scenes.room_pose(1)))
+    out = torch.empty(ds.n, device="cuda")
+    return _timed(lambda: r.contribution(out=out), reps)
+
+
 CASES = {"track": case_track, "mapping": case_mapping, "uneven": case_uneven, "net": case_net,
-         "sort": case_sort}
+         "sort": case_sort, "contrib": case_contrib}
 
 
 def main(argv):

@@ -49,6 +49,10 @@ SortFuse sort_fuse_args(void* workspace, int n, const gs2d_bins* bins, int tiles
 void sort_zero_region(void* workspace, int n, size_t capacity, int n_tiles, uint32_t** begin,
                       size_t* words);
 
+// Camera and tile configuration check shared by the tile kernels' entry
+// points (GS2D_OK or GS2D_ERR_INVALID_ARG).
+int validate_tile_cfg(const gs2d_camera* cam, const gs2d_config* cfg);
+
 int render_fwd_launch(const float* proj, const gs2d_bins* bins, const gs2d_camera* cam,
                       const gs2d_config* cfg, float* rgb, float* depth, float* normal,
                       float* opacity, float* t_final, uint32_t* n_last, const int32_t* gate,

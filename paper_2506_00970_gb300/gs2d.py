@@ -86,7 +86,8 @@ EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_stri
            "gs2d_render_batch_workspace", "gs2d_render_fwd_batch", "gs2d_render_bwd_batch",
            "gs2d_net_param_count", "gs2d_net_layout", "gs2d_net_workspace",
            "gs2d_net_pack_input", "gs2d_net_forward", "gs2d_net_grad", "gs2d_net_adamw",
-           "gs2d_net_apply", "gs2d_net_target", "gs2d_net_accept"]
+           "gs2d_net_apply", "gs2d_net_target", "gs2d_net_accept",
+           "gs2d_render_contrib_workspace", "gs2d_render_contrib", "gs2d_covisibility"]
 
 NET_LAYERS = 8
 NET_IN = (120, 160, 8)
@@ -152,6 +153,10 @@ def lib():
         L.gs2d_net_apply.argtypes = [vp, ip, vp, vp]
         L.gs2d_net_target.argtypes = [vp, vp, ip, vp, vp]
         L.gs2d_net_accept.argtypes = [vp, vp, vp, ip, vp, vp, vp]
+        L.gs2d_render_contrib_workspace.restype = sz
+        L.gs2d_render_contrib_workspace.argtypes = [sz]
+        L.gs2d_render_contrib.argtypes = [vp, vp, vp, ip, vp, vp, vp, vp, sz, vp, vp]
+        L.gs2d_covisibility.argtypes = [vp, vp, ip, fl, vp, vp, fl, fl, vp, vp, vp, vp]
         _LIB = L
     return _LIB
 
@@ -273,6 +278,26 @@ def gs2d_render_fwd(proj, bins: Bins, cam: Camera, cfg: Config, rgb, depth, norm
 def gs2d_render_count(proj, bins: Bins, cam: Camera, cfg: Config, counts, stream=None):
     check(lib().gs2d_render_count(_ptr(proj), _ref(bins), _ref(cam), _ref(cfg), _ptr(counts),
                                   _stream(stream)), "gs2d_render_count")
+
+
+def gs2d_render_contrib_workspace(capacity) -> int:
+    return int(lib().gs2d_render_contrib_workspace(int(capacity)))
+
+
+def gs2d_render_contrib(proj, bins: Bins, tiles, n, cam: Camera, cfg: Config, contrib, workspace,
+                        stream=None):
+    check(lib().gs2d_render_contrib(_ptr(proj), _ref(bins), _ptr(tiles), int(n), _ref(cam),
+                                    _ref(cfg), _ptr(contrib), _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(), None,
+                                    _stream(stream)), "gs2d_render_contrib")
+
+
+def gs2d_covisibility(contrib_a, contrib_b, n, vis_threshold, pose_a, pose_b, c_k, d_k, counts,
+                      score=None, is_keyframe=None, stream=None):
+    check(lib().gs2d_covisibility(_ptr(contrib_a), _ptr(contrib_b), int(n), float(vis_threshold),
+                                  _ptr(pose_a), _ptr(pose_b), float(c_k), float(d_k),
+                                  _ptr(counts), _ptr(score), _ptr(is_keyframe), _stream(stream)),
+          "gs2d_covisibility")
 
 
 def gs2d_render_bwd_workspace(n, capacity, n_tiles) -> int:
@@ -667,6 +692,19 @@ class Rasterizer:
         self.render_fwd(stream)
         return dict(rgb=self.rgb, depth=self.depth, normal=self.normal, opacity=self.opacity,
                     t_final=self.t_final, n_last=self.n_last)
+
+    def contribution(self, out=None, stream=None):
+        """Per-surfel contribution (sum of blending weights over the image)
+        of the last projected and binned view; device [n] FP32."""
+        contrib = out if out is not None else torch.empty(max(self.n, 1), dtype=torch.float32,
+                                                          device=self.device)
+        need = gs2d_render_contrib_workspace(self.capacity)
+        ws = getattr(self, "contrib_ws", None)
+        if ws is None or ws.numel() < need:
+            ws = self.contrib_ws = _bytes(need, self.device)
+        gs2d_render_contrib(self.proj, self.bins, self.tiles, self.n, self.cam, self.cfg, contrib,
+                            ws, stream)
+        return contrib[: self.n]
 
     def backward(self, surf: DeviceSurfels, pose, d_rgb, d_depth, d_normal=None, d_opacity=None,
                  full: bool = True, stream=None):
