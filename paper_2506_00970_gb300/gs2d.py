@@ -74,6 +74,16 @@ class View(ctypes.Structure):
                 ("d_opacity", ctypes.c_void_p), ("d_pose6", ctypes.c_void_p)]
 
 
+class MapState(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_void_p), ("t_c", ctypes.c_void_p), ("d_c", ctypes.c_void_p),
+                ("t_l", ctypes.c_void_p)]
+
+
+class StateParams(ctypes.Structure):
+    _fields_ = [("vis_threshold", ctypes.c_float), ("inactive_after", ctypes.c_int),
+                ("reactivate", ctypes.c_int), ("loop_h", ctypes.c_int)]
+
+
 MAX_VIEWS = 32
 
 EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_string",
@@ -87,7 +97,9 @@ EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_stri
            "gs2d_net_param_count", "gs2d_net_layout", "gs2d_net_workspace",
            "gs2d_net_pack_input", "gs2d_net_forward", "gs2d_net_grad", "gs2d_net_adamw",
            "gs2d_net_apply", "gs2d_net_target", "gs2d_net_accept",
-           "gs2d_render_contrib_workspace", "gs2d_render_contrib", "gs2d_covisibility"]
+           "gs2d_render_contrib_workspace", "gs2d_render_contrib", "gs2d_covisibility",
+           "gs2d_map_observe", "gs2d_map_correct_workspace", "gs2d_map_correct",
+           "gs2d_map_prune", "gs2d_map_compact_workspace", "gs2d_map_compact"]
 
 NET_LAYERS = 8
 NET_IN = (120, 160, 8)
@@ -157,6 +169,15 @@ def lib():
         L.gs2d_render_contrib_workspace.argtypes = [sz]
         L.gs2d_render_contrib.argtypes = [vp, vp, vp, ip, vp, vp, vp, vp, sz, vp, vp]
         L.gs2d_covisibility.argtypes = [vp, vp, ip, fl, vp, vp, fl, fl, vp, vp, vp, vp]
+        L.gs2d_map_observe.argtypes = [vp, vp, ip, vp, ip, vp, vp, vp, vp]
+        L.gs2d_map_correct_workspace.restype = sz
+        L.gs2d_map_correct_workspace.argtypes = [ip]
+        L.gs2d_map_correct.argtypes = [vp, vp, vp, ip, vp, vp, ip, vp, sz, vp, vp, vp]
+        L.gs2d_map_prune.argtypes = [vp, vp, ip, ip, fl, vp, vp]
+        L.gs2d_map_compact_workspace.restype = sz
+        L.gs2d_map_compact_workspace.argtypes = [ip]
+        L.gs2d_map_compact.argtypes = [vp, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp,
+                                       vp]
         _LIB = L
     return _LIB
 
@@ -298,6 +319,69 @@ def gs2d_covisibility(contrib_a, contrib_b, n, vis_threshold, pose_a, pose_b, c_
                                   _ptr(pose_a), _ptr(pose_b), float(c_k), float(d_k),
                                   _ptr(counts), _ptr(score), _ptr(is_keyframe), _stream(stream)),
           "gs2d_covisibility")
+
+
+class DeviceMapState:
+    """Per-surfel state of Eq. map (Sec. III-C) as CUDA tensors: delta
+    (uint8, 1 = active), t_c (int32), d_c (float32), t_l (int32)."""
+
+    def __init__(self, n, kf_id=0, d_c=float("inf"), device="cuda", active=True):
+        self.delta = torch.full((n,), 1 if active else 0, dtype=torch.uint8, device=device)
+        self.t_c = torch.full((n,), int(kf_id), dtype=torch.int32, device=device)
+        self.d_c = torch.full((n,), float(d_c), dtype=torch.float32, device=device)
+        self.t_l = torch.full((n,), int(kf_id), dtype=torch.int32, device=device)
+
+    @classmethod
+    def from_tensors(cls, delta, t_c, d_c, t_l):
+        o = cls.__new__(cls)
+        o.delta, o.t_c, o.d_c, o.t_l = (x.contiguous() for x in (delta, t_c, d_c, t_l))
+        return o
+
+    def struct(self) -> MapState:
+        return MapState(self.delta.data_ptr(), self.t_c.data_ptr(), self.d_c.data_ptr(),
+                        self.t_l.data_ptr())
+
+
+def gs2d_map_observe(contrib, mu, n, pose_cw, kf_id, prm: StateParams, st: DeviceMapState,
+                     counts=None, stream=None):
+    ms = st.struct()
+    check(lib().gs2d_map_observe(_ptr(contrib), _ptr(mu), int(n), _ptr(pose_cw), int(kf_id),
+                                 _ref(prm), _ref(ms), _ptr(counts), _stream(stream)),
+          "gs2d_map_observe")
+
+
+def gs2d_map_correct_workspace(n_kf) -> int:
+    return int(lib().gs2d_map_correct_workspace(int(n_kf)))
+
+
+def gs2d_map_correct(mu, quat, t_c, n, poses_old, poses_new, n_kf, workspace, n_skipped=None,
+                     stream=None):
+    check(lib().gs2d_map_correct(_ptr(mu), _ptr(quat), _ptr(t_c), int(n), _ptr(poses_old),
+                                 _ptr(poses_new), int(n_kf), _ptr(workspace),
+                                 workspace.numel() * workspace.element_size(), None,
+                                 _ptr(n_skipped), _stream(stream)), "gs2d_map_correct")
+
+
+def gs2d_map_prune(contrib, t_c, n, r, vis_threshold, keep, stream=None):
+    check(lib().gs2d_map_prune(_ptr(contrib), _ptr(t_c), int(n), int(r), float(vis_threshold),
+                               _ptr(keep), _stream(stream)), "gs2d_map_prune")
+
+
+def gs2d_map_compact_workspace(n) -> int:
+    return int(lib().gs2d_map_compact_workspace(int(n)))
+
+
+def gs2d_map_compact(keep, n, surf: "DeviceSurfels", st, out: "DeviceSurfels", st_out, new_index,
+                     n_out, workspace, stream=None):
+    sv = surf.struct()
+    si = st.struct() if st is not None else None
+    so = st_out.struct() if st_out is not None else None
+    check(lib().gs2d_map_compact(_ptr(keep), int(n), _ref(sv), _ref(si) if si else None,
+                                 _ptr(out.mu), _ptr(out.quat), _ptr(out.scale), _ptr(out.opacity),
+                                 _ptr(out.rgb), _ref(so) if so else None, _ptr(new_index),
+                                 _ptr(n_out), _ptr(workspace),
+                                 workspace.numel() * workspace.element_size(), None,
+                                 _stream(stream)), "gs2d_map_compact")
 
 
 def gs2d_render_bwd_workspace(n, capacity, n_tiles) -> int:
