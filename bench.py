@@ -347,6 +347,7 @@ def run_ours(args):
     roof = roofline(r, ds, frames, cam, cfg, stream, ms_iter, fused_ms)
     del graph
     batch = batch_workloads(K, W_, flush)
+    maint = map_maintenance(flush)
     tracking["learned_proposal"] = learned_proposal(flush)
 
     if rank == 0:
@@ -369,6 +370,7 @@ def run_ours(args):
             "roofline": roof["main"],
             "roofline_other": roof["other"],
             **batch,
+            **maint,
             "wall_s": wall,
             "peak_source": src,
         }
@@ -613,6 +615,170 @@ def batch_workloads(K, W_, flush):
                       "resolutions from {320x240, 640x480, 1200x680}, active subsets of "
                       "50k-1M surfels (log-uniform), same loss as the mapping window")
     return {"mapping_window": mw, "uneven_batch": ub}
+
+
+# FP32 operations per pair of the contribution pass: the forward's
+# evaluation (17 + 4 inside the cutoff) plus, per blended pair, T (1 - a)
+# and w += a T (4), and one add per evaluated pair in the per-warp sums.
+FLOPS_CONTRIB_BLEND = 4
+# Algorithmic bytes per surfel of the map-state passes (each array read or
+# written once): observe reads contrib, mu and the state (4 + 12 + 13) and
+# writes the state (13); correct reads t_c, mu, quat (32) and writes mu, quat
+# (28); prune reads contrib, t_c (8) and writes keep (1); compact reads keep
+# twice, the parameters and the state (2 + 52 + 13) and writes them and the
+# new index (65 + 4).
+MAP_BYTES = {"observe": 42, "correct": 60, "prune": 9, "compact": 136}
+# FP32 operations per pixel of the SSIM term with its gradient (3 channels):
+# five moment maps filtered separably (2 x 11 FMA each = 44 flops, plus 8
+# to form the products and the difference), the SSIM value and its partials
+# (~40), three partial maps filtered back (3 x 44) and the combination (4):
+# 3 x (5 x 44 + 8 + 40 + 132 + 4) = 1212, halo work not counted.
+SSIM_FLOPS_PER_PX = 1212
+
+
+def _timed_ms(fn, reps, flush, stream):
+    """Median device time of fn over reps calls, L2 flushed before each."""
+    import torch
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return float(np.median(ms))
+
+
+def map_maintenance(flush, reps=10):
+    """Keyframe bookkeeping of Sec. III-D / III-F / IV-C on the GPU.
+    (a) keyframe test of a tracking frame (200k-surfel room, 640x480):
+    projection, binning, per-surfel contributions (gs2d_render_contrib) and
+    the covisibility score + keyframe rule against the last keyframe's
+    contributions; the contribution kernel's FP32 roofline from the pair
+    counts.  (b) the map-state passes on a 2M-surfel map with the
+    contributions of a 1200x680 keyframe view: state update, correction by
+    64 keyframe increments, pruning and compaction, each against HBM."""
+    import torch
+    from paper_2506_00970_gb300 import gs2d, scenes
+    stream = torch.cuda.current_stream()
+    pk, _ = peaks()
+    peak_f = fp32_peak_tflops(float(pk.get("sm_max_mhz", 2070.0)))
+    hbm = float(pk["hbm_gbs"])
+    out = {}
+    # (a)
+    s = scenes.room_scene(0, N_SURFELS)
+    cam = scenes.tracking_camera()
+    ds = gs2d.DeviceSurfels(s)
+    r = gs2d.Rasterizer(cam, ds.n)
+    kf_pose = gs2d.pose_tensor(scenes.room_pose(1))
+    cur_pose = gs2d.pose_tensor(scenes.perturb_pose(scenes.room_pose(1), 0.05, 2.0, seed=3))
+    r.forward(ds, kf_pose)
+    c_kf = r.contribution().clone()
+    r.forward(ds, cur_pose)
+    c_cur = torch.empty(ds.n, device="cuda")
+    counts = torch.zeros(2, dtype=torch.int32, device="cuda")
+    score = torch.zeros(1, device="cuda")
+    is_kf = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
+    gs2d.gs2d_render_count(r.proj, r.bins, r.cam, r.cfg, cnt)
+    torch.cuda.synchronize()
+    E, Ein, B = (int(x) for x in cnt.cpu().numpy())
+    work = (FLOPS_EVAL + 1) * E + FLOPS_IN * Ein + FLOPS_CONTRIB_BLEND * B
+
+    def keyframe_test():
+        r.project(ds, cur_pose)
+        r.bin_sort(grow=False)
+        r.contribution(out=c_cur)
+        gs2d.gs2d_covisibility(c_cur, c_kf, ds.n, 0.5, cur_pose, kf_pose, 0.9, 0.15, counts, score,
+                               is_kf)
+
+    keyframe_test()
+    t_all = _timed_ms(keyframe_test, reps, flush, stream)
+    t_c = _timed_ms(lambda: r.contribution(out=c_cur), reps, flush, stream)
+    a = work / (t_c / 1e3) / 1e12
+    out["keyframe_test"] = {
+        "workload": f"tracking frame: {N_SURFELS} surfels, 640x480",
+        "ms": t_all, "contrib_ms": t_c, "mpix_s": cam.width * cam.height / t_c / 1e3,
+        "covisibility": float(score.item()), "is_keyframe": int(is_kf.item()),
+        "roofline": {"kernel": "contrib_tile_kernel + contrib_reduce_kernel", "bound": "alu",
+                     "achieved": a, "peak": peak_f, "unit": "TFLOP/s", "frac": a / peak_f,
+                     "flop_per_launch": work}}
+    del r, ds, s
+    # (b)
+    n = UNEVEN_SURFELS
+    s = scenes.room_scene(3, n)
+    ds = gs2d.DeviceSurfels(s)
+    kcam = scenes.mapping_camera()
+    r = gs2d.Rasterizer(kcam, n)
+    r.forward(ds, gs2d.pose_tensor(scenes.room_pose(5)))
+    contrib = r.contribution().clone()
+    del r
+    rng = np.random.default_rng(11)
+    n_kf = 64
+    st0 = {"delta": torch.ones(n, dtype=torch.uint8, device="cuda"),
+           "t_c": torch.tensor(rng.integers(0, n_kf, n).astype(np.int32), device="cuda"),
+           "d_c": torch.full((n,), 2.5, device="cuda"),
+           "t_l": torch.tensor(rng.integers(40, n_kf, n).astype(np.int32), device="cuda")}
+    st = gs2d.DeviceMapState.from_tensors(*(v.clone() for v in st0.values()))
+    prm = gs2d.StateParams(0.5, 20, 0, -1)
+    mcount = torch.zeros(4, dtype=torch.int32, device="cuda")
+    poses_old = torch.tensor(np.concatenate([np.r_[np.eye(3).ravel(), rng.normal(size=3)]
+                                             for _ in range(n_kf)]).astype(np.float32), device="cuda")
+    poses_new = poses_old + 1e-3
+    cws = torch.empty(gs2d.gs2d_map_correct_workspace(n_kf), dtype=torch.uint8, device="cuda")
+    keep = torch.empty(n, dtype=torch.uint8, device="cuda")
+    outs = gs2d.DeviceSurfels.from_tensors(torch.empty_like(ds.mu), torch.empty_like(ds.quat),
+                                           torch.empty_like(ds.scale), torch.empty_like(ds.opacity),
+                                           torch.empty_like(ds.rgb))
+    st_o = gs2d.DeviceMapState.from_tensors(*(torch.empty_like(v) for v in st0.values()))
+    n_out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    new_index = torch.empty(n, dtype=torch.int32, device="cuda")
+    kws = torch.empty(gs2d.gs2d_map_compact_workspace(n), dtype=torch.uint8, device="cuda")
+    kp = gs2d.pose_tensor(scenes.room_pose(5))
+    ops = {
+        "observe": lambda: gs2d.gs2d_map_observe(contrib, ds.mu, n, kp, n_kf, prm, st, mcount),
+        "correct": lambda: gs2d.gs2d_map_correct(ds.mu, ds.quat, st.t_c, n, poses_old, poses_new,
+                                                 n_kf, cws),
+        "prune": lambda: gs2d.gs2d_map_prune(contrib, st.t_c, n, 7, 0.5, keep),
+        "compact": lambda: gs2d.gs2d_map_compact(keep, n, ds, st, outs, st_o, new_index, n_out,
+                                                 kws),
+    }
+    res = {}
+    for name, fn in ops.items():
+        fn()
+        t = _timed_ms(fn, reps, flush, stream)
+        gbs = MAP_BYTES[name] * n / (t / 1e3) / 1e9
+        res[name] = {"ms": t, "bytes_per_surfel": MAP_BYTES[name], "achieved_gbs": gbs,
+                     "frac_of_hbm": gbs / hbm}
+    torch.cuda.synchronize()
+    res["visible_active"] = int(mcount[0].item())
+    res["kept"] = int(n_out.item())
+    out["map_state"] = {"workload": f"{n}-surfel map, contributions of a 1200x680 keyframe view, "
+                                    f"{n_kf} keyframe increments", "passes": res}
+    del ds, outs, st, st_o, contrib
+    # (c) the SSIM term of the full mapping loss (Table I weight) on one
+    # 1200x680 keyframe image: loss and gradient in one fused pass
+    h, w = kcam.height, kcam.width
+    yy = torch.rand(h, w, 3, generator=torch.Generator(device="cuda").manual_seed(1),
+                    device="cuda")
+    xx = (yy + 0.1 * torch.randn_like(yy)).clamp(0, 1)
+    gx = torch.zeros_like(xx)
+    lo = torch.zeros(1, device="cuda")
+    sws = torch.empty(gs2d.gs2d_ssim_workspace(h, w), dtype=torch.uint8, device="cuda")
+    fn = lambda: gs2d.gs2d_ssim_loss(xx, yy, h, w, 0.125, gx, lo, sws)
+    fn()
+    t = _timed_ms(fn, reps, flush, stream)
+    flops = SSIM_FLOPS_PER_PX * h * w
+    a = flops / (t / 1e3) / 1e12
+    out["ssim_term"] = {"workload": f"SSIM term + gradient, one {w}x{h} RGB image", "ms": t,
+                        "mpix_s": h * w / t / 1e3,
+                        "roofline": {"kernel": "ssim_kernel + ssim_sum_kernel", "bound": "alu",
+                                     "achieved": a, "peak": peak_f, "unit": "TFLOP/s",
+                                     "frac": a / peak_f, "flop_per_launch": flops}}
+    return out
 
 
 def net_flops_per_sample():

@@ -322,6 +322,33 @@ int gs2d_mapping_loss(const float* rgb, const float* depth, const float* normal,
                       float* g_normal, float* g_opacity, float* loss_out, void* workspace,
                       size_t ws_bytes, size_t* ws_needed, gs2d_stream stream);
 
+/* The full mapping loss of Sec. III-E, L_m = 1/|Omega| sum_p (L_c + w_d L_D
+ * + w_n L_n) with L_c = (1 - w_ssim) |I_r - I|_1 + w_ssim (1 - SSIM(p)),
+ * SSIM(p) the mean over the three channels of the SSIM of Wang et al. 2004
+ * (11 x 11 Gaussian window, sigma 1.5, C1 = 0.01^2, C2 = 0.03^2, zero
+ * padding at the border) of the rendered against the observed colour.
+ * Table I gives the SSIM term the weight 0.125 (w_ssim; the equation's
+ * lambda_c weights the L1 term, so lambda_c = 1 - w_ssim).  w_ssim = 0 is
+ * gs2d_mapping_loss.  w_ssim in [0, 1]; arguments otherwise as
+ * gs2d_mapping_loss; workspace gs2d_mapping_loss_ssim_workspace(cam). */
+size_t gs2d_mapping_loss_ssim_workspace(const gs2d_camera* cam);
+int gs2d_mapping_loss_ssim(const float* rgb, const float* depth, const float* normal,
+                           const float* opacity, const float* obs_rgb, const float* obs_depth,
+                           const gs2d_camera* cam, float w_ssim, float w_d, float w_n,
+                           float* g_rgb, float* g_depth, float* g_normal, float* g_opacity,
+                           float* loss_out, void* workspace, size_t ws_bytes, size_t* ws_needed,
+                           gs2d_stream stream);
+
+/* The SSIM term alone: *loss += weight / (H W) sum_p (1 - mean_c SSIM_c(p))
+ * of x against y (device [H*W*3], channel-last, SSIM as above) and, if g_x
+ * is not NULL, g_x += its gradient w.r.t. x.  One fused pass (moments,
+ * SSIM, adjoint filtering in shared memory); the block sums are reduced in
+ * a fixed order.  loss: device [1].  Workspace gs2d_ssim_workspace(H, W). */
+size_t gs2d_ssim_workspace(int height, int width);
+int gs2d_ssim_loss(const float* x, const float* y, int height, int width, float weight,
+                   float* g_x, float* loss, void* workspace, size_t ws_bytes, size_t* ws_needed,
+                   gs2d_stream stream);
+
 /* Frame-to-map tracking (Sec. III-D): n_iter iterations of
  * project -> bin_sort -> render_fwd -> tracking loss -> pose-only backward
  * -> AdamW on tau -> T <- Exp(tau) T with tau reset to 0 (the moments are

@@ -24,7 +24,9 @@ Contents (each cites the passage it follows):
   * ``tracking_loss``            -- masked L1 colour + depth loss, Eq.
     normal_mask, opacity_mask, tracking_loss (Sec. III-D).
   * ``normal_from_depth`` / ``mapping_loss`` -- Eq. normal_fromD and the
-    mapping loss of Sec. III-E without the SSIM term.
+    mapping loss of Sec. III-E, with or without the SSIM term;
+    ``ssim`` / ``ssim_loss`` -- SSIM of Wang et al. 2004 (11 x 11 Gaussian
+    window, sigma 1.5) and its loss term with gradient.
   * ``track``                    -- the frame-to-map tracking loop of
     Sec. III-D: render, loss, pose gradient, AdamW, retraction.
   * ``net`` (oracle/net.py)      -- the learned tracking-pose proposal
@@ -372,10 +374,59 @@ def normal_from_depth(depth, cam):
     return ND, valid
 
 
-def mapping_loss(img, obs_rgb, obs_depth, cam, w_d=0.5, w_n=0.02, depth_mode=1, valid_opacity=0.5):
-    """L_m = 1/|Omega| sum_p (|I_r - I|_1 + w_d |D_r - D| + w_n (1 - N_{D_r} . N_r))
-    (Sec. III-E, colour term without SSIM).  The normal term counts at
-    interior pixels whose own and 4-neighbour opacities exceed 0.5."""
+def ssim_window(radius: int = 5, sigma: float = 1.5):
+    """The SSIM window of Wang et al. 2004: an 11 x 11 Gaussian, sigma 1.5,
+    normalised to sum 1 (the outer product of the normalised 1D Gaussian)."""
+    d = np.arange(-radius, radius + 1, dtype=np.float64)
+    g = np.exp(-d * d / (2.0 * sigma * sigma))
+    g /= g.sum()
+    return np.outer(g, g)
+
+
+def _ssim_torch(x, y, C1=1e-4, C2=9e-4):
+    """Per-pixel, per-channel SSIM (Wang et al. 2004) of H x W x C tensors:
+    local means, variances and covariance under the window with zero padding
+    (a library 2D convolution), then the SSIM formula."""
+    import torch
+    import torch.nn.functional as F
+    C = x.shape[-1]
+    w = torch.tensor(ssim_window(), dtype=torch.float64)[None, None].repeat(C, 1, 1, 1)
+    X = x.permute(2, 0, 1)[None]
+    Y = y.permute(2, 0, 1)[None]
+    f = lambda a: F.conv2d(a, w, padding=5, groups=C)
+    mx, my = f(X), f(Y)
+    sxx = f(X * X) - mx * mx
+    syy = f(Y * Y) - my * my
+    sxy = f(X * Y) - mx * my
+    S = ((2 * mx * my + C1) * (2 * sxy + C2)) / ((mx * mx + my * my + C1) * (sxx + syy + C2))
+    return S[0].permute(1, 2, 0)
+
+
+def ssim(x, y):
+    """SSIM map (H x W x C, FP64) of x against y."""
+    import torch
+    return _ssim_torch(torch.tensor(np.asarray(x, np.float64)),
+                       torch.tensor(np.asarray(y, np.float64))).numpy()
+
+
+def ssim_loss(x, y, weight=1.0):
+    """weight / |Omega| sum_p (1 - mean_c SSIM_c(p)) and its gradient w.r.t. x."""
+    import torch
+    t = torch.tensor(np.asarray(x, np.float64), requires_grad=True)
+    S = _ssim_torch(t, torch.tensor(np.asarray(y, np.float64)))
+    H, W = S.shape[0], S.shape[1]
+    L = weight * (1.0 - S.mean(-1)).sum() / (H * W)
+    L.backward()
+    return float(L.detach()), t.grad.numpy().copy()
+
+
+def mapping_loss(img, obs_rgb, obs_depth, cam, w_d=0.5, w_n=0.02, depth_mode=1, valid_opacity=0.5,
+                 w_ssim=0.0):
+    """L_m = 1/|Omega| sum_p (L_c + w_d |D_r - D| + w_n (1 - N_{D_r} . N_r))
+    (Sec. III-E) with L_c = (1 - w_ssim) |I_r - I|_1 + w_ssim (1 - SSIM(p)),
+    SSIM(p) the channel mean (w_ssim = 0: the colour term without SSIM;
+    Table I gives the SSIM term 0.125).  The normal term counts at interior
+    pixels whose own and 4-neighbour opacities exceed 0.5."""
     import torch
     t = {k: torch.tensor(np.asarray(img[k], np.float64), requires_grad=True)
          for k in ("rgb", "depth", "normal", "opacity")}
@@ -391,7 +442,10 @@ def mapping_loss(img, obs_rgb, obs_depth, cam, w_d=0.5, w_n=0.02, depth_mode=1, 
                           & (O[:-2, 1:-1] > valid_opacity))
         ok &= valid
     Ln = torch.where(ok, 1.0 - (ND * t["normal"]).sum(-1), torch.zeros_like(O))
-    per = (t["rgb"] - I).abs().sum(-1) + w_d * (Dr - D).abs() + w_n * Ln
+    Lc = (1.0 - w_ssim) * (t["rgb"] - I).abs().sum(-1)
+    if w_ssim > 0.0:
+        Lc = Lc + w_ssim * (1.0 - _ssim_torch(t["rgb"], I).mean(-1))
+    per = Lc + w_d * (Dr - D).abs() + w_n * Ln
     L = per.sum() / (cam.width * cam.height)
     L.backward()
     return float(L.detach()), {k: (v.grad.numpy().copy() if v.grad is not None else np.zeros(v.shape))

@@ -12,6 +12,7 @@
   sort     bin_sort of a 200k-surfel room at 160x120 (long tile segments)
   contrib  per-surfel contributions (gs2d_render_contrib) of a 200k-surfel room
            at 640x480
+  ssim     the SSIM term with its gradient (gs2d_ssim_loss) at 1200x680
 
 Each case runs ``reps`` times (default 3) after one warm-up and prints the
 mean device time per repetition (CUDA events).  An optional third argument
@@ -143,8 +144,20 @@ def case_contrib(reps, px=1):
     return _timed(lambda: r.contribution(out=out), reps)
 
 
+def case_ssim(reps, px=1):
+    rng = np.random.default_rng(0)
+    h, w = 680, 1200
+    y = torch.tensor(rng.uniform(size=(h, w, 3)), dtype=torch.float32, device="cuda")
+    x = (y + 0.1 * torch.randn_like(y)).clamp(0, 1)
+    g = torch.zeros_like(x)
+    loss = torch.zeros(1, device="cuda")
+    ws = torch.empty(gs2d.gs2d_ssim_workspace(h, w), dtype=torch.uint8, device="cuda")
+    return _timed(lambda: gs2d.gs2d_ssim_loss(x, y, h, w, 0.125, g, loss, ws), reps)
+
+
 CASES = {"track": case_track, "mapping": case_mapping, "uneven": case_uneven, "net": case_net,
-         "sort": case_sort, "contrib": case_contrib}
+         "sort": case_sort, "contrib": case_contrib,
+         "ssim": case_ssim}
 
 
 def main(argv):

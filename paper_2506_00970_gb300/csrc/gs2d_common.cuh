@@ -72,4 +72,18 @@ __device__ __forceinline__ F3 mat_tmul(const float* m, F3 v) {
 
 __host__ __device__ inline int tiles_along(int px, int tile) { return (px + tile - 1) / tile; }
 
+
+// Sum over a 256-thread block (fixed order); the result is valid in thread 0.
+// s: shared scratch of 8 floats.  Every thread must call it.
+__device__ __forceinline__ float block_sum256(float v, float* s) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < 8; ++w) t += s[w];
+  return t;
+}
+
 }  // namespace gs2d

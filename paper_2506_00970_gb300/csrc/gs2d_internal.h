@@ -53,6 +53,13 @@ void sort_zero_region(void* workspace, int n, size_t capacity, int n_tiles, uint
 // points (GS2D_OK or GS2D_ERR_INVALID_ARG).
 int validate_tile_cfg(const gs2d_camera* cam, const gs2d_config* cfg);
 
+// SSIM term (weight / |Omega| sum_p (1 - mean_c SSIM_c(p)) added to *loss,
+// its gradient added to g_x): x, y [H*W*3].
+size_t ssim_ws_bytes(int height, int width);
+int ssim_launch(const float* x, const float* y, int height, int width, float weight, float* g_x,
+                float* loss, void* workspace, size_t ws_bytes, size_t* ws_needed,
+                cudaStream_t st);
+
 int render_fwd_launch(const float* proj, const gs2d_bins* bins, const gs2d_camera* cam,
                       const gs2d_config* cfg, float* rgb, float* depth, float* normal,
                       float* opacity, float* t_final, uint32_t* n_last, const int32_t* gate,

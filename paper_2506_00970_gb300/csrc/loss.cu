@@ -10,17 +10,6 @@ namespace gs2d {
 constexpr int kLossBlocks = 4 * 152;
 constexpr int kLossThreads = 256;
 
-__device__ __forceinline__ float block_sum256(float v, float* s) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
-  __syncthreads();
-  float t = 0.f;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < kLossThreads / 32; ++w) t += s[w];
-  return t;
-}
-
 // L_t = 1/|Omega| sum M_n M_o (|I_r - I|_1 + lambda_d |D_r - D|), Eq.
 // tracking_loss; M_n = [N_r . r > 0] (Eq. normal_mask; r's length does not
 // change the sign), M_o = [O > thresh] (Eq. opacity_mask); D_r = D/O in
@@ -144,7 +133,7 @@ struct MapSmem {
 __global__ void __launch_bounds__(kLossThreads) mapping_loss_kernel(
     const float* __restrict__ rgb, const float* __restrict__ depth, const float* __restrict__ normal,
     const float* __restrict__ opac, const float* __restrict__ obs_rgb,
-    const float* __restrict__ obs_depth, gs2d_camera cam, float w_d, float w_n,
+    const float* __restrict__ obs_depth, gs2d_camera cam, float w_l1, float w_d, float w_n,
     float* __restrict__ g_rgb, float* __restrict__ g_depth, float* __restrict__ g_normal,
     float* __restrict__ g_opac, float* __restrict__ part) {
   __shared__ float s[kLossThreads / 32];
@@ -197,10 +186,11 @@ __global__ void __launch_bounds__(kLossThreads) mapping_loss_kernel(
       const float d1 = rgb[3 * i + 1] - obs_rgb[3 * i + 1];
       const float d2 = rgb[3 * i + 2] - obs_rgb[3 * i + 2];
       const float dd = Dh - obs_depth[i];
-      acc += fabsf(d0) + fabsf(d1) + fabsf(d2) + w_d * fabsf(dd);
-      g_rgb[3 * i] = sgnf(d0) * inv;
-      g_rgb[3 * i + 1] = sgnf(d1) * inv;
-      g_rgb[3 * i + 2] = sgnf(d2) * inv;
+      acc += w_l1 * (fabsf(d0) + fabsf(d1) + fabsf(d2)) + w_d * fabsf(dd);
+      const float sl = w_l1 * inv;
+      g_rgb[3 * i] = sgnf(d0) * sl;
+      g_rgb[3 * i + 1] = sgnf(d1) * sl;
+      g_rgb[3 * i + 2] = sgnf(d2) * sl;
       float gDh = w_d * sgnf(dd) * inv;
       // own normal term
       const int ry = ly + 1, rx = lx + 1;
@@ -278,21 +268,42 @@ int gs2d_mapping_loss(const float* rgb, const float* depth, const float* normal,
                       const gs2d_camera* cam, float w_d, float w_n, float* g_rgb, float* g_depth,
                       float* g_normal, float* g_opacity, float* loss_out, void* workspace,
                       size_t ws_bytes, size_t* ws_needed, gs2d_stream stream) {
+  return gs2d_mapping_loss_ssim(rgb, depth, normal, opacity, obs_rgb, obs_depth, cam, 0.f, w_d,
+                                w_n, g_rgb, g_depth, g_normal, g_opacity, loss_out, workspace,
+                                ws_bytes, ws_needed, stream);
+}
+
+size_t gs2d_mapping_loss_ssim_workspace(const gs2d_camera* cam) {
+  if (!cam || cam->width <= 0 || cam->height <= 0) return 0;
+  return loss_ws_bytes(cam) + ssim_ws_bytes(cam->height, cam->width);
+}
+
+int gs2d_mapping_loss_ssim(const float* rgb, const float* depth, const float* normal,
+                           const float* opacity, const float* obs_rgb, const float* obs_depth,
+                           const gs2d_camera* cam, float w_ssim, float w_d, float w_n,
+                           float* g_rgb, float* g_depth, float* g_normal, float* g_opacity,
+                           float* loss_out, void* workspace, size_t ws_bytes, size_t* ws_needed,
+                           gs2d_stream stream) {
   if (!rgb || !depth || !normal || !opacity || !obs_rgb || !obs_depth || !cam || !g_rgb ||
       !g_depth || !g_normal || !g_opacity || !loss_out)
     return GS2D_ERR_INVALID_ARG;
-  if (cam->width <= 0 || cam->height <= 0) return GS2D_ERR_INVALID_ARG;
-  const size_t need = loss_ws_bytes(cam);
+  if (cam->width <= 0 || cam->height <= 0 || !(w_ssim >= 0.f && w_ssim <= 1.f))
+    return GS2D_ERR_INVALID_ARG;
+  const size_t base = loss_ws_bytes(cam);
+  const size_t need = w_ssim > 0.f ? base + ssim_ws_bytes(cam->height, cam->width) : base;
   if (ws_needed) *ws_needed = need;
   if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
   cudaStream_t st = (cudaStream_t)stream;
   float* part = static_cast<float*>(workspace);
-  mapping_loss_kernel<<<kLossBlocks, kLossThreads, 0, st>>>(rgb, depth, normal, opacity, obs_rgb,
-                                                            obs_depth, *cam, w_d, w_n, g_rgb,
-                                                            g_depth, g_normal, g_opacity, part);
+  mapping_loss_kernel<<<kLossBlocks, kLossThreads, 0, st>>>(
+      rgb, depth, normal, opacity, obs_rgb, obs_depth, *cam, 1.f - w_ssim, w_d, w_n, g_rgb,
+      g_depth, g_normal, g_opacity, part);
   GS2D_LAUNCH_CHECK();
   sum_parts_kernel<<<1, 256, 0, st>>>(part, kLossBlocks, loss_out, nullptr);
   GS2D_LAUNCH_CHECK();
+  if (w_ssim > 0.f)
+    return ssim_launch(rgb, obs_rgb, cam->height, cam->width, w_ssim, g_rgb, loss_out,
+                       static_cast<char*>(workspace) + base, ws_bytes - base, nullptr, st);
   return GS2D_OK;
 }
 

@@ -10,7 +10,7 @@
 namespace gs2d {
 
 constexpr int kMapThreads = 256;
-constexpr int kMapMaxBlocks = 152 * 8;
+constexpr int kMapMaxBlocks = 152 * 32;
 constexpr int kCompactPer = 4;                         // items per thread
 constexpr int kCompactBlock = kMapThreads * kCompactPer;
 

@@ -99,7 +99,9 @@ EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_stri
            "gs2d_net_apply", "gs2d_net_target", "gs2d_net_accept",
            "gs2d_render_contrib_workspace", "gs2d_render_contrib", "gs2d_covisibility",
            "gs2d_map_observe", "gs2d_map_correct_workspace", "gs2d_map_correct",
-           "gs2d_map_prune", "gs2d_map_compact_workspace", "gs2d_map_compact"]
+           "gs2d_map_prune", "gs2d_map_compact_workspace", "gs2d_map_compact",
+           "gs2d_mapping_loss_ssim_workspace", "gs2d_mapping_loss_ssim", "gs2d_ssim_workspace",
+           "gs2d_ssim_loss"]
 
 NET_LAYERS = 8
 NET_IN = (120, 160, 8)
@@ -174,6 +176,12 @@ def lib():
         L.gs2d_map_correct_workspace.argtypes = [ip]
         L.gs2d_map_correct.argtypes = [vp, vp, vp, ip, vp, vp, ip, vp, sz, vp, vp, vp]
         L.gs2d_map_prune.argtypes = [vp, vp, ip, ip, fl, vp, vp]
+        L.gs2d_mapping_loss_ssim_workspace.restype = sz
+        L.gs2d_mapping_loss_ssim_workspace.argtypes = [vp]
+        L.gs2d_mapping_loss_ssim.argtypes = [vp] * 7 + [fl, fl, fl] + [vp] * 6 + [sz, vp, vp]
+        L.gs2d_ssim_workspace.restype = sz
+        L.gs2d_ssim_workspace.argtypes = [ip, ip]
+        L.gs2d_ssim_loss.argtypes = [vp, vp, ip, ip, fl, vp, vp, vp, sz, vp, vp]
         L.gs2d_map_compact_workspace.restype = sz
         L.gs2d_map_compact_workspace.argtypes = [ip]
         L.gs2d_map_compact.argtypes = [vp, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp,
@@ -419,6 +427,33 @@ def gs2d_mapping_loss(rgb, depth, normal, opacity, obs_rgb, obs_depth, cam: Came
                                   _ptr(loss_out), _ptr(workspace),
                                   workspace.numel() * workspace.element_size(), None,
                                   _stream(stream)), "gs2d_mapping_loss")
+
+
+def gs2d_mapping_loss_ssim_workspace(cam: Camera) -> int:
+    return int(lib().gs2d_mapping_loss_ssim_workspace(_ref(cam)))
+
+
+def gs2d_mapping_loss_ssim(rgb, depth, normal, opacity, obs_rgb, obs_depth, cam: Camera, w_ssim,
+                           w_d, w_n, g_rgb, g_depth, g_normal, g_opacity, loss_out, workspace,
+                           stream=None):
+    check(lib().gs2d_mapping_loss_ssim(_ptr(rgb), _ptr(depth), _ptr(normal), _ptr(opacity),
+                                       _ptr(obs_rgb), _ptr(obs_depth), _ref(cam), float(w_ssim),
+                                       float(w_d), float(w_n), _ptr(g_rgb), _ptr(g_depth),
+                                       _ptr(g_normal), _ptr(g_opacity), _ptr(loss_out),
+                                       _ptr(workspace),
+                                       workspace.numel() * workspace.element_size(), None,
+                                       _stream(stream)), "gs2d_mapping_loss_ssim")
+
+
+def gs2d_ssim_workspace(height, width) -> int:
+    return int(lib().gs2d_ssim_workspace(int(height), int(width)))
+
+
+def gs2d_ssim_loss(x, y, height, width, weight, g_x, loss, workspace, stream=None):
+    check(lib().gs2d_ssim_loss(_ptr(x), _ptr(y), int(height), int(width), float(weight), _ptr(g_x),
+                               _ptr(loss), _ptr(workspace),
+                               workspace.numel() * workspace.element_size(), None,
+                               _stream(stream)), "gs2d_ssim_loss")
 
 
 def gs2d_track_workspace(n, capacity, cam: Camera, cfg: Config) -> int:
