@@ -86,4 +86,40 @@ __device__ __forceinline__ float block_sum256(float v, float* s) {
   return t;
 }
 
+
+// Unit quaternion (w, x, y, z) of a rotation matrix D (row-major [9]), by
+// the branch of the largest of w, x, y, z (no division by a small number);
+// returned as float4 (x = w, y = x, z = y, w = z).
+__device__ __forceinline__ float4 quat_from_matrix(const float* D) {
+  const float tr = D[0] + D[4] + D[8];
+  float w, x, y, z;
+  if (tr >= D[0] && tr >= D[4] && tr >= D[8]) {
+    const float s = 2.f * sqrtf(fmaxf(1.f + tr, 1e-30f));   // s = 4 w
+    w = 0.25f * s;
+    x = (D[7] - D[5]) / s;
+    y = (D[2] - D[6]) / s;
+    z = (D[3] - D[1]) / s;
+  } else if (D[0] >= D[4] && D[0] >= D[8]) {
+    const float s = 2.f * sqrtf(fmaxf(1.f + D[0] - D[4] - D[8], 1e-30f));   // s = 4 x
+    w = (D[7] - D[5]) / s;
+    x = 0.25f * s;
+    y = (D[1] + D[3]) / s;
+    z = (D[2] + D[6]) / s;
+  } else if (D[4] >= D[8]) {
+    const float s = 2.f * sqrtf(fmaxf(1.f + D[4] - D[0] - D[8], 1e-30f));   // s = 4 y
+    w = (D[2] - D[6]) / s;
+    x = (D[1] + D[3]) / s;
+    y = 0.25f * s;
+    z = (D[5] + D[7]) / s;
+  } else {
+    const float s = 2.f * sqrtf(fmaxf(1.f + D[8] - D[0] - D[4], 1e-30f));   // s = 4 z
+    w = (D[3] - D[1]) / s;
+    x = (D[2] + D[6]) / s;
+    y = (D[5] + D[7]) / s;
+    z = 0.25f * s;
+  }
+  const float qn = rsqrtf(w * w + x * x + y * y + z * z);
+  return make_float4(w * qn, x * qn, y * qn, z * qn);
+}
+
 }  // namespace gs2d

@@ -6,6 +6,7 @@
 #include "gs2d_common.cuh"
 #include "gs2d_internal.h"
 #include "gs2d_map.h"
+#include "scan.cuh"
 
 namespace gs2d {
 
@@ -74,8 +75,7 @@ __global__ void __launch_bounds__(kMapThreads) map_observe_kernel(
 }
 
 // Pose increments dT_j = (T^o_cw)^-1 T_cw: dR = R_o^T R, dt = R_o^T (t - t_o),
-// and the unit quaternion of dR (the largest-component branch of the
-// matrix-to-quaternion conversion, so no division by a small number).
+// and the unit quaternion of dR.
 // Record layout: dR [9], dt [3], q [4] (w, x, y, z).
 __global__ void map_delta_kernel(const float* __restrict__ old_p, const float* __restrict__ new_p,
                                  int n_kf, float* __restrict__ delta) {
@@ -91,44 +91,17 @@ __global__ void map_delta_kernel(const float* __restrict__ old_p, const float* _
       D[3 * r + c] = B[r] * A[c] + B[3 + r] * A[3 + c] + B[6 + r] * A[6 + c];
     t[r] = B[r] * (A[9] - B[9]) + B[3 + r] * (A[10] - B[10]) + B[6 + r] * (A[11] - B[11]);
   }
-  const float tr = D[0] + D[4] + D[8];
-  float w, x, y, z;
-  if (tr >= D[0] && tr >= D[4] && tr >= D[8]) {
-    const float s = 2.f * sqrtf(fmaxf(1.f + tr, 1e-30f));   // s = 4 w
-    w = 0.25f * s;
-    x = (D[7] - D[5]) / s;
-    y = (D[2] - D[6]) / s;
-    z = (D[3] - D[1]) / s;
-  } else if (D[0] >= D[4] && D[0] >= D[8]) {
-    const float s = 2.f * sqrtf(fmaxf(1.f + D[0] - D[4] - D[8], 1e-30f));   // s = 4 x
-    w = (D[7] - D[5]) / s;
-    x = 0.25f * s;
-    y = (D[1] + D[3]) / s;
-    z = (D[2] + D[6]) / s;
-  } else if (D[4] >= D[8]) {
-    const float s = 2.f * sqrtf(fmaxf(1.f + D[4] - D[0] - D[8], 1e-30f));   // s = 4 y
-    w = (D[2] - D[6]) / s;
-    x = (D[1] + D[3]) / s;
-    y = 0.25f * s;
-    z = (D[5] + D[7]) / s;
-  } else {
-    const float s = 2.f * sqrtf(fmaxf(1.f + D[8] - D[0] - D[4], 1e-30f));   // s = 4 z
-    w = (D[3] - D[1]) / s;
-    x = (D[2] + D[6]) / s;
-    y = (D[5] + D[7]) / s;
-    z = 0.25f * s;
-  }
-  const float qn = rsqrtf(w * w + x * x + y * y + z * z);
+  const float4 q = quat_from_matrix(D);
   float* o = delta + 16 * j;
 #pragma unroll
   for (int k = 0; k < 9; ++k) o[k] = D[k];
   o[9] = t[0];
   o[10] = t[1];
   o[11] = t[2];
-  o[12] = w * qn;
-  o[13] = x * qn;
-  o[14] = y * qn;
-  o[15] = z * qn;
+  o[12] = q.x;
+  o[13] = q.y;
+  o[14] = q.z;
+  o[15] = q.w;
 }
 
 __global__ void __launch_bounds__(kMapThreads) map_correct_kernel(
@@ -185,34 +158,6 @@ __global__ void __launch_bounds__(kMapThreads) compact_count_kernel(const uint8_
   }
 }
 
-// Block-wide exclusive scan of one int per thread (kMapThreads threads);
-// returns the exclusive prefix, *total the block sum.
-__device__ __forceinline__ int block_exscan(int v, int* s_w, int* total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int x = v;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, off);
-    if (lane >= off) x += y;
-  }
-  if (lane == 31) s_w[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    int w = lane < kMapThreads / 32 ? s_w[lane] : 0;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, w, off);
-      if (lane >= off) w += y;
-    }
-    if (lane < kMapThreads / 32) s_w[lane] = w;
-  }
-  __syncthreads();
-  const int pre = (warp ? s_w[warp - 1] : 0) + x - v;
-  *total = s_w[kMapThreads / 32 - 1];
-  __syncthreads();
-  return pre;
-}
-
 // Pass 2 (one block): exclusive scan of the block counts, in place; n_out.
 __global__ void __launch_bounds__(kMapThreads) compact_scan_kernel(int32_t* __restrict__ blk,
                                                                    int nb,
@@ -223,7 +168,7 @@ __global__ void __launch_bounds__(kMapThreads) compact_scan_kernel(int32_t* __re
     const int b = b0 + (int)threadIdx.x;
     const int v = b < nb ? blk[b] : 0;
     int total;
-    const int pre = block_exscan(v, s_w, &total);
+    const int pre = block_exscan256(v, s_w, &total);
     if (b < nb) blk[b] = carry + pre;
     carry += total;
   }
@@ -252,7 +197,7 @@ __global__ void __launch_bounds__(kMapThreads) compact_scatter_kernel(
     c += kf[k] ? 1 : 0;
   }
   int total;
-  int o = blk[blockIdx.x] + block_exscan(c, s_w, &total);
+  int o = blk[blockIdx.x] + block_exscan256(c, s_w, &total);
 #pragma unroll
   for (int k = 0; k < kCompactPer; ++k) {
     const int i = base + k;

@@ -84,6 +84,17 @@ class StateParams(ctypes.Structure):
                 ("reactivate", ctypes.c_int), ("loop_h", ctypes.c_int)]
 
 
+class VoxelTable(ctypes.Structure):
+    _fields_ = [("keys", ctypes.c_void_p), ("capacity", ctypes.c_uint32), ("voxel", ctypes.c_float),
+                ("status", ctypes.c_void_p)]
+
+
+class ExpandParams(ctypes.Structure):
+    _fields_ = [("ratio", ctypes.c_float), ("opacity", ctypes.c_float),
+                ("max_scale", ctypes.c_float), ("kf_id", ctypes.c_int),
+                ("insert_new", ctypes.c_int)]
+
+
 MAX_VIEWS = 32
 
 EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_string",
@@ -101,7 +112,8 @@ EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_stri
            "gs2d_map_observe", "gs2d_map_correct_workspace", "gs2d_map_correct",
            "gs2d_map_prune", "gs2d_map_compact_workspace", "gs2d_map_compact",
            "gs2d_mapping_loss_ssim_workspace", "gs2d_mapping_loss_ssim", "gs2d_ssim_workspace",
-           "gs2d_ssim_loss"]
+           "gs2d_ssim_loss", "gs2d_voxel_clear", "gs2d_voxel_insert", "gs2d_voxel_query",
+           "gs2d_expand_workspace", "gs2d_expand"]
 
 NET_LAYERS = 8
 NET_IN = (120, 160, 8)
@@ -182,6 +194,12 @@ def lib():
         L.gs2d_ssim_workspace.restype = sz
         L.gs2d_ssim_workspace.argtypes = [ip, ip]
         L.gs2d_ssim_loss.argtypes = [vp, vp, ip, ip, fl, vp, vp, vp, sz, vp, vp]
+        L.gs2d_voxel_clear.argtypes = [vp, vp]
+        L.gs2d_voxel_insert.argtypes = [vp, vp, vp, ip, vp]
+        L.gs2d_voxel_query.argtypes = [vp, vp, ip, vp, vp]
+        L.gs2d_expand_workspace.restype = sz
+        L.gs2d_expand_workspace.argtypes = [vp]
+        L.gs2d_expand.argtypes = [vp] * 8 + [ip, ip] + [vp] * 7 + [vp, sz, vp, vp]
         L.gs2d_map_compact_workspace.restype = sz
         L.gs2d_map_compact_workspace.argtypes = [ip]
         L.gs2d_map_compact.argtypes = [vp, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp,
@@ -454,6 +472,56 @@ def gs2d_ssim_loss(x, y, height, width, weight, g_x, loss, workspace, stream=Non
                                _ptr(loss), _ptr(workspace),
                                workspace.numel() * workspace.element_size(), None,
                                _stream(stream)), "gs2d_ssim_loss")
+
+
+class DeviceVoxelTable:
+    """Voxel hash table of occupied space (Sec. III-E) on the device."""
+
+    def __init__(self, capacity: int, voxel: float, device="cuda"):
+        cap = 1 << max(0, int(capacity - 1).bit_length())
+        self.keys = torch.empty(cap, dtype=torch.int64, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.capacity = cap
+        self.voxel = float(voxel)
+        self.clear()
+
+    def struct(self) -> VoxelTable:
+        return VoxelTable(self.keys.data_ptr(), self.capacity, self.voxel, self.status.data_ptr())
+
+    def clear(self, stream=None):
+        t = self.struct()
+        check(lib().gs2d_voxel_clear(_ref(t), _stream(stream)), "gs2d_voxel_clear")
+
+    def insert(self, points, mask=None, stream=None):
+        t = self.struct()
+        check(lib().gs2d_voxel_insert(_ref(t), _ptr(points), _ptr(mask), int(points.shape[0]),
+                                      _stream(stream)), "gs2d_voxel_insert")
+
+    def query(self, points, out=None, stream=None):
+        t = self.struct()
+        m = int(points.shape[0])
+        occ = out if out is not None else torch.empty(max(m, 1), dtype=torch.uint8,
+                                                      device=points.device)
+        check(lib().gs2d_voxel_query(_ref(t), _ptr(points), m, _ptr(occ), _stream(stream)),
+              "gs2d_voxel_query")
+        return occ[:m]
+
+
+def gs2d_expand_workspace(cam: Camera) -> int:
+    return int(lib().gs2d_expand_workspace(_ref(cam)))
+
+
+def gs2d_expand(rgb, depth, cam: Camera, pose_cw, u_keep, u_angle, table, prm: ExpandParams,
+                n_map, capacity, out: "DeviceSurfels", st, n_new, workspace, stream=None):
+    tb = table.struct() if table is not None else None
+    ms = st.struct() if st is not None else None
+    check(lib().gs2d_expand(_ptr(rgb), _ptr(depth), _ref(cam), _ptr(pose_cw), _ptr(u_keep),
+                            _ptr(u_angle), _ref(tb) if tb else None, _ref(prm), int(n_map),
+                            int(capacity), _ptr(out.mu), _ptr(out.quat), _ptr(out.scale),
+                            _ptr(out.opacity), _ptr(out.rgb), _ref(ms) if ms else None,
+                            _ptr(n_new), _ptr(workspace),
+                            workspace.numel() * workspace.element_size(), None, _stream(stream)),
+          "gs2d_expand")
 
 
 def gs2d_track_workspace(n, capacity, cam: Camera, cfg: Config) -> int:
