@@ -759,6 +759,52 @@ def map_maintenance(flush, reps=10):
     out["map_state"] = {"workload": f"{n}-surfel map, contributions of a 1200x680 keyframe view, "
                                     f"{n_kf} keyframe increments", "passes": res}
     del ds, outs, st, st_o, contrib
+    # (d) map expansion of a 1200x680 keyframe against the active map's voxel
+    # table (rebuilt from the active flags first, as after a state change)
+    cam_k = scenes.Camera(600.0, 600.0, 600.0, 340.0, 1200, 680)
+    rgb_k, dep_k = scenes.rgbd_frame(21, cam_k)
+    rng2 = np.random.default_rng(21)
+    T_ = lambda a: torch.tensor(a, device="cuda")
+    rgb_d, dep_d = T_(rgb_k), T_(dep_k)
+    u_keep = T_(rng2.uniform(size=dep_k.shape).astype(np.float32))
+    u_ang = T_(rng2.uniform(size=dep_k.shape).astype(np.float32))
+    pose_k = gs2d.pose_tensor(scenes.identity_pose())
+    ex_ratio = 0.04
+    n_act = 1_000_000
+    act_pts = T_(np.random.default_rng(22).uniform([-2.1, -1.4, 0.3], [2.1, 1.3, 3.2],
+                                                    (n_act, 3)).astype(np.float32))
+    table = gs2d.DeviceVoxelTable(1 << 22, 0.02)
+    cap_m = n_act + dep_k.size
+    f32 = dict(dtype=torch.float32, device="cuda")
+    new_s = gs2d.DeviceSurfels.from_tensors(torch.empty(cap_m, 3, **f32), torch.empty(cap_m, 4, **f32),
+                                            torch.empty(cap_m, 2, **f32), torch.empty(cap_m, **f32),
+                                            torch.empty(cap_m, 3, **f32))
+    new_st = gs2d.DeviceMapState(cap_m)
+    n_new = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ews = torch.empty(gs2d.gs2d_expand_workspace(gs2d.camera(cam_k)), dtype=torch.uint8,
+                      device="cuda")
+    eprm = gs2d.ExpandParams(ex_ratio, 0.99, 0.05, 9, 0)
+
+    def rebuild():
+        table.clear()
+        table.insert(act_pts)
+
+    def expand():
+        gs2d.gs2d_expand(rgb_d, dep_d, gs2d.camera(cam_k), pose_k, u_keep, u_ang, table, eprm,
+                         n_act, cap_m, new_s, new_st, n_new, ews)
+
+    rebuild()
+    expand()
+    t_rb = _timed_ms(rebuild, reps, flush, stream)
+    t_ex = _timed_ms(expand, reps, flush, stream)
+    m_ps = int(((dep_k > 0) & (u_keep.cpu().numpy() < ex_ratio)).sum())
+    out["map_expansion"] = {
+        "workload": (f"1200x680 RGB-D keyframe, random downsampling {ex_ratio}, voxel table of "
+                     f"{n_act} active surfels (2 cm voxels)"),
+        "table_rebuild_ms": t_rb, "expand_ms": t_ex, "points_ps": m_ps,
+        "new_surfels": int(n_new.item()),
+        "nearest_pairs": m_ps * m_ps}
+    del table, new_s, new_st, act_pts
     # (c) the SSIM term of the full mapping loss (Table I weight) on one
     # 1200x680 keyframe image: loss and gradient in one fused pass
     h, w = kcam.height, kcam.width
