@@ -48,28 +48,45 @@ struct SsimWin {
   float g[2 * kSsimR + 1];  // normalised 1D Gaussian; the window is g g^T
 };
 
-// Shared memory (floats): region A holds x and y (2 x 52 x 52), later the
-// three G maps (3 x 42 x 42); region B holds the five row-filtered moment
-// maps (5 x 52 x 42), later the three row-filtered G maps (3 x 42 x 32).
-constexpr int kSsimSmemA = 2 * kSsimA * kSsimA;
-constexpr int kSsimSmemB = 5 * kSsimA * kSsimB;
+// Shared memory (floats).  Region A: x and y (2 x 52 x 52, rows of 52), later
+// the three G maps (3 x 42 rows of 44).  Region B: the five row-filtered
+// moment maps (5 x 52 rows of 44), later the three row-filtered G maps
+// (3 x 42 rows of 32).  Row strides are multiples of 4 floats so a thread
+// reads 16 consecutive taps as four float4; each region has a little slack
+// for the taps past the last row that only padding outputs use.
+constexpr int kSsimBP = 44;                       // padded row of the 42-wide maps
+constexpr int kSsimSmemA = 3 * kSsimB * kSsimBP + 16;
+constexpr int kSsimSmemB = 5 * kSsimA * kSsimBP + 2 * kSsimBP + 16;
 constexpr size_t kSsimSmemBytes = (size_t)(kSsimSmemA + kSsimSmemB) * sizeof(float);
-static_assert(3 * kSsimB * kSsimB <= kSsimSmemA, "G maps fit region A");
+static_assert(2 * kSsimA * kSsimA + 16 <= kSsimSmemA, "x and y fit region A");
 static_assert(3 * kSsimB * kSsimT <= kSsimSmemB, "filtered G maps fit region B");
+constexpr int kSsimRB = 4;                        // outputs per thread along a row or column
+
+__device__ __forceinline__ void load16(const float* p, float (&v)[16]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float4 t = q[i];
+    v[4 * i] = t.x;
+    v[4 * i + 1] = t.y;
+    v[4 * i + 2] = t.z;
+    v[4 * i + 3] = t.w;
+  }
+}
 
 __global__ void __launch_bounds__(kSsimThreads) ssim_kernel(const float* __restrict__ x,
                                                            const float* __restrict__ y, int H,
                                                            int W, float weight, SsimWin win,
                                                            float* __restrict__ g_x,
                                                            float* __restrict__ part) {
-  extern __shared__ float smem[];
-  float* sa = smem;                 // x [52][52], y [52][52]  ->  G [3][42][42]
-  float* sb = smem + kSsimSmemA;    // M [5][52][42]           ->  F [3][42][32]
+  extern __shared__ float4 smem4[];
+  float* sa = reinterpret_cast<float*>(smem4);    // x, y [52][52]  ->  G [3][42][44]
+  float* sb = sa + kSsimSmemA;                    // M [5][52][44]  ->  F [3][42][32]
   __shared__ float s_red[kSsimThreads / 32];
   const int c = blockIdx.z;
   const int tx0 = blockIdx.x * kSsimT, ty0 = blockIdx.y * kSsimT;
   const int ax0 = tx0 - 2 * kSsimR, ay0 = ty0 - 2 * kSsimR;   // staged origin
-  // stage x, y (zero outside the image)
+  // stage x, y (zero outside the image) and clear the slack
   for (int e = threadIdx.x; e < kSsimA * kSsimA; e += kSsimThreads) {
     const int r = e / kSsimA, q = e % kSsimA;
     const int py = ay0 + r, px = ax0 + q;
@@ -82,100 +99,143 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_kernel(const float* __restr
     sa[e] = vx;
     sa[kSsimA * kSsimA + e] = vy;
   }
+  if (threadIdx.x < 16) sa[2 * kSsimA * kSsimA + threadIdx.x] = 0.f;
   __syncthreads();
-  // row filter of the five moments: M[k][r][q], r in [0,52), q in [0,42)
-  for (int e = threadIdx.x; e < kSsimA * kSsimB; e += kSsimThreads) {
-    const int r = e / kSsimB, q = e % kSsimB;
-    const float* rx = sa + r * kSsimA + q;
-    const float* ry = rx + kSsimA * kSsimA;
-    float mx = 0.f, md = 0.f, exx = 0.f, eyy = 0.f, edd = 0.f;
+  // row filter of the five moments (x, d = x - y, x^2, y^2, d^2): outputs
+  // M[k][r][q0 .. q0 + 3], r in [0, 52), q0 = 4 g, g in [0, 11)
+  constexpr int kG1 = (kSsimB + kSsimRB - 1) / kSsimRB;   // 11 groups along a row
+  for (int e = threadIdx.x; e < kSsimA * kG1; e += kSsimThreads) {
+    const int r = e / kG1, q0 = (e % kG1) * kSsimRB;
+    float xa[16], ya[16];
+    load16(sa + r * kSsimA + q0, xa);
+    load16(sa + kSsimA * kSsimA + r * kSsimA + q0, ya);
+    float m[5][kSsimRB];
 #pragma unroll
-    for (int t = 0; t <= 2 * kSsimR; ++t) {
-      const float a = rx[t], b = ry[t], w = win.g[t];
-      const float d = a - b;
-      const float wa = w * a, wb = w * b, wd = w * d;
-      mx += wa;
-      md += wd;
-      exx = fmaf(wa, a, exx);
-      eyy = fmaf(wb, b, eyy);
-      edd = fmaf(wd, d, edd);
+    for (int o = 0; o < kSsimRB; ++o) {
+      float mx = 0.f, md = 0.f, exx = 0.f, eyy = 0.f, edd = 0.f;
+#pragma unroll
+      for (int t = 0; t <= 2 * kSsimR; ++t) {
+        const float a = xa[o + t], b = ya[o + t], w = win.g[t];
+        const float d = a - b;
+        const float wa = w * a, wb = w * b, wd = w * d;
+        mx += wa;
+        md += wd;
+        exx = fmaf(wa, a, exx);
+        eyy = fmaf(wb, b, eyy);
+        edd = fmaf(wd, d, edd);
+      }
+      m[0][o] = mx;
+      m[1][o] = md;
+      m[2][o] = exx;
+      m[3][o] = eyy;
+      m[4][o] = edd;
     }
-    sb[e] = mx;
-    sb[kSsimA * kSsimB + e] = md;
-    sb[2 * kSsimA * kSsimB + e] = exx;
-    sb[3 * kSsimA * kSsimB + e] = eyy;
-    sb[4 * kSsimA * kSsimB + e] = edd;
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      *reinterpret_cast<float4*>(sb + (k * kSsimA + r) * kSsimBP + q0) =
+          make_float4(m[k][0], m[k][1], m[k][2], m[k][3]);
   }
   __syncthreads();
-  // column filter, S and the G maps on the 42 x 42 region (origin tile - 5);
-  // x and y are no longer needed, so the G maps take region A
+  // column filter, S and the G maps on the 42 x 42 region (origin tile - 5):
+  // rows r0 .. r0 + 3 of column q per thread; x and y are dead, so the G
+  // maps take region A
   const float up = -weight / (3.f * (float)H * (float)W);
   float loss = 0.f;
-  for (int e = threadIdx.x; e < kSsimB * kSsimB; e += kSsimThreads) {
-    const int r = e / kSsimB, q = e % kSsimB;
-    float m[5];
+  for (int e = threadIdx.x; e < kSsimB * kG1; e += kSsimThreads) {
+    const int q = e % kSsimB, r0 = (e / kSsimB) * kSsimRB;
+    float m[5][kSsimRB];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-      const float* col = sb + k * kSsimA * kSsimB + r * kSsimB + q;
-      float s = 0.f;
+      const float* col = sb + (k * kSsimA + r0) * kSsimBP + q;
+      float v[kSsimRB + 2 * kSsimR];
 #pragma unroll
-      for (int t = 0; t <= 2 * kSsimR; ++t) s = fmaf(win.g[t], col[t * kSsimB], s);
-      m[k] = s;
+      for (int t = 0; t < kSsimRB + 2 * kSsimR; ++t) v[t] = col[t * kSsimBP];
+#pragma unroll
+      for (int o = 0; o < kSsimRB; ++o) {
+        float a = 0.f;
+#pragma unroll
+        for (int t = 0; t <= 2 * kSsimR; ++t) a = fmaf(win.g[t], v[o + t], a);
+        m[k][o] = a;
+      }
     }
-    const int py = ty0 - kSsimR + r, px = tx0 - kSsimR + q;
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    if (px >= 0 && py >= 0 && px < W && py < H) {
-      const float mx = m[0], md = m[1], my = mx - md;
-      const float b1 = fmaf(mx, mx, fmaf(my, my, kSsimC1));
-      const float b2 = (m[2] - mx * mx) + (m[3] - my * my) + kSsimC2;
-      const float vd = m[4] - md * md;
-      const float ib1 = 1.f / b1, ib2 = 1.f / b2;
-      const float p1 = md * md * ib1, q1 = vd * ib2;   // 1 - P, 1 - Q
-      const float P = 1.f - p1, Q = 1.f - q1;
-      if (r >= kSsimR && r < kSsimR + kSsimT && q >= kSsimR && q < kSsimR + kSsimT)
-        loss += p1 + q1 - p1 * q1;                      // 1 - S
-      const float dmx = 2.f * (mx + my) * (Q * p1 * ib1 - P * q1 * ib2);
-      const float dmd = Q * (-2.f * ib1) * (md + my * p1) + P * (2.f * ib2) * (md + my * q1);
-      g0 = up * (dmx + dmd);
-      g1 = up * P * q1 * ib2;
-      g2 = -up * P * ib2;
+#pragma unroll
+    for (int o = 0; o < kSsimRB; ++o) {
+      const int r = r0 + o;
+      if (r >= kSsimB) break;
+      const int py = ty0 - kSsimR + r, px = tx0 - kSsimR + q;
+      float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+      if (px >= 0 && py >= 0 && px < W && py < H) {
+        const float mx = m[0][o], md = m[1][o], my = mx - md;
+        const float b1 = fmaf(mx, mx, fmaf(my, my, kSsimC1));
+        const float b2 = (m[2][o] - mx * mx) + (m[3][o] - my * my) + kSsimC2;
+        const float vd = m[4][o] - md * md;
+        const float ib1 = 1.f / b1, ib2 = 1.f / b2;
+        const float p1 = md * md * ib1, q1 = vd * ib2;   // 1 - P, 1 - Q
+        const float P = 1.f - p1, Q = 1.f - q1;
+        if (r >= kSsimR && r < kSsimR + kSsimT && q >= kSsimR && q < kSsimR + kSsimT)
+          loss += p1 + q1 - p1 * q1;                      // 1 - S
+        const float dmx = 2.f * (mx + my) * (Q * p1 * ib1 - P * q1 * ib2);
+        const float dmd = Q * (-2.f * ib1) * (md + my * p1) + P * (2.f * ib2) * (md + my * q1);
+        g0 = up * (dmx + dmd);
+        g1 = up * P * q1 * ib2;
+        g2 = -up * P * ib2;
+      }
+      sa[(0 * kSsimB + r) * kSsimBP + q] = g0;
+      sa[(1 * kSsimB + r) * kSsimBP + q] = g1;
+      sa[(2 * kSsimB + r) * kSsimBP + q] = g2;
     }
-    sa[e] = g0;
-    sa[kSsimB * kSsimB + e] = g1;
-    sa[2 * kSsimB * kSsimB + e] = g2;
   }
   __syncthreads();
-  // row filter of the G maps: F[k][r][q], r in [0,42), q in [0,32)
-  for (int e = threadIdx.x; e < kSsimB * kSsimT; e += kSsimThreads) {
-    const int r = e / kSsimT, q = e % kSsimT;
+  // row filter of the G maps: F[k][r][q0 .. q0 + 3], r in [0, 42), q0 = 4 g
+  constexpr int kG2 = kSsimT / kSsimRB;   // 8 groups along an output row
+  for (int e = threadIdx.x; e < kSsimB * kG2; e += kSsimThreads) {
+    const int r = e / kG2, q0 = (e % kG2) * kSsimRB;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const float* row = sa + k * kSsimB * kSsimB + r * kSsimB + q;
-      float s = 0.f;
+      float v[16];
+      load16(sa + (k * kSsimB + r) * kSsimBP + q0, v);
+      float f[kSsimRB];
 #pragma unroll
-      for (int t = 0; t <= 2 * kSsimR; ++t) s = fmaf(win.g[t], row[t], s);
-      sb[k * kSsimB * kSsimT + e] = s;
+      for (int o = 0; o < kSsimRB; ++o) {
+        float a = 0.f;
+#pragma unroll
+        for (int t = 0; t <= 2 * kSsimR; ++t) a = fmaf(win.g[t], v[o + t], a);
+        f[o] = a;
+      }
+      *reinterpret_cast<float4*>(sb + (k * kSsimB + r) * kSsimT + q0) =
+          make_float4(f[0], f[1], f[2], f[3]);
     }
   }
   __syncthreads();
-  // column filter to the tile and the gradient
+  // column filter to the tile (rows r0 .. r0 + 3 of column q) and the gradient
   if (g_x) {
-    for (int e = threadIdx.x; e < kSsimT * kSsimT; e += kSsimThreads) {
-      const int r = e / kSsimT, q = e % kSsimT;
-      const int py = ty0 + r, px = tx0 + q;
-      if (px >= W || py >= H) continue;
-      float f[3];
+    for (int e = threadIdx.x; e < kSsimT * kG2; e += kSsimThreads) {
+      const int q = e % kSsimT, r0 = (e / kSsimT) * kSsimRB;
+      const int px = tx0 + q;
+      float f[3][kSsimRB];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const float* col = sb + k * kSsimB * kSsimT + r * kSsimT + q;
-        float s = 0.f;
+        const float* col = sb + (k * kSsimB + r0) * kSsimT + q;
+        float v[kSsimRB + 2 * kSsimR];
 #pragma unroll
-        for (int t = 0; t <= 2 * kSsimR; ++t) s = fmaf(win.g[t], col[t * kSsimT], s);
-        f[k] = s;
+        for (int t = 0; t < kSsimRB + 2 * kSsimR; ++t) v[t] = col[t * kSsimT];
+#pragma unroll
+        for (int o = 0; o < kSsimRB; ++o) {
+          float a = 0.f;
+#pragma unroll
+          for (int t = 0; t <= 2 * kSsimR; ++t) a = fmaf(win.g[t], v[o + t], a);
+          f[k][o] = a;
+        }
       }
-      const size_t i = ((size_t)py * W + px) * 3 + c;
-      const float xv = x[i], yv = y[i];
-      g_x[i] += fmaf(2.f * xv, f[1], fmaf(2.f * (xv - yv), f[2], f[0]));
+      if (px >= W) continue;
+#pragma unroll
+      for (int o = 0; o < kSsimRB; ++o) {
+        const int py = ty0 + r0 + o;
+        if (py >= H) break;
+        const size_t i = ((size_t)py * W + px) * 3 + c;
+        const float xv = x[i], yv = y[i];
+        g_x[i] += fmaf(2.f * xv, f[1][o], fmaf(2.f * (xv - yv), f[2][o], f[0][o]));
+      }
     }
   }
   const float t = block_sum256(loss, s_red);
