@@ -9,9 +9,10 @@
 //                  (normal valid, voxel free);
 //   nearest        per point of P_s: the distance to its nearest other point
 //                  of P_s, by an exhaustive search in tiles of 256 points
-//                  staged in shared memory (exact; O(|P_s|^2) flops, which
-//                  at the paper's sparse downsampling is a fraction of a
-//                  millisecond);
+//                  staged in shared memory, the candidates split over 8
+//                  blocks per query block and min-combined (exact;
+//                  O(|P_s|^2) flops, a fraction of a millisecond at the
+//                  paper's sparse downsampling);
 //   emit           count + scan + scatter of the created points into the
 //                  map arrays at n_map + rank, with the tangent frame, the
 //                  quaternion and the state; optionally their voxels are
@@ -184,7 +185,8 @@ __global__ void __launch_bounds__(kExThreads) ps_point_kernel(
     const float* __restrict__ depth, gs2d_camera cam, const float* __restrict__ pose,
     const int32_t* __restrict__ idx,
     const int32_t* __restrict__ m_dev, gs2d_voxel_table table, int use_table,
-    float4* __restrict__ pts, float4* __restrict__ nrm, uint8_t* __restrict__ create) {
+    float4* __restrict__ pts, float4* __restrict__ nrm, uint8_t* __restrict__ create,
+    unsigned* __restrict__ nnd2) {
   __shared__ float T[12];   // T_cw: R row-major, t
   const int m = *m_dev;
   if ((int)(blockIdx.x * blockDim.x) >= m) return;
@@ -198,6 +200,7 @@ __global__ void __launch_bounds__(kExThreads) ps_point_kernel(
   const F3 Xc = back_project(cam, px, py, depth[p]);
   const F3 Xw = rot_t(T, f3(Xc.x - T[9], Xc.y - T[10], Xc.z - T[11]));
   pts[k] = make_float4(Xw.x, Xw.y, Xw.z, 0.f);
+  nnd2[k] = __float_as_uint(INFINITY);
   // Eq. normal_fromD: central differences of the back-projected points
   bool ok = px >= 1 && py >= 1 && px < W - 1 && py < H - 1;
   F3 n = f3(0.f, 0.f, 0.f);
@@ -220,31 +223,46 @@ __global__ void __launch_bounds__(kExThreads) ps_point_kernel(
   create[k] = (ok && free_vox) ? 1 : 0;
 }
 
-// distance from each point of P_s to its nearest other point
+// Squared distance from each point of P_s to its nearest other point, as
+// the bits of a non-negative float (ordered like the values) min-combined
+// with atomicMin: blockIdx.y splits the candidates so that small P_s still
+// fill the GPU; the result does not depend on the order of the atomics.
+constexpr int kNnSplit = 8;
 __global__ void __launch_bounds__(kExThreads) nearest_kernel(const float4* __restrict__ pts,
                                                             const int32_t* __restrict__ m_dev,
-                                                            float max_scale,
-                                                            float* __restrict__ nnd) {
+                                                            unsigned* __restrict__ nnd2) {
   __shared__ float4 s_p[kExThreads];
   const int m = *m_dev;
   const int k0 = blockIdx.x * kExThreads;
   if (k0 >= m) return;
+  const int per = (m + kNnSplit - 1) / kNnSplit;
+  const int c_lo = blockIdx.y * per, c_hi = min(m, c_lo + per);
+  if (c_lo >= c_hi) return;
   const int k = k0 + (int)threadIdx.x;
   const float4 q = k < m ? pts[k] : make_float4(0.f, 0.f, 0.f, 0.f);
   float best = INFINITY;
-  for (int j0 = 0; j0 < m; j0 += kExThreads) {
+  for (int j0 = c_lo; j0 < c_hi; j0 += kExThreads) {
     __syncthreads();
-    if (j0 + (int)threadIdx.x < m) s_p[threadIdx.x] = pts[j0 + threadIdx.x];
+    if (j0 + (int)threadIdx.x < c_hi) s_p[threadIdx.x] = pts[j0 + threadIdx.x];
     __syncthreads();
-    const int cnt = min(kExThreads, m - j0);
-    for (int j = 0; j < cnt; ++j) {
-      const float4 c = s_p[j];
-      const float dx = c.x - q.x, dy = c.y - q.y, dz = c.z - q.z;
-      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      if (j0 + j != k) best = fminf(best, d2);
+    const int cnt = min(kExThreads, c_hi - j0);
+    if (j0 + cnt <= k0 || j0 >= k0 + kExThreads) {
+      // no query of this block among these candidates: no self test
+      for (int j = 0; j < cnt; ++j) {
+        const float4 c = s_p[j];
+        const float dx = c.x - q.x, dy = c.y - q.y, dz = c.z - q.z;
+        best = fminf(best, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      }
+    } else {
+      for (int j = 0; j < cnt; ++j) {
+        const float4 c = s_p[j];
+        const float dx = c.x - q.x, dy = c.y - q.y, dz = c.z - q.z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (j0 + j != k) best = fminf(best, d2);
+      }
     }
   }
-  if (k < m) nnd[k] = best < INFINITY ? sqrtf(best) : max_scale;
+  if (k < m && best < INFINITY) atomicMin(nnd2 + k, __float_as_uint(best));
 }
 
 struct EmitArgs {
@@ -253,7 +271,8 @@ struct EmitArgs {
   const int32_t* idx;      // pixel of each P_s point
   const float4* pts;
   const float4* nrm;
-  const float* nnd;
+  const unsigned* nnd2;   // squared nearest distance (float bits)
+  float max_scale;
   const int32_t* sel;      // P_s point of each created surfel
   const int32_t* k_dev;    // number created
   float* mu;
@@ -300,7 +319,8 @@ __global__ void __launch_bounds__(kExThreads) emit_kernel(EmitArgs a) {
   a.mu[3 * o + 1] = X.y;
   a.mu[3 * o + 2] = X.z;
   reinterpret_cast<float4*>(a.quat)[o] = quat_from_matrix(D);
-  const float s = a.nnd[j];
+  const float d2 = __uint_as_float(a.nnd2[j]);
+  const float s = d2 < INFINITY ? sqrtf(d2) : a.max_scale;
   a.scale[2 * o] = s;
   a.scale[2 * o + 1] = s;
   a.opacity[o] = a.opac0;
@@ -317,7 +337,7 @@ __global__ void __launch_bounds__(kExThreads) emit_kernel(EmitArgs a) {
 struct ExWs {
   int32_t *blk, *blk2, *idx, *sel, *m, *k;
   float4 *pts, *nrm;
-  float* nnd;
+  unsigned* nnd2;
   uint8_t* create;
   size_t bytes;
 };
@@ -334,7 +354,7 @@ ExWs carve_expand(void* base, int P) {
   w.sel = c.take<int32_t>(P);
   w.pts = c.take<float4>(P);
   w.nrm = c.take<float4>(P);
-  w.nnd = c.take<float>(P);
+  w.nnd2 = c.take<unsigned>(P);
   w.create = c.take<uint8_t>(P);
   w.bytes = align_up(c.off, 256);
   return w;
@@ -415,9 +435,9 @@ int gs2d_expand(const float* rgb, const float* depth, const gs2d_camera* cam, co
   const gs2d_voxel_table tb = table ? *table : gs2d_voxel_table{nullptr, 0u, 1.f, nullptr};
   const int pb = (P + kExThreads - 1) / kExThreads;
   ps_point_kernel<<<pb, kExThreads, 0, s>>>(depth, *cam, pose_cw, w.idx, w.m, tb, table ? 1 : 0, w.pts,
-                                            w.nrm, w.create);
+                                            w.nrm, w.create, w.nnd2);
   GS2D_LAUNCH_CHECK();
-  nearest_kernel<<<pb, kExThreads, 0, s>>>(w.pts, w.m, prm->max_scale, w.nnd);
+  nearest_kernel<<<dim3(pb, kNnSplit), kExThreads, 0, s>>>(w.pts, w.m, w.nnd2);
   GS2D_LAUNCH_CHECK();
   const FlagPred fp{w.create};
   select_count_kernel<FlagPred><<<nb, kExThreads, 0, s>>>(fp, P, w.m, w.blk2);
@@ -432,7 +452,8 @@ int gs2d_expand(const float* rgb, const float* depth, const gs2d_camera* cam, co
   a.idx = w.idx;
   a.pts = w.pts;
   a.nrm = w.nrm;
-  a.nnd = w.nnd;
+  a.nnd2 = w.nnd2;
+  a.max_scale = prm->max_scale;
   a.sel = w.sel;
   a.k_dev = w.k;
   a.mu = mu;
