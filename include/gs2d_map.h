@@ -96,6 +96,13 @@ int gs2d_map_compact(const uint8_t* keep, int n, const gs2d_surfels* s, const gs
                      int32_t* n_out, void* workspace, size_t ws_bytes, size_t* ws_needed,
                      gs2d_stream stream);
 
+/* Back from a compacted subset to the whole map: out[i] = vals[new_index[i]]
+ * when new_index[i] >= 0, else fill (new_index as gs2d_map_compact writes
+ * it); e.g. the contributions of a view of the active map M_A, rendered from
+ * its compacted copy, indexed by the whole map's surfel ids. */
+int gs2d_map_expand_values(const float* vals, const int32_t* new_index, int n, float fill,
+                           float* out, gs2d_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

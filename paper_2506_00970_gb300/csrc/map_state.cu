@@ -217,6 +217,16 @@ __global__ void __launch_bounds__(kMapThreads) compact_scatter_kernel(
   }
 }
 
+__global__ void __launch_bounds__(kMapThreads) map_expand_values_kernel(
+    const float* __restrict__ vals, const int32_t* __restrict__ idx, int n, float fill,
+    float* __restrict__ out) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int k = idx[i];
+    out[i] = k >= 0 ? vals[k] : fill;
+  }
+}
+
 }  // namespace gs2d
 
 using namespace gs2d;
@@ -275,6 +285,17 @@ int gs2d_map_prune(const float* contrib, const int32_t* t_c, int n, int r, float
   if (!contrib || !t_c || !keep) return GS2D_ERR_INVALID_ARG;
   map_prune_kernel<<<map_blocks(n), kMapThreads, 0, (cudaStream_t)stream>>>(contrib, t_c, n, r,
                                                                            vis_threshold, keep);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+int gs2d_map_expand_values(const float* vals, const int32_t* new_index, int n, float fill,
+                           float* out, gs2d_stream stream) {
+  if (n < 0) return GS2D_ERR_INVALID_ARG;
+  if (n == 0) return GS2D_OK;
+  if (!vals || !new_index || !out) return GS2D_ERR_INVALID_ARG;
+  map_expand_values_kernel<<<map_blocks(n), kMapThreads, 0, (cudaStream_t)stream>>>(
+      vals, new_index, n, fill, out);
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
 }

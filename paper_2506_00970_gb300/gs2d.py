@@ -113,7 +113,7 @@ EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_stri
            "gs2d_map_prune", "gs2d_map_compact_workspace", "gs2d_map_compact",
            "gs2d_mapping_loss_ssim_workspace", "gs2d_mapping_loss_ssim", "gs2d_ssim_workspace",
            "gs2d_ssim_loss", "gs2d_voxel_clear", "gs2d_voxel_insert", "gs2d_voxel_query",
-           "gs2d_expand_workspace", "gs2d_expand"]
+           "gs2d_expand_workspace", "gs2d_expand", "gs2d_map_expand_values"]
 
 NET_LAYERS = 8
 NET_IN = (120, 160, 8)
@@ -195,6 +195,7 @@ def lib():
         L.gs2d_ssim_workspace.argtypes = [ip, ip]
         L.gs2d_ssim_loss.argtypes = [vp, vp, ip, ip, fl, vp, vp, vp, sz, vp, vp]
         L.gs2d_voxel_clear.argtypes = [vp, vp]
+        L.gs2d_map_expand_values.argtypes = [vp, vp, ip, fl, vp, vp]
         L.gs2d_voxel_insert.argtypes = [vp, vp, vp, ip, vp]
         L.gs2d_voxel_query.argtypes = [vp, vp, ip, vp, vp]
         L.gs2d_expand_workspace.restype = sz
@@ -391,6 +392,11 @@ def gs2d_map_correct(mu, quat, t_c, n, poses_old, poses_new, n_kf, workspace, n_
 def gs2d_map_prune(contrib, t_c, n, r, vis_threshold, keep, stream=None):
     check(lib().gs2d_map_prune(_ptr(contrib), _ptr(t_c), int(n), int(r), float(vis_threshold),
                                _ptr(keep), _stream(stream)), "gs2d_map_prune")
+
+
+def gs2d_map_expand_values(vals, new_index, n, fill, out, stream=None):
+    check(lib().gs2d_map_expand_values(_ptr(vals), _ptr(new_index), int(n), float(fill), _ptr(out),
+                                       _stream(stream)), "gs2d_map_expand_values")
 
 
 def gs2d_map_compact_workspace(n) -> int:

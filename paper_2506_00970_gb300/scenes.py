@@ -393,26 +393,34 @@ def pixel_sample(seed: int, h: int, w: int, n: int):
     return np.stack([idx % w, idx // w], axis=1).astype(np.int32)
 
 
-def rgbd_frame(seed: int, cam: Camera, noise_m: float = 0.001, hole_frac: float = 0.03):
-    """A synthetic observed RGB-D frame in the camera's own frame: the depth
-    (z) of a box room seen from inside -- back wall z = 3.2, side walls
-    x = +-2.1, floor y = 1.3, ceiling y = -1.4 (y down) -- with a sphere of
-    radius 0.45 m at (0.3, 0.25, 2.0), Gaussian depth noise and holes (depth
+def rgbd_frame(seed: int, cam: Camera, noise_m: float = 0.001, hole_frac: float = 0.03,
+               pose: Pose | None = None):
+    """A synthetic observed RGB-D frame of a box room seen from inside --
+    back wall z = 3.2, side walls x = +-2.1, floor y = 1.3, ceiling y = -1.4
+    (y down), front wall z = -2.0 -- with a sphere of radius 0.45 m at
+    (0.3, 0.25, 2.0), all in world coordinates, seen from the world-to-camera
+    ``pose`` (identity: the camera at the origin looking along +z).  Depth is
+    the camera-frame z of the first hit, with Gaussian noise and holes (depth
     0) at a random fraction of the pixels; colour a smooth random pattern
-    plus noise, in [0, 1].  Returns (rgb (H, W, 3), depth (H, W)) float32."""
+    over the image plus noise, in [0, 1].  Returns (rgb (H, W, 3), depth
+    (H, W)) float32."""
     rng = np.random.default_rng(seed)
+    R = np.eye(3) if pose is None else np.asarray(pose.R, np.float64)
+    tt = np.zeros(3) if pose is None else np.asarray(pose.t, np.float64)
+    c0 = -R.T @ tt
     x = (np.arange(cam.width) + 0.5 - cam.cx) / cam.fx
     y = (np.arange(cam.height) + 0.5 - cam.cy) / cam.fy
     rx, ry = np.meshgrid(x, y)
-    r = np.stack([rx, ry, np.ones_like(rx)], -1)
+    r = np.stack([rx, ry, np.ones_like(rx)], -1) @ R      # world direction, camera z = 1
     d = np.full(rx.shape, np.inf)
-    for n, c in (((0, 0, 1), 3.2), ((1, 0, 0), 2.1), ((-1, 0, 0), 2.1), ((0, 1, 0), 1.3),
-                 ((0, -1, 0), 1.4)):
-        nr = r @ np.array(n, float)
+    for n, c in (((0, 0, 1), 3.2), ((0, 0, -1), 2.0), ((1, 0, 0), 2.1), ((-1, 0, 0), 2.1),
+                 ((0, 1, 0), 1.3), ((0, -1, 0), 1.4)):
+        n = np.array(n, float)
+        nr = r @ n
         with np.errstate(divide="ignore", invalid="ignore"):
-            t = np.where(nr > 1e-9, c / nr, np.inf)
-        d = np.minimum(d, t)
-    C, rho = np.array([0.3, 0.25, 2.0]), 0.45
+            t = np.where(nr > 1e-9, (c - n @ c0) / nr, np.inf)
+        d = np.minimum(d, np.where(t > 0, t, np.inf))
+    C, rho = np.array([0.3, 0.25, 2.0]) - c0, 0.45
     a = (r * r).sum(-1)
     b = -2 * (r @ C)
     q = C @ C - rho * rho
@@ -420,7 +428,8 @@ def rgbd_frame(seed: int, cam: Camera, noise_m: float = 0.001, hole_frac: float 
     with np.errstate(invalid="ignore"):
         t = np.where(disc >= 0, (-b - np.sqrt(np.maximum(disc, 0))) / (2 * a), np.inf)
     d = np.minimum(d, np.where(t > 0, t, np.inf))
-    d = d + rng.normal(0, noise_m, d.shape)
+    d = np.where(np.isfinite(d), d, 0.0)
+    d = d + rng.normal(0, noise_m, d.shape) * (d > 0)
     d[rng.uniform(size=d.shape) < hole_frac] = 0.0
     f = rng.uniform(0.05, 0.3, 3)
     ph = rng.uniform(0, 2 * np.pi, 3)
