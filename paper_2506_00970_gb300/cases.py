@@ -2,6 +2,8 @@
 (ncu) and quick timing:  python -m paper_2506_00970_gb300.cases <case> [reps]
 
   track    tracking frames: 200k-surfel room, 640x480, 10 iterations each
+  track_small  tracking frames of the learned-proposal workload: 200k-surfel
+           room, 160x120, fx=fy=150, 10 iterations each
   mapping  a batched mapping step: 300k-surfel room, 4 keyframes at 1200x680
            (project, bin_sort, persistent forward, mapping loss, persistent
            backward + per-surfel reductions)
@@ -13,6 +15,9 @@
   contrib  per-surfel contributions (gs2d_render_contrib) of a 200k-surfel room
            at 640x480
   ssim     the SSIM term with its gradient (gs2d_ssim_loss) at 1200x680
+  map      map-state passes on a 2M-surfel map (state update, correction by 64
+           keyframe increments, pruning, compaction) and the expansion of a
+           1200x680 RGB-D keyframe (downsampling 0.04) against a voxel table
 
 Each case runs ``reps`` times (default 3) after one warm-up and prints the
 mean device time per repetition (CUDA events).  An optional third argument
@@ -43,9 +48,9 @@ def _timed(fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def case_track(reps, px=1):
+def case_track(reps, px=1, cam=None):
     s = scenes.room_scene(0, 200_000)
-    cam = scenes.tracking_camera()
+    cam = cam or scenes.tracking_camera()
     ds = gs2d.DeviceSurfels(s)
     tile = gs2d.TILE_SHAPES[px][0]
     r = gs2d.Rasterizer(cam, ds.n, tile=tile, px=px)
@@ -155,9 +160,68 @@ def case_ssim(reps, px=1):
     return _timed(lambda: gs2d.gs2d_ssim_loss(x, y, h, w, 0.125, g, loss, ws), reps)
 
 
-CASES = {"track": case_track, "mapping": case_mapping, "uneven": case_uneven, "net": case_net,
+def case_track_small(reps, px=1):
+    return case_track(reps, px, scenes.Camera(150.0, 150.0, 80.0, 60.0, 160, 120))
+
+
+def case_map(reps, px=1):
+    n, n_kf = 2_000_000, 64
+    rng = np.random.default_rng(0)
+    f = dict(dtype=torch.float32, device="cuda")
+    T = lambda a: torch.tensor(a, device="cuda")
+    mu = T(rng.uniform([-2.5, -2.0, 0.0], [2.5, 2.0, 3.0], (n, 3)).astype(np.float32))
+    ds = gs2d.DeviceSurfels.from_tensors(mu, T(rng.normal(size=(n, 4)).astype(np.float32)),
+                                         torch.full((n, 2), 0.02, **f), torch.full((n,), 0.9, **f),
+                                         torch.rand(n, 3, **f))
+    contrib = T(rng.choice(np.float32([0.0, 0.3, 0.7, 2.0]), n))
+    st = gs2d.DeviceMapState.from_tensors(torch.ones(n, dtype=torch.uint8, device="cuda"),
+                                          T(rng.integers(0, n_kf, n).astype(np.int32)),
+                                          torch.full((n,), 2.5, **f),
+                                          T(rng.integers(40, n_kf, n).astype(np.int32)))
+    out = gs2d.DeviceSurfels.from_tensors(*(torch.empty_like(t) for t in (
+        ds.mu, ds.quat, ds.scale, ds.opacity, ds.rgb)))
+    st_o = gs2d.DeviceMapState.from_tensors(*(torch.empty_like(t) for t in (
+        st.delta, st.t_c, st.d_c, st.t_l)))
+    keep = torch.empty(n, dtype=torch.uint8, device="cuda")
+    n_out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    kws = torch.empty(gs2d.gs2d_map_compact_workspace(n), dtype=torch.uint8, device="cuda")
+    po = T(np.concatenate([np.r_[np.eye(3).ravel(), rng.normal(size=3)]
+                           for _ in range(n_kf)]).astype(np.float32))
+    pn = po + 1e-3
+    cws = torch.empty(gs2d.gs2d_map_correct_workspace(n_kf), dtype=torch.uint8, device="cuda")
+    counts = torch.zeros(4, dtype=torch.int32, device="cuda")
+    prm = gs2d.StateParams(0.5, 20, 0, -1)
+    pose = gs2d.pose_tensor(scenes.identity_pose())
+    cam = scenes.Camera(600.0, 600.0, 600.0, 340.0, 1200, 680)
+    rgb, dep = scenes.rgbd_frame(21, cam)
+    rgb, dep = T(rgb), T(dep)
+    u_keep, u_ang = torch.rand(680, 1200, **f), torch.rand(680, 1200, **f)
+    table = gs2d.DeviceVoxelTable(1 << 22, 0.02)
+    table.insert(mu[:1_000_000])
+    new_s = gs2d.DeviceSurfels.from_tensors(torch.empty(cam.width * cam.height, 3, **f),
+                                            torch.empty(cam.width * cam.height, 4, **f),
+                                            torch.empty(cam.width * cam.height, 2, **f),
+                                            torch.empty(cam.width * cam.height, **f),
+                                            torch.empty(cam.width * cam.height, 3, **f))
+    n_new = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ews = torch.empty(gs2d.gs2d_expand_workspace(gs2d.camera(cam)), dtype=torch.uint8,
+                      device="cuda")
+    eprm = gs2d.ExpandParams(0.04, 0.99, 0.05, 9, 0)
+
+    def run():
+        gs2d.gs2d_map_observe(contrib, ds.mu, n, pose, n_kf, prm, st, counts)
+        gs2d.gs2d_map_correct(ds.mu, ds.quat, st.t_c, n, po, pn, n_kf, cws)
+        gs2d.gs2d_map_prune(contrib, st.t_c, n, 7, 0.5, keep)
+        gs2d.gs2d_map_compact(keep, n, ds, st, out, st_o, None, n_out, kws)
+        gs2d.gs2d_expand(rgb, dep, gs2d.camera(cam), pose, u_keep, u_ang, table, eprm, 0,
+                         cam.width * cam.height, new_s, None, n_new, ews)
+
+    return _timed(run, reps)
+
+
+CASES = {"track": case_track, "track_small": case_track_small, "mapping": case_mapping, "uneven": case_uneven, "net": case_net,
          "sort": case_sort, "contrib": case_contrib,
-         "ssim": case_ssim}
+         "ssim": case_ssim, "map": case_map}
 
 
 def main(argv):

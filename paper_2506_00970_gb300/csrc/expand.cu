@@ -9,8 +9,9 @@
 //                  (normal valid, voxel free);
 //   nearest        per point of P_s: the distance to its nearest other point
 //                  of P_s, by an exhaustive search in tiles of 256 points
-//                  staged in shared memory, the candidates split over 8
-//                  blocks per query block and min-combined (exact;
+//                  staged in shared memory, two queries per thread, the
+//                  candidates split over 16 blocks per query block and
+//                  min-combined (exact;
 //                  O(|P_s|^2) flops, a fraction of a millisecond at the
 //                  paper's sparse downsampling);
 //   emit           count + scan + scatter of the created points into the
@@ -225,44 +226,54 @@ __global__ void __launch_bounds__(kExThreads) ps_point_kernel(
 
 // Squared distance from each point of P_s to its nearest other point, as
 // the bits of a non-negative float (ordered like the values) min-combined
-// with atomicMin: blockIdx.y splits the candidates so that small P_s still
-// fill the GPU; the result does not depend on the order of the atomics.
-constexpr int kNnSplit = 8;
+// with atomicMin: each thread takes two queries (every staged candidate is
+// read once for both), blockIdx.y splits the candidates so that small P_s
+// still fill the GPU; the result does not depend on the order of the atomics.
+constexpr int kNnSplit = 16;
+constexpr int kNnQ = 2 * kExThreads;   // queries per block
 __global__ void __launch_bounds__(kExThreads) nearest_kernel(const float4* __restrict__ pts,
                                                             const int32_t* __restrict__ m_dev,
                                                             unsigned* __restrict__ nnd2) {
   __shared__ float4 s_p[kExThreads];
   const int m = *m_dev;
-  const int k0 = blockIdx.x * kExThreads;
+  const int k0 = blockIdx.x * kNnQ;
   if (k0 >= m) return;
   const int per = (m + kNnSplit - 1) / kNnSplit;
   const int c_lo = blockIdx.y * per, c_hi = min(m, c_lo + per);
   if (c_lo >= c_hi) return;
-  const int k = k0 + (int)threadIdx.x;
-  const float4 q = k < m ? pts[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-  float best = INFINITY;
+  const int ka = k0 + (int)threadIdx.x, kb = ka + kExThreads;
+  const float4 qa = ka < m ? pts[ka] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 qb = kb < m ? pts[kb] : make_float4(0.f, 0.f, 0.f, 0.f);
+  float ba = INFINITY, bb = INFINITY;
   for (int j0 = c_lo; j0 < c_hi; j0 += kExThreads) {
     __syncthreads();
     if (j0 + (int)threadIdx.x < c_hi) s_p[threadIdx.x] = pts[j0 + threadIdx.x];
     __syncthreads();
     const int cnt = min(kExThreads, c_hi - j0);
-    if (j0 + cnt <= k0 || j0 >= k0 + kExThreads) {
+    if (j0 + cnt <= k0 || j0 >= k0 + kNnQ) {
       // no query of this block among these candidates: no self test
+#pragma unroll 4
       for (int j = 0; j < cnt; ++j) {
         const float4 c = s_p[j];
-        const float dx = c.x - q.x, dy = c.y - q.y, dz = c.z - q.z;
-        best = fminf(best, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        const float ax = c.x - qa.x, ay = c.y - qa.y, az = c.z - qa.z;
+        const float bx = c.x - qb.x, by = c.y - qb.y, bz = c.z - qb.z;
+        ba = fminf(ba, fmaf(ax, ax, fmaf(ay, ay, az * az)));
+        bb = fminf(bb, fmaf(bx, bx, fmaf(by, by, bz * bz)));
       }
     } else {
       for (int j = 0; j < cnt; ++j) {
         const float4 c = s_p[j];
-        const float dx = c.x - q.x, dy = c.y - q.y, dz = c.z - q.z;
-        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (j0 + j != k) best = fminf(best, d2);
+        const float ax = c.x - qa.x, ay = c.y - qa.y, az = c.z - qa.z;
+        const float bx = c.x - qb.x, by = c.y - qb.y, bz = c.z - qb.z;
+        const float da = fmaf(ax, ax, fmaf(ay, ay, az * az));
+        const float db = fmaf(bx, bx, fmaf(by, by, bz * bz));
+        if (j0 + j != ka) ba = fminf(ba, da);
+        if (j0 + j != kb) bb = fminf(bb, db);
       }
     }
   }
-  if (k < m && best < INFINITY) atomicMin(nnd2 + k, __float_as_uint(best));
+  if (ka < m && ba < INFINITY) atomicMin(nnd2 + ka, __float_as_uint(ba));
+  if (kb < m && bb < INFINITY) atomicMin(nnd2 + kb, __float_as_uint(bb));
 }
 
 struct EmitArgs {
@@ -437,7 +448,7 @@ int gs2d_expand(const float* rgb, const float* depth, const gs2d_camera* cam, co
   ps_point_kernel<<<pb, kExThreads, 0, s>>>(depth, *cam, pose_cw, w.idx, w.m, tb, table ? 1 : 0, w.pts,
                                             w.nrm, w.create, w.nnd2);
   GS2D_LAUNCH_CHECK();
-  nearest_kernel<<<dim3(pb, kNnSplit), kExThreads, 0, s>>>(w.pts, w.m, w.nnd2);
+  nearest_kernel<<<dim3((P + kNnQ - 1) / kNnQ, kNnSplit), kExThreads, 0, s>>>(w.pts, w.m, w.nnd2);
   GS2D_LAUNCH_CHECK();
   const FlagPred fp{w.create};
   select_count_kernel<FlagPred><<<nb, kExThreads, 0, s>>>(fp, P, w.m, w.blk2);

@@ -138,15 +138,19 @@ __global__ void __launch_bounds__(kMapThreads) map_prune_kernel(const float* __r
     keep[i] = (t_c[i] == r && contrib[i] < thr) ? 0 : 1;
 }
 
-// Compaction, pass 1: kept items per block of kCompactBlock.
+// Compaction, pass 1: kept items per block of kCompactBlock (item
+// base + k * 256 + thread for k < 4: each warp access is 32 consecutive items).
 __global__ void __launch_bounds__(kMapThreads) compact_count_kernel(const uint8_t* __restrict__ keep,
                                                                     int n,
                                                                     int32_t* __restrict__ blk) {
   __shared__ int s_w[kMapThreads / 32];
-  const int base = blockIdx.x * kCompactBlock + threadIdx.x * kCompactPer;
+  const int base = blockIdx.x * kCompactBlock + threadIdx.x;
   int c = 0;
 #pragma unroll
-  for (int k = 0; k < kCompactPer; ++k) c += (base + k < n && keep[base + k]) ? 1 : 0;
+  for (int k = 0; k < kCompactPer; ++k) {
+    const int i = base + k * kMapThreads;
+    c += (i < n && keep[i]) ? 1 : 0;
+  }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
   if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
@@ -181,29 +185,24 @@ __device__ __forceinline__ void copy_n(const T* __restrict__ in, T* __restrict__
   for (int k = 0; k < w; ++k) out[(size_t)o * w + k] = in[(size_t)i * w + k];
 }
 
-// Pass 3: scatter every kept item to its slot.
+// Pass 3: scatter every kept item to its slot.  The block's items are taken
+// in four rounds of 256 consecutive items (coalesced loads and, for runs of
+// kept items, coalesced stores), each round ranked by a block scan.
 __global__ void __launch_bounds__(kMapThreads) compact_scatter_kernel(
     const uint8_t* __restrict__ keep, int n, const int32_t* __restrict__ blk, gs2d_surfels s,
     gs2d_map_state st, float* __restrict__ mu_o, float* __restrict__ quat_o,
     float* __restrict__ scale_o, float* __restrict__ opac_o, float* __restrict__ rgb_o,
     gs2d_map_state so, int32_t* __restrict__ new_index) {
   __shared__ int s_w[kMapThreads / 32];
-  const int base = blockIdx.x * kCompactBlock + threadIdx.x * kCompactPer;
-  bool kf[kCompactPer];
-  int c = 0;
-#pragma unroll
+  int carry = blk[blockIdx.x];
   for (int k = 0; k < kCompactPer; ++k) {
-    kf[k] = base + k < n && keep[base + k];
-    c += kf[k] ? 1 : 0;
-  }
-  int total;
-  int o = blk[blockIdx.x] + block_exscan256(c, s_w, &total);
-#pragma unroll
-  for (int k = 0; k < kCompactPer; ++k) {
-    const int i = base + k;
-    if (i >= n) break;
-    if (new_index) new_index[i] = kf[k] ? o : -1;
-    if (!kf[k]) continue;
+    const int i = blockIdx.x * kCompactBlock + k * kMapThreads + (int)threadIdx.x;
+    const bool kf = i < n && keep[i];
+    int total;
+    const int o = carry + block_exscan256(kf ? 1 : 0, s_w, &total);
+    carry += total;
+    if (i < n && new_index) new_index[i] = kf ? o : -1;
+    if (!kf) continue;
     copy_n(s.mu, mu_o, i, o, 3);
     reinterpret_cast<float4*>(quat_o)[o] = reinterpret_cast<const float4*>(s.quat)[i];
     copy_n(s.scale, scale_o, i, o, 2);
@@ -213,7 +212,6 @@ __global__ void __launch_bounds__(kMapThreads) compact_scatter_kernel(
     if (st.t_c) so.t_c[o] = st.t_c[i];
     if (st.d_c) so.d_c[o] = st.d_c[i];
     if (st.t_l) so.t_l[o] = st.t_l[i];
-    ++o;
   }
 }
 
