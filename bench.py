@@ -40,7 +40,7 @@ WORKLOAD = ("tracking-scale room: 200k surfels on a 5x4x3 m room with 20 boxes/s
             "fx=fy=525, target at ground truth + N(0, 1 mm) depth noise, 100 pose-only iterations "
             "from a 2 cm / 1 deg perturbation")
 ORACLE_CROP = 64          # reference arm: a 64x64 pixel crop per step (~1 s of host work)
-BASELINE_CROP = 192       # cpu_baseline: one 192x192 crop (~10 s of host work)
+CPU_SAMPLE_CROP = 192       # cpu_baseline: one 192x192 crop (~10 s of host work)
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes per launch of the roofline kernel from an ncu capture of the
 # same workload (profiles/track_tile_tracking_640x480.md); None if the kernel
@@ -903,8 +903,8 @@ def cpu_baseline(s, cam, fr):
     200k surfels (every host core via OpenMP)."""
     import oracle
     from paper_2506_00970_gb300 import scenes
-    y0, x0 = cam.height // 2 - BASELINE_CROP // 2, cam.width // 2 - BASELINE_CROP // 2
-    ys, xs = np.mgrid[y0:y0 + BASELINE_CROP, x0:x0 + BASELINE_CROP]
+    y0, x0 = cam.height // 2 - CPU_SAMPLE_CROP // 2, cam.width // 2 - CPU_SAMPLE_CROP // 2
+    ys, xs = np.mgrid[y0:y0 + CPU_SAMPLE_CROP, x0:x0 + CPU_SAMPLE_CROP]
     pix = np.stack([xs.ravel(), ys.ravel()], 1).astype(np.int32)
     obs_rgb = fr["obs_rgb"].cpu().numpy()[ys, xs].reshape(-1, 3)
     obs_d = fr["obs_depth"].cpu().numpy()[ys, xs].reshape(-1)
@@ -920,7 +920,7 @@ def cpu_baseline(s, cam, fr):
                       pixels=pix)
     dt = time.perf_counter() - t0
     return {"value": len(pix) / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"FP64 fwd + pose bwd of a {BASELINE_CROP}x{BASELINE_CROP} crop of one "
+            "sample": f"FP64 fwd + pose bwd of a {CPU_SAMPLE_CROP}x{CPU_SAMPLE_CROP} crop of one "
                       f"640x480 frame, all {N_SURFELS} surfels", "seconds": dt}
 
 

@@ -17,7 +17,7 @@
 //   * G(u, v) = exp(-(u^2 + v^2) / 2) (Sec. III-A), a = alpha G;
 //   * front-to-back alpha blending of colour, depth z, normal t_nc and
 //     opacity (Eq. alpha_blending), surfels ordered by (centre depth, id).
-// Readings of points the paper leaves open (all documented in the design doc):
+// Readings of points the paper leaves open:
 //   * a = min(alpha G, alpha_max); a surfel is skipped if a < alpha_min or
 //     u^2+v^2 > cutoff_r2; blending stops before the surfel whose inclusion
 //     would drive the transmittance below t_min.  "exact" mode disables the

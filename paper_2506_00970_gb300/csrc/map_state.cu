@@ -2,7 +2,7 @@
 // Sec. III-F, the map correction of Sec. IV-C, the occlusion pruning of
 // Sec. III-F and a stable compaction of the surfel arrays.  All of them are
 // one pass over the map's structure-of-arrays: HBM-bound, grid-stride loops
-// over 4 x 152 x 8 blocks at most, loads and stores coalesced per array.
+// over at most 152 x 32 blocks, loads and stores coalesced per array.
 #include "gs2d_common.cuh"
 #include "gs2d_internal.h"
 #include "gs2d_map.h"
