@@ -52,6 +52,8 @@ UNEVEN_SURFELS, UNEVEN_VIEWS = 2_000_000, 32
 MAP_W_D, MAP_W_N = 0.5, 0.02
 # learned proposal: training pairs, AdamW steps at batch 256, held-out frames
 PROP_PAIRS, PROP_STEPS, PROP_EVAL_FRAMES = 100_000, 6000, 256
+# the network refines its own proposal once (two passes of proposal + acceptance test)
+PROP_PASSES = 2
 
 
 def _args():
@@ -875,7 +877,9 @@ def learned_proposal(flush):
             step_ms.append(e[1].elapsed_time(e[2]))
     del X, Y
     torch.cuda.empty_cache()
-    ev = proposal.evaluate(scenes.room_scene(200, N_SURFELS), tr.params, PROP_EVAL_FRAMES, seed=3)
+    held_out = scenes.room_scene(200, N_SURFELS)
+    ev = proposal.evaluate(held_out, tr.params, PROP_EVAL_FRAMES, seed=3, passes=PROP_PASSES)
+    one = proposal.evaluate(held_out, tr.params, PROP_EVAL_FRAMES, seed=3, passes=1)
     fl_f, fl_t = net_flops_per_sample()
     pk, _ = peaks()
     peak = float(pk.get("bf16_tflops", 1900.0))
@@ -884,6 +888,12 @@ def learned_proposal(flush):
         "train_pairs": PROP_PAIRS, "train_steps": PROP_STEPS, "batch": 256,
         "pair_gen_s": gen_s, "train_s": train_s, "train_loss": hist,
         "held_out_room": "room seed 200 (training rooms 100-103)",
+        "proposal_passes": PROP_PASSES,
+        "single_pass": {"learned_ms_median": one["learned"]["ms_to_1cm_0.5deg_median"],
+                        "learned_iters_median": one["learned"]["iters_median"],
+                        "proposal_ms": one["proposal_ms"],
+                        "proposal_err_median_cm_deg": one["proposal_err_median_cm_deg"],
+                        "speedup_median": one["speedup_median"]},
         "net": {"fwd_batch256_ms": f_ms, "train_step_batch256_ms": s_ms,
                 "fwd_gflop_per_batch": fl_f * 256 / 1e9, "train_gflop_per_batch": fl_t * 256 / 1e9,
                 "roofline": {"kernel": "network forward: gemm_kernel (mma.sync bf16) for the convolution "

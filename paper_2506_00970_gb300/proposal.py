@@ -154,11 +154,15 @@ class Proposer:
     """One frame's proposal as a fixed launch sequence (capturable in a CUDA
     graph, no host round trip): render at the current pose, tracking loss
     there, pack with the observation, network forward, apply, render at the
-    proposal, tracking loss there, keep the better pose."""
+    proposal, tracking loss there, keep the better pose.  With passes > 1 the
+    sequence repeats from the kept pose (the network refines its own
+    proposal)."""
 
-    def __init__(self, surf: gs2d.DeviceSurfels, params, capacity: int, device="cuda"):
+    def __init__(self, surf: gs2d.DeviceSurfels, params, capacity: int, device="cuda",
+                 passes: int = 1):
         self.surf = surf
         self.params = params
+        self.passes = int(passes)
         self.r = gs2d.Rasterizer(CAM, surf.n, capacity=capacity, device=device)
         f = dict(dtype=torch.float32, device=device)
         self.pose = torch.empty(1, 12, **f)
@@ -189,16 +193,18 @@ class Proposer:
 
     def run(self):
         r = self.r
-        self._render(self.pose[0])
-        self._loss(self.loss_init)
-        gs2d.gs2d_net_pack_input(r.rgb[None], r.depth[None], r.opacity[None], self.obs_rgb[None],
-                                 self.obs_d[None], self.x)
-        gs2d.gs2d_net_forward(self.params, self.x, self.y, self.ws)
-        self.prop.copy_(self.pose)
-        gs2d.gs2d_net_apply(self.y, self.prop)
-        self._render(self.prop[0])
-        self._loss(self.loss_prop)
-        gs2d.gs2d_net_accept(self.loss_prop, self.loss_init, self.prop, self.pose, self.accepted)
+        for _ in range(self.passes):
+            self._render(self.pose[0])
+            self._loss(self.loss_init)
+            gs2d.gs2d_net_pack_input(r.rgb[None], r.depth[None], r.opacity[None],
+                                     self.obs_rgb[None], self.obs_d[None], self.x)
+            gs2d.gs2d_net_forward(self.params, self.x, self.y, self.ws)
+            self.prop.copy_(self.pose)
+            gs2d.gs2d_net_apply(self.y, self.prop)
+            self._render(self.prop[0])
+            self._loss(self.loss_prop)
+            gs2d.gs2d_net_accept(self.loss_prop, self.loss_init, self.prop, self.pose,
+                                 self.accepted)
 
     def status(self) -> int:
         return int(self.r.status.item())
@@ -234,7 +240,8 @@ def timed_replays(graph, reps: int, before=None) -> list[float]:
     return out
 
 
-def evaluate(scene, params, n_frames: int, seed: int, n_iter: int = 100, device="cuda"):
+def evaluate(scene, params, n_frames: int, seed: int, n_iter: int = 100, device="cuda",
+             passes: int = 1):
     """Plain loop vs proposal + loop on held-out frames of one room: per frame
     the iterations to 1 cm / 0.5 degrees (pose history of the fused tracking
     step), the proposal's own error, and the GPU time of one proposal and of
@@ -262,7 +269,7 @@ def evaluate(scene, params, n_frames: int, seed: int, n_iter: int = 100, device=
     del vr
     cap = 4 * kmax + 4096
     # the proposal, one frame per replay
-    pr = Proposer(ds, params, cap, device)
+    pr = Proposer(ds, params, cap, device, passes=passes)
     pr.pose.copy_(poses_tensor(inits[:1], device))
     pr.obs_rgb.copy_(obs_rgb[0])
     pr.obs_d.copy_(obs_d[0])
