@@ -54,6 +54,7 @@ MAP_W_D, MAP_W_N = 0.5, 0.02
 PROP_PAIRS, PROP_STEPS, PROP_EVAL_FRAMES = 100_000, 6000, 256
 # the network refines its own proposal once (two passes of proposal + acceptance test)
 PROP_PASSES = 2
+PROP_TRACK_FRAMES = 32    # tracking-workload frames for the proposal at tracking scale
 
 
 def _args():
@@ -351,6 +352,7 @@ def run_ours(args):
     batch = batch_workloads(K, W_, flush)
     maint = map_maintenance(flush)
     tracking["learned_proposal"] = learned_proposal(flush)
+    tracking["learned_proposal_tracking_scale"] = tracking_scale_proposal(rank)
 
     if rank == 0:
         clocks = clk.summary()
@@ -904,6 +906,36 @@ def learned_proposal(flush):
                              "train_achieved": fl_t * 256 / (s_ms / 1e3) / 1e12,
                              "peak_note": "dense bf16, of measured (cuBLAS burst)"}},
     })
+    return ev
+
+
+def tracking_scale_proposal(rank):
+    """The learned proposal on the tracking workload itself: a network for the
+    tracking camera's 160x120 view (640x480 / 4, fx = fy = 131.25) trained on
+    self-rendered pairs of rooms 100-103, then frames of the tracking room
+    (seed 0, 2 cm / 1 deg starts): proposal at 160x120 from the
+    box-downsampled observation, the full-resolution plain loop from the kept
+    pose, against the plain loop from the usual start."""
+    import torch
+    from paper_2506_00970_gb300 import proposal, scenes
+    _, cam, ds, _, frames, _ = make_frames(PROP_TRACK_FRAMES, rank)
+    lo = proposal.low_res_camera(cam, 4)
+    t0 = time.perf_counter()
+    rooms = [scenes.room_scene(100 + r, N_SURFELS) for r in range(4)]
+    X, Y = proposal.make_pairs(rooms, PROP_PAIRS, seed=11, cam=lo)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    tr = proposal.Trainer(seed=0, batch=256)
+    t0 = time.perf_counter()
+    tr.fit(X, Y, PROP_STEPS, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del X, Y
+    torch.cuda.empty_cache()
+    ev = proposal.evaluate_full_res(ds, tr.params, cam, frames, passes=PROP_PASSES)
+    ev.update({"train_pairs": PROP_PAIRS, "train_steps": PROP_STEPS, "pair_gen_s": gen_s,
+               "train_s": train_s, "train_rooms": "room seeds 100-103",
+               "frames_room": "room seed 0 (the tracking frames' room, not in training)"})
     return ev
 
 

@@ -75,6 +75,14 @@ int gs2d_net_pack_input(const float* r_rgb, const float* r_depth, const float* r
                         const float* o_rgb, const float* o_depth, int batch, int height,
                         int width, uint16_t* x, gs2d_stream stream);
 
+/* The network's view of a full-resolution observation: rgb [H*W*3] and
+ * depth [H*W] box-downsampled by an integer factor (H and W multiples of
+ * it) to rgb_out [(H/f)*(W/f)*3] (block mean) and depth_out [(H/f)*(W/f)]
+ * (mean of the block's valid depths, 0 if none); e.g. 640 x 480 -> 160 x 120
+ * with f = 4, the camera's fx, fy, cx, cy divided by f. */
+int gs2d_net_downsample_rgbd(const float* rgb, const float* depth, int height, int width,
+                             int factor, float* rgb_out, float* depth_out, gs2d_stream stream);
+
 /* Forward pass: y [batch * 6] (FP32) from x [batch * 120 * 160 * 8]. */
 int gs2d_net_forward(const float* params, const uint16_t* x, int batch, float* y,
                      void* workspace, size_t ws_bytes, size_t* ws_needed, gs2d_stream stream);

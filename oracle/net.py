@@ -210,6 +210,21 @@ def pack_input(r_rgb, r_depth, r_opacity, o_rgb, o_depth):
     return to_bf16(np.concatenate([r_rgb, dr[..., None], o_rgb, do[..., None]], axis=-1))
 
 
+def downsample_rgbd(rgb, depth, factor):
+    """The network's view of a full-resolution observation: colour averaged
+    over factor x factor blocks, depth the mean of each block's valid
+    (finite, positive) values, 0 where a block has none."""
+    rgb = np.asarray(rgb, np.float64)
+    d = np.asarray(depth, np.float64)
+    H, W = d.shape
+    f = int(factor)
+    c = rgb.reshape(H // f, f, W // f, f, 3).mean(axis=(1, 3))
+    ok = np.isfinite(d) & (d > 0)
+    s = np.where(ok, d, 0.0).reshape(H // f, f, W // f, f).sum(axis=(1, 3))
+    k = ok.reshape(H // f, f, W // f, f).sum(axis=(1, 3))
+    return c, np.where(k > 0, s / np.maximum(k, 1), 0.0)
+
+
 def target_delta(T_init, T_gt):
     """delta* with Exp(delta* * TAU_SCALE) T_init = T_gt."""
     R = T_gt.R @ T_init.R.T

@@ -686,6 +686,41 @@ __global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ y,
   if (threadIdx.x == 0) *loss = 0.5f * s[0] * inv;
 }
 
+// Box downsampling of an observed RGB-D frame by an integer factor: each
+// output pixel is the mean colour of its factor x factor block and the mean
+// of the block's valid (finite, positive) depths, 0 if it has none.  Sums in
+// row-major order within the block.
+__global__ void __launch_bounds__(256) downsample_kernel(const float* __restrict__ rgb,
+                                                         const float* __restrict__ depth, int W,
+                                                         int f, int wo, int n,
+                                                         float* __restrict__ rgb_out,
+                                                         float* __restrict__ depth_out) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n) return;
+  const int oy = o / wo, ox = o % wo;
+  float r = 0.f, g = 0.f, b = 0.f, d = 0.f;
+  int nd = 0;
+  for (int dy = 0; dy < f; ++dy) {
+    const size_t row = (size_t)(oy * f + dy) * W + (size_t)ox * f;
+    for (int dx = 0; dx < f; ++dx) {
+      const size_t p = row + dx;
+      r += rgb[3 * p];
+      g += rgb[3 * p + 1];
+      b += rgb[3 * p + 2];
+      const float z = depth[p];
+      if (z > 0.f && z < INFINITY) {
+        d += z;
+        ++nd;
+      }
+    }
+  }
+  const float inv = 1.f / (float)(f * f);
+  rgb_out[3 * o] = r * inv;
+  rgb_out[3 * o + 1] = g * inv;
+  rgb_out[3 * o + 2] = b * inv;
+  depth_out[o] = nd ? d / (float)nd : 0.f;
+}
+
 __global__ void pack_kernel(const float* __restrict__ r_rgb, const float* __restrict__ r_d,
                             const float* __restrict__ r_o, const float* __restrict__ o_rgb,
                             const float* __restrict__ o_d, size_t n_px, bf16* __restrict__ x) {
@@ -1245,6 +1280,19 @@ int gs2d_net_layout(size_t* w_off, size_t* b_off, int* fan_in) {
 size_t gs2d_net_workspace(int batch) {
   if (batch <= 0) return 0;
   return carve(nullptr, batch).bytes;
+}
+
+int gs2d_net_downsample_rgbd(const float* rgb, const float* depth, int height, int width,
+                             int factor, float* rgb_out, float* depth_out, gs2d_stream stream) {
+  if (height <= 0 || width <= 0 || factor <= 0 || height % factor || width % factor || !rgb ||
+      !depth || !rgb_out || !depth_out)
+    return GS2D_ERR_INVALID_ARG;
+  const int ho = height / factor, wo = width / factor;
+  const int n = ho * wo;
+  gs2d::net::downsample_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
+      rgb, depth, width, factor, wo, n, rgb_out, depth_out);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
 }
 
 int gs2d_net_pack_input(const float* r_rgb, const float* r_depth, const float* r_opacity,

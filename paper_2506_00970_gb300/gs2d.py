@@ -113,7 +113,8 @@ EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_stri
            "gs2d_map_prune", "gs2d_map_compact_workspace", "gs2d_map_compact",
            "gs2d_mapping_loss_ssim_workspace", "gs2d_mapping_loss_ssim", "gs2d_ssim_workspace",
            "gs2d_ssim_loss", "gs2d_voxel_clear", "gs2d_voxel_insert", "gs2d_voxel_query",
-           "gs2d_expand_workspace", "gs2d_expand", "gs2d_map_expand_values"]
+           "gs2d_expand_workspace", "gs2d_expand", "gs2d_map_expand_values",
+           "gs2d_net_downsample_rgbd"]
 
 NET_LAYERS = 8
 NET_IN = (120, 160, 8)
@@ -179,6 +180,7 @@ def lib():
         L.gs2d_net_apply.argtypes = [vp, ip, vp, vp]
         L.gs2d_net_target.argtypes = [vp, vp, ip, vp, vp]
         L.gs2d_net_accept.argtypes = [vp, vp, vp, ip, vp, vp, vp]
+        L.gs2d_net_downsample_rgbd.argtypes = [vp, vp, ip, ip, ip, vp, vp, vp]
         L.gs2d_render_contrib_workspace.restype = sz
         L.gs2d_render_contrib_workspace.argtypes = [sz]
         L.gs2d_render_contrib.argtypes = [vp, vp, vp, ip, vp, vp, vp, vp, sz, vp, vp]
@@ -627,6 +629,13 @@ def gs2d_net_pack_input(r_rgb, r_depth, r_opacity, o_rgb, o_depth, x, stream=Non
     check(lib().gs2d_net_pack_input(_ptr(r_rgb), _ptr(r_depth), _ptr(r_opacity), _ptr(o_rgb),
                                     _ptr(o_depth), B, H, W, _ptr(x), _stream(stream)),
           "gs2d_net_pack_input")
+
+
+def gs2d_net_downsample_rgbd(rgb, depth, factor, rgb_out, depth_out, stream=None):
+    H, W = int(depth.shape[-2]), int(depth.shape[-1])
+    check(lib().gs2d_net_downsample_rgbd(_ptr(rgb), _ptr(depth), H, W, int(factor), _ptr(rgb_out),
+                                         _ptr(depth_out), _stream(stream)),
+          "gs2d_net_downsample_rgbd")
 
 
 def gs2d_net_forward(params, x, y, workspace, stream=None):

@@ -59,12 +59,13 @@ def observed_depth(depth, opacity, gen, sigma=1e-3):
 
 
 class ViewRenderer:
-    """Forward renders of up to VIEWS poses of CAM per batched call."""
+    """Forward renders of up to VIEWS poses of a 160x120 camera (CAM by
+    default) per batched call."""
 
-    def __init__(self, surf: gs2d.DeviceSurfels, views: int = VIEWS):
+    def __init__(self, surf: gs2d.DeviceSurfels, views: int = VIEWS, cam=CAM):
         self.surf = surf
         self.views = views
-        self.br = gs2d.BatchRasterizer([CAM] * views, surf.n, capacities=[3 * surf.n] * views)
+        self.br = gs2d.BatchRasterizer([cam] * views, surf.n, capacities=[3 * surf.n] * views)
 
     def render(self, poses_t):
         n = poses_t.shape[0]
@@ -74,10 +75,10 @@ class ViewRenderer:
         return self.br.stacked
 
 
-def make_pairs(rooms, n_pairs: int, seed: int, device="cuda"):
+def make_pairs(rooms, n_pairs: int, seed: int, device="cuda", cam=CAM):
     """Training pairs over the given rooms (Surfels): x [n, 120, 160, 8]
     bfloat16 (rendered at the perturbed pose + observed at ground truth) and
-    the target y* [n, 6]."""
+    the target y* [n, 6]; ``cam``: the network's 160x120 camera."""
     X = torch.empty(n_pairs, 120, 160, 8, dtype=torch.bfloat16, device=device)
     Y = torch.empty(n_pairs, 6, device=device)
     gen = torch.Generator(device=device)
@@ -86,7 +87,7 @@ def make_pairs(rooms, n_pairs: int, seed: int, device="cuda"):
     i = 0
     for r, s in enumerate(rooms):
         ds = gs2d.DeviceSurfels(s)
-        vr = ViewRenderer(ds)
+        vr = ViewRenderer(ds, cam=cam)
         obs_rgb = torch.empty(VIEWS, 120, 160, 3, device=device)
         obs_d = torch.empty(VIEWS, 120, 160, device=device)
         c0 = 0
@@ -159,11 +160,11 @@ class Proposer:
     proposal)."""
 
     def __init__(self, surf: gs2d.DeviceSurfels, params, capacity: int, device="cuda",
-                 passes: int = 1):
+                 passes: int = 1, cam=CAM):
         self.surf = surf
         self.params = params
         self.passes = int(passes)
-        self.r = gs2d.Rasterizer(CAM, surf.n, capacity=capacity, device=device)
+        self.r = gs2d.Rasterizer(cam, surf.n, capacity=capacity, device=device)
         f = dict(dtype=torch.float32, device=device)
         self.pose = torch.empty(1, 12, **f)
         self.prop = torch.empty(1, 12, **f)
@@ -344,5 +345,97 @@ def evaluate(scene, params, n_frames: int, seed: int, n_iter: int = 100, device=
                     "accepted_frac": float(np.mean(res["accepted"]))},
         "speedup_median": float(np.median(plain_ms) / max(np.median(learned_ms), 1e-9)),
         "start_err_median_cm_deg": [float(np.median(st[:, 0]) * 100), float(np.median(st[:, 1]))],
+        "proposal_err_median_cm_deg": [float(np.median(pp[:, 0]) * 100), float(np.median(pp[:, 1]))],
+    }
+
+
+def low_res_camera(cam, factor: int):
+    """The network's camera for a full-resolution one: intrinsics and size
+    divided by ``factor`` (the pixel grid of gs2d_net_downsample_rgbd)."""
+    return scenes.Camera(cam.fx / factor, cam.fy / factor, cam.cx / factor, cam.cy / factor,
+                         cam.width // factor, cam.height // factor)
+
+
+def evaluate_full_res(surf: gs2d.DeviceSurfels, params, cam, frames, passes: int = 2,
+                      n_iter: int = 100, device="cuda"):
+    """Tracking at full resolution from the network's proposal: per frame the
+    observation (full-resolution RGB-D) is box-downsampled to the network's
+    160x120 view, the proposal (``passes`` passes with the acceptance test)
+    runs at that resolution, and the full-resolution plain loop refines the
+    kept pose; against the plain loop from the usual start.  ``frames``:
+    dicts with gt (Pose), start_t [12], obs_rgb [H, W, 3], obs_depth [H, W]
+    on the device.  Reports iterations and GPU time (CUDA graph replays) to
+    1 cm / 0.5 degrees."""
+    factor = cam.width // 160
+    lo = low_res_camera(cam, factor)
+    cap = 8 * surf.n
+    pr = Proposer(surf, params, cap, device, passes=passes, cam=lo)
+    obs_rgb = torch.empty(cam.height, cam.width, 3, device=device)
+    obs_d = torch.empty(cam.height, cam.width, device=device)
+
+    def propose():
+        gs2d.gs2d_net_downsample_rgbd(obs_rgb, obs_d, factor, pr.obs_rgb, pr.obs_d)
+        pr.run()
+
+    pr.pose.copy_(frames[0]["start_t"][None])
+    obs_rgb.copy_(frames[0]["obs_rgb"])
+    obs_d.copy_(frames[0]["obs_depth"])
+    pg = capture(propose)
+    ccam, cfg = gs2d.camera(cam), gs2d.default_config()
+    prm = gs2d.default_track_params(stop_tol=0.0)
+    tws = torch.empty(gs2d.gs2d_track_workspace(surf.n, cap, ccam, cfg), dtype=torch.uint8,
+                      device=device)
+    tpose = torch.empty(12, device=device)
+    lh = torch.zeros(n_iter, device=device)
+    ph = torch.zeros(n_iter, 12, device=device)
+    tpose.copy_(frames[0]["start_t"])
+
+    def track():
+        gs2d.gs2d_track_step(surf, ccam, cfg, prm, tpose, obs_rgb, obs_d, n_iter, cap, lh, ph, tws)
+
+    tg = capture(track)
+    res = dict(plain_it=[], learned_it=[], prop=[], accepted=[])
+    prop_ms, iter_ms = [], []
+    for fr in frames:
+        gt = fr["gt"]
+        obs_rgb.copy_(fr["obs_rgb"])
+        obs_d.copy_(fr["obs_depth"])
+        tpose.copy_(fr["start_t"])
+        iter_ms += [m / n_iter for m in timed_replays(tg, 1)]
+        if int(gs2d.gs2d_track_status(tws).item()) not in (0, gs2d.CONVERGED):
+            raise gs2d.Gs2dError("tracking status")
+        res["plain_it"].append(first_below(ph.cpu().numpy(), gt))
+        pr.pose.copy_(fr["start_t"][None])
+        prop_ms += timed_replays(pg, 1)
+        if pr.status() != 0:
+            raise gs2d.Gs2dError(f"proposal render status {pr.status()}")
+        res["accepted"].append(int(pr.accepted.item()))
+        start = pr.pose[0].clone()
+        e = pose_error(start.cpu().numpy(), gt)
+        res["prop"].append(e)
+        if e[0] < 0.01 and e[1] < 0.5:
+            res["learned_it"].append(0)
+            continue
+        tpose.copy_(start)
+        timed_replays(tg, 1)
+        res["learned_it"].append(first_below(ph.cpu().numpy(), gt))
+    ms_iter = float(np.median(iter_ms))
+    ms_prop = float(np.median(prop_ms))
+    cap_it = lambda v: n_iter if v is None else v
+    plain_ms = np.array([cap_it(v) * ms_iter for v in res["plain_it"]])
+    learned_ms = np.array([ms_prop + cap_it(v) * ms_iter for v in res["learned_it"]])
+    pp = np.array(res["prop"])
+    return {
+        "frames": len(frames), "ms_per_iter": ms_iter, "proposal_ms": ms_prop,
+        "proposal_passes": passes, "network_camera": [lo.fx, lo.fy, lo.cx, lo.cy, lo.width,
+                                                      lo.height],
+        "plain": {"ms_to_1cm_0.5deg_median": float(np.median(plain_ms)),
+                  "iters_median": float(np.median([cap_it(v) for v in res["plain_it"]])),
+                  "reached": int(sum(v is not None for v in res["plain_it"]))},
+        "learned": {"ms_to_1cm_0.5deg_median": float(np.median(learned_ms)),
+                    "iters_median": float(np.median([cap_it(v) for v in res["learned_it"]])),
+                    "reached": int(sum(v is not None for v in res["learned_it"])),
+                    "accepted_frac": float(np.mean(res["accepted"]))},
+        "speedup_median": float(np.median(plain_ms) / max(np.median(learned_ms), 1e-9)),
         "proposal_err_median_cm_deg": [float(np.median(pp[:, 0]) * 100), float(np.median(pp[:, 1]))],
     }

@@ -86,20 +86,36 @@ def _random_unit(rng: np.random.Generator, n: int) -> np.ndarray:
     return v / np.linalg.norm(v, axis=1, keepdims=True)
 
 
+def _cross(a, b):
+    return (a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0])
+
+
+def _unit(a):
+    n = math.sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2])
+    return (a[0] / n, a[1] / n, a[2] / n)
+
+
 def look_at(eye, target, down=(0.0, 0.0, -1.0)) -> Pose:
     """World->camera pose of a camera at ``eye`` looking at ``target``.
 
     Camera x points right, y down, z forward; the world z axis is up.
     """
-    eye = np.asarray(eye, float)
-    f = np.asarray(target, float) - eye
-    f /= np.linalg.norm(f)
-    x = np.cross(np.asarray(down, float), f)
-    x /= np.linalg.norm(x)
-    y = np.cross(f, x)
-    R_wc = np.stack([x, y, f], axis=1)
-    R = R_wc.T
-    return Pose(R, -R @ eye)
+    e = [float(v) for v in eye]
+    f = _unit([float(target[k]) - e[k] for k in range(3)])
+    x = _unit(_cross([float(v) for v in down], f))
+    y = _cross(f, x)
+    R = np.array([x, y, f])                      # rows: the camera axes in world coordinates
+    return Pose(R, -(R @ np.array(e)))
+
+
+def _rodrigues(axis, angle: float) -> np.ndarray:
+    """Rotation by ``angle`` (radians) about the unit ``axis``."""
+    kx, ky, kz = (float(v) for v in axis)
+    c, s = math.cos(angle), math.sin(angle)
+    v = 1.0 - c
+    return np.array([[c + kx * kx * v, kx * ky * v - kz * s, kx * kz * v + ky * s],
+                     [ky * kx * v + kz * s, c + ky * ky * v, ky * kz * v - kx * s],
+                     [kz * kx * v - ky * s, kz * ky * v + kx * s, c + kz * kz * v]])
 
 
 def perturb_pose(pose: Pose, trans_m: float, rot_deg: float, seed: int) -> Pose:
@@ -108,7 +124,7 @@ def perturb_pose(pose: Pose, trans_m: float, rot_deg: float, seed: int) -> Pose:
     camera side (left): R' = dR R, t' = dR t + dt."""
     rng = np.random.default_rng(seed)
     axis = _random_unit(rng, 1)[0]
-    dR = Rotation.from_rotvec(axis * math.radians(rot_deg)).as_matrix()
+    dR = _rodrigues(axis, math.radians(rot_deg))
     dt = _random_unit(rng, 1)[0] * trans_m
     return Pose(dR @ pose.R, dR @ pose.t + dt)
 

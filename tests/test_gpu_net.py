@@ -274,3 +274,24 @@ def test_target_and_accept_kernels(torch_cuda):
     assert acc.cpu().tolist() == want
     for b in range(6):
         assert torch.equal(poses[b], prop[b] if want[b] else -torch.ones(12, device="cuda"))
+
+
+def test_downsample_rgbd_matches_oracle(torch_cuda):
+    """640x480 -> 160x120 box downsampling of an observation with holes:
+    block sums of 16 values in FP32 against FP64 (1e-6 relative); blocks
+    without a valid depth are 0 on both sides."""
+    torch = torch_cuda
+    from oracle import net
+    from paper_2506_00970_gb300 import gs2d
+    cam = scenes.tracking_camera()
+    rgb, depth = scenes.rgbd_frame(3, cam, hole_frac=0.3)
+    depth[:8, :8] = 0.0                      # a block of holes
+    c_o, d_o = net.downsample_rgbd(rgb, depth, 4)
+    T = lambda a: torch.tensor(a, device="cuda")
+    c = torch.empty(120, 160, 3, device="cuda")
+    d = torch.empty(120, 160, device="cuda")
+    gs2d.gs2d_net_downsample_rgbd(T(rgb), T(depth), 4, c, d)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(c.cpu().numpy(), c_o, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(d.cpu().numpy(), d_o, rtol=1e-6, atol=0)
+    assert float(d[0, 0]) == 0.0 and float(d[0, 1]) == 0.0

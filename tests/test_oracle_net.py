@@ -177,3 +177,20 @@ def test_net_init_draws_he_normal_weights_and_zero_biases():
             assert np.all(v == 0)
         elif v.size > 5000:
             assert np.std(v) == pytest.approx(net.he_scale(int(np.prod(shape[1:]))), rel=0.05)
+
+
+def test_downsample_rgbd_hand_case():
+    from oracle import net
+    rgb = np.zeros((4, 4, 3))
+    rgb[:2, :2] = 1.0
+    rgb[2:, 2:, 0] = 0.5
+    depth = np.array([[1.0, 3.0, 0.0, 0.0],
+                      [0.0, 2.0, 0.0, 0.0],
+                      [5.0, 5.0, 4.0, np.inf],
+                      [5.0, 5.0, 0.0, 2.0]])
+    c, d = net.downsample_rgbd(rgb, depth, 2)
+    np.testing.assert_allclose(c[0, 0], 1.0)
+    np.testing.assert_allclose(c[1, 1], [0.5, 0.0, 0.0])
+    np.testing.assert_allclose(c[0, 1], 0.0)
+    # means of the valid depths; a block without any is 0
+    np.testing.assert_allclose(d, [[2.0, 0.0], [5.0, 3.0]])
