@@ -939,31 +939,40 @@ def tracking_scale_proposal(rank):
     return ev
 
 
-def cpu_baseline(s, cam, fr):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload:
-    forward + pose backward of a 192x192 pixel crop of one frame against all
-    200k surfels (every host core via OpenMP)."""
+def _oracle_sample(s, cam, fr, crop, n_threads):
+    """Seconds of the FP64 oracle's forward + pose backward (tracking-loss
+    gradient, Eq. tracking_loss) on a crop x crop pixel sample of one frame."""
     import oracle
-    from paper_2506_00970_gb300 import scenes
-    y0, x0 = cam.height // 2 - CPU_SAMPLE_CROP // 2, cam.width // 2 - CPU_SAMPLE_CROP // 2
-    ys, xs = np.mgrid[y0:y0 + CPU_SAMPLE_CROP, x0:x0 + CPU_SAMPLE_CROP]
+    y0, x0 = cam.height // 2 - crop // 2, cam.width // 2 - crop // 2
+    ys, xs = np.mgrid[y0:y0 + crop, x0:x0 + crop]
     pix = np.stack([xs.ravel(), ys.ravel()], 1).astype(np.int32)
     obs_rgb = fr["obs_rgb"].cpu().numpy()[ys, xs].reshape(-1, 3)
     obs_d = fr["obs_depth"].cpu().numpy()[ys, xs].reshape(-1)
-    cores = oracle.default_threads()
     t0 = time.perf_counter()
-    img = oracle.render(s, cam, fr["start"], pixels=pix)
-    # per-pixel L1 gradient of the tracking loss on the sample (Eq. tracking_loss)
+    img = oracle.render(s, cam, fr["start"], pixels=pix, n_threads=n_threads)
     Dh = img["depth"] / np.maximum(img["opacity"], 1e-6)
     m = (img["opacity"] > 0.95).astype(float)
     g_rgb = np.sign(img["rgb"] - obs_rgb) * m[:, None]
     g_d = np.sign(Dh - obs_d) * m / np.maximum(img["opacity"], 1e-6)
     oracle.render_bwd(s, cam, fr["start"], g_rgb, g_d, np.zeros_like(g_rgb), np.zeros_like(g_d),
-                      pixels=pix)
-    dt = time.perf_counter() - t0
-    return {"value": len(pix) / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+                      pixels=pix, n_threads=n_threads)
+    return len(pix), time.perf_counter() - t0
+
+
+def cpu_baseline(s, cam, fr):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    forward + pose backward of a 192x192 pixel crop of one frame against all
+    200k surfels on every host core (OpenMP), and of a 48x48 crop on one."""
+    import oracle
+    cores = oracle.default_threads()
+    n, dt = _oracle_sample(s, cam, fr, CPU_SAMPLE_CROP, cores)
+    n1, dt1 = _oracle_sample(s, cam, fr, CPU_SAMPLE_CROP // 4, 1)
+    return {"value": n / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 fwd + pose bwd of a {CPU_SAMPLE_CROP}x{CPU_SAMPLE_CROP} crop of one "
-                      f"640x480 frame, all {N_SURFELS} surfels", "seconds": dt}
+                      f"640x480 frame, all {N_SURFELS} surfels", "seconds": dt,
+            "single_thread": {"value": n1 / dt1 / 1e6, "unit": UNIT, "cores": 1,
+                              "sample": f"a {CPU_SAMPLE_CROP // 4}x{CPU_SAMPLE_CROP // 4} crop",
+                              "seconds": dt1}}
 
 
 def run_reference(args):
