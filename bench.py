@@ -55,6 +55,9 @@ PROP_PAIRS, PROP_STEPS, PROP_EVAL_FRAMES = 100_000, 6000, 256
 # the network refines its own proposal once (two passes of proposal + acceptance test)
 PROP_PASSES = 2
 PROP_TRACK_FRAMES = 32    # tracking-workload frames for the proposal at tracking scale
+# its network is trained on starts up to 3 cm / 1.5 deg (the tracking frames start 2 cm / 1 deg
+# off); one pass: at full resolution a loop iteration costs a third of a proposal pass
+PROP_TRACK_MAX, PROP_TRACK_PASSES = (0.03, 1.5), 1
 
 
 def _args():
@@ -912,17 +915,19 @@ def learned_proposal(flush):
 def tracking_scale_proposal(rank):
     """The learned proposal on the tracking workload itself: a network for the
     tracking camera's 160x120 view (640x480 / 4, fx = fy = 131.25) trained on
-    self-rendered pairs of rooms 100-103, then frames of the tracking room
-    (seed 0, 2 cm / 1 deg starts): proposal at 160x120 from the
-    box-downsampled observation, the full-resolution plain loop from the kept
-    pose, against the plain loop from the usual start."""
+    self-rendered pairs of rooms 100-103 with starts up to 3 cm / 1.5 deg,
+    then frames of the tracking room (seed 0, 2 cm / 1 deg starts): proposal
+    at 160x120 from the box-downsampled observation, the full-resolution
+    plain loop from the kept pose, against the plain loop from the usual
+    start."""
     import torch
     from paper_2506_00970_gb300 import proposal, scenes
     _, cam, ds, _, frames, _ = make_frames(PROP_TRACK_FRAMES, rank)
     lo = proposal.low_res_camera(cam, 4)
     t0 = time.perf_counter()
     rooms = [scenes.room_scene(100 + r, N_SURFELS) for r in range(4)]
-    X, Y = proposal.make_pairs(rooms, PROP_PAIRS, seed=11, cam=lo)
+    X, Y = proposal.make_pairs(rooms, PROP_PAIRS, seed=11, cam=lo, max_t=PROP_TRACK_MAX[0],
+                               max_deg=PROP_TRACK_MAX[1])
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
     tr = proposal.Trainer(seed=0, batch=256)
@@ -932,9 +937,11 @@ def tracking_scale_proposal(rank):
     train_s = time.perf_counter() - t0
     del X, Y
     torch.cuda.empty_cache()
-    ev = proposal.evaluate_full_res(ds, tr.params, cam, frames, passes=PROP_PASSES)
+    ev = proposal.evaluate_full_res(ds, tr.params, cam, frames, passes=PROP_TRACK_PASSES)
     ev.update({"train_pairs": PROP_PAIRS, "train_steps": PROP_STEPS, "pair_gen_s": gen_s,
                "train_s": train_s, "train_rooms": "room seeds 100-103",
+               "train_starts": f"magnitudes uniform in [0, {PROP_TRACK_MAX[0] * 100:.0f} cm] x "
+                               f"[0, {PROP_TRACK_MAX[1]} deg], random directions",
                "frames_room": "room seed 0 (the tracking frames' room, not in training)"})
     return ev
 

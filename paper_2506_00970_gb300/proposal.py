@@ -75,10 +75,13 @@ class ViewRenderer:
         return self.br.stacked
 
 
-def make_pairs(rooms, n_pairs: int, seed: int, device="cuda", cam=CAM):
+def make_pairs(rooms, n_pairs: int, seed: int, device="cuda", cam=CAM, max_t: float = MAX_T,
+               max_deg: float = MAX_DEG, fixed: bool = False):
     """Training pairs over the given rooms (Surfels): x [n, 120, 160, 8]
     bfloat16 (rendered at the perturbed pose + observed at ground truth) and
-    the target y* [n, 6]; ``cam``: the network's 160x120 camera."""
+    the target y* [n, 6]; ``cam``: the network's 160x120 camera; start poses
+    perturbed by magnitudes uniform in [0, max_t] and [0, max_deg], or by
+    exactly max_t and max_deg (``fixed``), in random directions."""
     X = torch.empty(n_pairs, 120, 160, 8, dtype=torch.bfloat16, device=device)
     Y = torch.empty(n_pairs, 6, device=device)
     gen = torch.Generator(device=device)
@@ -95,7 +98,9 @@ def make_pairs(rooms, n_pairs: int, seed: int, device="cuda", cam=CAM):
             cnt = min(VIEWS, n_pairs - i, per_room - c0)
             k = seed * 10_000_000 + r * 1_000_000 + c0
             gts = [scenes.room_pose(k + j) for j in range(cnt)]
-            inits = [scenes.perturb_uniform(g, MAX_T, MAX_DEG, k + j) for j, g in enumerate(gts)]
+            inits = [scenes.perturb_pose(g, max_t, max_deg, seed=k + j + 7_000_000) if fixed
+                     else scenes.perturb_uniform(g, max_t, max_deg, k + j)
+                     for j, g in enumerate(gts)]
             G, I = poses_tensor(gts, device), poses_tensor(inits, device)
             img = vr.render(G)
             obs_rgb.copy_(img["rgb"])
