@@ -60,3 +60,34 @@ def test_trained_proposal_shortens_tracking(torch_cuda):
     ev2 = proposal.evaluate(scenes.room_scene(200, 100_000), tr.params, 48, seed=3, passes=2)
     assert ev2["learned"]["ms_to_1cm_0.5deg_median"] < ev2["plain"]["ms_to_1cm_0.5deg_median"], ev2
     assert ev2["learned"]["reached"] >= ev2["plain"]["reached"] - 1, ev2
+
+
+def test_proposal_at_tracking_scale(torch_cuda):
+    """The proposal for full-resolution frames: a network for the 640x480
+    camera's 160x120 view (the observation box-downsampled), the loop at
+    full resolution refining the kept pose; a short training must already
+    improve the rotation of 2 cm / 1 deg starts and lose no frame."""
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d, proposal
+    cam = scenes.tracking_camera()
+    lo = proposal.low_res_camera(cam, 4)
+    assert (lo.width, lo.height) == (160, 120) and lo.fx == cam.fx / 4
+    rooms = [scenes.room_scene(100 + r, 100_000) for r in range(2)]
+    X, Y = proposal.make_pairs(rooms, 16_384, seed=1, cam=lo, max_t=0.03, max_deg=1.5)
+    tr = proposal.Trainer(seed=0, batch=256)
+    tr.fit(X, Y, 1200, lr=1e-3)
+    del X, Y
+    torch.cuda.empty_cache()
+    s = scenes.room_scene(0, 100_000)
+    ds = gs2d.DeviceSurfels(s)
+    r = gs2d.Rasterizer(cam, ds.n)
+    frames = []
+    for f in range(8):
+        gt = scenes.room_pose(300 + f)
+        out = r.forward(ds, gs2d.pose_tensor(gt))
+        obs_d = out["depth"] / out["opacity"].clamp_min(1e-6)
+        frames.append(dict(gt=gt, obs_rgb=out["rgb"].clone(), obs_depth=obs_d.clone(),
+                           start_t=gs2d.pose_tensor(scenes.perturb_pose(gt, 0.02, 1.0, seed=f))))
+    ev = proposal.evaluate_full_res(ds, tr.params, cam, frames, passes=1)
+    assert ev["proposal_err_median_cm_deg"][1] < 1.0, ev
+    assert ev["learned"]["reached"] >= ev["plain"]["reached"], ev
