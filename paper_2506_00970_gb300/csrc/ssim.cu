@@ -86,7 +86,9 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_kernel(const float* __restr
   const int c = blockIdx.z;
   const int tx0 = blockIdx.x * kSsimT, ty0 = blockIdx.y * kSsimT;
   const int ax0 = tx0 - 2 * kSsimR, ay0 = ty0 - 2 * kSsimR;   // staged origin
-  // stage x, y (zero outside the image) and clear the slack
+  // stage x, y (zero outside the image) and clear the slack; unrolled so
+  // that several loads of each thread are in flight
+#pragma unroll 4
   for (int e = threadIdx.x; e < kSsimA * kSsimA; e += kSsimThreads) {
     const int r = e / kSsimA, q = e % kSsimA;
     const int py = ay0 + r, px = ax0 + q;
