@@ -35,7 +35,7 @@ int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* p
 // kSortPreZeroed -- the caller has zeroed the counter region
 // (sort_zero_region) since the last binning, so no init launch;
 // kSortLongInBlock -- tiles with segments over 2048 keys are sorted by their
-// own 128-thread block (chunks + merges) instead of a separate launch.
+// own 256-thread block (chunks + merges) instead of a separate launch.
 // kSortPreScanned -- a fused projection already counted and scanned the
 // tiles (implies pre-zeroed counters; no emission offsets).
 constexpr unsigned kSortPreZeroed = 1u, kSortLongInBlock = 2u, kSortPreScanned = 4u;

@@ -38,7 +38,7 @@ constexpr int kScanItems = 16;
 constexpr int kChunk = kScanThreads * kScanItems;  // 4096 surfels per scan block
 constexpr int kWarps = kScanThreads / 32;
 constexpr int kSpinLimit = 1 << 22;
-constexpr int kSortThreads = 128;
+constexpr int kSortThreads = 256;
 constexpr int kSegSmem = 2048;                     // keys sorted in shared memory (16 KB)
 constexpr int kLongThreads = 1024;                 // long segments: one 1024-thread block
 constexpr int kLongChunk = 16384;                  // keys per shared-memory chunk (128 KB)
@@ -285,21 +285,23 @@ __device__ __forceinline__ void cmp_swap(unsigned long long* a, int i, int j) {
   }
 }
 __device__ void bitonic_sort(unsigned long long* a, int len) {
-  int n2 = 1;
-  while (n2 < len) n2 <<= 1;
-  for (int size = 2; size <= n2; size <<= 1) {
-    // flip step: i pairs with its mirror i ^ (size - 1) inside each block
-    const int half = size >> 1;
-    for (int q = threadIdx.x; q < n2 / 2; q += blockDim.x) {
-      const int i = (q / half) * size + (q % half);
-      const int j = i ^ (size - 1);
+  int lg = 0;
+  while ((1 << lg) < len) ++lg;
+  const int pairs = (1 << lg) >> 1;
+  for (int ls = 1; ls <= lg; ++ls) {
+    // flip step: i pairs with its mirror i ^ (size - 1) inside each block of
+    // size = 2^ls (the index arithmetic in shifts: sizes are powers of two)
+    const int lh = ls - 1;
+    for (int q = threadIdx.x; q < pairs; q += blockDim.x) {
+      const int i = ((q >> lh) << ls) | (q & ((1 << lh) - 1));
+      const int j = i ^ ((1 << ls) - 1);
       if (j < len) cmp_swap(a, i, j);
     }
     __syncthreads();
-    for (int stride = size >> 2; stride > 0; stride >>= 1) {
-      for (int q = threadIdx.x; q < n2 / 2; q += blockDim.x) {
-        const int i = (q / stride) * (2 * stride) + (q % stride);
-        const int j = i + stride;
+    for (int lst = ls - 2; lst >= 0; --lst) {
+      for (int q = threadIdx.x; q < pairs; q += blockDim.x) {
+        const int i = ((q >> lst) << (lst + 1)) | (q & ((1 << lst) - 1));
+        const int j = i + (1 << lst);
         if (j < len) cmp_swap(a, i, j);
       }
       __syncthreads();
@@ -307,7 +309,6 @@ __device__ void bitonic_sort(unsigned long long* a, int len) {
   }
 }
 
-// The final outputs of a tile's sorted segment a[0, len).
 __device__ __forceinline__ void write_outputs(const unsigned long long* a, int len, int start, int t,
                                               int tiles_x, int n, const float4* __restrict__ proj,
                                               const uint32_t* __restrict__ surfel_off,
@@ -403,7 +404,7 @@ __device__ void sort_long_segment(int t, const float4* __restrict__ proj, int n,
   write_outputs(src, len, start, t, tiles_x, n, proj, surfel_off, vals, emit, keys64);
 }
 
-// Segments of at most kSegSmem keys: sorted in shared memory by 128 threads (and,
+// Segments of at most kSegSmem keys: sorted in shared memory by 256 threads (and,
 // with long_here, longer ones too).
 __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(
     const float4* __restrict__ proj, int n, int tiles_x, const int32_t* __restrict__ ranges,
