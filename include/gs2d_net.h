@@ -87,6 +87,17 @@ int gs2d_net_downsample_rgbd(const float* rgb, const float* depth, int height, i
 int gs2d_net_forward(const float* params, const uint16_t* x, int batch, float* y,
                      void* workspace, size_t ws_bytes, size_t* ws_needed, gs2d_stream stream);
 
+/* Inference with fixed weights: gs2d_net_prepare writes the bfloat16 copy of
+ * the weights into a workspace sized for this batch; gs2d_net_forward_prepared
+ * is gs2d_net_forward without that cast, valid while the weights and the
+ * workspace are unchanged since the last gs2d_net_prepare with this batch
+ * (params still supplies the FP32 biases). */
+int gs2d_net_prepare(const float* params, int batch, void* workspace, size_t ws_bytes,
+                     size_t* ws_needed, gs2d_stream stream);
+int gs2d_net_forward_prepared(const float* params, const uint16_t* x, int batch, float* y,
+                              void* workspace, size_t ws_bytes, size_t* ws_needed,
+                              gs2d_stream stream);
+
 /* Forward + loss + backward: loss [1] (FP32) against target [batch * 6] and
  * the flat gradient grad [gs2d_net_param_count()] (FP32, overwritten);
  * y [batch * 6] may be NULL. */

@@ -1082,10 +1082,11 @@ int cast(const float* params, const Ws& w, cudaStream_t st) {
   return GS2D_OK;
 }
 
-int forward(const float* params, const bf16* x, int B, const Ws& w, float* y, cudaStream_t st) {
+int forward(const float* params, const bf16* x, int B, const Ws& w, float* y, cudaStream_t st,
+            bool do_cast = true) {
   const Layout L = layout();
   GS2D_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int), st));
-  int r = cast(params, w, st);
+  int r = do_cast ? cast(params, w, st) : GS2D_OK;
   if (r) return r;
   const bf16* in = x;
   for (int l = 0; l < kConv; ++l) {
@@ -1317,6 +1318,27 @@ int gs2d_net_forward(const float* params, const uint16_t* x, int batch, float* y
   if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
   const Ws w = carve(workspace, batch);
   return forward(params, reinterpret_cast<const bf16*>(x), batch, w, y, (cudaStream_t)stream);
+}
+
+int gs2d_net_prepare(const float* params, int batch, void* workspace, size_t ws_bytes,
+                     size_t* ws_needed, gs2d_stream stream) {
+  if (batch <= 0 || !params) return GS2D_ERR_INVALID_ARG;
+  const size_t need = gs2d_net_workspace(batch);
+  if (ws_needed) *ws_needed = need;
+  if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
+  return cast(params, carve(workspace, batch), (cudaStream_t)stream);
+}
+
+int gs2d_net_forward_prepared(const float* params, const uint16_t* x, int batch, float* y,
+                              void* workspace, size_t ws_bytes, size_t* ws_needed,
+                              gs2d_stream stream) {
+  if (batch <= 0 || !params || !y || !aligned16(x)) return GS2D_ERR_INVALID_ARG;
+  const size_t need = gs2d_net_workspace(batch);
+  if (ws_needed) *ws_needed = need;
+  if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
+  const Ws w = carve(workspace, batch);
+  return forward(params, reinterpret_cast<const bf16*>(x), batch, w, y, (cudaStream_t)stream,
+                 false);
 }
 
 int gs2d_net_grad(const float* params, const uint16_t* x, const float* target, int batch,

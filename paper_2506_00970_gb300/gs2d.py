@@ -114,7 +114,7 @@ EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_stri
            "gs2d_mapping_loss_ssim_workspace", "gs2d_mapping_loss_ssim", "gs2d_ssim_workspace",
            "gs2d_ssim_loss", "gs2d_voxel_clear", "gs2d_voxel_insert", "gs2d_voxel_query",
            "gs2d_expand_workspace", "gs2d_expand", "gs2d_map_expand_values",
-           "gs2d_net_downsample_rgbd"]
+           "gs2d_net_downsample_rgbd", "gs2d_net_prepare", "gs2d_net_forward_prepared"]
 
 NET_LAYERS = 8
 NET_IN = (120, 160, 8)
@@ -181,6 +181,8 @@ def lib():
         L.gs2d_net_target.argtypes = [vp, vp, ip, vp, vp]
         L.gs2d_net_accept.argtypes = [vp, vp, vp, ip, vp, vp, vp]
         L.gs2d_net_downsample_rgbd.argtypes = [vp, vp, ip, ip, ip, vp, vp, vp]
+        L.gs2d_net_prepare.argtypes = [vp, ip, vp, sz, vp, vp]
+        L.gs2d_net_forward_prepared.argtypes = [vp, vp, ip, vp, vp, sz, vp, vp]
         L.gs2d_render_contrib_workspace.restype = sz
         L.gs2d_render_contrib_workspace.argtypes = [sz]
         L.gs2d_render_contrib.argtypes = [vp, vp, vp, ip, vp, vp, vp, vp, sz, vp, vp]
@@ -636,6 +638,19 @@ def gs2d_net_downsample_rgbd(rgb, depth, factor, rgb_out, depth_out, stream=None
     check(lib().gs2d_net_downsample_rgbd(_ptr(rgb), _ptr(depth), H, W, int(factor), _ptr(rgb_out),
                                          _ptr(depth_out), _stream(stream)),
           "gs2d_net_downsample_rgbd")
+
+
+def gs2d_net_prepare(params, batch, workspace, stream=None):
+    check(lib().gs2d_net_prepare(_ptr(params), int(batch), _ptr(workspace),
+                                 workspace.numel() * workspace.element_size(), None,
+                                 _stream(stream)), "gs2d_net_prepare")
+
+
+def gs2d_net_forward_prepared(params, x, y, workspace, stream=None):
+    check(lib().gs2d_net_forward_prepared(_ptr(params), _ptr(x), int(x.shape[0]), _ptr(y),
+                                          _ptr(workspace),
+                                          workspace.numel() * workspace.element_size(), None,
+                                          _stream(stream)), "gs2d_net_forward_prepared")
 
 
 def gs2d_net_forward(params, x, y, workspace, stream=None):

@@ -178,6 +178,7 @@ class Proposer:
         self.x = torch.empty(1, 120, 160, 8, dtype=torch.bfloat16, device=device)
         self.y = torch.empty(1, 6, **f)
         self.ws = torch.empty(gs2d.gs2d_net_workspace(1), dtype=torch.uint8, device=device)
+        gs2d.gs2d_net_prepare(params, 1, self.ws)      # the bfloat16 weights, cast once
         self.g = [torch.empty(120, 160, 3, **f), torch.empty(120, 160, **f), torch.empty(120, 160, **f)]
         self.loss_init = torch.empty(1, **f)
         self.loss_prop = torch.empty(1, **f)
@@ -204,7 +205,7 @@ class Proposer:
             self._loss(self.loss_init)
             gs2d.gs2d_net_pack_input(r.rgb[None], r.depth[None], r.opacity[None],
                                      self.obs_rgb[None], self.obs_d[None], self.x)
-            gs2d.gs2d_net_forward(self.params, self.x, self.y, self.ws)
+            gs2d.gs2d_net_forward_prepared(self.params, self.x, self.y, self.ws)
             self.prop.copy_(self.pose)
             gs2d.gs2d_net_apply(self.y, self.prop)
             self._render(self.prop[0])

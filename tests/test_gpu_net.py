@@ -295,3 +295,21 @@ def test_downsample_rgbd_matches_oracle(torch_cuda):
     np.testing.assert_allclose(c.cpu().numpy(), c_o, rtol=1e-6, atol=1e-7)
     np.testing.assert_allclose(d.cpu().numpy(), d_o, rtol=1e-6, atol=0)
     assert float(d[0, 0]) == 0.0 and float(d[0, 1]) == 0.0
+
+
+def test_prepared_forward_is_the_forward(torch_cuda):
+    """gs2d_net_forward_prepared after gs2d_net_prepare gives the bits of
+    gs2d_net_forward (the same bfloat16 weights, cast once)."""
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d
+    params = torch.tensor(scenes.net_init(4, gs2d.net_init_blocks()), device="cuda")
+    x = (torch.rand(3, 120, 160, 8, device="cuda") * 2 - 1).to(torch.bfloat16)
+    ws = torch.empty(gs2d.gs2d_net_workspace(3), dtype=torch.uint8, device="cuda")
+    y0 = torch.empty(3, 6, device="cuda")
+    y1 = torch.empty(3, 6, device="cuda")
+    gs2d.gs2d_net_forward(params, x, y0, ws)
+    ws.zero_()
+    gs2d.gs2d_net_prepare(params, 3, ws)
+    gs2d.gs2d_net_forward_prepared(params, x, y1, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(y0, y1)
