@@ -117,7 +117,11 @@ typedef struct {
   uint32_t* vals;        /* [capacity] surfel id per sorted position            */
   uint32_t* isect_emit;  /* [capacity] emission index of each sorted position   */
   uint32_t* surfel_off;  /* [n] first emission index of surfel i (its k_i
-                            intersections are emission indices off..off+k_i-1) */
+                            intersections are emission indices off..off+k_i-1);
+                            both may be NULL (gs2d_bin_sort then skips the
+                            emission scan): bins for gs2d_render_fwd only --
+                            the full gs2d_render_bwd and gs2d_render_contrib
+                            need them */
   int32_t* tile_ranges;  /* [2 * n_tiles] [start, end) of each tile's list       */
   int32_t* n_isect;      /* [1] K (the needed count when K > capacity)          */
   int32_t* status;       /* [1] device status word (gs2d_status)                */

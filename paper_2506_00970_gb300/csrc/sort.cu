@@ -618,8 +618,10 @@ size_t gs2d_bin_sort_workspace(int n, size_t capacity) {
 int gs2d_bin_sort(const float* proj, const int32_t* tiles_per_surfel, int n,
                   const gs2d_camera* cam, const gs2d_config* cfg, void* workspace,
                   size_t ws_bytes, size_t* ws_needed, const gs2d_bins* bins, gs2d_stream stream) {
+  // without emission arrays the binning serves the forward pass only
+  const bool emit = bins && (bins->isect_emit || bins->surfel_off);
   return bin_sort_launch(proj, tiles_per_surfel, n, cam, cfg, workspace, ws_bytes, ws_needed, bins,
-                         true, (cudaStream_t)stream);
+                         emit, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -190,7 +190,9 @@ class Proposer:
         r = self.r
         r.status.zero_()
         r.project(self.surf, pose_row)
-        gs2d.gs2d_bin_sort(r.proj, r.tiles, r.n, r.cam, r.cfg, r.sort_ws, r.bins)
+        fwd_bins = gs2d.Bins(r.bins.keys, r.bins.vals, None, None, r.bins.tile_ranges,
+                             r.bins.n_isect, r.bins.status, r.bins.capacity)
+        gs2d.gs2d_bin_sort(r.proj, r.tiles, r.n, r.cam, r.cfg, r.sort_ws, fwd_bins)
         r.render_fwd()
 
     def _loss(self, out):

@@ -335,3 +335,27 @@ def test_autograd_render_matches_oracle_gradient(torch_cuda, orc):
     moved = scenes.Pose(pose.R.copy(), pose.t + np.array([0.01, 0.0, 0.0]))
     _, _, _, ref = gpu_render(s, cam, moved)
     assert np.abs(rgb2.cpu().numpy() - ref["rgb"]).max() < 1e-4
+
+
+def test_forward_only_binning_matches(torch_cuda):
+    """Bins without emission arrays (gs2d_bin_sort skips the emission scan)
+    hold the same surfel order and tile ranges, and the forward renders the
+    same bits."""
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d
+    s, cam, pose = scenes.room_scene(2, 50_000), scenes.tracking_camera(), scenes.room_pose(3)
+    r, ds, pose_t, g = gpu_render(s, cam, pose)
+    K = int(r.n_isect.item())
+    vals = r.vals[:K].clone()
+    ranges = r.ranges.clone()
+    rgb = r.rgb.clone()
+    r.vals.fill_(-1)
+    r.status.zero_()
+    fb = gs2d.Bins(r.bins.keys, r.bins.vals, None, None, r.bins.tile_ranges, r.bins.n_isect,
+                   r.bins.status, r.bins.capacity)
+    gs2d.gs2d_bin_sort(r.proj, r.tiles, r.n, r.cam, r.cfg, r.sort_ws, fb)
+    r.render_fwd()
+    torch.cuda.synchronize()
+    assert int(r.status.item()) == 0 and int(r.n_isect.item()) == K
+    assert torch.equal(r.vals[:K], vals) and torch.equal(r.ranges, ranges)
+    assert torch.equal(r.rgb, rgb)
