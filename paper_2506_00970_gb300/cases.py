@@ -15,6 +15,9 @@
   contrib  per-surfel contributions (gs2d_render_contrib) of a 200k-surfel room
            at 640x480
   ssim     the SSIM term with its gradient (gs2d_ssim_loss) at 1200x680
+  proposal one frame's learned pose proposal at 160x120 (two passes: render,
+           tracking loss, network at batch 1, render at the proposal, loss,
+           acceptance), replayed as a CUDA graph; random network weights
   map      map-state passes on a 2M-surfel map (state update, correction by 64
            keyframe increments, pruning, compaction) and the expansion of a
            1200x680 RGB-D keyframe (downsampling 0.04) against a voxel table
@@ -219,9 +222,24 @@ def case_map(reps, px=1):
     return _timed(run, reps)
 
 
+def case_proposal(reps, px=1):
+    from . import proposal
+    s = scenes.room_scene(200, 200_000)
+    ds = gs2d.DeviceSurfels(s)
+    params = torch.tensor(scenes.net_init(0, gs2d.net_init_blocks()), device="cuda")
+    pr = proposal.Proposer(ds, params, 8 * ds.n, passes=2)
+    gt = scenes.room_pose(5)
+    pr.pose.copy_(proposal.poses_tensor([scenes.perturb_pose(gt, 0.03, 2.0, seed=1)]))
+    img = proposal.ViewRenderer(ds).render(proposal.poses_tensor([gt]))
+    pr.obs_rgb.copy_(img["rgb"][0])
+    pr.obs_d.copy_(img["depth"][0] / img["opacity"][0].clamp_min(1e-6))
+    g = proposal.capture(pr.run)
+    return _timed(g.replay, reps)
+
+
 CASES = {"track": case_track, "track_small": case_track_small, "mapping": case_mapping, "uneven": case_uneven, "net": case_net,
          "sort": case_sort, "contrib": case_contrib,
-         "ssim": case_ssim, "map": case_map}
+         "ssim": case_ssim, "map": case_map, "proposal": case_proposal}
 
 
 def main(argv):
