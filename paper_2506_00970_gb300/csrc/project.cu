@@ -197,6 +197,10 @@ __device__ __forceinline__ void project_one(int i, const float* __restrict__ mu,
                      __uint_as_float(b23));
 }
 
+// Tile counters a fused projection keeps in shared memory (larger tile grids
+// count with global atomics).
+constexpr int kHistTiles = 2048;
+
 template <bool kFuse>
 __global__ void __launch_bounds__(256) project_kernel(
     const float* __restrict__ mu, const float* __restrict__ quat, const float* __restrict__ scale,
@@ -206,55 +210,52 @@ __global__ void __launch_bounds__(256) project_kernel(
     SortFuse fz, int32_t* __restrict__ status) {
   // records are assembled in shared memory (9 float4 per thread: padded so
   // both the per-thread writes and the block's coalesced copy-out are free
-  // of bank conflicts) and written as one contiguous 32 KB run per block
+  // of bank conflicts) and written as one contiguous 32 KB run per chunk of
+  // 256 surfels; the grid is resident (a block per slot) and strides over
+  // the chunks, so there is no partial last wave
   __shared__ float4 s_out[256 * 9];
+  __shared__ uint32_t s_hist[kFuse ? kHistTiles : 1];
   __shared__ float sp[12];
   __shared__ uint32_t s_w[32];
   __shared__ uint32_t s_carry;
   __shared__ bool s_last;
   if (gate && *gate) return;
   if (threadIdx.x < 12) sp[threadIdx.x] = pose[threadIdx.x];
-  __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t r01 = 1u, r23 = 0u;  // an empty rectangle
-  if (i < n) {
-    project_one(i, mu, quat, scale, opacity, rgb, sp, cam, cfg, s_out + threadIdx.x * 9,
-                tiles_out + i);
-    if (kFuse) {
-      const float4 rc = s_out[threadIdx.x * 9 + 7];
-      r01 = __float_as_uint(rc.x);
-      r23 = __float_as_uint(rc.y);
-    }
-  }
-  __syncthreads();
-  const int base = blockIdx.x * blockDim.x;
-  const int valid = min((int)blockDim.x, n - base);
-  float4* dst = proj + (size_t)base * (kProjFloats / 4);
-  for (int v = threadIdx.x; v < valid * 8; v += blockDim.x) dst[v] = s_out[(v >> 3) * 9 + (v & 7)];
-  if (!kFuse) return;
-  // tile counts: the staging buffer becomes the block's histogram (when the
-  // tile grid fits), flushed with one global atomic per touched tile
-  __syncthreads();
-  uint32_t* hist = reinterpret_cast<uint32_t*>(s_out);
-  const bool local = fz.n_tiles <= 256 * 9 * 4;
+  const bool local = kFuse && fz.n_tiles <= kHistTiles;
   if (local)
-    for (int t = threadIdx.x; t < fz.n_tiles; t += blockDim.x) hist[t] = 0u;
+    for (int t = threadIdx.x; t < fz.n_tiles; t += blockDim.x) s_hist[t] = 0u;
   __syncthreads();
-  {
-    const int tx0 = (int)(r01 & 0xFFFF), ty0 = (int)(r01 >> 16);
-    const int tx1 = (int)(r23 & 0xFFFF), ty1 = (int)(r23 >> 16);
-    if (tx0 <= tx1 && ty0 <= ty1) {
-      const int rw = tx1 - tx0 + 1, k = rw * (ty1 - ty0 + 1);
-      for (int j = 0; j < k; ++j) {
-        const int t = min((ty0 + j / rw) * fz.tiles_x + tx0 + j % rw, fz.n_tiles - 1);
-        atomicAdd(local ? hist + t : fz.tile_count + t, 1u);
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int i = base + (int)threadIdx.x;
+    if (i < n) {
+      project_one(i, mu, quat, scale, opacity, rgb, sp, cam, cfg, s_out + threadIdx.x * 9,
+                  tiles_out + i);
+      if (kFuse) {
+        // tile counts of this surfel's rectangle
+        const float4 rc = s_out[threadIdx.x * 9 + 7];
+        const uint32_t r01 = __float_as_uint(rc.x), r23 = __float_as_uint(rc.y);
+        const int tx0 = (int)(r01 & 0xFFFF), ty0 = (int)(r01 >> 16);
+        const int tx1 = (int)(r23 & 0xFFFF), ty1 = (int)(r23 >> 16);
+        if (tx0 <= tx1 && ty0 <= ty1) {
+          const int rw = tx1 - tx0 + 1, k = rw * (ty1 - ty0 + 1);
+          for (int j = 0; j < k; ++j) {
+            const int t = min((ty0 + j / rw) * fz.tiles_x + tx0 + j % rw, fz.n_tiles - 1);
+            atomicAdd(local ? s_hist + t : fz.tile_count + t, 1u);
+          }
+        }
       }
     }
+    __syncthreads();
+    const int valid = min((int)blockDim.x, n - base);
+    float4* dst = proj + (size_t)base * (kProjFloats / 4);
+    for (int v = threadIdx.x; v < valid * 8; v += blockDim.x) dst[v] = s_out[(v >> 3) * 9 + (v & 7)];
+    __syncthreads();
   }
-  __syncthreads();
+  if (!kFuse) return;
+  // the block's counts, one global atomic per touched tile
   if (local)
     for (int t = threadIdx.x; t < fz.n_tiles; t += blockDim.x)
-      if (hist[t]) atomicAdd(fz.tile_count + t, hist[t]);
+      if (s_hist[t]) atomicAdd(fz.tile_count + t, s_hist[t]);
   // the last block to finish turns the counts into tile ranges
   __threadfence();
   __syncthreads();
@@ -317,17 +318,27 @@ int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* p
   const int tx = tiles_along(cam->width, cfg->tile_w), ty = tiles_along(cam->height, cfg->tile_h);
   if (tx > 65535 || ty > 65535) return GS2D_ERR_INVALID_ARG;
   const int threads = 256;
+  const int chunks = (s->n + threads - 1) / threads;
   if (fuse) {
-    // with no surfel one block still runs the (empty) scan
-    const int blocks = max((s->n + threads - 1) / threads, 1);
+    // a resident grid (with no surfel one block still runs the empty scan)
+    static int resident = 0;
+    if (!resident) {
+      int per_sm = 0, dev = 0, sms = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, project_kernel<true>, threads,
+                                                        0) != cudaSuccess ||
+          cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GS2D_ERR_CUDA;
+      resident = max(per_sm, 1) * max(sms, 1);
+    }
+    const int blocks = max(min(chunks, resident), 1);
     project_kernel<true><<<blocks, threads, 0, st>>>(
         s->mu, s->quat, s->scale, s->opacity, s->rgb, s->n, pose, *cam, *cfg, tx, ty,
         reinterpret_cast<float4*>(proj_out), tiles_per_surfel_out, gate, *fuse,
         const_cast<int32_t*>(gate));
   } else {
     if (s->n == 0) return GS2D_OK;
-    const int blocks = (s->n + threads - 1) / threads;
-    project_kernel<false><<<blocks, threads, 0, st>>>(
+    project_kernel<false><<<chunks, threads, 0, st>>>(
         s->mu, s->quat, s->scale, s->opacity, s->rgb, s->n, pose, *cam, *cfg, tx, ty,
         reinterpret_cast<float4*>(proj_out), tiles_per_surfel_out, gate, SortFuse{}, nullptr);
   }
