@@ -145,6 +145,26 @@ class Trainer:
                 hist.append((k, float(self.loss.item())))
         return hist
 
+    def state_dict(self) -> dict:
+        """Everything a resumed training needs: FP32 master weights, AdamW
+        moments and the step count (host copies)."""
+        return {"params": self.params.detach().cpu(), "m": self.m.detach().cpu(),
+                "v": self.v.detach().cpu(), "step": int(self.step), "batch": int(self.batch)}
+
+    def load_state_dict(self, d: dict):
+        if d["params"].numel() != self.params.numel():
+            raise ValueError("checkpoint of a different network")
+        self.params.copy_(d["params"])
+        self.m.copy_(d["m"])
+        self.v.copy_(d["v"])
+        self.step = int(d["step"])
+
+    def save(self, path: str):
+        torch.save(self.state_dict(), path)
+
+    def load(self, path: str):
+        self.load_state_dict(torch.load(path, map_location="cpu"))
+
     def eval_loss(self, X, Y):
         """Mean loss over contiguous batches of (X, Y) (no update)."""
         B = self.batch

@@ -37,6 +37,34 @@ class SurfelMap:
                                                       torch.zeros(c, 3, **f))
         self.state = gs2d.DeviceMapState(c, device=self.device)
 
+    # checkpoint ----------------------------------------------------------------
+    def save(self, path: str):
+        """The map's parameters and state (the first n surfels) and settings
+        as a NumPy .npz; the voxel table is rebuilt on load."""
+        n = self.n
+        p, st = self.params, self.state
+        np.savez(path, mu=p.mu[:n].cpu().numpy(), quat=p.quat[:n].cpu().numpy(),
+                 scale=p.scale[:n].cpu().numpy(), opacity=p.opacity[:n].cpu().numpy(),
+                 rgb=p.rgb[:n].cpu().numpy(), delta=st.delta[:n].cpu().numpy(),
+                 t_c=st.t_c[:n].cpu().numpy(), d_c=st.d_c[:n].cpu().numpy(),
+                 t_l=st.t_l[:n].cpu().numpy(),
+                 settings=np.array([self.capacity, self.table.voxel, self.table.capacity,
+                                    self.inactive_after], np.float64))
+
+    @classmethod
+    def load(cls, path: str, device="cuda") -> "SurfelMap":
+        z = np.load(path)
+        cap, voxel, tcap, after = z["settings"]
+        m = cls(int(cap), float(voxel), int(tcap), int(after), device)
+        n = int(z["mu"].shape[0])
+        for name in ("mu", "quat", "scale", "opacity", "rgb"):
+            getattr(m.params, name)[:n].copy_(torch.from_numpy(z[name]))
+        for name in ("delta", "t_c", "d_c", "t_l"):
+            getattr(m.state, name)[:n].copy_(torch.from_numpy(z[name]))
+        m.n = n
+        m.rebuild_table()
+        return m
+
     # views of the first n surfels ------------------------------------------
     def surfels(self) -> gs2d.DeviceSurfels:
         p = self.params

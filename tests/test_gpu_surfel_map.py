@@ -96,3 +96,28 @@ def test_surfel_map_keyframe_flow(torch_cuda):
     # the freed voxels take new surfels again
     k3 = M.expand(T(rgb0), T(d0), cam, P(p0), 6, 0.25, gen)
     assert k3 > 0.5 * k0
+
+
+def test_surfel_map_checkpoint(torch_cuda, tmp_path):
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d
+    from paper_2506_00970_gb300.surfel_map import SurfelMap
+    cam = scenes.Camera(300.0, 300.0, 160.0, 120.0, 320, 240)
+    p0 = scenes.identity_pose()
+    M = SurfelMap(200_000, voxel=0.03)
+    rgb, d = scenes.rgbd_frame(4, cam, pose=p0)
+    T = lambda a: torch.tensor(a, device="cuda")
+    M.expand(T(rgb), T(d), cam, gs2d.pose_tensor(p0), 2, 0.2,
+             torch.Generator(device="cuda").manual_seed(1))
+    M.state.delta[: M.n : 3] = 0                     # some inactive surfels
+    M.rebuild_table()
+    path = str(tmp_path / "map.npz")
+    M.save(path)
+    L = SurfelMap.load(path)
+    assert L.n == M.n and L.capacity == M.capacity and L.table.voxel == M.table.voxel
+    for name in ("mu", "quat", "scale", "opacity", "rgb"):
+        assert torch.equal(getattr(L.params, name)[:L.n], getattr(M.params, name)[:M.n]), name
+    for name in ("delta", "t_c", "d_c", "t_l"):
+        assert torch.equal(getattr(L.state, name)[:L.n], getattr(M.state, name)[:M.n]), name
+    q = M.params.mu[: M.n]
+    assert torch.equal(L.table.query(q), M.table.query(q))
