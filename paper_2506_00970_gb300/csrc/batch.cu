@@ -41,7 +41,7 @@ __device__ __forceinline__ int view_of(const ViewTable& tab, int item) {
 }
 
 template <int P>
-__global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) fwd_batch_kernel(ViewTable tab,
+__global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 4 : 2)) fwd_batch_kernel(ViewTable tab,
                                                                  uint32_t* __restrict__ queue) {
   __shared__ float4 s_rec[kTileThreads][kFwdVec4];
   __shared__ HitLists hl;
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) f
 }
 
 template <int P>
-__global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) bwd_batch_kernel(ViewTable tab,
+__global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 4 : 2)) bwd_batch_kernel(ViewTable tab,
                                                                  uint32_t* __restrict__ queue) {
   __shared__ BwdSmem<true> sm;
   __shared__ int s_item;
