@@ -197,12 +197,37 @@ __device__ __forceinline__ void project_one(int i, const float* __restrict__ mu,
                      __uint_as_float(b23));
 }
 
+// One surfel per thread.  The same per-surfel code as the batched projection
+// (project_one), so single views and batches write bit-identical records.
+__global__ void __launch_bounds__(256) project_kernel(
+    const float* __restrict__ mu, const float* __restrict__ quat, const float* __restrict__ scale,
+    const float* __restrict__ opacity, const float* __restrict__ rgb, int n,
+    const float* __restrict__ pose, gs2d_camera cam, gs2d_config cfg,
+    float4* __restrict__ proj, int32_t* __restrict__ tiles_out, const int32_t* __restrict__ gate) {
+  // records are assembled in shared memory (9 float4 per thread: padded so
+  // both the per-thread writes and the block's coalesced copy-out are free
+  // of bank conflicts) and written as one contiguous 32 KB run per block
+  __shared__ float4 s_out[256 * 9];
+  __shared__ float sp[12];
+  if (gate && *gate) return;
+  if (threadIdx.x < 12) sp[threadIdx.x] = pose[threadIdx.x];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n)
+    project_one(i, mu, quat, scale, opacity, rgb, sp, cam, cfg, s_out + threadIdx.x * 9,
+                tiles_out + i);
+  __syncthreads();
+  const int base = blockIdx.x * blockDim.x;
+  const int valid = min((int)blockDim.x, n - base);
+  float4* dst = proj + (size_t)base * (kProjFloats / 4);
+  for (int v = threadIdx.x; v < valid * 8; v += blockDim.x) dst[v] = s_out[(v >> 3) * 9 + (v & 7)];
+}
+
 // Tile counters a fused projection keeps in shared memory (larger tile grids
 // count with global atomics).
 constexpr int kHistTiles = 2048;
 
-template <bool kFuse>
-__global__ void __launch_bounds__(256) project_kernel(
+__global__ void __launch_bounds__(256) project_fused_kernel(
     const float* __restrict__ mu, const float* __restrict__ quat, const float* __restrict__ scale,
     const float* __restrict__ opacity, const float* __restrict__ rgb, int n,
     const float* __restrict__ pose, gs2d_camera cam, gs2d_config cfg, int tiles_x, int tiles_y,
@@ -214,14 +239,14 @@ __global__ void __launch_bounds__(256) project_kernel(
   // 256 surfels; the grid is resident (a block per slot) and strides over
   // the chunks, so there is no partial last wave
   __shared__ float4 s_out[256 * 9];
-  __shared__ uint32_t s_hist[kFuse ? kHistTiles : 1];
+  __shared__ uint32_t s_hist[kHistTiles];
   __shared__ float sp[12];
   __shared__ uint32_t s_w[32];
   __shared__ uint32_t s_carry;
   __shared__ bool s_last;
   if (gate && *gate) return;
   if (threadIdx.x < 12) sp[threadIdx.x] = pose[threadIdx.x];
-  const bool local = kFuse && fz.n_tiles <= kHistTiles;
+  const bool local = fz.n_tiles <= kHistTiles;
   if (local)
     for (int t = threadIdx.x; t < fz.n_tiles; t += blockDim.x) s_hist[t] = 0u;
   __syncthreads();
@@ -230,7 +255,7 @@ __global__ void __launch_bounds__(256) project_kernel(
     if (i < n) {
       project_one(i, mu, quat, scale, opacity, rgb, sp, cam, cfg, s_out + threadIdx.x * 9,
                   tiles_out + i);
-      if (kFuse) {
+      {
         // tile counts of this surfel's rectangle
         const float4 rc = s_out[threadIdx.x * 9 + 7];
         const uint32_t r01 = __float_as_uint(rc.x), r23 = __float_as_uint(rc.y);
@@ -251,7 +276,6 @@ __global__ void __launch_bounds__(256) project_kernel(
     for (int v = threadIdx.x; v < valid * 8; v += blockDim.x) dst[v] = s_out[(v >> 3) * 9 + (v & 7)];
     __syncthreads();
   }
-  if (!kFuse) return;
   // the block's counts, one global atomic per touched tile
   if (local)
     for (int t = threadIdx.x; t < fz.n_tiles; t += blockDim.x)
@@ -324,7 +348,7 @@ int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* p
     static int resident = 0;
     if (!resident) {
       int per_sm = 0, dev = 0, sms = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, project_kernel<true>, threads,
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, project_fused_kernel, threads,
                                                         0) != cudaSuccess ||
           cudaGetDevice(&dev) != cudaSuccess ||
           cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -332,15 +356,16 @@ int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* p
       resident = max(per_sm, 1) * max(sms, 1);
     }
     const int blocks = max(min(chunks, resident), 1);
-    project_kernel<true><<<blocks, threads, 0, st>>>(
+    project_fused_kernel<<<blocks, threads, 0, st>>>(
         s->mu, s->quat, s->scale, s->opacity, s->rgb, s->n, pose, *cam, *cfg, tx, ty,
         reinterpret_cast<float4*>(proj_out), tiles_per_surfel_out, gate, *fuse,
         const_cast<int32_t*>(gate));
   } else {
     if (s->n == 0) return GS2D_OK;
-    project_kernel<false><<<chunks, threads, 0, st>>>(
-        s->mu, s->quat, s->scale, s->opacity, s->rgb, s->n, pose, *cam, *cfg, tx, ty,
-        reinterpret_cast<float4*>(proj_out), tiles_per_surfel_out, gate, SortFuse{}, nullptr);
+    project_kernel<<<chunks, threads, 0, st>>>(s->mu, s->quat, s->scale, s->opacity, s->rgb, s->n,
+                                               pose, *cam, *cfg,
+                                               reinterpret_cast<float4*>(proj_out),
+                                               tiles_per_surfel_out, gate);
   }
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
