@@ -80,10 +80,10 @@ typedef struct {
  * before the transmittance would fall below it) and cutoff_r2 = 9
  * (u^2 + v^2 beyond three standard deviations is skipped).  tile_w x tile_h
  * and px_per_thread P describe a tile of 256 P pixels handled by a 256-thread
- * block, P in {1, 2, 4}: thread t owns P pixels 4 rows apart and each warp an
- * 8 x 4P block, so tile_w is a multiple of 8 and tile_h of 4P (P = 1:
- * 16x16, 8x32, 32x8; P = 2: 16x32, 32x16, 8x64, 64x8; P = 4: 32x32, 16x64,
- * 64x16).  Other shapes return GS2D_ERR_INVALID_ARG.  The batch autotuner
+ * block, P in {1, 2, 3, 4}: thread t owns P pixels 4 rows apart and each warp
+ * an 8 x 4P block, so tile_w is a multiple of 8 and tile_h of 4P (P = 1:
+ * 16x16, 8x32, 32x8; P = 2: 16x32, 32x16, 8x64, 64x8; P = 3: 64x12, 32x24,
+ * 16x48, 8x96; P = 4: 32x32, 16x64, 64x16).  Other shapes return GS2D_ERR_INVALID_ARG.  The batch autotuner
  * picks the shape per resolution class and P per batch; every view of one
  * batched call must share P. */
 typedef struct {

@@ -1,6 +1,6 @@
 """Tile-shape and pixels-per-thread autotuner for batched rendering.
 
-For every pixels-per-thread count P (1, 2, 4) and every resolution class
+For every pixels-per-thread count P (1, 2, 3, 4) and every resolution class
 (width x height) of a batch, each tile shape of P is timed on a forward +
 backward pass of up to ``max_views`` of that class's views (CUDA events on
 the launching stream, the median of ``reps`` repetitions after one warm-up);
@@ -22,7 +22,7 @@ import torch
 from . import gs2d
 
 TILE_SHAPES = gs2d.TILE_SHAPES
-PX_COUNTS = (1, 2, 4)
+PX_COUNTS = (1, 2, 3, 4)
 
 _cache: dict[str, list] = {}
 

@@ -42,20 +42,24 @@ __device__ __forceinline__ TilePix<P> tile_pixel(int tile, int tiles_x, int tile
 }
 
 // A tile shape for P pixels per thread: 256 P pixels, widths a multiple of
-// 8, heights of 4P (eight 8 x 4P warp blocks), P in {1, 2, 4}.
+// 8, heights of 4P (eight 8 x 4P warp blocks), P in {1, 2, 3, 4}.
 __host__ __device__ inline bool tile_cfg_ok(const gs2d_config& c) {
   const int P = c.px_per_thread;
-  if (P != 1 && P != 2 && P != 4) return false;
+  if (P < 1 || P > 4) return false;
   return c.tile_w > 0 && c.tile_h > 0 && c.tile_w * c.tile_h == kTileThreads * P &&
          c.tile_w % 8 == 0 && c.tile_h % (4 * P) == 0;
 }
 
-// Runs the statement given after p (which names P) with P = p in {1, 2, 4}.
+// Runs the statement given after p (which names P) with P = p in {1, 2, 3, 4}.
 #define GS2D_DISPATCH_P(p, ...)           \
   do {                                    \
     switch (p) {                          \
       case 2: {                           \
         constexpr int P = 2;              \
+        __VA_ARGS__;                      \
+      } break;                            \
+      case 3: {                           \
+        constexpr int P = 3;              \
         __VA_ARGS__;                      \
       } break;                            \
       case 4: {                           \

@@ -246,7 +246,8 @@ def default_config(tile=(16, 16), px: int = 1) -> Config:
 
 # tile shapes of each pixels-per-thread count (256 P pixels, widths a
 # multiple of 8, heights of 4P)
-TILE_SHAPES = {1: ((16, 16), (8, 32), (32, 8)), 2: ((16, 32), (32, 16)), 4: ((32, 32), (16, 64))}
+TILE_SHAPES = {1: ((16, 16), (8, 32), (32, 8)), 2: ((16, 32), (32, 16)),
+               3: ((32, 24), (64, 12), (16, 48)), 4: ((32, 32), (16, 64))}
 
 
 def default_track_params(**kw) -> TrackParams:

@@ -110,18 +110,19 @@ def test_network_layout_matches_the_oracle(built_lib):
 def test_tile_configs_are_validated_on_the_host(built_lib):
     """Pixels-per-thread and tile shape are checked before anything is
     launched (no device needed): 256 P pixels, widths a multiple of 8,
-    heights a multiple of 4P, P in {1, 2, 4}."""
+    heights a multiple of 4P, P in {1, 2, 3, 4}."""
     from paper_2506_00970_gb300 import gs2d
     L = gs2d.lib()
     cam = gs2d.Camera(100.0, 100.0, 32.0, 32.0, 64, 64, 0.05)
     bins = gs2d.Bins(None, None, None, None, None, None, None, 0)
     for tile, px, ok in [((16, 16), 2, False), ((16, 32), 3, False), ((24, 16), 2, False),
                          ((8, 64), 2, True), ((32, 32), 4, True), ((64, 16), 4, True),
-                         ((32, 8), 1, True), ((16, 32), 1, False)]:
+                         ((32, 8), 1, True), ((16, 32), 1, False), ((32, 24), 3, True),
+                         ((64, 12), 3, True), ((24, 32), 3, False), ((32, 32), 5, False)]:
         cfg = gs2d.default_config(tile, px)
         rc = L.gs2d_render_fwd(None, ctypes.byref(bins), ctypes.byref(cam), ctypes.byref(cfg),
                                None, None, None, None, None, None, None)
         # a valid shape gets past the shape check and fails on the NULL buffers
         assert rc == 1, (tile, px, rc)
         assert ok == (tile[0] * tile[1] == 256 * px and tile[0] % 8 == 0 and
-                      tile[1] % (4 * px) == 0 and px in (1, 2, 4))
+                      tile[1] % (4 * px) == 0 and px in (1, 2, 3, 4))

@@ -35,7 +35,7 @@ def _setup(n_views=4, seed=0):
     return s, cams, poses, actives, tiles
 
 
-@pytest.mark.parametrize("px", [1, 2, 4])
+@pytest.mark.parametrize("px", [1, 2, 3, 4])
 def test_batch_forward_equals_single_views(torch_cuda, px):
     torch = torch_cuda
     from paper_2506_00970_gb300 import gs2d
@@ -221,15 +221,16 @@ def test_autotune_picks_a_candidate_and_caches(torch_cuda, tmp_path):
     assert tiles2 == tiles and table2 == {}
 
 
-def test_batch_backward_two_pixels_per_thread_equals_single_views(torch_cuda):
-    """The persistent backward with 2 pixels per thread equals the
+@pytest.mark.parametrize("px,tiles", [(2, [(16, 32), (32, 16), (16, 32)]),
+                                      (3, [(32, 24), (64, 12), (16, 48)])])
+def test_batch_backward_several_pixels_per_thread_equals_single_views(torch_cuda, px, tiles):
+    """The persistent backward with 2 or 3 pixels per thread equals the
     single-view backward (same per-pair arithmetic) summed over views."""
     torch = torch_cuda
     from paper_2506_00970_gb300 import gs2d
     s, cams, poses, actives, _ = _setup(n_views=3)
-    tiles = [(16, 32), (32, 16), (16, 32)]
     ds = gs2d.DeviceSurfels(s)
-    br = gs2d.BatchRasterizer(cams, s.n, actives=actives, tiles=tiles, px=2)
+    br = gs2d.BatchRasterizer(cams, s.n, actives=actives, tiles=tiles, px=px)
     br.set_poses(poses)
     br.forward(ds)
     for v, b in enumerate(br.keep):
@@ -240,7 +241,7 @@ def test_batch_backward_two_pixels_per_thread_equals_single_views(torch_cuda):
     single = {k: np.zeros(getattr(s, k).shape) for k in g}
     for v in range(len(cams)):
         ids = np.arange(s.n) if actives[v] is None else actives[v]
-        r, dsub, pt, _ = gpu_render(s.subset(ids), cams[v], poses[v], tile=tiles[v], px=2)
+        r, dsub, pt, _ = gpu_render(s.subset(ids), cams[v], poses[v], tile=tiles[v], px=px)
         b = br.keep[v]
         gv = r.backward(dsub, pt, b["d_rgb"], b["d_depth"], None, None, full=True)
         for k in single:
@@ -256,5 +257,5 @@ def test_autotune_sweeps_pixels_per_thread(torch_cuda):
     ds = gs2d.DeviceSurfels(s)
     autotune._cache.clear()
     px, tiles, table = autotune.tune(ds, cams, poses, actives, reps=1)
-    assert px in (1, 2, 4) and all(t in gs2d.TILE_SHAPES[px] for t in tiles)
-    assert set(table) == {"px1", "px2", "px4"}
+    assert px in (1, 2, 3, 4) and all(t in gs2d.TILE_SHAPES[px] for t in tiles)
+    assert set(table) == {"px1", "px2", "px3", "px4"}

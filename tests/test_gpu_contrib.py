@@ -44,7 +44,8 @@ def _check(g, o, rows=None):
     return int(tight.sum())
 
 
-@pytest.mark.parametrize("tile,px", [((16, 16), 1), ((8, 32), 1), ((32, 16), 2), ((32, 32), 4)])
+@pytest.mark.parametrize("tile,px", [((16, 16), 1), ((8, 32), 1), ((32, 16), 2), ((32, 24), 3),
+                                     ((32, 32), 4)])
 def test_contrib_slab_full_image(torch_cuda, orc, tile, px):
     torch = torch_cuda
     s, cam, pose = scenes.slab_scene(0), scenes.slab_camera(), scenes.identity_pose()

@@ -144,7 +144,8 @@ def test_project_rects_and_depth(torch_cuda, orc, which):
 # forward
 # ---------------------------------------------------------------------------
 # tile shapes with 1, 2 and 4 pixels per thread
-TILE_PX = [((16, 16), 1), ((16, 32), 2), ((32, 16), 2), ((64, 8), 2), ((32, 32), 4), ((16, 64), 4)]
+TILE_PX = [((16, 16), 1), ((16, 32), 2), ((32, 16), 2), ((64, 8), 2), ((32, 24), 3), ((64, 12), 3),
+           ((32, 32), 4), ((16, 64), 4)]
 
 
 @pytest.mark.parametrize("tile,px", TILE_PX)
@@ -180,7 +181,7 @@ def test_render_fwd_room_sampled_pixels(torch_cuda, orc):
     assert np.median(o["opacity"]) > 0.95
 
 
-@pytest.mark.parametrize("tile,px", [((16, 16), 1), ((16, 32), 2), ((32, 32), 4)])
+@pytest.mark.parametrize("tile,px", [((16, 16), 1), ((16, 32), 2), ((16, 48), 3), ((32, 32), 4)])
 def test_render_edge_cases(torch_cuda, orc, tile, px):
     cam = scenes.Camera(50.0, 50.0, 20.5, 10.0, 37, 21)   # ragged tiles both ways
     # everything behind the camera: empty image
@@ -225,7 +226,7 @@ def _slab_loss_setup(orc):
     return s, cam, gt, tgt
 
 
-@pytest.mark.parametrize("tile,px", [((16, 16), 1), ((32, 16), 2), ((32, 32), 4)])
+@pytest.mark.parametrize("tile,px", [((16, 16), 1), ((32, 16), 2), ((32, 24), 3), ((32, 32), 4)])
 def test_render_bwd_slab_all_params_and_pose(torch_cuda, orc, tile, px):
     """Workload 1: L1 colour + L1 depth against a target rendered at a pose
     offset by 2 cm / 1 degree; gradients to all surfel params and the pose

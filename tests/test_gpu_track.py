@@ -94,7 +94,7 @@ def _track_setup(orc, n=30_000, seed=0):
     return s, cam, gt
 
 
-@pytest.mark.parametrize("tile,px", [((16, 16), 1), ((32, 16), 2), ((32, 32), 4)])
+@pytest.mark.parametrize("tile,px", [((16, 16), 1), ((32, 16), 2), ((64, 12), 3), ((32, 32), 4)])
 def test_track_step_first_gradient_and_convergence(torch_cuda, orc, tile, px):
     """The fused tracking step: its first pose gradient equals the oracle's at
     the start pose (through the loss and the pose-only backward), and 100
