@@ -374,6 +374,15 @@ int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_co
 /* Device pointer of the status word inside a track workspace (int32). */
 int32_t* gs2d_track_status(void* workspace);
 
+/* Device pointer of the tile launch order inside a track workspace (int32
+ * [n_tiles], the same n, capacity, cam and cfg as gs2d_track_workspace):
+ * after an iteration, a permutation of the tile ids by decreasing tile list
+ * length (256 buckets linear in length / the longest length; arrival order
+ * within a bucket), the order in which the fused tile kernel launched the
+ * tiles.  A diagnostic; NULL for a NULL argument. */
+const int32_t* gs2d_track_tile_order(void* workspace, int n, size_t capacity,
+                                     const gs2d_camera* cam, const gs2d_config* cfg);
+
 /* Diagnostic timing of the fused tile kernel of gs2d_track_step: while set,
  * every later launch of that kernel (in any gs2d_track_step call, in launch
  * order) is bracketed by records of start_events[i] and stop_events[i] on

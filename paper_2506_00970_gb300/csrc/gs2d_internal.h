@@ -22,6 +22,7 @@ struct SortFuse {
   uint32_t* n_long;
   uint32_t* done;   // block completion counter (zeroed before the launch)
   int tiles_x, n_tiles, long_len;
+  int32_t* order;   // [n_tiles] launch order of the tiles, longest lists first (or NULL)
 };
 
 // Per-surfel projection; with fuse, also the binning's tile counts and scan
@@ -75,6 +76,7 @@ struct TrackStep {
   uint32_t* counter; // blocks finished in this iteration (reset by the last)
   uint32_t* sort_zero;   // binning counters the last block zeroes for the next
   size_t sort_zero_words;  // iteration's binning (kSortPreZeroed)
+  const int32_t* order;    // block b runs tile order[b] (or b when NULL)
 };
 
 // Fused tracking iteration per tile (forward, tracking loss, pose backward)

@@ -287,8 +287,18 @@ __global__ void __launch_bounds__(256) project_fused_kernel(
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  if (local) {
+    tile_scan_order_small<kHistTiles / 256>(fz.tile_count, fz.n_tiles, fz.ranges, fz.n_isect,
+                                            fz.capacity, fz.long_list, fz.n_long, fz.long_len,
+                                            status, fz.order, s_hist, s_w);
+    return;
+  }
   tile_scan_block(fz.tile_count, fz.n_tiles, fz.ranges, fz.n_isect, fz.capacity, fz.long_list,
                   fz.n_long, fz.long_len, status, s_w, &s_carry);
+  if (fz.order) {
+    __syncthreads();
+    tile_order_block(fz.tile_count, fz.n_tiles, fz.order, s_hist, s_w);
+  }
 }
 
 // All views of a batch in one launch (blockIdx.y = view): record j of a view

@@ -184,7 +184,9 @@ __global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) t
       return;
     }
   }
-  const int tile = blockIdx.x;
+  // longest lists first: the blocks of the heaviest tiles start in the first
+  // wave instead of trailing the grid (partials stay indexed by tile)
+  const int tile = ts.order ? ts.order[blockIdx.x] : (int)blockIdx.x;
   const TilePix<P> tp = tile_pixel<P>(tile, tiles_x, cfg.tile_w, cfg.tile_h);
   bool inside[P];
 #pragma unroll

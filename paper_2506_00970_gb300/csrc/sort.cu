@@ -526,6 +526,7 @@ SortFuse sort_fuse_args(void* workspace, int n, const gs2d_bins* bins, int tiles
   f.tiles_x = tiles_x;
   f.n_tiles = n_tiles;
   f.long_len = kSegSmem;
+  f.order = nullptr;
   return f;
 }
 

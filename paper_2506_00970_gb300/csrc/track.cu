@@ -50,7 +50,7 @@ struct TrackWs {
   float* proj;
   int32_t* tiles;
   uint32_t *vals, *emit, *soff;
-  int32_t *ranges, *n_isect;
+  int32_t *ranges, *n_isect, *order;
   void* sort_ws;
   size_t sort_bytes;
   float *loss_part, *pose_part, *adam;
@@ -72,6 +72,7 @@ TrackWs carve_track_ws(void* base, int n, size_t cap, const gs2d_camera* cam,
   w.soff = c.take<uint32_t>(nn);
   w.ranges = c.take<int32_t>(2 * (size_t)nt);
   w.n_isect = c.take<int32_t>(1);
+  w.order = c.take<int32_t>((size_t)nt);
   w.sort_bytes = gs2d_bin_sort_workspace(n, cap);
   w.sort_ws = c.take<char>(w.sort_bytes);
   w.loss_part = c.take<float>((size_t)nt);
@@ -110,6 +111,12 @@ int32_t* gs2d_track_status(void* workspace) {
   return workspace ? reinterpret_cast<int32_t*>(workspace) : nullptr;
 }
 
+const int32_t* gs2d_track_tile_order(void* workspace, int n, size_t capacity,
+                                     const gs2d_camera* cam, const gs2d_config* cfg) {
+  if (!workspace || !cam || !cfg) return nullptr;
+  return carve_track_ws(static_cast<char*>(workspace) + 256, n, capacity, cam, cfg).order;
+}
+
 int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_config* cfg,
                     const gs2d_track_params* prm, float* pose, const float* obs_rgb, const float* obs_depth, int n_iter, size_t capacity,
                     float* loss_hist, float* pose_hist, void* workspace, size_t ws_bytes,
@@ -144,8 +151,11 @@ int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_co
   // projection, tile counts and tile scan in one launch; the binning keeps
   // the scatter and the per-tile sort
   const int tiles_x = gs2d_tiles_x(cam, cfg);
-  const SortFuse fuse = sort_fuse_args(w.sort_ws, s->n, &bins, tiles_x,
-                                       tiles_x * gs2d_tiles_y(cam, cfg));
+  SortFuse fuse = sort_fuse_args(w.sort_ws, s->n, &bins, tiles_x,
+                                 tiles_x * gs2d_tiles_y(cam, cfg));
+  // the projection's last block also orders the tiles by decreasing list
+  // length; the fused tile kernel launches them in that order
+  fuse.order = w.order;
   for (int it = 0; it < n_iter; ++it) {
     int r = project_launch(s, cam, pose, cfg, w.proj, w.tiles, status, st, &fuse);
     if (r) return r;
@@ -154,7 +164,8 @@ int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_co
     if (r) return r;
     const bool timed = g_timer.used < g_timer.capacity;
     if (timed) GS2D_CUDA_TRY(record_timing_event(g_timer.start[g_timer.used], st));
-    TrackStep ts{pose, w.adam, loss_hist, pose_hist, it, w.counter, zero_begin, zero_words};
+    TrackStep ts{pose, w.adam, loss_hist, pose_hist, it, w.counter, zero_begin, zero_words,
+                 w.order};
     r = track_tile_launch(w.proj, &bins, cam, cfg, obs_rgb, obs_depth, prm, w.loss_part,
                           w.pose_part, ts, status, st);
     if (r) return r;

@@ -101,7 +101,7 @@ EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_stri
            "gs2d_tiles_x", "gs2d_tiles_y", "gs2d_project", "gs2d_bin_sort_workspace",
            "gs2d_bin_sort", "gs2d_render_fwd", "gs2d_render_bwd_workspace", "gs2d_render_bwd",
            "gs2d_tracking_loss", "gs2d_mapping_loss", "gs2d_track_workspace", "gs2d_track_step",
-           "gs2d_track_status", "gs2d_render_count", "gs2d_bin_sort_static",
+           "gs2d_track_status", "gs2d_track_tile_order", "gs2d_render_count", "gs2d_bin_sort_static",
            "gs2d_profile_track_kernel", "gs2d_profile_track_kernel_count",
            "gs2d_project_batch", "gs2d_bin_sort_batch_workspace", "gs2d_bin_sort_batch",
            "gs2d_render_batch_workspace", "gs2d_render_fwd_batch", "gs2d_render_bwd_batch",
@@ -168,6 +168,8 @@ def lib():
         L.gs2d_render_bwd_batch.argtypes = [vp, ip, vp, vp, vp, vp, vp, vp, vp, sz, vp, vp]
         L.gs2d_track_status.restype = vp
         L.gs2d_track_status.argtypes = [vp]
+        L.gs2d_track_tile_order.restype = vp
+        L.gs2d_track_tile_order.argtypes = [vp, ip, sz, vp, vp]
         fl = ctypes.c_float
         L.gs2d_net_param_count.restype = sz
         L.gs2d_net_layout.argtypes = [vp, vp, vp]
@@ -576,6 +578,18 @@ _PROFILE_KEEP = []
 def gs2d_track_status(workspace) -> torch.Tensor:
     """The int32 status word of a track workspace, as a 1-element view."""
     return workspace.view(torch.int32)[:1]
+
+
+def gs2d_track_tile_order(workspace, n: int, capacity: int, cam, cfg) -> torch.Tensor:
+    """The tile launch order of the last tracking iteration (int32 view of
+    the workspace, one entry per tile)."""
+    p = lib().gs2d_track_tile_order(ctypes.c_void_p(workspace.data_ptr()), int(n), int(capacity),
+                                    _ref(cam), _ref(cfg))
+    if not p:
+        raise Gs2dError("gs2d_track_tile_order: invalid arguments")
+    off = p - workspace.data_ptr()
+    nt = int(lib().gs2d_tiles_x(_ref(cam), _ref(cfg))) * int(lib().gs2d_tiles_y(_ref(cam), _ref(cfg)))
+    return workspace[off:off + 4 * nt].view(torch.int32)
 
 
 def gs2d_project_batch(surf: DeviceSurfels, views, stream=None):

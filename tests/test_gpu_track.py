@@ -149,6 +149,37 @@ def test_track_step_first_gradient_and_convergence(torch_cuda, orc, tile, px):
     assert lh[-1] < 0.5 * lh[0]
 
 
+@pytest.mark.parametrize("tile,px", [((16, 16), 1), ((32, 24), 3)])
+def test_track_step_tile_order(torch_cuda, orc, tile, px):
+    """The fused step launches the tiles longest list first: after one
+    iteration the order is a permutation of the tile ids whose list lengths
+    (from a separate binning at the same pose) fall into non-increasing
+    buckets of 1/255 of the longest length."""
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d
+    s, cam, gt = _track_setup(orc, n=30_000, seed=3)
+    ds = gs2d.DeviceSurfels(s)
+    start = scenes.perturb_pose(gt, 0.02, 1.0, seed=8)
+    r, _, _, img = gpu_render(s, cam, start, tile=tile, px=px)
+    counts = (r.ranges[1::2] - r.ranges[0::2]).cpu().numpy().astype(np.int64)
+    ccam, cfg = gs2d.camera(cam), gs2d.default_config(tile, px)
+    prm = gs2d.default_track_params()
+    cap = 8 * s.n
+    ws = torch.empty(gs2d.gs2d_track_workspace(s.n, cap, ccam, cfg), dtype=torch.uint8, device="cuda")
+    pose = gs2d.pose_tensor(start)
+    obs_rgb = torch.tensor(img["rgb"], device="cuda")
+    obs_d = torch.tensor(img["depth"] / np.maximum(img["opacity"], 1e-6), device="cuda") + 0.01
+    gs2d.gs2d_track_step(ds, ccam, cfg, prm, pose, obs_rgb, obs_d, 1, cap, None, None, ws)
+    torch.cuda.synchronize()
+    assert int(gs2d.gs2d_track_status(ws).item()) == 0
+    order = gs2d.gs2d_track_tile_order(ws, s.n, cap, ccam, cfg).cpu().numpy()
+    assert order.shape == counts.shape
+    np.testing.assert_array_equal(np.sort(order), np.arange(len(counts)))
+    bucket = 255 - counts[order] * 255 // max(int(counts.max()), 1)
+    assert np.all(np.diff(bucket) >= 0)
+    assert counts[order[0]] == counts.max()
+
+
 def test_track_step_graph_replay_is_bit_identical(torch_cuda, orc):
     """A tracking frame captured into a CUDA graph and replayed reproduces
     the direct call exactly (every reduction has a fixed order), twice."""
