@@ -45,7 +45,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes per launch of the roofline kernel from an ncu capture of the
 # same workload (profiles/track_tile_tracking_640x480.md); None if the kernel
 # changed since the capture.
-TRAFFIC_BYTES = {"track_tile": 6320128}
+TRAFFIC_BYTES = {"track_tile": 6324480}
 # batched workloads reported beside the tracking line
 MAP_SURFELS, MAP_VIEWS = 1_000_000, 8
 UNEVEN_SURFELS, UNEVEN_VIEWS = 2_000_000, 32
