@@ -201,6 +201,18 @@ int gs2d_render_fwd(const float* proj, const gs2d_bins* bins, const gs2d_camera*
 int gs2d_render_count(const float* proj, const gs2d_bins* bins, const gs2d_camera* cam,
                       const gs2d_config* cfg, unsigned long long* counts, gs2d_stream stream);
 
+/* Scheduling of the one-pixel-per-thread tile kernels of gs2d_render_fwd and
+ * gs2d_track_step (no counterpart in the paper; results do not depend on
+ * it): a tile grid of at most max_tiles tiles runs the grouped form of the
+ * compositing loops, which keeps four (pixel, surfel) evaluations in flight
+ * per thread at two blocks per SM -- for images too small to fill the GPU
+ * (160x120 has 80 tiles of 16x16), where each pixel's serial walk over its
+ * tile's list is the bound.  -1 (the default) = twice the device's SM count;
+ * 0 = never.  Process-wide; read at each launch (so a captured graph keeps
+ * the form it was captured with).  Not thread-safe against concurrent
+ * launches from other host threads. */
+void gs2d_set_grouped_tiles(int max_tiles);
+
 /* Backward of gs2d_render_fwd (Sec. III-B): replays compositing back to
  * front from (t_final, n_last) and returns dL/d(mu, quat, scale, opacity,
  * rgb) per surfel and dL/dtau (rho, theta) of the pose (Eq. derivatives)

@@ -46,8 +46,19 @@
 
 namespace gs2d {
 
-template <bool kCount, int P>
-__global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) render_fwd_kernel(
+// Blocks per SM of the tile kernels: with P pixels per thread, and for the
+// grouped one-pixel loops (kG > 1: kG evaluations in flight per thread,
+// meant for grids too small to fill the GPU, where registers are plentiful
+// and the per-pixel walk's latency is the bound).
+constexpr int kGroup = 4;  // evaluations in flight of the grouped loops
+
+template <int P, int kG>
+constexpr int tile_blocks_per_sm() {
+  return kG > 1 ? 2 : (P == 1 ? 4 : (P == 2 ? 3 : 2));
+}
+
+template <bool kCount, int P, int kG = 1>
+__global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<P, kG>()) render_fwd_kernel(
     const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
     const int32_t* __restrict__ ranges, gs2d_camera cam, gs2d_config cfg, int tiles_x,
     float* __restrict__ out_rgb, float* __restrict__ out_depth, float* __restrict__ out_normal,
@@ -66,8 +77,8 @@ __global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) r
   const float yt = (float)tile_y0 + 0.5f - cam.cy;
   uint32_t cnt[3] = {0u, 0u, 0u};
   FwdState st[P];
-  fwd_tile<kFwdVec4, kCount, P>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0,
-                                tile_y0, tp, inside, cam, cfg, s_rec, hl, cnt, st);
+  fwd_tile<kFwdVec4, kCount, P, kG>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt,
+                                    tile_x0, tile_y0, tp, inside, cam, cfg, s_rec, hl, cnt, st);
   if (kCount) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -164,8 +175,8 @@ __global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) r
 // loss and its image gradient per pixel (in registers), and the pose-only
 // backward replay -- the images never leave the chip.  Writes the tile's
 // loss partial (already divided by |Omega|) and pose 6-vector partial.
-template <int P>
-__global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) track_tile_kernel(
+template <int P, int kG = 1>
+__global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<P, kG>()) track_tile_kernel(
     const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
     const int32_t* __restrict__ ranges, gs2d_camera cam, gs2d_config cfg, int tiles_x,
     const float* __restrict__ obs_rgb, const float* __restrict__ obs_depth, gs2d_track_params prm,
@@ -197,8 +208,8 @@ __global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) t
   const float rx = (tp.px + 0.5f - cam.cx) / cam.fx, ry = (tp.py + 0.5f - cam.cy) / cam.fy;
   const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
   FwdState st[P];
-  fwd_tile<kBwdVec4, false, P>(proj, vals, start, end, xt, yt, tile_x0, tile_y0, tp, inside, cam,
-                               cfg, sm.rec, hl, nullptr, st);
+  fwd_tile<kBwdVec4, false, P, kG>(proj, vals, start, end, xt, yt, tile_x0, tile_y0, tp, inside,
+                                   cam, cfg, sm.rec, hl, nullptr, st);
   float pr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const float inv = 1.f / (float)(cam.width * cam.height);
   PixGrad pg[P];
@@ -235,8 +246,8 @@ __global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) t
       loss_part[tile] = t;
     }
   }
-  bwd_tile_pose<false, P>(proj, vals, start, end, xt, yt, tile_x0, tile_y0, tp, inside, rx, ry, cam,
-                          cfg, pg, sm, hl, pr);
+  bwd_tile_pose<false, P, kG>(proj, vals, start, end, xt, yt, tile_x0, tile_y0, tp, inside, rx, ry,
+                              cam, cfg, pg, sm, hl, pr);
   block_sum6(pr, s_pose, pose_part + (size_t)tile * 6);
   // the last block to finish reduces every tile's partials and updates the pose
   __threadfence();
@@ -403,6 +414,24 @@ int validate_tile_cfg(const gs2d_camera* cam, const gs2d_config* cfg) {
   return GS2D_OK;
 }
 
+// Tile grids of at most this many tiles run the grouped one-pixel loops
+// (-1: twice the device's SM count, i.e. at most two blocks per SM).
+static int g_grouped_max_tiles = -1;
+
+// Whether a one-pixel tile kernel over n_tiles tiles takes the grouped loops.
+static bool use_grouped(int px_per_thread, int n_tiles) {
+  if (px_per_thread != 1) return false;
+  int limit = g_grouped_max_tiles;
+  if (limit < 0) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return false;
+    limit = 2 * sms;
+  }
+  return n_tiles <= limit;
+}
+
 int render_fwd_launch(const float* proj, const gs2d_bins* bins, const gs2d_camera* cam,
                       const gs2d_config* cfg, float* rgb, float* depth, float* normal,
                       float* opacity, float* t_final, uint32_t* n_last, const int32_t* gate,
@@ -414,9 +443,14 @@ int render_fwd_launch(const float* proj, const gs2d_bins* bins, const gs2d_camer
     return GS2D_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(proj) & 15) return GS2D_ERR_INVALID_ARG;
   const int tx = gs2d_tiles_x(cam, cfg), ty = gs2d_tiles_y(cam, cfg);
-  GS2D_DISPATCH_P(cfg->px_per_thread, render_fwd_kernel<false, P><<<tx * ty, kTileThreads, 0, st>>>(
-      reinterpret_cast<const float4*>(proj), bins->vals, bins->tile_ranges, *cam, *cfg, tx, rgb,
-      depth, normal, opacity, t_final, n_last, nullptr, gate));
+  if (use_grouped(cfg->px_per_thread, tx * ty))
+    render_fwd_kernel<false, 1, kGroup><<<tx * ty, kTileThreads, 0, st>>>(
+        reinterpret_cast<const float4*>(proj), bins->vals, bins->tile_ranges, *cam, *cfg, tx, rgb,
+        depth, normal, opacity, t_final, n_last, nullptr, gate);
+  else
+    GS2D_DISPATCH_P(cfg->px_per_thread, render_fwd_kernel<false, P><<<tx * ty, kTileThreads, 0, st>>>(
+        reinterpret_cast<const float4*>(proj), bins->vals, bins->tile_ranges, *cam, *cfg, tx, rgb,
+        depth, normal, opacity, t_final, n_last, nullptr, gate));
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
 }
@@ -431,9 +465,14 @@ int track_tile_launch(const float* proj, const gs2d_bins* bins, const gs2d_camer
       !loss_part || !pose_part || !ts.pose || !ts.adam || !ts.counter || !status)
     return GS2D_ERR_INVALID_ARG;
   const int tx = gs2d_tiles_x(cam, cfg), ty = gs2d_tiles_y(cam, cfg);
-  GS2D_DISPATCH_P(cfg->px_per_thread, track_tile_kernel<P><<<tx * ty, kTileThreads, 0, st>>>(
-      reinterpret_cast<const float4*>(proj), bins->vals, bins->tile_ranges, *cam, *cfg, tx, obs_rgb,
-      obs_depth, *prm, loss_part, pose_part, ts, status));
+  if (use_grouped(cfg->px_per_thread, tx * ty))
+    track_tile_kernel<1, kGroup><<<tx * ty, kTileThreads, 0, st>>>(
+        reinterpret_cast<const float4*>(proj), bins->vals, bins->tile_ranges, *cam, *cfg, tx,
+        obs_rgb, obs_depth, *prm, loss_part, pose_part, ts, status);
+  else
+    GS2D_DISPATCH_P(cfg->px_per_thread, track_tile_kernel<P><<<tx * ty, kTileThreads, 0, st>>>(
+        reinterpret_cast<const float4*>(proj), bins->vals, bins->tile_ranges, *cam, *cfg, tx,
+        obs_rgb, obs_depth, *prm, loss_part, pose_part, ts, status));
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
 }
@@ -547,6 +586,8 @@ int gs2d_render_count(const float* proj, const gs2d_bins* bins, const gs2d_camer
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
 }
+
+void gs2d_set_grouped_tiles(int max_tiles) { g_grouped_max_tiles = max_tiles < -1 ? -1 : max_tiles; }
 
 size_t gs2d_render_bwd_workspace(int n, size_t capacity, int n_tiles) {
   return render_bwd_ws_bytes(n, capacity, n_tiles, true);

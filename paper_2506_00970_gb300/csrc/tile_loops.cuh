@@ -189,7 +189,12 @@ struct HitLists {
   uint8_t list[kTileThreads / 32][kTileThreads];
 };
 
-template <int kStride, bool kCount, int P>
+// kG > 1 (one pixel per thread, no counting): the warp's hits are taken kG at
+// a time -- their records loaded and their (pixel, surfel) pairs evaluated
+// independently, then blended in list order -- so a pixel's walk keeps kG
+// evaluations in flight instead of one.  Same evaluations, same order, same
+// results; pairs after a pixel's stop are evaluated and dropped.
+template <int kStride, bool kCount, int P, int kG = 1>
 __device__ __forceinline__ void fwd_tile(const float4* __restrict__ proj,
                                          const uint32_t* __restrict__ vals, int start, int end,
                                          float xt, float yt, int tile_x0, int tile_y0,
@@ -227,7 +232,48 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ proj,
     __syncthreads();
     const int cnt_b = min(kTileThreads, end - b);
     const int nh = warp_hit_list(hl.mask, hl.list[warp], cnt_b, warp, lane);
-    if (P == 1 && !all_done) {
+    if (P == 1 && kG > 1 && !kCount && !all_done) {
+      FwdState& q = st[0];
+      for (int h0 = 0; h0 < nh && !all_done; h0 += kG) {
+        int jg[kG];
+        float ag[kG], zg[kG], cg[kG];
+        bool hg[kG];
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+          // past the end: re-evaluate the last hit, never blended
+          jg[g] = hl.list[warp][min(h0 + g, nh - 1)];
+          const float4 r0 = s_rec[jg[g]][0], r1 = s_rec[jg[g]][1], r2 = s_rec[jg[g]][2];
+          Eval e;
+          hg[g] = eval_pair(r0, r1, r2, tp.lx, tp.ly, cam.near_z, cfg.cutoff_r2, cfg.alpha_min,
+                            cfg.alpha_max, e) &&
+                  h0 + g < nh;
+          ag[g] = e.a;
+          zg[g] = e.z;
+          cg[g] = r2.w;
+        }
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+          if (!hg[g]) continue;
+          const float Tn = q.T * (1.f - ag[g]);
+          if (Tn < cfg.t_min) {
+            all_done = true;
+            break;
+          }
+          const float4 r3 = s_rec[jg[g]][3];
+          const float tnz = s_rec[jg[g]][4].x;
+          const float w = ag[g] * q.T;
+          q.C.x = fmaf(w, cg[g], q.C.x);
+          q.C.y = fmaf(w, r3.x, q.C.y);
+          q.C.z = fmaf(w, r3.y, q.C.z);
+          q.D = fmaf(w, zg[g], q.D);
+          q.N.x = fmaf(w, r3.z, q.N.x);
+          q.N.y = fmaf(w, r3.w, q.N.y);
+          q.N.z = fmaf(w, tnz, q.N.z);
+          q.T = Tn;
+          q.last = (uint32_t)(b + jg[g] + 1 - start);
+        }
+      }
+    } else if (P == 1 && !all_done) {
       // one pixel: stop at its saturation
       FwdState& q = st[0];
       for (int h = 0; h < nh; ++h) {
@@ -492,6 +538,45 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ proj,
   }
 }
 
+// One replayed (pixel, surfel) pair of the pose-only backward: the blending
+// gradient from the running state (T, acc) and the pair's rank-one splat
+// gradient Gv, accumulated as sum Gv and sum z Gv (and the blended normals
+// for the normal image's term).  rec: the staged record; r2 its third float4.
+template <bool kNormal>
+__device__ __forceinline__ void pose_pair(const Eval& e, const float4 r2, const float4* rec,
+                                          const PixGrad& pgk, float rx, float ryk, float fxfy,
+                                          float alpha_max, float gOT, float& T, float& acc, F3& sG,
+                                          F3& szG, F3& sN) {
+  const F3 gC = pgk.gC, gN = pgk.gN;
+  const float gD = pgk.gD;
+  const float4 r3 = rec[3], r4 = rec[4], r5 = rec[5], r6 = rec[6];
+  const float iom = __fdividef(1.f, 1.f - e.a);
+  const float Tb = T * iom;
+  const float w = e.a * Tb;
+  float vj = fmaf(r2.w, gC.x, fmaf(r3.x, gC.y, fmaf(r3.y, gC.z, e.z * gD)));
+  if (kNormal) vj = fmaf(r3.z, gN.x, fmaf(r3.w, gN.y, fmaf(r4.x, gN.z, vj)));
+  const float ga = Tb * vj - (acc - gOT) * iom;
+  acc = fmaf(w, vj, acc);
+  T = Tb;
+  const float s = e.araw <= alpha_max ? -e.G * r2.z * ga : 0.f;
+  // P = u d_u + v d_v; q = s P
+  const float Px = fmaf(e.u, r5.x, e.v * r5.w);
+  const float Py = fmaf(e.u, r5.y, e.v * r6.x);
+  const float Pz = fmaf(e.u, r5.z, e.v * r6.y);
+  const float Pr = fmaf(Px, rx, fmaf(Py, ryk, Pz));
+  const float beta = fmaf(s, Pr, w * gD) * fxfy * e.rinv;
+  const float Gx = fmaf(beta, r4.y, -s * Px);
+  const float Gy = fmaf(beta, r4.z, -s * Py);
+  const float Gz = fmaf(beta, r4.w, -s * Pz);
+  sG.x += Gx;
+  sG.y += Gy;
+  sG.z += Gz;
+  szG.x = fmaf(e.z, Gx, szG.x);
+  szG.y = fmaf(e.z, Gy, szG.y);
+  szG.z = fmaf(e.z, Gz, szG.z);
+  if (kNormal) sN = sN + w * f3(r3.z, r3.w, r4.x);
+}
+
 // Pose-only back-to-front replay (tracking): like bwd_tile but each warp
 // visits only the surfels whose footprint touches its block, and the pose
 // gradient is accumulated per pixel.  With the hit point X = z r and r fixed
@@ -499,7 +584,10 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ proj,
 // and z Gv; with q = s (u d_u + v d_v), s = -G dL/dG, the pair's
 // Gv = beta n - q, beta = (q . r + gz) / (n . r).  kNormal adds the normal
 // image's term t_nc x w gN per pair (tracking has no normal gradient).
-template <bool kNormal, int P>
+// kG > 1 (one pixel per thread): hits are taken kG at a time, their pairs
+// evaluated independently and then replayed in back-to-front order (as in
+// fwd_tile).
+template <bool kNormal, int P, int kG = 1>
 __device__ __forceinline__ void bwd_tile_pose(const float4* __restrict__ proj,
                                               const uint32_t* __restrict__ vals, int start, int end,
                                               float xt, float yt, int tile_x0, int tile_y0,
@@ -551,6 +639,30 @@ __device__ __forceinline__ void bwd_tile_pose(const float4* __restrict__ proj,
     __syncthreads();
     const int nh = warp_hit_list(hl.mask, hl.list[warp], cnt, warp, lane);
     if (!any_inside) continue;
+    if (P == 1 && kG > 1) {
+      for (int h0 = nh - 1; h0 >= 0; h0 -= kG) {
+        int jg[kG];
+        bool vg[kG];
+        Eval eg[kG];
+        float4 r2g[kG];
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+          // before the start: re-evaluate the first hit, never replayed
+          jg[g] = hl.list[warp][max(h0 - g, 0)];
+          const float4 r0 = sm.rec[jg[g]][0], r1 = sm.rec[jg[g]][1];
+          r2g[g] = sm.rec[jg[g]][2];
+          vg[g] = eval_pair(r0, r1, r2g[g], tp.lx, lyk[0], cam.near_z, cfg.cutoff_r2,
+                            cfg.alpha_min, cfg.alpha_max, eg[g]) &&
+                  h0 - g >= 0 && bstart + jg[g] - start < (int)pg[0].nl;
+        }
+#pragma unroll
+        for (int g = 0; g < kG; ++g)
+          if (vg[g])
+            pose_pair<kNormal>(eg[g], r2g[g], sm.rec[jg[g]], pg[0], rx, ryk[0], fxfy,
+                               cfg.alpha_max, gOT[0], T[0], acc[0], sG, szG[0], sN[0]);
+      }
+      continue;
+    }
     for (int h = nh - 1; h >= 0; --h) {
       const int jj = hl.list[warp][h];
       const int jrel = bstart + jj - start;
@@ -562,34 +674,8 @@ __device__ __forceinline__ void bwd_tile_pose(const float4* __restrict__ proj,
         if (!eval_pair(r0, r1, r2, tp.lx, lyk[k], cam.near_z, cfg.cutoff_r2, cfg.alpha_min,
                        cfg.alpha_max, e))
           continue;
-        const F3 gC = pg[k].gC, gN = pg[k].gN;
-        const float gD = pg[k].gD;
-        const float4 r3 = sm.rec[jj][3], r4 = sm.rec[jj][4], r5 = sm.rec[jj][5], r6 = sm.rec[jj][6];
-        const float iom = __fdividef(1.f, 1.f - e.a);
-        const float Tb = T[k] * iom;
-        const float w = e.a * Tb;
-        float vj = fmaf(r2.w, gC.x, fmaf(r3.x, gC.y, fmaf(r3.y, gC.z, e.z * gD)));
-        if (kNormal) vj = fmaf(r3.z, gN.x, fmaf(r3.w, gN.y, fmaf(r4.x, gN.z, vj)));
-        const float ga = Tb * vj - (acc[k] - gOT[k]) * iom;
-        acc[k] = fmaf(w, vj, acc[k]);
-        T[k] = Tb;
-        const float s = e.araw <= cfg.alpha_max ? -e.G * r2.z * ga : 0.f;
-        // P = u d_u + v d_v; q = s P
-        const float Px = fmaf(e.u, r5.x, e.v * r5.w);
-        const float Py = fmaf(e.u, r5.y, e.v * r6.x);
-        const float Pz = fmaf(e.u, r5.z, e.v * r6.y);
-        const float Pr = fmaf(Px, rx, fmaf(Py, ryk[k], Pz));
-        const float beta = fmaf(s, Pr, w * gD) * fxfy * e.rinv;
-        const float Gx = fmaf(beta, r4.y, -s * Px);
-        const float Gy = fmaf(beta, r4.z, -s * Py);
-        const float Gz = fmaf(beta, r4.w, -s * Pz);
-        sG.x += Gx;
-        sG.y += Gy;
-        sG.z += Gz;
-        szG[k].x = fmaf(e.z, Gx, szG[k].x);
-        szG[k].y = fmaf(e.z, Gy, szG[k].y);
-        szG[k].z = fmaf(e.z, Gz, szG[k].z);
-        if (kNormal) sN[k] = sN[k] + w * f3(r3.z, r3.w, r4.x);
+        pose_pair<kNormal>(e, r2, sm.rec[jj], pg[k], rx, ryk[k], fxfy, cfg.alpha_max, gOT[k], T[k],
+                           acc[k], sG, szG[k], sN[k]);
       }
     }
   }

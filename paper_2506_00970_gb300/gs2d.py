@@ -102,6 +102,7 @@ EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_stri
            "gs2d_bin_sort", "gs2d_render_fwd", "gs2d_render_bwd_workspace", "gs2d_render_bwd",
            "gs2d_tracking_loss", "gs2d_mapping_loss", "gs2d_track_workspace", "gs2d_track_step",
            "gs2d_track_status", "gs2d_track_tile_order", "gs2d_render_count", "gs2d_bin_sort_static",
+           "gs2d_set_grouped_tiles",
            "gs2d_profile_track_kernel", "gs2d_profile_track_kernel_count",
            "gs2d_project_batch", "gs2d_bin_sort_batch_workspace", "gs2d_bin_sort_batch",
            "gs2d_render_batch_workspace", "gs2d_render_fwd_batch", "gs2d_render_bwd_batch",
@@ -148,6 +149,8 @@ def lib():
         L.gs2d_bin_sort_static.argtypes = [vp, vp, ip, vp, vp, vp, vp]
         L.gs2d_render_fwd.argtypes = [vp] * 11
         L.gs2d_render_count.argtypes = [vp] * 6
+        L.gs2d_set_grouped_tiles.argtypes = [ip]
+        L.gs2d_set_grouped_tiles.restype = None
         L.gs2d_render_bwd_workspace.restype = sz
         L.gs2d_render_bwd_workspace.argtypes = [ip, sz, ip]
         L.gs2d_render_bwd.argtypes = [vp] * 20 + [sz, vp, vp]
@@ -333,6 +336,12 @@ def gs2d_render_fwd(proj, bins: Bins, cam: Camera, cfg: Config, rgb, depth, norm
 def gs2d_render_count(proj, bins: Bins, cam: Camera, cfg: Config, counts, stream=None):
     check(lib().gs2d_render_count(_ptr(proj), _ref(bins), _ref(cam), _ref(cfg), _ptr(counts),
                                   _stream(stream)), "gs2d_render_count")
+
+
+def gs2d_set_grouped_tiles(max_tiles: int):
+    """Tile grids of at most max_tiles tiles run the grouped one-pixel
+    compositing loops (-1: twice the SM count, the default; 0: never)."""
+    lib().gs2d_set_grouped_tiles(int(max_tiles))
 
 
 def gs2d_render_contrib_workspace(capacity) -> int:
