@@ -901,9 +901,11 @@ def learned_proposal(flush):
                         "speedup_median": one["speedup_median"]},
         "net": {"fwd_batch256_ms": f_ms, "train_step_batch256_ms": s_ms,
                 "fwd_gflop_per_batch": fl_f * 256 / 1e9, "train_gflop_per_batch": fl_t * 256 / 1e9,
-                "roofline": {"kernel": "network forward: gemm_kernel (mma.sync bf16) for the convolution "
-                                       "and FC products; training adds gemm_tc_kernel (tcgen05 + TMEM) "
-                                       "for the split-K weight gradients", "bound": "tensor",
+                "roofline": {"kernel": "network forward: conv_s2_kernel (direct, mma.sync bf16) for "
+                                       "the first convolution, gemm_kernel (mma.sync bf16) for the "
+                                       "others and the FC products, gemm_tc_kernel (tcgen05 + TMEM) "
+                                       "for the split deep layers; training adds gemm_tc_kernel for "
+                                       "the split-K weight gradients", "bound": "tensor",
                              "achieved": fl_f * 256 / (f_ms / 1e3) / 1e12, "peak": peak,
                              "unit": "TFLOP/s", "frac": fl_f * 256 / (f_ms / 1e3) / 1e12 / peak,
                              "train_achieved": fl_t * 256 / (s_ms / 1e3) / 1e12,

@@ -2,10 +2,11 @@
 // starting pose of the tracking loop of Sec. III-D): forward, loss,
 // backward and AdamW on BF16 tensor cores with FP32 accumulation.
 //
-// Every contraction of the network -- each convolution's forward (implicit
-// im2col GEMM), data gradient (stride-2 transposed gather) and weight
-// gradient (split-K GEMM over the pixels), and each fully connected layer's
-// three products -- runs through one tiled GEMM kernel
+// Every contraction of the network but the first layer's forward (a direct
+// convolution kernel, conv_s2_kernel below) -- each convolution's forward
+// (implicit im2col GEMM), data gradient (stride-2 transposed gather) and
+// weight gradient (split-K GEMM over the pixels), and each fully connected
+// layer's three products -- runs through one tiled GEMM kernel
 //     C[M, N] = sum_k A[m, k] B[n, k]
 // whose operand tiles are gathered straight from the NHWC activations and
 // the weights by an address mode (no im2col buffer is materialised):
@@ -600,6 +601,199 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const Gemm g) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS));
 }
 
+// ---------------------------------------------------------------------------
+// Direct convolution of the first layer (stride 2, 3 x 3 taps, zero padding
+// 1, C_in = 8: one 16-byte chunk per pixel).  A tile is RB whole output rows of one image
+// (RB Wo pixels) for all C_out channels.  The grid is resident (blocks per
+// SM from the occupancy calculator) and each block walks the tiles
+// t = blockIdx.x, + gridDim.x, ...: it copies the layer's weights into
+// shared memory once, and for every tile the 2 RB + 1 input rows its pixels
+// read (zero rows and columns where the padding lies), the next tile's rows
+// in flight (cp.async, two buffers) while the current one computes.  Each
+// warp gathers the A fragments of its 32 pixels -- their im2col rows, 8
+// channels of one tap per 16-byte ldmatrix row -- straight from the staged
+// rows and issues mma.m16n8k16.  Against the implicit-im2col GEMM, an input
+// pixel leaves global memory once per tile instead of once per tap, the
+// weights once per block, and no tile column is padding (C_out = 32 would
+// fill half of a 64-wide tile).
+// Staged rows: [row][column parity][column / 2][C_in] over the columns
+// ix + 1 = 0 .. W + 1: pixels ox, ox + 1 read columns 2 ox + kx and
+// 2 ox + 2 + kx under one tap, neighbours in one parity plane, so the eight
+// pixels of an ldmatrix row group are eight consecutive 16-byte entries
+// (distinct banks).  Layer 1 (input 79 MB, output 79 MB at batch 256) takes
+// 55 us here against 124 us as an implicit-im2col GEMM.  The same scheme for
+// layer 2 (C_in = 32; two 47 KB row buffers leave one block per SM) took
+// 80-95 us against the GEMM's 62 us, so layer 2 stays a GEMM.
+template <int CIN, int COUT, int H, int W, int RB>
+struct ConvS2 {
+  static constexpr int Ho = H / 2, Wo = W / 2;
+  static constexpr int PIX = RB * Wo;               // output pixels per tile
+  static constexpr int TPI = (Ho + RB - 1) / RB;    // tiles per image
+  static constexpr int WARPS = (PIX + 31) / 32;     // 32 pixels per warp
+  static constexpr int NTHREADS = WARPS * 32;
+  static constexpr int RIN = 2 * RB + 1;            // staged input rows
+  static constexpr int WP = (W + 2) / 2;            // entries per parity plane
+  static constexpr int NCH = CIN / 8;               // 16-byte chunks per pixel
+  static constexpr int K = 9 * CIN;
+  static constexpr int KS = (K + 15) / 16;          // k16 steps
+  static constexpr int KP = KS * 16 + 8;            // staged weight row, padded
+  static constexpr int NT = COUT / 8;               // n8 tiles
+  static constexpr int PATCH = RIN * 2 * WP * CIN;  // bf16 elements per buffer
+  static constexpr int WSM = COUT * KP;
+  static constexpr int SMEM = (2 * PATCH + WSM + 8) * 2;  // + one zero chunk
+  static_assert(CIN == 8, "one 16-byte chunk per pixel");
+  static_assert(H % 2 == 0 && W % 2 == 0 && COUT % 16 == 0, "shape");
+  static_assert(PATCH % 8 == 0 && KP % 8 == 0, "16-byte rows");
+};
+
+// Issues the cp.async copies of tile t's input rows into patch.
+template <class C, int CIN, int H, int W>
+__device__ __forceinline__ void conv_stage_rows(bf16* patch, const bf16* __restrict__ x, int t) {
+  const int b = t / C::TPI, iy0 = 2 * (t - b * C::TPI) * (C::PIX / C::Wo) - 1;
+  const bf16* xb = x + (size_t)b * H * W * CIN;
+  constexpr int ROWCH = (W + 2) * C::NCH;
+  for (int e = threadIdx.x; e < C::RIN * ROWCH; e += C::NTHREADS) {
+    const int r = e / ROWCH, rem = e - r * ROWCH;
+    const int c = rem / C::NCH, q = rem - c * C::NCH;
+    const int iy = iy0 + r, ix = c - 1;
+    const bool ok = iy >= 0 && iy < H && ix >= 0 && ix < W;
+    const int ent = c >> 1;
+    bf16* dst = patch + ((r * 2 + (c & 1)) * C::WP + ent) * CIN + q * 8;
+    cp_async16(dst, ok ? xb + ((size_t)iy * W + ix) * CIN + q * 8 : xb, ok);
+  }
+}
+
+template <int CIN, int COUT, int H, int W, int RB>
+__global__ void __launch_bounds__(ConvS2<CIN, COUT, H, W, RB>::NTHREADS) conv_s2_kernel(
+    const bf16* __restrict__ x, const bf16* __restrict__ wt, const float* __restrict__ bias,
+    bf16* __restrict__ out, int n_tiles) {
+  using C = ConvS2<CIN, COUT, H, W, RB>;
+  extern __shared__ __align__(128) unsigned char conv_smem[];
+  bf16* patches = reinterpret_cast<bf16*>(conv_smem);
+  bf16* wsm = patches + 2 * C::PATCH;
+  bf16* zero = wsm + C::WSM;
+  // weights [C_out][K] -> rows of KP, zero past K (copy group 0)
+  constexpr int WCH = C::KP / 8;
+  for (int e = threadIdx.x; e < COUT * WCH; e += C::NTHREADS) {
+    const int n = e / WCH, q = e - n * WCH;
+    const bool ok = q * 8 < C::K;
+    cp_async16(wsm + n * C::KP + q * 8, ok ? wt + (size_t)n * C::K + q * 8 : wt, ok);
+  }
+  if (threadIdx.x == 0) *reinterpret_cast<uint4*>(zero) = make_uint4(0u, 0u, 0u, 0u);
+  if ((int)blockIdx.x < n_tiles) conv_stage_rows<C, CIN, H, W>(patches, x, blockIdx.x);
+  cp_async_commit();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mat = lane >> 3, rr = lane & 7;
+  const int gq = lane >> 2, cq = lane & 3;
+  // this lane's ldmatrix row in m16 tile i: pixel 32 warp + 16 i + rr + 8 (mat & 1)
+  int prow[2], pcol[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int m = 32 * warp + 16 * i + rr + 8 * (mat & 1);
+    const int dy = m / C::Wo;
+    prow[i] = 2 * dy;
+    pcol[i] = m - dy * C::Wo;
+  }
+  int it = 0;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
+    // the next tile's rows go to the other buffer, which the previous
+    // iteration finished reading before its closing barrier
+    const int tn = t + (int)gridDim.x;
+    if (tn < n_tiles) conv_stage_rows<C, CIN, H, W>(patches + ((it + 1) & 1) * C::PATCH, x, tn);
+    cp_async_commit();
+    cp_async_wait<1>();  // the weights and this tile's rows have landed
+    __syncthreads();
+    const bf16* patch = patches + (it & 1) * C::PATCH;
+    const int b = t / C::TPI, oy0 = (t - b * C::TPI) * RB;
+    bool pok[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int m = 32 * warp + 16 * i + rr + 8 * (mat & 1);
+      pok[i] = m < C::PIX && oy0 + prow[i] / 2 < C::Ho;
+    }
+    float acc[2][C::NT][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int n8 = 0; n8 < C::NT; ++n8)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[i][n8][v] = 0.f;
+#pragma unroll 2
+    for (int s = 0; s < C::KS; ++s) {
+      const int k = 16 * s + 8 * (mat >> 1);  // this lane's k offset
+      const int tap = k / CIN, q = (k % CIN) / 8;
+      const int ky = tap / 3, kx = tap - 3 * ky;
+      uint32_t af[2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const bf16* src = zero;
+        if (pok[i] && tap < 9) {
+          const int r = prow[i] + ky, c = 2 * pcol[i] + kx, ent = c >> 1;
+          src = patch + ((r * 2 + (c & 1)) * C::WP + ent) * CIN + q * 8;
+        }
+        ldsm_x4(af[i], src);
+      }
+#pragma unroll
+      for (int jj = 0; jj < C::NT / 2; ++jj) {
+        uint32_t bfr[4];
+        ldsm_x4(bfr, wsm + (16 * jj + rr + 8 * (mat >> 1)) * C::KP + 16 * s + 8 * (mat & 1));
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          mma_bf16(acc[i][2 * jj], af[i], bfr[0], bfr[1]);
+          mma_bf16(acc[i][2 * jj + 1], af[i], bfr[2], bfr[3]);
+        }
+      }
+    }
+    // bias + ReLU -> bf16, NHWC rows of C_out
+    bf16* ob = out + ((size_t)b * C::Ho + oy0) * C::Wo * COUT;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = 32 * warp + 16 * i + gq + 8 * h;
+        if (m >= C::PIX || oy0 + m / C::Wo >= C::Ho) continue;
+#pragma unroll
+        for (int n8 = 0; n8 < C::NT; ++n8) {
+          const int col = 8 * n8 + 2 * cq;
+          const float x0 = fmaxf(acc[i][n8][2 * h] + bias[col], 0.f);
+          const float x1 = fmaxf(acc[i][n8][2 * h + 1] + bias[col + 1], 0.f);
+          *reinterpret_cast<__nv_bfloat162*>(ob + (size_t)m * COUT + col) =
+              __floats2bfloat162_rn(x0, x1);
+        }
+      }
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+}
+
+static_assert(kCin[0] == 8 && kCout[0] == 32 && kHin[0] == 120 && kWin[0] == 160, "layer 1");
+
+// Launches the direct kernel over the B images (a resident grid).
+template <int CIN, int COUT, int H, int W, int RB>
+int conv_s2(const bf16* x, int B, const bf16* wt, const float* bias, bf16* out, cudaStream_t st) {
+  using C = ConvS2<CIN, COUT, H, W, RB>;
+  auto kernel = conv_s2_kernel<CIN, COUT, H, W, RB>;
+  static int slots[64] = {};  // resident blocks per device (0: not yet known)
+  int dev = 0;
+  GS2D_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return GS2D_ERR_CUDA;
+  if (!slots[dev]) {
+    GS2D_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    int per_sm = 0, sms = 0;
+    GS2D_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, C::NTHREADS, C::SMEM));
+    GS2D_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    slots[dev] = max(1, per_sm) * max(1, sms);
+  }
+  if (B <= 0) return GS2D_OK;
+  const long long n_tiles = (long long)B * C::TPI;
+  if (n_tiles > 0x7FFFFFFF) return GS2D_ERR_INVALID_ARG;
+  const int grid = (int)(n_tiles < (long long)slots[dev] ? n_tiles : (long long)slots[dev]);
+  kernel<<<grid, C::NTHREADS, C::SMEM, st>>>(x, wt, bias, out, (int)n_tiles);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
 // out[m * n_out + n] = sum_s part[(s * M + m) * N + n] for m < m_valid,
 // n < n_valid, summed in split order.
 __global__ void reduce_partials_kernel(const float* __restrict__ part, int S, int M, int N,
@@ -1088,8 +1282,11 @@ int forward(const float* params, const bf16* x, int B, const Ws& w, float* y, cu
   GS2D_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   int r = do_cast ? cast(params, w, st) : GS2D_OK;
   if (r) return r;
-  const bf16* in = x;
-  for (int l = 0; l < kConv; ++l) {
+  // layer 1: the direct kernel
+  r = conv_s2<8, 32, 120, 160, 2>(x, B, w.wbf + L.wbf_off[0], params + L.b_off[0], w.act[1], st);
+  if (r) return r;
+  const bf16* in = w.act[1];
+  for (int l = 1; l < kConv; ++l) {
     Gemm g{};
     g.err = w.err;
     g.M = B * kHin[l + 1] * kWin[l + 1];
