@@ -155,9 +155,11 @@ int gs2d_project(const gs2d_surfels* s, const gs2d_camera* cam, const float* pos
 
 /* Tile binning and depth ordering ("sorts them by depth", Sec. III-A): every
  * surfel with k_i > 0 emits one intersection per tile of its rectangle; the
- * intersections are ordered by (tile, mu_c.z bits, surfel id) -- a stable
- * sort by tile of the depth-ordered emission -- with hand-written LSD radix
- * passes.  proj: device [n * GS2D_PROJ_FLOATS] (only slots 26, 28, 29 are
+ * intersections are ordered by (tile, mu_c.z bits, surfel id) -- the order
+ * of a stable sort by tile of the depth-ordered emission -- by binning the
+ * pairs into per-tile segments and sorting every segment by (depth bits, id)
+ * in shared memory (hand-written bitonic networks; long segments in chunks
+ * merged in global memory), so the result is unique and deterministic.  proj: device [n * GS2D_PROJ_FLOATS] (only slots 26, 28, 29 are
  * read).  tiles_per_surfel: device [n], must equal the rectangle's tile count.
  * Workspace: gs2d_bin_sort_workspace(n, capacity) bytes. */
 size_t gs2d_bin_sort_workspace(int n, size_t capacity);
