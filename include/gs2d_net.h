@@ -130,6 +130,21 @@ int gs2d_net_target(const float* poses_init, const float* poses_gt, int batch, f
 int gs2d_net_accept(const float* loss_prop, const float* loss_init, const float* proposal,
                     int batch, float* poses, int32_t* accepted, gs2d_stream stream);
 
+/* gs2d_net_accept that also keeps what the kept pose's next proposal pass
+ * needs, so the network can refine its own proposal without rendering the
+ * kept pose again: where proposal b is taken, its rendered images (prop_rgb
+ * [n_px*3], prop_depth and prop_opacity [n_px] per element, as
+ * gs2d_render_fwd writes them) are copied over kept_rgb / kept_depth /
+ * kept_opacity (the images of the current pose), and loss_prop[b] over
+ * loss_init[b]; elsewhere both stay as they are.  Renders are deterministic,
+ * so the kept images equal a new render at the kept pose bit for bit.  The
+ * copy runs before the poses and losses change (two kernels in stream
+ * order). */
+int gs2d_net_accept_keep(const float* loss_prop, float* loss_init, const float* proposal, int batch,
+                         float* poses, int32_t* accepted, size_t n_px, const float* prop_rgb,
+                         const float* prop_depth, const float* prop_opacity, float* kept_rgb,
+                         float* kept_depth, float* kept_opacity, gs2d_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

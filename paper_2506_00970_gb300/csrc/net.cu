@@ -30,6 +30,8 @@
 // mma.m16n8k16 bf16 x bf16 -> f32.  Epilogues: bias + ReLU -> bf16, bias ->
 // f32, ReLU mask of the stored activation -> bf16, or FP32 split-K partials
 // that a second kernel sums in a fixed order.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -1025,6 +1027,45 @@ __global__ void accept_kernel(const float* __restrict__ lp, const float* __restr
   if (accepted) accepted[b] = take ? 1 : 0;
 }
 
+// Where the proposal of element b is taken (the same test as accept_kernel,
+// evaluated before accept_kernel updates anything), its rendered images
+// replace the kept ones: n_px pixels of colour (3 floats), accumulated depth
+// and opacity per element.
+__global__ void keep_images_kernel(const float* __restrict__ lp, const float* __restrict__ li,
+                                   int B, size_t n_px, const float* __restrict__ p_rgb,
+                                   const float* __restrict__ p_d, const float* __restrict__ p_o,
+                                   float* __restrict__ k_rgb, float* __restrict__ k_d,
+                                   float* __restrict__ k_o) {
+  const size_t per = 5 * n_px;  // floats per element: rgb, depth, opacity
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)B * per;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = e / per, r = e - b * per;
+    if (!(lp[b] <= li[b])) continue;
+    if (r < 3 * n_px) {
+      k_rgb[b * 3 * n_px + r] = p_rgb[b * 3 * n_px + r];
+    } else if (r < 4 * n_px) {
+      k_d[b * n_px + r - 3 * n_px] = p_d[b * n_px + r - 3 * n_px];
+    } else {
+      k_o[b * n_px + r - 4 * n_px] = p_o[b * n_px + r - 4 * n_px];
+    }
+  }
+}
+
+// accept_kernel, and the kept pose's loss: loss_init[b] <- loss_prop[b]
+// where the proposal is taken.
+__global__ void accept_loss_kernel(const float* __restrict__ lp, float* __restrict__ li,
+                                   const float* __restrict__ prop, int B, float* __restrict__ poses,
+                                   int32_t* __restrict__ accepted) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const bool take = lp[b] <= li[b];
+  if (take) {
+    for (int k = 0; k < 12; ++k) poses[12 * b + k] = prop[12 * b + k];
+    li[b] = lp[b];
+  }
+  if (accepted) accepted[b] = take ? 1 : 0;
+}
+
 // ---------------------------------------------------------------------------
 // host side
 struct Layout {
@@ -1594,6 +1635,25 @@ int gs2d_net_accept(const float* loss_prop, const float* loss_init, const float*
   if (batch <= 0 || !loss_prop || !loss_init || !proposal || !poses) return GS2D_ERR_INVALID_ARG;
   accept_kernel<<<(batch + 127) / 128, 128, 0, (cudaStream_t)stream>>>(loss_prop, loss_init, proposal,
                                                                       batch, poses, accepted);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+int gs2d_net_accept_keep(const float* loss_prop, float* loss_init, const float* proposal, int batch,
+                         float* poses, int32_t* accepted, size_t n_px, const float* prop_rgb,
+                         const float* prop_depth, const float* prop_opacity, float* kept_rgb,
+                         float* kept_depth, float* kept_opacity, gs2d_stream stream) {
+  if (batch <= 0 || n_px == 0 || !loss_prop || !loss_init || !proposal || !poses || !prop_rgb ||
+      !prop_depth || !prop_opacity || !kept_rgb || !kept_depth || !kept_opacity)
+    return GS2D_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t total = (size_t)batch * 5 * n_px;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
+  keep_images_kernel<<<blocks, 256, 0, st>>>(loss_prop, loss_init, batch, n_px, prop_rgb, prop_depth,
+                                             prop_opacity, kept_rgb, kept_depth, kept_opacity);
+  GS2D_LAUNCH_CHECK();
+  accept_loss_kernel<<<(batch + 127) / 128, 128, 0, st>>>(loss_prop, loss_init, proposal, batch,
+                                                         poses, accepted);
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
 }

@@ -108,7 +108,7 @@ EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_stri
            "gs2d_render_batch_workspace", "gs2d_render_fwd_batch", "gs2d_render_bwd_batch",
            "gs2d_net_param_count", "gs2d_net_layout", "gs2d_net_workspace",
            "gs2d_net_pack_input", "gs2d_net_forward", "gs2d_net_grad", "gs2d_net_adamw",
-           "gs2d_net_apply", "gs2d_net_target", "gs2d_net_accept",
+           "gs2d_net_apply", "gs2d_net_target", "gs2d_net_accept", "gs2d_net_accept_keep",
            "gs2d_render_contrib_workspace", "gs2d_render_contrib", "gs2d_covisibility",
            "gs2d_map_observe", "gs2d_map_correct_workspace", "gs2d_map_correct",
            "gs2d_map_prune", "gs2d_map_compact_workspace", "gs2d_map_compact",
@@ -185,6 +185,7 @@ def lib():
         L.gs2d_net_apply.argtypes = [vp, ip, vp, vp]
         L.gs2d_net_target.argtypes = [vp, vp, ip, vp, vp]
         L.gs2d_net_accept.argtypes = [vp, vp, vp, ip, vp, vp, vp]
+        L.gs2d_net_accept_keep.argtypes = [vp, vp, vp, ip, vp, vp, sz] + [vp] * 7
         L.gs2d_net_downsample_rgbd.argtypes = [vp, vp, ip, ip, ip, vp, vp, vp]
         L.gs2d_net_prepare.argtypes = [vp, ip, vp, sz, vp, vp]
         L.gs2d_net_forward_prepared.argtypes = [vp, vp, ip, vp, vp, sz, vp, vp]
@@ -711,6 +712,19 @@ def gs2d_net_accept(loss_prop, loss_init, proposal, poses, accepted=None, stream
     check(lib().gs2d_net_accept(_ptr(loss_prop), _ptr(loss_init), _ptr(proposal),
                                 int(poses.shape[0]), _ptr(poses), _ptr(accepted),
                                 _stream(stream)), "gs2d_net_accept")
+
+
+def gs2d_net_accept_keep(loss_prop, loss_init, proposal, poses, prop_images, kept_images,
+                         accepted=None, stream=None):
+    """gs2d_net_accept that also copies the taken proposals' images (rgb,
+    depth, opacity of prop_images) over kept_images and their loss over
+    loss_init."""
+    n_px = int(prop_images[1].numel()) // int(poses.shape[0])
+    check(lib().gs2d_net_accept_keep(_ptr(loss_prop), _ptr(loss_init), _ptr(proposal),
+                                     int(poses.shape[0]), _ptr(poses), _ptr(accepted), n_px,
+                                     *[_ptr(t) for t in prop_images],
+                                     *[_ptr(t) for t in kept_images], _stream(stream)),
+          "gs2d_net_accept_keep")
 
 
 def net_init_blocks():

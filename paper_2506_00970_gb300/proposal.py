@@ -182,14 +182,18 @@ class Proposer:
     there, pack with the observation, network forward, apply, render at the
     proposal, tracking loss there, keep the better pose.  With passes > 1 the
     sequence repeats from the kept pose (the network refines its own
-    proposal)."""
+    proposal); the kept pose's images and loss are kept with it
+    (gs2d_net_accept_keep), so later passes render only their proposal."""
 
     def __init__(self, surf: gs2d.DeviceSurfels, params, capacity: int, device="cuda",
                  passes: int = 1, cam=CAM):
         self.surf = surf
         self.params = params
         self.passes = int(passes)
+        # r renders the current (kept) pose, rp the proposals
         self.r = gs2d.Rasterizer(cam, surf.n, capacity=capacity, device=device)
+        self.rp = gs2d.Rasterizer(cam, surf.n, capacity=capacity, device=device) \
+            if self.passes > 1 else self.r
         f = dict(dtype=torch.float32, device=device)
         self.pose = torch.empty(1, 12, **f)
         self.prop = torch.empty(1, 12, **f)
@@ -206,8 +210,7 @@ class Proposer:
         self.accepted = torch.zeros(1, dtype=torch.int32, device=device)
         self.prm = gs2d.default_track_params()
 
-    def _render(self, pose_row):
-        r = self.r
+    def _render(self, pose_row, r):
         r.status.zero_()
         r.project(self.surf, pose_row)
         fwd_bins = gs2d.Bins(r.bins.keys, r.bins.vals, None, None, r.bins.tile_ranges,
@@ -215,28 +218,32 @@ class Proposer:
         gs2d.gs2d_bin_sort(r.proj, r.tiles, r.n, r.cam, r.cfg, r.sort_ws, fwd_bins)
         r.render_fwd()
 
-    def _loss(self, out):
-        r = self.r
+    def _loss(self, out, r):
         gs2d.gs2d_tracking_loss(r.rgb, r.depth, r.normal, r.opacity, self.obs_rgb, self.obs_d, r.cam,
                                 self.prm, self.g[0], self.g[1], self.g[2], out, self.lws)
 
     def run(self):
-        r = self.r
-        for _ in range(self.passes):
-            self._render(self.pose[0])
-            self._loss(self.loss_init)
+        r, rp = self.r, self.rp
+        self._render(self.pose[0], r)
+        self._loss(self.loss_init, r)
+        for p in range(self.passes):
             gs2d.gs2d_net_pack_input(r.rgb[None], r.depth[None], r.opacity[None],
                                      self.obs_rgb[None], self.obs_d[None], self.x)
             gs2d.gs2d_net_forward_prepared(self.params, self.x, self.y, self.ws)
             self.prop.copy_(self.pose)
             gs2d.gs2d_net_apply(self.y, self.prop)
-            self._render(self.prop[0])
-            self._loss(self.loss_prop)
-            gs2d.gs2d_net_accept(self.loss_prop, self.loss_init, self.prop, self.pose,
-                                 self.accepted)
+            self._render(self.prop[0], rp)
+            self._loss(self.loss_prop, rp)
+            if p + 1 < self.passes:
+                gs2d.gs2d_net_accept_keep(self.loss_prop, self.loss_init, self.prop, self.pose,
+                                          (rp.rgb, rp.depth, rp.opacity),
+                                          (r.rgb, r.depth, r.opacity), self.accepted)
+            else:
+                gs2d.gs2d_net_accept(self.loss_prop, self.loss_init, self.prop, self.pose,
+                                     self.accepted)
 
     def status(self) -> int:
-        return int(self.r.status.item())
+        return max(int(self.r.status.item()), int(self.rp.status.item()))
 
 
 def capture(fn, warm: int = 1):

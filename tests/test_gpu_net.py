@@ -276,6 +276,38 @@ def test_target_and_accept_kernels(torch_cuda):
         assert torch.equal(poses[b], prop[b] if want[b] else -torch.ones(12, device="cuda"))
 
 
+def test_accept_keep_copies_the_taken_images_and_losses(torch_cuda):
+    """gs2d_net_accept_keep: the same decisions as gs2d_net_accept; where a
+    proposal is taken its images and loss replace the kept ones, elsewhere
+    the kept ones are untouched (bit for bit)."""
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d
+    B, H, W = 6, 7, 9
+    g = torch.Generator(device="cuda")
+    g.manual_seed(4)
+    lp = torch.tensor([1.0, 2.0, 3.0, 3.0, 0.5, 9.0], device="cuda")
+    li = torch.tensor([2.0, 1.0, 3.0, 2.0, 0.6, 8.0], device="cuda")
+    prop = torch.arange(72, dtype=torch.float32, device="cuda").reshape(6, 12)
+    poses = -torch.ones(6, 12, device="cuda")
+    acc = torch.empty(6, dtype=torch.int32, device="cuda")
+    P = [torch.rand(B, H, W, 3, generator=g, device="cuda"), torch.rand(B, H, W, generator=g, device="cuda"),
+         torch.rand(B, H, W, generator=g, device="cuda")]
+    K = [torch.rand(B, H, W, 3, generator=g, device="cuda"), torch.rand(B, H, W, generator=g, device="cuda"),
+         torch.rand(B, H, W, generator=g, device="cuda")]
+    K0 = [k.clone() for k in K]
+    li0 = li.clone()
+    gs2d.gs2d_net_accept_keep(lp, li, prop, poses, P, K, acc)
+    torch.cuda.synchronize()
+    want = [1, 0, 1, 0, 1, 0]
+    assert acc.cpu().tolist() == want
+    for b in range(B):
+        take = bool(want[b])
+        assert torch.equal(poses[b], prop[b] if take else -torch.ones(12, device="cuda"))
+        assert float(li[b]) == float(lp[b] if take else li0[b])
+        for k, p0, k0 in zip(K, P, K0):
+            assert torch.equal(k[b], p0[b] if take else k0[b])
+
+
 def test_downsample_rgbd_matches_oracle(torch_cuda):
     """640x480 -> 160x120 box downsampling of an observation with holes:
     block sums of 16 values in FP32 against FP64 (1e-6 relative); blocks

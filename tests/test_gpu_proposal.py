@@ -40,6 +40,50 @@ def test_pairs_have_the_targets_of_their_poses(torch_cuda):
     assert np.isfinite(x).all() and np.abs(x[..., 4:7]).max() <= 1.0
 
 
+def test_two_pass_proposal_equals_rendering_the_kept_pose_again(torch_cuda):
+    """The Proposer's later passes start from the kept pose's images and loss
+    carried over by gs2d_net_accept_keep; the same sequence that renders the
+    kept pose again (and recomputes its loss) gives bit-identical poses and
+    losses.  The network's weights are zero and its output bias is the
+    start's exact correction, so pass 1 is taken (the copy path) and the
+    later passes, which overshoot, are not."""
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d, proposal
+    s = scenes.room_scene(200, 60_000)
+    ds = gs2d.DeviceSurfels(s)
+    gt = scenes.room_pose(5)
+    img = proposal.ViewRenderer(ds).render(proposal.poses_tensor([gt]))
+    obs_rgb = img["rgb"][0].clone()
+    obs_d = img["depth"][0] / img["opacity"][0].clamp_min(1e-6)
+    _, b_off, _ = gs2d.gs2d_net_layout()
+    for seed in range(2):
+        start = proposal.poses_tensor([scenes.perturb_pose(gt, 0.03, 2.0, seed=seed)])
+        target = torch.empty(1, 6, device="cuda")
+        gs2d.gs2d_net_target(start, proposal.poses_tensor([gt]), target)
+        params = torch.zeros(gs2d.gs2d_net_param_count(), device="cuda")
+        params[b_off[-1]:b_off[-1] + 6] = target[0]
+        pr = proposal.Proposer(ds, params, 8 * ds.n, passes=3)
+        pr.pose.copy_(start)
+        pr.obs_rgb.copy_(obs_rgb)
+        pr.obs_d.copy_(obs_d)
+        pr.run()
+        # reference: every pass renders its starting pose and recomputes its loss
+        ref = proposal.Proposer(ds, params, 8 * ds.n, passes=1)
+        ref.pose.copy_(start)
+        ref.obs_rgb.copy_(obs_rgb)
+        ref.obs_d.copy_(obs_d)
+        taken = []
+        for _ in range(3):
+            ref.run()
+            taken.append(int(ref.accepted.item()))
+        torch.cuda.synchronize()
+        assert taken == [1, 0, 0], taken
+        assert pr.status() == 0 and ref.status() == 0
+        assert torch.equal(pr.pose, ref.pose), seed
+        assert torch.equal(pr.loss_init, ref.loss_init), seed
+        assert torch.equal(pr.loss_prop, ref.loss_prop), seed
+
+
 def test_trained_proposal_shortens_tracking(torch_cuda):
     torch = torch_cuda
     from paper_2506_00970_gb300 import proposal
