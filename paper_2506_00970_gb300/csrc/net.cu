@@ -697,6 +697,13 @@ __global__ void __launch_bounds__(ConvS2<CIN, COUT, H, W, RB>::NTHREADS) conv_s2
     prow[i] = 2 * dy;
     pcol[i] = m - dy * C::Wo;
   }
+  // the biases of this lane's output columns, loaded once
+  float bv[C::NT][2];
+#pragma unroll
+  for (int n8 = 0; n8 < C::NT; ++n8) {
+    bv[n8][0] = bias[8 * n8 + 2 * cq];
+    bv[n8][1] = bias[8 * n8 + 2 * cq + 1];
+  }
   int it = 0;
   for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
     // the next tile's rows go to the other buffer, which the previous
@@ -758,8 +765,8 @@ __global__ void __launch_bounds__(ConvS2<CIN, COUT, H, W, RB>::NTHREADS) conv_s2
 #pragma unroll
         for (int n8 = 0; n8 < C::NT; ++n8) {
           const int col = 8 * n8 + 2 * cq;
-          const float x0 = fmaxf(acc[i][n8][2 * h] + bias[col], 0.f);
-          const float x1 = fmaxf(acc[i][n8][2 * h + 1] + bias[col + 1], 0.f);
+          const float x0 = fmaxf(acc[i][n8][2 * h] + bv[n8][0], 0.f);
+          const float x1 = fmaxf(acc[i][n8][2 * h + 1] + bv[n8][1], 0.f);
           *reinterpret_cast<__nv_bfloat162*>(ob + (size_t)m * COUT + col) =
               __floats2bfloat162_rn(x0, x1);
         }

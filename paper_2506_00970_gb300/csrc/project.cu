@@ -244,6 +244,7 @@ __global__ void __launch_bounds__(256) project_fused_kernel(
   __shared__ uint32_t s_w[32];
   __shared__ uint32_t s_carry;
   __shared__ bool s_last;
+  __shared__ bool s_emit[256];  // does the chunk's surfel touch a tile?
   if (gate && *gate) return;
   if (threadIdx.x < 12) sp[threadIdx.x] = pose[threadIdx.x];
   const bool local = fz.n_tiles <= kHistTiles;
@@ -252,6 +253,7 @@ __global__ void __launch_bounds__(256) project_fused_kernel(
   __syncthreads();
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const int i = base + (int)threadIdx.x;
+    s_emit[threadIdx.x] = false;
     if (i < n) {
       project_one(i, mu, quat, scale, opacity, rgb, sp, cam, cfg, s_out + threadIdx.x * 9,
                   tiles_out + i);
@@ -262,6 +264,7 @@ __global__ void __launch_bounds__(256) project_fused_kernel(
         const int tx0 = (int)(r01 & 0xFFFF), ty0 = (int)(r01 >> 16);
         const int tx1 = (int)(r23 & 0xFFFF), ty1 = (int)(r23 >> 16);
         if (tx0 <= tx1 && ty0 <= ty1) {
+          s_emit[threadIdx.x] = true;
           const int rw = tx1 - tx0 + 1, k = rw * (ty1 - ty0 + 1);
           for (int j = 0; j < k; ++j) {
             const int t = min((ty0 + j / rw) * fz.tiles_x + tx0 + j % rw, fz.n_tiles - 1);
@@ -273,7 +276,11 @@ __global__ void __launch_bounds__(256) project_fused_kernel(
     __syncthreads();
     const int valid = min((int)blockDim.x, n - base);
     float4* dst = proj + (size_t)base * (kProjFloats / 4);
-    for (int v = threadIdx.x; v < valid * 8; v += blockDim.x) dst[v] = s_out[(v >> 3) * 9 + (v & 7)];
+    // only the records of surfels that touch a tile are ever read (the
+    // scatter and the tile kernel reach records through the tile lists), so
+    // culled surfels' records are not written
+    for (int v = threadIdx.x; v < valid * 8; v += blockDim.x)
+      if (s_emit[v >> 3]) dst[v] = s_out[(v >> 3) * 9 + (v & 7)];
     __syncthreads();
   }
   // the block's counts, one global atomic per touched tile
