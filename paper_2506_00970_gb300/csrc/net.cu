@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const Gemm g) {
 // 2 ox + 2 + kx under one tap, neighbours in one parity plane, so the eight
 // pixels of an ldmatrix row group are eight consecutive 16-byte entries
 // (distinct banks).  Layer 1 (input 79 MB, output 79 MB at batch 256) takes
-// 55 us here against 124 us as an implicit-im2col GEMM.  The same scheme for
+// 51 us here against 124 us as an implicit-im2col GEMM.  The same scheme for
 // layer 2 (C_in = 32; two 47 KB row buffers leave one block per SM) took
 // 80-95 us against the GEMM's 62 us, so layer 2 stays a GEMM.
 template <int CIN, int COUT, int H, int W, int RB>
