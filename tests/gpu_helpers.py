@@ -4,7 +4,6 @@ from __future__ import annotations
 
 import numpy as np
 
-from paper_2506_00970_gb300 import scenes
 
 # tolerances of the parity contract: colour / opacity max-abs, depth and
 # normal relative, gradients relative

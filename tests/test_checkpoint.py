@@ -1,7 +1,6 @@
 """Checkpoint / resume of the learned proposal's training state (host side,
 no GPU): the FP32 master weights, the AdamW moments and the step count
 survive a save and a load bit for bit."""
-import numpy as np
 import torch
 
 from paper_2506_00970_gb300 import proposal

@@ -14,7 +14,6 @@ hand-checked cases (no GPU):
   * downsampling keeps exactly the pixels with u < ratio; holes and their
     neighbours get no surfel; occupied voxels block creation.
 """
-import math
 
 import numpy as np
 

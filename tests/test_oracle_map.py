@@ -15,7 +15,6 @@ geometric identities (no GPU).
 import math
 
 import numpy as np
-import pytest
 
 import oracle.map_state as ms
 from paper_2506_00970_gb300 import scenes

@@ -13,7 +13,6 @@ tracking loop (no GPU).
 * tracking loop: zero loss and gradient at ground truth; convergence from a
   2 cm / 1 degree perturbation to 1 cm / 0.5 degree (Sec. III-D).
 """
-import math
 
 import numpy as np
 import pytest

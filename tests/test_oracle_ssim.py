@@ -16,7 +16,6 @@ plain definition (no GPU):
 import math
 
 import numpy as np
-import pytest
 
 from paper_2506_00970_gb300 import scenes
 
