@@ -81,6 +81,28 @@ def test_invalid_arguments_rejected_without_launch(built_lib):
                              8, 8, 8, 8, 8, 8, None) == 1
 
 
+def test_net_accept_keep_rejects_missing_buffers_without_launch(built_lib):
+    """gs2d_net_accept_keep checks every pointer and size on the host: a
+    missing image buffer, an empty image or an empty batch is rejected
+    before anything is launched."""
+    from paper_2506_00970_gb300 import gs2d
+    L = gs2d.lib()
+    ok = [8] * 7   # stand-in non-NULL pointers (never dereferenced on these paths)
+    args = lambda batch, n_px, imgs: (8, 8, 8, batch, 8, None, n_px, *imgs, None)
+    assert L.gs2d_net_accept_keep(*args(1, 100, [8, 8, None, 8, 8, 8])) == 1
+    assert L.gs2d_net_accept_keep(*args(1, 100, [8, 8, 8, 8, 8, None])) == 1
+    assert L.gs2d_net_accept_keep(*args(1, 0, ok[:6])) == 1
+    assert L.gs2d_net_accept_keep(*args(0, 100, ok[:6])) == 1
+    assert L.gs2d_net_accept_keep(None, 8, 8, 1, 8, None, 100, *ok[:6], None) == 1
+
+
+def test_grouped_tile_threshold_setter_is_host_only(built_lib):
+    """gs2d_set_grouped_tiles only stores the threshold (no device call)."""
+    from paper_2506_00970_gb300 import gs2d
+    for v in (0, 1 << 30, -5, -1):
+        gs2d.gs2d_set_grouped_tiles(v)
+
+
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     from paper_2506_00970_gb300 import build, gs2d
     monkeypatch.setattr(build, "LIB", str(tmp_path / "missing.so"))
