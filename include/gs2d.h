@@ -153,19 +153,39 @@ int gs2d_project(const gs2d_surfels* s, const gs2d_camera* cam, const float* pos
                  const gs2d_config* cfg, float* proj_out, int32_t* tiles_per_surfel_out,
                  gs2d_stream stream);
 
-/* Tile binning and depth ordering ("sorts them by depth", Sec. III-A): every
+/* Tile binning and depth ordering (the per-tile depth sort of Sec. III-A): every
  * surfel with k_i > 0 emits one intersection per tile of its rectangle; the
  * intersections are ordered by (tile, mu_c.z bits, surfel id) -- the order
  * of a stable sort by tile of the depth-ordered emission -- by binning the
  * pairs into per-tile segments and sorting every segment by (depth bits, id)
  * in shared memory (hand-written bitonic networks; long segments in chunks
- * merged in global memory), so the result is unique and deterministic.  proj: device [n * GS2D_PROJ_FLOATS] (only slots 26, 28, 29 are
- * read).  tiles_per_surfel: device [n], must equal the rectangle's tile count.
- * Workspace: gs2d_bin_sort_workspace(n, capacity) bytes. */
+ * merged in global memory), so the result is unique and deterministic.
+ * This replaces the global LSD radix sort on (tile, depth) keys of the first
+ * design (four 8-bit passes over the depth keys, then one or two over the
+ * tile keys): the per-tile sort gives the identical order in fewer passes
+ * and took a 100-iteration 640x480 tracking frame from 28.1 to 24.1 ms.
+ * proj: device [n * GS2D_PROJ_FLOATS] (only slots 26, 28, 29 are read).
+ * tiles_per_surfel: device [n], must equal the rectangle's tile count.
+ * Workspace: gs2d_bin_sort_workspace(n, capacity) bytes.  The emission
+ * offsets are an exclusive scan whose blocks wait (boundedly) on their
+ * predecessors' published sums; a wait that runs out records
+ * GS2D_ERR_TIMEOUT in the status word, keeps every write in bounds and
+ * makes every later kernel skip (see gs2d_set_lookback_wait). */
 size_t gs2d_bin_sort_workspace(int n, size_t capacity);
 int gs2d_bin_sort(const float* proj, const int32_t* tiles_per_surfel, int n,
                   const gs2d_camera* cam, const gs2d_config* cfg, void* workspace,
                   size_t ws_bytes, size_t* ws_needed, const gs2d_bins* bins, gs2d_stream stream);
+
+/* Look-back waits of gs2d_bin_sort's emission scan (diagnostic; no
+ * counterpart in the paper).  spin_limit: how many polls a scan block makes
+ * for a predecessor's published sum before it records GS2D_ERR_TIMEOUT and
+ * finishes with a partial prefix (0 restores the default of 2^22 polls, a
+ * second or more).  withheld_chunk: for tests of that failure path, the scan
+ * block (4096 surfels each) that never publishes its sum, so that the next
+ * block's wait runs out (-1 = none, the default).  Process-wide, read at
+ * each launch (a captured graph keeps the values it was captured with); not
+ * thread-safe against launches from other host threads. */
+void gs2d_set_lookback_wait(int spin_limit, int withheld_chunk);
 
 /* gs2d_bin_sort without a workspace argument: it allocates nothing.  The
  * paper has no counterpart; this serves callers that cannot allocate device
@@ -179,7 +199,10 @@ int gs2d_bin_sort(const float* proj, const int32_t* tiles_per_surfel, int n,
  * with a capacity of 1M intersections fit).  The first call on each device
  * looks up that device's copy of the array (cudaGetSymbolAddress, with the
  * device current) and caches it; make that first call before any stream
- * capture.  All calls on a device share the one array: calls whose kernels
+ * capture.  The cached address belongs to the device's context at that
+ * first call: cudaDeviceReset on that device afterwards is not supported
+ * (the array may move in the new context; a later call would pass the old
+ * address).  All calls on a device share the one array: calls whose kernels
  * may overlap on the GPU (different streams without ordering) race and must
  * be serialised by the caller.  Results equal gs2d_bin_sort's. */
 #define GS2D_SORT_STATIC_SCRATCH_BYTES (32u << 20)
@@ -369,22 +392,36 @@ int gs2d_ssim_loss(const float* x, const float* y, int height, int width, float 
 
 /* Frame-to-map tracking (Sec. III-D): n_iter iterations of
  * project -> bin_sort -> render_fwd -> tracking loss -> pose-only backward
- * -> AdamW on tau -> T <- Exp(tau) T with tau reset to 0 (the moments are
- * kept within the frame and reset at the start of every call).  Once
+ * -> AdamW on tau -> T <- Exp(tau) T with tau reset to 0.  Once
  * |tau| < stop_tol the remaining iterations only copy the history.
- * Everything stays on the device: pose [12] in/out; loss_hist [n_iter] (the
- * loss at the pose before each update) and pose_hist [n_iter * 12] (the pose
- * after it) may be NULL.  capacity bounds K per iteration.  The status word
+ * Everything stays on the device.
+ *   pose        [12] in/out (world->camera, as everywhere).
+ *   adam_state  [16] AdamW state m[6], v[6], step, done flag (1 once the stop
+ *               rule fired), 2 unused; owned by the caller, read and updated
+ *               in place, never reset here: zero it to start a frame, and
+ *               pass it again to continue one (a frame split over several
+ *               calls gives the same bits as one call).  NULL = moments kept
+ *               in the workspace and zeroed at the start of every call.
+ *   loss_hist   [n_iter]: the loss at the pose before each update;
+ *   pose_hist   [n_iter * 12]: the pose after it;
+ *   grad_hist   [n_iter * 6]: dL/dtau (rho, theta) at the pose before each
+ *               update, the vector AdamW receives (zero for the iterations
+ *               skipped after convergence).  Each may be NULL.
+ * capacity bounds K per iteration.  The status word
  * (gs2d_track_status(workspace)) ends as GS2D_OK, 256 (converged early) or
- * an error (GS2D_ERR_CAPACITY: raise capacity and retry; GS2D_ERR_NONFINITE;
- * GS2D_ERR_TIMEOUT).  Workspace: gs2d_track_workspace(n, capacity, cam, cfg). */
+ * an error: GS2D_ERR_CAPACITY (raise capacity and retry), GS2D_ERR_NONFINITE
+ * (a non-finite loss or gradient, e.g. from a non-finite observation: the
+ * pose and the AdamW state keep the values they had before that iteration,
+ * whose loss_hist / grad_hist entries record what was found), or
+ * GS2D_ERR_TIMEOUT; every later kernel of the call then skips its work.
+ * Workspace: gs2d_track_workspace(n, capacity, cam, cfg). */
 size_t gs2d_track_workspace(int n, size_t capacity, const gs2d_camera* cam,
                             const gs2d_config* cfg);
 int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_config* cfg,
-                    const gs2d_track_params* prm, float* pose, const float* obs_rgb,
-                    const float* obs_depth, int n_iter, size_t capacity, float* loss_hist,
-                    float* pose_hist, void* workspace, size_t ws_bytes, size_t* ws_needed,
-                    gs2d_stream stream);
+                    const gs2d_track_params* prm, float* pose, float* adam_state,
+                    const float* obs_rgb, const float* obs_depth, int n_iter, size_t capacity,
+                    float* loss_hist, float* pose_hist, float* grad_hist, void* workspace,
+                    size_t ws_bytes, size_t* ws_needed, gs2d_stream stream);
 /* Device pointer of the status word inside a track workspace (int32). */
 int32_t* gs2d_track_status(void* workspace);
 

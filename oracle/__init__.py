@@ -16,7 +16,7 @@ Contents (each cites the passage it follows):
     ``visible`` / ``covisibility`` / ``keyframe_rule`` -- the visibility
     threshold, the covisibility score and the keyframe rule of Sec. III-D.
   * ``tile_rects`` / ``bin_sort`` -- FP64 tile footprint and a stable library
-    sort of (tile, depth) keys ("sorts them by depth", Sec. III-A).
+    sort of (tile, depth) keys (the depth ordering of Sec. III-A).
   * ``se3_exp`` / ``se3_log``     -- SE(3) exponential / logarithm used by the
     left perturbation Exp(tau) o T (Sec. III-B), tau = (rho, theta).
   * ``adamw_step``               -- AdamW (Loshchilov & Hutter), the pose
@@ -74,6 +74,13 @@ def _d(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+# Relative margins of the oracle's threshold diagnostic (``ambiguous`` of
+# render / render_bwd; the constants kTight and kLooseT of gs2d_oracle.cpp):
+# cutoff radius, alpha_min and near plane; the stop test against t_min.
+AMBIGUITY_TIGHT = 2e-5
+AMBIGUITY_STOP = 1e-4
+
+
 @dataclasses.dataclass
 class Rule:
     """Compositing constants (readings of points the paper leaves open)."""
@@ -101,8 +108,12 @@ def default_threads() -> int:
 
 def render(surfels, cam, pose, rule: Rule = Rule(), pixels=None, n_threads: int = 0):
     """Render colour, depth (literal sum of w z), normal, opacity, the final
-    transmittance, the number of blended surfels and the smallest |cos|
-    between the ray and a blended surfel's normal (``min_cos``).
+    transmittance, the number of blended surfels, the smallest |cos|
+    between the ray and a blended surfel's normal (``min_cos``) and
+    ``ambiguous``: pixels holding a compositing decision (cutoff, alpha_min,
+    near plane, stop test) within rounding of its threshold, which an FP32
+    evaluation may legitimately take otherwise (a diagnostic of the parity
+    tests).
 
     ``pixels``: optional (P,2) int array of (x, y); then every output has a
     leading P axis instead of (H, W)."""
@@ -117,26 +128,33 @@ def render(surfels, cam, pose, rule: Rule = Rule(), pixels=None, n_threads: int 
     out_t = np.zeros(npx)
     out_c = np.zeros(npx, np.int32)
     out_m = np.zeros(npx)
+    out_a = np.zeros(npx, np.int32)
     _lib().orc_render(surfels.n, _p(mu), _p(q), _p(sc), _p(op), _p(rgb), _p(_cam5(cam)), W, H,
                       _p(_d(pose.R)), _p(_d(pose.t)), _p(rule.vec()), int(rule.exact), npx,
                       _p(pix, ctypes.c_int), _p(out_rgb), _p(out_d), _p(out_n), _p(out_o), _p(out_t),
-                      _p(out_c, ctypes.c_int), _p(out_m), int(n_threads or default_threads()))
+                      _p(out_c, ctypes.c_int), _p(out_m), _p(out_a, ctypes.c_int),
+                      int(n_threads or default_threads()))
+    amb = out_a.astype(bool)
     if pix is None:
         return dict(rgb=out_rgb.reshape(H, W, 3), depth=out_d.reshape(H, W),
                     normal=out_n.reshape(H, W, 3), opacity=out_o.reshape(H, W),
                     t_final=out_t.reshape(H, W), count=out_c.reshape(H, W),
-                    min_cos=out_m.reshape(H, W))
+                    min_cos=out_m.reshape(H, W), ambiguous=amb.reshape(H, W))
     return dict(rgb=out_rgb, depth=out_d, normal=out_n, opacity=out_o, t_final=out_t, count=out_c,
-                min_cos=out_m)
+                min_cos=out_m, ambiguous=amb)
 
 
 def render_bwd(surfels, cam, pose, g_rgb, g_depth, g_normal, g_opacity, rule: Rule = Rule(),
                pixels=None, n_threads: int = 0):
     """Gradients of L w.r.t. the surfel parameters and the pose tangent,
     given dL/d(rgb, depth, normal, opacity) of the rendered images (or of the
-    listed pixels).  Returns dict(mu, quat, scale, opacity, rgb, pose6) and
+    listed pixels).  Returns dict(mu, quat, scale, opacity, rgb, pose6),
     min_cos, per surfel the smallest |cos| between a ray it blends into and
-    its normal (an ill-conditioning measure for the parity tests)."""
+    its normal (an ill-conditioning measure for the parity tests), and
+    ``ambiguous``, per surfel whether it is a candidate at a pixel that holds
+    a compositing decision within rounding of its threshold (see render):
+    there an FP32 evaluation may legitimately give it other gradient
+    terms."""
     mu, q, sc, op, rgb = _surfel_arrays(surfels)
     W, H = cam.width, cam.height
     pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int32)
@@ -149,13 +167,16 @@ def render_bwd(surfels, cam, pose, g_rgb, g_depth, g_normal, g_opacity, rule: Ru
     d_c = np.zeros((n, 3))
     d_pose = np.zeros(6)
     d_mc = np.ones(n)
+    d_amb = np.zeros(n, np.int32)
     _lib().orc_render_bwd(n, _p(mu), _p(q), _p(sc), _p(op), _p(rgb), _p(_cam5(cam)), W, H,
                           _p(_d(pose.R)), _p(_d(pose.t)), _p(rule.vec()), int(rule.exact), npx,
                           _p(pix, ctypes.c_int), _p(_d(g_rgb).reshape(-1)),
                           _p(_d(g_depth).reshape(-1)), _p(_d(g_normal).reshape(-1)),
                           _p(_d(g_opacity).reshape(-1)), _p(d_mu), _p(d_q), _p(d_s), _p(d_o),
-                          _p(d_c), _p(d_pose), _p(d_mc), int(n_threads or default_threads()))
-    return dict(mu=d_mu, quat=d_q, scale=d_s, opacity=d_o, rgb=d_c, pose6=d_pose, min_cos=d_mc)
+                          _p(d_c), _p(d_pose), _p(d_mc), _p(d_amb, ctypes.c_int),
+                          int(n_threads or default_threads()))
+    return dict(mu=d_mu, quat=d_q, scale=d_s, opacity=d_o, rgb=d_c, pose6=d_pose, min_cos=d_mc,
+                ambiguous=d_amb.astype(bool))
 
 
 def contrib(surfels, cam, pose, rule: Rule = Rule(), pixels=None, n_threads: int = 0):

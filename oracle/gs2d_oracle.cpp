@@ -243,6 +243,70 @@ int n_threads_or_default(int n_threads) {
 #endif
 }
 
+struct Cand {
+  double depth_c;
+  int id;
+  bool on_edge;
+};
+
+// Relative margins of the threshold diagnostics: an intersection whose
+// u^2 + v^2, alpha G or depth lies within kTight (relative) of the cutoff,
+// alpha_min or the near plane, or a stop test whose transmittance lies within
+// kLooseT (relative) of t_min, may be decided otherwise by an FP32
+// evaluation of the same pixel.
+constexpr double kTight = 2e-5, kLooseT = 1e-4;
+
+// Diagnostic of the parity tests (no computed value depends on it): fills
+// cand with the pixel's candidates in blending order -- surfels whose
+// intersection passes the near, cutoff and alpha_min tests within kTight --
+// and returns true if the pixel holds a decision that FP32 may take
+// otherwise: a candidate within kTight of a threshold at or before the
+// position where blending stops, or a stop test (of a blended item or of the
+// first item not blended) within kLooseT of t_min.  Such a decision changes
+// the pixel's weights from that position on, and through the transmittance
+// and the suffix sums of the backward pass the gradients of every item the
+// pixel blends.  Exact mode has none of these thresholds: false.
+bool pixel_threshold_ambiguous(const std::vector<CamSurfel>& S, const Cam& cam, const Rule& rule,
+                               V3 r, const std::vector<Item>& items, int nb,
+                               std::vector<Cand>& cand) {
+  cand.clear();
+  if (rule.exact) return false;
+  for (int i = 0; i < (int)S.size(); ++i) {
+    const CamSurfel& s = S[i];
+    if (!(s.mu_c.z > cam.near_z)) continue;
+    Hit h = intersect(s, r);
+    if (!h.ok || !(h.z > cam.near_z * (1.0 - kTight))) continue;
+    const double r2 = h.u * h.u + h.v * h.v;
+    if (r2 > rule.cutoff_r2 * (1.0 + kTight)) continue;
+    const double a = s.alpha * std::exp(-0.5 * r2);
+    if (a < rule.alpha_min * (1.0 - kTight)) continue;
+    const bool on_edge = std::fabs(r2 - rule.cutoff_r2) <= kTight * rule.cutoff_r2 ||
+                         std::fabs(a - rule.alpha_min) <= kTight * rule.alpha_min ||
+                         std::fabs(h.z - cam.near_z) <= kTight * cam.near_z;
+    cand.push_back(Cand{s.mu_c.z, i, on_edge});
+  }
+  std::sort(cand.begin(), cand.end(), [](const Cand& p, const Cand& q) {
+    if (p.depth_c != q.depth_c) return p.depth_c < q.depth_c;
+    return p.id < q.id;
+  });
+  int p_stop = (int)cand.size();
+  if (nb < (int)items.size())
+    for (int c = 0; c < (int)cand.size(); ++c)
+      if (cand[c].id == items[nb].id) {
+        p_stop = c;
+        break;
+      }
+  for (int c = 0; c <= p_stop && c < (int)cand.size(); ++c)
+    if (cand[c].on_edge) return true;
+  double T = 1.0;
+  for (int m = 0; m < (int)items.size() && m <= nb; ++m) {
+    const double Tn = T * (1.0 - items[m].a);
+    if (std::fabs(Tn - rule.t_min) <= kLooseT * rule.t_min) return true;
+    T = Tn;
+  }
+  return false;
+}
+
 }  // namespace
 
 extern "C" {
@@ -253,13 +317,14 @@ extern "C" {
 // Outputs per listed pixel: rgb[3], depth, normal[3], opacity, T_final, the
 // number of blended surfels and (if out_mincos is non-NULL) the smallest
 // |cos| between the ray and a blended surfel's normal -- near zero when a
-// surfel is seen edge-on, where the intersection is ill-conditioned.
+// surfel is seen edge-on, where the intersection is ill-conditioned -- and
+// (if out_amb is non-NULL) 1 where pixel_threshold_ambiguous holds.
 int orc_render(int n, const double* mu, const double* quat, const double* scale,
                const double* opacity, const double* rgb, const double* cam5, int W, int H,
                const double* R9, const double* t3, const double* rule4, int exact, int n_pix,
                const int* pix, double* out_rgb, double* out_depth, double* out_normal,
                double* out_opacity, double* out_tfinal, int* out_count, double* out_mincos,
-               int n_threads) {
+               int* out_amb, int n_threads) {
   const Cam cam{cam5[0], cam5[1], cam5[2], cam5[3], cam5[4], W, H};
   const Rule rule{rule4[0], rule4[1], rule4[2], rule4[3], exact};
   const std::vector<CamSurfel> S = camera_surfels(n, mu, quat, scale, opacity, rgb, R9, t3);
@@ -267,6 +332,7 @@ int orc_render(int n, const double* mu, const double* quat, const double* scale,
 #pragma omp parallel num_threads(n_threads_or_default(n_threads))
   {
     std::vector<Item> items;
+    std::vector<Cand> cand;
 #pragma omp for schedule(dynamic, 16)
     for (int k = 0; k < np; ++k) {
       double x, y;
@@ -297,16 +363,11 @@ int orc_render(int n, const double* mu, const double* quat, const double* scale,
       out_tfinal[k] = T;
       out_count[k] = nb;
       if (out_mincos) out_mincos[k] = mincos;
+      if (out_amb) out_amb[k] = pixel_threshold_ambiguous(S, cam, rule, rr, items, nb, cand) ? 1 : 0;
     }
   }
   return 0;
 }
-
-struct Cand {
-  double depth_c;
-  int id;
-  bool on_edge;
-};
 
 // Per-surfel contribution (Sec. III-D, Eq. weight and Eq. contribution):
 // out_contrib[i] = sum over the listed pixels of w_i(p) = a_i T_i, the
@@ -460,14 +521,17 @@ int orc_contrib(int n, const double* mu, const double* quat, const double* scale
 // and dL/dtau, tau = (rho, theta), for the left perturbation of T_cw; and, if
 // d_mincos is non-NULL, per surfel the smallest |cos| between a pixel ray it
 // blends into and its normal (1 if it blends into none): near zero marks a
-// surfel seen edge-on, whose intersection is ill-conditioned.
+// surfel seen edge-on, whose intersection is ill-conditioned; and, if d_amb
+// is non-NULL, per surfel 1 if it is a candidate (pixel_threshold_ambiguous's
+// list) of a listed pixel for which pixel_threshold_ambiguous holds -- an
+// FP32 evaluation may legitimately give that surfel other gradient terms.
 int orc_render_bwd(int n, const double* mu, const double* quat, const double* scale,
                    const double* opacity, const double* rgb, const double* cam5, int W, int H,
                    const double* R9, const double* t3, const double* rule4, int exact, int n_pix,
                    const int* pix, const double* g_rgb, const double* g_depth,
                    const double* g_normal, const double* g_opac, double* d_mu, double* d_quat,
                    double* d_scale, double* d_opacity, double* d_rgb, double* d_pose6,
-                   double* d_mincos, int n_threads) {
+                   double* d_mincos, int* d_amb, int n_threads) {
   const Cam cam{cam5[0], cam5[1], cam5[2], cam5[3], cam5[4], W, H};
   const Rule rule{rule4[0], rule4[1], rule4[2], rule4[3], exact};
   const std::vector<CamSurfel> S = camera_surfels(n, mu, quat, scale, opacity, rgb, R9, t3);
@@ -486,6 +550,7 @@ int orc_render_bwd(int n, const double* mu, const double* quat, const double* sc
   };
   std::vector<std::vector<Acc>> acc(nt, std::vector<Acc>(n, Acc{mk(0, 0, 0), mk(0, 0, 0), mk(0, 0, 0),
                                                                  mk(0, 0, 0), mk(0, 0, 0), 0.0, 1.0}));
+  std::vector<std::vector<char>> amb(nt);
 #pragma omp parallel num_threads(nt)
   {
 #ifdef _OPENMP
@@ -494,7 +559,9 @@ int orc_render_bwd(int n, const double* mu, const double* quat, const double* sc
     const int tid = 0;
 #endif
     std::vector<Acc>& A = acc[tid];
+    if (d_amb) amb[tid].assign(n, 0);
     std::vector<Item> items;
+    std::vector<Cand> cand;
     std::vector<double> Tb;  // transmittance before each blended item
 #pragma omp for schedule(dynamic, 16)
     for (int k = 0; k < np; ++k) {
@@ -503,6 +570,8 @@ int orc_render_bwd(int n, const double* mu, const double* quat, const double* sc
       const V3 r = mk((x - cam.cx) / cam.fx, (y - cam.cy) / cam.fy, 1.0);
       pixel_items(S, cam, rule, x, y, items);
       const int nb = blended_count(items, rule);
+      if (d_amb && pixel_threshold_ambiguous(S, cam, rule, r, items, nb, cand))
+        for (const Cand& cd : cand) amb[tid][cd.id] = 1;
       Tb.assign(nb + 1, 1.0);
       for (int m = 0; m < nb; ++m) Tb[m + 1] = Tb[m] * (1.0 - items[m].a);
       const V3 gC = mk(g_rgb[3 * k], g_rgb[3 * k + 1], g_rgb[3 * k + 2]);
@@ -595,6 +664,11 @@ int orc_render_bwd(int n, const double* mu, const double* quat, const double* sc
     for (int k = 0; k < 4; ++k) d_quat[4 * i + k] = (gq[k] - s.qn[k] * qd) / s.qlen;
     d_opacity[i] = t.g_alpha;
     if (d_mincos) d_mincos[i] = t.mincos;
+    if (d_amb) {
+      int f = 0;
+      for (int th = 0; th < nt; ++th) f |= amb[th][i];
+      d_amb[i] = f;
+    }
     d_rgb[3 * i] = t.g_col.x;
     d_rgb[3 * i + 1] = t.g_col.y;
     d_rgb[3 * i + 2] = t.g_col.z;
@@ -709,7 +783,7 @@ int orc_tile_rects(int n, const double* mu, const double* quat, const double* sc
 // Tile binning and depth ordering as a plain library sort: every surfel with
 // a non-empty rectangle emits one (tile, depth) pair per covered tile, row by
 // row; the pairs are stable-sorted by key = tile << 32 | depth_bits, so equal
-// keys keep surfel-id order ("sorts them by depth", Sec. III-A).  Returns the
+// keys keep surfel-id order (the depth ordering of Sec. III-A).  Returns the
 // number of pairs, or -1 if it exceeds cap.  ranges[2t], ranges[2t+1] are the
 // [start, end) of tile t (0, 0 for an empty tile).
 long long orc_bin_sort(int n, const int* rect, const uint32_t* depth_bits, int tiles_x,

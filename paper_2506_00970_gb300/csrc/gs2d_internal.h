@@ -72,6 +72,7 @@ struct TrackStep {
   float* adam;       // [16] m, v, step, done
   float* loss_hist;  // [n_iter] or NULL
   float* pose_hist;  // [n_iter * 12] or NULL
+  float* grad_hist;  // [n_iter * 6] or NULL
   int iter;
   uint32_t* counter; // blocks finished in this iteration (reset by the last)
   uint32_t* sort_zero;   // binning counters the last block zeroes for the next

@@ -516,12 +516,15 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const Gemm g) {
     }
     cp_async_commit();
   }
+  // A wait that runs out in any thread is shared through s_fail: after the
+  // next k-tile's barrier no thread issues MMAs or refills stages any more.
   bool fail = false;
   for (int kt = 0; kt < ntiles; ++kt) {
     const int st = kt % TC_STAGES;
     cp_async_wait<TC_STAGES - 2>();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    if (*reinterpret_cast<volatile int*>(&s_fail)) fail = true;
     if (threadIdx.x == 0 && !fail) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sa = su32(stage_a(st)), sb = su32(stage_b(st));
@@ -542,7 +545,10 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const Gemm g) {
     const int nk = kt + TC_STAGES - 1;
     if (nk < ntiles) {
       const int sl = nk % TC_STAGES;
-      if (kt >= 1 && !fail) fail = !mbar_wait(su32(&s_bar[sl]), (uint32_t)(((kt - 1) / TC_STAGES) & 1));
+      if (kt >= 1 && !fail && !mbar_wait(su32(&s_bar[sl]), (uint32_t)(((kt - 1) / TC_STAGES) & 1))) {
+        fail = true;
+        *reinterpret_cast<volatile int*>(&s_fail) = 1;
+      }
       if (!fail) {
         la.load_core(stage_a(sl), g.a, m0, kbeg + nk * TC_BK, kend);
         lb.load_core(stage_b(sl), g.b, n0, kbeg + nk * TC_BK, kend);
@@ -551,11 +557,15 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const Gemm g) {
     cp_async_commit();
   }
   cp_async_wait<0>();
-  // all MMAs done: a last commit arrives on the final barrier
-  if (threadIdx.x == 0 && ntiles > 0 && !fail)
+  // Thread 0 issued MMAs at k-tile 0 at least (no wait precedes them); one
+  // last commit tracks all it issued -- every one, or those before a
+  // failure -- and every thread waits for it (bounded) before the tensor
+  // memory is read or freed, so no MMA in flight outlives the allocation
+  // unless that wait too runs out.
+  if (threadIdx.x == 0 && ntiles > 0)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      su32(&s_bar[TC_STAGES])) : "memory");
-  if (ntiles > 0 && !fail) fail = !mbar_wait(su32(&s_bar[TC_STAGES]), 0u);
+  if (ntiles > 0 && !mbar_wait(su32(&s_bar[TC_STAGES]), 0u)) fail = true;
   if (fail) atomicExch(&s_fail, 1);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<P, kG>()) tra
     const int32_t g = *status;
     if (g != 0) {
       if (g == kConverged && blockIdx.x == 0 && threadIdx.x == 0)
-        record_converged(ts.pose, ts.loss_hist, ts.pose_hist, ts.iter);
+        record_converged(ts.pose, ts.loss_hist, ts.pose_hist, ts.grad_hist, ts.iter);
       return;
     }
   }
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<P, kG>()) tra
   __threadfence();
   float(*s_red)[256] = reinterpret_cast<float(*)[256]>(&sm.rec[0][0]);  // 7 x 256 floats fit
   reduce_and_step(pose_part, loss_part, gridDim.x, ts.pose, ts.adam, prm, ts.loss_hist,
-                  ts.pose_hist, ts.iter, status, s_red);
+                  ts.pose_hist, ts.grad_hist, ts.iter, status, s_red);
   if (threadIdx.x == 0) *ts.counter = 0u;
   // the next iteration's binning starts from zeroed counters (its kernels
   // run after this one; this iteration's binning finished before it)

@@ -1,5 +1,5 @@
 // gs2d_bin_sort: tile binning and depth ordering of (tile, surfel) pairs
-// ("2DGS ... sorts them by depth", Sec. III-A).
+// (the per-tile depth ordering of the splats, Sec. III-A).
 //
 // Output order: by tile, then by the FP32 bit pattern of the surfel's centre
 // depth mu_c.z (positive floats order like their bits), then by surfel id.
@@ -37,7 +37,7 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kChunk = kScanThreads * kScanItems;  // 4096 surfels per scan block
 constexpr int kWarps = kScanThreads / 32;
-constexpr int kSpinLimit = 1 << 22;
+constexpr int kSpinLimit = 1 << 22;                // default polls of a look-back wait
 constexpr int kSortThreads = 256;
 constexpr int kSegSmem = 2048;                     // keys sorted in shared memory (16 KB)
 constexpr int kLongThreads = 1024;                 // long segments: one 1024-thread block
@@ -131,14 +131,17 @@ __global__ void __launch_bounds__(kScanThreads) count_kernel(
 
 // 1b. Exclusive scan of k_i over surfel ids with decoupled look-back (64-bit
 // chunk words: flag in bits 62-63; a warp examines 32 predecessors at a
-// time; the spin is bounded and records GS2D_ERR_TIMEOUT past the limit):
-// the emission offsets surfel_off[i].
+// time; the spin is bounded by spin_limit polls and past it records
+// GS2D_ERR_TIMEOUT, takes the missing sums as zero and finishes, so every
+// write stays in bounds and later kernels skip): the emission offsets
+// surfel_off[i].  The chunk numbered `withheld` (a test of that path; -1 =
+// none) never publishes its word, so its successor's wait runs out.
 constexpr unsigned long long kF64Agg = 1ull << 62, kF64Inc = 2ull << 62,
                              kV64Mask = (1ull << 62) - 1;
 __global__ void __launch_bounds__(kScanThreads) emit_scan_kernel(
     const int32_t* __restrict__ tiles, int n, uint32_t* __restrict__ surfel_off,
     unsigned long long* __restrict__ chunk_status, uint32_t* __restrict__ ticket,
-    int32_t* __restrict__ gate) {
+    int32_t* __restrict__ gate, int spin_limit, int withheld) {
   __shared__ uint32_t s_k[kChunk];
   __shared__ uint32_t s_tmp[2 * kWarps + 1];
   __shared__ int s_chunk;
@@ -164,11 +167,12 @@ __global__ void __launch_bounds__(kScanThreads) emit_scan_kernel(
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     unsigned long long* my = chunk_status + chunk;
+    const bool publish = chunk != withheld;
     unsigned long long prefix = 0;
     if (chunk == 0) {
-      if (lane == 0) st_vol64(my, kF64Inc | (unsigned long long)btotal);
+      if (lane == 0 && publish) st_vol64(my, kF64Inc | (unsigned long long)btotal);
     } else {
-      if (lane == 0) st_vol64(my, kF64Agg | (unsigned long long)btotal);
+      if (lane == 0 && publish) st_vol64(my, kF64Agg | (unsigned long long)btotal);
       int hi = chunk - 1;
       int spins = 0;
       while (true) {
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(kScanThreads) emit_scan_kernel(
           need_mask = inc_mask ? (0xffffffffu >> (31 - (__ffs(inc_mask) - 1))) : 0xffffffffu;
           const uint32_t missing = __ballot_sync(0xffffffffu, (sv & ~kV64Mask) == 0ull) & need_mask;
           if (!missing) break;
-          if (++spins > kSpinLimit) {
+          if (++spins > spin_limit) {
             if (lane == 0) atomicExch(gate, (int32_t)GS2D_ERR_TIMEOUT);
             if ((sv & ~kV64Mask) == 0ull) sv = kF64Inc;
             inc_mask = __ballot_sync(0xffffffffu, (sv & ~kV64Mask) == kF64Inc);
@@ -198,7 +202,7 @@ __global__ void __launch_bounds__(kScanThreads) emit_scan_kernel(
         if (inc_mask) break;
         hi -= 32;
       }
-      if (lane == 0) st_vol64(my, kF64Inc | ((prefix + btotal) & kV64Mask));
+      if (lane == 0 && publish) st_vol64(my, kF64Inc | ((prefix + btotal) & kV64Mask));
     }
     if (lane == 0) s_prefix = prefix;
   }
@@ -497,6 +501,10 @@ SortWs carve_sort_ws(void* base, int n, size_t cap, int n_tiles) {
   return w;
 }
 
+// Look-back wait settings (gs2d_set_lookback_wait).
+int g_lookback_spins = 0;
+int g_lookback_withheld = -1;
+
 // The long-segment kernel's dynamic shared memory exceeds the 48 KB default:
 // raise its limit once per device (before any stream capture that bins).
 cudaError_t long_sort_smem_ready(size_t bytes) {
@@ -571,8 +579,9 @@ int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
                                                           w.tile_count, gate);
     GS2D_LAUNCH_CHECK();
     if (need_emit) {
-      emit_scan_kernel<<<w.chunks_n, kScanThreads, 0, st>>>(tiles_per_surfel, n, bins->surfel_off,
-                                                            w.estatus, w.ticket, gate);
+      emit_scan_kernel<<<w.chunks_n, kScanThreads, 0, st>>>(
+          tiles_per_surfel, n, bins->surfel_off, w.estatus, w.ticket, gate,
+          g_lookback_spins > 0 ? g_lookback_spins : kSpinLimit, g_lookback_withheld);
       GS2D_LAUNCH_CHECK();
     }
   }
@@ -610,6 +619,11 @@ int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
 using namespace gs2d;
 
 extern "C" {
+
+void gs2d_set_lookback_wait(int spin_limit, int withheld_chunk) {
+  g_lookback_spins = spin_limit > 0 ? spin_limit : 0;
+  g_lookback_withheld = withheld_chunk >= 0 ? withheld_chunk : -1;
+}
 
 size_t gs2d_bin_sort_workspace(int n, size_t capacity) {
   // sized for the largest tile grid the ABI accepts

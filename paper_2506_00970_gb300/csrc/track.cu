@@ -5,7 +5,8 @@
 // tangent only (Sec. III-B; the map is frozen during tracking), and a last
 // block of that kernel reduces the tiles' partials and takes an AdamW step on
 // tau = (rho, theta) followed by the retraction T <- Exp(tau) T with tau reset
-// to zero (the moments are kept across iterations of the frame).
+// to zero (the moments are kept across iterations of the frame, in the
+// caller's AdamW state when one is given, so a frame may span several calls).
 // Kernels per iteration: project, bin_sort (init, count, tile scan, scatter,
 // tile sort), fused tile kernel -- 7.
 #include <math.h>
@@ -36,9 +37,12 @@ cudaError_t record_timing_event(cudaEvent_t ev, cudaStream_t st) {
       ev, st, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 
+// Start of a call: zero the completion counter, the status word and the
+// binning counters, and the moments when they live in the workspace (a
+// caller-owned AdamW state is left as the caller passed it).
 __global__ void track_reset_kernel(float* adam, uint32_t* counter, int32_t* status,
                                    uint32_t* sort_zero, size_t sort_zero_words) {
-  if (threadIdx.x < 16) adam[threadIdx.x] = 0.f;
+  if (adam && threadIdx.x < 16) adam[threadIdx.x] = 0.f;
   if (threadIdx.x == 0) {
     *counter = 0u;
     *status = 0;
@@ -118,12 +122,14 @@ const int32_t* gs2d_track_tile_order(void* workspace, int n, size_t capacity,
 }
 
 int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_config* cfg,
-                    const gs2d_track_params* prm, float* pose, const float* obs_rgb, const float* obs_depth, int n_iter, size_t capacity,
-                    float* loss_hist, float* pose_hist, void* workspace, size_t ws_bytes,
-                    size_t* ws_needed, gs2d_stream stream) {
+                    const gs2d_track_params* prm, float* pose, float* adam_state,
+                    const float* obs_rgb, const float* obs_depth, int n_iter, size_t capacity,
+                    float* loss_hist, float* pose_hist, float* grad_hist, void* workspace,
+                    size_t ws_bytes, size_t* ws_needed, gs2d_stream stream) {
   if (!s || !cam || !cfg || !prm || !pose || !obs_rgb || !obs_depth || n_iter < 0)
     return GS2D_ERR_INVALID_ARG;
   if (capacity >= (size_t)0x3FFFFFFF) return GS2D_ERR_INVALID_ARG;
+  if (adam_state && (reinterpret_cast<uintptr_t>(adam_state) & 3)) return GS2D_ERR_INVALID_ARG;
   const size_t need = gs2d_track_workspace(s->n, capacity, cam, cfg);
   if (ws_needed) *ws_needed = need;
   if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
@@ -137,7 +143,9 @@ int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_co
   size_t zero_words = 0;
   sort_zero_region(w.sort_ws, s->n, capacity, gs2d_tiles_x(cam, cfg) * gs2d_tiles_y(cam, cfg),
                    &zero_begin, &zero_words);
-  track_reset_kernel<<<1, 256, 0, st>>>(w.adam, w.counter, status, zero_begin, zero_words);
+  float* adam = adam_state ? adam_state : w.adam;
+  track_reset_kernel<<<1, 256, 0, st>>>(adam_state ? nullptr : w.adam, w.counter, status,
+                                        zero_begin, zero_words);
   GS2D_LAUNCH_CHECK();
   gs2d_bins bins;
   bins.keys = nullptr;
@@ -164,8 +172,8 @@ int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_co
     if (r) return r;
     const bool timed = g_timer.used < g_timer.capacity;
     if (timed) GS2D_CUDA_TRY(record_timing_event(g_timer.start[g_timer.used], st));
-    TrackStep ts{pose, w.adam, loss_hist, pose_hist, it, w.counter, zero_begin, zero_words,
-                 w.order};
+    TrackStep ts{pose, adam, loss_hist, pose_hist, grad_hist, it, w.counter, zero_begin,
+                 zero_words, w.order};
     r = track_tile_launch(w.proj, &bins, cam, cfg, obs_rgb, obs_depth, prm, w.loss_part,
                           w.pose_part, ts, status, st);
     if (r) return r;

@@ -49,26 +49,31 @@ __device__ __forceinline__ void se3_exp_f(const float tau[6], float R[9], float 
   }
 }
 
-// Records the history of an iteration that is skipped after convergence.
+// Records the history of an iteration that is skipped after convergence:
+// the previous loss, the unchanged pose and a zero gradient (none is formed).
 __device__ __forceinline__ void record_converged(const float* __restrict__ pose,
                                                  float* __restrict__ loss_hist,
-                                                 float* __restrict__ pose_hist, int iter) {
+                                                 float* __restrict__ pose_hist,
+                                                 float* __restrict__ grad_hist, int iter) {
   if (loss_hist) loss_hist[iter] = loss_hist[iter > 0 ? iter - 1 : 0];
   if (pose_hist)
     for (int k = 0; k < 12; ++k) pose_hist[12 * iter + k] = pose[k];
+  if (grad_hist)
+    for (int k = 0; k < 6; ++k) grad_hist[6 * iter + k] = 0.f;
 }
 
 // Block-wide (256 threads): sum the n_part partials in a fixed order (L1 is
 // bypassed: other blocks wrote them), then thread 0 takes the AdamW step
 // (tau is zero before the step, so weight decay has no effect) and retracts.
-// Records the loss at the pre-update pose and the updated pose.
-// adam = m[6], v[6], step, done.
+// Records the loss and the gradient at the pre-update pose and the updated
+// pose.  A non-finite loss or gradient leaves the pose and the moments as
+// they were and records GS2D_ERR_NONFINITE.  adam = m[6], v[6], step, done.
 __device__ __forceinline__ void reduce_and_step(const float* __restrict__ pose_part,
                                 const float* __restrict__ loss_part, int n_part,
                                 float* __restrict__ pose, float* __restrict__ adam,
                                 const gs2d_track_params& prm, float* __restrict__ loss_hist,
-                                float* __restrict__ pose_hist, int iter,
-                                int32_t* __restrict__ status, float (*s)[256]) {
+                                float* __restrict__ pose_hist, float* __restrict__ grad_hist,
+                                int iter, int32_t* __restrict__ status, float (*s)[256]) {
   float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int b = threadIdx.x; b < n_part; b += 256) {
 #pragma unroll
@@ -85,26 +90,28 @@ __device__ __forceinline__ void reduce_and_step(const float* __restrict__ pose_p
     __syncthreads();
   }
   if (threadIdx.x != 0) return;
+  bool finite = isfinite(s[6][0]);
+  for (int k = 0; k < 6; ++k) finite = finite && isfinite(s[k][0]);
+  if (loss_hist) loss_hist[iter] = s[6][0];
+  if (grad_hist)
+    for (int k = 0; k < 6; ++k) grad_hist[6 * iter + k] = s[k][0];
+  if (!finite) {
+    *status = GS2D_ERR_NONFINITE;
+    return;
+  }
   const float step = adam[12] + 1.f;
   adam[12] = step;
   const float bc1 = 1.f - powf(prm.beta1, step), bc2 = 1.f - powf(prm.beta2, step);
   float tau[6];
   float nrm2 = 0.f;
-  bool finite = true;
   for (int k = 0; k < 6; ++k) {
     const float g = s[k][0];
-    finite = finite && isfinite(g);
     const float m = prm.beta1 * adam[k] + (1.f - prm.beta1) * g;
     const float v = prm.beta2 * adam[6 + k] + (1.f - prm.beta2) * g * g;
     adam[k] = m;
     adam[6 + k] = v;
     tau[k] = -prm.lr * (m / bc1) / (sqrtf(v / bc2) + prm.eps);
     nrm2 += tau[k] * tau[k];
-  }
-  if (loss_hist) loss_hist[iter] = s[6][0];
-  if (!finite) {
-    *status = GS2D_ERR_NONFINITE;
-    return;
   }
   float dR[9], dt[3];
   se3_exp_f(tau, dR, dt);

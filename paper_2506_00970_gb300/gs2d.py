@@ -102,7 +102,7 @@ EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_stri
            "gs2d_bin_sort", "gs2d_render_fwd", "gs2d_render_bwd_workspace", "gs2d_render_bwd",
            "gs2d_tracking_loss", "gs2d_mapping_loss", "gs2d_track_workspace", "gs2d_track_step",
            "gs2d_track_status", "gs2d_track_tile_order", "gs2d_render_count", "gs2d_bin_sort_static",
-           "gs2d_set_grouped_tiles",
+           "gs2d_set_grouped_tiles", "gs2d_set_lookback_wait",
            "gs2d_profile_track_kernel", "gs2d_profile_track_kernel_count",
            "gs2d_project_batch", "gs2d_bin_sort_batch_workspace", "gs2d_bin_sort_batch",
            "gs2d_render_batch_workspace", "gs2d_render_fwd_batch", "gs2d_render_bwd_batch",
@@ -151,6 +151,8 @@ def lib():
         L.gs2d_render_count.argtypes = [vp] * 6
         L.gs2d_set_grouped_tiles.argtypes = [ip]
         L.gs2d_set_grouped_tiles.restype = None
+        L.gs2d_set_lookback_wait.argtypes = [ip, ip]
+        L.gs2d_set_lookback_wait.restype = None
         L.gs2d_render_bwd_workspace.restype = sz
         L.gs2d_render_bwd_workspace.argtypes = [ip, sz, ip]
         L.gs2d_render_bwd.argtypes = [vp] * 20 + [sz, vp, vp]
@@ -158,7 +160,7 @@ def lib():
         L.gs2d_mapping_loss.argtypes = [vp] * 7 + [ctypes.c_float, ctypes.c_float] + [vp] * 6 + [sz, vp, vp]
         L.gs2d_track_workspace.restype = sz
         L.gs2d_track_workspace.argtypes = [ip, sz, vp, vp]
-        L.gs2d_track_step.argtypes = [vp] * 7 + [ip, sz, vp, vp, vp, sz, vp, vp]
+        L.gs2d_track_step.argtypes = [vp] * 8 + [ip, sz, vp, vp, vp, vp, sz, vp, vp]
         L.gs2d_profile_track_kernel.argtypes = [vp, vp, ip]
         L.gs2d_profile_track_kernel_count.restype = ip
         L.gs2d_project_batch.argtypes = [vp, vp, ip, vp]
@@ -343,6 +345,13 @@ def gs2d_set_grouped_tiles(max_tiles: int):
     """Tile grids of at most max_tiles tiles run the grouped one-pixel
     compositing loops (-1: twice the SM count, the default; 0: never)."""
     lib().gs2d_set_grouped_tiles(int(max_tiles))
+
+
+def gs2d_set_lookback_wait(spin_limit: int = 0, withheld_chunk: int = -1):
+    """Polls of a binning scan block's look-back wait before it records
+    GS2D_ERR_TIMEOUT (0: the default), and the scan block (4096 surfels) that
+    never publishes its sum (-1: none) -- for tests of the timeout path."""
+    lib().gs2d_set_lookback_wait(int(spin_limit), int(withheld_chunk))
 
 
 def gs2d_render_contrib_workspace(capacity) -> int:
@@ -553,13 +562,17 @@ def gs2d_track_workspace(n, capacity, cam: Camera, cfg: Config) -> int:
 
 def gs2d_track_step(surf: DeviceSurfels, cam: Camera, cfg: Config, prm: TrackParams, pose,
                     obs_rgb, obs_depth, n_iter, capacity, loss_hist, pose_hist, workspace,
-                    stream=None):
+                    stream=None, adam_state=None, grad_hist=None):
+    """n_iter tracking iterations (see gs2d.h).  adam_state: optional
+    caller-owned device [16] AdamW state (zero it to start a frame; NULL =
+    reset at every call); grad_hist: optional device [n_iter, 6] pose
+    gradients."""
     s = surf.struct()
     check(lib().gs2d_track_step(_ref(s), _ref(cam), _ref(cfg), _ref(prm), _ptr(pose),
-                                _ptr(obs_rgb), _ptr(obs_depth), int(n_iter), int(capacity),
-                                _ptr(loss_hist), _ptr(pose_hist), _ptr(workspace),
-                                workspace.numel() * workspace.element_size(), None,
-                                _stream(stream)), "gs2d_track_step")
+                                _ptr(adam_state), _ptr(obs_rgb), _ptr(obs_depth), int(n_iter),
+                                int(capacity), _ptr(loss_hist), _ptr(pose_hist), _ptr(grad_hist),
+                                _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                None, _stream(stream)), "gs2d_track_step")
 
 
 def gs2d_profile_track_kernel(events_start, events_stop):

@@ -10,13 +10,17 @@
   ragged last tile row) and on sampled pixels of the 200k-surfel room at
   640x480;
 * gs2d_render_bwd: surfel and pose gradients within 1e-3 relative, full
-  and tracking (pose-only) modes, deterministic across runs.
+  and tracking (pose-only) modes, deterministic across runs: every element
+  of every surfel that the oracle does not flag (a candidate at a pixel with
+  a threshold decision within rounding, or seen within ~3 degrees of
+  edge-on) within 1e-3 relative plus 2^-17 of the array's scale, no
+  exceptions; every surfel within 1e-3 of the array's scale.
 """
 import numpy as np
 import pytest
 
 from paper_2506_00970_gb300 import scenes
-from gpu_helpers import TOL_GRAD, assert_images_close, gpu_render, to_np
+from gpu_helpers import assert_grads_close, assert_images_close, gpu_render, grad_rows_ok, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -202,23 +206,6 @@ def test_render_edge_cases(torch_cuda, orc, tile, px):
 # ---------------------------------------------------------------------------
 # backward
 # ---------------------------------------------------------------------------
-def _grad_close(a, b, name, tol=TOL_GRAD, rows=None, elem_frac=2e-3):
-    """max |a - b| <= tol * max |b| over the array, and per element for
-    elements above 1% of the array's scale (99.8% of them), on the rows (surfels) selected by
-    ``rows`` -- those not seen within ~3 degrees of edge-on at any pixel, where the FP32
-    intersection is ill-conditioned."""
-    a = np.asarray(a, np.float64)
-    b = np.asarray(b, np.float64)
-    scale = max(np.abs(b).max(), 1e-12)
-    err = np.abs(a - b)
-    assert err.max() <= tol * scale, (name, err.max() / scale)
-    if rows is not None and b.ndim >= 1 and b.shape[0] == rows.shape[0]:
-        err, b = err[rows], b[rows]
-    big = np.abs(b) > 1e-2 * scale
-    rel = err[big] / np.abs(b[big])
-    assert np.mean(rel > tol) < elem_frac, (name, np.mean(rel > tol))
-
-
 def _slab_loss_setup(orc):
     s, cam, gt = scenes.slab_scene(0), scenes.slab_camera(), scenes.identity_pose()
     target_pose = scenes.perturb_pose(gt, 0.02, 1.0, seed=11)
@@ -244,12 +231,13 @@ def test_render_bwd_slab_all_params_and_pose(torch_cuda, orc, tile, px):
     T = lambda a: torch.tensor(np.asarray(a, np.float32), device="cuda")
     gg = r.backward(ds, pose_t, T(d_rgb), T(d_depth), None, None, full=True)
     torch.cuda.synchronize()
-    ok = og["min_cos"] > 0.05
-    for k in ("mu", "quat", "scale", "opacity", "rgb", "pose6"):
-        _grad_close(to_np(gg[k]), og[k], k, rows=ok)
+    ok = grad_rows_ok(og)
+    for k in ("mu", "quat", "scale", "opacity", "rgb"):
+        assert_grads_close(to_np(gg[k]), og[k], k, rows_ok=ok)
+    assert_grads_close(to_np(gg["pose6"]), og["pose6"], "pose6", tol=1e-3)
     # tracking mode returns the same pose gradient
     gp = r.backward(ds, pose_t, T(d_rgb), T(d_depth), None, None, full=False)
-    _grad_close(to_np(gp["pose6"]), og["pose6"], "pose6 (tracking mode)")
+    assert_grads_close(to_np(gp["pose6"]), og["pose6"], "pose6 (tracking mode)")
 
 
 @pytest.mark.parametrize("tile,px", [((16, 16), 1), ((16, 64), 4)])
@@ -261,13 +249,14 @@ def test_render_bwd_with_normal_and_opacity_grads(torch_cuda, orc, tile, px):
     og = orc.render_bwd(s, cam, pose, *up)
     T = lambda a: torch.tensor(np.asarray(a, np.float32), device="cuda")
     gg = r.backward(ds, pose_t, T(up[0]), T(up[1]), T(up[2]), T(up[3]), full=True)
-    ok = og["min_cos"] > 0.05
-    # random-sign upstream gradients make many surfel sums cancel, so the
-    # per-element relative check allows 1%; the array-wide bound is unchanged
-    for k in ("mu", "quat", "scale", "opacity", "rgb", "pose6"):
-        _grad_close(to_np(gg[k]), og[k], k, rows=ok, elem_frac=1e-2)
+    ok = grad_rows_ok(og)
+    # random-sign upstream gradients make many surfel sums cancel: the
+    # floor of the per-element bound covers their FP32 rounding
+    for k in ("mu", "quat", "scale", "opacity", "rgb"):
+        assert_grads_close(to_np(gg[k]), og[k], k, rows_ok=ok)
+    assert_grads_close(to_np(gg["pose6"]), og["pose6"], "pose6")
     gp = r.backward(ds, pose_t, T(up[0]), T(up[1]), T(up[2]), T(up[3]), full=False)
-    _grad_close(to_np(gp["pose6"]), og["pose6"], "pose6 (tracking mode)")
+    assert_grads_close(to_np(gp["pose6"]), og["pose6"], "pose6 (tracking mode)")
 
 
 def test_render_bwd_deterministic(torch_cuda):
@@ -301,9 +290,10 @@ def test_render_bwd_room_pixel_subset(torch_cuda, orc):
     gg = r.backward(ds, pose_t, *(T(u) for u in up), full=True)
     touched = np.abs(og["rgb"]).sum(1) > 0
     assert touched.sum() > 100
-    ok = og["min_cos"] > 0.05
-    for k in ("mu", "quat", "scale", "opacity", "rgb", "pose6"):
-        _grad_close(to_np(gg[k]), og[k], k, rows=ok)
+    ok = grad_rows_ok(og)
+    for k in ("mu", "quat", "scale", "opacity", "rgb"):
+        assert_grads_close(to_np(gg[k]), og[k], k, rows_ok=ok, min_rows=0.5)
+    assert_grads_close(to_np(gg["pose6"]), og["pose6"], "pose6")
 
 
 def test_autograd_render_matches_oracle_gradient(torch_cuda, orc):
@@ -325,10 +315,10 @@ def test_autograd_render_matches_oracle_gradient(torch_cuda, orc):
     o = orc.render(s, cam, pose)
     og = orc.render_bwd(s, cam, pose, np.sign(o["rgb"] - tgt["rgb"]), np.sign(o["depth"] - tgt["depth"]),
                         np.zeros_like(o["rgb"]), np.zeros_like(o["depth"]))
-    ok = og["min_cos"] > 0.05
+    ok = grad_rows_ok(og)
     for k, p in zip(("mu", "quat", "scale", "opacity", "rgb"), params):
-        _grad_close(to_np(p.grad), og[k], k, rows=ok)
-    _grad_close(to_np(tau.grad), og["pose6"], "pose6")
+        assert_grads_close(to_np(p.grad), og[k], k, rows_ok=ok)
+    assert_grads_close(to_np(tau.grad), og["pose6"], "pose6")
     # a non-zero tangent renders at Exp(tau) T
     tau2 = torch.tensor([0.01, 0.0, 0.0, 0.0, 0.0, 0.0], device="cuda")
     with torch.no_grad():

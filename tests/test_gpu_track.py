@@ -96,10 +96,13 @@ def _track_setup(orc, n=30_000, seed=0):
 
 @pytest.mark.parametrize("tile,px", [((16, 16), 1), ((32, 16), 2), ((64, 12), 3), ((32, 32), 4)])
 def test_track_step_first_gradient_and_convergence(torch_cuda, orc, tile, px):
-    """The fused tracking step: its first pose gradient equals the oracle's at
-    the start pose (through the loss and the pose-only backward), and 100
-    iterations from a 2 cm / 1 degree perturbation reach 1 cm / 0.5 degree
-    (1, 2 and 4 pixels per thread)."""
+    """Tracking from a 2 cm / 1 degree perturbation on the unshifted
+    observation (1 to 4 pixels per thread): the fused step's first loss
+    matches the oracle's, the standalone render + tracking loss + pose-only
+    gs2d_render_bwd at the start pose gives the oracle's pose gradient, and
+    100 fused iterations reach 1 cm / 0.5 degree.  The fused kernel's own
+    per-iteration gradients, AdamW steps and retractions are held to the
+    oracle element by element in test_gpu_track_parity.py."""
     torch = torch_cuda
     from paper_2506_00970_gb300 import gs2d
     s, cam, gt = _track_setup(orc)
@@ -129,6 +132,9 @@ def test_track_step_first_gradient_and_convergence(torch_cuda, orc, tile, px):
     assert st in (0, gs2d.CONVERGED), st
     lh = lh.cpu().numpy()
     ph = ph.cpu().numpy().astype(np.float64)
+    # on the unshifted observation many residuals sit within rounding of
+    # zero (the L1 sub-gradient is not unique there) and edge-on surfels are
+    # kept, so these two checks are looser than the parity file's
     assert lh[0] == pytest.approx(L0, rel=2e-3)
     # the pose gradient of the first iteration, through the same C ABI calls
     r, _, pt, _ = gpu_render(s, cam, start)
