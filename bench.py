@@ -42,10 +42,10 @@ WORKLOAD = ("tracking-scale room: 200k surfels on a 5x4x3 m room with 20 boxes/s
 ORACLE_CROP = 64          # reference arm: a 64x64 pixel crop per step (~1 s of host work)
 CPU_SAMPLE_CROP = 192       # cpu_baseline: one 192x192 crop (~10 s of host work)
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes per launch of the roofline kernel from an ncu capture of the
-# same workload (profiles/track_tile_tracking_640x480.md); None if the kernel
-# changed since the capture.
-TRAFFIC_BYTES = {"track_tile": 6324480}
+# DRAM bytes per launch of the roofline kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of the fused tracking kernel on
+# this workload); None while the kernel has changed since the capture.
+TRAFFIC_BYTES = {"track_tile": None}
 # batched workloads reported beside the tracking line
 MAP_SURFELS, MAP_VIEWS = 1_000_000, 8
 UNEVEN_SURFELS, UNEVEN_VIEWS = 2_000_000, 32
@@ -172,8 +172,8 @@ def _pose_err_np(row, gt):
     t = row[9:]
     c = -R.T @ t
     cg = -gt.R.T @ gt.t
-    cosang = np.clip((np.trace(R @ gt.R.T) - 1) / 2, -1.0, 1.0)
-    return float(np.linalg.norm(c - cg)), float(np.degrees(np.arccos(cosang)))
+    from paper_2506_00970_gb300.proposal import rotation_angle_deg
+    return float(np.linalg.norm(c - cg)), rotation_angle_deg(R @ gt.R.T)
 
 
 def peaks():
@@ -197,8 +197,8 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
 #  w, colour, depth and normal accumulation (3 + 6 + 2 + 6) -> 17.  The
 #  pose-only backward adds per replayed blended pair ~80 (transmittance
 #  recovery, dL/da, the chain through G, q, beta, Gv, X x Gv, t_nc x g and
-#  the 6-vector accumulation); its evaluated pairs are bounded by the
-#  forward's counts.
+#  the 6-vector accumulation); it evaluates the pairs up to each pixel's
+#  last blended one (gs2d_render_count's replayed counts).
 FLOPS_EVAL, FLOPS_IN, FLOPS_BLEND, FLOPS_BWD_BLEND = 17, 4, 17, 80
 FLOPS_LOSS_PIXEL = 20   # masks, three colour and one depth difference, signs
 
@@ -353,6 +353,7 @@ def run_ours(args):
     roof = roofline(r, ds, frames, cam, cfg, stream, ms_iter, fused_ms)
     del graph
     batch = batch_workloads(K, W_, flush)
+    batch["slab_single_view"] = slab_render(K, W_, flush)
     maint = map_maintenance(flush)
     tracking["learned_proposal"] = learned_proposal(flush)
     tracking["learned_proposal_tracking_scale"] = tracking_scale_proposal(rank)
@@ -405,14 +406,14 @@ def roofline(r, ds, frames, cam, cfg, stream, ms_iter, fused_ms):
     pk, src = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(sm_mhz)
-    counts = torch.zeros(3, dtype=torch.int64, device="cuda")
+    counts = torch.zeros(5, dtype=torch.int64, device="cuda")
     g_rgb = torch.zeros(cam.height, cam.width, 3, device="cuda")
     g_d = torch.zeros(cam.height, cam.width, device="cuda")
     g_o = torch.zeros(cam.height, cam.width, device="cuda")
     loss = torch.zeros(1, device="cuda")
     lws = torch.empty(1 << 16, dtype=torch.uint8, device="cuda")
     prm = gs2d.default_track_params()
-    fwd_ms, bwd_ms, work_f, work_b = [], [], [], []
+    fwd_ms, bwd_ms, work_f, work_b, pairs = [], [], [], [], []
     R = 10
     for fr in frames[:4]:
         pt = fr["start_t"]
@@ -421,9 +422,10 @@ def roofline(r, ds, frames, cam, cfg, stream, ms_iter, fused_ms):
                                 r.cam, prm, g_rgb, g_d, g_o, loss, lws)
         gs2d.gs2d_render_count(r.proj, r.bins, r.cam, r.cfg, counts)
         torch.cuda.synchronize()
-        E, Ein, B = (int(x) for x in counts.cpu().numpy())
+        E, Ein, B, Eb, Ebin = (int(x) for x in counts.cpu().numpy())
         work_f.append(FLOPS_EVAL * E + FLOPS_IN * Ein + FLOPS_BLEND * B)
-        work_b.append(FLOPS_EVAL * E + FLOPS_IN * Ein + FLOPS_BWD_BLEND * B)
+        work_b.append(FLOPS_EVAL * Eb + FLOPS_IN * Ebin + FLOPS_BWD_BLEND * B)
+        pairs.append((E, Ein, B, Eb, Ebin))
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * R)]
         for k in range(R):
             ev[2 * k].record(stream)
@@ -448,6 +450,12 @@ def roofline(r, ds, frames, cam, cfg, stream, ms_iter, fused_ms):
              "achieved": afu, "peak": peak, "unit": "TFLOP/s", "frac": afu / peak,
              "traffic": TRAFFIC_BYTES["track_tile"], "launch_ms": fused_ms,
              "share_of_iter": fused_ms / ms_iter, "flop_per_launch": work_fused,
+             "pairs_per_launch": dict(zip(("evaluated", "inside_cutoff", "blended",
+                                           "replayed_evaluated", "replayed_inside_cutoff"),
+                                          (float(x) for x in np.mean(pairs, axis=0)))),
+             "flop_per_pair": {"evaluated": FLOPS_EVAL, "inside_cutoff": FLOPS_IN,
+                               "blended_fwd": FLOPS_BLEND, "blended_bwd": FLOPS_BWD_BLEND,
+                               "loss_per_pixel": FLOPS_LOSS_PIXEL},
              "peak_note": f"FP32 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz (of measured max clock)"}
     af = np.mean(work_f) / tf / 1e12
     ab = np.mean(work_b) / tb / 1e12
@@ -561,8 +569,8 @@ def measure_batch(name, s_true, cams, poses, actives, K, W_, flush, seed):
     if any(st):
         raise RuntimeError(f"{name}: batch status {st}")
     # algorithmic FP32 work of the two compositing launches from pair counts
-    counts = torch.zeros(3, dtype=torch.int64, device="cuda")
-    E = np.zeros(3)
+    counts = torch.zeros(5, dtype=torch.int64, device="cuda")
+    E = np.zeros(5)
     for b in br.keep:
         gs2d.gs2d_render_count(b["proj"], b["bins"], b["ccam"], b["cfg"], counts)
         torch.cuda.synchronize()
@@ -570,7 +578,7 @@ def measure_batch(name, s_true, cams, poses, actives, K, W_, flush, seed):
     pk, src = peaks()
     peak = fp32_peak_tflops(float(pk.get("sm_max_mhz", 2070.0)))
     w_f = FLOPS_EVAL * E[0] + FLOPS_IN * E[1] + FLOPS_BLEND * E[2]
-    w_b = FLOPS_EVAL * E[0] + FLOPS_IN * E[1] + FLOPS_BWD_BLEND * E[2]
+    w_b = FLOPS_EVAL * E[3] + FLOPS_IN * E[4] + FLOPS_BWD_BLEND * E[2]
     tf, tb = np.median(per["render_fwd"]) / 1e3, np.median(per["render_bwd"]) / 1e3
     P = sum(int(c.width) * int(c.height) for c in cams)
     g_ms = float(np.median(gms))
@@ -585,7 +593,8 @@ def measure_batch(name, s_true, cams, poses, actives, K, W_, flush, seed):
         "px_per_thread": px, "tiles": [f"{t[0]}x{t[1]}" for t in tiles],
         "autotune_ms_per_view": sweep,
         "autotune_s": tune_s, "loss": [float(x) for x in loss.cpu().numpy()],
-        "pairs": {"evaluated": int(E[0]), "inside_cutoff": int(E[1]), "blended": int(E[2])},
+        "pairs": {"evaluated": int(E[0]), "inside_cutoff": int(E[1]), "blended": int(E[2]),
+                  "replayed_evaluated": int(E[3]), "replayed_inside_cutoff": int(E[4])},
         "roofline": [
             {"kernel": "fwd_batch_kernel (persistent)", "bound": "alu",
              "achieved": w_f / tf / 1e12, "peak": peak, "unit": "TFLOP/s",
@@ -600,6 +609,148 @@ def measure_batch(name, s_true, cams, poses, actives, K, W_, flush, seed):
     del graph, br, ds
     torch.cuda.empty_cache()
     return out
+
+
+def slab_render(K, W_, flush):
+    """The plain single-view workload: 4,096 surfels, centres uniform in a
+    2 x 2 m slab 1-3 m in front of a 160x120 camera (fx = fy = 150),
+    log-uniform 1-5 cm scales, random rotations, sigmoid(N(0,1)) opacity,
+    random colours; L1 colour + L1 depth (on D/O, lambda_d = 1) against a
+    target rendered at a pose 2 cm / 1 deg away; one step = project,
+    bin_sort, render_fwd, the loss and the full render_bwd (gradients to
+    every surfel parameter and the pose), timed as direct calls and as one
+    CUDA graph replay (L2 flushed before each).  The FP64 oracle runs the
+    same step on the full image."""
+    import torch
+    from paper_2506_00970_gb300 import gs2d, scenes
+    import oracle
+    stream = torch.cuda.current_stream()
+    s, cam = scenes.slab_scene(0), scenes.slab_camera()
+    pose = scenes.identity_pose()
+    target = scenes.perturb_pose(pose, 0.02, 1.0, seed=11)
+    ds = gs2d.DeviceSurfels(s)
+    r = gs2d.Rasterizer(cam, ds.n, capacity=64 * ds.n)
+    out = r.forward(ds, gs2d.pose_tensor(target))
+    obs_rgb = out["rgb"].clone()
+    obs_d = out["depth"] / out["opacity"].clamp_min(1e-6)
+    pose_t = gs2d.pose_tensor(pose)
+    r.forward(ds, pose_t)
+    torch.cuda.synchronize()
+    H, W, n = cam.height, cam.width, ds.n
+    f = dict(dtype=torch.float32, device="cuda")
+    g = [torch.empty(H, W, 3, **f), torch.empty(H, W, **f), torch.empty(H, W, 3, **f),
+         torch.empty(H, W, **f)]
+    loss = torch.empty(1, **f)
+    lws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    grads = [torch.empty(n, 3, **f), torch.empty(n, 4, **f), torch.empty(n, 2, **f),
+             torch.empty(n, **f), torch.empty(n, 3, **f), torch.empty(6, **f)]
+
+    def project():
+        gs2d.gs2d_project(ds, r.cam, pose_t, r.cfg, r.proj, r.tiles)
+
+    def bin_sort():
+        gs2d.gs2d_bin_sort(r.proj, r.tiles, r.n, r.cam, r.cfg, r.sort_ws, r.bins)
+
+    def render_fwd():
+        r.render_fwd()
+
+    def loss_fn():
+        gs2d.gs2d_mapping_loss(r.rgb, r.depth, r.normal, r.opacity, obs_rgb, obs_d, r.cam, 1.0, 0.0,
+                               *g, loss, lws)
+
+    def render_bwd():
+        gs2d.gs2d_render_bwd(r.proj, r.bins, r.tiles, ds, pose_t, r.cam, r.cfg, r.t_final, r.n_last,
+                             g[0], g[1], g[2], g[3], *grads, r.bwd_ws)
+
+    phases = (("project", project), ("bin_sort", bin_sort), ("render_fwd", render_fwd),
+              ("loss", loss_fn), ("render_bwd", render_bwd))
+
+    def step():
+        for _, fn in phases:
+            fn()
+
+    per = {k: [] for k, _ in phases}
+    direct = []
+    for i in range(W_ + K):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(phases) + 1)]
+        ev[0].record(stream)
+        for j, (_, fn) in enumerate(phases):
+            fn()
+            ev[j + 1].record(stream)
+        ev[-1].synchronize()
+        if i >= W_:
+            for j, (k, _) in enumerate(phases):
+                per[k].append(ev[j].elapsed_time(ev[j + 1]))
+            direct.append(ev[0].elapsed_time(ev[-1]))
+    if int(r.status.item()) != 0:
+        raise RuntimeError(f"slab status {int(r.status.item())}")
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        step()
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for _ in range(W_):
+        graph.replay()
+    gms = []
+    for _ in range(K):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        e1.synchronize()
+        gms.append(e0.elapsed_time(e1))
+    if int(r.status.item()) != 0:
+        raise RuntimeError(f"slab status {int(r.status.item())}")
+    counts = torch.zeros(5, dtype=torch.int64, device="cuda")
+    gs2d.gs2d_render_count(r.proj, r.bins, r.cam, r.cfg, counts)
+    torch.cuda.synchronize()
+    E = counts.cpu().numpy().astype(np.float64)
+    w_f = FLOPS_EVAL * E[0] + FLOPS_IN * E[1] + FLOPS_BLEND * E[2]
+    w_b = FLOPS_EVAL * E[3] + FLOPS_IN * E[4] + FLOPS_BWD_BLEND * E[2]
+    pk, src = peaks()
+    peak = fp32_peak_tflops(float(pk.get("sm_max_mhz", 2070.0)))
+    tf, tb = np.median(per["render_fwd"]) / 1e3, np.median(per["render_bwd"]) / 1e3
+    g_ms = float(np.median(gms))
+    P = H * W
+    # the oracle on the full image: forward, the same loss, full backward
+    cores = oracle.default_threads()
+    ot = oracle.render(s, cam, target, n_threads=cores)
+    o_rgb, o_d = ot["rgb"], ot["depth"] / np.maximum(ot["opacity"], 1e-6)
+    t0 = time.perf_counter()
+    o = oracle.render(s, cam, pose, n_threads=cores)
+    img = {k: o[k] for k in ("rgb", "depth", "normal", "opacity")}
+    _, og = oracle.mapping_loss(img, o_rgb, o_d, cam, w_d=1.0, w_n=0.0)
+    oracle.render_bwd(s, cam, pose, og["rgb"], og["depth"], og["normal"], og["opacity"],
+                      n_threads=cores)
+    dt = time.perf_counter() - t0
+    return {
+        "workload": (f"plain single view: {n} surfels in a 2x2 m slab 1-3 m ahead, 160x120, "
+                     "fx=fy=150, L1 colour + L1 depth against a target 2 cm / 1 deg away, "
+                     "gradients to all surfel parameters and the pose"),
+        "value": P / (g_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": g_ms,
+        "ms_per_step_direct": float(np.median(direct)),
+        "mpix_per_s_direct": P / (np.median(direct) / 1e3) / 1e6,
+        "phases_ms": {k: float(np.median(v)) for k, v in per.items()},
+        "launch": "one CUDA graph per step (project, bin_sort 5 kernels, render_fwd, loss, "
+                  "render_bwd 2 kernels); L2 flushed before each",
+        "pairs": {"evaluated": int(E[0]), "inside_cutoff": int(E[1]), "blended": int(E[2]),
+                  "replayed_evaluated": int(E[3]), "replayed_inside_cutoff": int(E[4])},
+        "roofline": {"kernel": "render_fwd_kernel + render_bwd_kernel<full> + surfel_grad_kernel",
+                     "bound": "alu", "unit": "TFLOP/s", "peak": peak,
+                     "fwd_achieved": w_f / tf / 1e12, "fwd_frac": w_f / tf / 1e12 / peak,
+                     "bwd_achieved": w_b / tb / 1e12, "bwd_frac": w_b / tb / 1e12 / peak,
+                     "note": "a 160x120 view has 80 tiles on 152 SMs: launch- and "
+                             "latency-bound, not throughput-bound"},
+        "cpu_baseline": {"value": P / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "the full step on the full 160x120 image (FP64 forward, "
+                                   "loss, full backward)", "seconds": dt},
+    }
 
 
 def batch_workloads(K, W_, flush):
@@ -689,10 +840,10 @@ def map_maintenance(flush, reps=10):
     counts = torch.zeros(2, dtype=torch.int32, device="cuda")
     score = torch.zeros(1, device="cuda")
     is_kf = torch.zeros(1, dtype=torch.int32, device="cuda")
-    cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(5, dtype=torch.int64, device="cuda")
     gs2d.gs2d_render_count(r.proj, r.bins, r.cam, r.cfg, cnt)
     torch.cuda.synchronize()
-    E, Ein, B = (int(x) for x in cnt.cpu().numpy())
+    E, Ein, B = (int(x) for x in cnt.cpu().numpy()[:3])
     work = (FLOPS_EVAL + 1) * E + FLOPS_IN * Ein + FLOPS_CONTRIB_BLEND * B
 
     def keyframe_test():

@@ -221,8 +221,10 @@ int gs2d_render_fwd(const float* proj, const gs2d_bins* bins, const gs2d_camera*
 
 /* Work counter of gs2d_render_fwd (diagnostic, same loop and culling):
  * counts[0] = evaluated (pixel, surfel) pairs, counts[1] = pairs inside the
- * cutoff radius, counts[2] = blended pairs; device uint64 [3], zeroed here.
- * The roofline of the compositing kernels is stated per these counts. */
+ * cutoff radius, counts[2] = blended pairs, counts[3] / counts[4] = the
+ * evaluated pairs / those inside the cutoff up to each pixel's last blended
+ * pair (the pairs a backward replay evaluates); device uint64 [5], zeroed
+ * here.  The roofline of the compositing kernels is stated per these counts. */
 int gs2d_render_count(const float* proj, const gs2d_bins* bins, const gs2d_camera* cam,
                       const gs2d_config* cfg, unsigned long long* counts, gs2d_stream stream);
 

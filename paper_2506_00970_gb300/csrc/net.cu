@@ -1250,7 +1250,8 @@ Operand conv_op(const bf16* p, int rows, int l, int C) {
 // gradients and the split deep layers) run on the tcgen05 kernel; GEMMs with
 // a direct epilogue (large M, the gather-bound convolutions) on the mma.sync
 // kernel, whose smaller blocks keep more warps resident to hide the gathers
-// (profiles/ holds the per-kind comparison).
+// (measured on the batch-256 training step: all mma.sync 2.38 ms, this split
+// 2.46 ms, all tcgen05 3.19 ms).
 template <int AM, int BMODE, int EPI>
 int run(Gemm g, int splits, cudaStream_t st, int* n_splits = nullptr) {
   constexpr bool tc = EPI == E_PARTIAL;

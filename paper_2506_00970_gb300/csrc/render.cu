@@ -75,13 +75,13 @@ __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<P, kG>()) ren
   const int tile_x0 = (tile % tiles_x) * cfg.tile_w, tile_y0 = (tile / tiles_x) * cfg.tile_h;
   const float xt = (float)tile_x0 + 0.5f - cam.cx;
   const float yt = (float)tile_y0 + 0.5f - cam.cy;
-  uint32_t cnt[3] = {0u, 0u, 0u};
+  uint32_t cnt[5] = {0u, 0u, 0u, 0u, 0u};
   FwdState st[P];
   fwd_tile<kFwdVec4, kCount, P, kG>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt,
                                     tile_x0, tile_y0, tp, inside, cam, cfg, s_rec, hl, cnt, st);
   if (kCount) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 5; ++k) {
       unsigned long long v = cnt[k];
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -578,7 +578,7 @@ int gs2d_render_count(const float* proj, const gs2d_bins* bins, const gs2d_camer
   if (v) return v;
   if (!proj || !bins || !bins->vals || !bins->tile_ranges || !counts) return GS2D_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  GS2D_CUDA_TRY(cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned long long), st));
+  GS2D_CUDA_TRY(cudaMemsetAsync(counts, 0, 5 * sizeof(unsigned long long), st));
   const int tx = gs2d_tiles_x(cam, cfg), ty = gs2d_tiles_y(cam, cfg);
   GS2D_DISPATCH_P(cfg->px_per_thread, render_fwd_kernel<true, P><<<tx * ty, kTileThreads, 0, st>>>(
       reinterpret_cast<const float4*>(proj), bins->vals, bins->tile_ranges, *cam, *cfg, tx, nullptr,

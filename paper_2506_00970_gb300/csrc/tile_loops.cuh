@@ -183,7 +183,9 @@ struct FwdState {
 // Front-to-back compositing of the thread's P pixels over its tile's list.
 // Each warp visits only the staged surfels whose footprint touches its
 // block; a surfel's staged record is read once for all P pixels.  With
-// kCount it counts evaluated pairs, pairs inside the cutoff and blended pairs.
+// kCount it counts (cnt[0..4]) evaluated pairs, pairs inside the cutoff,
+// blended pairs, and the evaluated pairs and those inside the cutoff up to
+// each pixel's last blended pair (the pairs a backward replay evaluates).
 struct HitLists {
   uint32_t mask[kTileThreads];
   uint8_t list[kTileThreads / 32][kTileThreads];
@@ -216,6 +218,11 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ proj,
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int kFp = kStride == kFwdVec4 ? 4 : 6;  // slot holding the footprint
+  // kCount: per pixel, evaluations (inside the cutoff) so far and at its
+  // last blended pair
+  uint32_t ev_k[P], in_k[P], last_ev[P], last_in[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) ev_k[k] = in_k[k] = last_ev[k] = last_in[k] = 0u;
   float lyk[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) lyk[k] = k ? tp.ly + 4.f * k : tp.ly;
@@ -292,6 +299,10 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ proj,
           all_done = true;
           break;
         }
+        if (kCount) {
+          last_ev[0] = cnt[0];
+          last_in[0] = cnt[1];
+        }
         const float4 r3 = s_rec[j][3];
         const float tnz = s_rec[j][4].x;
         const float w = e.a * q.T;
@@ -318,13 +329,21 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ proj,
                                      cfg.alpha_min, cfg.alpha_max, e);
           if (kCount) {
             ++cnt[0];
-            if (fmaf(e.u, e.u, __fmul_rn(e.v, e.v)) <= cfg.cutoff_r2) ++cnt[1];
+            ++ev_k[k];
+            if (fmaf(e.u, e.u, __fmul_rn(e.v, e.v)) <= cfg.cutoff_r2) {
+              ++cnt[1];
+              ++in_k[k];
+            }
           }
           if (!hit) continue;
           const float Tn = st[k].T * (1.f - e.a);
           if (Tn < cfg.t_min) {
             done[k] = true;
             continue;
+          }
+          if (kCount) {
+            last_ev[k] = ev_k[k];
+            last_in[k] = in_k[k];
           }
           const float4 r3 = s_rec[j][3];
           const float tnz = s_rec[j][4].x;
@@ -345,6 +364,13 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ proj,
         for (int k = 0; k < P; ++k) all_done = all_done && done[k];
         if (all_done) break;
       }
+    }
+  }
+  if (kCount) {
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      cnt[3] += last_ev[k];
+      cnt[4] += last_in[k];
     }
   }
 }

@@ -337,6 +337,9 @@ def gs2d_render_fwd(proj, bins: Bins, cam: Camera, cfg: Config, rgb, depth, norm
 
 
 def gs2d_render_count(proj, bins: Bins, cam: Camera, cfg: Config, counts, stream=None):
+    """counts: device int64 [5] (see gs2d.h)."""
+    if counts.numel() < 5 or counts.element_size() != 8:
+        raise Gs2dError("gs2d_render_count needs a 5-element 64-bit counts buffer")
     check(lib().gs2d_render_count(_ptr(proj), _ref(bins), _ref(cam), _ref(cfg), _ptr(counts),
                                   _stream(stream)), "gs2d_render_count")
 

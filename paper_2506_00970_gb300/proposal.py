@@ -29,6 +29,15 @@ def poses_tensor(poses, device="cuda"):
     return torch.stack([gs2d.pose_tensor(p, device) for p in poses])
 
 
+def rotation_angle_deg(Rd) -> float:
+    """Angle of a rotation matrix in degrees, atan2(|vee(R - R^T)| / 2,
+    (tr R - 1) / 2): unlike acos of the trace alone it keeps small angles
+    of an FP32 rotation (acos loses everything below ~0.03 degrees)."""
+    Rd = np.asarray(Rd, np.float64)
+    w = np.array([Rd[2, 1] - Rd[1, 2], Rd[0, 2] - Rd[2, 0], Rd[1, 0] - Rd[0, 1]])
+    return math.degrees(math.atan2(0.5 * float(np.linalg.norm(w)), 0.5 * (np.trace(Rd) - 1.0)))
+
+
 def pose_error(P12, gt) -> tuple[float, float]:
     """Camera-centre distance (m) and geodesic rotation angle (degrees)
     between a pose given as 12 floats and a ground-truth Pose."""
@@ -36,8 +45,7 @@ def pose_error(P12, gt) -> tuple[float, float]:
     R, t = P[:9].reshape(3, 3), P[9:]
     c = -R.T @ t
     cg = -gt.R.T @ gt.t
-    cosang = np.clip((np.trace(R @ gt.R.T) - 1.0) / 2.0, -1.0, 1.0)
-    return float(np.linalg.norm(c - cg)), math.degrees(math.acos(cosang))
+    return float(np.linalg.norm(c - cg)), rotation_angle_deg(R @ gt.R.T)
 
 
 def first_below(pose_hist, gt, tcm=0.01, tdeg=0.5):
@@ -276,12 +284,200 @@ def timed_replays(graph, reps: int, before=None) -> list[float]:
     return out
 
 
+def timed_ms(fn) -> float:
+    """Device time of fn's launches on the current stream (CUDA events)."""
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    fn()
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+# The plain loop's limits under the stop rule of Sec. III-D: n_iter of
+# Table I and the step-size reading |tau| < 1e-5.
+STOP_ITERS, STOP_TOL = 120, 1e-5
+
+
+class LoopGraphs:
+    """The plain tracking loop on fixed buffers (pose, observation, a
+    caller-owned AdamW state zeroed at the start of every frame) as CUDA
+    graphs, one per (iterations, stop tolerance), captured on first use."""
+
+    def __init__(self, surf, cam, capacity: int, obs_rgb, obs_d, device="cuda"):
+        self.surf, self.obs_rgb, self.obs_d = surf, obs_rgb, obs_d
+        self.ccam, self.cfg = gs2d.camera(cam), gs2d.default_config()
+        self.cap = capacity
+        self.pose = torch.empty(12, device=device)
+        self.adam = torch.zeros(16, device=device)
+        self.ws = torch.empty(gs2d.gs2d_track_workspace(surf.n, capacity, self.ccam, self.cfg),
+                              dtype=torch.uint8, device=device)
+        self.device = device
+        self._graphs, self.hist = {}, {}
+
+    def graph(self, n_iter: int, stop_tol: float = 0.0):
+        key = (int(n_iter), float(stop_tol))
+        if key not in self._graphs:
+            prm = gs2d.default_track_params(stop_tol=stop_tol)
+            lh = torch.zeros(n_iter, device=self.device)
+            ph = torch.zeros(n_iter, 12, device=self.device)
+
+            def frame():
+                self.adam.zero_()
+                gs2d.gs2d_track_step(self.surf, self.ccam, self.cfg, prm, self.pose, self.obs_rgb,
+                                     self.obs_d, n_iter, self.cap, lh, ph, self.ws,
+                                     adam_state=self.adam)
+
+            saved = self.pose.clone()
+            self._graphs[key] = capture(frame)
+            self.pose.copy_(saved)
+            self.hist[key] = (lh, ph)
+        return self._graphs[key]
+
+    def status(self) -> int:
+        return int(gs2d.gs2d_track_status(self.ws).item())
+
+    def iterations_run(self) -> int:
+        """AdamW steps of the last frame: the iterations before the stop."""
+        return int(self.adam[12].item())
+
+
+def compare_frames(loops: LoopGraphs, propose, proposal_pose, frames, n_iter: int):
+    """Plain loop vs proposal + loop, frame by frame.  ``frames``: (gt, load)
+    with load(target) writing the frame's observation and its usual start
+    pose into the proposer's and the loop's buffers (target 'loop' or
+    'proposal'); ``propose``: the proposal's captured graph, whose kept pose
+    ends in ``proposal_pose`` [12].
+    Per frame:
+      * untimed passes find the iteration where the pose first comes within
+        1 cm / 0.5 degrees of gt, from the usual start and from the proposal;
+      * timed end to end (CUDA events around everything the frame runs):
+        the loop cut at that iteration, and the proposal + acceptance + the
+        loop cut at its iteration (frames already within the threshold after
+        the proposal run no loop);
+      * timed under the stop rule (|tau| < STOP_TOL or STOP_ITERS
+        iterations): both arms, with the iterations run and the error at
+        the stop.
+    The GT-based cut needs the untimed pass; the stop-rule frames are what a
+    tracker without ground truth runs."""
+    g_full = loops.graph(n_iter)
+    g_stop = loops.graph(STOP_ITERS, STOP_TOL)
+    ph_full = loops.hist[(n_iter, 0.0)][1]
+    res = {k: [] for k in ("plain_it", "learned_it", "prop", "accepted", "plain_ms", "learned_ms",
+                           "prop_ms", "iter_ms", "stop_plain_ms", "stop_learned_ms",
+                           "stop_plain_it", "stop_learned_it", "stop_plain_err",
+                           "stop_learned_err")}
+    for gt, load, accepted in frames:
+        # untimed: iterations to the threshold from both starts
+        load("loop")
+        res["iter_ms"].append(timed_ms(g_full.replay) / n_iter)
+        if loops.status() not in (0, gs2d.CONVERGED):
+            raise gs2d.Gs2dError("tracking status")
+        k_plain = first_below(ph_full.cpu().numpy(), gt)
+        load("proposal")
+        res["prop_ms"].append(timed_ms(propose.replay))
+        res["accepted"].append(int(accepted().item()))
+        start = proposal_pose.clone()
+        e = pose_error(start.cpu().numpy(), gt)
+        res["prop"].append(e)
+        if e[0] < 0.01 and e[1] < 0.5:
+            k_learned = 0
+        else:
+            loops.pose.copy_(start)
+            g_full.replay()
+            k_learned = first_below(ph_full.cpu().numpy(), gt)
+        res["plain_it"].append(k_plain)
+        res["learned_it"].append(k_learned)
+        # timed end to end: the loop cut where it reaches the threshold
+        kp = n_iter if k_plain is None else k_plain
+        kl = n_iter if k_learned is None else k_learned
+        gp = loops.graph(kp) if kp > 0 else None
+        gl = loops.graph(kl) if kl > 0 else None
+        load("loop")
+        res["plain_ms"].append(timed_ms(gp.replay) if gp is not None else 0.0)
+        load("proposal")
+
+        def learned():
+            propose.replay()
+            if gl is not None:
+                loops.pose.copy_(proposal_pose)
+                gl.replay()
+
+        res["learned_ms"].append(timed_ms(learned))
+        # timed under the stop rule
+        load("loop")
+        res["stop_plain_ms"].append(timed_ms(g_stop.replay))
+        res["stop_plain_it"].append(loops.iterations_run())
+        res["stop_plain_err"].append(pose_error(loops.pose.cpu().numpy(), gt))
+        load("proposal")
+
+        def learned_stop():
+            propose.replay()
+            loops.pose.copy_(proposal_pose)
+            g_stop.replay()
+
+        res["stop_learned_ms"].append(timed_ms(learned_stop))
+        res["stop_learned_it"].append(loops.iterations_run())
+        res["stop_learned_err"].append(pose_error(loops.pose.cpu().numpy(), gt))
+        if loops.status() not in (0, gs2d.CONVERGED):
+            raise gs2d.Gs2dError("tracking status")
+    return res
+
+
+def summarize_frames(res, n_iter: int) -> dict:
+    """Medians of compare_frames: the timed frames are the primary numbers;
+    the composite (median proposal time + iterations x median iteration
+    time) is kept beside them."""
+    cap_it = lambda v: n_iter if v is None else v
+    ms_iter = float(np.median(res["iter_ms"]))
+    ms_prop = float(np.median(res["prop_ms"]))
+    plain_c = np.array([cap_it(v) * ms_iter for v in res["plain_it"]])
+    learned_c = np.array([ms_prop + cap_it(v) * ms_iter for v in res["learned_it"]])
+    pm, lm = np.array(res["plain_ms"]), np.array(res["learned_ms"])
+    pp = np.array(res["prop"])
+    sp, sl = np.array(res["stop_plain_err"]), np.array(res["stop_learned_err"])
+    reach = lambda e: int(np.sum((e[:, 0] < 0.01) & (e[:, 1] < 0.5)))
+    return {
+        "frames": len(pm),
+        "ms_per_iter": ms_iter,
+        "proposal_ms": ms_prop,
+        "timing": "each frame timed end to end on the device (CUDA events around the proposal "
+                  "graph, the acceptance and the loop graph cut at the iteration an untimed pass "
+                  "found within 1 cm / 0.5 deg of ground truth)",
+        "plain": {"ms_to_1cm_0.5deg_median": float(np.median(pm)), "ms_mean": float(np.mean(pm)),
+                  "iters_median": float(np.median([cap_it(v) for v in res["plain_it"]])),
+                  "reached": int(sum(v is not None for v in res["plain_it"]))},
+        "learned": {"ms_to_1cm_0.5deg_median": float(np.median(lm)), "ms_mean": float(np.mean(lm)),
+                    "iters_median": float(np.median([cap_it(v) for v in res["learned_it"]])),
+                    "reached": int(sum(v is not None for v in res["learned_it"])),
+                    "accepted_frac": float(np.mean(res["accepted"]))},
+        "speedup_median": float(np.median(pm) / max(np.median(lm), 1e-9)),
+        "composite": {"plain_ms_median": float(np.median(plain_c)),
+                      "learned_ms_median": float(np.median(learned_c)),
+                      "note": "proposal median + iterations x median iteration time"},
+        "stop_rule": {"n_iter": STOP_ITERS, "stop_tol": STOP_TOL,
+                      "plain": {"ms_median": float(np.median(res["stop_plain_ms"])),
+                                "iters_median": float(np.median(res["stop_plain_it"])),
+                                "err_cm_median": float(np.median(sp[:, 0]) * 100),
+                                "err_deg_median": float(np.median(sp[:, 1])),
+                                "within_1cm_0.5deg": reach(sp)},
+                      "learned": {"ms_median": float(np.median(res["stop_learned_ms"])),
+                                  "iters_median": float(np.median(res["stop_learned_it"])),
+                                  "err_cm_median": float(np.median(sl[:, 0]) * 100),
+                                  "err_deg_median": float(np.median(sl[:, 1])),
+                                  "within_1cm_0.5deg": reach(sl)}},
+        "proposal_err_median_cm_deg": [float(np.median(pp[:, 0]) * 100), float(np.median(pp[:, 1]))],
+    }
+
+
 def evaluate(scene, params, n_frames: int, seed: int, n_iter: int = 100, device="cuda",
              passes: int = 1):
-    """Plain loop vs proposal + loop on held-out frames of one room: per frame
-    the iterations to 1 cm / 0.5 degrees (pose history of the fused tracking
-    step), the proposal's own error, and the GPU time of one proposal and of
-    one tracking iteration (CUDA graph replays)."""
+    """Plain loop vs proposal + loop on held-out frames of one room
+    (compare_frames): per frame the iterations and the end-to-end device
+    time to 1 cm / 0.5 degrees, the frames under the stop rule, and the
+    proposal's own error."""
     ds = gs2d.DeviceSurfels(scene)
     vr = ViewRenderer(ds)
     gen = torch.Generator(device=device)
@@ -310,78 +506,32 @@ def evaluate(scene, params, n_frames: int, seed: int, n_iter: int = 100, device=
     pr.obs_rgb.copy_(obs_rgb[0])
     pr.obs_d.copy_(obs_d[0])
     pg = capture(pr.run)
-    # the plain loop, one frame (n_iter iterations) per replay
-    ccam, cfg = gs2d.camera(CAM), gs2d.default_config()
-    prm = gs2d.default_track_params(stop_tol=0.0)
-    tws = torch.empty(gs2d.gs2d_track_workspace(ds.n, cap, ccam, cfg), dtype=torch.uint8,
-                      device=device)
-    tpose = torch.empty(12, device=device)
+    # the plain loop, one frame per replay
     t_rgb = torch.empty(120, 160, 3, device=device)
     t_d = torch.empty(120, 160, device=device)
-    lh = torch.zeros(n_iter, device=device)
-    ph = torch.zeros(n_iter, 12, device=device)
-    tpose.copy_(pr.pose[0])
-    t_rgb.copy_(obs_rgb[0])
-    t_d.copy_(obs_d[0])
-
-    def track():
-        gs2d.gs2d_track_step(ds, ccam, cfg, prm, tpose, t_rgb, t_d, n_iter, cap, lh, ph, tws)
-
-    tg = capture(track)
+    loops = LoopGraphs(ds, CAM, cap, t_rgb, t_d, device)
     init_t = poses_tensor(inits, device)
-    res = dict(start=[], prop=[], plain_it=[], learned_it=[], accepted=[])
-    prop_ms, iter_ms = [], []
-    for f in range(n_frames):
-        gt = gts[f]
-        res["start"].append(pose_error(init_t[f].cpu().numpy(), gt))
-        # plain loop from the usual start
-        tpose.copy_(init_t[f])
-        t_rgb.copy_(obs_rgb[f])
-        t_d.copy_(obs_d[f])
-        iter_ms += [m / n_iter for m in timed_replays(tg, 1)]
-        if int(gs2d.gs2d_track_status(tws).item()) not in (0, gs2d.CONVERGED):
-            raise gs2d.Gs2dError("tracking status")
-        res["plain_it"].append(first_below(ph.cpu().numpy(), gt))
-        # proposal, then the same loop from the chosen pose
-        pr.pose.copy_(init_t[f:f + 1])
-        pr.obs_rgb.copy_(obs_rgb[f])
-        pr.obs_d.copy_(obs_d[f])
-        prop_ms += timed_replays(pg, 1)
-        if pr.status() != 0:
-            raise gs2d.Gs2dError(f"proposal render status {pr.status()}")
-        res["accepted"].append(int(pr.accepted.item()))
-        start = pr.pose[0].clone()
-        res["prop"].append(pose_error(start.cpu().numpy(), gt))
-        if pose_error(start.cpu().numpy(), gt)[0] < 0.01 and pose_error(start.cpu().numpy(), gt)[1] < 0.5:
-            res["learned_it"].append(0)
-            continue
-        tpose.copy_(start)
-        timed_replays(tg, 1)
-        res["learned_it"].append(first_below(ph.cpu().numpy(), gt))
-    ms_iter = float(np.median(iter_ms))
-    ms_prop = float(np.median(prop_ms))
-    cap_it = lambda v: n_iter if v is None else v
-    plain_ms = np.array([cap_it(v) * ms_iter for v in res["plain_it"]])
-    learned_ms = np.array([ms_prop + cap_it(v) * ms_iter for v in res["learned_it"]])
-    st = np.array(res["start"])
-    pp = np.array(res["prop"])
-    return {
-        "frames": n_frames,
-        "ms_per_iter": ms_iter,
-        "proposal_ms": ms_prop,
-        "plain": {"ms_to_1cm_0.5deg_median": float(np.median(plain_ms)),
-                  "ms_mean": float(np.mean(plain_ms)),
-                  "iters_median": float(np.median([cap_it(v) for v in res["plain_it"]])),
-                  "reached": int(sum(v is not None for v in res["plain_it"]))},
-        "learned": {"ms_to_1cm_0.5deg_median": float(np.median(learned_ms)),
-                    "ms_mean": float(np.mean(learned_ms)),
-                    "iters_median": float(np.median([cap_it(v) for v in res["learned_it"]])),
-                    "reached": int(sum(v is not None for v in res["learned_it"])),
-                    "accepted_frac": float(np.mean(res["accepted"]))},
-        "speedup_median": float(np.median(plain_ms) / max(np.median(learned_ms), 1e-9)),
-        "start_err_median_cm_deg": [float(np.median(st[:, 0]) * 100), float(np.median(st[:, 1]))],
-        "proposal_err_median_cm_deg": [float(np.median(pp[:, 0]) * 100), float(np.median(pp[:, 1]))],
-    }
+    st = np.array([pose_error(init_t[f].cpu().numpy(), gts[f]) for f in range(n_frames)])
+
+    def frame(f):
+        def load(target):
+            t_rgb.copy_(obs_rgb[f])
+            t_d.copy_(obs_d[f])
+            pr.obs_rgb.copy_(obs_rgb[f])
+            pr.obs_d.copy_(obs_d[f])
+            if target == "loop":
+                loops.pose.copy_(init_t[f])
+            else:
+                pr.pose.copy_(init_t[f:f + 1])
+        return gts[f], load, lambda: pr.accepted
+
+    res = compare_frames(loops, pg, pr.pose[0], (frame(f) for f in range(n_frames)), n_iter)
+    if pr.status() != 0:
+        raise gs2d.Gs2dError(f"proposal render status {pr.status()}")
+    out = summarize_frames(res, n_iter)
+    out["start_err_median_cm_deg"] = [float(np.median(st[:, 0]) * 100), float(np.median(st[:, 1]))]
+    out["proposal_passes"] = passes
+    return out
 
 
 def low_res_camera(cam, factor: int):
@@ -399,8 +549,7 @@ def evaluate_full_res(surf: gs2d.DeviceSurfels, params, cam, frames, passes: int
     runs at that resolution, and the full-resolution plain loop refines the
     kept pose; against the plain loop from the usual start.  ``frames``:
     dicts with gt (Pose), start_t [12], obs_rgb [H, W, 3], obs_depth [H, W]
-    on the device.  Reports iterations and GPU time (CUDA graph replays) to
-    1 cm / 0.5 degrees."""
+    on the device.  Reports what compare_frames measures."""
     factor = cam.width // 160
     lo = low_res_camera(cam, factor)
     cap = 8 * surf.n
@@ -416,61 +565,22 @@ def evaluate_full_res(surf: gs2d.DeviceSurfels, params, cam, frames, passes: int
     obs_rgb.copy_(frames[0]["obs_rgb"])
     obs_d.copy_(frames[0]["obs_depth"])
     pg = capture(propose)
-    ccam, cfg = gs2d.camera(cam), gs2d.default_config()
-    prm = gs2d.default_track_params(stop_tol=0.0)
-    tws = torch.empty(gs2d.gs2d_track_workspace(surf.n, cap, ccam, cfg), dtype=torch.uint8,
-                      device=device)
-    tpose = torch.empty(12, device=device)
-    lh = torch.zeros(n_iter, device=device)
-    ph = torch.zeros(n_iter, 12, device=device)
-    tpose.copy_(frames[0]["start_t"])
+    loops = LoopGraphs(surf, cam, cap, obs_rgb, obs_d, device)
 
-    def track():
-        gs2d.gs2d_track_step(surf, ccam, cfg, prm, tpose, obs_rgb, obs_d, n_iter, cap, lh, ph, tws)
+    def frame(fr):
+        def load(target):
+            obs_rgb.copy_(fr["obs_rgb"])
+            obs_d.copy_(fr["obs_depth"])
+            if target == "loop":
+                loops.pose.copy_(fr["start_t"])
+            else:
+                pr.pose.copy_(fr["start_t"][None])
+        return fr["gt"], load, lambda: pr.accepted
 
-    tg = capture(track)
-    res = dict(plain_it=[], learned_it=[], prop=[], accepted=[])
-    prop_ms, iter_ms = [], []
-    for fr in frames:
-        gt = fr["gt"]
-        obs_rgb.copy_(fr["obs_rgb"])
-        obs_d.copy_(fr["obs_depth"])
-        tpose.copy_(fr["start_t"])
-        iter_ms += [m / n_iter for m in timed_replays(tg, 1)]
-        if int(gs2d.gs2d_track_status(tws).item()) not in (0, gs2d.CONVERGED):
-            raise gs2d.Gs2dError("tracking status")
-        res["plain_it"].append(first_below(ph.cpu().numpy(), gt))
-        pr.pose.copy_(fr["start_t"][None])
-        prop_ms += timed_replays(pg, 1)
-        if pr.status() != 0:
-            raise gs2d.Gs2dError(f"proposal render status {pr.status()}")
-        res["accepted"].append(int(pr.accepted.item()))
-        start = pr.pose[0].clone()
-        e = pose_error(start.cpu().numpy(), gt)
-        res["prop"].append(e)
-        if e[0] < 0.01 and e[1] < 0.5:
-            res["learned_it"].append(0)
-            continue
-        tpose.copy_(start)
-        timed_replays(tg, 1)
-        res["learned_it"].append(first_below(ph.cpu().numpy(), gt))
-    ms_iter = float(np.median(iter_ms))
-    ms_prop = float(np.median(prop_ms))
-    cap_it = lambda v: n_iter if v is None else v
-    plain_ms = np.array([cap_it(v) * ms_iter for v in res["plain_it"]])
-    learned_ms = np.array([ms_prop + cap_it(v) * ms_iter for v in res["learned_it"]])
-    pp = np.array(res["prop"])
-    return {
-        "frames": len(frames), "ms_per_iter": ms_iter, "proposal_ms": ms_prop,
-        "proposal_passes": passes, "network_camera": [lo.fx, lo.fy, lo.cx, lo.cy, lo.width,
-                                                      lo.height],
-        "plain": {"ms_to_1cm_0.5deg_median": float(np.median(plain_ms)),
-                  "iters_median": float(np.median([cap_it(v) for v in res["plain_it"]])),
-                  "reached": int(sum(v is not None for v in res["plain_it"]))},
-        "learned": {"ms_to_1cm_0.5deg_median": float(np.median(learned_ms)),
-                    "iters_median": float(np.median([cap_it(v) for v in res["learned_it"]])),
-                    "reached": int(sum(v is not None for v in res["learned_it"])),
-                    "accepted_frac": float(np.mean(res["accepted"]))},
-        "speedup_median": float(np.median(plain_ms) / max(np.median(learned_ms), 1e-9)),
-        "proposal_err_median_cm_deg": [float(np.median(pp[:, 0]) * 100), float(np.median(pp[:, 1]))],
-    }
+    res = compare_frames(loops, pg, pr.pose[0], (frame(fr) for fr in frames), n_iter)
+    if pr.status() != 0:
+        raise gs2d.Gs2dError(f"proposal render status {pr.status()}")
+    out = summarize_frames(res, n_iter)
+    out["proposal_passes"] = passes
+    out["network_camera"] = [lo.fx, lo.fy, lo.cx, lo.cy, lo.width, lo.height]
+    return out
