@@ -447,6 +447,10 @@ const int32_t* gs2d_track_tile_order(void* workspace, int n, size_t capacity,
  * recorded so far.  Not thread safe. */
 int gs2d_profile_track_kernel(void* const* start_events, void* const* stop_events, int n);
 int gs2d_profile_track_kernel_count(void);
+/* Bracket only the launches of iterations it with it % every == 0 of each
+ * gs2d_track_step call (default 1: every launch), so a timed frame carries
+ * fewer event records; every < 1 returns GS2D_ERR_INVALID_ARG. */
+int gs2d_profile_track_kernel_every(int every);
 
 #ifdef __cplusplus
 }

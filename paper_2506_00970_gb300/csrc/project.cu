@@ -28,6 +28,7 @@
 
 #include "gs2d_common.cuh"
 #include "tile_scan.cuh"
+#include "tile_walk.cuh"
 #include "gs2d_internal.h"
 
 namespace gs2d {
@@ -245,6 +246,7 @@ __global__ void __launch_bounds__(256) project_fused_kernel(
   __shared__ uint32_t s_carry;
   __shared__ bool s_last;
   __shared__ bool s_emit[256];  // does the chunk's surfel touch a tile?
+  __shared__ WalkScratch s_walk[8];
   if (gate && *gate) return;
   if (threadIdx.x < 12) sp[threadIdx.x] = pose[threadIdx.x];
   const bool local = fz.n_tiles <= kHistTiles;
@@ -254,25 +256,24 @@ __global__ void __launch_bounds__(256) project_fused_kernel(
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const int i = base + (int)threadIdx.x;
     s_emit[threadIdx.x] = false;
+    int k = 0, tx0 = 1, ty0 = 1, tx1 = 0;
     if (i < n) {
       project_one(i, mu, quat, scale, opacity, rgb, sp, cam, cfg, s_out + threadIdx.x * 9,
                   tiles_out + i);
-      {
-        // tile counts of this surfel's rectangle
-        const float4 rc = s_out[threadIdx.x * 9 + 7];
-        const uint32_t r01 = __float_as_uint(rc.x), r23 = __float_as_uint(rc.y);
-        const int tx0 = (int)(r01 & 0xFFFF), ty0 = (int)(r01 >> 16);
-        const int tx1 = (int)(r23 & 0xFFFF), ty1 = (int)(r23 >> 16);
-        if (tx0 <= tx1 && ty0 <= ty1) {
-          s_emit[threadIdx.x] = true;
-          const int rw = tx1 - tx0 + 1, k = rw * (ty1 - ty0 + 1);
-          for (int j = 0; j < k; ++j) {
-            const int t = min((ty0 + j / rw) * fz.tiles_x + tx0 + j % rw, fz.n_tiles - 1);
-            atomicAdd(local ? s_hist + t : fz.tile_count + t, 1u);
-          }
-        }
+      const float4 rc = s_out[threadIdx.x * 9 + 7];
+      const uint32_t r01 = __float_as_uint(rc.x), r23 = __float_as_uint(rc.y);
+      tx0 = (int)(r01 & 0xFFFF);
+      ty0 = (int)(r01 >> 16);
+      tx1 = (int)(r23 & 0xFFFF);
+      const int ty1 = (int)(r23 >> 16);
+      if (tx0 <= tx1 && ty0 <= ty1) {
+        s_emit[threadIdx.x] = true;
+        k = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
       }
     }
+    // tile counts of the warp's rectangles, walked cooperatively
+    warp_tile_walk(k, tx0, ty0, tx1, fz.tiles_x, fz.n_tiles, s_walk[threadIdx.x >> 5],
+                   [&](int, int t) { atomicAdd(local ? s_hist + t : fz.tile_count + t, 1u); });
     __syncthreads();
     const int valid = min((int)blockDim.x, n - base);
     float4* dst = proj + (size_t)base * (kProjFloats / 4);

@@ -246,8 +246,9 @@ __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<P, kG>()) tra
       loss_part[tile] = t;
     }
   }
+  // a list of at most one batch is still staged with its hit lists
   bwd_tile_pose<false, P, kG>(proj, vals, start, end, xt, yt, tile_x0, tile_y0, tp, inside, rx, ry,
-                              cam, cfg, pg, sm, hl, pr);
+                              cam, cfg, pg, sm, hl, pr, end - start <= kTileThreads);
   block_sum6(pr, s_pose, pose_part + (size_t)tile * 6);
   // the last block to finish reduces every tile's partials and updates the pose
   __threadfence();

@@ -30,6 +30,7 @@
 #include "gs2d_common.cuh"
 #include "gs2d_internal.h"
 #include "tile_scan.cuh"
+#include "tile_walk.cuh"
 
 namespace gs2d {
 
@@ -107,21 +108,21 @@ __global__ void __launch_bounds__(kScanThreads) count_kernel(
     const float4* __restrict__ proj, const int32_t* __restrict__ tiles, int n, int tiles_x,
     int n_tiles, uint32_t* __restrict__ tile_count, const int32_t* __restrict__ gate) {
   extern __shared__ uint32_t s_hist[];
+  __shared__ WalkScratch s_walk[kScanThreads / 32];
   if (*gate) return;
   const bool local = n_tiles <= kSmemTiles;
   if (local)
     for (int t = threadIdx.x; t < n_tiles; t += kScanThreads) s_hist[t] = 0u;
   __syncthreads();
   const int stride = gridDim.x * kScanThreads;
-  for (int i = blockIdx.x * kScanThreads + threadIdx.x; i < n; i += stride) {
-    const int k = tiles[i];
-    if (k <= 0) continue;
-    const Rect r = load_rect(proj, (uint32_t)i);
-    const int rw = max(r.tx1 - r.tx0 + 1, 1);
-    for (int j = 0; j < k; ++j) {
-      const int t = min((r.ty0 + j / rw) * tiles_x + r.tx0 + j % rw, n_tiles - 1);
-      atomicAdd(local ? s_hist + t : tile_count + t, 1u);
-    }
+  // block-uniform trip count: every lane takes part in each warp walk
+  for (int base = blockIdx.x * kScanThreads; base < n; base += stride) {
+    const int i = base + (int)threadIdx.x;
+    const int k = i < n ? max(tiles[i], 0) : 0;
+    Rect r{1, 1, 0, 0};
+    if (k > 0) r = load_rect(proj, (uint32_t)i);
+    warp_tile_walk(k, r.tx0, r.ty0, r.tx1, tiles_x, n_tiles, s_walk[threadIdx.x >> 5],
+                   [&](int, int t) { atomicAdd(local ? s_hist + t : tile_count + t, 1u); });
   }
   if (!local) return;
   __syncthreads();
@@ -236,13 +237,16 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
 // 3. Scatter of the (depth bits << 32 | id) keys into the tile segments.
 // A block counts its own pairs per tile in shared memory, claims one run of
 // slots per tile with a single global atomic, and hands the slots out with
-// shared-memory atomics.
+// shared-memory atomics; both passes walk the warp's pairs cooperatively
+// (warp_tile_walk).
 __global__ void __launch_bounds__(256) scatter_kernel(
     const float4* __restrict__ proj, const int32_t* __restrict__ tiles, int n, int tiles_x,
     int n_tiles, const int32_t* __restrict__ ranges, uint32_t* __restrict__ cursor,
     unsigned long long* __restrict__ seg_keys, long long capacity,
     const int32_t* __restrict__ gate) {
   extern __shared__ uint32_t s_cnt[];  // [n_tiles] counts, then [n_tiles] bases
+  __shared__ WalkScratch s_walk[8];
+  __shared__ unsigned long long s_key[256];
   if (*gate) return;
   const bool local = n_tiles <= kSmemTiles;
   uint32_t* s_base = s_cnt + (local ? n_tiles : 0);
@@ -260,22 +264,28 @@ __global__ void __launch_bounds__(256) scatter_kernel(
     const uint32_t db = __float_as_uint(proj[(size_t)i * (kProjFloats / 4) + 6].z);
     key = ((unsigned long long)db << 32) | (uint32_t)i;
   }
+  (void)rw;
+  s_key[threadIdx.x] = key;
+  WalkScratch& ws = s_walk[threadIdx.x >> 5];
+  const unsigned long long* wkey = s_key + (threadIdx.x & ~31);
+  const int kk = max(k, 0);
   if (local) {
-    for (int j = 0; j < k; ++j)
-      atomicAdd(s_cnt + min((r.ty0 + j / rw) * tiles_x + r.tx0 + j % rw, n_tiles - 1), 1u);
+    warp_tile_walk(kk, r.tx0, r.ty0, r.tx1, tiles_x, n_tiles, ws,
+                   [&](int, int t) { atomicAdd(s_cnt + t, 1u); });
     __syncthreads();
     for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
       const uint32_t c = s_cnt[t];
       s_base[t] = c ? (uint32_t)ranges[2 * t] + atomicAdd(cursor + t, c) : 0u;
     }
     __syncthreads();
+  } else {
+    __syncwarp();
   }
-  for (int j = 0; j < k; ++j) {
-    const int t = min((r.ty0 + j / rw) * tiles_x + r.tx0 + j % rw, n_tiles - 1);
+  warp_tile_walk(kk, r.tx0, r.ty0, r.tx1, tiles_x, n_tiles, ws, [&](int owner, int t) {
     const long long pos = local ? (long long)atomicAdd(s_base + t, 1u)
                                 : (long long)ranges[2 * t] + atomicAdd(cursor + t, 1u);
-    if (pos < min((long long)ranges[2 * t + 1], capacity)) seg_keys[pos] = key;
-  }
+    if (pos < min((long long)ranges[2 * t + 1], capacity)) seg_keys[pos] = wkey[owner];
+  });
 }
 
 // 4. Per-tile sort of the segment and the final outputs.  The flip-form

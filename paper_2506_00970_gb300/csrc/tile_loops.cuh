@@ -115,8 +115,8 @@ __device__ __forceinline__ uint32_t footprint_mask(float bi, float bj, int tile_
 __device__ __forceinline__ int warp_hit_list(const uint32_t* s_mask, uint8_t* my_list, int cnt,
                                              int warp, int lane) {
   int n = 0;
-#pragma unroll
-  for (int c = 0; c < kTileThreads; c += 32) {
+#pragma unroll 2
+  for (int c = 0; c < cnt; c += 32) {
     const int j = c + lane;
     const bool hit = j < cnt && ((s_mask[j] >> warp) & 1u);
     const uint32_t b = __ballot_sync(0xffffffffu, hit);
@@ -189,6 +189,7 @@ struct FwdState {
 struct HitLists {
   uint32_t mask[kTileThreads];
   uint8_t list[kTileThreads / 32][kTileThreads];
+  int count[kTileThreads / 32];  // each warp's hit count of the last staged batch
 };
 
 // kG > 1 (one pixel per thread, no counting): the warp's hits are taken kG at
@@ -239,6 +240,7 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ proj,
     __syncthreads();
     const int cnt_b = min(kTileThreads, end - b);
     const int nh = warp_hit_list(hl.mask, hl.list[warp], cnt_b, warp, lane);
+    if (lane == 0) hl.count[warp] = nh;
     if (P == 1 && kG > 1 && !kCount && !all_done) {
       FwdState& q = st[0];
       for (int h0 = 0; h0 < nh && !all_done; h0 += kG) {
@@ -612,7 +614,10 @@ __device__ __forceinline__ void pose_pair(const Eval& e, const float4 r2, const 
 // image's term t_nc x w gN per pair (tracking has no normal gradient).
 // kG > 1 (one pixel per thread): hits are taken kG at a time, their pairs
 // evaluated independently and then replayed in back-to-front order (as in
-// fwd_tile).
+// fwd_tile).  staged: the tile's whole list (at most one batch) is still
+// staged in sm.rec with the per-warp hit lists of fwd_tile<kBwdVec4> in hl
+// (the fused tracking kernel), so neither is rebuilt; entries past a
+// pixel's last blended one are skipped per pixel as always.
 template <bool kNormal, int P, int kG = 1>
 __device__ __forceinline__ void bwd_tile_pose(const float4* __restrict__ proj,
                                               const uint32_t* __restrict__ vals, int start, int end,
@@ -620,7 +625,8 @@ __device__ __forceinline__ void bwd_tile_pose(const float4* __restrict__ proj,
                                               const TilePix<P>& tp, const bool (&inside)[P],
                                               float rx, float ry, const gs2d_camera& cam,
                                               const gs2d_config& cfg, const PixGrad (&pg)[P],
-                                              BwdSmem<false>& sm, HitLists& hl, float (&pr)[6]) {
+                                              BwdSmem<false>& sm, HitLists& hl, float (&pr)[6],
+                                              bool staged = false) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float fxfy = cam.fx * cam.fy;
   if (threadIdx.x == 0) sm.max_nl = 0u;
@@ -656,14 +662,20 @@ __device__ __forceinline__ void bwd_tile_pose(const float4* __restrict__ proj,
   for (int bend = hi; bend > start; bend -= kTileThreads) {
     const int bstart = max(start, bend - kTileThreads);
     const int cnt = bend - bstart;
-    __syncthreads();
-    if ((int)threadIdx.x < cnt) {
-      stage_record<kBwdVec4>(proj, vals[bstart + (int)threadIdx.x], xt, yt, sm.rec);
-      const float4 rf = sm.rec[threadIdx.x][6];
-      hl.mask[threadIdx.x] = footprint_mask<P>(rf.z, rf.w, tile_x0, tile_y0, cfg.tile_w);
+    int nh;
+    if (staged) {
+      // one batch: bstart == start, records and hit lists as fwd_tile left them
+      nh = hl.count[warp];
+    } else {
+      __syncthreads();
+      if ((int)threadIdx.x < cnt) {
+        stage_record<kBwdVec4>(proj, vals[bstart + (int)threadIdx.x], xt, yt, sm.rec);
+        const float4 rf = sm.rec[threadIdx.x][6];
+        hl.mask[threadIdx.x] = footprint_mask<P>(rf.z, rf.w, tile_x0, tile_y0, cfg.tile_w);
+      }
+      __syncthreads();
+      nh = warp_hit_list(hl.mask, hl.list[warp], cnt, warp, lane);
     }
-    __syncthreads();
-    const int nh = warp_hit_list(hl.mask, hl.list[warp], cnt, warp, lane);
     if (!any_inside) continue;
     if (P == 1 && kG > 1) {
       for (int h0 = nh - 1; h0 >= 0; h0 -= kG) {

@@ -24,6 +24,7 @@ struct KernelTimer {
   cudaEvent_t* stop = nullptr;
   int capacity = 0;
   int used = 0;
+  int every = 1;  // bracket the launches of iterations it % every == 0
 };
 KernelTimer g_timer;
 
@@ -111,6 +112,12 @@ int gs2d_profile_track_kernel(void* const* start_events, void* const* stop_event
 
 int gs2d_profile_track_kernel_count(void) { return g_timer.used; }
 
+int gs2d_profile_track_kernel_every(int every) {
+  if (every < 1) return GS2D_ERR_INVALID_ARG;
+  g_timer.every = every;
+  return GS2D_OK;
+}
+
 int32_t* gs2d_track_status(void* workspace) {
   return workspace ? reinterpret_cast<int32_t*>(workspace) : nullptr;
 }
@@ -170,7 +177,7 @@ int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_co
     r = bin_sort_launch(w.proj, w.tiles, s->n, cam, cfg, w.sort_ws, w.sort_bytes, nullptr, &bins,
                         false, st, kSortPreZeroed | kSortLongInBlock | kSortPreScanned);
     if (r) return r;
-    const bool timed = g_timer.used < g_timer.capacity;
+    const bool timed = g_timer.used < g_timer.capacity && it % g_timer.every == 0;
     if (timed) GS2D_CUDA_TRY(record_timing_event(g_timer.start[g_timer.used], st));
     TrackStep ts{pose, adam, loss_hist, pose_hist, grad_hist, it, w.counter, zero_begin,
                  zero_words, w.order};

@@ -104,6 +104,7 @@ EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_stri
            "gs2d_track_status", "gs2d_track_tile_order", "gs2d_render_count", "gs2d_bin_sort_static",
            "gs2d_set_grouped_tiles", "gs2d_set_lookback_wait",
            "gs2d_profile_track_kernel", "gs2d_profile_track_kernel_count",
+           "gs2d_profile_track_kernel_every",
            "gs2d_project_batch", "gs2d_bin_sort_batch_workspace", "gs2d_bin_sort_batch",
            "gs2d_render_batch_workspace", "gs2d_render_fwd_batch", "gs2d_render_bwd_batch",
            "gs2d_net_param_count", "gs2d_net_layout", "gs2d_net_workspace",
@@ -163,6 +164,7 @@ def lib():
         L.gs2d_track_step.argtypes = [vp] * 8 + [ip, sz, vp, vp, vp, vp, sz, vp, vp]
         L.gs2d_profile_track_kernel.argtypes = [vp, vp, ip]
         L.gs2d_profile_track_kernel_count.restype = ip
+        L.gs2d_profile_track_kernel_every.argtypes = [ip]
         L.gs2d_project_batch.argtypes = [vp, vp, ip, vp]
         L.gs2d_bin_sort_batch_workspace.restype = sz
         L.gs2d_bin_sort_batch_workspace.argtypes = [vp, ip, ip]
@@ -596,6 +598,11 @@ def gs2d_profile_track_kernel(events_start, events_stop):
 
 def gs2d_profile_track_kernel_count() -> int:
     return int(lib().gs2d_profile_track_kernel_count())
+
+
+def gs2d_profile_track_kernel_every(every: int):
+    """Bracket only the launches of iterations it % every == 0."""
+    check(lib().gs2d_profile_track_kernel_every(int(every)), "gs2d_profile_track_kernel_every")
 
 
 _PROFILE_KEEP = []

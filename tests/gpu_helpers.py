@@ -52,7 +52,7 @@ def grad_rows_ok(og):
 FLAGGED_TOL = 1e-2
 
 
-def assert_grads_close(a, b, name, rows_ok=None, tol=TOL_GRAD, min_rows=0.9):
+def assert_grads_close(a, b, name, rows_ok=None, tol=TOL_GRAD, min_rows=0.9, floor=GRAD_FLOOR):
     """Gradient parity at the contract's 1e-3 relative.
     Per element on rows_ok (all rows if None): |a - b| <= tol |b| +
     GRAD_FLOOR max|b|, no exceptions.  The floor, 2^-17 of the array's
@@ -62,19 +62,21 @@ def assert_grads_close(a, b, name, rows_ok=None, tol=TOL_GRAD, min_rows=0.9):
     nearly edge-on): |a - b| <= FLAGGED_TOL max|b| -- a threshold decision
     taken otherwise moves a surfel's gradient by about one pixel's term.
     min_rows: the share of surfels with a non-zero gradient row that must be
-    held to the per-element bound (the exemptions stay few)."""
+    held to the per-element bound (the exemptions stay few).  floor: the
+    floor's share of the scale (a sum over V views takes V times it: every
+    view's sum rounds at its own scale)."""
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     scale = max(np.abs(b).max(), 1e-300)
     err = np.abs(a - b)
     if rows_ok is None or b.ndim == 0 or b.shape[0] != rows_ok.shape[0]:
-        bad = err > tol * np.abs(b) + GRAD_FLOOR * scale
+        bad = err > tol * np.abs(b) + floor * scale
         assert not bad.any(), (name, int(bad.sum()), (err[bad] / scale)[:4], (np.abs(b[bad]) / scale)[:4])
         return
     live = np.abs(b.reshape(len(b), -1)).max(1) > 0
     assert (rows_ok & live).sum() >= min_rows * live.sum(), (name, int((rows_ok & live).sum()), int(live.sum()))
     e, r = err[rows_ok], b[rows_ok]
-    bad = e > tol * np.abs(r) + GRAD_FLOOR * scale
+    bad = e > tol * np.abs(r) + floor * scale
     assert not bad.any(), (name, int(bad.sum()), (e[bad] / scale)[:4], (np.abs(r[bad]) / scale)[:4])
     if (~rows_ok).any():
         assert err[~rows_ok].max() <= FLAGGED_TOL * scale, (name, err[~rows_ok].max() / scale)
