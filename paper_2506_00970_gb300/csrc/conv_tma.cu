@@ -1,0 +1,348 @@
+// Forward 3x3 / stride 2 / padding 1 convolutions of the proposal network
+// (layers 2-4: NHWC bfloat16 maps 60x80x32 -> 30x40x64 -> 15x20x128 ->
+// 8x10x256) on the 5th-generation tensor cores with TMA-fed operands.
+//
+// One CTA computes an output tile of 128 pixels (TH rows x TW columns of one
+// image) for all C_out channels as a 128 x C_out x (9 C_in) product: one
+// tcgen05.mma (M = 128, N = C_out, K = 16, bf16 x bf16 -> f32 in tensor
+// memory) per tap and 16 input channels.  Its operands come straight from
+// tiled TMA loads, no gather in software:
+//  * A (im2col rows): for tap (ky, kx) and KB channels (KB = 32 or 64, a
+//    64- or 128-byte row per pixel), a box of the input map {KB channels,
+//    2 TW columns, 2 TH rows} starting at input pixel (2 ox0 + kx - 1,
+//    2 oy0 + ky - 1) with element stride 2 in both pixel dimensions loads
+//    the TH x TW input pixels that tap reads -- zero-filled where the
+//    padding lies (negative or past-the-edge coordinates).  In shared memory
+//    output pixel m's KB channels are row m, written with the TMA's 64- or
+//    128-byte swizzle: the K-major swizzled layout tcgen05 reads (8-row
+//    atoms of 8 x KB x 2 bytes), the K steps of 16 channels 32 bytes apart
+//    inside a row.
+//  * B (weights [C_out][9 C_in], K = tap x C_in + channel): a box {KB k,
+//    C_out rows} in the same swizzled K-major layout.
+// One thread issues the loads S stages ahead (mbarrier transaction counts)
+// and the MMAs; a stage is refilled once the tcgen05.commit of the MMAs that
+// read it has arrived.  Four warps read the accumulator back (tcgen05.ld)
+// and apply bias, ReLU and the bfloat16 rounding of the other kernels.
+// Every wait is bounded: past the limit the kernel records an error in
+// *err, stops issuing, waits (bounded) for what it issued and frees its
+// tensor memory.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "conv_tma.h"
+#include "gs2d_common.cuh"
+
+namespace gs2d {
+namespace net {
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int kConvThreads = 128;
+constexpr int kWaitSpins = 1 << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+  for (int i = 0; i < kWaitSpins; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{.reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;}\n"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+// Shared-memory matrix descriptor of a K-major operand with rows of SW bytes
+// (64 or 128) under the matching swizzle: start address, leading offset 16
+// bytes (unused by the swizzled K-major layouts), stride 8 x SW bytes
+// between the 8-row atoms, swizzle mode in bits 61-63 (2 = 128 B, 4 = 64 B).
+template <int SW>
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
+  constexpr uint64_t mode = SW == 128 ? 2ull : 4ull;
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | (1ull << 16) |
+         ((uint64_t)(((8 * SW) >> 4) & 0x3FFF) << 32) | (1ull << 46) | (mode << 61);
+}
+// Instruction descriptor of kind::f16: f32 accumulate, bf16 A and B, both
+// K-major, N = n, M = 128.
+__host__ __device__ constexpr uint32_t mma_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+template <int CIN, int COUT, int HI, int WI, int TW, int TH, int S>
+struct ConvTma {
+  static constexpr int HO = (HI + 1) / 2, WO = (WI + 1) / 2;
+  static constexpr int TX = (WO + TW - 1) / TW, TY = (HO + TH - 1) / TH;
+  static constexpr int KB = CIN < 64 ? CIN : 64;  // channels per box row
+  static constexpr int SW = KB * 2;               // row bytes = swizzle span
+  static constexpr int CB = CIN / KB;             // boxes (stages) per tap
+  static constexpr int KS = 9 * CB;               // stages per tile
+  static constexpr int MMAS = KB / 16;            // MMAs per stage
+  static constexpr int A_BYTES = TW * TH * SW;    // one input box
+  static constexpr int B_BYTES = COUT * SW;       // one weight box
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int SMEM = S * STAGE + 1024;   // + slack for 1024-byte alignment
+  static constexpr int TMEM_COLS = COUT;
+  static_assert(TW * TH == 128, "one 128-row MMA tile");
+  static_assert(KB == 32 || KB == 64, "64- or 128-byte swizzled rows");
+  static_assert(CIN % KB == 0 && COUT >= 32 && COUT <= 256 && (COUT & (COUT - 1)) == 0,
+                "tensor-memory columns: a power of two in [32, 256]");
+  static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "swizzle atoms stay aligned");
+  static_assert(2 * TW <= 256 && 2 * TH <= 256, "TMA box dimensions");
+};
+
+template <int CIN, int COUT, int HI, int WI, int TW, int TH, int S>
+__global__ void __launch_bounds__(kConvThreads) conv_tma_kernel(
+    const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_w,
+    const float* __restrict__ bias, bf16* __restrict__ out, int* __restrict__ err) {
+  using C = ConvTma<CIN, COUT, HI, WI, TW, TH, S>;
+  extern __shared__ unsigned char conv_raw[];
+  __shared__ __align__(8) uint64_t s_full[S], s_empty[S], s_done;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  unsigned char* stages = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(conv_raw) + 1023) & ~(uintptr_t)1023);
+  const int tile = blockIdx.x;
+  const int img = tile / (C::TX * C::TY), r = tile % (C::TX * C::TY);
+  const int oy0 = (r / C::TX) * TH, ox0 = (r % C::TX) * TW;
+  const int warp = threadIdx.x >> 5;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int i = 0; i < S; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_empty[i])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_done)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(C::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+
+  // warp 0's lane 0 issues every load and MMA; its other lanes wait for it
+  // at the __syncwarp below rather than spinning beside it
+  if (threadIdx.x == 0) {
+    // stage s: the input box of tap s / CB, channels cb .. cb + KB, and the
+    // matching weight box
+    auto load = [&](int s) {
+      const int st = s % S;
+      const uint32_t base = smem_u32(stages + st * C::STAGE);
+      const uint32_t bar = smem_u32(&s_full[st]);
+      const int tap = s / C::CB, cb = (s % C::CB) * C::KB;
+      const int ky = tap / 3, kx = tap - 3 * (tap / 3);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                   "r"(C::STAGE)
+                   : "memory");
+      tma_load_4d(base, &map_x, cb, 2 * ox0 + kx - 1, 2 * oy0 + ky - 1, img, bar);
+      tma_load_2d(base + C::A_BYTES, &map_w, tap * CIN + cb, 0, bar);
+    };
+    bool fail = false;
+    int issued = 0, consumed = 0;
+    for (; issued < S && issued < C::KS; ++issued) load(issued);
+    for (int s = 0; s < C::KS; ++s) {
+      const int st = s % S;
+      if (!bar_wait(smem_u32(&s_full[st]), (uint32_t)((s / S) & 1))) {
+        fail = true;
+        break;
+      }
+      consumed = s + 1;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = smem_u32(stages + st * C::STAGE);
+#pragma unroll
+      for (int j = 0; j < C::MMAS; ++j) {
+        // K step j of the stage: 16 channels, 32 bytes into every swizzled row
+        const uint64_t ad = sw_desc<C::SW>(base + 32 * j);
+        const uint64_t bd = sw_desc<C::SW>(base + C::A_BYTES + 32 * j);
+        const uint32_t acc = (s > 0 || j > 0) ? 1u : 0u;
+        asm volatile(
+            "{.reg .pred p; setp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(mma_idesc(COUT)), "r"(acc));
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&s_empty[st]))
+          : "memory");
+      // refill the stage the previous step read once its MMA is done (the
+      // MMA just issued keeps the tensor pipe busy meanwhile)
+      if (s >= 1 && issued < C::KS) {
+        const int ps = (s - 1) % S;
+        if (!bar_wait(smem_u32(&s_empty[ps]), (uint32_t)(((s - 1) / S) & 1))) {
+          fail = true;
+          break;
+        }
+        load(issued++);
+      }
+    }
+    // one last commit tracks every MMA issued (all, or those before a failure)
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&s_done))
+        : "memory");
+    if (fail) {
+      s_fail = 1;
+      // loads still in flight must land before the CTA exits (bounded)
+      for (int s = consumed; s < issued; ++s)
+        bar_wait(smem_u32(&s_full[s % S]), (uint32_t)((s / S) & 1));
+    }
+  }
+  if (warp == 0) __syncwarp();
+  if (!bar_wait(smem_u32(&s_done), 0u)) atomicExch(&s_fail, 1);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!*reinterpret_cast<volatile int*>(&s_fail)) {
+    // TMEM lane = row m = output pixel (oy0 + m / TW, ox0 + m % TW)
+    const int m = threadIdx.x;
+    const int oy = oy0 + m / TW, ox = ox0 + m % TW;
+    const bool ok = oy < C::HO && ox < C::WO;
+    bf16* dst = out + (((size_t)img * C::HO + oy) * C::WO + ox) * COUT;
+#pragma unroll 1
+    for (int c0 = 0; c0 < COUT; c0 += 16) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+          "%10, %11, %12, %13, %14, %15}, [%16];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (ok) {
+        uint32_t packed[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float x0 = fmaxf(__uint_as_float(v[2 * j]) + bias[c0 + 2 * j], 0.f);
+          const float x1 = fmaxf(__uint_as_float(v[2 * j + 1]) + bias[c0 + 2 * j + 1], 0.f);
+          const __nv_bfloat162 b2 = __floats2bfloat162_rn(x0, x1);
+          packed[j] = *reinterpret_cast<const uint32_t*>(&b2);
+        }
+        uint4* d = reinterpret_cast<uint4*>(dst + c0);
+        d[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        d[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+      }
+    }
+  } else if (threadIdx.x == 0 && err) {
+    atomicExch(err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(C::TMEM_COLS));
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (looked up once).
+EncodeTiledFn encode_tiled() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Input map: NHWC bfloat16 {C, W, H, N}, box {KB, 2 TW, 2 TH, 1} with
+// element stride 2 in W and H (TW x TH pixels land); weight map: [C_out]
+// [9 C_in] as {9 C_in, C_out}, box {KB, C_out}; both with the swizzle of
+// their KB x 2-byte rows.  Zero fill outside the tensors.
+template <int CIN, int COUT, int HI, int WI, int TW, int TH, int S>
+int run(const bf16* x, int B, const bf16* w, const float* bias, bf16* out, int* err,
+        cudaStream_t st) {
+  using C = ConvTma<CIN, COUT, HI, WI, TW, TH, S>;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return GS2D_ERR_CUDA;
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(w) |
+       reinterpret_cast<uintptr_t>(out)) & 15)
+    return GS2D_ERR_INVALID_ARG;
+  CUtensorMap mx, mw;
+  const cuuint64_t xdim[4] = {(cuuint64_t)CIN, (cuuint64_t)WI, (cuuint64_t)HI, (cuuint64_t)B};
+  const cuuint64_t xstr[3] = {(cuuint64_t)CIN * 2, (cuuint64_t)WI * CIN * 2,
+                              (cuuint64_t)HI * WI * CIN * 2};
+  const cuuint32_t xbox[4] = {(cuuint32_t)C::KB, 2 * TW, 2 * TH, 1};
+  const cuuint32_t xes[4] = {1, 2, 2, 1};
+  if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(x), xdim, xstr, xbox, xes,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, C::SW == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return GS2D_ERR_CUDA;
+  const cuuint64_t wdim[2] = {(cuuint64_t)9 * CIN, (cuuint64_t)COUT};
+  const cuuint64_t wstr[1] = {(cuuint64_t)9 * CIN * 2};
+  const cuuint32_t wbox[2] = {(cuuint32_t)C::KB, COUT};
+  const cuuint32_t wes[2] = {1, 1};
+  if (enc(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(w), wdim, wstr, wbox, wes,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, C::SW == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return GS2D_ERR_CUDA;
+  // the dynamic shared memory exceeds the 48 KB default: raise the limit once
+  // (before any stream capture that runs the network)
+  static std::once_flag smem_once;
+  static cudaError_t smem_err = cudaSuccess;
+  std::call_once(smem_once, [] {
+    smem_err = cudaFuncSetAttribute(conv_tma_kernel<CIN, COUT, HI, WI, TW, TH, S>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  });
+  if (smem_err != cudaSuccess) return GS2D_ERR_CUDA;
+  const int grid = B * C::TX * C::TY;
+  if (grid <= 0) return GS2D_OK;
+  conv_tma_kernel<CIN, COUT, HI, WI, TW, TH, S><<<grid, kConvThreads, C::SMEM, st>>>(
+      mx, mw, bias, out, err);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+}  // namespace
+
+bool conv_tma_layer(int layer) { return layer >= 1 && layer <= 3; }
+
+int conv_tma_forward(int layer, const bf16* x, int B, const bf16* w, const float* bias, bf16* out,
+                     int* err, cudaStream_t st) {
+  switch (layer) {
+    case 1: return run<32, 64, 60, 80, 8, 16, 4>(x, B, w, bias, out, err, st);
+    case 2: return run<64, 128, 30, 40, 8, 16, 3>(x, B, w, bias, out, err, st);
+    case 3: return run<128, 256, 15, 20, 16, 8, 2>(x, B, w, bias, out, err, st);
+    default: return GS2D_ERR_INVALID_ARG;
+  }
+}
+
+}  // namespace net
+}  // namespace gs2d

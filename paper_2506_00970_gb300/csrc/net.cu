@@ -35,6 +35,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include "conv_tma.h"
 #include "gs2d_common.cuh"
 #include "gs2d_net.h"
 #include "track_update.cuh"
@@ -1346,6 +1347,14 @@ int forward(const float* params, const bf16* x, int B, const Ws& w, float* y, cu
   if (r) return r;
   const bf16* in = w.act[1];
   for (int l = 1; l < kConv; ++l) {
+    if (conv_tma_layer(l)) {
+      // layers 2-4: tcgen05 with TMA-fed operands
+      r = conv_tma_forward(l, in, B, w.wbf + L.wbf_off[l], params + L.b_off[l], w.act[l + 1],
+                           w.err, st);
+      if (r) return r;
+      in = w.act[l + 1];
+      continue;
+    }
     Gemm g{};
     g.err = w.err;
     g.M = B * kHin[l + 1] * kWin[l + 1];
