@@ -46,7 +46,7 @@ TIMED_EVERY = 10          # fused-kernel launches bracketed by events: every 10t
 # DRAM bytes per launch of the roofline kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of the fused tracking kernel on
 # this workload); None while the kernel has changed since the capture.
-TRAFFIC_BYTES = {"track_tile": None}
+TRAFFIC_BYTES = {"track_tile": 6324480}
 # batched workloads reported beside the tracking line
 MAP_SURFELS, MAP_VIEWS = 1_000_000, 8
 UNEVEN_SURFELS, UNEVEN_VIEWS = 2_000_000, 32
@@ -454,7 +454,10 @@ def roofline(r, ds, frames, cam, cfg, stream, ms_iter, fused_ms):
     afu = work_fused / tfu / 1e12
     fused = {"kernel": "track_tile_kernel (render + tracking loss + pose backward)", "bound": "alu",
              "achieved": afu, "peak": peak, "unit": "TFLOP/s", "frac": afu / peak,
-             "traffic": TRAFFIC_BYTES["track_tile"], "launch_ms": fused_ms,
+             "traffic": TRAFFIC_BYTES["track_tile"],
+             "traffic_note": "ncu capture of one launch on the first of the timed frames "
+                             "(the lightest); the other frames read their own records",
+             "launch_ms": fused_ms,
              "launch_timing": f"CUDA events around the launches of every {TIMED_EVERY}th "
                               "iteration inside each timed frame graph",
              "share_of_iter": fused_ms / ms_iter, "flop_per_launch": work_fused,
@@ -1061,10 +1064,13 @@ def learned_proposal(flush):
         "net": {"fwd_batch256_ms": f_ms, "train_step_batch256_ms": s_ms,
                 "fwd_gflop_per_batch": fl_f * 256 / 1e9, "train_gflop_per_batch": fl_t * 256 / 1e9,
                 "roofline": {"kernel": "network forward: conv_s2_kernel (direct, mma.sync bf16) for "
-                                       "the first convolution, gemm_kernel (mma.sync bf16) for the "
-                                       "others and the FC products, gemm_tc_kernel (tcgen05 + TMEM) "
-                                       "for the split deep layers; training adds gemm_tc_kernel for "
-                                       "the split-K weight gradients", "bound": "tensor",
+                                       "the first convolution, conv_tma_kernel (tcgen05 + TMEM, "
+                                       "operands by tiled TMA with element strides and 64/128-byte "
+                                       "swizzle) for layers 2-4, gemm_tc_kernel (tcgen05 split-K) "
+                                       "for layers 5-6 and the FC products; training adds "
+                                       "gemm_tc_kernel for the split-K weight gradients and "
+                                       "gemm_kernel (mma.sync) for the data gradients",
+                             "bound": "tensor",
                              "achieved": fl_f * 256 / (f_ms / 1e3) / 1e12, "peak": peak,
                              "unit": "TFLOP/s", "frac": fl_f * 256 / (f_ms / 1e3) / 1e12 / peak,
                              "train_achieved": fl_t * 256 / (s_ms / 1e3) / 1e12,

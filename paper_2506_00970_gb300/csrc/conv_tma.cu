@@ -334,12 +334,23 @@ int run(const bf16* x, int B, const bf16* w, const float* bias, bf16* out, int* 
 
 bool conv_tma_layer(int layer) { return layer >= 1 && layer <= 3; }
 
+// Stages in flight: with a grid that fills the GPU several CTAs share an SM
+// (fewer stages each; the SM keeps as many loads in flight); a small batch's
+// few CTAs each keep as many stages as shared memory holds.  The stage count
+// changes no result (every tile sums its K steps in the same order).
 int conv_tma_forward(int layer, const bf16* x, int B, const bf16* w, const float* bias, bf16* out,
                      int* err, cudaStream_t st) {
+  constexpr int kFull = 2 * 152;  // CTAs that fill the GPU twice over
   switch (layer) {
-    case 1: return run<32, 64, 60, 80, 8, 16, 4>(x, B, w, bias, out, err, st);
-    case 2: return run<64, 128, 30, 40, 8, 16, 3>(x, B, w, bias, out, err, st);
-    case 3: return run<128, 256, 15, 20, 16, 8, 2>(x, B, w, bias, out, err, st);
+    case 1:
+      return B * 10 >= kFull ? run<32, 64, 60, 80, 8, 16, 4>(x, B, w, bias, out, err, st)
+                             : run<32, 64, 60, 80, 8, 16, 8>(x, B, w, bias, out, err, st);
+    case 2:
+      return B * 3 >= kFull ? run<64, 128, 30, 40, 8, 16, 3>(x, B, w, bias, out, err, st)
+                            : run<64, 128, 30, 40, 8, 16, 6>(x, B, w, bias, out, err, st);
+    case 3:
+      return B >= kFull / 2 ? run<128, 256, 15, 20, 16, 8, 2>(x, B, w, bias, out, err, st)
+                            : run<128, 256, 15, 20, 16, 8, 4>(x, B, w, bias, out, err, st);
     default: return GS2D_ERR_INVALID_ARG;
   }
 }
