@@ -9,6 +9,7 @@
 // gradients equal those of the single-view entry points.
 #include <mutex>
 
+#include "bwd_warp.cuh"
 #include "gs2d_common.cuh"
 #include "gs2d_internal.h"
 #include "tile_loops.cuh"
@@ -27,7 +28,7 @@ struct ViewDev {
   float *rgb, *depth, *normal, *opac, *T;
   uint32_t* nlast;
   const float *d_rgb, *d_depth, *d_normal, *d_opac;
-  float* partials;                  // this view's (tile, surfel) partials
+  float* partials;                  // this view's (tile, region, surfel) partials
 };
 struct ViewTable {
   int n_views, n_items;
@@ -84,48 +85,27 @@ __global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 4 : 2)) f
   }
 }
 
-template <int P>
-__global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 4 : 2)) bwd_batch_kernel(ViewTable tab,
-                                                                 uint32_t* __restrict__ queue) {
-  __shared__ BwdSmem<true> sm;
-  __shared__ int s_item;
+// Full backward of every view: persistent warps take (tile, region) work
+// units (Q regions per tile, the same for every view of a launch) from an
+// atomic counter; each unit is the single-view replay of bwd_warp.cuh.
+__global__ void __launch_bounds__(kBwdWarps * 32, kBwdWarpBlocks) bwd_batch_kernel(
+    ViewTable tab, int Q, uint32_t* __restrict__ queue) {
+  __shared__ WarpBwdSmem<kBwdRegion> sm[kBwdWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_units = tab.n_items * Q;
   while (true) {
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
-    __syncthreads();
-    const int item = s_item;
-    __syncthreads();
-    if (item >= tab.n_items) return;
+    uint32_t u = 0u;
+    if (lane == 0) u = atomicAdd(queue, 1u);
+    const int unit = (int)__shfl_sync(0xffffffffu, u, 0);
+    if (unit >= n_units) return;
+    const int item = unit / Q, region = unit - item * Q;
     const ViewDev& V = tab.v[view_of(tab, item)];
     if (V.status && *V.status) continue;
     const int tile = item - V.item0;
-    const TilePix<P> tp = tile_pixel<P>(tile, V.tiles_x, V.cfg.tile_w, V.cfg.tile_h);
-    bool inside[P];
-#pragma unroll
-    for (int k = 0; k < P; ++k) inside[k] = tp.px < V.cam.width && tp.py + 4 * k < V.cam.height;
-    const float xt = (float)((tile % V.tiles_x) * V.cfg.tile_w) + 0.5f - V.cam.cx;
-    const float yt = (float)((tile / V.tiles_x) * V.cfg.tile_h) + 0.5f - V.cam.cy;
-    const float rx = (tp.px + 0.5f - V.cam.cx) / V.cam.fx, ry = (tp.py + 0.5f - V.cam.cy) / V.cam.fy;
-    PixGrad pg[P];
-#pragma unroll
-    for (int k = 0; k < P; ++k) {
-      pg[k].Tf = 1.f;
-      pg[k].nl = 0;
-      pg[k].gC = f3(0.f, 0.f, 0.f);
-      pg[k].gN = f3(0.f, 0.f, 0.f);
-      pg[k].gD = 0.f;
-      pg[k].gO = 0.f;
-      if (!inside[k]) continue;
-      const size_t p = (size_t)(tp.py + 4 * k) * V.cam.width + tp.px;
-      pg[k].Tf = V.T[p];
-      pg[k].nl = V.nlast[p];
-      pg[k].gC = f3(V.d_rgb[3 * p], V.d_rgb[3 * p + 1], V.d_rgb[3 * p + 2]);
-      pg[k].gD = V.d_depth[p];
-      if (V.d_normal) pg[k].gN = f3(V.d_normal[3 * p], V.d_normal[3 * p + 1], V.d_normal[3 * p + 2]);
-      if (V.d_opac) pg[k].gO = V.d_opac[p];
-    }
-    float pr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    bwd_tile<true, P>(V.proj, V.vals, V.emit, V.ranges[2 * tile], V.ranges[2 * tile + 1], xt, yt,
-                      tp, inside, rx, ry, V.cam, V.cfg, pg, V.partials, sm, pr);
+    bwd_region<kBwdRegion>(V.proj, V.vals, V.emit, V.ranges[2 * tile], V.ranges[2 * tile + 1],
+                           (tile % V.tiles_x) * V.cfg.tile_w, (tile / V.tiles_x) * V.cfg.tile_h,
+                           region, Q, V.cam, V.cfg, V.T, V.nlast, V.d_rgb, V.d_depth, V.d_normal,
+                           V.d_opac, V.partials, sm[warp]);
   }
 }
 
@@ -167,7 +147,7 @@ BatchWs carve_batch_ws(void* base, const gs2d_view* views, int n_views, int n) {
   int max_parts = 1;
   for (int v = 0; v < n_views; ++v) {
     const size_t cap = views[v].bins.capacity > 0 ? views[v].bins.capacity : 1;
-    w.partials[v] = c.take<float>(cap * 16);
+    w.partials[v] = c.take<float>(cap * bwd_regions(views[v].cfg) * 16);
     const int m = views[v].active ? views[v].n_active : n;
     max_parts = max(max_parts, (m + 255) / 256);
   }
@@ -176,11 +156,11 @@ BatchWs carve_batch_ws(void* base, const gs2d_view* views, int n_views, int n) {
   return w;
 }
 
-int persistent_grid(const void* kernel) {
+int persistent_grid(const void* kernel, int threads = kTileThreads) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kTileThreads, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess)
     return 0;
   return sms * max(per_sm, 1);
 }
@@ -353,12 +333,12 @@ int gs2d_render_bwd_batch(const gs2d_view* views, int n_views, const gs2d_surfel
   cudaStream_t st = (cudaStream_t)stream;
   zero_words_kernel<<<1, 64, 0, st>>>(w.queue, 2);
   GS2D_LAUNCH_CHECK();
-  GS2D_DISPATCH_P(views[0].cfg.px_per_thread, {
-    const int grid = min(persistent_grid(reinterpret_cast<const void*>(bwd_batch_kernel<P>)),
-                         tab.n_items);
-    if (grid <= 0) return GS2D_ERR_CUDA;
-    bwd_batch_kernel<P><<<grid, kTileThreads, 0, st>>>(tab, w.queue + 1);
-  });
+  const int Q = bwd_regions(views[0].cfg);
+  const int grid = min(persistent_grid(reinterpret_cast<const void*>(bwd_batch_kernel),
+                                       kBwdWarps * 32),
+                       (tab.n_items * Q + kBwdWarps - 1) / kBwdWarps);
+  if (grid <= 0) return GS2D_ERR_CUDA;
+  bwd_batch_kernel<<<grid, kBwdWarps * 32, 0, st>>>(tab, Q, w.queue + 1);
   GS2D_LAUNCH_CHECK();
   // surfels outside every view's subset receive zero: clear, then add view by view
   GS2D_CUDA_TRY(cudaMemsetAsync(d_mu, 0, sizeof(float) * 3 * s->n, st));
@@ -369,7 +349,7 @@ int gs2d_render_bwd_batch(const gs2d_view* views, int n_views, const gs2d_surfel
   for (int v = 0; v < n_views; ++v) {
     const gs2d_view& x = views[v];
     const int m = x.active ? x.n_active : s->n;
-    r = surfel_grad_launch(s, x.active, m, 1, x.pose, x.tiles_per_surfel, x.bins.surfel_off,
+    r = surfel_grad_launch(s, x.active, m, 1, x.pose, x.tiles_per_surfel, x.bins.surfel_off, Q,
                            w.partials[v], d_mu, d_quat, d_scale, d_opac, d_rgb, w.pose_part,
                            x.bins.status, st);
     if (r) return r;

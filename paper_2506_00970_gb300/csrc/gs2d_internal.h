@@ -88,7 +88,7 @@ int track_tile_launch(const float* proj, const gs2d_bins* bins, const gs2d_camer
                       const gs2d_track_params* prm, float* loss_part, float* pose_part,
                       const TrackStep& ts, int32_t* status, cudaStream_t st);
 
-size_t render_bwd_ws_bytes(int n, size_t cap, int n_tiles, bool full);
+size_t render_bwd_ws_bytes(int n, size_t cap, int n_tiles, bool full, int Q);
 int render_bwd_launch(const float* proj, const gs2d_bins* bins, const int32_t* tiles_per_surfel,
                       const gs2d_surfels* s, const float* pose, const gs2d_camera* cam,
                       const gs2d_config* cfg, const float* t_final, const uint32_t* n_last,
@@ -104,11 +104,12 @@ int tracking_loss_launch(const float* rgb, const float* depth, const float* norm
                          float* g_depth, float* g_opacity, float* loss_out, void* workspace,
                          size_t ws_bytes, size_t* ws_needed, const int32_t* gate, cudaStream_t st);
 
-// Per-surfel reduction of one view's (tile, surfel) partials (record i is
-// surfel active[i] or i; accumulate adds into the outputs) and the block
-// partials of that view's pose gradient; fixed-order pose reduction.
+// Per-surfel reduction of one view's (tile, region, surfel) partials, Q
+// region slots per tile (record i is surfel active[i] or i; accumulate adds
+// into the outputs) and the block partials of that view's pose gradient;
+// fixed-order pose reduction.
 int surfel_grad_launch(const gs2d_surfels* s, const int32_t* active, int m, int accumulate,
-                       const float* pose, const int32_t* tiles, const uint32_t* surfel_off,
+                       const float* pose, const int32_t* tiles, const uint32_t* surfel_off, int Q,
                        const float* partials, float* d_mu, float* d_quat, float* d_scale,
                        float* d_opac, float* d_rgb, float* pose_part, const int32_t* gate,
                        cudaStream_t st);

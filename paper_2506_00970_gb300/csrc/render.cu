@@ -38,6 +38,7 @@
 // chains to world space, scales and the quaternion, and forms the pose term.
 // Tracking mode: pixels accumulate the 6-vector pose gradient directly; one
 // partial per tile, reduced in a fixed order.
+#include "bwd_warp.cuh"
 #include "gs2d_common.cuh"
 #include "gs2d_internal.h"
 #include "loss_pixel.cuh"
@@ -132,16 +133,17 @@ __device__ __forceinline__ void load_pix_grads(const TilePix<P>& tp, const bool 
   }
 }
 
-template <bool kFull, int P>
+// Pose-only backward (the full backward is render_bwd_warp_kernel): the
+// tile's pose 6-vector partial.
+template <int P>
 __global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) render_bwd_kernel(
     const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
-    const uint32_t* __restrict__ emit, const int32_t* __restrict__ ranges, gs2d_camera cam,
-    gs2d_config cfg, int tiles_x, const float* __restrict__ T_final,
-    const uint32_t* __restrict__ n_last, const float* __restrict__ g_rgb,
-    const float* __restrict__ g_depth, const float* __restrict__ g_normal,
-    const float* __restrict__ g_opac, float* __restrict__ partials, float* __restrict__ pose_part,
-    const int32_t* __restrict__ gate) {
-  __shared__ BwdSmem<kFull> sm;
+    const int32_t* __restrict__ ranges, gs2d_camera cam, gs2d_config cfg, int tiles_x,
+    const float* __restrict__ T_final, const uint32_t* __restrict__ n_last,
+    const float* __restrict__ g_rgb, const float* __restrict__ g_depth,
+    const float* __restrict__ g_normal, const float* __restrict__ g_opac,
+    float* __restrict__ pose_part, const int32_t* __restrict__ gate) {
+  __shared__ BwdSmem sm;
   __shared__ HitLists hl;
   __shared__ float s_pose[kTileThreads / 32][6];
   if (gate && *gate) return;
@@ -157,18 +159,35 @@ __global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) r
   PixGrad pg[P];
   load_pix_grads<P>(tp, inside, cam, T_final, n_last, g_rgb, g_depth, g_normal, g_opac, pg);
   float pr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if constexpr (kFull) {
-    bwd_tile<true, P>(proj, vals, emit, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tp, inside,
-                      rx, ry, cam, cfg, pg, partials, sm, pr);
-  } else {
-    if (g_normal)
-      bwd_tile_pose<true, P>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0,
-                             tile_y0, tp, inside, rx, ry, cam, cfg, pg, sm, hl, pr);
-    else
-      bwd_tile_pose<false, P>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0,
-                              tile_y0, tp, inside, rx, ry, cam, cfg, pg, sm, hl, pr);
-    block_sum6(pr, s_pose, pose_part + (size_t)tile * 6);
-  }
+  if (g_normal)
+    bwd_tile_pose<true, P>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0,
+                           tile_y0, tp, inside, rx, ry, cam, cfg, pg, sm, hl, pr);
+  else
+    bwd_tile_pose<false, P>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0,
+                            tile_y0, tp, inside, rx, ry, cam, cfg, pg, sm, hl, pr);
+  block_sum6(pr, s_pose, pose_part + (size_t)tile * 6);
+}
+
+// Full backward: one warp per (tile, region) work item, kBwdWarps warps per
+// block and no block barrier (bwd_warp.cuh).
+__global__ void __launch_bounds__(kBwdWarps * 32, kBwdWarpBlocks) render_bwd_warp_kernel(
+    const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ emit, const int32_t* __restrict__ ranges, gs2d_camera cam,
+    gs2d_config cfg, int tiles_x, int Q, int n_units, const float* __restrict__ T_final,
+    const uint32_t* __restrict__ n_last, const float* __restrict__ g_rgb,
+    const float* __restrict__ g_depth, const float* __restrict__ g_normal,
+    const float* __restrict__ g_opac, float* __restrict__ partials,
+    const int32_t* __restrict__ gate) {
+  __shared__ WarpBwdSmem<kBwdRegion> sm[kBwdWarps];
+  if (gate && *gate) return;
+  const int warp = threadIdx.x >> 5;
+  const int unit = blockIdx.x * kBwdWarps + warp;
+  if (unit >= n_units) return;
+  const int tile = unit / Q, region = unit - tile * Q;
+  bwd_region<kBwdRegion>(proj, vals, emit, ranges[2 * tile], ranges[2 * tile + 1],
+                         (tile % tiles_x) * cfg.tile_w, (tile / tiles_x) * cfg.tile_h, region, Q,
+                         cam, cfg, T_final, n_last, g_rgb, g_depth, g_normal, g_opac, partials,
+                         sm[warp]);
 }
 
 // Fused tracking iteration on one tile: forward compositing, the tracking
@@ -182,7 +201,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<P, kG>()) tra
     const float* __restrict__ obs_rgb, const float* __restrict__ obs_depth, gs2d_track_params prm,
     float* __restrict__ loss_part, float* __restrict__ pose_part, TrackStep ts,
     int32_t* __restrict__ status) {
-  __shared__ BwdSmem<false> sm;
+  __shared__ BwdSmem sm;
   __shared__ HitLists hl;
   __shared__ float s_pose[kTileThreads / 32][6];
   __shared__ float s_loss[kTileThreads / 32];
@@ -267,17 +286,19 @@ __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<P, kG>()) tra
     for (size_t i = threadIdx.x; i < ts.sort_zero_words; i += blockDim.x) ts.sort_zero[i] = 0u;
 }
 
-// Per-surfel reduction of the (tile, surfel) partials in emission order and
-// the chain rule to world-space parameters; pose term per block.
+// Per-surfel reduction of the (tile, region, surfel) partials in emission
+// order (Q region slots per tile) and the chain rule to world-space
+// parameters; pose term per block.
 // Record i is surfel active[i] (or i); with accumulate the gradients are
 // added to the outputs (several views, one after another).
 __global__ void __launch_bounds__(256) surfel_grad_kernel(
     const float* __restrict__ mu, const float* __restrict__ quat, const float* __restrict__ scale,
     int n, const int32_t* __restrict__ active, int accumulate, const float* __restrict__ pose,
     const int32_t* __restrict__ tiles, const uint32_t* __restrict__ surfel_off,
-    const float* __restrict__ partials, float* __restrict__ d_mu, float* __restrict__ d_quat,
-    float* __restrict__ d_scale, float* __restrict__ d_opac, float* __restrict__ d_rgb,
-    float* __restrict__ pose_part, int n_all, const int32_t* __restrict__ gate) {
+    int Q, const float* __restrict__ partials, float* __restrict__ d_mu,
+    float* __restrict__ d_quat, float* __restrict__ d_scale, float* __restrict__ d_opac,
+    float* __restrict__ d_rgb, float* __restrict__ pose_part, int n_all,
+    const int32_t* __restrict__ gate) {
   __shared__ float sp[12];
   __shared__ float s_pose[8][6];
   if (gate && *gate) return;
@@ -289,9 +310,9 @@ __global__ void __launch_bounds__(256) surfel_grad_kernel(
     float S[kRedVals];
 #pragma unroll
     for (int c = 0; c < kRedVals; ++c) S[c] = 0.f;
-    const int k = tiles[i];
+    const int k = tiles[i] * Q;
     if (k > 0) {
-      const float4* p = reinterpret_cast<const float4*>(partials) + (size_t)surfel_off[i] * 4;
+      const float4* p = reinterpret_cast<const float4*>(partials) + (size_t)surfel_off[i] * Q * 4;
       for (int e = 0; e < k; ++e) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -395,10 +416,10 @@ struct BwdWs {
   float* pose_part;
   size_t bytes;
 };
-BwdWs carve_bwd_ws(void* base, int n, size_t cap, int n_tiles, bool full) {
+BwdWs carve_bwd_ws(void* base, int n, size_t cap, int n_tiles, bool full, int Q) {
   Carver c(base);
   BwdWs w;
-  w.partials = c.take<float>(full ? (cap > 0 ? cap : 1) * kRedVals : 1);
+  w.partials = c.take<float>(full ? (cap > 0 ? cap : 1) * Q * kRedVals : 1);
   const int nb = max(n_tiles, (n + 255) / 256);
   w.pose_part = c.take<float>((size_t)max(nb, 1) * 6);
   w.bytes = align_up(c.off, 256);
@@ -479,13 +500,14 @@ int track_tile_launch(const float* proj, const gs2d_bins* bins, const gs2d_camer
 }
 
 int surfel_grad_launch(const gs2d_surfels* s, const int32_t* active, int m, int accumulate,
-                       const float* pose, const int32_t* tiles, const uint32_t* surfel_off,
+                       const float* pose, const int32_t* tiles, const uint32_t* surfel_off, int Q,
                        const float* partials, float* d_mu, float* d_quat, float* d_scale,
                        float* d_opac, float* d_rgb, float* pose_part, const int32_t* gate,
                        cudaStream_t st) {
   if (m <= 0) return GS2D_OK;
   surfel_grad_kernel<<<(m + 255) / 256, 256, 0, st>>>(s->mu, s->quat, s->scale, m, active,
-                                                      accumulate, pose, tiles, surfel_off, partials,
+                                                      accumulate, pose, tiles, surfel_off, Q,
+                                                      partials,
                                                       d_mu, d_quat, d_scale, d_opac, d_rgb,
                                                       pose_part, s->n, gate);
   GS2D_LAUNCH_CHECK();
@@ -499,8 +521,8 @@ int pose_reduce_launch(const float* part, int n_part, float* out, const int32_t*
   return GS2D_OK;
 }
 
-size_t render_bwd_ws_bytes(int n, size_t cap, int n_tiles, bool full) {
-  return carve_bwd_ws(nullptr, n, cap, n_tiles, full).bytes;
+size_t render_bwd_ws_bytes(int n, size_t cap, int n_tiles, bool full, int Q) {
+  return carve_bwd_ws(nullptr, n, cap, n_tiles, full, Q).bytes;
 }
 
 int render_bwd_launch(const float* proj, const gs2d_bins* bins, const int32_t* tiles_per_surfel,
@@ -524,20 +546,24 @@ int render_bwd_launch(const float* proj, const gs2d_bins* bins, const int32_t* t
   if (!full && !d_pose6) return GS2D_ERR_INVALID_ARG;
   const int tx = gs2d_tiles_x(cam, cfg), ty = gs2d_tiles_y(cam, cfg);
   const int n_tiles = tx * ty;
-  const size_t need = render_bwd_ws_bytes(s->n, bins->capacity, n_tiles, full);
+  // partials sized for the largest tile shape, so the size follows from
+  // (n, capacity, n_tiles) alone
+  const size_t need = render_bwd_ws_bytes(s->n, bins->capacity, n_tiles, full, kBwdMaxRegions);
   if (ws_needed) *ws_needed = need;
   if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
-  const BwdWs w = carve_bwd_ws(workspace, s->n, bins->capacity, n_tiles, full);
+  const BwdWs w = carve_bwd_ws(workspace, s->n, bins->capacity, n_tiles, full, kBwdMaxRegions);
   const float4* p4 = reinterpret_cast<const float4*>(proj);
   if (full) {
-    GS2D_DISPATCH_P(cfg->px_per_thread, render_bwd_kernel<true, P><<<n_tiles, kTileThreads, 0, st>>>(
-        p4, bins->vals, bins->isect_emit, bins->tile_ranges, *cam, *cfg, tx, t_final, n_last, d_rgb,
-        d_depth, d_normal, d_opacity, w.partials, w.pose_part, gate));
+    const int Q = bwd_regions(*cfg);
+    const int units = n_tiles * Q;
+    render_bwd_warp_kernel<<<(units + kBwdWarps - 1) / kBwdWarps, kBwdWarps * 32, 0, st>>>(
+        p4, bins->vals, bins->isect_emit, bins->tile_ranges, *cam, *cfg, tx, Q, units, t_final,
+        n_last, d_rgb, d_depth, d_normal, d_opacity, w.partials, gate);
     GS2D_LAUNCH_CHECK();
     if (s->n > 0) {
       const int nb = (s->n + 255) / 256;
       surfel_grad_kernel<<<nb, 256, 0, st>>>(s->mu, s->quat, s->scale, s->n, nullptr, 0, pose,
-                                             tiles_per_surfel, bins->surfel_off, w.partials, d_mu,
+                                             tiles_per_surfel, bins->surfel_off, Q, w.partials, d_mu,
                                              d_quat, d_scale, d_opac, d_rgb_out, w.pose_part, s->n,
                                              gate);
       GS2D_LAUNCH_CHECK();
@@ -549,9 +575,9 @@ int render_bwd_launch(const float* proj, const gs2d_bins* bins, const int32_t* t
       GS2D_CUDA_TRY(cudaMemsetAsync(d_pose6, 0, 6 * sizeof(float), st));
     }
   } else {
-    GS2D_DISPATCH_P(cfg->px_per_thread, render_bwd_kernel<false, P><<<n_tiles, kTileThreads, 0, st>>>(
-        p4, bins->vals, bins->isect_emit, bins->tile_ranges, *cam, *cfg, tx, t_final, n_last, d_rgb,
-        d_depth, d_normal, d_opacity, w.partials, w.pose_part, gate));
+    GS2D_DISPATCH_P(cfg->px_per_thread, render_bwd_kernel<P><<<n_tiles, kTileThreads, 0, st>>>(
+        p4, bins->vals, bins->tile_ranges, *cam, *cfg, tx, t_final, n_last, d_rgb, d_depth,
+        d_normal, d_opacity, w.pose_part, gate));
     GS2D_LAUNCH_CHECK();
     pose_reduce_kernel<<<1, 256, 0, st>>>(w.pose_part, n_tiles, d_pose6, gate);
     GS2D_LAUNCH_CHECK();
@@ -591,7 +617,7 @@ int gs2d_render_count(const float* proj, const gs2d_bins* bins, const gs2d_camer
 void gs2d_set_grouped_tiles(int max_tiles) { g_grouped_max_tiles = max_tiles < -1 ? -1 : max_tiles; }
 
 size_t gs2d_render_bwd_workspace(int n, size_t capacity, int n_tiles) {
-  return render_bwd_ws_bytes(n, capacity, n_tiles, true);
+  return render_bwd_ws_bytes(n, capacity, n_tiles, true, kBwdMaxRegions);
 }
 
 int gs2d_render_bwd(const float* proj, const gs2d_bins* bins, const int32_t* tiles_per_surfel,

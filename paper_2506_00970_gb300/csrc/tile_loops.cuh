@@ -152,26 +152,32 @@ __device__ __forceinline__ bool eval_pair(const float4 r0, const float4 r1, cons
   return e.a >= alpha_min;
 }
 
-// Stages the records of list positions [b, b + 256) into s_rec: the forward
-// layout (5 float4) or the backward layout (7 float4); slot 4.y/z (forward)
-// or 6.z/w (backward) carries the packed pixel footprint.
+// Stages the record of surfel id at dst (stage_record: row threadIdx.x of
+// s_rec): the forward layout (5 float4) or the backward layout (7 float4);
+// slot 4.y/z (forward) or 6.z/w (backward) carries the packed pixel
+// footprint.
+template <int kStride>
+__device__ __forceinline__ void stage_record_to(const float4* __restrict__ proj, uint32_t id,
+                                                float xt, float yt, float4* dst) {
+  const float4* src = proj + (size_t)id * (kProjFloats / 4);
+  const float4 r0 = src[0], r1 = src[1], r2 = src[2], r7 = src[7];
+  dst[0] = stage_c0(r0, r1, r2, xt, yt);
+  dst[1] = r1;
+  dst[2] = r2;
+  dst[3] = src[3];
+  if (kStride == kFwdVec4) {
+    dst[4] = make_float4(src[4].x, r7.z, r7.w, 0.f);
+  } else {
+    const float4 r6 = src[6];
+    dst[4] = src[4];
+    dst[5] = src[5];
+    dst[6] = make_float4(r6.x, r6.y, r7.z, r7.w);
+  }
+}
 template <int kStride>
 __device__ __forceinline__ void stage_record(const float4* __restrict__ proj, uint32_t id, float xt,
                                              float yt, float4 (*s_rec)[kStride]) {
-  const float4* src = proj + (size_t)id * (kProjFloats / 4);
-  const float4 r0 = src[0], r1 = src[1], r2 = src[2], r7 = src[7];
-  s_rec[threadIdx.x][0] = stage_c0(r0, r1, r2, xt, yt);
-  s_rec[threadIdx.x][1] = r1;
-  s_rec[threadIdx.x][2] = r2;
-  s_rec[threadIdx.x][3] = src[3];
-  if (kStride == kFwdVec4) {
-    s_rec[threadIdx.x][4] = make_float4(src[4].x, r7.z, r7.w, 0.f);
-  } else {
-    const float4 r6 = src[6];
-    s_rec[threadIdx.x][4] = src[4];
-    s_rec[threadIdx.x][5] = src[5];
-    s_rec[threadIdx.x][6] = make_float4(r6.x, r6.y, r7.z, r7.w);
-  }
+  stage_record_to<kStride>(proj, id, xt, yt, s_rec[threadIdx.x]);
 }
 
 struct FwdState {
@@ -395,12 +401,10 @@ __device__ __forceinline__ void warp_reduce_scatter16(float (&v)[kRedVals], int 
   v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-// Shared-memory scratch of the backward loop.
-template <bool kFull>
+// Shared-memory scratch of the pose-only backward loops: the staged
+// records and the tile's largest blended-entry count.
 struct BwdSmem {
   float4 rec[kTileThreads][kBwdVec4];
-  uint32_t emit[kFull ? kTileThreads : 1];
-  float red[kFull ? 8 : 1][kFull ? 32 : 1][kRedVals];
   uint32_t max_nl;
 };
 
@@ -412,159 +416,6 @@ struct PixGrad {
   F3 gC, gN;
   float gD, gO;
 };
-
-// Back-to-front replay of the thread's P pixels over the tile's list.  Full
-// mode sums a pair's 16 gradient terms over the P pixels, reduces them over
-// the warp and then the block, and writes the per-(tile, surfel) partials;
-// pose mode accumulates the pose 6-vector in pr.  ry is the first pixel's
-// ray y; pixel k's is ry + 4k / fy.
-template <bool kFull, int P>
-__device__ __forceinline__ void bwd_tile(const float4* __restrict__ proj,
-                                         const uint32_t* __restrict__ vals,
-                                         const uint32_t* __restrict__ emit, int start, int end,
-                                         float xt, float yt, const TilePix<P>& tp,
-                                         const bool (&inside)[P], float rx, float ry,
-                                         const gs2d_camera& cam, const gs2d_config& cfg,
-                                         const PixGrad (&pg)[P], float* __restrict__ partials,
-                                         BwdSmem<kFull>& sm, float (&pr)[6]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float fxfy = cam.fx * cam.fy;
-  if (threadIdx.x == 0) sm.max_nl = 0u;
-  __syncthreads();
-  uint32_t my_nl = 0;
-#pragma unroll
-  for (int k = 0; k < P; ++k) my_nl = max(my_nl, pg[k].nl);
-  if (my_nl) atomicMax(&sm.max_nl, my_nl);
-  __syncthreads();
-  const int hi = start + (int)sm.max_nl;
-  float T[P], acc[P], gOT[P], lyk[P], ryk[P];
-#pragma unroll
-  for (int k = 0; k < P; ++k) {
-    T[k] = pg[k].Tf;
-    acc[k] = 0.f;
-    gOT[k] = pg[k].gO * pg[k].Tf;
-    lyk[k] = k ? tp.ly + 4.f * k : tp.ly;
-    ryk[k] = k ? ry + (4.f * k) / cam.fy : ry;
-  }
-  for (int bend = hi; bend > start; bend -= kTileThreads) {
-    const int bstart = max(start, bend - kTileThreads);
-    const int cnt = bend - bstart;
-    __syncthreads();
-    if ((int)threadIdx.x < cnt) {
-      const int idx = bstart + (int)threadIdx.x;
-      stage_record<kBwdVec4>(proj, vals[idx], xt, yt, sm.rec);
-      if (kFull) sm.emit[threadIdx.x] = emit[idx];
-    }
-    __syncthreads();
-    // chunks of 32 staged entries, back to front; per chunk one ballot finds
-    // the entries whose footprint touches this warp's block, and only those
-    // are replayed (the others cannot reach any of its pixels)
-    for (int c_lo = ((cnt - 1) >> 5) << 5; c_lo >= 0; c_lo -= 32) {
-      const int c_n = min(32, cnt - c_lo);
-      bool h = false;
-      if (lane < c_n) {
-        const float4 r6 = sm.rec[c_lo + lane][6];
-        h = warp_hits<P>(r6.z, r6.w, tp.bx0, tp.by0);
-      }
-      uint32_t hits = __ballot_sync(0xffffffffu, h);
-      if (kFull && !h) {
-        float4* z = reinterpret_cast<float4*>(&sm.red[warp][lane][0]);
-        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int q = 0; q < kRedVals / 4; ++q) z[q] = zero;
-      }
-      while (hits) {
-        const int slot = 31 - __clz(hits);
-        hits &= ~(1u << slot);
-        const int jj = c_lo + slot;
-        const int jrel = bstart + jj - start;
-        float val[kRedVals];
-        bool contrib = false;
-        const float4 r0 = sm.rec[jj][0], r1 = sm.rec[jj][1], r2 = sm.rec[jj][2];
-#pragma unroll
-        for (int k = 0; k < P; ++k) {
-          if (!(inside[k] && jrel < (int)pg[k].nl)) continue;
-          Eval e;
-          if (!eval_pair(r0, r1, r2, tp.lx, lyk[k], cam.near_z, cfg.cutoff_r2, cfg.alpha_min,
-                         cfg.alpha_max, e))
-            continue;
-          const float4 r3 = sm.rec[jj][3], r4 = sm.rec[jj][4], r5 = sm.rec[jj][5];
-          const float4 r6 = sm.rec[jj][6];
-          const F3 col = f3(r2.w, r3.x, r3.y);
-          const F3 tn = f3(r3.z, r3.w, r4.x);
-          const F3 nrm = f3(r4.y, r4.z, r4.w);
-          const F3 du = f3(r5.x, r5.y, r5.z), dv = f3(r5.w, r6.x, r6.y);
-          const F3 gC = pg[k].gC, gN = pg[k].gN;
-          const float gD = pg[k].gD;
-          const float om = 1.f - e.a;
-          const float iom = __fdividef(1.f, om);
-          const float Tb = T[k] * iom;
-          const float w = e.a * Tb;
-          const float vj = dot3(col, gC) + e.z * gD + dot3(tn, gN);
-          const float ga = Tb * vj - (acc[k] - gOT[k]) * iom;
-          acc[k] = fmaf(w, vj, acc[k]);
-          T[k] = Tb;
-          float galpha = 0.f, gG = 0.f;
-          if (e.araw <= cfg.alpha_max) {
-            galpha = e.G * ga;
-            gG = r2.z * ga;
-          }
-          const float gr2 = -0.5f * e.G * gG;
-          const float gu = 2.f * e.u * gr2, gv = 2.f * e.v * gr2;
-          const float gz = w * gD;
-          const F3 q = gu * du + gv * dv;
-          const float beta = (fmaf(q.x, rx, fmaf(q.y, ryk[k], q.z)) + gz) * fxfy * e.rinv;
-          const F3 Gv = beta * nrm - q;
-          if (kFull) {
-            const float t[kRedVals] = {Gv.x, Gv.y, Gv.z, e.u * Gv.x, e.u * Gv.y, e.u * Gv.z,
-                                       e.v * Gv.x, e.v * Gv.y, e.v * Gv.z, galpha, w * gC.x,
-                                       w * gC.y, w * gC.z, w * gN.x, w * gN.y, w * gN.z};
-#pragma unroll
-            for (int i = 0; i < kRedVals; ++i) val[i] = contrib ? val[i] + t[i] : t[i];
-          } else {
-            const F3 X = f3(e.z * rx, e.z * ryk[k], e.z);
-            const F3 gtn = w * gN;
-            const F3 th = cross3(X, Gv) + cross3(tn, gtn);
-            pr[0] += Gv.x; pr[1] += Gv.y; pr[2] += Gv.z;
-            pr[3] += th.x; pr[4] += th.y; pr[5] += th.z;
-          }
-          contrib = true;
-        }
-        if (kFull) {
-          if (__any_sync(0xffffffffu, contrib)) {
-            if (!contrib) {
-#pragma unroll
-              for (int i = 0; i < kRedVals; ++i) val[i] = 0.f;
-            }
-            warp_reduce_scatter16(val, lane);
-            if ((lane & 1) == 0) sm.red[warp][slot][lane >> 1] = val[0];
-          } else if (lane < kRedVals) {
-            sm.red[warp][slot][lane] = 0.f;
-          }
-        }
-      }
-      if (kFull) {
-        __syncthreads();
-        for (int o = threadIdx.x; o < c_n * kRedVals; o += kTileThreads) {
-          const int s = o / kRedVals, c = o % kRedVals;
-          float sum = 0.f;
-#pragma unroll
-          for (int ww = 0; ww < 8; ++ww) sum += sm.red[ww][s][c];
-          partials[(size_t)sm.emit[c_lo + s] * kRedVals + c] = sum;
-        }
-        __syncthreads();
-      }
-    }
-  }
-  if (kFull) {
-    // pairs past every pixel's last blended surfel contribute nothing
-    const int tail = end - max(hi, start);
-    for (int o = threadIdx.x; o < tail * kRedVals; o += kTileThreads) {
-      const int s = o / kRedVals, c = o % kRedVals;
-      partials[(size_t)emit[hi + s] * kRedVals + c] = 0.f;
-    }
-  }
-}
 
 // One replayed (pixel, surfel) pair of the pose-only backward: the blending
 // gradient from the running state (T, acc) and the pair's rank-one splat
@@ -605,9 +456,10 @@ __device__ __forceinline__ void pose_pair(const Eval& e, const float4 r2, const 
   if (kNormal) sN = sN + w * f3(r3.z, r3.w, r4.x);
 }
 
-// Pose-only back-to-front replay (tracking): like bwd_tile but each warp
-// visits only the surfels whose footprint touches its block, and the pose
-// gradient is accumulated per pixel.  With the hit point X = z r and r fixed
+// Pose-only back-to-front replay (tracking): the thread's P pixels walk the
+// tile's list from each pixel's last blended entry to the front, undoing the
+// compositing (T / (1 - a)) and accumulating the pose gradient per pixel;
+// each warp visits only the surfels whose footprint touches its block.  With the hit point X = z r and r fixed
 // per pixel, sum_pairs X x Gv = r x sum_pairs z Gv, so a pair only adds Gv
 // and z Gv; with q = s (u d_u + v d_v), s = -G dL/dG, the pair's
 // Gv = beta n - q, beta = (q . r + gz) / (n . r).  kNormal adds the normal
@@ -625,7 +477,7 @@ __device__ __forceinline__ void bwd_tile_pose(const float4* __restrict__ proj,
                                               const TilePix<P>& tp, const bool (&inside)[P],
                                               float rx, float ry, const gs2d_camera& cam,
                                               const gs2d_config& cfg, const PixGrad (&pg)[P],
-                                              BwdSmem<false>& sm, HitLists& hl, float (&pr)[6],
+                                              BwdSmem& sm, HitLists& hl, float (&pr)[6],
                                               bool staged = false) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float fxfy = cam.fx * cam.fy;

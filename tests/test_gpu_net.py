@@ -71,6 +71,24 @@ def test_net_rows_are_independent_of_batch_tiling(torch_cuda):
         assert torch.equal(y1[0], y[b]), b
 
 
+def test_net_rows_of_a_full_batch_equal_single_samples(torch_cuda):
+    """At a batch that fills the GPU (160 samples) the layers 2-4
+    convolutions run with fewer pipeline stages per CTA than for a single
+    sample; a tile sums its K steps in the same order either way, so rows
+    of the full batch equal single-sample calls bit for bit."""
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d
+    params, x, t, P, X, T, ws = _setup(torch, 160, seed=5)
+    y = torch.empty(160, 6, device="cuda")
+    gs2d.gs2d_net_forward(P, X, y, ws)
+    ws1 = torch.empty(gs2d.gs2d_net_workspace(1), dtype=torch.uint8, device="cuda")
+    for b in (0, 77, 159):
+        y1 = torch.empty(1, 6, device="cuda")
+        gs2d.gs2d_net_forward(P, X[b:b + 1].contiguous(), y1, ws1)
+        torch.cuda.synchronize()
+        assert torch.equal(y1[0], y[b]), b
+
+
 def _exact_setup(torch, B, seed):
     """Inputs on which every FP32 accumulation is exact: x and the biases
     integer multiples of 1/4, weights sparse in {-1, 0, 1} (about 3.5
