@@ -350,7 +350,7 @@ int gs2d_render_bwd_batch(const gs2d_view* views, int n_views, const gs2d_surfel
     const gs2d_view& x = views[v];
     const int m = x.active ? x.n_active : s->n;
     r = surfel_grad_launch(s, x.active, m, 1, x.pose, x.tiles_per_surfel, x.bins.surfel_off, Q,
-                           w.partials[v], d_mu, d_quat, d_scale, d_opac, d_rgb, w.pose_part,
+                           x.proj, w.partials[v], d_mu, d_quat, d_scale, d_opac, d_rgb, w.pose_part,
                            x.bins.status, st);
     if (r) return r;
     if (x.d_pose6) {

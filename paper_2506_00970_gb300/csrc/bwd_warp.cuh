@@ -8,10 +8,14 @@
 // tile's list back to front, 32 staged records at a time, and for each entry
 // whose footprint touches the region evaluates only the touched blocks (a
 // warp-uniform branch per block), sums the entry's 16 gradient terms over
-// the lane's R pixels in registers and then over the warp with one
-// reduce-scatter.  Nothing is shared between warps, so there is no block
+// the lane's R pixels in registers and then over the warp through shared
+// memory.  Nothing is shared between warps, so there is no block
 // barrier: a region's partial sums go straight to its own slot,
 //   partials[(emit * Q + region) * 16 + c],   Q = regions per tile,
+// the pair sums of (beta, u beta, v beta, g, u g, v g, u^2 g, u v g, v^2 g,
+// w dC, w dN, 0), g the pair's opacity gradient (the splat gradient
+// Gv = beta n + o g (u d_u + v d_v) is linear in them, so the per-surfel
+// reduction forms sum Gv, sum u Gv, sum v Gv from the surfel's n, d_u, d_v),
 // and every (entry, region) slot is written exactly once (zeros where the
 // footprint misses the region, no pixel of it blends the entry, or the entry
 // lies past the region's last blended entry).  The per-surfel reduction
@@ -40,6 +44,7 @@ template <int R>
 struct WarpBwdSmem {
   float4 rec[32][kBwdVec4];
   float4 up[R][2][32];
+  float red[32][20];  // one entry's 16 per-lane sums, rows padded to 20 floats
 };
 
 // Bit k set if the footprint (packed absolute pixel ranges) touches block k
@@ -150,8 +155,6 @@ __device__ __forceinline__ void bwd_region(
         const float4 u0 = sm.up[k][0][lane], u1 = sm.up[k][1][lane];
         const F3 col = f3(r2.w, r3.x, r3.y);
         const F3 tn = f3(r3.z, r3.w, r4.x);
-        const F3 nrm = f3(r4.y, r4.z, r4.w);
-        const F3 du = f3(r5.x, r5.y, r5.z), dv = f3(r5.w, r6.x, r6.y);
         const F3 gC = f3(u0.x, u0.y, u0.z), gN = f3(u1.x, u1.y, u1.z);
         const float gD = u0.w;
         const float om = 1.f - e.a;
@@ -162,29 +165,55 @@ __device__ __forceinline__ void bwd_region(
         const float ga = Tb * vj - (acc[k] - u1.w) * iom;
         acc[k] = fmaf(w, vj, acc[k]);
         T[k] = Tb;
-        float galpha = 0.f, gG = 0.f;
-        if (e.araw <= cfg.alpha_max) {
-          galpha = e.G * ga;
-          gG = r2.z * ga;
-        }
-        const float gr2 = -0.5f * e.G * gG;
-        const float gu = 2.f * e.u * gr2, gv = 2.f * e.v * gr2;
-        const float gz = w * gD;
-        const F3 q = gu * du + gv * dv;
+        // g = dL/d(opacity) of the pair; the splat gradient is
+        // Gv = beta n + o g (u d_u + v d_v) with
+        // beta = (w dD - o g (u d_u + v d_v) . r) / (n . r), 1 / (n . r) = fx fy rinv
+        const float g = e.araw <= cfg.alpha_max ? e.G * ga : 0.f;
         const float rx = fmaf(lx[k], ifx, rx0), ry = fmaf(ly[k], ify, ry0);
-        const float beta = (fmaf(q.x, rx, fmaf(q.y, ry, q.z)) + gz) * fxfy * e.rinv;
-        const F3 Gv = beta * nrm - q;
-        const float t[kRedVals] = {Gv.x, Gv.y, Gv.z, e.u * Gv.x, e.u * Gv.y, e.u * Gv.z,
-                                   e.v * Gv.x, e.v * Gv.y, e.v * Gv.z, galpha, w * gC.x,
-                                   w * gC.y, w * gC.z, w * gN.x, w * gN.y, w * gN.z};
-#pragma unroll
-        for (int i = 0; i < kRedVals; ++i) val[i] += t[i];
+        const float dur = fmaf(r5.x, rx, fmaf(r5.y, ry, r5.z));
+        const float dvr = fmaf(r5.w, rx, fmaf(r6.x, ry, r6.y));
+        const float Pr = fmaf(e.u, dur, e.v * dvr);
+        const float beta = fmaf(-r2.z * g, Pr, w * gD) * fxfy * e.rinv;
+        const float ug = e.u * g, vg = e.v * g;
+        val[0] += beta;
+        val[1] = fmaf(e.u, beta, val[1]);
+        val[2] = fmaf(e.v, beta, val[2]);
+        val[3] += g;
+        val[4] += ug;
+        val[5] += vg;
+        val[6] = fmaf(e.u, ug, val[6]);
+        val[7] = fmaf(e.u, vg, val[7]);
+        val[8] = fmaf(e.v, vg, val[8]);
+        val[9] = fmaf(w, gC.x, val[9]);
+        val[10] = fmaf(w, gC.y, val[10]);
+        val[11] = fmaf(w, gC.z, val[11]);
+        val[12] = fmaf(w, gN.x, val[12]);
+        val[13] = fmaf(w, gN.y, val[13]);
+        val[14] = fmaf(w, gN.z, val[14]);
         contrib = true;
       }
       float* dst = partials + ((size_t)e_j * Q + slot_base) * kRedVals;
       if (__any_sync(0xffffffffu, contrib)) {
-        warp_reduce_scatter16(val, lane);
-        if ((lane & 1) == 0) dst[lane >> 1] = val[0];
+        // sum over the warp through shared memory: lane l writes its 16
+        // sums as row l, then lane l adds up column l & 15 over the rows of
+        // its half-warp (the upper half four rows on, so the halves read
+        // disjoint banks; 80-byte rows keep the row stores conflict-free)
+        float4* row = reinterpret_cast<float4*>(&sm.red[lane][0]);
+#pragma unroll
+        for (int q = 0; q < kRedVals / 4; ++q)
+          row[q] = make_float4(val[4 * q], val[4 * q + 1], val[4 * q + 2], val[4 * q + 3]);
+        __syncwarp();
+        const int c = lane & 15, upper = lane >> 4;
+        float part[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) part[i] = sm.red[upper ? 16 + ((i + 4) & 15) : i][c];
+#pragma unroll
+        for (int h = 8; h > 0; h >>= 1)
+#pragma unroll
+          for (int i = 0; i < h; ++i) part[i] += part[i + h];
+        const float sum = part[0] + __shfl_xor_sync(0xffffffffu, part[0], 16);
+        if (lane < kRedVals) dst[lane] = sum;
+        __syncwarp();  // the next entry rewrites red
       } else if (lane < kRedVals) {
         dst[lane] = 0.f;
       }

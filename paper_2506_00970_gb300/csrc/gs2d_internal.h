@@ -105,14 +105,14 @@ int tracking_loss_launch(const float* rgb, const float* depth, const float* norm
                          size_t ws_bytes, size_t* ws_needed, const int32_t* gate, cudaStream_t st);
 
 // Per-surfel reduction of one view's (tile, region, surfel) partials, Q
-// region slots per tile (record i is surfel active[i] or i; accumulate adds
-// into the outputs) and the block partials of that view's pose gradient;
+// region slots per tile, with the view's projected records proj (record i
+// is surfel active[i] or i; accumulate adds into the outputs) and the block partials of that view's pose gradient;
 // fixed-order pose reduction.
 int surfel_grad_launch(const gs2d_surfels* s, const int32_t* active, int m, int accumulate,
                        const float* pose, const int32_t* tiles, const uint32_t* surfel_off, int Q,
-                       const float* partials, float* d_mu, float* d_quat, float* d_scale,
-                       float* d_opac, float* d_rgb, float* pose_part, const int32_t* gate,
-                       cudaStream_t st);
+                       const float* proj, const float* partials, float* d_mu, float* d_quat,
+                       float* d_scale, float* d_opac, float* d_rgb, float* pose_part,
+                       const int32_t* gate, cudaStream_t st);
 int pose_reduce_launch(const float* part, int n_part, float* out, const int32_t* gate,
                        cudaStream_t st);
 

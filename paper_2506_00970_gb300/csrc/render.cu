@@ -295,7 +295,8 @@ __global__ void __launch_bounds__(256) surfel_grad_kernel(
     const float* __restrict__ mu, const float* __restrict__ quat, const float* __restrict__ scale,
     int n, const int32_t* __restrict__ active, int accumulate, const float* __restrict__ pose,
     const int32_t* __restrict__ tiles, const uint32_t* __restrict__ surfel_off,
-    int Q, const float* __restrict__ partials, float* __restrict__ d_mu,
+    int Q, const float* __restrict__ proj, const float* __restrict__ partials,
+    float* __restrict__ d_mu,
     float* __restrict__ d_quat, float* __restrict__ d_scale, float* __restrict__ d_opac,
     float* __restrict__ d_rgb, float* __restrict__ pose_part, int n_all,
     const int32_t* __restrict__ gate) {
@@ -336,18 +337,29 @@ __global__ void __launch_bounds__(256) surfel_grad_kernel(
     const F3 mu_c = mat_mul(R, f3(mu[3 * sid], mu[3 * sid + 1], mu[3 * sid + 2])) + f3(sp[9], sp[10], sp[11]);
     const F3 tuc = mat_mul(R, tu), tvc = mat_mul(R, tv), tnc = mat_mul(R, tn);
     const float su = scale[2 * sid], sv = scale[2 * sid + 1];
-    const F3 g_muc = f3(S[0], S[1], S[2]);
-    const F3 g_mu = f3(S[3], S[4], S[5]), g_mv = f3(S[6], S[7], S[8]);
-    const F3 g_tnc = f3(S[13], S[14], S[15]);
+    // sum Gv, sum u Gv, sum v Gv from the moment sums and the record's
+    // n, d_u, d_v and opacity (a surfel in no tile has all sums zero)
+    F3 g_muc = f3(0.f, 0.f, 0.f), g_mu = g_muc, g_mv = g_muc;
+    if (k > 0) {
+      const float* rec = proj + (size_t)i * kProjFloats;
+      const F3 nrm = f3(rec[kNrm], rec[kNrm + 1], rec[kNrm + 2]);
+      const F3 du = f3(rec[kDu], rec[kDu + 1], rec[kDu + 2]);
+      const F3 dv = f3(rec[kDv], rec[kDv + 1], rec[kDv + 2]);
+      const float op = rec[kAlpha];
+      g_muc = S[0] * nrm + op * (S[4] * du + S[5] * dv);
+      g_mu = S[1] * nrm + op * (S[6] * du + S[7] * dv);
+      g_mv = S[2] * nrm + op * (S[7] * du + S[8] * dv);
+    }
+    const F3 g_tnc = f3(S[12], S[13], S[14]);
     const F3 g_tuc = su * g_mu, g_tvc = sv * g_mv;
     // o(p, v): write, or add when accumulating over views
     auto o = [&](float* p, float v) { *p = accumulate ? *p + v : v; };
     o(d_scale + 2 * sid, dot3(tuc, g_mu));
     o(d_scale + 2 * sid + 1, dot3(tvc, g_mv));
-    o(d_opac + sid, S[9]);
-    o(d_rgb + 3 * sid, S[10]);
-    o(d_rgb + 3 * sid + 1, S[11]);
-    o(d_rgb + 3 * sid + 2, S[12]);
+    o(d_opac + sid, S[3]);
+    o(d_rgb + 3 * sid, S[9]);
+    o(d_rgb + 3 * sid + 1, S[10]);
+    o(d_rgb + 3 * sid + 2, S[11]);
     const F3 th = cross3(mu_c, g_muc) + cross3(tuc, g_tuc) + cross3(tvc, g_tvc) + cross3(tnc, g_tnc);
     pr[0] = g_muc.x; pr[1] = g_muc.y; pr[2] = g_muc.z;
     pr[3] = th.x; pr[4] = th.y; pr[5] = th.z;
@@ -501,12 +513,12 @@ int track_tile_launch(const float* proj, const gs2d_bins* bins, const gs2d_camer
 
 int surfel_grad_launch(const gs2d_surfels* s, const int32_t* active, int m, int accumulate,
                        const float* pose, const int32_t* tiles, const uint32_t* surfel_off, int Q,
-                       const float* partials, float* d_mu, float* d_quat, float* d_scale,
-                       float* d_opac, float* d_rgb, float* pose_part, const int32_t* gate,
-                       cudaStream_t st) {
+                       const float* proj, const float* partials, float* d_mu, float* d_quat,
+                       float* d_scale, float* d_opac, float* d_rgb, float* pose_part,
+                       const int32_t* gate, cudaStream_t st) {
   if (m <= 0) return GS2D_OK;
   surfel_grad_kernel<<<(m + 255) / 256, 256, 0, st>>>(s->mu, s->quat, s->scale, m, active,
-                                                      accumulate, pose, tiles, surfel_off, Q,
+                                                      accumulate, pose, tiles, surfel_off, Q, proj,
                                                       partials,
                                                       d_mu, d_quat, d_scale, d_opac, d_rgb,
                                                       pose_part, s->n, gate);
@@ -563,7 +575,8 @@ int render_bwd_launch(const float* proj, const gs2d_bins* bins, const int32_t* t
     if (s->n > 0) {
       const int nb = (s->n + 255) / 256;
       surfel_grad_kernel<<<nb, 256, 0, st>>>(s->mu, s->quat, s->scale, s->n, nullptr, 0, pose,
-                                             tiles_per_surfel, bins->surfel_off, Q, w.partials, d_mu,
+                                             tiles_per_surfel, bins->surfel_off, Q, proj,
+                                             w.partials, d_mu,
                                              d_quat, d_scale, d_opac, d_rgb_out, w.pose_part, s->n,
                                              gate);
       GS2D_LAUNCH_CHECK();

@@ -383,24 +383,6 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ proj,
   }
 }
 
-// Butterfly reduce-scatter of 16 values over a warp: afterwards lane l holds
-// the warp sum of value (l >> 1) in v[0].
-__device__ __forceinline__ void warp_reduce_scatter16(float (&v)[kRedVals], int lane) {
-#pragma unroll
-  for (int lvl = 0; lvl < 4; ++lvl) {
-    const int off = 16 >> lvl;
-    const int half = 8 >> lvl;
-    const bool up = (lane & off) != 0;
-#pragma unroll
-    for (int i = 0; i < half; ++i) {
-      const float send = up ? v[i] : v[i + half];
-      const float keep = up ? v[i + half] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-    }
-  }
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-}
-
 // Shared-memory scratch of the pose-only backward loops: the staged
 // records and the tile's largest blended-entry count.
 struct BwdSmem {
