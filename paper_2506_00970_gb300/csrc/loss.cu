@@ -67,42 +67,50 @@ __global__ void __launch_bounds__(256) sum_parts_kernel(const float* __restrict_
 // pixels whose own and 4-neighbour opacities exceed 0.5.  The normal term's
 // gradient w.r.t. the depth of pixel q collects the four stencils that use
 // q, recomputed here (a gather, so no atomics).
-struct MapCtx {
-  const float* depth;
-  const float* opac;
-  const float* normal;
-  gs2d_camera cam;
+// Tiles of 32 x 8 pixels; a block strides over tiles in a fixed order.
+// Phase 0 stages D/O and O of the tile and a two-pixel ring in shared
+// memory; phase 1 evaluates the normal term once for every position of the
+// tile and its one-pixel edge ring (the four neighbours' stencils read it);
+// phase 2 forms each pixel's outputs, gathering the neighbours' gradients
+// w.r.t. its back-projected point from there.
+constexpr int kMapTW = 32, kMapTH = 8;
+constexpr int kMapRW = kMapTW + 2, kMapRH = kMapTH + 2;  // with the ring
+constexpr int kMapSW = kMapTW + 4, kMapSH = kMapTH + 4;  // with two rings
+struct MapSmem {
+  float dh[kMapSH][kMapSW];     // D / max(O, 1e-6); 0 outside the image
+  float op[kMapSH][kMapSW];     // O; 0 outside the image
+  float g[kMapRH][kMapRW][12];  // dL_n / dX of the four stencil points
+  float ln[kMapTH][kMapTW];     // L_n of the tile's own pixels
+  float gn[kMapTH][kMapTW][3];  // dL_n / dN_r of the tile's own pixels
+  bool ok[kMapRH][kMapRW];
 };
 
 __device__ __forceinline__ F3 ray_of(const gs2d_camera& cam, int px, int py) {
   return f3((px + 0.5f - cam.cx) / cam.fx, (py + 0.5f - cam.cy) / cam.fy, 1.f);
 }
-__device__ __forceinline__ float dhat(const MapCtx& c, int i) {
-  return c.depth[i] / fmaxf(c.opac[i], 1e-6f);
-}
-__device__ __forceinline__ bool ln_valid(const MapCtx& c, int px, int py) {
-  const int W = c.cam.width, H = c.cam.height;
+// Normal term at pixel (px, py), staged at (sx, sy) of the two-ring arrays:
+// returns L_n (false if invalid: border pixel, own or a 4-neighbour's
+// opacity <= 0.5, degenerate cross product) and the gradients of L_n w.r.t.
+// X(p+ex), X(p-ex), X(p+ey), X(p-ey) and N_r(p).
+__device__ bool ln_eval(const MapSmem& sm, const float* __restrict__ normal,
+                        const gs2d_camera& cam, int px, int py, int sx, int sy, float& Ln,
+                        F3 g[4], F3& gNr) {
+  const int W = cam.width, H = cam.height;
   if (px < 1 || py < 1 || px > W - 2 || py > H - 2) return false;
+  if (!(sm.op[sy][sx] > 0.5f && sm.op[sy][sx - 1] > 0.5f && sm.op[sy][sx + 1] > 0.5f &&
+        sm.op[sy - 1][sx] > 0.5f && sm.op[sy + 1][sx] > 0.5f))
+    return false;
   const int i = py * W + px;
-  return c.opac[i] > 0.5f && c.opac[i - 1] > 0.5f && c.opac[i + 1] > 0.5f && c.opac[i - W] > 0.5f &&
-         c.opac[i + W] > 0.5f;
-}
-// Normal term at pixel p: returns L_n (0 if invalid) and the gradients of
-// L_n w.r.t. X(p+ex), X(p-ex), X(p+ey), X(p-ey) and N_r(p).
-__device__ bool ln_eval(const MapCtx& c, int px, int py, float& Ln, F3 g[4], F3& gNr) {
-  if (!ln_valid(c, px, py)) return false;
-  const int W = c.cam.width;
-  const int i = py * W + px;
-  const F3 Xr = dhat(c, i + 1) * ray_of(c.cam, px + 1, py);
-  const F3 Xl = dhat(c, i - 1) * ray_of(c.cam, px - 1, py);
-  const F3 Xd = dhat(c, i + W) * ray_of(c.cam, px, py + 1);
-  const F3 Xu = dhat(c, i - W) * ray_of(c.cam, px, py - 1);
+  const F3 Xr = sm.dh[sy][sx + 1] * ray_of(cam, px + 1, py);
+  const F3 Xl = sm.dh[sy][sx - 1] * ray_of(cam, px - 1, py);
+  const F3 Xd = sm.dh[sy + 1][sx] * ray_of(cam, px, py + 1);
+  const F3 Xu = sm.dh[sy - 1][sx] * ray_of(cam, px, py - 1);
   const F3 gx = 0.5f * (Xr - Xl), gy = 0.5f * (Xd - Xu);
   const F3 n = cross3(gx, gy);
   const float nn = sqrtf(dot3(n, n));
   if (!(nn > 0.f)) return false;
   const F3 ND = (1.f / nn) * n;
-  const F3 Nr = f3(c.normal[3 * i], c.normal[3 * i + 1], c.normal[3 * i + 2]);
+  const F3 Nr = f3(normal[3 * i], normal[3 * i + 1], normal[3 * i + 2]);
   const float dp = dot3(ND, Nr);
   Ln = 1.f - dp;
   gNr = (-1.f) * ND;
@@ -116,20 +124,6 @@ __device__ bool ln_eval(const MapCtx& c, int px, int py, float& Ln, F3 g[4], F3&
   return true;
 }
 
-// Tiles of 32 x 8 pixels; a block strides over tiles in a fixed order.
-// Phase 1 evaluates the normal term once for every position of the tile and
-// its one-pixel edge ring (the four neighbours' stencils read it) into
-// shared memory; phase 2 forms each pixel's outputs, gathering the
-// neighbours' gradients w.r.t. its back-projected point from there.
-constexpr int kMapTW = 32, kMapTH = 8;
-constexpr int kMapRW = kMapTW + 2, kMapRH = kMapTH + 2;  // with the ring
-struct MapSmem {
-  float g[kMapRH][kMapRW][12];  // dL_n / dX of the four stencil points
-  float ln[kMapTH][kMapTW];     // L_n of the tile's own pixels
-  float gn[kMapTH][kMapTW][3];  // dL_n / dN_r of the tile's own pixels
-  bool ok[kMapRH][kMapRW];
-};
-
 __global__ void __launch_bounds__(kLossThreads) mapping_loss_kernel(
     const float* __restrict__ rgb, const float* __restrict__ depth, const float* __restrict__ normal,
     const float* __restrict__ opac, const float* __restrict__ obs_rgb,
@@ -140,11 +134,24 @@ __global__ void __launch_bounds__(kLossThreads) mapping_loss_kernel(
   __shared__ MapSmem sm;
   const int W = cam.width, H = cam.height, P = W * H;
   const float inv = 1.f / (float)P;
-  const MapCtx c{depth, opac, normal, cam};
   const int tiles_x = (W + kMapTW - 1) / kMapTW, tiles_y = (H + kMapTH - 1) / kMapTH;
   float acc = 0.f;
   for (int tile = blockIdx.x; tile < tiles_x * tiles_y; tile += gridDim.x) {
     const int x0 = (tile % tiles_x) * kMapTW, y0 = (tile / tiles_x) * kMapTH;
+    __syncthreads();
+    // phase 0: D/O and O on the tile and two rings
+    for (int e = threadIdx.x; e < kMapSW * kMapSH; e += blockDim.x) {
+      const int sy = e / kMapSW, sx = e % kMapSW;
+      const int px = x0 + sx - 2, py = y0 + sy - 2;
+      float d = 0.f, o = 0.f;
+      if (px >= 0 && py >= 0 && px < W && py < H) {
+        const int i = py * W + px;
+        o = opac[i];
+        d = depth[i] / fmaxf(o, 1e-6f);
+      }
+      sm.dh[sy][sx] = d;
+      sm.op[sy][sx] = o;
+    }
     __syncthreads();
     // phase 1: the normal term on the tile and its ring
     for (int e = threadIdx.x; e < kMapRW * kMapRH; e += blockDim.x) {
@@ -156,7 +163,7 @@ __global__ void __launch_bounds__(kLossThreads) mapping_loss_kernel(
       F3 g4[4], gNr = f3(0.f, 0.f, 0.f);
       bool ok = false;
       if ((tile_px || ring) && px >= 0 && py >= 0 && px < W && py < H)
-        ok = ln_eval(c, px, py, Ln, g4, gNr);
+        ok = ln_eval(sm, normal, cam, px, py, rx + 1, ry + 1, Ln, g4, gNr);
       sm.ok[ry][rx] = ok;
       if (ok)
 #pragma unroll
@@ -178,10 +185,10 @@ __global__ void __launch_bounds__(kLossThreads) mapping_loss_kernel(
     const int px = x0 + lx, py = y0 + ly;
     if (px < W && py < H) {
       const int i = py * W + px;
-      const float O = opac[i];
+      const float O = sm.op[ly + 2][lx + 2];
       const float Oc = fmaxf(O, 1e-6f);
       const float D = depth[i];
-      const float Dh = D / Oc;
+      const float Dh = sm.dh[ly + 2][lx + 2];
       const float d0 = rgb[3 * i] - obs_rgb[3 * i];
       const float d1 = rgb[3 * i + 1] - obs_rgb[3 * i + 1];
       const float d2 = rgb[3 * i + 2] - obs_rgb[3 * i + 2];
