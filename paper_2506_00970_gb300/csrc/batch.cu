@@ -41,14 +41,64 @@ __device__ __forceinline__ int view_of(const ViewTable& tab, int item) {
   return v;
 }
 
+// Work order of the persistent passes: every (view, tile) item sorted by
+// decreasing list length (a counting sort on the length's octave and its
+// next three bits), so the heaviest tiles start first and the launch ends on
+// short items instead of idling SMs behind a late long one.  Items of a view
+// with a failed status sort last.  Results do not depend on the order (each
+// item writes only its own pixels and partial slots).
+constexpr int kOrderBuckets = 256;
+constexpr int kOrderThreads = 1024;
+__device__ __forceinline__ int length_bucket(uint32_t len) {
+  if (len < 16u) return (int)len;
+  const int oct = 31 - __clz(len);  // >= 4
+  return 16 + (oct - 4) * 8 + (int)((len >> (oct - 3)) & 7u);  // <= 239
+}
+__global__ void __launch_bounds__(kOrderThreads) order_items_kernel(ViewTable tab,
+                                                                  int32_t* __restrict__ order) {
+  __shared__ uint32_t hist[kOrderBuckets];
+  for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) hist[b] = 0u;
+  __syncthreads();
+  for (int v = 0; v < tab.n_views; ++v) {
+    const ViewDev& V = tab.v[v];
+    const bool dead = V.status && *V.status;
+    for (int t = threadIdx.x; t < V.n_tiles; t += blockDim.x) {
+      const uint32_t len = dead ? 0u : (uint32_t)max(V.ranges[2 * t + 1] - V.ranges[2 * t], 0);
+      atomicAdd(&hist[length_bucket(len)], 1u);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // exclusive scan, longest bucket first
+    uint32_t run = 0u;
+    for (int b = kOrderBuckets - 1; b >= 0; --b) {
+      const uint32_t c = hist[b];
+      hist[b] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int v = 0; v < tab.n_views; ++v) {
+    const ViewDev& V = tab.v[v];
+    const bool dead = V.status && *V.status;
+    for (int t = threadIdx.x; t < V.n_tiles; t += blockDim.x) {
+      const uint32_t len = dead ? 0u : (uint32_t)max(V.ranges[2 * t + 1] - V.ranges[2 * t], 0);
+      order[atomicAdd(&hist[length_bucket(len)], 1u)] = V.item0 + t;
+    }
+  }
+}
+
 template <int P>
 __global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 4 : 2)) fwd_batch_kernel(ViewTable tab,
-                                                                 uint32_t* __restrict__ queue) {
+                                                                 uint32_t* __restrict__ queue,
+                                                                 const int32_t* __restrict__ order) {
   __shared__ float4 s_rec[kTileThreads][kFwdVec4];
   __shared__ HitLists hl;
   __shared__ int s_item;
   while (true) {
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
+    if (threadIdx.x == 0) {
+      const int k = (int)atomicAdd(queue, 1u);
+      s_item = k < tab.n_items ? order[k] : tab.n_items;
+    }
     __syncthreads();
     const int item = s_item;
     __syncthreads();
@@ -87,9 +137,10 @@ __global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 4 : 2)) f
 
 // Full backward of every view: persistent warps take (tile, region) work
 // units (Q regions per tile, the same for every view of a launch) from an
-// atomic counter; each unit is the single-view replay of bwd_warp.cuh.
+// atomic counter, items in the heavy-first order; each unit is the
+// single-view replay of bwd_warp.cuh.
 __global__ void __launch_bounds__(kBwdWarps * 32, kBwdWarpBlocks) bwd_batch_kernel(
-    ViewTable tab, int Q, uint32_t* __restrict__ queue) {
+    ViewTable tab, int Q, uint32_t* __restrict__ queue, const int32_t* __restrict__ order) {
   __shared__ WarpBwdSmem<kBwdRegion> sm[kBwdWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_units = tab.n_items * Q;
@@ -98,7 +149,8 @@ __global__ void __launch_bounds__(kBwdWarps * 32, kBwdWarpBlocks) bwd_batch_kern
     if (lane == 0) u = atomicAdd(queue, 1u);
     const int unit = (int)__shfl_sync(0xffffffffu, u, 0);
     if (unit >= n_units) return;
-    const int item = unit / Q, region = unit - item * Q;
+    const int slot = unit / Q, region = unit - slot * Q;
+    const int item = order[slot];
     const ViewDev& V = tab.v[view_of(tab, item)];
     if (V.status && *V.status) continue;
     const int tile = item - V.item0;
@@ -135,6 +187,7 @@ int check_view(const gs2d_view& w) {
 
 struct BatchWs {
   uint32_t* queue;        // [2] fwd, bwd work counters
+  int32_t* order;         // [items] heavy-first work order
   float* partials[GS2D_MAX_VIEWS];
   float* pose_part;       // [max parts * 6]
   size_t bytes;
@@ -144,6 +197,12 @@ BatchWs carve_batch_ws(void* base, const gs2d_view* views, int n_views, int n) {
   Carver c(base);
   BatchWs w{};
   w.queue = c.take<uint32_t>(64);
+  size_t items = 0;
+  for (int v = 0; v < n_views; ++v) {
+    int tx;
+    items += (size_t)max(view_tiles(views[v], &tx), 0);
+  }
+  w.order = c.take<int32_t>(items > 0 ? items : 1);
   int max_parts = 1;
   for (int v = 0; v < n_views; ++v) {
     const size_t cap = views[v].bins.capacity > 0 ? views[v].bins.capacity : 1;
@@ -302,11 +361,13 @@ int gs2d_render_fwd_batch(const gs2d_view* views, int n_views, void* workspace, 
   const BatchWs w = carve_batch_ws(workspace, views, n_views, 0);
   zero_words_kernel<<<1, 64, 0, st>>>(w.queue, 2);
   GS2D_LAUNCH_CHECK();
+  order_items_kernel<<<1, kOrderThreads, 0, st>>>(tab, w.order);
+  GS2D_LAUNCH_CHECK();
   GS2D_DISPATCH_P(views[0].cfg.px_per_thread, {
     const int grid = min(persistent_grid(reinterpret_cast<const void*>(fwd_batch_kernel<P>)),
                          tab.n_items);
     if (grid <= 0) return GS2D_ERR_CUDA;
-    fwd_batch_kernel<P><<<grid, kTileThreads, 0, st>>>(tab, w.queue);
+    fwd_batch_kernel<P><<<grid, kTileThreads, 0, st>>>(tab, w.queue, w.order);
   });
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
@@ -333,12 +394,14 @@ int gs2d_render_bwd_batch(const gs2d_view* views, int n_views, const gs2d_surfel
   cudaStream_t st = (cudaStream_t)stream;
   zero_words_kernel<<<1, 64, 0, st>>>(w.queue, 2);
   GS2D_LAUNCH_CHECK();
+  order_items_kernel<<<1, kOrderThreads, 0, st>>>(tab, w.order);
+  GS2D_LAUNCH_CHECK();
   const int Q = bwd_regions(views[0].cfg);
   const int grid = min(persistent_grid(reinterpret_cast<const void*>(bwd_batch_kernel),
                                        kBwdWarps * 32),
                        (tab.n_items * Q + kBwdWarps - 1) / kBwdWarps);
   if (grid <= 0) return GS2D_ERR_CUDA;
-  bwd_batch_kernel<<<grid, kBwdWarps * 32, 0, st>>>(tab, Q, w.queue + 1);
+  bwd_batch_kernel<<<grid, kBwdWarps * 32, 0, st>>>(tab, Q, w.queue + 1, w.order);
   GS2D_LAUNCH_CHECK();
   // surfels outside every view's subset receive zero: clear, then add view by view
   GS2D_CUDA_TRY(cudaMemsetAsync(d_mu, 0, sizeof(float) * 3 * s->n, st));
