@@ -114,7 +114,8 @@ __global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 4 : 2)) f
     const int tile_y0 = (tile / V.tiles_x) * V.cfg.tile_h;
     const float xt = (float)tile_x0 + 0.5f - V.cam.cx, yt = (float)tile_y0 + 0.5f - V.cam.cy;
     FwdState st[P];
-    fwd_tile<kFwdVec4, false, P>(V.proj, V.vals, V.ranges[2 * tile], V.ranges[2 * tile + 1], xt, yt,
+    const int start = V.ranges[2 * tile];
+    fwd_tile<kFwdVec4, false, P>(V.proj, V.vals + start, start, V.ranges[2 * tile + 1], xt, yt,
                                  tile_x0, tile_y0, tp, inside, V.cam, V.cfg, s_rec, hl, nullptr,
                                  st);
 #pragma unroll

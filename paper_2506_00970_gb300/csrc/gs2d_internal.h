@@ -38,14 +38,20 @@ int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* p
 // kSortLongInBlock -- tiles with segments over 2048 keys are sorted by their
 // own 256-thread block (chunks + merges) instead of a separate launch.
 // kSortPreScanned -- a fused projection already counted and scanned the
-// tiles (implies pre-zeroed counters; no emission offsets).
-constexpr unsigned kSortPreZeroed = 1u, kSortLongInBlock = 2u, kSortPreScanned = 4u;
+// tiles (implies pre-zeroed counters; no emission offsets);
+// kSortInTileKernel -- no per-tile sort launch: the tile kernel that reads
+// the bins sorts each tile's segment itself (sort_seg_args).
+constexpr unsigned kSortPreZeroed = 1u, kSortLongInBlock = 2u, kSortPreScanned = 4u,
+                   kSortInTileKernel = 8u;
 int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
                     const gs2d_camera* cam, const gs2d_config* cfg, void* workspace,
                     size_t ws_bytes, size_t* ws_needed, const gs2d_bins* bins, bool need_emit,
                     cudaStream_t st, unsigned flags = 0u);
 // Pointers of a sort workspace for a fused projection.
 SortFuse sort_fuse_args(void* workspace, int n, const gs2d_bins* bins, int tiles_x, int n_tiles);
+// The unsorted segment keys and the merge buffer of a sort workspace.
+void sort_seg_args(void* workspace, int n, size_t capacity, int n_tiles,
+                   unsigned long long** seg_keys, unsigned long long** seg_tmp);
 // The counter region of a sort workspace that every binning needs zeroed.
 void sort_zero_region(void* workspace, int n, size_t capacity, int n_tiles, uint32_t** begin,
                       size_t* words);
@@ -78,6 +84,11 @@ struct TrackStep {
   uint32_t* sort_zero;   // binning counters the last block zeroes for the next
   size_t sort_zero_words;  // iteration's binning (kSortPreZeroed)
   const int32_t* order;    // block b runs tile order[b] (or b when NULL)
+  // the binning's unsorted tile segments (kSortInTileKernel): each block
+  // sorts its own tile's keys; seg_tmp is the merge buffer of long segments
+  unsigned long long* seg_keys;
+  unsigned long long* seg_tmp;
+  int n;  // surfels (ids are clamped below it)
 };
 
 // Fused tracking iteration per tile (forward, tracking loss, pose backward)

@@ -43,6 +43,7 @@
 #include "gs2d_internal.h"
 #include "loss_pixel.cuh"
 #include "tile_loops.cuh"
+#include "tile_sort.cuh"
 #include "track_update.cuh"
 
 namespace gs2d {
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<P, kG>()) ren
   const float yt = (float)tile_y0 + 0.5f - cam.cy;
   uint32_t cnt[5] = {0u, 0u, 0u, 0u, 0u};
   FwdState st[P];
-  fwd_tile<kFwdVec4, kCount, P, kG>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt,
+  fwd_tile<kFwdVec4, kCount, P, kG>(proj, vals + ranges[2 * tile], ranges[2 * tile], ranges[2 * tile + 1], xt, yt,
                                     tile_x0, tile_y0, tp, inside, cam, cfg, s_rec, hl, cnt, st);
   if (kCount) {
 #pragma unroll
@@ -160,10 +161,10 @@ __global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) r
   load_pix_grads<P>(tp, inside, cam, T_final, n_last, g_rgb, g_depth, g_normal, g_opac, pg);
   float pr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (g_normal)
-    bwd_tile_pose<true, P>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0,
+    bwd_tile_pose<true, P>(proj, vals + ranges[2 * tile], ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0,
                            tile_y0, tp, inside, rx, ry, cam, cfg, pg, sm, hl, pr);
   else
-    bwd_tile_pose<false, P>(proj, vals, ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0,
+    bwd_tile_pose<false, P>(proj, vals + ranges[2 * tile], ranges[2 * tile], ranges[2 * tile + 1], xt, yt, tile_x0,
                             tile_y0, tp, inside, rx, ry, cam, cfg, pg, sm, hl, pr);
   block_sum6(pr, s_pose, pose_part + (size_t)tile * 6);
 }
@@ -190,13 +191,17 @@ __global__ void __launch_bounds__(kBwdWarps * 32, kBwdWarpBlocks) render_bwd_war
                          sm[warp]);
 }
 
-// Fused tracking iteration on one tile: forward compositing, the tracking
-// loss and its image gradient per pixel (in registers), and the pose-only
-// backward replay -- the images never leave the chip.  Writes the tile's
-// loss partial (already divided by |Omega|) and pose 6-vector partial.
+// Fused tracking iteration on one tile: the depth sort of the tile's
+// segment, forward compositing, the tracking loss and its image gradient per
+// pixel (in registers), and the pose-only backward replay -- the images never
+// leave the chip.  Writes the tile's loss partial (already divided by
+// |Omega|) and pose 6-vector partial.  A segment of at most kSegSmem keys is
+// sorted in shared memory and its ids stay there; a longer one is sorted in
+// chunks merged in global memory and its ids written to vals, which this
+// block then reads back (coherent loads: vals is written in this launch).
 template <int P, int kG = 1>
 __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<P, kG>()) track_tile_kernel(
-    const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
+    const float4* __restrict__ proj, uint32_t* vals,
     const int32_t* __restrict__ ranges, gs2d_camera cam, gs2d_config cfg, int tiles_x,
     const float* __restrict__ obs_rgb, const float* __restrict__ obs_depth, gs2d_track_params prm,
     float* __restrict__ loss_part, float* __restrict__ pose_part, TrackStep ts,
@@ -206,6 +211,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<P, kG>()) tra
   __shared__ float s_pose[kTileThreads / 32][6];
   __shared__ float s_loss[kTileThreads / 32];
   __shared__ bool s_last;
+  __shared__ uint32_t s_ids[kSegSmem];
   {
     const int32_t g = *status;
     if (g != 0) {
@@ -226,8 +232,30 @@ __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<P, kG>()) tra
   const float yt = (float)tile_y0 + 0.5f - cam.cy;
   const float rx = (tp.px + 0.5f - cam.cx) / cam.fx, ry = (tp.py + 0.5f - cam.cy) / cam.fy;
   const int start = ranges[2 * tile], end = ranges[2 * tile + 1];
+  // the segment's depth order, keys (depth bits << 32 | id) sorted in the
+  // record staging area before any record is staged
+  const uint32_t* ids;
+  {
+    const int len = end - start;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(&sm.rec[0][0]);
+    static_assert(sizeof(sm.rec) >= kSegSmem * sizeof(unsigned long long), "sort area");
+    if (len <= kSegSmem) {
+      for (int i = threadIdx.x; i < len; i += kTileThreads) keys[i] = ts.seg_keys[start + i];
+      __syncthreads();
+      bitonic_sort(keys, len);
+      for (int i = threadIdx.x; i < len; i += kTileThreads)
+        s_ids[i] = min((uint32_t)(keys[i] & 0xFFFFFFFFull), (uint32_t)(ts.n - 1));
+      __syncthreads();
+      ids = s_ids;
+    } else {
+      sort_long_segment<kSegSmem>(tile, proj, ts.n, tiles_x, ranges, ts.seg_keys, ts.seg_tmp,
+                                  nullptr, vals, nullptr, nullptr, (long long)end, keys);
+      __syncthreads();
+      ids = vals + start;
+    }
+  }
   FwdState st[P];
-  fwd_tile<kBwdVec4, false, P, kG>(proj, vals, start, end, xt, yt, tile_x0, tile_y0, tp, inside,
+  fwd_tile<kBwdVec4, false, P, kG>(proj, ids, start, end, xt, yt, tile_x0, tile_y0, tp, inside,
                                    cam, cfg, sm.rec, hl, nullptr, st);
   float pr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const float inv = 1.f / (float)(cam.width * cam.height);
@@ -266,7 +294,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<P, kG>()) tra
     }
   }
   // a list of at most one batch is still staged with its hit lists
-  bwd_tile_pose<false, P, kG>(proj, vals, start, end, xt, yt, tile_x0, tile_y0, tp, inside, rx, ry,
+  bwd_tile_pose<false, P, kG>(proj, ids, start, end, xt, yt, tile_x0, tile_y0, tp, inside, rx, ry,
                               cam, cfg, pg, sm, hl, pr, end - start <= kTileThreads);
   block_sum6(pr, s_pose, pose_part + (size_t)tile * 6);
   // the last block to finish reduces every tile's partials and updates the pose

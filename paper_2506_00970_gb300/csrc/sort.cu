@@ -30,6 +30,7 @@
 #include "gs2d_common.cuh"
 #include "gs2d_internal.h"
 #include "tile_scan.cuh"
+#include "tile_sort.cuh"
 #include "tile_walk.cuh"
 
 namespace gs2d {
@@ -40,7 +41,6 @@ constexpr int kChunk = kScanThreads * kScanItems;  // 4096 surfels per scan bloc
 constexpr int kWarps = kScanThreads / 32;
 constexpr int kSpinLimit = 1 << 22;                // default polls of a look-back wait
 constexpr int kSortThreads = 256;
-constexpr int kSegSmem = 2048;                     // keys sorted in shared memory (16 KB)
 constexpr int kLongThreads = 1024;                 // long segments: one 1024-thread block
 constexpr int kLongChunk = 16384;                  // keys per shared-memory chunk (128 KB)
 
@@ -79,15 +79,6 @@ __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* s_t
   *total = s_tmp[2 * kWarps];
   __syncthreads();
   return r;
-}
-
-struct Rect {
-  int tx0, ty0, tx1, ty1;
-};
-__device__ __forceinline__ Rect load_rect(const float4* proj, uint32_t id) {
-  const float4 rc = proj[(size_t)id * (kProjFloats / 4) + 7];
-  const uint32_t r01 = __float_as_uint(rc.x), r23 = __float_as_uint(rc.y);
-  return Rect{(int)(r01 & 0xFFFF), (int)(r01 >> 16), (int)(r23 & 0xFFFF), (int)(r23 >> 16)};
 }
 
 // Zeroes the per-call counters (tile counts and cursors, scan words, K).
@@ -288,136 +279,6 @@ __global__ void __launch_bounds__(256) scatter_kernel(
   });
 }
 
-// 4. Per-tile sort of the segment and the final outputs.  The flip-form
-// bitonic network sorts ascending with the smaller key to the lower index;
-// comparisons whose partner lies past the end are skipped (a virtual +inf).
-__device__ __forceinline__ void cmp_swap(unsigned long long* a, int i, int j) {
-  const unsigned long long x = a[i], y = a[j];
-  if (y < x) {
-    a[i] = y;
-    a[j] = x;
-  }
-}
-__device__ void bitonic_sort(unsigned long long* a, int len) {
-  int lg = 0;
-  while ((1 << lg) < len) ++lg;
-  const int pairs = (1 << lg) >> 1;
-  for (int ls = 1; ls <= lg; ++ls) {
-    // flip step: i pairs with its mirror i ^ (size - 1) inside each block of
-    // size = 2^ls (the index arithmetic in shifts: sizes are powers of two)
-    const int lh = ls - 1;
-    for (int q = threadIdx.x; q < pairs; q += blockDim.x) {
-      const int i = ((q >> lh) << ls) | (q & ((1 << lh) - 1));
-      const int j = i ^ ((1 << ls) - 1);
-      if (j < len) cmp_swap(a, i, j);
-    }
-    __syncthreads();
-    for (int lst = ls - 2; lst >= 0; --lst) {
-      for (int q = threadIdx.x; q < pairs; q += blockDim.x) {
-        const int i = ((q >> lst) << (lst + 1)) | (q & ((1 << lst) - 1));
-        const int j = i + (1 << lst);
-        if (j < len) cmp_swap(a, i, j);
-      }
-      __syncthreads();
-    }
-  }
-}
-
-__device__ __forceinline__ void write_outputs(const unsigned long long* a, int len, int start, int t,
-                                              int tiles_x, int n, const float4* __restrict__ proj,
-                                              const uint32_t* __restrict__ surfel_off,
-                                              uint32_t* __restrict__ vals, uint32_t* __restrict__ emit,
-                                              unsigned long long* __restrict__ keys64) {
-  const int tx = t % tiles_x, ty = t / tiles_x;
-  for (int i = threadIdx.x; i < len; i += blockDim.x) {
-    const unsigned long long key = a[i];
-    const uint32_t id = min((uint32_t)(key & 0xFFFFFFFFull), (uint32_t)(n - 1));
-    vals[start + i] = id;
-    if (emit) {
-      const Rect r = load_rect(proj, id);
-      const int rw = max(r.tx1 - r.tx0 + 1, 1);
-      emit[start + i] = surfel_off[id] + (uint32_t)((ty - r.ty0) * rw + (tx - r.tx0));
-    }
-    if (keys64) keys64[start + i] = ((unsigned long long)t << 32) | (key >> 32);
-  }
-}
-
-// Position in the merge of sorted runs A[0, la) and B[0, lb) (unique keys):
-// the number i of elements taken from A among the first d outputs.
-__device__ __forceinline__ int co_rank(const unsigned long long* A, int la, const unsigned long long* B,
-                                       int lb, int d) {
-  int lo = max(0, d - lb), hi = min(d, la);
-  while (lo < hi) {
-    const int i = (lo + hi) >> 1;  // i from A, d - i from B
-    if (A[i] < B[d - i - 1])
-      lo = i + 1;
-    else
-      hi = i;
-  }
-  return lo;
-}
-
-// Segments longer than kSegSmem: chunks of kLongChunk keys are sorted in
-// shared memory by 1024 threads, then adjacent sorted runs are merged in
-// global memory (seg_keys <-> seg_tmp), each thread producing a contiguous
-// span of the output located by a co-rank search.
-// One long segment (tile t) by the whole block.
-template <int kChunkKeys>
-__device__ void sort_long_segment(int t, const float4* __restrict__ proj, int n, int tiles_x,
-                                  const int32_t* __restrict__ ranges,
-                                  unsigned long long* __restrict__ seg_keys,
-                                  unsigned long long* __restrict__ seg_tmp,
-                                  const uint32_t* __restrict__ surfel_off, uint32_t* __restrict__ vals,
-                                  uint32_t* __restrict__ emit, unsigned long long* __restrict__ keys64,
-                                  long long capacity, unsigned long long* s_keys) {
-  const int start = ranges[2 * t];
-  const int end = (int)min((long long)ranges[2 * t + 1], capacity);
-  const int len = end - start;
-  if (len <= kSegSmem) return;
-  unsigned long long* src = seg_keys + start;
-  unsigned long long* dst = seg_tmp + start;
-  const int chunks = (len + kChunkKeys - 1) / kChunkKeys;
-  for (int c = 0; c < chunks; ++c) {
-    const int c0 = c * kChunkKeys, cl = min(kChunkKeys, len - c0);
-    for (int i = threadIdx.x; i < cl; i += blockDim.x) s_keys[i] = src[c0 + i];
-    __syncthreads();
-    bitonic_sort(s_keys, cl);
-    if (chunks == 1) {
-      write_outputs(s_keys, len, start, t, tiles_x, n, proj, surfel_off, vals, emit, keys64);
-      return;
-    }
-    for (int i = threadIdx.x; i < cl; i += blockDim.x) src[c0 + i] = s_keys[i];
-    __syncthreads();
-  }
-  const int span = (len + blockDim.x - 1) / blockDim.x;
-  for (int w = kChunkKeys; w < len; w <<= 1) {
-    const int p0 = min(len, (int)threadIdx.x * span), p1 = min(len, p0 + span);
-    int p = p0;
-    while (p < p1) {
-      // the run pair holding output position p
-      const int lo = (p / (2 * w)) * (2 * w);
-      const int mid = min(lo + w, len), hi = min(lo + 2 * w, len);
-      const unsigned long long* A = src + lo;
-      const unsigned long long* B = src + mid;
-      const int la = mid - lo, lb = hi - mid;
-      int i = co_rank(A, la, B, lb, p - lo);
-      int j = (p - lo) - i;
-      const int stop = min(p1, hi);
-      for (; p < stop; ++p) {
-        if (j >= lb || (i < la && A[i] < B[j]))
-          dst[p] = A[i++];
-        else
-          dst[p] = B[j++];
-      }
-    }
-    __syncthreads();
-    unsigned long long* x = src;
-    src = dst;
-    dst = x;
-  }
-  write_outputs(src, len, start, t, tiles_x, n, proj, surfel_off, vals, emit, keys64);
-}
-
 // Segments of at most kSegSmem keys: sorted in shared memory by 256 threads (and,
 // with long_here, longer ones too).
 __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(
@@ -548,6 +409,13 @@ SortFuse sort_fuse_args(void* workspace, int n, const gs2d_bins* bins, int tiles
   return f;
 }
 
+void sort_seg_args(void* workspace, int n, size_t capacity, int n_tiles,
+                   unsigned long long** seg_keys, unsigned long long** seg_tmp) {
+  const SortWs w = carve_sort_ws(workspace, n, capacity, n_tiles);
+  *seg_keys = w.seg_keys;
+  *seg_tmp = w.seg_tmp;
+}
+
 void sort_zero_region(void* workspace, int n, size_t capacity, int n_tiles, uint32_t** begin,
                       size_t* words) {
   const SortWs w = carve_sort_ws(workspace, n, capacity, n_tiles);
@@ -604,6 +472,7 @@ int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
   scatter_kernel<<<(n + 255) / 256, 256, 2 * hist_smem, st>>>(
       p4, tiles_per_surfel, n, tx, n_tiles, bins->tile_ranges, w.cursor, w.seg_keys, cap, gate);
   GS2D_LAUNCH_CHECK();
+  if (flags & kSortInTileKernel) return GS2D_OK;
   const size_t smem = (size_t)kSegSmem * sizeof(unsigned long long);
   const bool long_here = (flags & kSortLongInBlock) != 0;
   tile_sort_kernel<<<n_tiles, kSortThreads, smem, st>>>(

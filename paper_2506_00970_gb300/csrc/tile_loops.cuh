@@ -186,8 +186,9 @@ struct FwdState {
   uint32_t last;
 };
 
-// Front-to-back compositing of the thread's P pixels over its tile's list.
-// Each warp visits only the staged surfels whose footprint touches its
+// Front-to-back compositing of the thread's P pixels over its tile's list
+// (ids[0, end - start): the surfel ids of entries start .. end - 1, in
+// global or shared memory).  Each warp visits only the staged surfels whose footprint touches its
 // block; a surfel's staged record is read once for all P pixels.  With
 // kCount it counts (cnt[0..4]) evaluated pairs, pairs inside the cutoff,
 // blended pairs, and the evaluated pairs and those inside the cutoff up to
@@ -205,7 +206,7 @@ struct HitLists {
 // results; pairs after a pixel's stop are evaluated and dropped.
 template <int kStride, bool kCount, int P, int kG = 1>
 __device__ __forceinline__ void fwd_tile(const float4* __restrict__ proj,
-                                         const uint32_t* __restrict__ vals, int start, int end,
+                                         const uint32_t* ids, int start, int end,
                                          float xt, float yt, int tile_x0, int tile_y0,
                                          const TilePix<P>& tp, const bool (&inside)[P],
                                          const gs2d_camera& cam, const gs2d_config& cfg,
@@ -237,7 +238,7 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ proj,
     if (__syncthreads_count(!all_done) == 0) break;
     const int idx = b + (int)threadIdx.x;
     if (idx < end) {
-      stage_record<kStride>(proj, vals[idx], xt, yt, s_rec);
+      stage_record<kStride>(proj, ids[idx - start], xt, yt, s_rec);
       const float4 rf = s_rec[threadIdx.x][kFp];
       hl.mask[threadIdx.x] = kStride == kFwdVec4
                                  ? footprint_mask<P>(rf.y, rf.z, tile_x0, tile_y0, cfg.tile_w)
@@ -454,7 +455,7 @@ __device__ __forceinline__ void pose_pair(const Eval& e, const float4 r2, const 
 // pixel's last blended one are skipped per pixel as always.
 template <bool kNormal, int P, int kG = 1>
 __device__ __forceinline__ void bwd_tile_pose(const float4* __restrict__ proj,
-                                              const uint32_t* __restrict__ vals, int start, int end,
+                                              const uint32_t* ids, int start, int end,
                                               float xt, float yt, int tile_x0, int tile_y0,
                                               const TilePix<P>& tp, const bool (&inside)[P],
                                               float rx, float ry, const gs2d_camera& cam,
@@ -503,7 +504,7 @@ __device__ __forceinline__ void bwd_tile_pose(const float4* __restrict__ proj,
     } else {
       __syncthreads();
       if ((int)threadIdx.x < cnt) {
-        stage_record<kBwdVec4>(proj, vals[bstart + (int)threadIdx.x], xt, yt, sm.rec);
+        stage_record<kBwdVec4>(proj, ids[bstart - start + (int)threadIdx.x], xt, yt, sm.rec);
         const float4 rf = sm.rec[threadIdx.x][6];
         hl.mask[threadIdx.x] = footprint_mask<P>(rf.z, rf.w, tile_x0, tile_y0, cfg.tile_w);
       }
