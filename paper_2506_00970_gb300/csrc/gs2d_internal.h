@@ -23,7 +23,15 @@ struct SortFuse {
   uint32_t* done;   // block completion counter (zeroed before the launch)
   int tiles_x, n_tiles, long_len;
   int32_t* order;   // [n_tiles] launch order of the tiles, longest lists first (or NULL)
+  // scatter fused into the projection (NULL: not fused): after a grid-wide
+  // barrier every block writes its own pairs' keys into the tile segments
+  unsigned long long* seg_keys;
+  uint32_t* cursor;  // [n_tiles] slots claimed per tile (zeroed before the launch)
+  uint32_t* bar;     // grid barrier counter (zeroed before the launch)
 };
+// Whether the projection can also scatter the pairs (its tile histograms
+// fit in shared memory).
+bool project_can_fuse_scatter(int n_tiles);
 
 // Per-surfel projection; with fuse, also the binning's tile counts and scan
 // (the binning then runs with kSortPreScanned).

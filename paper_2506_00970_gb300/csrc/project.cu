@@ -227,6 +227,36 @@ __global__ void __launch_bounds__(256) project_kernel(
 // Tile counters a fused projection keeps in shared memory (larger tile grids
 // count with global atomics).
 constexpr int kHistTiles = 2048;
+constexpr int kGridSpins = 1 << 22;  // polls of the grid barrier before it reports a timeout
+
+// Grid-wide barrier of a cooperative launch (every block resident): block
+// arrivals counted on *bar (zeroed before the launch), thread 0 polls with a
+// bounded wait; past the limit it records GS2D_ERR_TIMEOUT in *status and
+// the block returns false (all later kernels skip on the status).
+__device__ __forceinline__ bool grid_sync(uint32_t* bar, uint32_t blocks, int32_t* status,
+                                          int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int ok = 1;
+    for (int i = 0;; ++i) {
+      uint32_t v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (v >= blocks) break;
+      if (i >= kGridSpins) {
+        atomicExch(status, (int32_t)GS2D_ERR_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
 
 __global__ void __launch_bounds__(256) project_fused_kernel(
     const float* __restrict__ mu, const float* __restrict__ quat, const float* __restrict__ scale,
@@ -288,6 +318,75 @@ __global__ void __launch_bounds__(256) project_fused_kernel(
   if (local)
     for (int t = threadIdx.x; t < fz.n_tiles; t += blockDim.x)
       if (s_hist[t]) atomicAdd(fz.tile_count + t, s_hist[t]);
+  if (fz.seg_keys && local) {
+    // fused scatter (a cooperative launch): once every block's counts are
+    // in, each block scans them itself, claims its slots in the tiles it
+    // touches and writes its pairs' keys (depth bits << 32 | id), exactly as
+    // the binning's scatter kernel would; block 0 also writes the tile
+    // ranges, K, the capacity check and the launch order
+    __shared__ int s_ok;
+    if (!grid_sync(fz.bar, gridDim.x, status, &s_ok)) return;
+    uint32_t* s_start = reinterpret_cast<uint32_t*>(s_out);             // [kHistTiles]
+    uint32_t* s_n = s_start + kHistTiles;                               // [257]
+    unsigned long long* s_key = reinterpret_cast<unsigned long long*>(s_n + 264);  // [256]
+    constexpr int kPer = kHistTiles / 256;
+    const int per = (fz.n_tiles + 255) / 256;
+    const int t0 = (int)threadIdx.x * per;
+    uint32_t c[kPer];
+    uint32_t sum = 0u;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      c[k] = (k < per && t0 + k < fz.n_tiles) ? __ldcg(fz.tile_count + t0 + k) : 0u;
+      sum += c[k];
+    }
+    uint32_t K;
+    uint32_t run = block_exscan256<uint32_t>(sum, s_w, &K);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k)
+      if (k < per && t0 + k < fz.n_tiles) {
+        s_start[t0 + k] = run;
+        run += c[k];
+      }
+    if (blockIdx.x == 0)
+      tile_scan_order_small<kPer>(fz.tile_count, fz.n_tiles, fz.ranges, fz.n_isect, fz.capacity,
+                                  fz.long_list, fz.n_long, fz.long_len, status, fz.order, s_n,
+                                  s_w);
+    __syncthreads();
+    if ((unsigned long long)K > (unsigned long long)fz.capacity) return;  // block 0 flagged it
+    for (int t = threadIdx.x; t < fz.n_tiles; t += blockDim.x) {
+      const uint32_t cb = s_hist[t];
+      if (cb) s_hist[t] = s_start[t] + atomicAdd(fz.cursor + t, cb);
+    }
+    __syncthreads();
+    const unsigned long long* wkey = s_key + (threadIdx.x & ~31);
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+      const int i = base + (int)threadIdx.x;
+      int k = 0, tx0 = 1, ty0 = 1, tx1 = 0;
+      unsigned long long key = 0ull;
+      if (i < n) {
+        k = max(tiles_out[i], 0);
+        if (k > 0) {
+          // this block wrote the record: read it back past L1
+          const float4* rec = proj + (size_t)i * (kProjFloats / 4);
+          const float4 rc = __ldcg(rec + 7);
+          const uint32_t r01 = __float_as_uint(rc.x), r23 = __float_as_uint(rc.y);
+          tx0 = (int)(r01 & 0xFFFF);
+          ty0 = (int)(r01 >> 16);
+          tx1 = (int)(r23 & 0xFFFF);
+          key = ((unsigned long long)__float_as_uint(__ldcg(rec + 6).z) << 32) | (uint32_t)i;
+        }
+      }
+      s_key[threadIdx.x] = key;
+      __syncwarp();
+      warp_tile_walk(k, tx0, ty0, tx1, fz.tiles_x, fz.n_tiles, s_walk[threadIdx.x >> 5],
+                     [&](int owner, int t) {
+                       const uint32_t pos = atomicAdd(s_hist + t, 1u);
+                       if ((long long)pos < fz.capacity) fz.seg_keys[pos] = wkey[owner];
+                     });
+      __syncwarp();
+    }
+    return;
+  }
   // the last block to finish turns the counts into tile ranges
   __threadfence();
   __syncthreads();
@@ -347,6 +446,8 @@ __global__ void __launch_bounds__(256) project_batch_kernel(
   for (int v = threadIdx.x; v < valid * 8; v += blockDim.x) dst[v] = s_out[(v >> 3) * 9 + (v & 7)];
 }
 
+bool project_can_fuse_scatter(int n_tiles) { return n_tiles > 0 && n_tiles <= kHistTiles; }
+
 int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* pose,
                    const gs2d_config* cfg, float* proj_out, int32_t* tiles_per_surfel_out,
                    const int32_t* gate, cudaStream_t st, const SortFuse* fuse) {
@@ -374,10 +475,29 @@ int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* p
       resident = max(per_sm, 1) * max(sms, 1);
     }
     const int blocks = max(min(chunks, resident), 1);
-    project_fused_kernel<<<blocks, threads, 0, st>>>(
-        s->mu, s->quat, s->scale, s->opacity, s->rgb, s->n, pose, *cam, *cfg, tx, ty,
-        reinterpret_cast<float4*>(proj_out), tiles_per_surfel_out, gate, *fuse,
-        const_cast<int32_t*>(gate));
+    if (fuse->seg_keys) {
+      if (!project_can_fuse_scatter(fuse->n_tiles)) return GS2D_ERR_INVALID_ARG;
+      // blocks wait on one another at the grid barrier: a cooperative launch
+      cudaLaunchConfig_t lc = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeCooperative;
+      at[0].val.cooperative = 1;
+      lc.gridDim = dim3(blocks);
+      lc.blockDim = dim3(threads);
+      lc.dynamicSmemBytes = 0;
+      lc.stream = st;
+      lc.attrs = at;
+      lc.numAttrs = 1;
+      GS2D_CUDA_TRY(cudaLaunchKernelEx(&lc, project_fused_kernel, s->mu, s->quat, s->scale,
+                                       s->opacity, s->rgb, s->n, pose, *cam, *cfg, tx, ty,
+                                       reinterpret_cast<float4*>(proj_out), tiles_per_surfel_out,
+                                       gate, *fuse, const_cast<int32_t*>(gate)));
+    } else {
+      project_fused_kernel<<<blocks, threads, 0, st>>>(
+          s->mu, s->quat, s->scale, s->opacity, s->rgb, s->n, pose, *cam, *cfg, tx, ty,
+          reinterpret_cast<float4*>(proj_out), tiles_per_surfel_out, gate, *fuse,
+          const_cast<int32_t*>(gate));
+    }
   } else {
     if (s->n == 0) return GS2D_OK;
     project_kernel<<<chunks, threads, 0, st>>>(s->mu, s->quat, s->scale, s->opacity, s->rgb, s->n,

@@ -334,6 +334,7 @@ struct SortWs {
   uint32_t* long_list;           // [n_tiles] tiles with segments over kSegSmem
   uint32_t* n_long;              // [1] (zeroed per call)
   uint32_t* proj_done;           // [1] blocks of a fused projection finished (zeroed per call)
+  uint32_t* grid_bar;            // [1] grid barrier of a projection with fused scatter (zeroed)
   uint32_t* zero_begin;          // start of the zeroed region
   uint32_t* tile_count;          // [n_tiles]
   uint32_t* cursor;              // [n_tiles]
@@ -366,6 +367,7 @@ SortWs carve_sort_ws(void* base, int n, size_t cap, int n_tiles) {
   w.ticket = zt(8);
   w.n_long = zt(1);
   w.proj_done = zt(1);
+  w.grid_bar = zt(1);
   w.estatus = reinterpret_cast<unsigned long long*>(zt((size_t)2 * w.chunks_n + 2));
   w.zero_words = words;
   w.bytes = align_up(zstart + words * sizeof(uint32_t), 256);
@@ -406,6 +408,9 @@ SortFuse sort_fuse_args(void* workspace, int n, const gs2d_bins* bins, int tiles
   f.n_tiles = n_tiles;
   f.long_len = kSegSmem;
   f.order = nullptr;
+  f.seg_keys = nullptr;  // the caller opts in to the fused scatter
+  f.cursor = w.cursor;
+  f.bar = w.grid_bar;
   return f;
 }
 

@@ -7,9 +7,10 @@
 // tau = (rho, theta) followed by the retraction T <- Exp(tau) T with tau reset
 // to zero (the moments are kept across iterations of the frame, in the
 // caller's AdamW state when one is given, so a frame may span several calls).
-// Kernels per iteration: the projection (which also counts and scans the
-// tile pairs), the binning's scatter, and the fused tile kernel (which first
-// sorts its tile's segment by depth) -- 3.
+// Kernels per iteration: the projection (which also counts, scans and --
+// for up to 2048 tiles -- scatters the tile pairs; otherwise the binning's
+// scatter kernel follows) and the fused tile kernel (which first sorts its
+// tile's segment by depth) -- 2 or 3.
 #include <math.h>
 
 #include "gs2d_common.cuh"
@@ -164,9 +165,8 @@ int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_co
   bins.n_isect = w.n_isect;
   bins.status = status;
   bins.capacity = capacity;
-  // projection, tile counts and tile scan in one launch; the binning keeps
-  // the scatter, and every block of the fused tile kernel sorts its own
-  // tile's segment
+  // projection, tile counts and tile scan in one launch, and every block of
+  // the fused tile kernel sorts its own tile's segment
   const int tiles_x = gs2d_tiles_x(cam, cfg);
   SortFuse fuse = sort_fuse_args(w.sort_ws, s->n, &bins, tiles_x,
                                  tiles_x * gs2d_tiles_y(cam, cfg));
@@ -175,12 +175,19 @@ int gs2d_track_step(const gs2d_surfels* s, const gs2d_camera* cam, const gs2d_co
   fuse.order = w.order;
   unsigned long long *seg_keys = nullptr, *seg_tmp = nullptr;
   sort_seg_args(w.sort_ws, s->n, capacity, tiles_x * gs2d_tiles_y(cam, cfg), &seg_keys, &seg_tmp);
+  // up to 2048 tiles the projection also scatters the pairs into the tile
+  // segments (a cooperative launch with a grid barrier); beyond, the
+  // binning's scatter kernel does
+  const bool fused_scatter = project_can_fuse_scatter(fuse.n_tiles);
+  if (fused_scatter) fuse.seg_keys = seg_keys;
   for (int it = 0; it < n_iter; ++it) {
     int r = project_launch(s, cam, pose, cfg, w.proj, w.tiles, status, st, &fuse);
     if (r) return r;
-    r = bin_sort_launch(w.proj, w.tiles, s->n, cam, cfg, w.sort_ws, w.sort_bytes, nullptr, &bins,
-                        false, st, kSortPreZeroed | kSortPreScanned | kSortInTileKernel);
-    if (r) return r;
+    if (!fused_scatter) {
+      r = bin_sort_launch(w.proj, w.tiles, s->n, cam, cfg, w.sort_ws, w.sort_bytes, nullptr,
+                          &bins, false, st, kSortPreZeroed | kSortPreScanned | kSortInTileKernel);
+      if (r) return r;
+    }
     const bool timed = g_timer.used < g_timer.capacity && it % g_timer.every == 0;
     if (timed) GS2D_CUDA_TRY(record_timing_event(g_timer.start[g_timer.used], st));
     TrackStep ts{pose, adam, loss_hist, pose_hist, grad_hist, it, w.counter, zero_begin,
