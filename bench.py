@@ -236,7 +236,7 @@ def run_ours(args):
     def track():
         gs2d.gs2d_track_step(ds, ccam, cfg, prm, pose, obs_rgb, obs_d, N_ITER, cap, lh, ph, ws)
 
-    # one direct call, then capture a whole frame (reset + 100 x 4 kernels)
+    # one direct call, then capture a whole frame (reset + 100 x 2 kernels)
     # into a CUDA graph; the fused tile kernel's launches of every
     # TIMED_EVERY-th iteration are bracketed by event-record nodes inside the
     # graph (live timing inside the timed region; a node pair costs about
@@ -374,7 +374,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "surfels": N_SURFELS, "width": cam.width,
                        "height": cam.height, "iterations_per_step": N_ITER, "frames": n_frames,
                        "tile": "16x16", "l2": "256 MB buffer written between steps",
-                       "launch": "one CUDA graph per frame (reset + 100 x 4 kernels)",
+                       "launch": "one CUDA graph per frame (reset + 100 x 2 kernels)",
                        "parallelism": f"replicas x{ws_n}"},
             "tracking": tracking,
             "clocks": clocks,
@@ -393,12 +393,13 @@ def run_ours(args):
     replicas.finish()
 
 
-# kernels per tracking iteration: projection with the tile counts and (in
-# its last block) the tile scan 1; scatter 1; per-tile sort 1 (long
-# segments in-block; the counters are zeroed by the previous iteration's
-# fused kernel); fused render + loss + pose backward with the reduction +
-# AdamW + retraction in its last block 1.  Plus one reset per frame.
-LAUNCHES_PER_ITER = 4
+# kernels per tracking iteration at 640x480 (1200 tiles): the projection
+# with the tile counts, the tile scan and the scatter of the pairs (one
+# cooperative launch; the counters are zeroed by the previous iteration's
+# fused kernel) 1; the fused tile kernel (per-tile depth sort, render, loss,
+# pose backward, and the reduction + AdamW + retraction in its last block) 1.
+# Plus one reset per frame.
+LAUNCHES_PER_ITER = 2
 
 
 def roofline(r, ds, frames, cam, cfg, stream, ms_iter, fused_ms):

@@ -239,7 +239,24 @@ __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<P, kG>()) tra
     const int len = end - start;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(&sm.rec[0][0]);
     static_assert(sizeof(sm.rec) >= kSegSmem * sizeof(unsigned long long), "sort area");
-    if (len <= kSegSmem) {
+    if (len <= kTileThreads) {
+      // one key per thread: its rank among the segment's (distinct) keys is
+      // its position -- two barriers instead of a bitonic network's stages
+      unsigned long long ki = 0ull;
+      if ((int)threadIdx.x < len) ki = keys[threadIdx.x] = ts.seg_keys[start + threadIdx.x];
+      __syncthreads();
+      if ((int)threadIdx.x < len) {
+        int rank = 0, j = 0;
+        for (; j + 1 < len; j += 2) {
+          const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(keys + j);
+          rank += (int)(kk.x < ki) + (int)(kk.y < ki);
+        }
+        if (j < len) rank += (int)(keys[j] < ki);
+        s_ids[rank] = min((uint32_t)(ki & 0xFFFFFFFFull), (uint32_t)(ts.n - 1));
+      }
+      __syncthreads();
+      ids = s_ids;
+    } else if (len <= kSegSmem) {
       for (int i = threadIdx.x; i < len; i += kTileThreads) keys[i] = ts.seg_keys[start + i];
       __syncthreads();
       bitonic_sort(keys, len);
