@@ -283,11 +283,15 @@ __global__ void __launch_bounds__(256) project_fused_kernel(
   if (local)
     for (int t = threadIdx.x; t < fz.n_tiles; t += blockDim.x) s_hist[t] = 0u;
   __syncthreads();
-  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+  // every block takes an equal contiguous share of the surfels (passes of
+  // blockDim.x), so no block trails the others by a whole extra chunk
+  const int share = (n + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int my0 = min(n, (int)blockIdx.x * share), my1 = min(n, my0 + share);
+  for (int base = my0; base < my1; base += blockDim.x) {
     const int i = base + (int)threadIdx.x;
     s_emit[threadIdx.x] = false;
     int k = 0, tx0 = 1, ty0 = 1, tx1 = 0;
-    if (i < n) {
+    if (i < my1) {
       project_one(i, mu, quat, scale, opacity, rgb, sp, cam, cfg, s_out + threadIdx.x * 9,
                   tiles_out + i);
       const float4 rc = s_out[threadIdx.x * 9 + 7];
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(256) project_fused_kernel(
     warp_tile_walk(k, tx0, ty0, tx1, fz.tiles_x, fz.n_tiles, s_walk[threadIdx.x >> 5],
                    [&](int, int t) { atomicAdd(local ? s_hist + t : fz.tile_count + t, 1u); });
     __syncthreads();
-    const int valid = min((int)blockDim.x, n - base);
+    const int valid = min((int)blockDim.x, my1 - base);
     float4* dst = proj + (size_t)base * (kProjFloats / 4);
     // only the records of surfels that touch a tile are ever read (the
     // scatter and the tile kernel reach records through the tile lists), so
@@ -359,11 +363,11 @@ __global__ void __launch_bounds__(256) project_fused_kernel(
     }
     __syncthreads();
     const unsigned long long* wkey = s_key + (threadIdx.x & ~31);
-    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    for (int base = my0; base < my1; base += blockDim.x) {
       const int i = base + (int)threadIdx.x;
       int k = 0, tx0 = 1, ty0 = 1, tx1 = 0;
       unsigned long long key = 0ull;
-      if (i < n) {
+      if (i < my1) {
         k = max(tiles_out[i], 0);
         if (k > 0) {
           // this block wrote the record: read it back past L1
