@@ -85,37 +85,40 @@ struct MapSmem {
   bool ok[kMapRH][kMapRW];
 };
 
-__device__ __forceinline__ F3 ray_of(const gs2d_camera& cam, int px, int py) {
-  return f3((px + 0.5f - cam.cx) / cam.fx, (py + 0.5f - cam.cy) / cam.fy, 1.f);
+// Pixel ray (x', y', 1) of pixel (px, py) with the reciprocal focal lengths
+// (ifx, ify) = (1/fx, 1/fy) taken once per kernel.
+__device__ __forceinline__ F3 ray_of(const gs2d_camera& cam, float ifx, float ify, int px, int py) {
+  return f3((px + 0.5f - cam.cx) * ifx, (py + 0.5f - cam.cy) * ify, 1.f);
 }
 // Normal term at pixel (px, py), staged at (sx, sy) of the two-ring arrays:
 // returns L_n (false if invalid: border pixel, own or a 4-neighbour's
 // opacity <= 0.5, degenerate cross product) and the gradients of L_n w.r.t.
 // X(p+ex), X(p-ex), X(p+ey), X(p-ey) and N_r(p).
 __device__ bool ln_eval(const MapSmem& sm, const float* __restrict__ normal,
-                        const gs2d_camera& cam, int px, int py, int sx, int sy, float& Ln,
-                        F3 g[4], F3& gNr) {
+                        const gs2d_camera& cam, float ifx, float ify, int px, int py, int sx,
+                        int sy, float& Ln, F3 g[4], F3& gNr) {
   const int W = cam.width, H = cam.height;
   if (px < 1 || py < 1 || px > W - 2 || py > H - 2) return false;
   if (!(sm.op[sy][sx] > 0.5f && sm.op[sy][sx - 1] > 0.5f && sm.op[sy][sx + 1] > 0.5f &&
         sm.op[sy - 1][sx] > 0.5f && sm.op[sy + 1][sx] > 0.5f))
     return false;
   const int i = py * W + px;
-  const F3 Xr = sm.dh[sy][sx + 1] * ray_of(cam, px + 1, py);
-  const F3 Xl = sm.dh[sy][sx - 1] * ray_of(cam, px - 1, py);
-  const F3 Xd = sm.dh[sy + 1][sx] * ray_of(cam, px, py + 1);
-  const F3 Xu = sm.dh[sy - 1][sx] * ray_of(cam, px, py - 1);
+  const F3 Xr = sm.dh[sy][sx + 1] * ray_of(cam, ifx, ify, px + 1, py);
+  const F3 Xl = sm.dh[sy][sx - 1] * ray_of(cam, ifx, ify, px - 1, py);
+  const F3 Xd = sm.dh[sy + 1][sx] * ray_of(cam, ifx, ify, px, py + 1);
+  const F3 Xu = sm.dh[sy - 1][sx] * ray_of(cam, ifx, ify, px, py - 1);
   const F3 gx = 0.5f * (Xr - Xl), gy = 0.5f * (Xd - Xu);
   const F3 n = cross3(gx, gy);
-  const float nn = sqrtf(dot3(n, n));
-  if (!(nn > 0.f)) return false;
-  const F3 ND = (1.f / nn) * n;
+  const float n2 = dot3(n, n);
+  if (!(n2 > 0.f)) return false;
+  const float inn = rsqrtf(n2);  // 1 / |n|
+  const F3 ND = inn * n;
   const F3 Nr = f3(normal[3 * i], normal[3 * i + 1], normal[3 * i + 2]);
   const float dp = dot3(ND, Nr);
   Ln = 1.f - dp;
   gNr = (-1.f) * ND;
   // dLn/dn = -(Nr - ND (ND . Nr)) / |n|
-  const F3 gn = (-1.f / nn) * (Nr - dp * ND);
+  const F3 gn = (-inn) * (Nr - dp * ND);
   const F3 ggx = cross3(gy, gn), ggy = cross3(gn, gx);
   g[0] = 0.5f * ggx;
   g[1] = (-0.5f) * ggx;
@@ -135,6 +138,7 @@ __global__ void __launch_bounds__(kLossThreads) mapping_loss_kernel(
   const int W = cam.width, H = cam.height, P = W * H;
   const float inv = 1.f / (float)P;
   const int tiles_x = (W + kMapTW - 1) / kMapTW, tiles_y = (H + kMapTH - 1) / kMapTH;
+  const float ifx = 1.f / cam.fx, ify = 1.f / cam.fy;
   float acc = 0.f;
   for (int tile = blockIdx.x; tile < tiles_x * tiles_y; tile += gridDim.x) {
     const int x0 = (tile % tiles_x) * kMapTW, y0 = (tile / tiles_x) * kMapTH;
@@ -163,7 +167,7 @@ __global__ void __launch_bounds__(kLossThreads) mapping_loss_kernel(
       F3 g4[4], gNr = f3(0.f, 0.f, 0.f);
       bool ok = false;
       if ((tile_px || ring) && px >= 0 && py >= 0 && px < W && py < H)
-        ok = ln_eval(sm, normal, cam, px, py, rx + 1, ry + 1, Ln, g4, gNr);
+        ok = ln_eval(sm, normal, cam, ifx, ify, px, py, rx + 1, ry + 1, Ln, g4, gNr);
       sm.ok[ry][rx] = ok;
       if (ok)
 #pragma unroll
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(kLossThreads) mapping_loss_kernel(
       // stencils of the four neighbours that read X(q): p = q-ex uses X(p+ex)
       // (slot 0), p = q+ex uses X(p-ex) (1), p = q-ey uses X(p+ey) (2),
       // p = q+ey uses X(p-ey) (3)
-      const F3 rq = ray_of(cam, px, py);
+      const F3 rq = ray_of(cam, ifx, ify, px, py);
       const int nb[4][3] = {{rx - 1, ry, 0}, {rx + 1, ry, 1}, {rx, ry - 1, 2}, {rx, ry + 1, 3}};
       F3 gX = f3(0.f, 0.f, 0.f);
 #pragma unroll

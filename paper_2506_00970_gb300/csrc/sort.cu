@@ -13,8 +13,7 @@
 //      into its tile's segment at an atomically claimed slot (the order
 //      inside a segment is arbitrary at this point);
 //   4. tile sort: one block per tile sorts its segment by that key in shared
-//      memory (up to 256 keys by rank: each thread counts the keys below its
-//      own; longer ones by a bitonic network in its "flip" form, in which every comparator
+//      memory (bitonic network in its "flip" form, in which every comparator
 //      puts the smaller key at the lower index, so a segment of any length
 //      behaves as if padded with +inf), then writes the surfel ids, the
 //      64-bit (tile, depth) keys and each pair's emission index.  Segments
@@ -280,8 +279,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(
   });
 }
 
-// Segments of at most kSegSmem keys: sorted in shared memory by 256 threads
-// (by rank up to 256 keys, else by the bitonic network; and,
+// Segments of at most kSegSmem keys: sorted in shared memory by 256 threads (and,
 // with long_here, longer ones too).
 __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(
     const float4* __restrict__ proj, int n, int tiles_x, const int32_t* __restrict__ ranges,
@@ -306,10 +304,7 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(
   }
   for (int i = threadIdx.x; i < len; i += blockDim.x) s_keys[i] = seg_keys[start + i];
   __syncthreads();
-  if (len <= (int)blockDim.x)
-    rank_sort(s_keys, len);
-  else
-    bitonic_sort(s_keys, len);
+  bitonic_sort(s_keys, len);
   write_outputs(s_keys, len, start, t, tiles_x, n, proj, surfel_off, vals, emit, keys64);
 }
 

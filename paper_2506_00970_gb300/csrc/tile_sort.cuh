@@ -56,28 +56,6 @@ __device__ inline void bitonic_sort(unsigned long long* a, int len) {
   }
 }
 
-// In-place sort of len <= blockDim.x distinct keys by rank: thread i counts
-// the keys below a[i], which is its key's final position, and moves it
-// there -- two block barriers instead of a bitonic network's log^2 stages.
-// a: 16-byte aligned, loaded (and synchronised) before the call; every
-// thread of the block calls it.
-__device__ inline void rank_sort(unsigned long long* a, int len) {
-  unsigned long long ki = 0ull;
-  int rank = 0;
-  if ((int)threadIdx.x < len) {
-    ki = a[threadIdx.x];
-    int j = 0;
-    for (; j + 1 < len; j += 2) {
-      const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(a + j);
-      rank += (int)(kk.x < ki) + (int)(kk.y < ki);
-    }
-    if (j < len) rank += (int)(a[j] < ki);
-  }
-  __syncthreads();
-  if ((int)threadIdx.x < len) a[rank] = ki;
-  __syncthreads();
-}
-
 __device__ __forceinline__ void write_outputs(const unsigned long long* a, int len, int start, int t,
                                               int tiles_x, int n, const float4* __restrict__ proj,
                                               const uint32_t* __restrict__ surfel_off,
