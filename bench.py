@@ -46,7 +46,7 @@ TIMED_EVERY = 10          # fused-kernel launches bracketed by events: every 10t
 # DRAM bytes per launch of the roofline kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of the fused tracking kernel on
 # this workload); None while the kernel has changed since the capture.
-TRAFFIC_BYTES = {"track_tile": 6324480}
+TRAFFIC_BYTES = {"track_tile": 6610432}
 # batched workloads reported beside the tracking line
 MAP_SURFELS, MAP_VIEWS = 1_000_000, 8
 UNEVEN_SURFELS, UNEVEN_VIEWS = 2_000_000, 32
