@@ -89,7 +89,13 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-template <int CIN, int COUT, int HI, int WI, int TW, int TH, int S>
+// A tile is NI images' TW x TH output pixels (NI = 1: a 128-pixel part of one
+// image; NI > 1: whole small images, TW x TH = the output map) times NB of the
+// C_out channels.  One box per tap and channel block spans the NI images
+// (its fourth dimension), so image g's pixels are rows [g TW TH, (g + 1) TW TH)
+// of the 128-row MMA tile; rows past NI TW TH hold stale data whose results
+// the epilogue drops.
+template <int CIN, int COUT, int HI, int WI, int TW, int TH, int S, int NI = 1, int NB = COUT>
 struct ConvTma {
   static constexpr int HO = (HI + 1) / 2, WO = (WI + 1) / 2;
   static constexpr int TX = (WO + TW - 1) / TW, TY = (HO + TH - 1) / TH;
@@ -98,24 +104,30 @@ struct ConvTma {
   static constexpr int CB = CIN / KB;             // boxes (stages) per tap
   static constexpr int KS = 9 * CB;               // stages per tile
   static constexpr int MMAS = KB / 16;            // MMAs per stage
-  static constexpr int A_BYTES = TW * TH * SW;    // one input box
-  static constexpr int B_BYTES = COUT * SW;       // one weight box
+  static constexpr int ROWS = NI * TW * TH;       // rows one input box lands
+  static constexpr int BOX_BYTES = ROWS * SW;     // one input box (NI images)
+  static constexpr int A_BYTES = 128 * SW;        // the 128-row A operand
+  static constexpr int B_BYTES = NB * SW;         // one weight box
   static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int TX_BYTES = BOX_BYTES + B_BYTES;  // bytes a stage's loads bring
   static constexpr int SMEM = S * STAGE + 1024;   // + slack for 1024-byte alignment
-  static constexpr int TMEM_COLS = COUT;
-  static_assert(TW * TH == 128, "one 128-row MMA tile");
+  static constexpr int TMEM_COLS = NB;
+  static constexpr int NSPLIT = COUT / NB;        // channel groups (grid.y)
+  static_assert(NI == 1 ? TW * TH == 128 : (TX == 1 && TY == 1 && ROWS <= 128),
+                "one 128-row MMA tile: a part of one image, or whole images");
   static_assert(KB == 32 || KB == 64, "64- or 128-byte swizzled rows");
-  static_assert(CIN % KB == 0 && COUT >= 32 && COUT <= 256 && (COUT & (COUT - 1)) == 0,
+  static_assert(CIN % KB == 0 && NB >= 32 && NB <= 256 && (NB & (NB - 1)) == 0 &&
+                    COUT % NB == 0,
                 "tensor-memory columns: a power of two in [32, 256]");
   static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "swizzle atoms stay aligned");
   static_assert(2 * TW <= 256 && 2 * TH <= 256, "TMA box dimensions");
 };
 
-template <int CIN, int COUT, int HI, int WI, int TW, int TH, int S>
+template <int CIN, int COUT, int HI, int WI, int TW, int TH, int S, int NI, int NB>
 __global__ void __launch_bounds__(kConvThreads) conv_tma_kernel(
     const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_w,
-    const float* __restrict__ bias, bf16* __restrict__ out, int* __restrict__ err) {
-  using C = ConvTma<CIN, COUT, HI, WI, TW, TH, S>;
+    const float* __restrict__ bias, bf16* __restrict__ out, int B, int* __restrict__ err) {
+  using C = ConvTma<CIN, COUT, HI, WI, TW, TH, S, NI, NB>;
   extern __shared__ unsigned char conv_raw[];
   __shared__ __align__(8) uint64_t s_full[S], s_empty[S], s_done;
   __shared__ uint32_t s_tmem;
@@ -123,8 +135,11 @@ __global__ void __launch_bounds__(kConvThreads) conv_tma_kernel(
   unsigned char* stages = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(conv_raw) + 1023) & ~(uintptr_t)1023);
   const int tile = blockIdx.x;
-  const int img = tile / (C::TX * C::TY), r = tile % (C::TX * C::TY);
+  // NI == 1: tile -> (image, TH x TW part); NI > 1: images tile NI .. tile NI + NI - 1
+  const int img = NI == 1 ? tile / (C::TX * C::TY) : tile * NI;
+  const int r = NI == 1 ? tile % (C::TX * C::TY) : 0;
   const int oy0 = (r / C::TX) * TH, ox0 = (r % C::TX) * TW;
+  const int nb0 = (int)blockIdx.y * NB;  // first output channel of the tile
   const int warp = threadIdx.x >> 5;
 
   if (threadIdx.x == 0) {
@@ -159,10 +174,11 @@ __global__ void __launch_bounds__(kConvThreads) conv_tma_kernel(
       const int tap = s / C::CB, cb = (s % C::CB) * C::KB;
       const int ky = tap / 3, kx = tap - 3 * (tap / 3);
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                   "r"(C::STAGE)
+                   "r"(C::TX_BYTES)
                    : "memory");
+      // images past the batch read as zeros (out-of-range coordinates)
       tma_load_4d(base, &map_x, cb, 2 * ox0 + kx - 1, 2 * oy0 + ky - 1, img, bar);
-      tma_load_2d(base + C::A_BYTES, &map_w, tap * CIN + cb, 0, bar);
+      tma_load_2d(base + C::A_BYTES, &map_w, tap * CIN + cb, nb0, bar);
     };
     bool fail = false;
     int issued = 0, consumed = 0;
@@ -185,7 +201,7 @@ __global__ void __launch_bounds__(kConvThreads) conv_tma_kernel(
         asm volatile(
             "{.reg .pred p; setp.ne.b32 p, %4, 0;\n"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;}\n" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(mma_idesc(COUT)), "r"(acc));
+            "l"(ad), "l"(bd), "r"(mma_idesc(NB)), "r"(acc));
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -219,13 +235,16 @@ __global__ void __launch_bounds__(kConvThreads) conv_tma_kernel(
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!*reinterpret_cast<volatile int*>(&s_fail)) {
-    // TMEM lane = row m = output pixel (oy0 + m / TW, ox0 + m % TW)
+    // TMEM lane = row m: image img + m / (TW TH), output pixel (oy0 + q / TW,
+    // ox0 + q % TW) with q = m % (TW TH)
     const int m = threadIdx.x;
-    const int oy = oy0 + m / TW, ox = ox0 + m % TW;
-    const bool ok = oy < C::HO && ox < C::WO;
-    bf16* dst = out + (((size_t)img * C::HO + oy) * C::WO + ox) * COUT;
+    const int g = m / (TW * TH), q = m % (TW * TH);
+    const int oy = oy0 + q / TW, ox = ox0 + q % TW;
+    const bool ok = g < NI && img + g < B && oy < C::HO && ox < C::WO;
+    bf16* dst = out + (((size_t)(img + g) * C::HO + oy) * C::WO + ox) * COUT + nb0;
+    const float* bs = bias + nb0;
 #pragma unroll 1
-    for (int c0 = 0; c0 < COUT; c0 += 16) {
+    for (int c0 = 0; c0 < NB; c0 += 16) {
       uint32_t v[16];
       const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
       asm volatile(
@@ -240,8 +259,8 @@ __global__ void __launch_bounds__(kConvThreads) conv_tma_kernel(
         uint32_t packed[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const float x0 = fmaxf(__uint_as_float(v[2 * j]) + bias[c0 + 2 * j], 0.f);
-          const float x1 = fmaxf(__uint_as_float(v[2 * j + 1]) + bias[c0 + 2 * j + 1], 0.f);
+          const float x0 = fmaxf(__uint_as_float(v[2 * j]) + bs[c0 + 2 * j], 0.f);
+          const float x1 = fmaxf(__uint_as_float(v[2 * j + 1]) + bs[c0 + 2 * j + 1], 0.f);
           const __nv_bfloat162 b2 = __floats2bfloat162_rn(x0, x1);
           packed[j] = *reinterpret_cast<const uint32_t*>(&b2);
         }
@@ -286,10 +305,10 @@ EncodeTiledFn encode_tiled() {
 // element stride 2 in W and H (TW x TH pixels land); weight map: [C_out]
 // [9 C_in] as {9 C_in, C_out}, box {KB, C_out}; both with the swizzle of
 // their KB x 2-byte rows.  Zero fill outside the tensors.
-template <int CIN, int COUT, int HI, int WI, int TW, int TH, int S>
+template <int CIN, int COUT, int HI, int WI, int TW, int TH, int S, int NI = 1, int NB = COUT>
 int run(const bf16* x, int B, const bf16* w, const float* bias, bf16* out, int* err,
         cudaStream_t st) {
-  using C = ConvTma<CIN, COUT, HI, WI, TW, TH, S>;
+  using C = ConvTma<CIN, COUT, HI, WI, TW, TH, S, NI, NB>;
   EncodeTiledFn enc = encode_tiled();
   if (!enc) return GS2D_ERR_CUDA;
   if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(w) |
@@ -299,7 +318,7 @@ int run(const bf16* x, int B, const bf16* w, const float* bias, bf16* out, int* 
   const cuuint64_t xdim[4] = {(cuuint64_t)CIN, (cuuint64_t)WI, (cuuint64_t)HI, (cuuint64_t)B};
   const cuuint64_t xstr[3] = {(cuuint64_t)CIN * 2, (cuuint64_t)WI * CIN * 2,
                               (cuuint64_t)HI * WI * CIN * 2};
-  const cuuint32_t xbox[4] = {(cuuint32_t)C::KB, 2 * TW, 2 * TH, 1};
+  const cuuint32_t xbox[4] = {(cuuint32_t)C::KB, 2 * TW, 2 * TH, (cuuint32_t)NI};
   const cuuint32_t xes[4] = {1, 2, 2, 1};
   if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(x), xdim, xstr, xbox, xes,
           CU_TENSOR_MAP_INTERLEAVE_NONE, C::SW == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
@@ -307,7 +326,7 @@ int run(const bf16* x, int B, const bf16* w, const float* bias, bf16* out, int* 
     return GS2D_ERR_CUDA;
   const cuuint64_t wdim[2] = {(cuuint64_t)9 * CIN, (cuuint64_t)COUT};
   const cuuint64_t wstr[1] = {(cuuint64_t)9 * CIN * 2};
-  const cuuint32_t wbox[2] = {(cuuint32_t)C::KB, COUT};
+  const cuuint32_t wbox[2] = {(cuuint32_t)C::KB, (cuuint32_t)NB};
   const cuuint32_t wes[2] = {1, 1};
   if (enc(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(w), wdim, wstr, wbox, wes,
           CU_TENSOR_MAP_INTERLEAVE_NONE, C::SW == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
@@ -318,21 +337,21 @@ int run(const bf16* x, int B, const bf16* w, const float* bias, bf16* out, int* 
   static std::once_flag smem_once;
   static cudaError_t smem_err = cudaSuccess;
   std::call_once(smem_once, [] {
-    smem_err = cudaFuncSetAttribute(conv_tma_kernel<CIN, COUT, HI, WI, TW, TH, S>,
+    smem_err = cudaFuncSetAttribute(conv_tma_kernel<CIN, COUT, HI, WI, TW, TH, S, NI, NB>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
   });
   if (smem_err != cudaSuccess) return GS2D_ERR_CUDA;
-  const int grid = B * C::TX * C::TY;
+  const int grid = NI == 1 ? B * C::TX * C::TY : (B + NI - 1) / NI;
   if (grid <= 0) return GS2D_OK;
-  conv_tma_kernel<CIN, COUT, HI, WI, TW, TH, S><<<grid, kConvThreads, C::SMEM, st>>>(
-      mx, mw, bias, out, err);
+  conv_tma_kernel<CIN, COUT, HI, WI, TW, TH, S, NI, NB>
+      <<<dim3(grid, C::NSPLIT), kConvThreads, C::SMEM, st>>>(mx, mw, bias, out, B, err);
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
 }
 
 }  // namespace
 
-bool conv_tma_layer(int layer) { return layer >= 1 && layer <= 3; }
+bool conv_tma_layer(int layer) { return layer >= 1 && layer <= 5; }
 
 // Stages in flight: with a grid that fills the GPU several CTAs share an SM
 // (fewer stages each; the SM keeps as many loads in flight); a small batch's
@@ -351,6 +370,13 @@ int conv_tma_forward(int layer, const bf16* x, int B, const bf16* w, const float
     case 3:
       return B >= kFull / 2 ? run<128, 256, 15, 20, 16, 8, 2>(x, B, w, bias, out, err, st)
                             : run<128, 256, 15, 20, 16, 8, 4>(x, B, w, bias, out, err, st);
+    // layers 5 and 6 (4 x 5 and 2 x 3 outputs): whole images per tile (5 and
+    // 21: 100 and 126 rows), the 256 output channels in halves or quarters so
+    // the grid still spreads over the SMs
+    case 4:
+      return run<256, 256, 8, 10, 5, 4, 6, 5, 128>(x, B, w, bias, out, err, st);
+    case 5:
+      return run<256, 256, 4, 5, 3, 2, 8, 21, 32>(x, B, w, bias, out, err, st);
     default: return GS2D_ERR_INVALID_ARG;
   }
 }

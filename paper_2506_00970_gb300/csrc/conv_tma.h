@@ -1,4 +1,4 @@
-// Forward convolutions of the proposal network's layers 2-4 on tcgen05 with
+// Forward convolutions of the proposal network's layers 2-6 on tcgen05 with
 // TMA-fed operands (conv_tma.cu).  Internal to the library.
 #pragma once
 
@@ -8,7 +8,7 @@
 namespace gs2d {
 namespace net {
 
-// Whether conv layer `layer` (0-based: 1, 2, 3 = the network's layers 2-4)
+// Whether conv layer `layer` (0-based: 1 .. 5 = the network's layers 2-6)
 // runs on conv_tma_forward.
 bool conv_tma_layer(int layer);
 
