@@ -27,7 +27,7 @@
 
 namespace gs2d {
 
-constexpr int kBwdRegion = 4;      // 8 x 4 blocks per region: pixels per lane
+constexpr int kBwdRegion = 8;      // 8 x 4 blocks per region (a 256-pixel tile): pixels per lane
 constexpr int kBwdWarps = 4;       // warps (independent work items) per block
 constexpr int kBwdWarpBlocks = 4;  // resident blocks per SM the registers are sized for
 // Regions per tile of a tile shape, and for the largest shape (1024 pixels).

@@ -277,3 +277,42 @@ def test_track_step_on_dense_low_resolution_view(torch_cuda, orc):
     assert int(gs2d.gs2d_track_status(ws).item()) in (0, gs2d.CONVERGED)
     assert float(lh[0].item()) == pytest.approx(float(loss.item()), rel=1e-4)
     assert float(lh[-1].item()) < float(lh[0].item())
+
+
+def test_track_step_beyond_the_fused_scatter_tile_count(torch_cuda, orc):
+    """A 1200x680 view has 3225 tiles, more than the projection's shared
+    tile histogram holds, so the tracking step scatters the pairs with the
+    binning's scatter kernel between the projection and the tile kernel
+    (which still sorts its own segment).  Its first loss equals the
+    standalone render + tracking loss at the start pose, and the loop lowers
+    the loss; a 640x480 step (projection with the fused scatter) of the same
+    room agrees with its own standalone loss the same way."""
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d
+    s = scenes.room_scene(4, 60_000)
+    gt = scenes.room_pose(5)
+    start = scenes.perturb_pose(gt, 0.02, 1.0, seed=9)
+    for cam in (scenes.mapping_camera(), scenes.tracking_camera()):
+        ds = gs2d.DeviceSurfels(s)
+        _, _, _, img = gpu_render(s, cam, gt, capacity=16 * s.n)
+        obs_rgb = torch.tensor(img["rgb"], device="cuda")
+        obs_d = torch.tensor(img["depth"] / np.maximum(img["opacity"], 1e-6), device="cuda")
+        r2, _, pt, _ = gpu_render(s, cam, start, capacity=16 * s.n)
+        f = dict(dtype=torch.float32, device="cuda")
+        g = [torch.empty(cam.height, cam.width, 3, **f), torch.empty(cam.height, cam.width, **f),
+             torch.empty(cam.height, cam.width, **f)]
+        loss = torch.empty(1, **f)
+        lws = torch.empty(1 << 16, dtype=torch.uint8, device="cuda")
+        ccam, cfg, prm = gs2d.camera(cam), gs2d.default_config(), gs2d.default_track_params()
+        gs2d.gs2d_tracking_loss(r2.rgb, r2.depth, r2.normal, r2.opacity, obs_rgb, obs_d, ccam, prm,
+                                *g, loss, lws)
+        cap = 16 * s.n
+        ws = torch.empty(gs2d.gs2d_track_workspace(s.n, cap, ccam, cfg), dtype=torch.uint8,
+                         device="cuda")
+        lh = torch.zeros(8, device="cuda")
+        pose = pt.clone()
+        gs2d.gs2d_track_step(ds, ccam, cfg, prm, pose, obs_rgb, obs_d, 8, cap, lh, None, ws)
+        torch.cuda.synchronize()
+        assert int(gs2d.gs2d_track_status(ws).item()) in (0, gs2d.CONVERGED), cam.width
+        assert float(lh[0].item()) == pytest.approx(float(loss.item()), rel=1e-4), cam.width
+        assert float(lh[-1].item()) < float(lh[0].item()), cam.width
