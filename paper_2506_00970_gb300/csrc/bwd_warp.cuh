@@ -27,14 +27,19 @@
 
 namespace gs2d {
 
-constexpr int kBwdRegion = 8;      // 8 x 4 blocks per region (a 256-pixel tile): pixels per lane
+// 8 x 4 blocks per region (pixels per lane): a whole 256-pixel tile per warp
+// when the view has tiles enough to fill the GPU (one partial per (tile,
+// surfel)), half a tile for small views (twice the work units).
+constexpr int kBwdRegion = 8;
+constexpr int kBwdRegionSmall = 4;
 constexpr int kBwdWarps = 4;       // warps (independent work items) per block
 constexpr int kBwdWarpBlocks = 4;  // resident blocks per SM the registers are sized for
-// Regions per tile of a tile shape, and for the largest shape (1024 pixels).
-__host__ __device__ inline int bwd_regions(const gs2d_config& c) {
-  return c.tile_w * c.tile_h / (32 * kBwdRegion);
+// Regions per tile of a tile shape with R blocks per region, and the most
+// any shape (up to 1024 pixels) and region size can have.
+__host__ __device__ inline int bwd_regions(const gs2d_config& c, int R = kBwdRegion) {
+  return c.tile_w * c.tile_h / (32 * R);
 }
-constexpr int kBwdMaxRegions = 1024 / (32 * kBwdRegion);
+constexpr int kBwdMaxRegions = 1024 / (32 * kBwdRegionSmall);
 
 // Per-warp shared memory: the staged records of 32 list entries and the
 // region's per-pixel upstream gradients, [k][0] = (dC, dD), [k][1] = (dN,

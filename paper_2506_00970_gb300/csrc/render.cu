@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(kTileThreads, P == 1 ? 4 : (P == 2 ? 3 : 2)) r
 
 // Full backward: one warp per (tile, region) work item, kBwdWarps warps per
 // block and no block barrier (bwd_warp.cuh).
+template <int R>
 __global__ void __launch_bounds__(kBwdWarps * 32, kBwdWarpBlocks) render_bwd_warp_kernel(
     const float4* __restrict__ proj, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ emit, const int32_t* __restrict__ ranges, gs2d_camera cam,
@@ -179,13 +180,13 @@ __global__ void __launch_bounds__(kBwdWarps * 32, kBwdWarpBlocks) render_bwd_war
     const float* __restrict__ g_depth, const float* __restrict__ g_normal,
     const float* __restrict__ g_opac, float* __restrict__ partials,
     const int32_t* __restrict__ gate) {
-  __shared__ WarpBwdSmem<kBwdRegion> sm[kBwdWarps];
+  __shared__ WarpBwdSmem<R> sm[kBwdWarps];
   if (gate && *gate) return;
   const int warp = threadIdx.x >> 5;
   const int unit = blockIdx.x * kBwdWarps + warp;
   if (unit >= n_units) return;
   const int tile = unit / Q, region = unit - tile * Q;
-  bwd_region<kBwdRegion>(proj, vals, emit, ranges[2 * tile], ranges[2 * tile + 1],
+  bwd_region<R>(proj, vals, emit, ranges[2 * tile], ranges[2 * tile + 1],
                          (tile % tiles_x) * cfg.tile_w, (tile / tiles_x) * cfg.tile_h, region, Q,
                          cam, cfg, T_final, n_last, g_rgb, g_depth, g_normal, g_opac, partials,
                          sm[warp]);
@@ -611,11 +612,19 @@ int render_bwd_launch(const float* proj, const gs2d_bins* bins, const int32_t* t
   const BwdWs w = carve_bwd_ws(workspace, s->n, bins->capacity, n_tiles, full, kBwdMaxRegions);
   const float4* p4 = reinterpret_cast<const float4*>(proj);
   if (full) {
-    const int Q = bwd_regions(*cfg);
+    // a view of few tiles (fewer than two per SM) replays half tiles
+    const bool small = n_tiles < 2 * 152;
+    const int Q = bwd_regions(*cfg, small ? kBwdRegionSmall : kBwdRegion);
     const int units = n_tiles * Q;
-    render_bwd_warp_kernel<<<(units + kBwdWarps - 1) / kBwdWarps, kBwdWarps * 32, 0, st>>>(
-        p4, bins->vals, bins->isect_emit, bins->tile_ranges, *cam, *cfg, tx, Q, units, t_final,
-        n_last, d_rgb, d_depth, d_normal, d_opacity, w.partials, gate);
+    const int blocks = (units + kBwdWarps - 1) / kBwdWarps;
+    if (small)
+      render_bwd_warp_kernel<kBwdRegionSmall><<<blocks, kBwdWarps * 32, 0, st>>>(
+          p4, bins->vals, bins->isect_emit, bins->tile_ranges, *cam, *cfg, tx, Q, units, t_final,
+          n_last, d_rgb, d_depth, d_normal, d_opacity, w.partials, gate);
+    else
+      render_bwd_warp_kernel<kBwdRegion><<<blocks, kBwdWarps * 32, 0, st>>>(
+          p4, bins->vals, bins->isect_emit, bins->tile_ranges, *cam, *cfg, tx, Q, units, t_final,
+          n_last, d_rgb, d_depth, d_normal, d_opacity, w.partials, gate);
     GS2D_LAUNCH_CHECK();
     if (s->n > 0) {
       const int nb = (s->n + 255) / 256;
