@@ -814,6 +814,128 @@ int conv_s2(const bf16* x, int B, const bf16* wt, const float* bias, bf16* out, 
   return GS2D_OK;
 }
 
+// Layer 1's weight gradient dW[c_out][k] = sum over output pixels p of
+// dY[p][c_out] im2col(x)[p][k] (k = tap x 8 + c_in) as a direct kernel on
+// the forward's staging: a tile is two output rows of one image, its five
+// input rows staged in column-parity planes and its 160 x 32 output
+// gradients beside them (the next tile's in flight); warp w contracts the
+// tile's pixels 32 w .. 32 w + 31 with mma.m16n8k16 (A = dY^T by ldmatrix
+// .trans from the staged gradients, B = each tap's 8 input channels by
+// ldmatrix .trans from the staged rows), accumulating the 32 x 72 product
+// over all its tiles in registers.  The block's warps are summed in a fixed
+// order into one partial per block (reduce_partials_wide_kernel adds the
+// blocks in a fixed order), so the result does not depend on timing.  Reads the input map
+// and the output gradients once (2 x 78.6 MB at batch 256).
+constexpr int kW1Grid = 3 * 152;  // fixed grid: the partials' count and order
+using W1 = ConvS2<8, 32, 120, 160, 2>;
+constexpr int kW1Dy = W1::PIX * 32;  // bf16 per staged gradient tile
+constexpr int kW1Smem = (2 * W1::PATCH + 2 * kW1Dy + 8) * 2;
+static_assert(W1::PIX == 160 && W1::NTHREADS == 160, "five warps of 32 pixels");
+
+__device__ __forceinline__ void w1_stage_dy(bf16* dst, const bf16* __restrict__ dy, int t) {
+  const int b = t / W1::TPI, oy0 = (t - b * W1::TPI) * 2;
+  const bf16* src = dy + ((size_t)b * W1::Ho + oy0) * W1::Wo * 32;
+  // pixel p's 16-byte chunk q lands at chunk q ^ ((p >> 1) & 3) of its row,
+  // so that eight consecutive pixels' chunk q fall in distinct banks
+  for (int e = threadIdx.x; e < kW1Dy / 8; e += W1::NTHREADS) {
+    const int p = e >> 2, q = e & 3;
+    cp_async16(dst + 32 * p + 8 * (q ^ ((p >> 1) & 3)), src + 8 * e, true);
+  }
+}
+
+__global__ void __launch_bounds__(W1::NTHREADS) wgrad1_kernel(const bf16* __restrict__ x,
+                                                              const bf16* __restrict__ dy,
+                                                              float* __restrict__ part,
+                                                              int n_tiles) {
+  extern __shared__ __align__(128) unsigned char w1_smem[];
+  bf16* patches = reinterpret_cast<bf16*>(w1_smem);
+  bf16* dys = patches + 2 * W1::PATCH;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mat = lane >> 3, rr = lane & 7, gq = lane >> 2, cq = lane & 3;
+  if ((int)blockIdx.x < n_tiles) {
+    conv_stage_rows<W1, 8, 120, 160>(patches, x, blockIdx.x);
+    w1_stage_dy(dys, dy, blockIdx.x);
+  }
+  cp_async_commit();
+  // this lane's B row in k16 step s: pixel 32 warp + 16 s + 8 (mat & 1) + rr
+  int prow[2], pcol[2];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int m = 32 * warp + 16 * s + 8 * (mat & 1) + rr;
+    const int dyr = m / W1::Wo;
+    prow[s] = 2 * dyr;
+    pcol[s] = m - dyr * W1::Wo;
+  }
+  float acc[2][9][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int n8 = 0; n8 < 9; ++n8)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[i][n8][v] = 0.f;
+  int it = 0;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
+    const int tn = t + (int)gridDim.x;
+    if (tn < n_tiles) {
+      conv_stage_rows<W1, 8, 120, 160>(patches + ((it + 1) & 1) * W1::PATCH, x, tn);
+      w1_stage_dy(dys + ((it + 1) & 1) * kW1Dy, dy, tn);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();  // this tile's rows and gradients have landed
+    __syncthreads();
+    const bf16* patch = patches + (it & 1) * W1::PATCH;
+    const bf16* dyt = dys + (it & 1) * kW1Dy;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int p0 = 32 * warp + 16 * s;
+      uint32_t af[2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int p = p0 + 8 * (mat >> 1) + rr, q = 2 * i + (mat & 1);
+        ldsm_x4_t(af[i], dyt + 32 * p + 8 * (q ^ ((p >> 1) & 3)));
+      }
+#pragma unroll
+      for (int t0 = 0; t0 < 9; t0 += 2) {
+        // matrices: tap t0 and t0 + 1 (the last pair's second is tap 8 again,
+        // unused), pixels p0 .. p0 + 7 and p0 + 8 .. p0 + 15
+        const int tap = min(t0 + (mat >> 1), 8);
+        const int ky = tap / 3, kx = tap - 3 * ky;
+        const int r = prow[s] + ky, c = 2 * pcol[s] + kx;
+        uint32_t bf[4];
+        ldsm_x4_t(bf, patch + ((r * 2 + (c & 1)) * W1::WP + (c >> 1)) * 8);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          mma_bf16(acc[i][t0], af[i], bf[0], bf[1]);
+          if (t0 + 1 < 9) mma_bf16(acc[i][t0 + 1], af[i], bf[2], bf[3]);
+        }
+      }
+    }
+    __syncthreads();  // the buffers are refilled next iteration
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  // the warps' sums, added in warp order: warp w's 32 x 72 block staged,
+  // then every thread adds its elements over the warps
+  float* red = reinterpret_cast<float*>(w1_smem);  // 5 x 2304 floats fit the buffers
+  static_assert(5 * 32 * 72 * 4 <= kW1Smem, "reduction area");
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int n8 = 0; n8 < 9; ++n8)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int m = 16 * i + gq + 8 * (v >> 1), n = 8 * n8 + 2 * cq + (v & 1);
+        red[(warp * 32 + m) * 72 + n] = acc[i][n8][v];
+      }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 32 * 72; e += W1::NTHREADS) {
+    float v = 0.f;
+#pragma unroll
+    for (int w = 0; w < W1::WARPS; ++w) v += red[w * 32 * 72 + e];
+    part[(size_t)blockIdx.x * 32 * 72 + e] = v;
+  }
+}
+
 // out[m * n_out + n] = sum_s part[(s * M + m) * N + n] for m < m_valid,
 // n < n_valid, summed in split order.
 __global__ void reduce_partials_kernel(const float* __restrict__ part, int S, int M, int N,
@@ -825,6 +947,28 @@ __global__ void reduce_partials_kernel(const float* __restrict__ part, int S, in
     float acc = 0.f;
     for (int s = 0; s < S; ++s) acc += part[((size_t)s * M + m) * N + n];
     out[e] = acc;
+  }
+}
+
+// out[e] = sum_s part[s * E + e] for e < E with many partials: block
+// (32, 16) takes 32 consecutive e, thread (x, y) adds s = y, y + 16, ... in
+// order, and the 16 row sums are added in y order (a fixed order, so the
+// result does not depend on timing).
+__global__ void __launch_bounds__(512) reduce_partials_wide_kernel(const float* __restrict__ part,
+                                                                   int S, int E,
+                                                                   float* __restrict__ out) {
+  __shared__ float rows[16][33];
+  const int e = blockIdx.x * 32 + threadIdx.x;
+  float acc = 0.f;
+  if (e < E)
+    for (int s = threadIdx.y; s < S; s += 16) acc += part[(size_t)s * E + e];
+  rows[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && e < E) {
+    float v = 0.f;
+#pragma unroll
+    for (int y = 0; y < 16; ++y) v += rows[y][threadIdx.x];
+    out[e] = v;
   }
 }
 
@@ -1164,7 +1308,7 @@ int splits_count(int K, int s) {
 int class_hc(int H, int py) { return (H + 1 - py) / 2; }
 
 size_t max_partials(int B) {
-  size_t mx = 0;
+  size_t mx = (size_t)kW1Grid * 32 * 72;  // layer 1's weight gradient
   auto upd = [&](int M, int N, int K) {
     const int s = splits_for(M, N, K);
     const int ks = k_split_for(K, s);
@@ -1308,6 +1452,28 @@ int wgrad(Gemm g, int m_valid, float* part, float* out, cudaStream_t st) {
   const size_t total = (size_t)m_valid * g.N;
   const int blocks = (int)min((total + 255) / 256, (size_t)4096);
   reduce_partials_kernel<<<blocks, 256, 0, st>>>(part, S, g.M, g.N, m_valid, g.N, out);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+// Layer 1's weight gradient (wgrad1_kernel) into out [32][72].
+int wgrad1(const bf16* x, const bf16* dy, int B, float* part, float* out, cudaStream_t st) {
+  static bool ready[64] = {};
+  int dev = 0;
+  GS2D_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return GS2D_ERR_CUDA;
+  if (!ready[dev]) {
+    GS2D_CUDA_TRY(cudaFuncSetAttribute(wgrad1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kW1Smem));
+    ready[dev] = true;
+  }
+  const long long n_tiles = (long long)B * W1::TPI;
+  if (n_tiles <= 0 || n_tiles > 0x7FFFFFFF) return n_tiles <= 0 ? GS2D_OK : GS2D_ERR_INVALID_ARG;
+  // a fixed grid (the partials' count), idle blocks contributing zeros
+  wgrad1_kernel<<<kW1Grid, W1::NTHREADS, kW1Smem, st>>>(x, dy, part, (int)n_tiles);
+  GS2D_LAUNCH_CHECK();
+  reduce_partials_wide_kernel<<<(32 * 72 + 31) / 32, dim3(32, 16), 0, st>>>(part, kW1Grid, 32 * 72,
+                                                                           out);
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
 }
@@ -1469,7 +1635,8 @@ int backward(const float* params, const bf16* x, int B, const Ws& w, float* grad
     g.K = P;
     g.a = op(cur, kCout[l], kCout[l]);
     g.b = conv_op(a_in, g.N, l, kCin[l]);
-    r = wgrad<R_DENSE, R_IM2COL>(g, kCout[l], w.part, grad + L.w_off[l], st);
+    r = l == 0 ? wgrad1(x, cur, B, w.part, grad + L.w_off[0], st)
+               : wgrad<R_DENSE, R_IM2COL>(g, kCout[l], w.part, grad + L.w_off[l], st);
     if (r) return r;
     r = bias_grad(cur, P, kCout[l], kCout[l], w.part, grad + L.b_off[l], st);
     if (r) return r;
