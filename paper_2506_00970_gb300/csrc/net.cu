@@ -822,14 +822,18 @@ int conv_s2(const bf16* x, int B, const bf16* wt, const float* bias, bf16* out, 
 // tile's pixels 32 w .. 32 w + 31 with mma.m16n8k16 (A = dY^T by ldmatrix
 // .trans from the staged gradients, B = each tap's 8 input channels by
 // ldmatrix .trans from the staged rows), accumulating the 32 x 72 product
-// over all its tiles in registers.  The block's warps are summed in a fixed
-// order into one partial per block (reduce_partials_wide_kernel adds the
-// blocks in a fixed order), so the result does not depend on timing.  Reads the input map
-// and the output gradients once (2 x 78.6 MB at batch 256).
+// over all its tiles in registers; lane c of warp w also adds channel c of
+// the bias gradient db[c] = sum_p dY[p][c] over the same pixels.  The
+// block's warps are summed in a fixed order into one partial per block
+// ([32 x 72 weights | 32 bias] floats; reduce_partials_wide_kernel adds the
+// blocks in a fixed order), so the result does not depend on timing.
+// Reads the input map and the output gradients once (2 x 78.6 MB at batch
+// 256).
 constexpr int kW1Grid = 3 * 152;  // fixed grid: the partials' count and order
 using W1 = ConvS2<8, 32, 120, 160, 2>;
 constexpr int kW1Dy = W1::PIX * 32;  // bf16 per staged gradient tile
 constexpr int kW1Smem = (2 * W1::PATCH + 2 * kW1Dy + 8) * 2;
+constexpr int kW1Part = 32 * 72 + 32;  // floats per block partial
 static_assert(W1::PIX == 160 && W1::NTHREADS == 160, "five warps of 32 pixels");
 
 __device__ __forceinline__ void w1_stage_dy(bf16* dst, const bf16* __restrict__ dy, int t) {
@@ -866,7 +870,7 @@ __global__ void __launch_bounds__(W1::NTHREADS) wgrad1_kernel(const bf16* __rest
     prow[s] = 2 * dyr;
     pcol[s] = m - dyr * W1::Wo;
   }
-  float acc[2][9][4];
+  float acc[2][9][4], bsum = 0.f;
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -910,6 +914,13 @@ __global__ void __launch_bounds__(W1::NTHREADS) wgrad1_kernel(const bf16* __rest
         }
       }
     }
+    // bias: channel `lane` over this warp's 32 pixels (chunk lane / 8 of
+    // pixel p sits at chunk (lane / 8) ^ ((p >> 1) & 3))
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) {
+      const int p = 32 * warp + j;
+      bsum += __bfloat162float(dyt[32 * p + 8 * ((lane >> 3) ^ ((p >> 1) & 3)) + (lane & 7)]);
+    }
     __syncthreads();  // the buffers are refilled next iteration
   }
   cp_async_wait<0>();
@@ -918,6 +929,8 @@ __global__ void __launch_bounds__(W1::NTHREADS) wgrad1_kernel(const bf16* __rest
   // then every thread adds its elements over the warps
   float* red = reinterpret_cast<float*>(w1_smem);  // 5 x 2304 floats fit the buffers
   static_assert(5 * 32 * 72 * 4 <= kW1Smem, "reduction area");
+  __shared__ float bred[W1::WARPS][32];
+  bred[warp][lane] = bsum;
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -932,8 +945,152 @@ __global__ void __launch_bounds__(W1::NTHREADS) wgrad1_kernel(const bf16* __rest
     float v = 0.f;
 #pragma unroll
     for (int w = 0; w < W1::WARPS; ++w) v += red[w * 32 * 72 + e];
-    part[(size_t)blockIdx.x * 32 * 72 + e] = v;
+    part[(size_t)blockIdx.x * kW1Part + e] = v;
   }
+  if (threadIdx.x < 32) {
+    float v = 0.f;
+#pragma unroll
+    for (int w = 0; w < W1::WARPS; ++w) v += bred[w][threadIdx.x];
+    part[(size_t)blockIdx.x * kW1Part + 32 * 72 + threadIdx.x] = v;
+  }
+}
+
+// Layer 2's data gradient dX[b][iy][ix][ci] = mask(b, iy, ix, ci) x
+// sum over the taps (ky, kx) that reach (iy, ix) of sum_co dY[b][oy][ox][co]
+// W[co][ky][kx][ci] with oy = (iy + 1 - ky) / 2, ox = (ix + 1 - kx) / 2 (the
+// transpose of the stride-2 convolution; iy even is reached by ky = 1 only,
+// iy odd by ky in {0, 2}, likewise for columns), mask = (layer-1 output > 0)
+// (the ReLU).  A tile is four input rows 4a .. 4a + 3 of one image; it needs
+// output-gradient rows 2a .. 2a + 2 (41 columns, the last and a missing row
+// staged as zeros), staged with the next tile's in flight, and the weights
+// stay in shared memory for the block's whole walk.  The 320 pixels fall in
+// the four parity classes of 80 pixels (5 m16 row tiles each); warp w takes
+// row tile w of every class (9 taps x 64 output channels of K in all), so
+// the warps are balanced; A = the pixels' gradient rows (ldmatrix), B = the
+// tap's weights (ldmatrix .trans).  Results go through shared memory so the
+// masked bf16 gradient is written in whole rows.
+constexpr int kD2Ci = 32, kD2Co = 64, kD2H = 60, kD2W = 80, kD2Ho = 30, kD2Wo = 40;
+constexpr int kD2Rows = 4;                          // input rows per tile
+constexpr int kD2Tpi = kD2H / kD2Rows;              // tiles per image
+constexpr int kD2Cols = kD2Wo + 1;                  // staged gradient columns
+constexpr int kD2Dy = 3 * kD2Cols * kD2Co;          // bf16 per staged gradient tile
+constexpr int kD2Wt = 9 * kD2Co * kD2Ci;            // bf16 of the weights
+constexpr int kD2Out = kD2Rows * kD2W * kD2Ci;      // bf16 of a tile's result
+constexpr int kD2Threads = 160;
+constexpr int kD2Smem = (2 * kD2Dy + kD2Wt + kD2Out) * 2;
+static_assert(kD2Rows * kD2W == 4 * 5 * 16 && kD2H % kD2Rows == 0, "5 row tiles per class");
+static_assert(kCin[1] == kD2Ci && kCout[1] == kD2Co && kHin[1] == kD2H && kWin[1] == kD2W &&
+                  kHin[2] == kD2Ho && kWin[2] == kD2Wo,
+              "layer 2");
+
+__device__ __forceinline__ void d2_stage_dy(bf16* dst, const bf16* __restrict__ dy, int t) {
+  const int b = t / kD2Tpi, oy0 = 2 * (t - b * kD2Tpi);
+  // row lr, column ox, chunk q at chunk q ^ (ox & 7) of its 128-byte row
+  for (int e = threadIdx.x; e < 3 * kD2Cols * 8; e += kD2Threads) {
+    const int lr = e / (kD2Cols * 8), rem = e - lr * kD2Cols * 8;
+    const int ox = rem >> 3, q = rem & 7, oy = oy0 + lr;
+    const bool ok = oy < kD2Ho && ox < kD2Wo;
+    cp_async16(dst + (lr * kD2Cols + ox) * kD2Co + 8 * (q ^ (ox & 7)),
+               ok ? dy + (((size_t)b * kD2Ho + oy) * kD2Wo + ox) * kD2Co + 8 * q : dy, ok);
+  }
+}
+
+__global__ void __launch_bounds__(kD2Threads, 2) dgrad2_kernel(const bf16* __restrict__ dy,
+                                                              const bf16* __restrict__ wt,
+                                                              const bf16* __restrict__ mask,
+                                                              bf16* __restrict__ dx, int n_tiles) {
+  extern __shared__ __align__(128) unsigned char d2_smem[];
+  bf16* dys = reinterpret_cast<bf16*>(d2_smem);
+  bf16* wts = dys + 2 * kD2Dy;
+  bf16* outs = wts + kD2Wt;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mat = lane >> 3, rr = lane & 7, gq = lane >> 2, cq = lane & 3;
+  // weights [tap][co][ci], chunk q of row co at q ^ ((co >> 1) & 3)
+  for (int e = threadIdx.x; e < kD2Wt / 8; e += kD2Threads) {
+    const int co = e / 36, rem = e - co * 36, tap = rem >> 2, q = rem & 3;
+    cp_async16(wts + (tap * kD2Co + co) * kD2Ci + 8 * (q ^ ((co >> 1) & 3)),
+               wt + (size_t)co * 9 * kD2Ci + tap * kD2Ci + 8 * q, true);
+  }
+  if ((int)blockIdx.x < n_tiles) d2_stage_dy(dys, dy, blockIdx.x);
+  cp_async_commit();
+  int it = 0;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
+    const int tn = t + (int)gridDim.x;
+    if (tn < n_tiles) d2_stage_dy(dys + ((it + 1) & 1) * kD2Dy, dy, tn);
+    cp_async_commit();
+    cp_async_wait<1>();  // this tile's gradient rows (and the weights) have landed
+    __syncthreads();
+    const bf16* dyt = dys + (it & 1) * kD2Dy;
+#pragma unroll 1
+    for (int cls = 0; cls < 4; ++cls) {
+      const int pr = cls >> 1, pc = cls & 1;
+      // this lane's A row: class pixel u = 16 warp + 8 (mat & 1) + rr
+      const int u = 16 * warp + 8 * (mat & 1) + rr;
+      const int r = pr + 2 * (u / kD2Wo), ix = pc + 2 * (u % kD2Wo);
+      float acc[4][4];
+#pragma unroll
+      for (int n8 = 0; n8 < 4; ++n8)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[n8][v] = 0.f;
+      const int nky = pr ? 2 : 1, nkx = pc ? 2 : 1;
+      for (int tyi = 0; tyi < nky; ++tyi)
+        for (int txi = 0; txi < nkx; ++txi) {
+          const int ky = pr ? 2 * tyi : 1, kx = pc ? 2 * txi : 1;
+          const int lr = (r + 1 - ky) >> 1, ox = (ix + 1 - kx) >> 1;
+          const bf16* arow = dyt + (lr * kD2Cols + ox) * kD2Co;
+          const bf16* wtap = wts + (ky * 3 + kx) * kD2Co * kD2Ci;
+#pragma unroll
+          for (int kk = 0; kk < kD2Co / 16; ++kk) {
+            uint32_t af[4];
+            ldsm_x4(af, arow + 8 * ((2 * kk + (mat >> 1)) ^ (ox & 7)));
+            const int co = 16 * kk + 8 * (mat & 1) + rr;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              uint32_t bf[4];
+              ldsm_x4_t(bf, wtap + co * kD2Ci + 8 * ((2 * h + (mat >> 1)) ^ ((co >> 1) & 3)));
+              mma_bf16(acc[2 * h], af, bf[0], bf[1]);
+              mma_bf16(acc[2 * h + 1], af, bf[2], bf[3]);
+            }
+          }
+        }
+      // bf16 results into the tile's [row][column][ci] staging, chunk n8 of
+      // pixel ix at n8 ^ ((ix >> 1) & 3)
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int uo = 16 * warp + gq + 8 * hh;
+        const int ro = pr + 2 * (uo / kD2Wo), xo = pc + 2 * (uo % kD2Wo);
+        bf16* orow = outs + (ro * kD2W + xo) * kD2Ci;
+#pragma unroll
+        for (int n8 = 0; n8 < 4; ++n8)
+          *reinterpret_cast<__nv_bfloat162*>(orow + 8 * (n8 ^ ((xo >> 1) & 3)) + 2 * cq) =
+              __floats2bfloat162_rn(acc[n8][2 * hh], acc[n8][2 * hh + 1]);
+      }
+    }
+    __syncthreads();
+    // masked rows out: 16-byte chunks, the mask read beside them
+    {
+      const int b = t / kD2Tpi, iy0 = kD2Rows * (t - b * kD2Tpi);
+      const size_t base = ((size_t)b * kD2H + iy0) * kD2W * kD2Ci;
+      for (int e = threadIdx.x; e < kD2Out / 8; e += kD2Threads) {
+        const int px = e >> 2, q = e & 3, ix = px % kD2W;
+        const uint4 v = *reinterpret_cast<const uint4*>(outs + px * kD2Ci + 8 * (q ^ ((ix >> 1) & 3)));
+        const uint4 m = __ldg(reinterpret_cast<const uint4*>(mask + base + 8 * (size_t)e));
+        const uint32_t vv[4] = {v.x, v.y, v.z, v.w}, mm[4] = {m.x, m.y, m.z, m.w};
+        uint32_t o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          // a bf16 is > 0 iff its bits lie in [0x0001, 0x7F80] (positive,
+          // nonzero, not NaN)
+          const uint32_t lo = (mm[k] & 0xFFFFu) - 1u < 0x7F80u ? 0xFFFFu : 0u;
+          const uint32_t hi = (mm[k] >> 16) - 1u < 0x7F80u ? 0xFFFF0000u : 0u;
+          o[k] = vv[k] & (lo | hi);
+        }
+        *reinterpret_cast<uint4*>(dx + base + 8 * (size_t)e) = make_uint4(o[0], o[1], o[2], o[3]);
+      }
+    }
+    __syncthreads();  // the gradient buffer and the staging are refilled next
+  }
+  cp_async_wait<0>();
 }
 
 // out[m * n_out + n] = sum_s part[(s * M + m) * N + n] for m < m_valid,
@@ -950,25 +1107,29 @@ __global__ void reduce_partials_kernel(const float* __restrict__ part, int S, in
   }
 }
 
-// out[e] = sum_s part[s * E + e] for e < E with many partials: block
-// (32, 16) takes 32 consecutive e, thread (x, y) adds s = y, y + 16, ... in
-// order, and the 16 row sums are added in y order (a fixed order, so the
-// result does not depend on timing).
-__global__ void __launch_bounds__(512) reduce_partials_wide_kernel(const float* __restrict__ part,
-                                                                   int S, int E,
-                                                                   float* __restrict__ out) {
-  __shared__ float rows[16][33];
+// sum_s part[s * ld + e] for e < E with many partials, into out0[e] for
+// e < E0 and out1[e - E0] beyond: block (32, 32) takes 32 consecutive e,
+// thread (x, y) adds s = y, y + 32, ... in order, and the 32 row sums are
+// added in y order (a fixed order, so the result does not depend on timing).
+__global__ void __launch_bounds__(1024) reduce_partials_wide_kernel(
+    const float* __restrict__ part, int S, int ld, int E, int E0, float* __restrict__ out0,
+    float* __restrict__ out1) {
+  __shared__ float rows[32][33];
   const int e = blockIdx.x * 32 + threadIdx.x;
   float acc = 0.f;
   if (e < E)
-    for (int s = threadIdx.y; s < S; s += 16) acc += part[(size_t)s * E + e];
+#pragma unroll 8
+    for (int s = threadIdx.y; s < S; s += 32) acc += part[(size_t)s * ld + e];
   rows[threadIdx.y][threadIdx.x] = acc;
   __syncthreads();
   if (threadIdx.y == 0 && e < E) {
     float v = 0.f;
 #pragma unroll
-    for (int y = 0; y < 16; ++y) v += rows[y][threadIdx.x];
-    out[e] = v;
+    for (int y = 0; y < 32; ++y) v += rows[y][threadIdx.x];
+    if (e < E0)
+      out0[e] = v;
+    else
+      out1[e - E0] = v;
   }
 }
 
@@ -1308,7 +1469,7 @@ int splits_count(int K, int s) {
 int class_hc(int H, int py) { return (H + 1 - py) / 2; }
 
 size_t max_partials(int B) {
-  size_t mx = (size_t)kW1Grid * 32 * 72;  // layer 1's weight gradient
+  size_t mx = (size_t)kW1Grid * kW1Part;  // layer 1's weight and bias gradients
   auto upd = [&](int M, int N, int K) {
     const int s = splits_for(M, N, K);
     const int ks = k_split_for(K, s);
@@ -1456,8 +1617,10 @@ int wgrad(Gemm g, int m_valid, float* part, float* out, cudaStream_t st) {
   return GS2D_OK;
 }
 
-// Layer 1's weight gradient (wgrad1_kernel) into out [32][72].
-int wgrad1(const bf16* x, const bf16* dy, int B, float* part, float* out, cudaStream_t st) {
+// Layer 1's weight gradient (wgrad1_kernel) into out_w [32][72] and its
+// bias gradient into out_b [32].
+int wgrad1(const bf16* x, const bf16* dy, int B, float* part, float* out_w, float* out_b,
+           cudaStream_t st) {
   static bool ready[64] = {};
   int dev = 0;
   GS2D_CUDA_TRY(cudaGetDevice(&dev));
@@ -1472,8 +1635,33 @@ int wgrad1(const bf16* x, const bf16* dy, int B, float* part, float* out, cudaSt
   // a fixed grid (the partials' count), idle blocks contributing zeros
   wgrad1_kernel<<<kW1Grid, W1::NTHREADS, kW1Smem, st>>>(x, dy, part, (int)n_tiles);
   GS2D_LAUNCH_CHECK();
-  reduce_partials_wide_kernel<<<(32 * 72 + 31) / 32, dim3(32, 16), 0, st>>>(part, kW1Grid, 32 * 72,
-                                                                           out);
+  reduce_partials_wide_kernel<<<kW1Part / 32, dim3(32, 32), 0, st>>>(part, kW1Grid, kW1Part,
+                                                                     kW1Part, 32 * 72, out_w, out_b);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
+// Layer 2's data gradient (dgrad2_kernel): dy [B][30][40][64], the layer's
+// bf16 weights, mask = the layer-1 output [B][60][80][32], dx like mask.
+int dgrad2(const bf16* dy, int B, const bf16* wt, const bf16* mask, bf16* dx, cudaStream_t st) {
+  static int slots[64] = {};  // resident blocks per device (0: not yet known)
+  int dev = 0;
+  GS2D_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return GS2D_ERR_CUDA;
+  if (!slots[dev]) {
+    GS2D_CUDA_TRY(
+        cudaFuncSetAttribute(dgrad2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kD2Smem));
+    int per_sm = 0, sms = 0;
+    GS2D_CUDA_TRY(
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dgrad2_kernel, kD2Threads, kD2Smem));
+    GS2D_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    slots[dev] = max(1, per_sm) * max(1, sms);
+  }
+  if (B <= 0) return GS2D_OK;
+  const long long n_tiles = (long long)B * kD2Tpi;
+  if (n_tiles > 0x7FFFFFFF) return GS2D_ERR_INVALID_ARG;
+  const int grid = (int)(n_tiles < (long long)slots[dev] ? n_tiles : (long long)slots[dev]);
+  dgrad2_kernel<<<grid, kD2Threads, kD2Smem, st>>>(dy, wt, mask, dx, (int)n_tiles);
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
 }
@@ -1483,7 +1671,8 @@ int bias_grad(const bf16* z, int rows, int C, int c_valid, float* part, float* o
   const int chunks = (rows + rpb - 1) / rpb;
   colsum_partial_kernel<<<chunks, 256, 0, st>>>(z, rows, C, rpb, part);
   GS2D_LAUNCH_CHECK();
-  reduce_partials_kernel<<<1, 256, 0, st>>>(part, chunks, 1, C, 1, c_valid, out);
+  reduce_partials_wide_kernel<<<(c_valid + 31) / 32, dim3(32, 32), 0, st>>>(part, chunks, C, c_valid,
+                                                                           c_valid, out, nullptr);
   GS2D_LAUNCH_CHECK();
   return GS2D_OK;
 }
@@ -1635,15 +1824,23 @@ int backward(const float* params, const bf16* x, int B, const Ws& w, float* grad
     g.K = P;
     g.a = op(cur, kCout[l], kCout[l]);
     g.b = conv_op(a_in, g.N, l, kCin[l]);
-    r = l == 0 ? wgrad1(x, cur, B, w.part, grad + L.w_off[0], st)
-               : wgrad<R_DENSE, R_IM2COL>(g, kCout[l], w.part, grad + L.w_off[l], st);
+    if (l == 0) {
+      r = wgrad1(x, cur, B, w.part, grad + L.w_off[0], grad + L.b_off[0], st);
+      if (r) return r;
+      break;
+    }
+    r = wgrad<R_DENSE, R_IM2COL>(g, kCout[l], w.part, grad + L.w_off[l], st);
     if (r) return r;
     r = bias_grad(cur, P, kCout[l], kCout[l], w.part, grad + L.b_off[l], st);
     if (r) return r;
-    if (l == 0) break;
-    // data gradient: one GEMM per parity class of the input pixels, each
-    // with only the taps that reach it (9 taps over the 4 classes)
-    for (int py = 0; py < 2; ++py)
+    // data gradient: layer 2's by its direct kernel; the others by one GEMM
+    // per parity class of the input pixels, each with only the taps that
+    // reach it (9 taps over the 4 classes)
+    if (l == 1) {
+      r = dgrad2(cur, B, w.wbf + L.wbf_off[1], w.act[1], nxt, st);
+      if (r) return r;
+    }
+    for (int py = 0; py < 2 && l != 1; ++py)
       for (int px = 0; px < 2; ++px) {
         const int Hc = class_hc(kHin[l], py), Wc = class_hc(kWin[l], px);
         Gemm d{};
