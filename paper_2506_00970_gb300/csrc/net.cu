@@ -1093,6 +1093,145 @@ __global__ void __launch_bounds__(kD2Threads, 2) dgrad2_kernel(const bf16* __res
   cp_async_wait<0>();
 }
 
+// Layer 2's weight and bias gradients dW[co][tap x 32 + ci] = sum_p dY[p][co]
+// x[p, tap][ci], db[co] = sum_p dY[p][co], on the staging of wgrad1_kernel
+// widened to 32 input channels: a tile is two output rows (80 pixels) of one
+// image with its five input rows in column-parity planes and its 80 x 64
+// output gradients (the next tile's in flight).  Warp w owns output channels
+// 32 (w & 1) .. + 31 and the nine n8 column tiles 9 (w >> 1) .. + 8 of the
+// 288 (tap, ci) columns: per 16 pixels two A fragments (dY^T, ldmatrix
+// .trans) and nine B fragments (x, ldmatrix .trans), 18 mma.m16n8k16.  Thread
+// t also adds channel t % 64 of the bias over pixels t / 64, + 4, ...  One
+// partial per block ([64 x 288 | 64] floats; fixed grid, warps and blocks
+// summed in a fixed order).
+constexpr int kW2Ci = 32, kW2Co = 64, kW2H = 60, kW2W = 80, kW2Ho = 30, kW2Wo = 40;
+constexpr int kW2Pix = 2 * kW2Wo;                     // output pixels per tile
+constexpr int kW2Tpi = kW2Ho / 2;                     // tiles per image
+constexpr int kW2Wp = (kW2W + 2) / 2;                 // entries per parity plane
+constexpr int kW2Patch = 5 * 2 * kW2Wp * kW2Ci;       // bf16 per staged input tile
+constexpr int kW2Dy = kW2Pix * kW2Co;                 // bf16 per staged gradient tile
+constexpr int kW2Threads = 256;
+constexpr int kW2Smem = (2 * kW2Patch + 2 * kW2Dy) * 2;
+constexpr int kW2Grid = 2 * 152;                      // fixed grid: the partials' count
+constexpr int kW2N = 9 * kW2Ci;
+constexpr int kW2Part = kW2Co * kW2N + kW2Co;         // floats per block partial
+static_assert(kCin[1] == kW2Ci && kCout[1] == kW2Co && kHin[1] == kW2H && kWin[1] == kW2W &&
+                  kHin[2] == kW2Ho && kWin[2] == kW2Wo,
+              "layer 2");
+static_assert(kW2Pix % 16 == 0 && 8 * 4 * 9 * 8 == kW2Co * kW2N / 8, "warp split");
+
+__device__ __forceinline__ void w2_stage(bf16* patch, bf16* dys, const bf16* __restrict__ x,
+                                         const bf16* __restrict__ dy, int t) {
+  const int b = t / kW2Tpi, oy0 = 2 * (t - b * kW2Tpi), iy0 = 2 * oy0 - 1;
+  const bf16* xb = x + (size_t)b * kW2H * kW2W * kW2Ci;
+  // input row r, padded column c = ix + 1: plane c & 1, entry c >> 1, chunk
+  // q at q ^ ((entry >> 1) & 3)
+  constexpr int ROWCH = (kW2W + 2) * 4;
+  for (int e = threadIdx.x; e < 5 * ROWCH; e += kW2Threads) {
+    const int r = e / ROWCH, rem = e - r * ROWCH;
+    const int c = rem >> 2, q = rem & 3;
+    const int iy = iy0 + r, ix = c - 1;
+    const bool ok = iy >= 0 && iy < kW2H && ix >= 0 && ix < kW2W;
+    const int ent = c >> 1;
+    cp_async16(patch + ((r * 2 + (c & 1)) * kW2Wp + ent) * kW2Ci + 8 * (q ^ ((ent >> 1) & 3)),
+               ok ? xb + ((size_t)iy * kW2W + ix) * kW2Ci + 8 * q : xb, ok);
+  }
+  // gradient pixel p, chunk q at q ^ (p & 7)
+  const bf16* src = dy + ((size_t)b * kW2Ho + oy0) * kW2Wo * kW2Co;
+  for (int e = threadIdx.x; e < kW2Dy / 8; e += kW2Threads) {
+    const int p = e >> 3, q = e & 7;
+    cp_async16(dys + p * kW2Co + 8 * (q ^ (p & 7)), src + 8 * e, true);
+  }
+}
+
+__global__ void __launch_bounds__(kW2Threads) wgrad2_kernel(const bf16* __restrict__ x,
+                                                            const bf16* __restrict__ dy,
+                                                            float* __restrict__ part,
+                                                            int n_tiles) {
+  extern __shared__ __align__(128) unsigned char w2_smem[];
+  bf16* patches = reinterpret_cast<bf16*>(w2_smem);
+  bf16* dys = patches + 2 * kW2Patch;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mat = lane >> 3, rr = lane & 7, gq = lane >> 2, cq = lane & 3;
+  const int mh = warp & 1, j0 = 9 * (warp >> 1);
+  if ((int)blockIdx.x < n_tiles) w2_stage(patches, dys, x, dy, blockIdx.x);
+  cp_async_commit();
+  float acc[2][9][4], bsum = 0.f;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int n8 = 0; n8 < 9; ++n8)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[i][n8][v] = 0.f;
+  int it = 0;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
+    const int tn = t + (int)gridDim.x;
+    if (tn < n_tiles)
+      w2_stage(patches + ((it + 1) & 1) * kW2Patch, dys + ((it + 1) & 1) * kW2Dy, x, dy, tn);
+    cp_async_commit();
+    cp_async_wait<1>();  // this tile's rows and gradients have landed
+    __syncthreads();
+    const bf16* patch = patches + (it & 1) * kW2Patch;
+    const bf16* dyt = dys + (it & 1) * kW2Dy;
+#pragma unroll 1
+    for (int p0 = 0; p0 < kW2Pix; p0 += 16) {
+      uint32_t af[2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int p = p0 + 8 * (mat >> 1) + rr, q = 4 * mh + 2 * i + (mat & 1);
+        ldsm_x4_t(af[i], dyt + p * kW2Co + 8 * (q ^ (p & 7)));
+      }
+      // this lane's B row: pixel p0 + 8 (mat & 1) + rr
+      const int pb = p0 + 8 * (mat & 1) + rr;
+      const int dyr = pb / kW2Wo, ox = pb - dyr * kW2Wo;
+#pragma unroll
+      for (int jj = 0; jj < 9; jj += 2) {
+        // matrices: column tiles j0 + jj and j0 + jj + 1 (the last pair's
+        // second repeats the first, unused)
+        const int j = j0 + min(jj + (mat >> 1), 8);
+        const int tap = j >> 2, q = j & 3;
+        const int ky = tap / 3, kx = tap - 3 * ky;
+        const int r = 2 * dyr + ky, c = 2 * ox + kx, ent = c >> 1;
+        uint32_t bf[4];
+        ldsm_x4_t(bf, patch + ((r * 2 + (c & 1)) * kW2Wp + ent) * kW2Ci + 8 * (q ^ ((ent >> 1) & 3)));
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          mma_bf16(acc[i][jj], af[i], bf[0], bf[1]);
+          if (jj + 1 < 9) mma_bf16(acc[i][jj + 1], af[i], bf[2], bf[3]);
+        }
+      }
+    }
+    {  // bias: channel threadIdx.x % 64 over pixels threadIdx.x / 64 + 4 k
+      const int c = threadIdx.x & 63;
+#pragma unroll 4
+      for (int p = threadIdx.x >> 6; p < kW2Pix; p += 4)
+        bsum += __bfloat162float(dyt[p * kW2Co + 8 * ((c >> 3) ^ (p & 7)) + (c & 7)]);
+    }
+    __syncthreads();  // the buffers are refilled next iteration
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  // the warps' blocks are disjoint: every warp writes its 32 x 72 block; the
+  // bias's four pixel groups are added in order
+  float* out = part + (size_t)blockIdx.x * kW2Part;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int n8 = 0; n8 < 9; ++n8)
+#pragma unroll
+      for (int hv = 0; hv < 2; ++hv) {
+        const int m = 32 * mh + 16 * i + gq + 8 * hv, n = 8 * (j0 + n8) + 2 * cq;
+        *reinterpret_cast<float2*>(out + m * kW2N + n) =
+            make_float2(acc[i][n8][2 * hv], acc[i][n8][2 * hv + 1]);
+      }
+  float* red = reinterpret_cast<float*>(w2_smem);
+  red[threadIdx.x] = bsum;
+  __syncthreads();
+  if (threadIdx.x < kW2Co)
+    out[kW2Co * kW2N + threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + 64] +
+                                      red[threadIdx.x + 128] + red[threadIdx.x + 192];
+}
+
 // out[m * n_out + n] = sum_s part[(s * M + m) * N + n] for m < m_valid,
 // n < n_valid, summed in split order.
 __global__ void reduce_partials_kernel(const float* __restrict__ part, int S, int M, int N,
@@ -1468,8 +1607,17 @@ int splits_count(int K, int s) {
 }
 int class_hc(int H, int py) { return (H + 1 - py) / 2; }
 
+// Rows per block of the bias-gradient column sums: about 304 blocks, a
+// multiple of the rows one pass of the block covers (256 / (C / 8)).
+int colsum_rows_per_block(int rows, int C) {
+  const int nsub = 256 / (C / 8);
+  const int want = (rows + 303) / 304;
+  return max(nsub, (want + nsub - 1) / nsub * nsub);
+}
+
 size_t max_partials(int B) {
-  size_t mx = (size_t)kW1Grid * kW1Part;  // layer 1's weight and bias gradients
+  // layers 1 and 2's weight and bias gradients
+  size_t mx = max((size_t)kW1Grid * kW1Part, (size_t)kW2Grid * kW2Part);
   auto upd = [&](int M, int N, int K) {
     const int s = splits_for(M, N, K);
     const int ks = k_split_for(K, s);
@@ -1482,7 +1630,8 @@ size_t max_partials(int B) {
   for (int l = 0; l < kConv; ++l) {
     upd(kCout[l], 9 * kCin[l], B * kHin[l + 1] * kWin[l + 1]);
     const int rows = B * kHin[l + 1] * kWin[l + 1];
-    mx = max(mx, (size_t)((rows + 1023) / 1024) * kCout[l]);
+    const int rpb = colsum_rows_per_block(rows, kCout[l]);
+    mx = max(mx, (size_t)((rows + rpb - 1) / rpb) * kCout[l]);
     nom(kHin[l + 1] * kWin[l + 1], kCout[l], 9 * kCin[l]);
     for (int py = 0; py < 2; ++py)
       for (int px = 0; px < 2; ++px)
@@ -1495,7 +1644,10 @@ size_t max_partials(int B) {
   nom(1, kOutPad, kHidden);
   nom(1, kFlat, kHidden);
   nom(1, kHidden, kOutPad);
-  mx = max(mx, (size_t)((B + 1023) / 1024) * kHidden);
+  for (const int C : {kHidden, kOutPad}) {
+    const int rpb = colsum_rows_per_block(B, C);
+    mx = max(mx, (size_t)((B + rpb - 1) / rpb) * C);
+  }
   return mx;
 }
 
@@ -1666,8 +1818,31 @@ int dgrad2(const bf16* dy, int B, const bf16* wt, const bf16* mask, bf16* dx, cu
   return GS2D_OK;
 }
 
+// Layer 2's weight gradient (wgrad2_kernel) into out_w [64][288] and its
+// bias gradient into out_b [64].
+int wgrad2(const bf16* x, const bf16* dy, int B, float* part, float* out_w, float* out_b,
+           cudaStream_t st) {
+  static bool ready[64] = {};
+  int dev = 0;
+  GS2D_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return GS2D_ERR_CUDA;
+  if (!ready[dev]) {
+    GS2D_CUDA_TRY(cudaFuncSetAttribute(wgrad2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kW2Smem));
+    ready[dev] = true;
+  }
+  const long long n_tiles = (long long)B * kW2Tpi;
+  if (n_tiles <= 0 || n_tiles > 0x7FFFFFFF) return n_tiles <= 0 ? GS2D_OK : GS2D_ERR_INVALID_ARG;
+  wgrad2_kernel<<<kW2Grid, kW2Threads, kW2Smem, st>>>(x, dy, part, (int)n_tiles);
+  GS2D_LAUNCH_CHECK();
+  reduce_partials_wide_kernel<<<kW2Part / 32, dim3(32, 32), 0, st>>>(part, kW2Grid, kW2Part, kW2Part,
+                                                                     kW2Co * kW2N, out_w, out_b);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
+}
+
 int bias_grad(const bf16* z, int rows, int C, int c_valid, float* part, float* out, cudaStream_t st) {
-  const int rpb = 1024;
+  const int rpb = colsum_rows_per_block(rows, C);
   const int chunks = (rows + rpb - 1) / rpb;
   colsum_partial_kernel<<<chunks, 256, 0, st>>>(z, rows, C, rpb, part);
   GS2D_LAUNCH_CHECK();
@@ -1829,10 +2004,15 @@ int backward(const float* params, const bf16* x, int B, const Ws& w, float* grad
       if (r) return r;
       break;
     }
-    r = wgrad<R_DENSE, R_IM2COL>(g, kCout[l], w.part, grad + L.w_off[l], st);
-    if (r) return r;
-    r = bias_grad(cur, P, kCout[l], kCout[l], w.part, grad + L.b_off[l], st);
-    if (r) return r;
+    if (l == 1) {
+      r = wgrad2(a_in, cur, B, w.part, grad + L.w_off[1], grad + L.b_off[1], st);
+      if (r) return r;
+    } else {
+      r = wgrad<R_DENSE, R_IM2COL>(g, kCout[l], w.part, grad + L.w_off[l], st);
+      if (r) return r;
+      r = bias_grad(cur, P, kCout[l], kCout[l], w.part, grad + L.b_off[l], st);
+      if (r) return r;
+    }
     // data gradient: layer 2's by its direct kernel; the others by one GEMM
     // per parity class of the input pixels, each with only the taps that
     // reach it (9 taps over the 4 classes)
