@@ -968,7 +968,8 @@ __global__ void __launch_bounds__(W1::NTHREADS) wgrad1_kernel(const bf16* __rest
 // row tile w of every class (9 taps x 64 output channels of K in all), so
 // the warps are balanced; A = the pixels' gradient rows (ldmatrix), B = the
 // tap's weights (ldmatrix .trans).  Results go through shared memory so the
-// masked bf16 gradient is written in whole rows.
+// masked bf16 gradient is written in whole rows; the tile's mask rows are
+// copied in (cp.async) while it computes.
 constexpr int kD2Ci = 32, kD2Co = 64, kD2H = 60, kD2W = 80, kD2Ho = 30, kD2Wo = 40;
 constexpr int kD2Rows = 4;                          // input rows per tile
 constexpr int kD2Tpi = kD2H / kD2Rows;              // tiles per image
@@ -977,7 +978,7 @@ constexpr int kD2Dy = 3 * kD2Cols * kD2Co;          // bf16 per staged gradient 
 constexpr int kD2Wt = 9 * kD2Co * kD2Ci;            // bf16 of the weights
 constexpr int kD2Out = kD2Rows * kD2W * kD2Ci;      // bf16 of a tile's result
 constexpr int kD2Threads = 160;
-constexpr int kD2Smem = (2 * kD2Dy + kD2Wt + kD2Out) * 2;
+constexpr int kD2Smem = (2 * kD2Dy + kD2Wt + 2 * kD2Out) * 2;
 static_assert(kD2Rows * kD2W == 4 * 5 * 16 && kD2H % kD2Rows == 0, "5 row tiles per class");
 static_assert(kCin[1] == kD2Ci && kCout[1] == kD2Co && kHin[1] == kD2H && kWin[1] == kD2W &&
                   kHin[2] == kD2Ho && kWin[2] == kD2Wo,
@@ -1003,6 +1004,7 @@ __global__ void __launch_bounds__(kD2Threads, 2) dgrad2_kernel(const bf16* __res
   bf16* dys = reinterpret_cast<bf16*>(d2_smem);
   bf16* wts = dys + 2 * kD2Dy;
   bf16* outs = wts + kD2Wt;
+  bf16* masks = outs + kD2Out;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int mat = lane >> 3, rr = lane & 7, gq = lane >> 2, cq = lane & 3;
   // weights [tap][co][ci], chunk q of row co at q ^ ((co >> 1) & 3)
@@ -1015,11 +1017,18 @@ __global__ void __launch_bounds__(kD2Threads, 2) dgrad2_kernel(const bf16* __res
   cp_async_commit();
   int it = 0;
   for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
+    // this tile's gradient rows (and the weights) have landed, and the last
+    // tile's write-out is done with the result and mask buffers
+    cp_async_wait<0>();
+    __syncthreads();
+    const int b = t / kD2Tpi, iy0 = kD2Rows * (t - b * kD2Tpi);
+    const size_t base = ((size_t)b * kD2H + iy0) * kD2W * kD2Ci;
+    for (int e = threadIdx.x; e < kD2Out / 8; e += kD2Threads)
+      cp_async16(masks + 8 * e, mask + base + 8 * (size_t)e, true);
+    cp_async_commit();
     const int tn = t + (int)gridDim.x;
     if (tn < n_tiles) d2_stage_dy(dys + ((it + 1) & 1) * kD2Dy, dy, tn);
     cp_async_commit();
-    cp_async_wait<1>();  // this tile's gradient rows (and the weights) have landed
-    __syncthreads();
     const bf16* dyt = dys + (it & 1) * kD2Dy;
 #pragma unroll 1
     for (int cls = 0; cls < 4; ++cls) {
@@ -1066,15 +1075,14 @@ __global__ void __launch_bounds__(kD2Threads, 2) dgrad2_kernel(const bf16* __res
               __floats2bfloat162_rn(acc[n8][2 * hh], acc[n8][2 * hh + 1]);
       }
     }
+    cp_async_wait<1>();  // the mask rows have landed (the next gradient rows may not)
     __syncthreads();
-    // masked rows out: 16-byte chunks, the mask read beside them
+    // masked rows out: 16-byte chunks
     {
-      const int b = t / kD2Tpi, iy0 = kD2Rows * (t - b * kD2Tpi);
-      const size_t base = ((size_t)b * kD2H + iy0) * kD2W * kD2Ci;
       for (int e = threadIdx.x; e < kD2Out / 8; e += kD2Threads) {
         const int px = e >> 2, q = e & 3, ix = px % kD2W;
         const uint4 v = *reinterpret_cast<const uint4*>(outs + px * kD2Ci + 8 * (q ^ ((ix >> 1) & 3)));
-        const uint4 m = __ldg(reinterpret_cast<const uint4*>(mask + base + 8 * (size_t)e));
+        const uint4 m = *reinterpret_cast<const uint4*>(masks + 8 * e);
         const uint32_t vv[4] = {v.x, v.y, v.z, v.w}, mm[4] = {m.x, m.y, m.z, m.w};
         uint32_t o[4];
 #pragma unroll
@@ -1088,7 +1096,6 @@ __global__ void __launch_bounds__(kD2Threads, 2) dgrad2_kernel(const bf16* __res
         *reinterpret_cast<uint4*>(dx + base + 8 * (size_t)e) = make_uint4(o[0], o[1], o[2], o[3]);
       }
     }
-    __syncthreads();  // the gradient buffer and the staging are refilled next
   }
   cp_async_wait<0>();
 }
