@@ -51,8 +51,9 @@ TRAFFIC_BYTES = {"track_tile": 6610432}
 MAP_SURFELS, MAP_VIEWS = 1_000_000, 8
 UNEVEN_SURFELS, UNEVEN_VIEWS = 2_000_000, 32
 MAP_W_D, MAP_W_N = 0.5, 0.02
-# learned proposal: training pairs, AdamW steps at batch 256, held-out frames
-PROP_PAIRS, PROP_STEPS, PROP_EVAL_FRAMES = 100_000, 6000, 256
+# learned proposal: training pairs, AdamW steps at batch 256 (about 12 s of training), held-out
+# frames
+PROP_PAIRS, PROP_STEPS, PROP_EVAL_FRAMES = 100_000, 9000, 256
 # the network refines its own proposal once (two passes of proposal + acceptance test)
 PROP_PASSES = 2
 PROP_TRACK_FRAMES = 32    # tracking-workload frames for the proposal at tracking scale
@@ -489,8 +490,9 @@ def _perturbed_map(s, seed):
 
 def measure_batch(name, s_true, cams, poses, actives, K, W_, flush, seed):
     """One batched mapping step over all views: project, bin_sort, forward
-    (one persistent launch), the mapping loss per view (colour L1 + 0.5 depth
-    L1 + 0.02 normal consistency) and backward (one persistent launch + the
+    (one persistent launch), the mapping loss of every view in one launch
+    (colour L1 + 0.5 depth L1 + 0.02 normal consistency, each view's mean over
+    its pixels) and backward (one persistent launch + the
     per-surfel reductions), gradients to every surfel parameter.  Tile shapes
     come from the autotuner per resolution class.  Timed as direct calls
     (per phase) and as one CUDA graph replay per step."""
@@ -514,13 +516,14 @@ def measure_batch(name, s_true, cams, poses, actives, K, W_, flush, seed):
     del ds_true
     kv = br.fit(ds)
     loss = torch.zeros(len(cams), device="cuda")
-    lws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    lviews = gs2d.loss_views([(b["ccam"], b["rgb"], b["depth"], b["normal"], b["opacity"],
+                               obs[v][0], obs[v][1], b["d_rgb"], b["d_depth"], b["d_normal"],
+                               b["d_opacity"]) for v, b in enumerate(br.keep)])
+    lws = torch.empty(gs2d.gs2d_mapping_loss_batch_workspace(lviews), dtype=torch.uint8,
+                      device="cuda")
 
     def losses():
-        for v, b in enumerate(br.keep):
-            gs2d.gs2d_mapping_loss(b["rgb"], b["depth"], b["normal"], b["opacity"], obs[v][0],
-                                   obs[v][1], b["ccam"], MAP_W_D, MAP_W_N, b["d_rgb"],
-                                   b["d_depth"], b["d_normal"], b["d_opacity"], loss[v:v + 1], lws)
+        gs2d.gs2d_mapping_loss_batch(lviews, MAP_W_D, MAP_W_N, loss, lws)
 
     def step():
         br.forward(ds, check_status=False)

@@ -365,6 +365,34 @@ int gs2d_mapping_loss(const float* rgb, const float* depth, const float* normal,
                       float* g_normal, float* g_opacity, float* loss_out, void* workspace,
                       size_t ws_bytes, size_t* ws_needed, gs2d_stream stream);
 
+/* gs2d_mapping_loss of several views in one launch (the mapping window of
+ * Sec. III-E renders every keyframe; each view's loss is its own mean over
+ * its pixels).  View v's images and gradients are device buffers laid out as
+ * for gs2d_mapping_loss at its own resolution; every pointer non-NULL.  The
+ * gradients are bit-identical to gs2d_mapping_loss on the same view; the
+ * loss (loss_out: device [n_views]) equals it up to the order of the FP32
+ * sum (per-warp partials of each 32 x 8 tile, added in a fixed order).
+ * 1 <= n_views <= GS2D_MAX_VIEWS; workspace
+ * gs2d_mapping_loss_batch_workspace(views, n_views) bytes (0 for invalid
+ * views).  GS2D_ERR_INVALID_ARG / GS2D_ERR_WORKSPACE before any launch. */
+typedef struct {
+  gs2d_camera cam;
+  const float* rgb;      /* rendered H x W x 3, H x W, H x W x 3, H x W */
+  const float* depth;
+  const float* normal;
+  const float* opacity;
+  const float* obs_rgb;  /* observed H x W x 3, H x W                    */
+  const float* obs_depth;
+  float* g_rgb;          /* gradient outputs, shaped as the rendered     */
+  float* g_depth;
+  float* g_normal;
+  float* g_opacity;
+} gs2d_loss_view;
+size_t gs2d_mapping_loss_batch_workspace(const gs2d_loss_view* views, int n_views);
+int gs2d_mapping_loss_batch(const gs2d_loss_view* views, int n_views, float w_d, float w_n,
+                            float* loss_out, void* workspace, size_t ws_bytes, size_t* ws_needed,
+                            gs2d_stream stream);
+
 /* The full mapping loss of Sec. III-E, L_m = 1/|Omega| sum_p (L_c + w_d L_D
  * + w_n L_n) with L_c = (1 - w_ssim) |I_r - I|_1 + w_ssim (1 - SSIM(p)),
  * SSIM(p) the mean over the three channels of the SSIM of Wang et al. 2004

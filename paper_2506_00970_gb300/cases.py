@@ -83,14 +83,15 @@ def _batch(s, cams, poses, actives, reps, px=1):
     br.forward(ds)
     obs = [(b["rgb"].clone(), b["depth"] / b["opacity"].clamp_min(1e-6) + 0.01) for b in br.keep]
     loss = torch.zeros(len(cams), device="cuda")
-    lws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    lviews = gs2d.loss_views([(b["ccam"], b["rgb"], b["depth"], b["normal"], b["opacity"],
+                               obs[v][0], obs[v][1], b["d_rgb"], b["d_depth"], b["d_normal"],
+                               b["d_opacity"]) for v, b in enumerate(br.keep)])
+    lws = torch.empty(gs2d.gs2d_mapping_loss_batch_workspace(lviews), dtype=torch.uint8,
+                      device="cuda")
 
     def run():
         br.forward(ds, check_status=False)
-        for v, b in enumerate(br.keep):
-            gs2d.gs2d_mapping_loss(b["rgb"], b["depth"], b["normal"], b["opacity"], obs[v][0],
-                                   obs[v][1], b["ccam"], 0.5, 0.02, b["d_rgb"], b["d_depth"],
-                                   b["d_normal"], b["d_opacity"], loss[v:v + 1], lws)
+        gs2d.gs2d_mapping_loss_batch(lviews, 0.5, 0.02, loss, lws)
         br.backward(ds)
 
     return _timed(run, reps)

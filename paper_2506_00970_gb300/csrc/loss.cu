@@ -127,6 +127,102 @@ __device__ bool ln_eval(const MapSmem& sm, const float* __restrict__ normal,
   return true;
 }
 
+// One 32 x 8 tile of the mapping loss at (x0, y0): gradients written for
+// its pixels, this thread's pixel's loss terms added to acc (unscaled).
+__device__ __forceinline__ void mapping_loss_tile(
+    MapSmem& sm, int x0, int y0, const float* __restrict__ rgb, const float* __restrict__ depth,
+    const float* __restrict__ normal, const float* __restrict__ opac,
+    const float* __restrict__ obs_rgb, const float* __restrict__ obs_depth,
+    const gs2d_camera& cam, float ifx, float ify, float inv, float w_l1, float w_d, float w_n,
+    float* __restrict__ g_rgb, float* __restrict__ g_depth, float* __restrict__ g_normal,
+    float* __restrict__ g_opac, float& acc) {
+  const int W = cam.width, H = cam.height;
+  __syncthreads();
+  // phase 0: D/O and O on the tile and two rings
+  for (int e = threadIdx.x; e < kMapSW * kMapSH; e += blockDim.x) {
+    const int sy = e / kMapSW, sx = e % kMapSW;
+    const int px = x0 + sx - 2, py = y0 + sy - 2;
+    float d = 0.f, o = 0.f;
+    if (px >= 0 && py >= 0 && px < W && py < H) {
+      const int i = py * W + px;
+      o = opac[i];
+      d = depth[i] / fmaxf(o, 1e-6f);
+    }
+    sm.dh[sy][sx] = d;
+    sm.op[sy][sx] = o;
+  }
+  __syncthreads();
+  // phase 1: the normal term on the tile and its ring
+  for (int e = threadIdx.x; e < kMapRW * kMapRH; e += blockDim.x) {
+    const int ry = e / kMapRW, rx = e % kMapRW;
+    const int px = x0 + rx - 1, py = y0 + ry - 1;
+    const bool tile_px = rx >= 1 && rx <= kMapTW && ry >= 1 && ry <= kMapTH;
+    const bool ring = !tile_px && !((rx == 0 || rx == kMapRW - 1) && (ry == 0 || ry == kMapRH - 1));
+    float Ln = 0.f;
+    F3 g4[4], gNr = f3(0.f, 0.f, 0.f);
+    bool ok = false;
+    if ((tile_px || ring) && px >= 0 && py >= 0 && px < W && py < H)
+      ok = ln_eval(sm, normal, cam, ifx, ify, px, py, rx + 1, ry + 1, Ln, g4, gNr);
+    sm.ok[ry][rx] = ok;
+    if (ok)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        sm.g[ry][rx][3 * k] = g4[k].x;
+        sm.g[ry][rx][3 * k + 1] = g4[k].y;
+        sm.g[ry][rx][3 * k + 2] = g4[k].z;
+      }
+    if (tile_px) {
+      sm.ln[ry - 1][rx - 1] = ok ? Ln : 0.f;
+      sm.gn[ry - 1][rx - 1][0] = ok ? gNr.x : 0.f;
+      sm.gn[ry - 1][rx - 1][1] = ok ? gNr.y : 0.f;
+      sm.gn[ry - 1][rx - 1][2] = ok ? gNr.z : 0.f;
+    }
+  }
+  __syncthreads();
+  // phase 2: one pixel per thread
+  const int lx = threadIdx.x % kMapTW, ly = threadIdx.x / kMapTW;
+  const int px = x0 + lx, py = y0 + ly;
+  if (px < W && py < H) {
+    const int i = py * W + px;
+    const float O = sm.op[ly + 2][lx + 2];
+    const float Oc = fmaxf(O, 1e-6f);
+    const float D = depth[i];
+    const float Dh = sm.dh[ly + 2][lx + 2];
+    const float d0 = rgb[3 * i] - obs_rgb[3 * i];
+    const float d1 = rgb[3 * i + 1] - obs_rgb[3 * i + 1];
+    const float d2 = rgb[3 * i + 2] - obs_rgb[3 * i + 2];
+    const float dd = Dh - obs_depth[i];
+    acc += w_l1 * (fabsf(d0) + fabsf(d1) + fabsf(d2)) + w_d * fabsf(dd);
+    const float sl = w_l1 * inv;
+    g_rgb[3 * i] = sgnf(d0) * sl;
+    g_rgb[3 * i + 1] = sgnf(d1) * sl;
+    g_rgb[3 * i + 2] = sgnf(d2) * sl;
+    float gDh = w_d * sgnf(dd) * inv;
+    // own normal term
+    const int ry = ly + 1, rx = lx + 1;
+    if (sm.ok[ry][rx]) acc += w_n * sm.ln[ly][lx];
+    const float sn = w_n * inv;
+    g_normal[3 * i] = sn * sm.gn[ly][lx][0];
+    g_normal[3 * i + 1] = sn * sm.gn[ly][lx][1];
+    g_normal[3 * i + 2] = sn * sm.gn[ly][lx][2];
+    // stencils of the four neighbours that read X(q): p = q-ex uses X(p+ex)
+    // (slot 0), p = q+ex uses X(p-ex) (1), p = q-ey uses X(p+ey) (2),
+    // p = q+ey uses X(p-ey) (3)
+    const F3 rq = ray_of(cam, ifx, ify, px, py);
+    const int nb[4][3] = {{rx - 1, ry, 0}, {rx + 1, ry, 1}, {rx, ry - 1, 2}, {rx, ry + 1, 3}};
+    F3 gX = f3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int qx = nb[k][0], qy = nb[k][1], sl2 = nb[k][2];
+      if (sm.ok[qy][qx])
+        gX = gX + f3(sm.g[qy][qx][3 * sl2], sm.g[qy][qx][3 * sl2 + 1], sm.g[qy][qx][3 * sl2 + 2]);
+    }
+    gDh += w_n * inv * dot3(gX, rq);
+    g_depth[i] = gDh / Oc;
+    g_opac[i] = O > 1e-6f ? -gDh * D / (O * O) : 0.f;
+  }
+}
+
 __global__ void __launch_bounds__(kLossThreads) mapping_loss_kernel(
     const float* __restrict__ rgb, const float* __restrict__ depth, const float* __restrict__ normal,
     const float* __restrict__ opac, const float* __restrict__ obs_rgb,
@@ -140,95 +236,70 @@ __global__ void __launch_bounds__(kLossThreads) mapping_loss_kernel(
   const int tiles_x = (W + kMapTW - 1) / kMapTW, tiles_y = (H + kMapTH - 1) / kMapTH;
   const float ifx = 1.f / cam.fx, ify = 1.f / cam.fy;
   float acc = 0.f;
-  for (int tile = blockIdx.x; tile < tiles_x * tiles_y; tile += gridDim.x) {
-    const int x0 = (tile % tiles_x) * kMapTW, y0 = (tile / tiles_x) * kMapTH;
-    __syncthreads();
-    // phase 0: D/O and O on the tile and two rings
-    for (int e = threadIdx.x; e < kMapSW * kMapSH; e += blockDim.x) {
-      const int sy = e / kMapSW, sx = e % kMapSW;
-      const int px = x0 + sx - 2, py = y0 + sy - 2;
-      float d = 0.f, o = 0.f;
-      if (px >= 0 && py >= 0 && px < W && py < H) {
-        const int i = py * W + px;
-        o = opac[i];
-        d = depth[i] / fmaxf(o, 1e-6f);
-      }
-      sm.dh[sy][sx] = d;
-      sm.op[sy][sx] = o;
-    }
-    __syncthreads();
-    // phase 1: the normal term on the tile and its ring
-    for (int e = threadIdx.x; e < kMapRW * kMapRH; e += blockDim.x) {
-      const int ry = e / kMapRW, rx = e % kMapRW;
-      const int px = x0 + rx - 1, py = y0 + ry - 1;
-      const bool tile_px = rx >= 1 && rx <= kMapTW && ry >= 1 && ry <= kMapTH;
-      const bool ring = !tile_px && !((rx == 0 || rx == kMapRW - 1) && (ry == 0 || ry == kMapRH - 1));
-      float Ln = 0.f;
-      F3 g4[4], gNr = f3(0.f, 0.f, 0.f);
-      bool ok = false;
-      if ((tile_px || ring) && px >= 0 && py >= 0 && px < W && py < H)
-        ok = ln_eval(sm, normal, cam, ifx, ify, px, py, rx + 1, ry + 1, Ln, g4, gNr);
-      sm.ok[ry][rx] = ok;
-      if (ok)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          sm.g[ry][rx][3 * k] = g4[k].x;
-          sm.g[ry][rx][3 * k + 1] = g4[k].y;
-          sm.g[ry][rx][3 * k + 2] = g4[k].z;
-        }
-      if (tile_px) {
-        sm.ln[ry - 1][rx - 1] = ok ? Ln : 0.f;
-        sm.gn[ry - 1][rx - 1][0] = ok ? gNr.x : 0.f;
-        sm.gn[ry - 1][rx - 1][1] = ok ? gNr.y : 0.f;
-        sm.gn[ry - 1][rx - 1][2] = ok ? gNr.z : 0.f;
-      }
-    }
-    __syncthreads();
-    // phase 2: one pixel per thread
-    const int lx = threadIdx.x % kMapTW, ly = threadIdx.x / kMapTW;
-    const int px = x0 + lx, py = y0 + ly;
-    if (px < W && py < H) {
-      const int i = py * W + px;
-      const float O = sm.op[ly + 2][lx + 2];
-      const float Oc = fmaxf(O, 1e-6f);
-      const float D = depth[i];
-      const float Dh = sm.dh[ly + 2][lx + 2];
-      const float d0 = rgb[3 * i] - obs_rgb[3 * i];
-      const float d1 = rgb[3 * i + 1] - obs_rgb[3 * i + 1];
-      const float d2 = rgb[3 * i + 2] - obs_rgb[3 * i + 2];
-      const float dd = Dh - obs_depth[i];
-      acc += w_l1 * (fabsf(d0) + fabsf(d1) + fabsf(d2)) + w_d * fabsf(dd);
-      const float sl = w_l1 * inv;
-      g_rgb[3 * i] = sgnf(d0) * sl;
-      g_rgb[3 * i + 1] = sgnf(d1) * sl;
-      g_rgb[3 * i + 2] = sgnf(d2) * sl;
-      float gDh = w_d * sgnf(dd) * inv;
-      // own normal term
-      const int ry = ly + 1, rx = lx + 1;
-      if (sm.ok[ry][rx]) acc += w_n * sm.ln[ly][lx];
-      const float sn = w_n * inv;
-      g_normal[3 * i] = sn * sm.gn[ly][lx][0];
-      g_normal[3 * i + 1] = sn * sm.gn[ly][lx][1];
-      g_normal[3 * i + 2] = sn * sm.gn[ly][lx][2];
-      // stencils of the four neighbours that read X(q): p = q-ex uses X(p+ex)
-      // (slot 0), p = q+ex uses X(p-ex) (1), p = q-ey uses X(p+ey) (2),
-      // p = q+ey uses X(p-ey) (3)
-      const F3 rq = ray_of(cam, ifx, ify, px, py);
-      const int nb[4][3] = {{rx - 1, ry, 0}, {rx + 1, ry, 1}, {rx, ry - 1, 2}, {rx, ry + 1, 3}};
-      F3 gX = f3(0.f, 0.f, 0.f);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int qx = nb[k][0], qy = nb[k][1], sl = nb[k][2];
-        if (sm.ok[qy][qx])
-          gX = gX + f3(sm.g[qy][qx][3 * sl], sm.g[qy][qx][3 * sl + 1], sm.g[qy][qx][3 * sl + 2]);
-      }
-      gDh += w_n * inv * dot3(gX, rq);
-      g_depth[i] = gDh / Oc;
-      g_opac[i] = O > 1e-6f ? -gDh * D / (O * O) : 0.f;
-    }
-  }
+  for (int tile = blockIdx.x; tile < tiles_x * tiles_y; tile += gridDim.x)
+    mapping_loss_tile(sm, (tile % tiles_x) * kMapTW, (tile / tiles_x) * kMapTH, rgb, depth, normal,
+                      opac, obs_rgb, obs_depth, cam, ifx, ify, inv, w_l1, w_d, w_n, g_rgb,
+                      g_depth, g_normal, g_opac, acc);
   const float t = block_sum256(acc, s);
   if (threadIdx.x == 0) part[blockIdx.x] = t * inv;
+}
+
+// The mapping loss of many views in one launch: work items are the views'
+// 32 x 8 tiles in view order; each tile's loss terms are summed per warp
+// into part[item * 8 + warp] (no block barrier beyond the tile's own), and
+// mapping_loss_batch_sum_kernel adds each view's items in order.
+struct LossViewDev {
+  gs2d_camera cam;
+  const float *rgb, *depth, *normal, *opac, *obs_rgb, *obs_depth;
+  float *g_rgb, *g_depth, *g_normal, *g_opac;
+  int tiles_x, item0, n_items;
+};
+struct LossTable {
+  int n_views, n_items;
+  LossViewDev v[GS2D_MAX_VIEWS];
+};
+constexpr int kLossWarps = kLossThreads / 32;
+
+__global__ void __launch_bounds__(kLossThreads) mapping_loss_batch_kernel(const LossTable tab,
+                                                                          float w_d, float w_n,
+                                                                          float* __restrict__ part) {
+  __shared__ MapSmem sm;
+  for (int item = blockIdx.x; item < tab.n_items; item += gridDim.x) {
+    int v = 0;
+    while (v + 1 < tab.n_views && item >= tab.v[v + 1].item0) ++v;
+    const LossViewDev& V = tab.v[v];
+    const int tile = item - V.item0;
+    const float inv = 1.f / (float)(V.cam.width * V.cam.height);
+    float acc = 0.f;
+    mapping_loss_tile(sm, (tile % V.tiles_x) * kMapTW, (tile / V.tiles_x) * kMapTH, V.rgb, V.depth,
+                      V.normal, V.opac, V.obs_rgb, V.obs_depth, V.cam, 1.f / V.cam.fx,
+                      1.f / V.cam.fy, inv, 1.f, w_d, w_n, V.g_rgb, V.g_depth, V.g_normal, V.g_opac,
+                      acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) part[(size_t)item * kLossWarps + (threadIdx.x >> 5)] = acc;
+  }
+}
+
+// loss_out[v] = inv_v x the sum of view v's per-warp partials: thread t adds
+// entries t, t + 256, ... in order, then a fixed tree over the threads.
+__global__ void __launch_bounds__(256) mapping_loss_batch_sum_kernel(const LossTable tab,
+                                                                     const float* __restrict__ part,
+                                                                     float* __restrict__ loss_out) {
+  __shared__ float s[256];
+  const LossViewDev& V = tab.v[blockIdx.x];
+  const float* p = part + (size_t)V.item0 * kLossWarps;
+  const int n = V.n_items * kLossWarps;
+  float a = 0.f;
+#pragma unroll 8
+  for (int e = threadIdx.x; e < n; e += 256) a += p[e];
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss_out[blockIdx.x] = s[0] / (float)(V.cam.width * V.cam.height);
 }
 
 size_t loss_ws_bytes(const gs2d_camera* cam) {
@@ -282,6 +353,75 @@ int gs2d_mapping_loss(const float* rgb, const float* depth, const float* normal,
   return gs2d_mapping_loss_ssim(rgb, depth, normal, opacity, obs_rgb, obs_depth, cam, 0.f, w_d,
                                 w_n, g_rgb, g_depth, g_normal, g_opacity, loss_out, workspace,
                                 ws_bytes, ws_needed, stream);
+}
+
+size_t gs2d_mapping_loss_batch_workspace(const gs2d_loss_view* views, int n_views) {
+  if (!views || n_views <= 0 || n_views > GS2D_MAX_VIEWS) return 0;
+  size_t items = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const gs2d_camera& c = views[v].cam;
+    if (c.width <= 0 || c.height <= 0) return 0;
+    items += (size_t)((c.width + kMapTW - 1) / kMapTW) * ((c.height + kMapTH - 1) / kMapTH);
+  }
+  return align_up(items * kLossWarps * sizeof(float), 256);
+}
+
+int gs2d_mapping_loss_batch(const gs2d_loss_view* views, int n_views, float w_d, float w_n,
+                            float* loss_out, void* workspace, size_t ws_bytes, size_t* ws_needed,
+                            gs2d_stream stream) {
+  if (!views || n_views <= 0 || n_views > GS2D_MAX_VIEWS || !loss_out) return GS2D_ERR_INVALID_ARG;
+  LossTable tab;
+  tab.n_views = n_views;
+  long long items = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const gs2d_loss_view& x = views[v];
+    if (!x.rgb || !x.depth || !x.normal || !x.opacity || !x.obs_rgb || !x.obs_depth || !x.g_rgb ||
+        !x.g_depth || !x.g_normal || !x.g_opacity)
+      return GS2D_ERR_INVALID_ARG;
+    if (x.cam.width <= 0 || x.cam.height <= 0) return GS2D_ERR_INVALID_ARG;
+    LossViewDev& d = tab.v[v];
+    d.cam = x.cam;
+    d.rgb = x.rgb;
+    d.depth = x.depth;
+    d.normal = x.normal;
+    d.opac = x.opacity;
+    d.obs_rgb = x.obs_rgb;
+    d.obs_depth = x.obs_depth;
+    d.g_rgb = x.g_rgb;
+    d.g_depth = x.g_depth;
+    d.g_normal = x.g_normal;
+    d.g_opac = x.g_opacity;
+    d.tiles_x = (x.cam.width + kMapTW - 1) / kMapTW;
+    d.item0 = (int)items;
+    d.n_items = d.tiles_x * ((x.cam.height + kMapTH - 1) / kMapTH);
+    items += d.n_items;
+    if (items > 0x7FFFFFFF / kLossWarps) return GS2D_ERR_INVALID_ARG;
+  }
+  tab.n_items = (int)items;
+  const size_t need = gs2d_mapping_loss_batch_workspace(views, n_views);
+  if (ws_needed) *ws_needed = need;
+  if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  float* part = static_cast<float*>(workspace);
+  // a resident grid (the partials are per item, so the result does not
+  // depend on it)
+  static int slots[64] = {};
+  int dev = 0;
+  GS2D_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return GS2D_ERR_CUDA;
+  if (!slots[dev]) {
+    int per_sm = 0, sms = 0;
+    GS2D_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mapping_loss_batch_kernel,
+                                                                kLossThreads, 0));
+    GS2D_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    slots[dev] = max(1, per_sm) * max(1, sms);
+  }
+  mapping_loss_batch_kernel<<<min(slots[dev], tab.n_items), kLossThreads, 0, st>>>(tab, w_d, w_n,
+                                                                                  part);
+  GS2D_LAUNCH_CHECK();
+  mapping_loss_batch_sum_kernel<<<n_views, 256, 0, st>>>(tab, part, loss_out);
+  GS2D_LAUNCH_CHECK();
+  return GS2D_OK;
 }
 
 size_t gs2d_mapping_loss_ssim_workspace(const gs2d_camera* cam) {

@@ -74,6 +74,14 @@ class View(ctypes.Structure):
                 ("d_opacity", ctypes.c_void_p), ("d_pose6", ctypes.c_void_p)]
 
 
+class LossView(ctypes.Structure):
+    _fields_ = [("cam", Camera), ("rgb", ctypes.c_void_p), ("depth", ctypes.c_void_p),
+                ("normal", ctypes.c_void_p), ("opacity", ctypes.c_void_p),
+                ("obs_rgb", ctypes.c_void_p), ("obs_depth", ctypes.c_void_p),
+                ("g_rgb", ctypes.c_void_p), ("g_depth", ctypes.c_void_p),
+                ("g_normal", ctypes.c_void_p), ("g_opacity", ctypes.c_void_p)]
+
+
 class MapState(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_void_p), ("t_c", ctypes.c_void_p), ("d_c", ctypes.c_void_p),
                 ("t_l", ctypes.c_void_p)]
@@ -116,7 +124,8 @@ EXPORTS = ["gs2d_default_config", "gs2d_default_track_params", "gs2d_status_stri
            "gs2d_mapping_loss_ssim_workspace", "gs2d_mapping_loss_ssim", "gs2d_ssim_workspace",
            "gs2d_ssim_loss", "gs2d_voxel_clear", "gs2d_voxel_insert", "gs2d_voxel_query",
            "gs2d_expand_workspace", "gs2d_expand", "gs2d_map_expand_values",
-           "gs2d_net_downsample_rgbd", "gs2d_net_prepare", "gs2d_net_forward_prepared"]
+           "gs2d_net_downsample_rgbd", "gs2d_net_prepare", "gs2d_net_forward_prepared",
+           "gs2d_mapping_loss_batch_workspace", "gs2d_mapping_loss_batch"]
 
 NET_LAYERS = 8
 NET_IN = (120, 160, 8)
@@ -202,6 +211,9 @@ def lib():
         L.gs2d_map_correct_workspace.argtypes = [ip]
         L.gs2d_map_correct.argtypes = [vp, vp, vp, ip, vp, vp, ip, vp, sz, vp, vp, vp]
         L.gs2d_map_prune.argtypes = [vp, vp, ip, ip, fl, vp, vp]
+        L.gs2d_mapping_loss_batch_workspace.restype = sz
+        L.gs2d_mapping_loss_batch_workspace.argtypes = [vp, ip]
+        L.gs2d_mapping_loss_batch.argtypes = [vp, ip, fl, fl, vp, vp, sz, vp, vp]
         L.gs2d_mapping_loss_ssim_workspace.restype = sz
         L.gs2d_mapping_loss_ssim_workspace.argtypes = [vp]
         L.gs2d_mapping_loss_ssim.argtypes = [vp] * 7 + [fl, fl, fl] + [vp] * 6 + [sz, vp, vp]
@@ -482,6 +494,30 @@ def gs2d_mapping_loss(rgb, depth, normal, opacity, obs_rgb, obs_depth, cam: Came
                                   _ptr(loss_out), _ptr(workspace),
                                   workspace.numel() * workspace.element_size(), None,
                                   _stream(stream)), "gs2d_mapping_loss")
+
+
+def loss_views(views):
+    """ctypes array of LossView from (cam, rgb, depth, normal, opacity,
+    obs_rgb, obs_depth, g_rgb, g_depth, g_normal, g_opacity) tuples."""
+    arr = (LossView * len(views))()
+    for k, v in enumerate(views):
+        arr[k] = LossView(v[0], *[t.data_ptr() for t in v[1:]])
+    return arr
+
+
+def gs2d_mapping_loss_batch_workspace(views) -> int:
+    arr = views if isinstance(views, ctypes.Array) else loss_views(views)
+    return int(lib().gs2d_mapping_loss_batch_workspace(arr, len(arr)))
+
+
+def gs2d_mapping_loss_batch(views, w_d, w_n, loss_out, workspace, stream=None):
+    """gs2d_mapping_loss over every view in one launch; views as for
+    loss_views (or its result), loss_out device [n_views]."""
+    arr = views if isinstance(views, ctypes.Array) else loss_views(views)
+    check(lib().gs2d_mapping_loss_batch(arr, len(arr), float(w_d), float(w_n), _ptr(loss_out),
+                                        _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(), None,
+                                        _stream(stream)), "gs2d_mapping_loss_batch")
 
 
 def gs2d_mapping_loss_ssim_workspace(cam: Camera) -> int:

@@ -81,6 +81,33 @@ def test_invalid_arguments_rejected_without_launch(built_lib):
                              8, 8, 8, 8, 8, 8, None) == 1
 
 
+def test_mapping_loss_batch_rejects_bad_views_without_launch(built_lib):
+    """gs2d_mapping_loss_batch validates the view count, every pointer and
+    every camera on the host; the workspace size is 0 for invalid views and
+    grows with the views' 32 x 8 tiles."""
+    from paper_2506_00970_gb300 import gs2d
+    L = gs2d.lib()
+    cam = gs2d.Camera(100.0, 100.0, 50.0, 30.0, 100, 60, 0.05)
+    views = (gs2d.LossView * 2)()
+    for k in range(2):
+        views[k] = gs2d.LossView(cam, *([8] * 10))
+    # 4 x 8 tiles per view, 8 warp partials of 4 bytes each, 256-byte aligned
+    assert L.gs2d_mapping_loss_batch_workspace(views, 2) == 2 * 4 * 8 * 8 * 4
+    assert L.gs2d_mapping_loss_batch_workspace(views, 0) == 0
+    assert L.gs2d_mapping_loss_batch_workspace(views, 33) == 0
+    need = ctypes.c_size_t(0)
+    assert L.gs2d_mapping_loss_batch(views, 2, 0.5, 0.02, 8, None, 0, ctypes.byref(need), None) == 2
+    assert need.value == 2 * 4 * 8 * 8 * 4
+    assert L.gs2d_mapping_loss_batch(views, 0, 0.5, 0.02, 8, 8, 1 << 20, None, None) == 1
+    assert L.gs2d_mapping_loss_batch(views, 2, 0.5, 0.02, None, 8, 1 << 20, None, None) == 1
+    views[1].g_normal = None
+    assert L.gs2d_mapping_loss_batch(views, 2, 0.5, 0.02, 8, 8, 1 << 20, None, None) == 1
+    views[1].g_normal = 8
+    views[0].cam.width = 0
+    assert L.gs2d_mapping_loss_batch(views, 2, 0.5, 0.02, 8, 8, 1 << 20, None, None) == 1
+    assert L.gs2d_mapping_loss_batch_workspace(views, 2) == 0
+
+
 def test_net_accept_keep_rejects_missing_buffers_without_launch(built_lib):
     """gs2d_net_accept_keep checks every pointer and size on the host: a
     missing image buffer, an empty image or an empty batch is rejected

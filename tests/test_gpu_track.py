@@ -87,6 +87,50 @@ def test_mapping_loss_matches_oracle(torch_cuda, orc):
         assert err.max() < 5e-2 * scale, key
 
 
+def test_mapping_loss_batch_matches_per_view(torch_cuda):
+    """gs2d_mapping_loss_batch over views of three sizes (several tiles with
+    ragged edges, one view smaller than a tile row) gives gs2d_mapping_loss's
+    gradients bit for bit and its losses up to the FP32 summation order;
+    the per-view call is held to the oracle in the test above."""
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d
+    rng = np.random.default_rng(5)
+    f = dict(dtype=torch.float32, device="cuda")
+    views, singles = [], []
+    for (w, h) in ((160, 120), (70, 45), (33, 9)):
+        cam = gs2d.Camera(0.8 * w, 0.8 * w, w / 2, h / 2, w, h, 0.05)
+        op = np.where(rng.random((h, w)) < 0.8, rng.uniform(0.6, 1.0, (h, w)),
+                      rng.uniform(0.0, 1.0, (h, w)))
+        nrm = rng.normal(size=(h, w, 3))
+        nrm /= np.linalg.norm(nrm, axis=2, keepdims=True)
+        # a smooth depth surface plus noise, so the normal term is active
+        yy, xx = np.mgrid[0:h, 0:w]
+        dep = (2.0 + 0.3 * np.sin(xx / 7.0) + 0.2 * np.cos(yy / 5.0)
+               + 0.01 * rng.normal(size=(h, w))) * op
+        ins = [torch.tensor(a, **f) for a in (rng.random((h, w, 3)), dep, nrm, op,
+                                               rng.random((h, w, 3)),
+                                               rng.uniform(1.0, 3.0, (h, w)))]
+        outs = [torch.full((h, w, 3), 7.0, **f), torch.full((h, w), 7.0, **f),
+                torch.full((h, w, 3), 7.0, **f), torch.full((h, w), 7.0, **f)]
+        ref = [torch.empty_like(o) for o in outs]
+        views.append((cam, *ins, *outs))
+        singles.append((cam, ins, ref))
+    ws1 = torch.empty(1 << 16, dtype=torch.uint8, device="cuda")
+    ref_loss = torch.empty(len(singles), **f)
+    for k, (cam, ins, ref) in enumerate(singles):
+        gs2d.gs2d_mapping_loss(*ins, cam, 0.5, 0.02, *ref, ref_loss[k:k + 1], ws1)
+    arr = gs2d.loss_views(views)
+    ws = torch.empty(gs2d.gs2d_mapping_loss_batch_workspace(arr), dtype=torch.uint8, device="cuda")
+    loss = torch.full((len(views),), -1.0, **f)
+    gs2d.gs2d_mapping_loss_batch(arr, 0.5, 0.02, loss, ws)
+    torch.cuda.synchronize()
+    for k, (cam, ins, ref) in enumerate(singles):
+        for got, exp in zip(views[k][7:], ref):
+            assert torch.equal(got, exp), (k, cam.width)
+        assert float(loss[k]) == pytest.approx(float(ref_loss[k]), rel=1e-5)
+        assert float(loss[k]) > 0.0
+
+
 def _track_setup(orc, n=30_000, seed=0):
     s = scenes.room_scene(seed, n, scale_cm=(2.0, 4.0))
     cam = scenes.Camera(262.5, 262.5, 160.0, 120.0, 320, 240)
