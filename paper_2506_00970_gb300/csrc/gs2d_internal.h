@@ -51,6 +51,11 @@ int project_launch(const gs2d_surfels* s, const gs2d_camera* cam, const float* p
 // the bins sorts each tile's segment itself (sort_seg_args).
 constexpr unsigned kSortPreZeroed = 1u, kSortLongInBlock = 2u, kSortPreScanned = 4u,
                    kSortInTileKernel = 8u;
+// Binning of several views, one launch per stage (sort.cu): the workspace
+// is a 256-byte header followed by each view's gs2d_bin_sort workspace.
+size_t bin_sort_batch_bytes(const gs2d_view* views, int n_views, int n);
+int bin_sort_batch_launch(const gs2d_view* views, int n_views, int n, void* workspace,
+                          size_t ws_bytes, size_t* ws_needed, cudaStream_t st);
 int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
                     const gs2d_camera* cam, const gs2d_config* cfg, void* workspace,
                     size_t ws_bytes, size_t* ws_needed, const gs2d_bins* bins, bool need_emit,

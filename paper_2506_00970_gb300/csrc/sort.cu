@@ -25,6 +25,7 @@
 // (surfel i, tile t) = surfel_off[i] + the row-major position of t in i's
 // rectangle, so each surfel's pairs are contiguous in emission order (the
 // backward pass stores its per-pair partials there).
+#include <algorithm>
 #include <mutex>
 
 #include "gs2d_common.cuh"
@@ -43,6 +44,7 @@ constexpr int kSpinLimit = 1 << 22;                // default polls of a look-ba
 constexpr int kSortThreads = 256;
 constexpr int kLongThreads = 1024;                 // long segments: one 1024-thread block
 constexpr int kLongChunk = 16384;                  // keys per shared-memory chunk (128 KB)
+constexpr size_t kSortBatchHeader = 256;           // batched binning: the scan's ticket
 
 __device__ __forceinline__ unsigned long long ld_vol64(const unsigned long long* p) {
   return *reinterpret_cast<const volatile unsigned long long*>(p);
@@ -95,19 +97,19 @@ constexpr int kSmemTiles = 6144;  // 2 x 24 KB: the scatter's histogram + bases
 
 // 1a. Tile counts: every covered tile's counter is incremented, through a
 // per-block shared-memory histogram (one global atomic per block and tile).
-__global__ void __launch_bounds__(kScanThreads) count_kernel(
-    const float4* __restrict__ proj, const int32_t* __restrict__ tiles, int n, int tiles_x,
-    int n_tiles, uint32_t* __restrict__ tile_count, const int32_t* __restrict__ gate) {
-  extern __shared__ uint32_t s_hist[];
-  __shared__ WalkScratch s_walk[kScanThreads / 32];
-  if (*gate) return;
+// Block vblock of vgrid (a view's share of a batched launch, or the grid).
+__device__ __forceinline__ void count_body(const float4* __restrict__ proj,
+                                           const int32_t* __restrict__ tiles, int n, int tiles_x,
+                                           int n_tiles, uint32_t* __restrict__ tile_count,
+                                           int vblock, int vgrid, uint32_t* s_hist,
+                                           WalkScratch* s_walk) {
   const bool local = n_tiles <= kSmemTiles;
   if (local)
     for (int t = threadIdx.x; t < n_tiles; t += kScanThreads) s_hist[t] = 0u;
   __syncthreads();
-  const int stride = gridDim.x * kScanThreads;
+  const int stride = vgrid * kScanThreads;
   // block-uniform trip count: every lane takes part in each warp walk
-  for (int base = blockIdx.x * kScanThreads; base < n; base += stride) {
+  for (int base = vblock * kScanThreads; base < n; base += stride) {
     const int i = base + (int)threadIdx.x;
     const int k = i < n ? max(tiles[i], 0) : 0;
     Rect r{1, 1, 0, 0};
@@ -121,6 +123,15 @@ __global__ void __launch_bounds__(kScanThreads) count_kernel(
     if (s_hist[t]) atomicAdd(tile_count + t, s_hist[t]);
 }
 
+__global__ void __launch_bounds__(kScanThreads) count_kernel(
+    const float4* __restrict__ proj, const int32_t* __restrict__ tiles, int n, int tiles_x,
+    int n_tiles, uint32_t* __restrict__ tile_count, const int32_t* __restrict__ gate) {
+  extern __shared__ uint32_t s_hist[];
+  __shared__ WalkScratch s_walk[kScanThreads / 32];
+  if (*gate) return;
+  count_body(proj, tiles, n, tiles_x, n_tiles, tile_count, blockIdx.x, gridDim.x, s_hist, s_walk);
+}
+
 // 1b. Exclusive scan of k_i over surfel ids with decoupled look-back (64-bit
 // chunk words: flag in bits 62-63; a warp examines 32 predecessors at a
 // time; the spin is bounded by spin_limit polls and past it records
@@ -130,18 +141,21 @@ __global__ void __launch_bounds__(kScanThreads) count_kernel(
 // none) never publishes its word, so its successor's wait runs out.
 constexpr unsigned long long kF64Agg = 1ull << 62, kF64Inc = 2ull << 62,
                              kV64Mask = (1ull << 62) - 1;
-__global__ void __launch_bounds__(kScanThreads) emit_scan_kernel(
-    const int32_t* __restrict__ tiles, int n, uint32_t* __restrict__ surfel_off,
-    unsigned long long* __restrict__ chunk_status, uint32_t* __restrict__ ticket,
-    int32_t* __restrict__ gate, int spin_limit, int withheld) {
-  __shared__ uint32_t s_k[kChunk];
-  __shared__ uint32_t s_tmp[2 * kWarps + 1];
-  __shared__ int s_chunk;
-  __shared__ unsigned long long s_prefix;
-  if (*gate) return;
-  if (threadIdx.x == 0) s_chunk = (int)atomicAdd(ticket, 1u);
-  __syncthreads();
-  const int chunk = s_chunk;
+struct ScanSmem {
+  uint32_t k[kChunk];
+  uint32_t tmp[2 * kWarps + 1];
+  unsigned long long prefix;
+};
+
+// Chunk `chunk` of one view's scan; every chunk before it in that view was
+// handed to a block that started earlier (tickets in chunk order).
+__device__ __forceinline__ void emit_scan_body(const int32_t* __restrict__ tiles, int n,
+                                               uint32_t* __restrict__ surfel_off,
+                                               unsigned long long* __restrict__ chunk_status,
+                                               int chunk, int32_t* __restrict__ gate,
+                                               int spin_limit, int withheld, ScanSmem& sm) {
+  uint32_t* s_k = sm.k;
+  uint32_t* s_tmp = sm.tmp;
   const long long base = (long long)chunk * kChunk;
   if (base >= n) return;
   const int count = (int)min((long long)kChunk, (long long)n - base);
@@ -196,10 +210,10 @@ __global__ void __launch_bounds__(kScanThreads) emit_scan_kernel(
       }
       if (lane == 0 && publish) st_vol64(my, kF64Inc | ((prefix + btotal) & kV64Mask));
     }
-    if (lane == 0) s_prefix = prefix;
+    if (lane == 0) sm.prefix = prefix;
   }
   __syncthreads();
-  unsigned long long off = s_prefix + excl;
+  unsigned long long off = sm.prefix + excl;
 #pragma unroll
   for (int j = 0; j < kScanItems; ++j) {
     const int i = threadIdx.x * kScanItems + j;
@@ -208,6 +222,18 @@ __global__ void __launch_bounds__(kScanThreads) emit_scan_kernel(
       off += s_k[i];
     }
   }
+}
+
+__global__ void __launch_bounds__(kScanThreads) emit_scan_kernel(
+    const int32_t* __restrict__ tiles, int n, uint32_t* __restrict__ surfel_off,
+    unsigned long long* __restrict__ chunk_status, uint32_t* __restrict__ ticket,
+    int32_t* __restrict__ gate, int spin_limit, int withheld) {
+  __shared__ ScanSmem sm;
+  __shared__ int s_chunk;
+  if (*gate) return;
+  if (threadIdx.x == 0) s_chunk = (int)atomicAdd(ticket, 1u);
+  __syncthreads();
+  emit_scan_body(tiles, n, surfel_off, chunk_status, s_chunk, gate, spin_limit, withheld, sm);
 }
 
 // 2. Tile ranges from the tile counts (one block), K and the capacity check.
@@ -230,32 +256,26 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
 // slots per tile with a single global atomic, and hands the slots out with
 // shared-memory atomics; both passes walk the warp's pairs cooperatively
 // (warp_tile_walk).
-__global__ void __launch_bounds__(256) scatter_kernel(
+// Block vblock of a view (surfels 256 vblock .. + 255).
+__device__ __forceinline__ void scatter_body(
     const float4* __restrict__ proj, const int32_t* __restrict__ tiles, int n, int tiles_x,
     int n_tiles, const int32_t* __restrict__ ranges, uint32_t* __restrict__ cursor,
-    unsigned long long* __restrict__ seg_keys, long long capacity,
-    const int32_t* __restrict__ gate) {
-  extern __shared__ uint32_t s_cnt[];  // [n_tiles] counts, then [n_tiles] bases
-  __shared__ WalkScratch s_walk[8];
-  __shared__ unsigned long long s_key[256];
-  if (*gate) return;
+    unsigned long long* __restrict__ seg_keys, long long capacity, int vblock, uint32_t* s_cnt,
+    WalkScratch* s_walk, unsigned long long* s_key) {
   const bool local = n_tiles <= kSmemTiles;
   uint32_t* s_base = s_cnt + (local ? n_tiles : 0);
   if (local)
     for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) s_cnt[t] = 0u;
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = vblock * blockDim.x + threadIdx.x;
   const int k = i < n ? tiles[i] : 0;
   Rect r{1, 1, 0, 0};
   unsigned long long key = 0ull;
-  int rw = 1;
   if (k > 0) {
     r = load_rect(proj, (uint32_t)i);
-    rw = max(r.tx1 - r.tx0 + 1, 1);
     const uint32_t db = __float_as_uint(proj[(size_t)i * (kProjFloats / 4) + 6].z);
     key = ((unsigned long long)db << 32) | (uint32_t)i;
   }
-  (void)rw;
   s_key[threadIdx.x] = key;
   WalkScratch& ws = s_walk[threadIdx.x >> 5];
   const unsigned long long* wkey = s_key + (threadIdx.x & ~31);
@@ -279,17 +299,27 @@ __global__ void __launch_bounds__(256) scatter_kernel(
   });
 }
 
-// Segments of at most kSegSmem keys: sorted in shared memory by 256 threads (and,
-// with long_here, longer ones too).
-__global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(
-    const float4* __restrict__ proj, int n, int tiles_x, const int32_t* __restrict__ ranges,
+__global__ void __launch_bounds__(256) scatter_kernel(
+    const float4* __restrict__ proj, const int32_t* __restrict__ tiles, int n, int tiles_x,
+    int n_tiles, const int32_t* __restrict__ ranges, uint32_t* __restrict__ cursor,
+    unsigned long long* __restrict__ seg_keys, long long capacity,
+    const int32_t* __restrict__ gate) {
+  extern __shared__ uint32_t s_cnt[];  // [n_tiles] counts, then [n_tiles] bases
+  __shared__ WalkScratch s_walk[8];
+  __shared__ unsigned long long s_key[256];
+  if (*gate) return;
+  scatter_body(proj, tiles, n, tiles_x, n_tiles, ranges, cursor, seg_keys, capacity, blockIdx.x,
+               s_cnt, s_walk, s_key);
+}
+
+// Tile t's segment (sorted here when at most kSegSmem keys, or with
+// long_here any length).
+__device__ __forceinline__ void tile_sort_body(
+    int t, const float4* __restrict__ proj, int n, int tiles_x, const int32_t* __restrict__ ranges,
     unsigned long long* __restrict__ seg_keys, unsigned long long* __restrict__ seg_tmp,
     const uint32_t* __restrict__ surfel_off, uint32_t* __restrict__ vals,
     uint32_t* __restrict__ emit, unsigned long long* __restrict__ keys64, long long capacity,
-    int long_here, const int32_t* __restrict__ gate) {
-  extern __shared__ unsigned long long s_keys[];
-  if (*gate) return;
-  const int t = blockIdx.x;
+    int long_here, unsigned long long* s_keys) {
   const int start = ranges[2 * t];
   const int end = (int)min((long long)ranges[2 * t + 1], capacity);
   const int len = end - start;
@@ -308,6 +338,20 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(
   write_outputs(s_keys, len, start, t, tiles_x, n, proj, surfel_off, vals, emit, keys64);
 }
 
+// Segments of at most kSegSmem keys: sorted in shared memory by 256 threads (and,
+// with long_here, longer ones too).
+__global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(
+    const float4* __restrict__ proj, int n, int tiles_x, const int32_t* __restrict__ ranges,
+    unsigned long long* __restrict__ seg_keys, unsigned long long* __restrict__ seg_tmp,
+    const uint32_t* __restrict__ surfel_off, uint32_t* __restrict__ vals,
+    uint32_t* __restrict__ emit, unsigned long long* __restrict__ keys64, long long capacity,
+    int long_here, const int32_t* __restrict__ gate) {
+  extern __shared__ unsigned long long s_keys[];
+  if (*gate) return;
+  tile_sort_body(blockIdx.x, proj, n, tiles_x, ranges, seg_keys, seg_tmp, surfel_off, vals, emit,
+                 keys64, capacity, long_here, s_keys);
+}
+
 // Segments longer than kSegSmem, listed by the tile scan: a small persistent
 // grid takes them one per block.
 __global__ void __launch_bounds__(kLongThreads) tile_sort_long_kernel(
@@ -323,6 +367,115 @@ __global__ void __launch_bounds__(kLongThreads) tile_sort_long_kernel(
     sort_long_segment<kLongChunk>((int)long_list[i], proj, n, tiles_x, ranges, seg_keys, seg_tmp,
                                   surfel_off, vals, emit, keys64, capacity, s_keys);
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Several views in one launch per stage (gs2d_bin_sort_batch): each view keeps
+// its own workspace region, counters and status word; a stage's blocks are
+// split over the views by the offsets in the table, and the emission scan's
+// chunks take tickets from one counter in view-major order, so every chunk's
+// predecessors in its view started earlier (the look-back's condition).
+struct SortViewDev {
+  const float4* proj;
+  const int32_t* tiles;
+  int n, tiles_x, n_tiles;
+  uint32_t* zero_begin;
+  size_t zero_words;
+  uint32_t *tile_count, *cursor, *n_long, *long_list;
+  unsigned long long *estatus, *seg_keys, *seg_tmp;
+  int32_t *ranges, *n_isect;
+  uint32_t *surfel_off, *vals, *emit;
+  unsigned long long* keys64;
+  long long capacity;
+  int32_t* gate;
+  int count0, count_blocks, chunk0, scatter0, tile0;
+};
+struct SortTable {
+  int n_views, count_total, chunk_total, scatter_total, tile_total;
+  SortViewDev v[GS2D_MAX_VIEWS];
+};
+
+// The view whose share of a stage's blocks holds block b.
+__device__ __forceinline__ int sort_view_of(const SortTable& T, int b, int SortViewDev::*first) {
+  int v = 0;
+  while (v + 1 < T.n_views && b >= T.v[v + 1].*first) ++v;
+  return v;
+}
+
+__global__ void bin_init_batch_kernel(const SortTable T, uint32_t* __restrict__ batch_ticket) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *batch_ticket = 0u;
+  const SortViewDev& V = T.v[blockIdx.y];
+  if (*V.gate) return;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < V.zero_words; i += stride)
+    V.zero_begin[i] = 0u;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *V.n_isect = 0;
+}
+
+__global__ void __launch_bounds__(kScanThreads) count_batch_kernel(const SortTable T) {
+  extern __shared__ uint32_t s_hist[];
+  __shared__ WalkScratch s_walk[kScanThreads / 32];
+  const SortViewDev& V = T.v[sort_view_of(T, blockIdx.x, &SortViewDev::count0)];
+  if (*V.gate) return;
+  count_body(V.proj, V.tiles, V.n, V.tiles_x, V.n_tiles, V.tile_count, blockIdx.x - V.count0,
+             V.count_blocks, s_hist, s_walk);
+}
+
+__global__ void __launch_bounds__(kScanThreads) emit_scan_batch_kernel(
+    const SortTable T, uint32_t* __restrict__ batch_ticket, int spin_limit, int withheld) {
+  __shared__ ScanSmem sm;
+  __shared__ int s_t;
+  if (threadIdx.x == 0) s_t = (int)atomicAdd(batch_ticket, 1u);
+  __syncthreads();
+  const int t = s_t;
+  if (t >= T.chunk_total) return;
+  const SortViewDev& V = T.v[sort_view_of(T, t, &SortViewDev::chunk0)];
+  if (*V.gate) return;
+  emit_scan_body(V.tiles, V.n, V.surfel_off, V.estatus, t - V.chunk0, V.gate, spin_limit,
+                 withheld, sm);
+}
+
+__global__ void __launch_bounds__(1024) tile_scan_batch_kernel(const SortTable T) {
+  __shared__ uint32_t s_w[32];
+  __shared__ uint32_t s_carry;
+  const SortViewDev& V = T.v[blockIdx.x];
+  if (*V.gate) return;
+  tile_scan_block(V.tile_count, V.n_tiles, V.ranges, V.n_isect, V.capacity, V.long_list,
+                  V.n_long, kSegSmem, V.gate, s_w, &s_carry);
+}
+
+__global__ void __launch_bounds__(256) scatter_batch_kernel(const SortTable T) {
+  extern __shared__ uint32_t s_cnt[];
+  __shared__ WalkScratch s_walk[8];
+  __shared__ unsigned long long s_key[256];
+  const SortViewDev& V = T.v[sort_view_of(T, blockIdx.x, &SortViewDev::scatter0)];
+  if (*V.gate) return;
+  scatter_body(V.proj, V.tiles, V.n, V.tiles_x, V.n_tiles, V.ranges, V.cursor, V.seg_keys,
+               V.capacity, blockIdx.x - V.scatter0, s_cnt, s_walk, s_key);
+}
+
+__global__ void __launch_bounds__(kSortThreads) tile_sort_batch_kernel(const SortTable T) {
+  extern __shared__ unsigned long long s_keys[];
+  const SortViewDev& V = T.v[sort_view_of(T, blockIdx.x, &SortViewDev::tile0)];
+  if (*V.gate) return;
+  tile_sort_body(blockIdx.x - V.tile0, V.proj, V.n, V.tiles_x, V.ranges, V.seg_keys, V.seg_tmp,
+                 V.surfel_off, V.vals, V.emit, V.keys64, V.capacity, 0, s_keys);
+}
+
+// Every view's segments longer than kSegSmem, one per block of a small grid.
+__global__ void __launch_bounds__(kLongThreads) tile_sort_long_batch_kernel(const SortTable T) {
+  extern __shared__ unsigned long long s_keys[];
+  for (int v = 0; v < T.n_views; ++v) {
+    const SortViewDev& V = T.v[v];
+    if (*V.gate) continue;
+    const int cnt = (int)*V.n_long;
+    for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+      sort_long_segment<kLongChunk>((int)V.long_list[i], V.proj, V.n, V.tiles_x, V.ranges,
+                                    V.seg_keys, V.seg_tmp, V.surfel_off, V.vals, V.emit, V.keys64,
+                                    V.capacity, s_keys);
+      __syncthreads();
+    }
   }
 }
 
@@ -493,6 +646,139 @@ int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
         p4, n, tx, bins->tile_ranges, w.long_list, w.n_long, w.seg_keys, w.seg_tmp,
         need_emit ? bins->surfel_off : nullptr, bins->vals, need_emit ? bins->isect_emit : nullptr,
         reinterpret_cast<unsigned long long*>(bins->keys), cap, gate);
+    GS2D_LAUNCH_CHECK();
+  }
+  return GS2D_OK;
+}
+
+// Raises a kernel's dynamic shared-memory limit once per device.
+cudaError_t smem_limit_ready(const void* fn, int bytes, bool* done_per_dev) {
+  static std::mutex mu;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= 0 && dev < 64 && done_per_dev[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done_per_dev[dev] = true;
+  return e;
+}
+
+size_t bin_sort_batch_view_bytes(int m, size_t capacity) {
+  return align_up(gs2d_bin_sort_workspace(m, capacity), 256);
+}
+
+size_t bin_sort_batch_bytes(const gs2d_view* views, int n_views, int n) {
+  if (!views || n_views <= 0 || n_views > GS2D_MAX_VIEWS || n < 0) return 0;
+  size_t total = kSortBatchHeader;
+  for (int v = 0; v < n_views; ++v) {
+    const int m = views[v].active ? views[v].n_active : n;
+    if (m < 0) return 0;
+    total += bin_sort_batch_view_bytes(m, views[v].bins.capacity);
+  }
+  return total;
+}
+
+int bin_sort_batch_launch(const gs2d_view* views, int n_views, int n, void* workspace,
+                          size_t ws_bytes, size_t* ws_needed, cudaStream_t st) {
+  if (!views || n_views <= 0 || n_views > GS2D_MAX_VIEWS || n < 0) return GS2D_ERR_INVALID_ARG;
+  const size_t need = bin_sort_batch_bytes(views, n_views, n);
+  if (need == 0) return GS2D_ERR_INVALID_ARG;
+  if (ws_needed) *ws_needed = need;
+  if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
+  SortTable T;
+  T.n_views = n_views;
+  T.count_total = T.chunk_total = T.scatter_total = T.tile_total = 0;
+  size_t count_smem = 0, scatter_smem = 0;
+  char* base = static_cast<char*>(workspace) + kSortBatchHeader;
+  for (int v = 0; v < n_views; ++v) {
+    const gs2d_view& x = views[v];
+    const gs2d_bins* bins = &x.bins;
+    const int m = x.active ? x.n_active : n;
+    // the checks of bin_sort_launch, per view
+    if (m > 0 && (!x.proj || !x.tiles_per_surfel)) return GS2D_ERR_INVALID_ARG;
+    if (!bins->vals || !bins->tile_ranges || !bins->n_isect || !bins->status)
+      return GS2D_ERR_INVALID_ARG;
+    const bool emit = bins->isect_emit || bins->surfel_off;
+    if (emit && (!bins->isect_emit || !bins->surfel_off)) return GS2D_ERR_INVALID_ARG;
+    if (bins->capacity >= (size_t)0x7FFFFFFF) return GS2D_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(x.proj) & 15) return GS2D_ERR_INVALID_ARG;
+    if (x.cfg.tile_w <= 0 || x.cfg.tile_h <= 0) return GS2D_ERR_INVALID_ARG;
+    const int tx = gs2d_tiles_x(&x.cam, &x.cfg), ty = gs2d_tiles_y(&x.cam, &x.cfg);
+    if (tx <= 0 || ty <= 0 || (long long)tx * ty > 65535) return GS2D_ERR_INVALID_ARG;
+    const int n_tiles = tx * ty;
+    const size_t bytes = bin_sort_batch_view_bytes(m, bins->capacity);
+    const SortWs w = carve_sort_ws(base, m, bins->capacity, n_tiles);
+    base += bytes;
+    SortViewDev& d = T.v[v];
+    d.proj = reinterpret_cast<const float4*>(x.proj);
+    d.tiles = x.tiles_per_surfel;
+    d.n = m;
+    d.tiles_x = tx;
+    d.n_tiles = n_tiles;
+    d.zero_begin = w.zero_begin;
+    d.zero_words = w.zero_words;
+    d.tile_count = w.tile_count;
+    d.cursor = w.cursor;
+    d.n_long = w.n_long;
+    d.long_list = w.long_list;
+    d.estatus = w.estatus;
+    d.seg_keys = w.seg_keys;
+    d.seg_tmp = w.seg_tmp;
+    d.ranges = bins->tile_ranges;
+    d.n_isect = bins->n_isect;
+    d.surfel_off = emit ? bins->surfel_off : nullptr;
+    d.vals = bins->vals;
+    d.emit = emit ? bins->isect_emit : nullptr;
+    d.keys64 = reinterpret_cast<unsigned long long*>(bins->keys);
+    d.capacity = (long long)bins->capacity;
+    d.gate = bins->status;
+    // the single-view launch shapes: count on at most 608 blocks, a scan
+    // block per 4096 surfels, a scatter block per 256, a sort block per tile
+    d.count0 = T.count_total;
+    d.count_blocks = m > 0 ? min((m + kScanThreads - 1) / kScanThreads, 152 * 4) : 0;
+    T.count_total += d.count_blocks;
+    d.chunk0 = T.chunk_total;
+    T.chunk_total += (m > 0 && emit) ? w.chunks_n : 0;
+    d.scatter0 = T.scatter_total;
+    T.scatter_total += m > 0 ? (m + 255) / 256 : 0;
+    d.tile0 = T.tile_total;
+    T.tile_total += m > 0 ? n_tiles : 0;
+    if (n_tiles <= kSmemTiles) {
+      count_smem = std::max(count_smem, (size_t)n_tiles * sizeof(uint32_t));
+      scatter_smem = std::max(scatter_smem, (size_t)2 * n_tiles * sizeof(uint32_t));
+    }
+  }
+  static bool ready_scatter[64] = {}, ready_long[64] = {};
+  const size_t sort_smem = (size_t)kSegSmem * sizeof(unsigned long long);
+  const size_t long_smem = (size_t)kLongChunk * sizeof(unsigned long long);
+  if (smem_limit_ready(reinterpret_cast<const void*>(scatter_batch_kernel), (int)(2 * kSmemTiles * 4),
+                       ready_scatter) != cudaSuccess ||
+      smem_limit_ready(reinterpret_cast<const void*>(tile_sort_long_batch_kernel), (int)long_smem,
+                       ready_long) != cudaSuccess)
+    return GS2D_ERR_CUDA;
+  uint32_t* batch_ticket = static_cast<uint32_t*>(workspace);
+  bin_init_batch_kernel<<<dim3(32, n_views), 256, 0, st>>>(T, batch_ticket);
+  GS2D_LAUNCH_CHECK();
+  if (T.count_total > 0) {
+    count_batch_kernel<<<T.count_total, kScanThreads, count_smem, st>>>(T);
+    GS2D_LAUNCH_CHECK();
+  }
+  if (T.chunk_total > 0) {
+    emit_scan_batch_kernel<<<T.chunk_total, kScanThreads, 0, st>>>(
+        T, batch_ticket, g_lookback_spins > 0 ? g_lookback_spins : kSpinLimit, g_lookback_withheld);
+    GS2D_LAUNCH_CHECK();
+  }
+  tile_scan_batch_kernel<<<n_views, 1024, 0, st>>>(T);
+  GS2D_LAUNCH_CHECK();
+  if (T.scatter_total > 0) {
+    scatter_batch_kernel<<<T.scatter_total, 256, scatter_smem, st>>>(T);
+    GS2D_LAUNCH_CHECK();
+  }
+  if (T.tile_total > 0) {
+    tile_sort_batch_kernel<<<T.tile_total, kSortThreads, sort_smem, st>>>(T);
+    GS2D_LAUNCH_CHECK();
+    tile_sort_long_batch_kernel<<<min(T.tile_total, 152), kLongThreads, long_smem, st>>>(T);
     GS2D_LAUNCH_CHECK();
   }
   return GS2D_OK;

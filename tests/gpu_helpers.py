@@ -120,3 +120,21 @@ def assert_images_close(gpu, orc, max_bad_frac=1e-4, min_bad=2, grazing_frac=1e-
         loose_bad |= v
     assert (loose_bad & grazing).sum() <= allow, report
     return report, ~bad_any
+
+
+def records_to_proj(torch, rect, depth, count):
+    """Projection records (device, PROJ_FLOATS per record) carrying only what
+    the binning reads: the tile rectangle and the centre depth; and the
+    per-record tile counts."""
+    from paper_2506_00970_gb300 import gs2d
+    n = len(depth)
+    proj = np.zeros((max(n, 1), gs2d.PROJ_FLOATS), np.float32)
+    if n:
+        proj[:n, 26] = depth
+        r01 = (rect[:, 0].astype(np.uint32) | (rect[:, 1].astype(np.uint32) << 16))
+        r23 = (rect[:, 2].astype(np.uint32) | (rect[:, 3].astype(np.uint32) << 16))
+        proj[:n, 28] = r01.view(np.float32)
+        proj[:n, 29] = r23.view(np.float32)
+    return (torch.tensor(proj.reshape(-1), device="cuda"),
+            torch.tensor(np.asarray(count, np.int32).reshape(-1) if n else np.zeros(1, np.int32),
+                         device="cuda"))

@@ -7,7 +7,7 @@ import pytest
 
 from paper_2506_00970_gb300 import scenes
 from gpu_helpers import (EDGE_ON_COS, GRAD_FLOOR, TOL_GRAD, assert_grads_close, gpu_render,
-                         to_np)
+                         records_to_proj, to_np)
 
 pytestmark = pytest.mark.gpu
 
@@ -134,6 +134,68 @@ def test_batch_backward_matches_oracle_sum(torch_cuda, orc):
     for v in range(len(cams)):
         seen[np.arange(s.n) if actives[v] is None else actives[v]] = True
     assert seen.all() or np.all(to_np(g["mu"])[~seen] == 0)
+
+
+def test_batch_binning_equals_per_view_binning(torch_cuda):
+    """gs2d_bin_sort_batch (one launch per stage over all views) gives every
+    view the bins gs2d_bin_sort gives it alone, bit for bit, on synthetic tile
+    records: views of several tile grids, one with more tiles than the
+    per-block shared-memory histograms hold (81 x 76), one whose four tiles
+    hold segments longer than a shared-memory sort (~6k and ~40k keys), one
+    with more surfels than a scan chunk (several look-back chunks), one
+    without emission arrays, and an empty one."""
+    torch = torch_cuda
+    from paper_2506_00970_gb300 import gs2d
+    specs = [(4097, 10, 8, 3, True), (20000, 81, 76, 4, True), (9000, 2, 2, 6, True),
+             (60000, 2, 2, 7, True), (1, 5, 4, 1, True), (7000, 12, 9, 8, False),
+             (0, 5, 4, 0, True)]
+    i32 = dict(dtype=torch.int32, device="cuda")
+    views, keep = [], []
+    for n, tx, ty, seed, emit in specs:
+        if n:
+            rect, depth, count = scenes.random_tile_records(seed, n, tx, ty)
+        else:
+            rect, depth, count = np.zeros((0, 4), np.int32), np.zeros(0, np.float32), np.zeros(0, np.int32)
+        proj, tiles = records_to_proj(torch, rect, depth, count)
+        cam = gs2d.camera(scenes.Camera(100.0, 100.0, 8.0, 8.0, tx * 16 - 5, ty * 16 - 3))
+        cfg = gs2d.default_config((16, 16))
+        cap = int(count.sum()) + 17
+        act = torch.arange(max(n, 1), **i32)
+
+        def bufs():
+            return dict(vals=torch.full((cap,), -7, **i32), emit=torch.full((cap,), -7, **i32),
+                        off=torch.full((max(n, 1),), -7, **i32),
+                        ranges=torch.full((2 * tx * ty,), -7, **i32),
+                        n_isect=torch.zeros(1, **i32), status=torch.zeros(1, **i32))
+
+        def mk_bins(o):
+            return gs2d.Bins(None, o["vals"].data_ptr(), o["emit"].data_ptr() if emit else None,
+                             o["off"].data_ptr() if emit else None, o["ranges"].data_ptr(),
+                             o["n_isect"].data_ptr(), o["status"].data_ptr(), cap)
+
+        batch, single = bufs(), bufs()
+        views.append(gs2d.View(cam, cfg, None, act.data_ptr(), n, proj.data_ptr(),
+                               tiles.data_ptr(), mk_bins(batch)))
+        keep.append((n, emit, cam, cfg, cap, proj, tiles, act, batch, single, mk_bins(single)))
+    arr = (gs2d.View * len(views))(*views)
+    ws = torch.empty(gs2d.lib().gs2d_bin_sort_batch_workspace(arr, len(views), 0),
+                     dtype=torch.uint8, device="cuda")
+    gs2d.gs2d_bin_sort_batch(views, 0, ws)
+    torch.cuda.synchronize()
+    for v, (n, emit, cam, cfg, cap, proj, tiles, act, batch, single, sb) in enumerate(keep):
+        w1 = torch.empty(gs2d.gs2d_bin_sort_workspace(n, cap), dtype=torch.uint8, device="cuda")
+        gs2d.gs2d_bin_sort(proj, tiles, n, cam, cfg, w1, sb)
+        torch.cuda.synchronize()
+        assert int(batch["status"].item()) == 0 and int(single["status"].item()) == 0, v
+        K = int(single["n_isect"].item())
+        assert int(batch["n_isect"].item()) == K and (K > 0 or n < 10), v
+        assert torch.equal(batch["ranges"], single["ranges"]), v
+        assert torch.equal(batch["vals"][:K], single["vals"][:K]), v
+        if emit:
+            assert torch.equal(batch["emit"][:K], single["emit"][:K]), v
+            assert torch.equal(batch["off"][:n], single["off"][:n]), v
+    r = keep[3][8]["ranges"].view(-1, 2)
+    assert int((r[:, 1] - r[:, 0]).max()) > 16384
 
 
 def test_batch_capacity_error_is_per_view(torch_cuda):

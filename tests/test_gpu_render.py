@@ -20,7 +20,8 @@ import numpy as np
 import pytest
 
 from paper_2506_00970_gb300 import scenes
-from gpu_helpers import assert_grads_close, assert_images_close, gpu_render, grad_rows_ok, to_np
+from gpu_helpers import (assert_grads_close, assert_images_close, gpu_render, grad_rows_ok,
+                         records_to_proj, to_np)
 
 pytestmark = pytest.mark.gpu
 
@@ -38,21 +39,6 @@ def torch_cuda():
 # ---------------------------------------------------------------------------
 # binning / sort
 # ---------------------------------------------------------------------------
-def _records_to_proj(torch, rect, depth, count):
-    from paper_2506_00970_gb300 import gs2d
-    n = len(depth)
-    proj = np.zeros((max(n, 1), gs2d.PROJ_FLOATS), np.float32)
-    if n:
-        proj[:n, 26] = depth
-        r01 = (rect[:, 0].astype(np.uint32) | (rect[:, 1].astype(np.uint32) << 16))
-        r23 = (rect[:, 2].astype(np.uint32) | (rect[:, 3].astype(np.uint32) << 16))
-        proj[:n, 28] = r01.view(np.float32)
-        proj[:n, 29] = r23.view(np.float32)
-    return (torch.tensor(proj.reshape(-1), device="cuda"),
-            torch.tensor(np.asarray(count, np.int32).reshape(-1) if n else np.zeros(1, np.int32),
-                         device="cuda"))
-
-
 @pytest.mark.parametrize("n,tiles_x,tiles_y,seed", [
     (0, 5, 4, 0), (1, 5, 4, 1), (7, 3, 2, 2), (4097, 10, 8, 3),
     (20000, 40, 30, 4), (150_000, 75, 43, 5),
@@ -68,7 +54,7 @@ def test_bin_sort_bit_exact(torch_cuda, orc, n, tiles_x, tiles_y, seed):
         rect = np.zeros((0, 4), np.int32)
         depth = np.zeros(0, np.float32)
         count = np.zeros(0, np.int32)
-    proj, tiles = _records_to_proj(torch, rect, depth, count)
+    proj, tiles = records_to_proj(torch, rect, depth, count)
     cam = scenes.Camera(100.0, 100.0, 8.0, 8.0, tiles_x * 16 - 5, tiles_y * 16 - 3)
     r = gs2d.Rasterizer(cam, n, capacity=int(count.sum()) + 17, keys=True)
     r.proj.copy_(proj[: r.proj.numel()]) if n else None
@@ -100,7 +86,7 @@ def test_bin_sort_capacity_overflow_reports_needed(torch_cuda, orc):
     torch = torch_cuda
     from paper_2506_00970_gb300 import gs2d
     rect, depth, count = scenes.random_tile_records(9, 3000, 12, 9)
-    proj, tiles = _records_to_proj(torch, rect, depth, count)
+    proj, tiles = records_to_proj(torch, rect, depth, count)
     cam = scenes.Camera(100.0, 100.0, 8.0, 8.0, 12 * 16, 9 * 16)
     r = gs2d.Rasterizer(cam, 3000, capacity=100)
     r.proj.copy_(proj)
