@@ -321,11 +321,15 @@ typedef struct {
 } gs2d_view;
 
 /* Projection of every view (one launch; record j of a view is surfel
- * active[j], or j).  Binning of every view: gs2d_bin_sort's stages, each one
- * launch over all views (the blocks of a stage split over the views; every
- * view has its own slice of the workspace after a 256-byte header, its own
- * counters and its own bins.status, which must be 0 on entry; the bins equal
- * gs2d_bin_sort's on the same view bit for bit).  The
+ * active[j], or j).  Binning of every view, equal to gs2d_bin_sort's on the
+ * same view bit for bit: up to 8 views each on its own side stream of the
+ * device (forked from and joined back to `stream` by events -- parallel
+ * branches when captured into a CUDA graph; the side streams are created by
+ * the first call with several views on each device, so make that call before
+ * any stream capture), more views in one launch per stage (the stage's blocks
+ * split over the views); every view has its own slice of the workspace
+ * after a 256-byte header, its own counters and its own bins.status, which
+ * must be 0 on entry.  The
  * forward pass of every view in one persistent launch.  The backward pass of
  * every view in one persistent launch, then the per-surfel reductions view by
  * view in a fixed order: d_* (device [n*3], [n*4], [n*2], [n], [n*3]) receive

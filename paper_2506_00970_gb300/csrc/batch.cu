@@ -7,7 +7,7 @@
 // by its arguments and can be captured in a CUDA graph.  The per-tile work is
 // the single-view code of tile_loops.cuh, so every view's images and partial
 // gradients equal those of the single-view entry points.
-
+#include <mutex>
 
 #include "bwd_warp.cuh"
 #include "gs2d_common.cuh"
@@ -262,6 +262,36 @@ int build_table(const gs2d_view* views, int n_views, const BatchWs* w, ViewTable
   return GS2D_OK;
 }
 
+// Side streams of one device for the binning of up to kSideStreams views:
+// each view's kernels go to its own non-blocking stream, forked from and
+// joined back to the caller's stream by events (parallel branches when
+// captured into a CUDA graph), so the stages of different views overlap.
+// More views bin in one launch per stage (bin_sort_batch_launch): sharing
+// streams, views would queue behind each other.  Created on the first
+// batched binning call with several views on the device.
+constexpr int kSideStreams = 8;
+struct SidePool {
+  bool ready = false;
+  cudaStream_t s[kSideStreams];
+  cudaEvent_t fork;
+  cudaEvent_t join[kSideStreams];
+};
+std::mutex g_side_mu;
+SidePool g_side[64];
+
+SidePool* side_pool(int dev) {
+  if (dev < 0 || dev >= 64) return nullptr;
+  SidePool& P = g_side[dev];
+  if (P.ready) return &P;
+  for (int k = 0; k < kSideStreams; ++k) {
+    if (cudaStreamCreateWithFlags(&P.s[k], cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&P.join[k], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+  }
+  if (cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+  P.ready = true;
+  return &P;
+}
+
 }  // namespace
 }  // namespace gs2d
 
@@ -275,8 +305,41 @@ size_t gs2d_bin_sort_batch_workspace(const gs2d_view* views, int n_views, int n)
 
 int gs2d_bin_sort_batch(const gs2d_view* views, int n_views, int n, void* workspace,
                         size_t ws_bytes, size_t* ws_needed, gs2d_stream stream) {
-  return bin_sort_batch_launch(views, n_views, n, workspace, ws_bytes, ws_needed,
-                               (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!views || n_views <= 0 || n_views > GS2D_MAX_VIEWS || n < 0) return GS2D_ERR_INVALID_ARG;
+  if (n_views > kSideStreams)
+    return bin_sort_batch_launch(views, n_views, n, workspace, ws_bytes, ws_needed, st);
+  // one view per side stream; the workspace layout is the batched launch's
+  const size_t need = bin_sort_batch_bytes(views, n_views, n);
+  if (need == 0) return GS2D_ERR_INVALID_ARG;
+  if (ws_needed) *ws_needed = need;
+  if (!workspace || ws_bytes < need) return GS2D_ERR_WORKSPACE;
+  int dev = 0;
+  GS2D_CUDA_TRY(cudaGetDevice(&dev));
+  // one host thread at a time enqueues on a device's side streams
+  std::lock_guard<std::mutex> lock(g_side_mu);
+  SidePool* P = n_views > 1 ? side_pool(dev) : nullptr;
+  if (n_views > 1 && !P) return GS2D_ERR_CUDA;
+  if (P) {
+    GS2D_CUDA_TRY(cudaEventRecord(P->fork, st));
+    for (int k = 0; k < n_views; ++k) GS2D_CUDA_TRY(cudaStreamWaitEvent(P->s[k], P->fork, 0));
+  }
+  char* base = static_cast<char*>(workspace) + bin_sort_batch_header();
+  int r = GS2D_OK;
+  for (int v = 0; v < n_views && r == GS2D_OK; ++v) {
+    const gs2d_view& w = views[v];
+    const int m = w.active ? w.n_active : n;
+    const size_t bytes = bin_sort_batch_view_bytes(m, w.bins.capacity);
+    r = gs2d_bin_sort(w.proj, w.tiles_per_surfel, m, &w.cam, &w.cfg, base, bytes, nullptr, &w.bins,
+                      (gs2d_stream)(P ? P->s[v] : st));
+    base += bytes;
+  }
+  if (P)  // join every branch back, also after an error
+    for (int k = 0; k < n_views; ++k) {
+      GS2D_CUDA_TRY(cudaEventRecord(P->join[k], P->s[k]));
+      GS2D_CUDA_TRY(cudaStreamWaitEvent(st, P->join[k], 0));
+    }
+  return r;
 }
 
 size_t gs2d_render_batch_workspace(const gs2d_view* views, int n_views, int n) {

@@ -54,6 +54,8 @@ constexpr unsigned kSortPreZeroed = 1u, kSortLongInBlock = 2u, kSortPreScanned =
 // Binning of several views, one launch per stage (sort.cu): the workspace
 // is a 256-byte header followed by each view's gs2d_bin_sort workspace.
 size_t bin_sort_batch_bytes(const gs2d_view* views, int n_views, int n);
+size_t bin_sort_batch_header();
+size_t bin_sort_batch_view_bytes(int m, size_t capacity);
 int bin_sort_batch_launch(const gs2d_view* views, int n_views, int n, void* workspace,
                           size_t ws_bytes, size_t* ws_needed, cudaStream_t st);
 int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,

@@ -463,19 +463,29 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_batch_kernel(const Sor
                  V.surfel_off, V.vals, V.emit, V.keys64, V.capacity, 0, s_keys);
 }
 
-// Every view's segments longer than kSegSmem, one per block of a small grid.
+// Every view's segments longer than kSegSmem, numbered across the views
+// (view-major) and taken one per block of a small grid in that numbering.
 __global__ void __launch_bounds__(kLongThreads) tile_sort_long_batch_kernel(const SortTable T) {
   extern __shared__ unsigned long long s_keys[];
-  for (int v = 0; v < T.n_views; ++v) {
-    const SortViewDev& V = T.v[v];
-    if (*V.gate) continue;
-    const int cnt = (int)*V.n_long;
-    for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
-      sort_long_segment<kLongChunk>((int)V.long_list[i], V.proj, V.n, V.tiles_x, V.ranges,
-                                    V.seg_keys, V.seg_tmp, V.surfel_off, V.vals, V.emit, V.keys64,
-                                    V.capacity, s_keys);
-      __syncthreads();
+  __shared__ int s_first[GS2D_MAX_VIEWS + 1];
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int v = 0; v < T.n_views; ++v) {
+      s_first[v] = acc;
+      acc += *T.v[v].gate ? 0 : (int)*T.v[v].n_long;
     }
+    s_first[T.n_views] = acc;
+  }
+  __syncthreads();
+  const int total = s_first[T.n_views];
+  int v = 0;
+  for (int g = blockIdx.x; g < total; g += gridDim.x) {
+    while (g >= s_first[v + 1]) ++v;
+    const SortViewDev& V = T.v[v];
+    sort_long_segment<kLongChunk>((int)V.long_list[g - s_first[v]], V.proj, V.n, V.tiles_x,
+                                  V.ranges, V.seg_keys, V.seg_tmp, V.surfel_off, V.vals, V.emit,
+                                  V.keys64, V.capacity, s_keys);
+    __syncthreads();
   }
 }
 
@@ -668,6 +678,8 @@ size_t bin_sort_batch_view_bytes(int m, size_t capacity) {
   return align_up(gs2d_bin_sort_workspace(m, capacity), 256);
 }
 
+size_t bin_sort_batch_header() { return kSortBatchHeader; }
+
 size_t bin_sort_batch_bytes(const gs2d_view* views, int n_views, int n) {
   if (!views || n_views <= 0 || n_views > GS2D_MAX_VIEWS || n < 0) return 0;
   size_t total = kSortBatchHeader;
@@ -733,10 +745,11 @@ int bin_sort_batch_launch(const gs2d_view* views, int n_views, int n, void* work
     d.keys64 = reinterpret_cast<unsigned long long*>(bins->keys);
     d.capacity = (long long)bins->capacity;
     d.gate = bins->status;
-    // the single-view launch shapes: count on at most 608 blocks, a scan
-    // block per 4096 surfels, a scatter block per 256, a sort block per tile
+    // the single-view launch shapes but for the counts (at most 152 blocks
+    // per view, fewer per-block histograms to flush): a scan block per 4096
+    // surfels, a scatter block per 256, a sort block per tile
     d.count0 = T.count_total;
-    d.count_blocks = m > 0 ? min((m + kScanThreads - 1) / kScanThreads, 152 * 4) : 0;
+    d.count_blocks = m > 0 ? min((m + kScanThreads - 1) / kScanThreads, 152) : 0;
     T.count_total += d.count_blocks;
     d.chunk0 = T.chunk_total;
     T.chunk_total += (m > 0 && emit) ? w.chunks_n : 0;
