@@ -9,6 +9,9 @@
            backward + per-surfel reductions)
   uneven   a batched step over 8 views of mixed resolution with active
            subsets of a 1M-surfel room
+  uneven32 the same over 32 views of a 2M-surfel room (active subsets of
+           50k-1M surfels: more views than side streams, so the binning runs
+           one launch per stage over all views)
   net      the proposal network at batch 256: forward, then forward + loss +
            backward (gs2d_net_grad) + AdamW
   sort     bin_sort of a 200k-surfel room at 160x120 (long tile segments)
@@ -106,6 +109,12 @@ def case_mapping(reps, px=1):
 def case_uneven(reps, px=1):
     s = scenes.room_scene(3, 1_000_000)
     cams, poses, actives = scenes.uneven_batch(4, s, 8, sizes=(50_000, 500_000))
+    return _batch(s, cams, poses, actives, reps, px)
+
+
+def case_uneven32(reps, px=1):
+    s = scenes.room_scene(3, 2_000_000)
+    cams, poses, actives = scenes.uneven_batch(4, s, 32)
     return _batch(s, cams, poses, actives, reps, px)
 
 
@@ -238,7 +247,8 @@ def case_proposal(reps, px=1):
     return _timed(g.replay, reps)
 
 
-CASES = {"track": case_track, "track_small": case_track_small, "mapping": case_mapping, "uneven": case_uneven, "net": case_net,
+CASES = {"track": case_track, "track_small": case_track_small, "mapping": case_mapping, "uneven": case_uneven,
+         "uneven32": case_uneven32, "net": case_net,
          "sort": case_sort, "contrib": case_contrib,
          "ssim": case_ssim, "map": case_map, "proposal": case_proposal}
 
