@@ -81,6 +81,33 @@ def test_invalid_arguments_rejected_without_launch(built_lib):
                              8, 8, 8, 8, 8, 8, None) == 1
 
 
+def test_bin_sort_batch_workspace_and_bad_views_on_the_host(built_lib):
+    """gs2d_bin_sort_batch's workspace is a 256-byte header plus each view's
+    gs2d_bin_sort workspace (256-byte aligned); view counts outside 1..32 and
+    a negative active count are rejected before anything is launched."""
+    from paper_2506_00970_gb300 import gs2d
+    L = gs2d.lib()
+    cam = gs2d.Camera(100.0, 100.0, 50.0, 30.0, 100, 60, 0.05)
+    cfg = gs2d.default_config()
+    sizes = [(1000, 5000), (0, 1024), (70_000, 400_000)]
+    views = (gs2d.View * len(sizes))()
+    for k, (m, cap) in enumerate(sizes):
+        bins = gs2d.Bins(None, 8, 8, 8, 8, 8, 8, cap)
+        views[k] = gs2d.View(cam, cfg, 8, 8, m, 16, 8, bins)
+    align = lambda b: (b + 255) // 256 * 256
+    want = 256 + sum(align(gs2d.gs2d_bin_sort_workspace(m, cap)) for m, cap in sizes)
+    assert L.gs2d_bin_sort_batch_workspace(views, len(sizes), 0) == want
+    assert L.gs2d_bin_sort_batch_workspace(views, 0, 0) == 0
+    assert L.gs2d_bin_sort_batch_workspace(views, 33, 0) == 0
+    need = ctypes.c_size_t(0)
+    assert L.gs2d_bin_sort_batch(views, len(sizes), 0, None, 0, ctypes.byref(need), None) == 2
+    assert need.value == want
+    assert L.gs2d_bin_sort_batch(views, 0, 0, 8, 1 << 30, None, None) == 1
+    views[1].n_active = -1
+    assert L.gs2d_bin_sort_batch_workspace(views, len(sizes), 0) == 0
+    assert L.gs2d_bin_sort_batch(views, len(sizes), 0, 8, 1 << 30, None, None) == 1
+
+
 def test_mapping_loss_batch_rejects_bad_views_without_launch(built_lib):
     """gs2d_mapping_loss_batch validates the view count, every pointer and
     every camera on the host; the workspace size is 0 for invalid views and
