@@ -94,6 +94,9 @@ __global__ void bin_init_kernel(uint32_t* __restrict__ zero_a, size_t n_a,
 
 // Per-block tile histograms live in shared memory when the tile grid fits.
 constexpr int kSmemTiles = 6144;  // 2 x 24 KB: the scatter's histogram + bases
+// dynamic shared memory the scatter kernel may take without raising its
+// limit: 48 KB less its static arrays (s_walk, s_key: 6 KB)
+constexpr size_t kScatterDefaultSmem = 48 * 1024 - 6 * 1024;
 
 // 1a. Tile counts: every covered tile's counter is incremented, through a
 // per-block shared-memory histogram (one global atomic per block and tile).
@@ -591,6 +594,19 @@ void sort_zero_region(void* workspace, int n, size_t capacity, int n_tiles, uint
   *words = w.zero_words;
 }
 
+// Raises a kernel's dynamic shared-memory limit once per device.
+cudaError_t smem_limit_ready(const void* fn, int bytes, bool* done_per_dev) {
+  static std::mutex mu;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= 0 && dev < 64 && done_per_dev[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done_per_dev[dev] = true;
+  return e;
+}
+
 int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
                     const gs2d_camera* cam, const gs2d_config* cfg, void* workspace,
                     size_t ws_bytes, size_t* ws_needed, const gs2d_bins* bins, bool need_emit,
@@ -637,6 +653,15 @@ int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
     GS2D_LAUNCH_CHECK();
   }
   if (n == 0) return GS2D_OK;
+  // two shared-memory histograms of more than ~5.4k tiles and the kernel's
+  // static arrays exceed the default 48 KB per block: raise the limit once
+  // per device (grids that fit never make the call, so captures of them are
+  // unaffected)
+  static bool scatter_ready[64] = {};
+  if (2 * hist_smem > kScatterDefaultSmem &&
+      smem_limit_ready(reinterpret_cast<const void*>(scatter_kernel), 2 * kSmemTiles * 4,
+                       scatter_ready) != cudaSuccess)
+    return GS2D_ERR_CUDA;
   scatter_kernel<<<(n + 255) / 256, 256, 2 * hist_smem, st>>>(
       p4, tiles_per_surfel, n, tx, n_tiles, bins->tile_ranges, w.cursor, w.seg_keys, cap, gate);
   GS2D_LAUNCH_CHECK();
@@ -659,19 +684,6 @@ int bin_sort_launch(const float* proj, const int32_t* tiles_per_surfel, int n,
     GS2D_LAUNCH_CHECK();
   }
   return GS2D_OK;
-}
-
-// Raises a kernel's dynamic shared-memory limit once per device.
-cudaError_t smem_limit_ready(const void* fn, int bytes, bool* done_per_dev) {
-  static std::mutex mu;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  std::lock_guard<std::mutex> lock(mu);
-  if (dev >= 0 && dev < 64 && done_per_dev[dev]) return cudaSuccess;
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess && dev >= 0 && dev < 64) done_per_dev[dev] = true;
-  return e;
 }
 
 size_t bin_sort_batch_view_bytes(int m, size_t capacity) {

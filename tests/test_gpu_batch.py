@@ -139,10 +139,11 @@ def test_batch_backward_matches_oracle_sum(torch_cuda, orc):
 @pytest.mark.parametrize("extra", [0, 5])
 def test_batch_binning_equals_per_view_binning(torch_cuda, extra):
     """gs2d_bin_sort_batch gives every view the bins gs2d_bin_sort gives it
-    alone, bit for bit, on synthetic tile records -- with 7 views (one side
-    stream each) and 12 (one launch per stage over all views): views of
+    alone, bit for bit, on synthetic tile records -- with 8 views (one side
+    stream each) and 13 (one launch per stage over all views): views of
     several tile grids, one with more tiles than the per-block shared-memory
-    histograms hold (81 x 76), two whose four tiles hold segments longer than
+    histograms hold (81 x 76), one whose histograms need more than 48 KB of
+    shared memory (80 x 68), two whose four tiles hold segments longer than
     a shared-memory sort (~6k and ~40k keys), several with more surfels than
     a scan chunk (several look-back chunks), one without emission arrays, and
     an empty one."""
@@ -150,7 +151,7 @@ def test_batch_binning_equals_per_view_binning(torch_cuda, extra):
     from paper_2506_00970_gb300 import gs2d
     specs = [(4097, 10, 8, 3, True), (20000, 81, 76, 4, True), (9000, 2, 2, 6, True),
              (60000, 2, 2, 7, True), (1, 5, 4, 1, True), (7000, 12, 9, 8, False),
-             (0, 5, 4, 0, True)]
+             (0, 5, 4, 0, True), (30000, 80, 68, 9, True)]
     specs += [(5000 + 3000 * k, 20 - k, 14, 20 + k, k % 2 == 0) for k in range(extra)]
     i32 = dict(dtype=torch.int32, device="cuda")
     views, keep = [], []

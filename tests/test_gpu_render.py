@@ -42,6 +42,9 @@ def torch_cuda():
 @pytest.mark.parametrize("n,tiles_x,tiles_y,seed", [
     (0, 5, 4, 0), (1, 5, 4, 1), (7, 3, 2, 2), (4097, 10, 8, 3),
     (20000, 40, 30, 4), (150_000, 75, 43, 5),
+    # a tile grid whose scatter histograms need more than the default
+    # 48 KB of shared memory per block (5440 tiles: 1280x1080 at 16x16)
+    (30000, 80, 68, 9),
     # long tile segments: ~6k keys (one shared-memory chunk of the long
     # path) and ~40k keys (three chunks, two merge passes) per tile
     (9000, 2, 2, 6), (60000, 2, 2, 7)])
